@@ -1,0 +1,89 @@
+"""Oracle: the linear-algebra building blocks of Sec. 2, in plain FP64.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+* ``null(M)``   -- orthonormal basis of the null space of a wide l x s matrix
+  (eq. null), taken as the trailing s-l columns of the complete Q of a
+  Householder QR of M^T (LAPACK through numpy, a library primitive).
+* ``pinv_right(Y, M)`` -- Y M^dagger for a wide full-row-rank M, through the
+  reduced QR of M^T: M^T = Q R gives M^dagger = Q R^-T (eq. pinvformula).
+* ``cpqr_id(M, k, tau)`` -- row interpolative decomposition of M (eq. id_def)
+  by column-pivoted Householder QR of M^T stopped after k steps (Sec. 2.3:
+  "standard pivoted QR with a greedy approach").  Column norms are recomputed
+  from scratch every step; an exact tie goes to the lowest original column.
+  T = R11^-1 R12, with the rows from the first numerically dependent pivot
+  (|R_jj| < tau |R_00|) on set to zero (truncated back-substitution).
+* ``lu`` -- LU with partial pivoting (LAPACK getrf via scipy).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+
+
+def null(m: np.ndarray) -> np.ndarray:
+    l, s = m.shape
+    if l >= s:
+        raise ValueError("null space needs more columns than rows")
+    q, _ = np.linalg.qr(m.T, mode="complete")
+    return q[:, l:]
+
+
+def pinv_right(y: np.ndarray, m: np.ndarray) -> np.ndarray:
+    """y @ pinv(m) for m (l x s, l <= s) of full row rank."""
+    q, r = np.linalg.qr(m.T, mode="reduced")
+    # y Q R^-T = (R^-1 (y Q)^T)^T
+    return sla.solve_triangular(r, (y @ q).T, lower=False).T
+
+
+def cpqr_id(m: np.ndarray, k: int, tau: float):
+    """Row ID of m (b x c): returns (skel, red, T) with m[red] ~= T^T m[skel].
+
+    skel: k row indices in pivot order; red: the other rows, ascending;
+    T: k x (b-k) interpolation matrix.
+    """
+    a = np.array(m.T, dtype=np.float64, copy=True)  # c x b: pivot over columns = rows of m
+    c, b = a.shape
+    perm = np.arange(b)
+    for j in range(k):
+        norms = np.sqrt(np.sum(a[j:, j:] ** 2, axis=0))
+        best = norms.max()
+        cand = np.nonzero(norms == best)[0]
+        p = j + cand[np.argmin(perm[j + cand])]
+        if p != j:
+            a[:, [j, p]] = a[:, [p, j]]
+            perm[[j, p]] = perm[[p, j]]
+        x = a[j:, j]
+        alpha = np.linalg.norm(x)
+        if alpha == 0.0:
+            continue
+        sign = 1.0 if x[0] >= 0 else -1.0
+        v = x.copy()
+        v[0] += sign * alpha
+        v /= np.linalg.norm(v)
+        a[j:, j:] -= 2.0 * np.outer(v, v @ a[j:, j:])
+    r11 = np.triu(a[:k, :k])
+    r12 = a[:k, k:]
+    diag = np.abs(np.diag(r11))
+    j0 = k
+    if k > 0:
+        small = np.nonzero(diag < tau * diag[0])[0]
+        if len(small):
+            j0 = int(small[0])
+    t = np.zeros((k, b - k))
+    if j0 > 0:
+        t[:j0] = sla.solve_triangular(r11[:j0, :j0], r12[:j0], lower=False)
+    skel = perm[:k].copy()
+    red = np.sort(perm[k:])
+    # columns of t follow perm[k:]; reorder them to ascending red
+    order = np.argsort(perm[k:])
+    t = t[:, order]
+    return skel, red, t
+
+
+def lu(a: np.ndarray):
+    return sla.lu_factor(a)
+
+
+def lu_solve(f, rhs: np.ndarray, trans: int = 0) -> np.ndarray:
+    return sla.lu_solve(f, rhs, trans=trans)

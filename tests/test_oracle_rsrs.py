@@ -1,0 +1,213 @@
+"""Whole-pipeline pins for the oracle's Algorithm 1, factorization, solve and refinement."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import linalg as la
+from oracle import operators as ops
+from oracle import refine, rsrs
+from oracle.tree import Schedule, Tree
+
+
+def _dense_h2(tr, r, seed=11):
+    """A = D + U V^T: D block-diagonal by leaf box, U, V Gaussian N x r (every off-box block has rank r)."""
+    rng = np.random.default_rng(seed)
+    n = tr.n
+    a = np.zeros((n, n))
+    for b in tr.boxes:
+        if b.is_leaf:
+            m = len(b.pts)
+            a[np.ix_(b.pts, b.pts)] = 2.0 * np.eye(m) + 0.3 * rng.standard_normal((m, m)) / np.sqrt(m)
+    u = rng.standard_normal((n, r)) / np.sqrt(n)
+    v = rng.standard_normal((n, r)) / np.sqrt(n)
+    return a + u @ v.T
+
+
+class DenseOp:
+    def __init__(self, a):
+        self.a = a
+        self.n = a.shape[0]
+
+    def matvec(self, x, adjoint=False):
+        return (self.a.T if adjoint else self.a) @ x
+
+
+def _run_dense(tr, a, k, s=None, seed=12, trace=None):
+    sc = Schedule(tr, k)
+    s = sc.s_req if s is None else s
+    rng = np.random.default_rng(seed)
+    om = rng.standard_normal((tr.n, s))
+    ps = rng.standard_normal((tr.n, s))
+    fac = rsrs.factor(tr, sc, a @ om, a.T @ ps, om, ps, trace=trace)
+    return sc, fac, (om, ps)
+
+
+def _dense_of(fn, fac, n):
+    return fn(fac, np.eye(n))
+
+
+def test_exact_h2_matrix_is_reproduced_to_rounding():
+    """P6: with every off-box block of rank r (and 2r < k), RSRS is exact to rounding."""
+    tr = Tree(W.grid_points_2d(24), 16)
+    a = _dense_h2(tr, r=3)
+    trace = []
+    sc, fac, _ = _run_dense(tr, a, k=8, trace=trace)
+    assert len(fac.boxes) > 10 and tr.depth >= 3
+    aa = _dense_of(rsrs.apply, fac, tr.n)
+    rel = np.linalg.norm(aa - a, 2) / np.linalg.norm(a, 2)
+    assert rel < 1e-12
+    ai = _dense_of(rsrs.solve, fac, tr.n)
+    es = np.linalg.norm(np.eye(tr.n) - ai @ a, 2)
+    assert es < 1e-11 * np.linalg.cond(a)
+    # the dependent pivots beyond rank 2r were truncated
+    assert any(np.abs(bf.T[6:]).max() == 0.0 for bf in fac.boxes if bf.T.shape[0] == 8)
+    # diagonalization: V^-1 A W^-1 equals P D P^T (eq. diag_sys) to rounding
+    at = rsrs.sweep_inv(fac, rsrs.sweep_inv(fac, a.T, adjoint=True).T)  # V^-1 A W^-1
+    d = np.zeros_like(a)
+    for bf in fac.boxes:
+        d[np.ix_(bf.R, bf.R)] = bf.XRR
+    d[np.ix_(fac.root, fac.root)] = fac.root_A
+    assert np.abs(at - d).max() < 1e-12 * np.abs(a).max()
+
+
+def test_exact_h2_matrix_3d():
+    """P6 on an octree over random 3D points."""
+    tr = Tree(W.uniform_points(1024, 3, W.rng_for(90, 0, 0)), 16)
+    a = _dense_h2(tr, r=3)
+    sc, fac, _ = _run_dense(tr, a, k=8)
+    aa = _dense_of(rsrs.apply, fac, tr.n)
+    assert np.linalg.norm(aa - a, 2) / np.linalg.norm(a, 2) < 1e-11
+
+
+def test_extraction_is_exact_when_far_field_vanishes():
+    """P5 (eq. pinvformula): for the first box, X blocks equal the entries of E A F."""
+    tr = Tree(W.grid_points_2d(24), 16)
+    a = _dense_h2(tr, r=3)
+    trace = []
+    _run_dense(tr, a, k=8, trace=trace)
+    bf = trace[0]["box"]
+    R, S, N, T = bf.R, bf.S, bf.N, bf.T
+    ix = np.ix_
+    x_rr = (a[ix(R, R)] - T.T @ a[ix(S, R)]) - (a[ix(R, S)] - T.T @ a[ix(S, S)]) @ T
+    x_rs = a[ix(R, S)] - T.T @ a[ix(S, S)]
+    x_rn = a[ix(R, N)] - T.T @ a[ix(S, N)]
+    x_sr = a[ix(S, R)] - a[ix(S, S)] @ T
+    x_nr = a[ix(N, R)] - a[ix(N, S)] @ T
+    sc = np.abs(a).max()
+    assert np.abs(bf.XRR - x_rr).max() < 1e-12 * sc
+    assert np.abs(bf.UcS - np.linalg.solve(x_rr, x_rs)).max() < 1e-11
+    assert np.abs(bf.UcN - np.linalg.solve(x_rr, x_rn)).max() < 1e-11
+    assert np.abs(bf.LcS - x_sr @ np.linalg.inv(x_rr)).max() < 1e-11
+    assert np.abs(bf.LcN - x_nr @ np.linalg.inv(x_rr)).max() < 1e-11
+    # the Y-side and Z-side estimates of X_RR agree
+    assert np.abs(bf.XRR - bf.XRR_z).max() < 1e-12 * sc
+
+
+def test_nullification_isolates_far_field_at_leaf_level():
+    """P4 (eq. nullformula): Y_B null([Om_B; Om_N]) = A_BF Om_F null(...) for a leaf-level box."""
+    pr = W.small_problem(n_side=24, leaf=16, k=8)
+    trace = []
+    tr, sc, fac, (Y, Z, om, ps) = rsrs.build(pr, trace=trace)
+    a = ops.make_operator(pr).dense()
+    bf = trace[0]["box"]
+    bn = np.concatenate([bf.B, bf.N])
+    far = np.setdiff1d(np.arange(pr.n), bn)
+    nw = la.null(om[bn])
+    ref = a[np.ix_(bf.B, far)] @ om[far] @ nw
+    assert np.abs(trace[0]["Yp"] - ref).max() < 1e-13 * np.abs(Y).max()
+    assert np.linalg.norm(ref) > 1e-3 * np.linalg.norm(Y[bf.B])  # the far field is not empty
+
+
+def test_sketch_pair_invariant():
+    """P1 (Sec. 1.1, eqs. updateVW_*): updated sketches stay sample pairs of the diagonalized matrix."""
+    pr = W.small_problem(n_side=24, leaf=16, k=8)
+    tr, sc, fac, (Y, Z, om, ps) = rsrs.build(pr)
+    a = ops.make_operator(pr).dense()
+    fin = fac.final
+    winv_omt = rsrs.sweep_inv_down(fac, fin["Om"])  # W^-1 Om~ = Om
+    assert np.abs(winv_omt - om).max() < 1e-12 * np.abs(om).max()
+    at = rsrs.sweep_inv(fac, rsrs.sweep_inv(fac, a.T, adjoint=True).T)  # V^-1 A W^-1
+    assert np.abs(fin["Y"] - at @ fin["Om"]).max() < 1e-12 * np.abs(Y).max()
+    assert np.abs(fin["Z"] - at.T @ fin["Ps"]).max() < 1e-12 * np.abs(Z).max()
+
+
+@pytest.mark.parametrize("case", ["grid2d", "rand3d"])
+def test_brute_force_against_dense_lu(case):
+    """P7: solve vs numpy dense LU; eq. (err_solve_cond); errors fall with k."""
+    if case == "grid2d":
+        mk = lambda k: W.small_problem(n_side=32, leaf=16, k=k)
+        ks = [4, 8, 12]
+    else:
+        # a 1024-point octree is too shallow for the error to fall monotonically in k;
+        # here only the bound of eq. (err_solve_cond) is checked
+        mk = lambda k: W.small_problem(n=1024, d=3, kernel="invr3d", leaf=16, k=k)
+        ks = [4, 8]
+    rel, es = [], []
+    for k in ks:
+        pr = mk(k)
+        tr, sc, fac, _ = rsrs.build(pr)
+        a = ops.make_operator(pr).dense()
+        aa = _dense_of(rsrs.apply, fac, pr.n)
+        eps = np.linalg.norm(a - aa, 2) / np.linalg.norm(a, 2)
+        cond = np.linalg.cond(a)
+        b = pr.rhs()
+        x = np.linalg.solve(a, b)
+        xt = rsrs.solve(fac, b)
+        fe = np.linalg.norm(x - xt) / np.linalg.norm(x)
+        if eps * cond < 1:
+            assert fe <= refine.solve_error_bound(eps, cond)
+        rel.append(eps)
+        es.append(np.linalg.norm(np.eye(pr.n) - _dense_of(rsrs.solve, fac, pr.n) @ a, 2))
+    if case == "grid2d":
+        assert all(r1 > r2 for r1, r2 in zip(rel, rel[1:]))
+        assert all(e1 > e2 for e1, e2 in zip(es, es[1:]))
+    assert max(rel) < 0.1
+
+
+def test_apply_solve_inverse_and_adjoints():
+    """P2: apply and solve are exact inverses; adjoint sweeps are the transposes."""
+    pr = W.small_problem(n_side=24, leaf=16, k=8)
+    tr, sc, fac, _ = rsrs.build(pr)
+    rng = np.random.default_rng(6)
+    f = rng.standard_normal((pr.n, 3))
+    g = rng.standard_normal((pr.n, 3))
+    for adj in (False, True):
+        assert np.abs(rsrs.apply(fac, rsrs.solve(fac, f, adj), adj) - f).max() < 1e-12
+        assert np.abs(rsrs.solve(fac, rsrs.apply(fac, f, adj), adj) - f).max() < 1e-12
+    for fn in (rsrs.apply, rsrs.solve):
+        lhs = np.sum(fn(fac, f) * g)
+        rhs = np.sum(f * fn(fac, g, True))
+        assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_refinement_reaches_dense_solution():
+    """P10: FP64 refinement with the factor as preconditioner reaches the dense LU solution."""
+    pr = W.small_problem(n_side=32, leaf=16, k=6)
+    tr, sc, fac, _ = rsrs.build(pr)
+    op = ops.make_operator(pr)
+    b = pr.rhs()
+    x, hist = refine.refine(fac, op, b, rtol=1e-13)
+    assert hist[-1] <= 1e-13 and len(hist) >= 3
+    assert all(h1 > h2 for h1, h2 in zip(hist, hist[1:]))
+    xd = np.linalg.solve(op.dense(), b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-12
+
+
+def test_undersampled_is_refused():
+    pr = W.small_problem(n_side=24, leaf=16, k=8)
+    tr = Tree(pr.points, pr.leaf)
+    sc = Schedule(tr, 8)
+    with pytest.raises(ValueError):
+        rsrs.build(pr, s=sc.s_req - 1)
+
+
+def test_power_iteration_metrics_match_dense_norms():
+    pr = W.small_problem(n_side=24, leaf=16, k=6)
+    tr, sc, fac, _ = rsrs.build(pr)
+    op = ops.make_operator(pr)
+    a = op.dense()
+    aa = _dense_of(rsrs.apply, fac, pr.n)
+    rel_dense = np.linalg.norm(a - aa, 2) / np.linalg.norm(a, 2)
+    es_dense = np.linalg.norm(np.eye(pr.n) - _dense_of(rsrs.solve, fac, pr.n) @ a, 2)
+    assert 0.5 * rel_dense <= refine.relerr(fac, op, iters=60) <= 1.01 * rel_dense
+    assert 0.5 * es_dense <= refine.errsolve(fac, op, iters=60) <= 1.0001 * es_dense
