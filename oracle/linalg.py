@@ -12,7 +12,8 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
   "standard pivoted QR with a greedy approach").  Column norms are recomputed
   from scratch every step; an exact tie goes to the lowest original column.
   T = R11^-1 R12, with the rows from the first numerically dependent pivot
-  (|R_jj| < tau |R_00|) on set to zero (truncated back-substitution).
+  (|R_jj| <= tau |R_00|, so an all-zero sketch gives T = 0) on set to zero
+  (truncated back-substitution).
 * ``lu`` -- LU with partial pivoting (LAPACK getrf via scipy).
 """
 from __future__ import annotations
@@ -67,7 +68,7 @@ def cpqr_id(m: np.ndarray, k: int, tau: float):
     diag = np.abs(np.diag(r11))
     j0 = k
     if k > 0:
-        small = np.nonzero(diag < tau * diag[0])[0]
+        small = np.nonzero(diag <= tau * diag[0])[0]
         if len(small):
             j0 = int(small[0])
     t = np.zeros((k, b - k))
