@@ -1,0 +1,194 @@
+/*
+ * rsrs.h -- C ABI of the GB300 (sm_103a) implementation of randomized strong
+ * recursive skeletonization (RSRS), Yesypenko & Martinsson, arXiv 2311.01451.
+ *
+ * The library follows the paper's statement of the problem (Sec. 1 and
+ * Algorithm 1): given a matrix A reachable through products with A and A*,
+ * points x_i in R^d with a quad/octree over them, a rank k and a sample count s,
+ * it draws (or takes) Gaussian test matrices Omega, Psi (N x s), forms the
+ * sketches Y = A Omega, Z = A* Psi (eq. rand_sample_setting), and post-processes
+ * them level by level into the invertible factorization
+ *     A ~ V_1 ... V_M P D P^T W_M ... W_1            (eq. Afact)
+ * whose inverse gives a direct solver / preconditioner (eq. Ainvfact).
+ *
+ * Conventions for every entry point:
+ *  - Every function returns rsrs_status; 0 (RSRS_OK) is success.  The library
+ *    never aborts, exits or traps.  Invalid arguments are rejected before any
+ *    device work (RSRS_E_INVAL); conditions found on the device (a zero or
+ *    non-finite pivot) are reported after the call's stream synchronises.
+ *  - "stream" is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream.  Calls synchronise that stream before they return.
+ *  - Device pointers ("_dev") are CUDA device memory owned by the caller, read
+ *    during the call or overwritten in place where stated.  Host pointers
+ *    ("_host") are read during the call only.
+ *  - Right-hand-side blocks are column-major N x nrhs with leading dimension
+ *    ld >= N, indexed by ORIGINAL point number; the library permutes internally.
+ *  - Trees and factors are opaque and library-owned until freed.
+ */
+#ifndef RSRS_H
+#define RSRS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RSRS_OK = 0,
+  RSRS_E_INVAL = 1,         /* bad argument (null pointer, size, layout)           */
+  RSRS_E_UNDERSAMPLED = 2,  /* s below the sample bound of Sec. 4.4 (see s_req)     */
+  RSRS_E_SINGULAR = 3,      /* zero pivot in the LU of an X_RR block or the root    */
+  RSRS_E_NONFINITE = 4,     /* NaN/Inf met in a sketch, a Gram or a pivot           */
+  RSRS_E_NOMEM = 5,         /* device allocation failed                             */
+  RSRS_E_CUDA = 6,          /* a CUDA runtime call failed                           */
+  RSRS_E_CALLBACK = 7,      /* the user matvec callback returned non-zero           */
+  RSRS_E_TIMEOUT = 8,       /* a bounded device wait ran out                        */
+  RSRS_E_NOT_CONVERGED = 9  /* refinement stopped at maxit above rtol               */
+} rsrs_status;
+
+typedef struct rsrs_tree rsrs_tree;
+typedef struct rsrs_factor rsrs_factor;
+
+/* Operator kinds.  Built-in kernels are A = diag_shift*I + scale*K with
+ * K_ij = log|x_i - x_j| (2D) or 1/|x_i - x_j| (3D) for i != j and K_ii = 0,
+ * evaluated on the fly on the device (symmetric, so A* = A). */
+enum { RSRS_OP_LOG2D = 1, RSRS_OP_INVR3D = 2, RSRS_OP_CALLBACK = 3 };
+
+/* User matvec: Y = A X (adjoint = 0) or Y = A* X (adjoint = 1), all device
+ * memory, column-major n x ncols with leading dimensions ldx, ldy, rows in
+ * ORIGINAL point order.  It must enqueue its work on `stream` only and return
+ * 0 on success; any other value aborts the call with RSRS_E_CALLBACK. */
+typedef int (*rsrs_matvec_fn)(void* ctx, int adjoint, int64_t n, int32_t ncols,
+                              const double* X_dev, int64_t ldx, double* Y_dev,
+                              int64_t ldy, void* stream);
+
+typedef struct {
+  int kind;            /* RSRS_OP_*                                            */
+  double diag_shift;   /* built-in kernels: A = diag_shift*I + scale*K           */
+  double scale;
+  rsrs_matvec_fn fn;   /* RSRS_OP_CALLBACK only                                  */
+  void* ctx;
+} rsrs_operator;
+
+/* Arithmetic of the build and of the factor. */
+enum {
+  RSRS_PREC_FP64 = 0,   /* every step in FP64                                               */
+  RSRS_PREC_MIXED = 1   /* sampling and Schur updates in FP32 SIMT; ID, LU, nullification,   */
+                        /* extraction and the refinement residual in FP64                   */
+};
+
+typedef struct {
+  int precision;          /* RSRS_PREC_*                                               */
+  int p;                  /* oversampling; < 0 selects p = k (Sec. 5)                  */
+  int proj_passes;        /* projection passes of the nullification (1 or 2; 0 -> 2)   */
+  uint64_t seed;          /* used only when omega/psi are NULL                         */
+  const double* omega_host; /* optional caller test matrices, row-major N x s in        */
+  const double* psi_host;   /* ORIGINAL point order (point i's samples contiguous)      */
+  int keep_sketches;      /* keep the final Y, Z, Omega, Psi on the device (tests)     */
+} rsrs_options;
+
+typedef struct {
+  int d;                  /* dimension of the points                                  */
+  int depth;              /* deepest level L of the tree                              */
+  int64_t n;              /* number of points                                         */
+  int64_t n_boxes;        /* boxes in the tree                                        */
+  int64_t n_leaves;
+  int64_t n_compress;     /* boxes compressed by Algorithm 1 for this k               */
+  int64_t n_groups;       /* (level, colour) groups = launches per step                */
+  int64_t max_l;          /* largest |B_act| + |N_act| at processing time             */
+  int64_t root_size;      /* |B_t|                                                    */
+  int64_t s_req;          /* smallest admissible s: max(max_l + k + p, |B_t|)         */
+} rsrs_tree_info_t;
+
+typedef struct {
+  int64_t n, s, k;
+  int64_t n_boxes;        /* compressed boxes (factor blocks)                         */
+  int64_t root_size;
+  int64_t factor_bytes;   /* device bytes held by the factor                          */
+  int64_t work_bytes;     /* peak device workspace of the build                       */
+  double t_sample_ms, t_compress_ms, t_root_ms;  /* stream-event timings of the build */
+  int64_t kernel_launches; /* kernels launched by the last build                     */
+} rsrs_stats;
+
+typedef struct {
+  int iterations;         /* corrections applied after the first solve                */
+  double rel_residual;    /* final max over columns of ||b - A x|| / ||b||            */
+  double history[64];     /* relative residual after each step                        */
+} rsrs_refine_report;
+
+/* ---- tree (Sec. 3: quad/octree, adjacency, 2:1 balance) --------------------
+ * pts_host: n x d row-major doubles.  leaf_cap: at most leaf_cap points per
+ * leaf.  d must be 2 or 3. */
+rsrs_status rsrs_tree_build(const double* pts_host, int64_t n, int d, int leaf_cap,
+                            rsrs_tree** out);
+/* Sizes of Algorithm 1 on this tree for rank k and oversampling p (p < 0: p = k),
+ * including the sample bound of Sec. 4.4 (s_req). */
+rsrs_status rsrs_tree_info(const rsrs_tree* tree, int k, int p, rsrs_tree_info_t* out);
+/* perm_host[t] = original index of the point at tree position t (n entries). */
+rsrs_status rsrs_tree_perm(const rsrs_tree* tree, int64_t* perm_host);
+/* Per-level schedule dump for tests: for every compressed box in processing
+ * order, 6 int64 values (level, colour, morton key, b, n, first tree position).
+ * rows_host must hold 6*n_compress values. */
+rsrs_status rsrs_tree_schedule(const rsrs_tree* tree, int k, int p, int64_t* rows_host);
+void rsrs_tree_free(rsrs_tree* tree);
+
+/* ---- factorization (Algorithm 1) ----------------------------------------------
+ * Draws Omega, Psi (or copies opts->omega_host/psi_host), samples Y, Z with the
+ * operator, and runs Algorithm 1 on the device.  Returns RSRS_E_UNDERSAMPLED
+ * (before any device work) when s < s_req. */
+rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, int s,
+                       const rsrs_options* opts, void* stream, rsrs_factor** out);
+
+/* F <- A_approx^-1 F (eq. Ainvfact), or its adjoint; F_dev column-major N x nrhs. */
+rsrs_status rsrs_solve(const rsrs_factor* f, double* F_dev, int64_t ldf, int32_t nrhs,
+                       int adjoint, void* stream);
+/* F <- A_approx F (eq. Afact), or its adjoint. */
+rsrs_status rsrs_apply(const rsrs_factor* f, double* F_dev, int64_t ldf, int32_t nrhs,
+                       int adjoint, void* stream);
+/* FP64 iterative refinement: X = A_approx^-1 B, then X += A_approx^-1 (B - A X)
+ * with the FP64 residual of the operator the factor was built from, until
+ * max_j ||B_j - A X_j|| / ||B_j|| <= rtol or maxit corrections. */
+rsrs_status rsrs_refine(const rsrs_factor* f, const double* B_dev, double* X_dev, int64_t ld,
+                        int32_t nrhs, double rtol, int maxit, void* stream,
+                        rsrs_refine_report* out);
+/* Y = A X with the factor's operator in FP64 (the residual product of rsrs_refine). */
+rsrs_status rsrs_matvec(const rsrs_factor* f, const double* X_dev, double* Y_dev, int64_t ld,
+                        int32_t nrhs, void* stream);
+
+rsrs_status rsrs_factor_stats(const rsrs_factor* f, rsrs_stats* out);
+
+/* Host copy of one compressed box's factor block, for parity tests.  Index
+ * lists are ORIGINAL point numbers; matrices are row-major.  Call with NULL
+ * buffers to get the sizes (b, n, kp, r) first. */
+typedef struct {
+  int32_t level, colour;
+  int64_t b, n, kp, r;
+  int64_t* S;       /* kp  skeletons, pivot order                               */
+  int64_t* R;       /* r   redundant, tree order                                */
+  int64_t* N;       /* n   active neighbours, tree order                        */
+  double* T;        /* kp x r                                                   */
+  double* XRR;      /* r x r (as extracted, before factorization)               */
+  double* LcS;      /* kp x r   X_SR X_RR^-1                                    */
+  double* LcN;      /* n  x r   X_NR X_RR^-1                                    */
+  double* UcS;      /* r  x kp  X_RR^-1 X_RS                                    */
+  double* UcN;      /* r  x n   X_RR^-1 X_RN                                    */
+} rsrs_box_view;
+rsrs_status rsrs_factor_box(const rsrs_factor* f, int64_t i, rsrs_box_view* v);
+/* Root block: indices (original numbering, tree order) and the dense r x r
+ * extracted matrix, row-major.  Either buffer may be NULL. */
+rsrs_status rsrs_factor_root(const rsrs_factor* f, int64_t* idx_host, double* A_host,
+                             int64_t* size_out);
+/* Final sketches (requires keep_sketches): row-major N x s, original order. */
+rsrs_status rsrs_factor_sketches(const rsrs_factor* f, double* Y_host, double* Z_host,
+                                 double* Om_host, double* Ps_host);
+
+void rsrs_factor_free(rsrs_factor* f);
+const char* rsrs_status_string(rsrs_status st);
+/* Message of the last failed call on this thread (empty string if none). */
+const char* rsrs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RSRS_H */

@@ -1,0 +1,148 @@
+// Internal declarations shared by the CUDA translation units of librsrs.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/rsrs.h"
+#include "tree.h"
+
+namespace rsrs {
+
+// Device error word: set (first writer wins) by kernels that meet a bad pivot.
+enum DevErr : int { kDevOk = 0, kDevSingular = 1, kDevNonfinite = 2 };
+
+// One compressed box of a (level, colour) group, as the device kernels see it.
+// All offsets are element offsets into the buffers named in the comments.
+struct BoxDesc {
+  int32_t b, n, l, kp, r, pad_;
+  int64_t bn_off;   // int32 work: l tree positions [B_act | N_act]
+  int64_t g_off;    // double work: two l x l Grams (Omega side, then Psi side)
+  int64_t x_off;    // double work: two b x l least-squares coefficient blocks (Y, Z)
+  int64_t x2_off;   // double work: two b x l second-pass blocks
+  int64_t m_off;    // double work: b x 2s projected sketches [Y' | Z']
+  int64_t cp_off;   // double work: CPQR R rows, kp x b; then extraction blocks 2 x r x l
+  int64_t pv_off;   // int32 work: b CPQR local permutation
+  int64_t fi_off;   // int32 factor: R (r), S (kp), N (n), LU pivots (r)
+  int64_t fd_off;   // double factor: T (kp x r), XRR (r x r), LU (r x r), LcT (r x (kp+n)), Uc (r x (kp+n))
+  int64_t act_off;  // int32 active-list pool slot of the box
+};
+
+// Offsets inside a box's factor blocks.
+__host__ __device__ inline int64_t fd_T(const BoxDesc& d) { return d.fd_off; }
+__host__ __device__ inline int64_t fd_XRR(const BoxDesc& d) { return d.fd_off + (int64_t)d.kp * d.r; }
+__host__ __device__ inline int64_t fd_LU(const BoxDesc& d) { return fd_XRR(d) + (int64_t)d.r * d.r; }
+__host__ __device__ inline int64_t fd_LcT(const BoxDesc& d) { return fd_LU(d) + (int64_t)d.r * d.r; }
+__host__ __device__ inline int64_t fd_Uc(const BoxDesc& d) { return fd_LcT(d) + (int64_t)d.r * (d.kp + d.n); }
+__host__ __device__ inline int64_t fd_size(int64_t kp, int64_t r, int64_t n) {
+  return kp * r + 2 * r * r + 2 * r * (kp + n);
+}
+__host__ __device__ inline int64_t fi_R(const BoxDesc& d) { return d.fi_off; }
+__host__ __device__ inline int64_t fi_S(const BoxDesc& d) { return d.fi_off + d.r; }   // S then N: the "SN" list
+__host__ __device__ inline int64_t fi_N(const BoxDesc& d) { return d.fi_off + d.r + d.kp; }
+__host__ __device__ inline int64_t fi_piv(const BoxDesc& d) { return d.fi_off + d.r + d.kp + d.n; }
+__host__ __device__ inline int64_t fi_size(int64_t kp, int64_t r, int64_t n) { return 2 * r + kp + n; }
+
+// Segment copy of int32 lists (active-list assembly, neighbour gathers).
+struct Seg {
+  int64_t src, dst, len;
+};
+
+// ---- launch wrappers (defined in kernels.cu) --------------------------------
+struct Launch {
+  cudaStream_t st;
+  int64_t* counter;  // kernels launched (for stats), may be null
+};
+
+void launch_copy_segments(Launch L, const Seg* segs, int nseg, const int32_t* src, int32_t* dst);
+
+// Gather rows: out[i][c] = in[rows[i]][c] for i < m, c < ncols.
+void launch_gather_rows(Launch L, const double* in, int64_t ld_in, const int32_t* rows, int64_t m,
+                        int64_t ncols, double* out, int64_t ld_out);
+
+// Kernel-matrix product on the fly (tree order): out = shift*in + scale*K*in.
+void launch_kernel_matvec(Launch L, int kind, const double* pts, int d, int64_t n, double shift,
+                          double scale, const double* in, int64_t ld_in, double* out, int64_t ld_out,
+                          int64_t ncols);
+// Same, with the kernel part in FP32 (fp32 != 0; identity term and partial-sum flushes in FP64).
+void launch_kernel_matvec_prec(Launch L, int kind, const double* pts, int d, int64_t n, double shift,
+                               double scale, const double* in, int64_t ld_in, double* out, int64_t ld_out,
+                               int64_t ncols, int fp32);
+
+// Group-batched kernels (descriptors of one (level, colour) group).
+struct GroupArgs {
+  const BoxDesc* desc;  // device array, nbox entries
+  int nbox;
+  int64_t s;
+  double* Y;
+  double* Z;
+  double* Om;
+  double* Ps;
+  double* work;
+  int32_t* iwork;
+  double* fd;
+  int32_t* fi;
+  int32_t* act;
+  int* err;
+};
+
+void launch_gram(Launch L, const GroupArgs& g, int64_t items);                    // G = W W^T
+void launch_chol_panel(Launch L, const GroupArgs& g, int panel);                   // diag block
+void launch_chol_trsm(Launch L, const GroupArgs& g, int panel, int64_t items);     // below-diag panel
+void launch_chol_update(Launch L, const GroupArgs& g, int panel, int64_t items);   // trailing update
+void launch_gather_box(Launch L, const GroupArgs& g, int64_t items);               // M = [Y_B | Z_B]
+void launch_proj_nt(Launch L, const GroupArgs& g, int pass, int64_t items);        // X = M W^T
+void launch_proj_solve(Launch L, const GroupArgs& g, int pass, int64_t items);     // X <- X G^-1
+void launch_proj_acc(Launch L, const GroupArgs& g, int pass, int64_t items);       // M -= X W
+void launch_cpqr(Launch L, const GroupArgs& g, int max_b);                         // ID pivots + R
+void launch_id_finish(Launch L, const GroupArgs& g, int max_b);                    // T, R/S/N lists
+void launch_ef_update(Launch L, const GroupArgs& g, int64_t items);                // E, F on sketches
+void launch_extract(Launch L, const GroupArgs& g, int64_t items);                  // X blocks
+void launch_lu(Launch L, const GroupArgs& g);                                      // LU(X_RR)
+void launch_lu_rhs(Launch L, const GroupArgs& g, int64_t items);                   // Lc, Uc
+void launch_schur(Launch L, const GroupArgs& g, int64_t items);                    // L, U on sketches
+
+// Number of 64-row x 64-col tiles for the group kernels (host-side planning).
+constexpr int kT = 64;
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Solve / apply sweeps over one group (defined in solve.cu).
+struct SweepArgs {
+  const BoxDesc* desc;
+  int nbox;
+  const double* fd;
+  const int32_t* fi;
+  double* F;  // N x nrhs row-major, tree order
+  int nrhs;
+  int adjoint;
+};
+// C rows += alpha * op(A) * B rows; row sets 0 = R, 1 = S, 2 = SN; matrices 0 = T, 1 = LcT, 2 = Uc.
+void launch_sweep_op(Launch L, const SweepArgs& a, int cset, int mat, int trans, int bset, double alpha,
+                     int64_t items);
+void launch_sweep_diag(Launch L, const SweepArgs& a, int solve, int64_t items, int max_r);
+void launch_dense_apply(Launch L, const double* A, int64_t n, const int32_t* rows, double* F, int nrhs,
+                        int adjoint);
+
+// Item counts (host planning) matching the device decoding of each kernel.
+int64_t items_gram(const std::vector<BoxDesc>& h);
+int64_t items_chol_trsm(const std::vector<BoxDesc>& h, int p);
+int64_t items_chol_update(const std::vector<BoxDesc>& h, int p);
+int64_t items_gather(const std::vector<BoxDesc>& h);
+int64_t items_proj_nt(const std::vector<BoxDesc>& h);
+int64_t items_proj_solve(const std::vector<BoxDesc>& h);
+int64_t items_proj_acc(const std::vector<BoxDesc>& h, int64_t s);
+int64_t items_ef(const std::vector<BoxDesc>& h, int64_t s);
+int64_t items_extract(const std::vector<BoxDesc>& h);
+int64_t items_lu_rhs(const std::vector<BoxDesc>& h);
+int64_t items_schur(const std::vector<BoxDesc>& h, int64_t s);
+int64_t items_sweep(const std::vector<BoxDesc>& h, int cset);
+int64_t items_diag(const std::vector<BoxDesc>& h, int nrhs);
+
+// Root block (dense): LU in place with partial pivoting, single CTA.
+void launch_dense_lu(Launch L, double* A, int64_t n, int32_t* piv, int* err);
+void launch_dense_lu_solve(Launch L, const double* LU, const int32_t* piv, int64_t n,
+                           const int32_t* rows, double* F, int nrhs, int adjoint);
+
+}  // namespace rsrs

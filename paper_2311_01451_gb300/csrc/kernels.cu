@@ -1,0 +1,1307 @@
+// Batched FP64 kernels for one (level, colour) group of Algorithm 1.
+//
+// Every kernel runs over the boxes of one group (boxes with disjoint closed
+// neighbourhoods, so their row sets never overlap).  A 1D grid of "items"
+// (tiles, row chunks or whole boxes) is decoded on the device: each CTA scans
+// the group's descriptors with the same per-box item count the host used to
+// size the launch.
+//
+// GB300 note: FP64 runs at about 1 TFLOP/s on this part (1/64 of FP32), so
+// these kernels are bound by the FP64 pipe as soon as a tile reuses its
+// operands a few times; 64x64 output tiles with 16-deep K slices in shared
+// memory are enough to keep the pipe busy.
+#include <cfloat>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace rsrs {
+
+namespace {
+
+constexpr int TB = 64;   // output tile edge
+constexpr int KC = 16;   // K slice
+constexpr int NT = 256;  // threads per tiled CTA (16 x 16), 4 x 4 outputs each
+
+__host__ __device__ inline int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ inline int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }
+__host__ __device__ inline int64_t tri(int64_t t) { return t * (t + 1) / 2; }
+
+__device__ inline void tri_decode(int64_t idx, int64_t& ti, int64_t& tj) {
+  int64_t t = (int64_t)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
+  while (tri(t) > idx) --t;
+  while (tri(t + 1) <= idx) ++t;
+  ti = t;
+  tj = idx - tri(t);
+}
+
+__host__ __device__ inline int64_t cdv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+template <class F>
+__device__ inline int find_item(const BoxDesc* desc, int nbox, int64_t item, F count, int64_t& local) {
+  __shared__ int s_box;
+  __shared__ int64_t s_local;
+  if (threadIdx.x == 0) {
+    int64_t acc = 0;
+    s_box = -1;
+    for (int i = 0; i < nbox; ++i) {
+      int64_t c = count(desc[i]);
+      if (item < acc + c) {
+        s_box = i;
+        s_local = item - acc;
+        break;
+      }
+      acc += c;
+    }
+  }
+  __syncthreads();
+  local = s_local;
+  return s_box;
+}
+
+__device__ inline void set_err(int* err, int code) {
+  if (err) atomicCAS(err, 0, code);
+}
+
+// Row source: row i of a row-major matrix, through an optional int32 index list.
+struct Rows {
+  const double* base;
+  int64_t ld;
+  const int32_t* idx;  // may be null: row i -> base + i*ld
+  __device__ const double* row(int64_t i) const { return base + (idx ? (int64_t)idx[i] : i) * ld; }
+};
+struct RowsW {
+  double* base;
+  int64_t ld;
+  const int32_t* idx;
+  __device__ double* row(int64_t i) const { return base + (idx ? (int64_t)idx[i] : i) * ld; }
+};
+
+// C tile (64 x 64) = sum_t A[i][t] B[j][t] over t < K, rows gathered.  acc: 4 x 4 per thread,
+// rows ty + 16a, cols tx + 16c (a, c < 4).
+__device__ void tile_nt(Rows A, int64_t ma, Rows B, int64_t mb, int64_t koff, int64_t K, int64_t i0,
+                        int64_t j0, double acc[4][4]) {
+  __shared__ double As[KC][TB + 1];
+  __shared__ double Bs[KC][TB + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int lr = tid >> 2, lk = (tid & 3) * 4;
+  const double* arow = (i0 + lr < ma) ? A.row(i0 + lr) + koff : nullptr;
+  const double* brow = (j0 + lr < mb) ? B.row(j0 + lr) + koff : nullptr;
+  for (int64_t k0 = 0; k0 < K; k0 += KC) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int64_t k = k0 + lk + u;
+      As[lk + u][lr] = (arow && k < K) ? arow[k] : 0.0;
+      Bs[lk + u][lr] = (brow && k < K) ? brow[k] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = As[kk][ty + 16 * u];
+        b[u] = Bs[kk][tx + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+}
+
+// A operand of C += alpha A B: element (i, q) of an m x K matrix, row-major or transposed storage.
+struct MatA {
+  const double* p;
+  int64_t lda;
+  bool trans;
+  __device__ double at(int64_t i, int64_t q) const { return trans ? p[q * lda + i] : p[i * lda + q]; }
+};
+
+// C[crow(i)][coff + t] += alpha * sum_q A(i,q) B[brow(q)][t] for the 64 x 64 tile (i0, t0);
+// t ranges over ncols, q over K.
+__device__ void tile_acc(double alpha, MatA A, int64_t m, int64_t K, Rows B, int64_t boff, RowsW C,
+                         int64_t coff, int64_t ncols, int64_t i0, int64_t t0) {
+  __shared__ double As[KC][TB + 1];
+  __shared__ double Bs[KC][TB + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  double acc[4][4] = {};
+  for (int64_t q0 = 0; q0 < K; q0 += KC) {
+    // A tile: 64 rows x 16 q
+    if (!A.trans) {
+      int lr = tid >> 2, lq = (tid & 3) * 4;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        int64_t i = i0 + lr, q = q0 + lq + u;
+        As[lq + u][lr] = (i < m && q < K) ? A.at(i, q) : 0.0;
+      }
+    } else {
+      int lr = tid & 63, lq = (tid >> 6) * 4;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        int64_t i = i0 + lr, q = q0 + lq + u;
+        As[lq + u][lr] = (i < m && q < K) ? A.at(i, q) : 0.0;
+      }
+    }
+    // B tile: 16 rows (q) x 64 cols (t)
+    {
+      int lq = tid >> 4, lt = (tid & 15) * 4;
+      int64_t q = q0 + lq;
+      const double* brow = (q < K) ? B.row(q) + boff : nullptr;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        int64_t t = t0 + lt + u;
+        Bs[lq][lt + u] = (brow && t < ncols) ? brow[t] : 0.0;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = As[kk][ty + 16 * u];
+        b[u] = Bs[kk][tx + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    int64_t i = i0 + ty + 16 * u;
+    if (i >= m) continue;
+    double* crow = C.row(i) + coff;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int64_t t = t0 + tx + 16 * v;
+      if (t < ncols) crow[t] += alpha * acc[u][v];
+    }
+  }
+}
+
+// ---- kernels -----------------------------------------------------------------
+
+__global__ void k_copy_segments(const Seg* segs, int nseg, const int32_t* src, int32_t* dst) {
+  int sidx = blockIdx.x;
+  if (sidx >= nseg) return;
+  Seg sg = segs[sidx];
+  for (int64_t i = threadIdx.x; i < sg.len; i += blockDim.x) dst[sg.dst + i] = src[sg.src + i];
+}
+
+__global__ void k_gather_rows(const double* in, int64_t ld_in, const int32_t* rows, int64_t m, int64_t ncols,
+                              double* out, int64_t ld_out) {
+  int64_t i = blockIdx.x;
+  if (i >= m) return;
+  const double* src = in + (int64_t)rows[i] * ld_in;
+  double* dst = out + i * ld_out;
+  for (int64_t c = threadIdx.x; c < ncols; c += blockDim.x) dst[c] = src[c];
+}
+
+struct CntGram {
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const { return 2 * tri(cdv(d.l, TB)); }
+};
+__global__ void __launch_bounds__(NT) k_gram(GroupArgs g) {
+  int64_t loc;
+  int bi = find_item(g.desc, g.nbox, blockIdx.x, CntGram(), loc);
+  if (bi < 0) return;
+  const BoxDesc d = g.desc[bi];
+  int64_t per = tri(cdv(d.l, TB));
+  int side = (int)(loc / per);
+  int64_t ti, tj;
+  tri_decode(loc % per, ti, tj);
+  const int32_t* bn = g.iwork + d.bn_off;
+  Rows W{side ? g.Ps : g.Om, g.s, bn};
+  double acc[4][4] = {};
+  tile_nt(W, d.l, W, d.l, 0, g.s, ti * TB, tj * TB, acc);
+  double* G = g.work + d.g_off + (int64_t)side * d.l * d.l;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    int64_t i = ti * TB + ty + 16 * u;
+    if (i >= d.l) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int64_t j = tj * TB + tx + 16 * v;
+      if (j < d.l) G[i * d.l + j] = acc[u][v];
+    }
+  }
+}
+
+// Blocked right-looking Cholesky, lower, in place on each l x l Gram, 64-wide panels.
+struct CntPanel {
+  int p;
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const { return (d.l > (int64_t)p * TB) ? 2 : 0; }
+};
+__global__ void __launch_bounds__(NT) k_chol_panel(GroupArgs g, int p) {
+  int64_t loc;
+  int bi = find_item(g.desc, g.nbox, blockIdx.x, CntPanel{p}, loc);
+  if (bi < 0) return;
+  const BoxDesc d = g.desc[bi];
+  const int side = (int)loc;
+  double* G = g.work + d.g_off + (int64_t)side * d.l * d.l;
+  const int64_t o = (int64_t)p * TB;
+  const int nb = (int)imin64(TB, d.l - o);
+  __shared__ double S[TB][TB + 1];
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    int i = e / nb, j = e % nb;
+    S[i][j] = G[(o + i) * d.l + o + j];
+  }
+  __syncthreads();
+  for (int c = 0; c < nb; ++c) {
+    // column c: pivot, scale, rank-1 update of the trailing block (lower part)
+    if (threadIdx.x == 0) {
+      double piv = S[c][c];
+      if (!(piv > 0.0) || !isfinite(piv)) {
+        s_bad = 1;
+        piv = 1.0;
+      }
+      S[c][c] = sqrt(piv);
+    }
+    __syncthreads();
+    double dc = S[c][c];
+    for (int i = c + 1 + threadIdx.x; i < nb; i += blockDim.x) S[i][c] /= dc;
+    __syncthreads();
+    int rem = nb - c - 1;
+    for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+      int i = c + 1 + e / rem, j = c + 1 + e % rem;
+      if (j <= i) S[i][j] -= S[i][c] * S[j][c];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && s_bad) set_err(g.err, kDevNonfinite);
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    int i = e / nb, j = e % nb;
+    G[(o + i) * d.l + o + j] = (j <= i) ? S[i][j] : 0.0;
+  }
+}
+
+struct CntPanelRows {
+  int p;
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const {
+    int64_t below = d.l - (int64_t)(p + 1) * TB;
+    return below > 0 ? 2 * cdv(below, TB) : 0;
+  }
+};
+// L_ip = G_ip L_pp^-T for the 64-row tiles below the diagonal block of panel p.
+__global__ void __launch_bounds__(NT) k_chol_trsm(GroupArgs g, int p) {
+  int64_t loc;
+  int bi = find_item(g.desc, g.nbox, blockIdx.x, CntPanelRows{p}, loc);
+  if (bi < 0) return;
+  const BoxDesc d = g.desc[bi];
+  int64_t below = d.l - (int64_t)(p + 1) * TB;
+  int64_t per = cdv(below, TB);
+  int side = (int)(loc / per);
+  int64_t ti = loc % per;
+  double* G = g.work + d.g_off + (int64_t)side * d.l * d.l;
+  const int64_t o = (int64_t)p * TB;
+  const int nb = (int)imin64(TB, d.l - o);
+  const int64_t r0 = (int64_t)(p + 1) * TB + ti * TB;
+  const int nr = (int)imin64(TB, d.l - r0);
+  extern __shared__ double trsm_sm[];
+  double(*Lp)[TB + 1] = reinterpret_cast<double(*)[TB + 1]>(trsm_sm);
+  double(*X)[TB + 1] = reinterpret_cast<double(*)[TB + 1]>(trsm_sm + TB * (TB + 1));
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    int i = e / TB, j = e % TB;
+    Lp[i][j] = (i < nb && j < nb) ? G[(o + i) * d.l + o + j] : 0.0;
+    X[i][j] = (i < nr && j < nb) ? G[(r0 + i) * d.l + o + j] : 0.0;
+  }
+  __syncthreads();
+  // x L^T = g, column by column; threads over the rows of the tile (4 threads per row, 16 cols each)
+  for (int c = 0; c < nb; ++c) {
+    if (threadIdx.x < nr) X[threadIdx.x][c] /= Lp[c][c];
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * (nb - c - 1); e += blockDim.x) {
+      int i = e / (nb - c - 1), j = c + 1 + e % (nb - c - 1);
+      X[i][j] -= X[i][c] * Lp[j][c];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < nr * nb; e += blockDim.x) {
+    int i = e / nb, j = e % nb;
+    G[(r0 + i) * d.l + o + j] = X[i][j];
+  }
+}
+
+struct CntUpdate {
+  int p;
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const {
+    int64_t t = cdv(d.l, TB) - p - 1;
+    return t > 0 ? 2 * tri(t) : 0;
+  }
+};
+// G_ij -= L_ip L_jp^T for trailing tiles i >= j > p.
+__global__ void __launch_bounds__(NT) k_chol_update(GroupArgs g, int p) {
+  int64_t loc;
+  int bi = find_item(g.desc, g.nbox, blockIdx.x, CntUpdate{p}, loc);
+  if (bi < 0) return;
+  const BoxDesc d = g.desc[bi];
+  int64_t t = cdv(d.l, TB) - p - 1;
+  int64_t per = tri(t);
+  int side = (int)(loc / per);
+  int64_t ti, tj;
+  tri_decode(loc % per, ti, tj);
+  ti += p + 1;
+  tj += p + 1;
+  double* G = g.work + d.g_off + (int64_t)side * d.l * d.l;
+  const int64_t o = (int64_t)p * TB;
+  const int64_t nb = imin64(TB, d.l - o);
+  Rows L{G, d.l, nullptr};
+  double acc[4][4] = {};
+  tile_nt(L, d.l, L, d.l, o, nb, ti * TB, tj * TB, acc);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    int64_t i = ti * TB + ty + 16 * u;
+    if (i >= d.l) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int64_t j = tj * TB + tx + 16 * v;
+      if (j < d.l) G[i * d.l + j] -= acc[u][v];
+    }
+  }
+}
+
+// M = [Y_B | Z_B]: b rows, 4 rows per CTA.
+struct CntGather {
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const { return cdv(d.b, 4); }
+};
+__global__ void k_gather_box(GroupArgs g) {
+  int64_t loc;
+  int bi = find_item(g.desc, g.nbox, blockIdx.x, CntGather(), loc);
+  if (bi < 0) return;
+  const BoxDesc d = g.desc[bi];
+  const int32_t* bn = g.iwork + d.bn_off;
+  for (int rr = 0; rr < 4; ++rr) {
+    int64_t i = loc * 4 + rr;
+    if (i >= d.b) break;
+    const double* y = g.Y + (int64_t)bn[i] * g.s;
+    const double* z = g.Z + (int64_t)bn[i] * g.s;
+    double* m = g.work + d.m_off + i * 2 * g.s;
+    for (int64_t c = threadIdx.x; c < g.s; c += blockDim.x) {
+      m[c] = y[c];
+      m[g.s + c] = z[c];
+    }
+  }
+}
+
+// X_side = M_side W_side^T (b x l), pass 0 -> x_off, pass 1 -> x2_off.
+struct CntProjNT {
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const { return 2 * cdv(d.b, TB) * cdv(d.l, TB); }
+};
+__global__ void __launch_bounds__(NT) k_proj_nt(GroupArgs g, int pass) {
+  int64_t loc;
+  int bi = find_item(g.desc, g.nbox, blockIdx.x, CntProjNT(), loc);
+  if (bi < 0) return;
+  const BoxDesc d = g.desc[bi];
+  int64_t per = cdv(d.b, TB) * cdv(d.l, TB);
+  int side = (int)(loc / per);
+  int64_t rem = loc % per;
+  int64_t ti = rem / cdv(d.l, TB), tj = rem % cdv(d.l, TB);
+  const int32_t* bn = g.iwork + d.bn_off;
+  Rows M{g.work + d.m_off + (int64_t)side * g.s, 2 * g.s, nullptr};
+  Rows W{side ? g.Ps : g.Om, g.s, bn};
+  double acc[4][4] = {};
+  tile_nt(M, d.b, W, d.l, 0, g.s, ti * TB, tj * TB, acc);
+  double* X = g.work + (pass ? d.x2_off : d.x_off) + (int64_t)side * d.b * d.l;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    int64_t i = ti * TB + ty + 16 * u;
+    if (i >= d.b) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int64_t j = tj * TB + tx + 16 * v;
+      if (j < d.l) X[i * d.l + j] = acc[u][v];
+    }
+  }
+}
+
+// X <- X G^-1 with G = L L^T (L from the blocked Cholesky); 16 rows per CTA.
+constexpr int SR = 16;
+struct CntProjSolve {
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const { return 2 * cdv(d.b, SR); }
+};
+__global__ void __launch_bounds__(NT) k_proj_solve(GroupArgs g, int pass) {
+  int64_t loc;
+  int bi = find_item(g.desc, g.nbox, blockIdx.x, CntProjSolve(), loc);
+  if (bi < 0) return;
+  const BoxDesc d = g.desc[bi];
+  int64_t per = cdv(d.b, SR);
+  int side = (int)(loc / per);
+  int64_t r0 = (loc % per) * SR;
+  const int nr = (int)imin64(SR, d.b - r0);
+  const double* L = g.work + d.g_off + (int64_t)side * d.l * d.l;
+  double* X = g.work + (pass ? d.x2_off : d.x_off) + (int64_t)side * d.b * d.l + r0 * d.l;
+  const int64_t l = d.l;
+  const int64_t nblk = cdv(l, TB);
+  __shared__ double Ls[TB][TB + 1];
+  __shared__ double Xs[SR][TB + 1];
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;  // row ty, cols tx + 16u
+  // forward: U L^T = X  (U[:, c] = (X[:, c] - sum_{q<c} U[:, q] L[c][q]) / L[c][c])
+  for (int64_t jb = 0; jb < nblk; ++jb) {
+    const int64_t c0 = jb * TB;
+    const int nc = (int)imin64(TB, l - c0);
+    double acc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int c = tx + 16 * u;
+      acc[u] = (ty < nr && c < nc) ? X[ty * l + c0 + c] : 0.0;
+    }
+    for (int64_t kb = 0; kb < jb; ++kb) {
+      const int64_t q0 = kb * TB;
+      for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+        int i = e / TB, j = e % TB;
+        Ls[i][j] = (i < nc) ? L[(c0 + i) * l + q0 + j] : 0.0;
+      }
+      for (int e = threadIdx.x; e < SR * TB; e += blockDim.x) {
+        int i = e / TB, j = e % TB;
+        Xs[i][j] = (i < nr) ? X[i * l + q0 + j] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int q = 0; q < TB; ++q) {
+        double xv = Xs[ty][q];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = fma(-xv, Ls[tx + 16 * u][q], acc[u]);
+      }
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+      int i = e / TB, j = e % TB;
+      Ls[i][j] = (i < nc && j < nc) ? L[(c0 + i) * l + c0 + j] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) Xs[ty][tx + 16 * u] = acc[u];
+    __syncthreads();
+    for (int c = 0; c < nc; ++c) {
+      if (threadIdx.x < SR) Xs[threadIdx.x][c] /= Ls[c][c];
+      __syncthreads();
+      for (int e = threadIdx.x; e < SR * (nc - c - 1); e += blockDim.x) {
+        int i = e / (nc - c - 1), j = c + 1 + e % (nc - c - 1);
+        Xs[i][j] -= Xs[i][c] * Ls[j][c];
+      }
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
+      int i = e / nc, j = e % nc;
+      X[i * l + c0 + j] = Xs[i][j];
+    }
+    __syncthreads();
+  }
+  // backward: X L = U  (X[:, c] = (U[:, c] - sum_{q>c} X[:, q] L[q][c]) / L[c][c])
+  for (int64_t jb = nblk - 1; jb >= 0; --jb) {
+    const int64_t c0 = jb * TB;
+    const int nc = (int)imin64(TB, l - c0);
+    double acc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int c = tx + 16 * u;
+      acc[u] = (ty < nr && c < nc) ? X[ty * l + c0 + c] : 0.0;
+    }
+    for (int64_t kb = jb + 1; kb < nblk; ++kb) {
+      const int64_t q0 = kb * TB;
+      const int nq = (int)imin64(TB, l - q0);
+      for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+        int i = e / TB, j = e % TB;  // Ls[i][j] = L[q0 + i][c0 + j]
+        Ls[i][j] = (i < nq && j < nc) ? L[(q0 + i) * l + c0 + j] : 0.0;
+      }
+      for (int e = threadIdx.x; e < SR * TB; e += blockDim.x) {
+        int i = e / TB, j = e % TB;
+        Xs[i][j] = (i < nr && j < nq) ? X[i * l + q0 + j] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int q = 0; q < TB; ++q) {
+        double xv = Xs[ty][q];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = fma(-xv, Ls[q][tx + 16 * u], acc[u]);
+      }
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+      int i = e / TB, j = e % TB;
+      Ls[i][j] = (i < nc && j < nc) ? L[(c0 + i) * l + c0 + j] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) Xs[ty][tx + 16 * u] = acc[u];
+    __syncthreads();
+    for (int c = nc - 1; c >= 0; --c) {
+      if (threadIdx.x < SR) Xs[threadIdx.x][c] /= Ls[c][c];
+      __syncthreads();
+      for (int e = threadIdx.x; e < SR * c; e += blockDim.x) {
+        int i = e / c, j = e % c;
+        Xs[i][j] -= Xs[i][c] * Ls[c][j];
+      }
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
+      int i = e / nc, j = e % nc;
+      X[i * l + c0 + j] = Xs[i][j];
+    }
+    __syncthreads();
+  }
+  if (pass) {  // accumulate the least-squares correction into the first-pass coefficients
+    double* X1 = g.work + d.x_off + (int64_t)side * d.b * d.l + r0 * d.l;
+    for (int64_t e = threadIdx.x; e < (int64_t)nr * l; e += blockDim.x) X1[e] += X[e];
+  }
+}
+
+// M_side -= X_side W_side  (b x s).
+struct CntProjAcc {
+  int64_t s;
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const { return 2 * cdv(d.b, TB) * cdv(s, TB); }
+};
+__global__ void __launch_bounds__(NT) k_proj_acc(GroupArgs g, int pass) {
+  int64_t loc;
+  int bi = find_item(g.desc, g.nbox, blockIdx.x, CntProjAcc{g.s}, loc);
+  if (bi < 0) return;
+  const BoxDesc d = g.desc[bi];
+  int64_t nt = cdv(g.s, TB);
+  int64_t per = cdv(d.b, TB) * nt;
+  int side = (int)(loc / per);
+  int64_t rem = loc % per;
+  int64_t ti = rem / nt, tt = rem % nt;
+  const int32_t* bn = g.iwork + d.bn_off;
+  MatA X{g.work + (pass ? d.x2_off : d.x_off) + (int64_t)side * d.b * d.l, d.l, false};
+  Rows W{side ? g.Ps : g.Om, g.s, bn};
+  RowsW M{g.work + d.m_off, 2 * g.s, nullptr};
+  tile_acc(-1.0, X, d.b, d.l, W, 0, M, (int64_t)side * g.s, g.s, ti * TB, tt * TB);
+}
+
+// Column-pivoted Householder QR of M^T (pivoting over the b rows of M), kp steps.
+// One CTA per box; the reflectors act on the 2s columns of M in place.
+__global__ void __launch_bounds__(512) k_cpqr(GroupArgs g) {
+  const BoxDesc d = g.desc[blockIdx.x];
+  const int b = d.b, kp = d.kp;
+  const int64_t c = 2 * g.s;
+  double* M = g.work + d.m_off;
+  double* Rp = g.work + d.cp_off;  // kp x b, Rp[j][pos]
+  int32_t* perm = g.iwork + d.pv_off;
+  extern __shared__ double sm[];
+  double* nrm = sm;                       // b
+  int* rid = (int*)(sm + b);              // b
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ double s_vn2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < b; i += blockDim.x) rid[i] = i;
+  // initial squared row norms
+  for (int i = warp; i < b; i += nw) {
+    const double* row = M + (int64_t)i * c;
+    double acc = 0.0;
+    for (int64_t t = lane; t < c; t += 32) acc = fma(row[t], row[t], acc);
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) nrm[i] = acc;
+  }
+  __syncthreads();
+  for (int j = 0; j < kp; ++j) {
+    // pivot: largest residual norm, ties to the lowest local index
+    double bv = -1.0;
+    int bp = -1;
+    for (int pos = j + threadIdx.x; pos < b; pos += blockDim.x) {
+      double v = nrm[pos];
+      if (v > bv || (v == bv && rid[pos] < rid[bp])) {
+        bv = v;
+        bp = pos;
+      }
+    }
+    for (int o = 16; o; o >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      int op = __shfl_xor_sync(0xffffffffu, bp, o);
+      if (op >= 0 && (ov > bv || (ov == bv && (bp < 0 || rid[op] < rid[bp])))) {
+        bv = ov;
+        bp = op;
+      }
+    }
+    if (lane == 0) {
+      red_v[warp] = bv;
+      red_i[warp] = bp;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double v0 = -1.0;
+      int p0 = -1;
+      for (int w = 0; w < nw; ++w) {
+        int op = red_i[w];
+        double ov = red_v[w];
+        if (op >= 0 && (ov > v0 || (ov == v0 && (p0 < 0 || rid[op] < rid[p0])))) {
+          v0 = ov;
+          p0 = op;
+        }
+      }
+      if (p0 < 0) {  // no finite candidate: keep the order, report
+        p0 = j;
+        set_err(g.err, kDevNonfinite);
+      }
+      if (p0 != j) {
+        int ti = rid[j];
+        rid[j] = rid[p0];
+        rid[p0] = ti;
+        double tv = nrm[j];
+        nrm[j] = nrm[p0];
+        nrm[p0] = tv;
+      }
+    }
+    __syncthreads();
+    // reflector from the pivot row x = M[rid[j]][j:]
+    double* x = M + (int64_t)rid[j] * c;
+    {
+      double acc = 0.0;
+      for (int64_t t = j + threadIdx.x; t < c; t += blockDim.x) acc = fma(x[t], x[t], acc);
+      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) red_v[warp] = acc;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double a2 = 0.0;
+        for (int w = 0; w < nw; ++w) a2 += red_v[w];
+        double alpha = sqrt(a2);
+        double x0 = x[j];
+        double sg = (x0 >= 0.0) ? 1.0 : -1.0;
+        s_vn2 = 2.0 * alpha * (alpha + fabs(x0));
+        Rp[(int64_t)j * b + j] = -sg * alpha;
+        x[j] = x0 + sg * alpha;
+      }
+      __syncthreads();
+    }
+    const double vn2 = s_vn2;
+    for (int pos = j + 1 + warp; pos < b; pos += nw) {
+      double* row = M + (int64_t)rid[pos] * c;
+      double w = 0.0;
+      if (vn2 > 0.0) {
+        for (int64_t t = j + lane; t < c; t += 32) w = fma(row[t], x[t], w);
+        for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      }
+      const double f = (vn2 > 0.0) ? 2.0 * w / vn2 : 0.0;
+      double nn = 0.0;
+      for (int64_t t = j + lane; t < c; t += 32) {
+        double v = fma(-f, x[t], row[t]);
+        row[t] = v;
+        if (t > j) nn = fma(v, v, nn);
+      }
+      for (int o = 16; o; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+      if (lane == 0) {
+        nrm[pos] = nn;
+        Rp[(int64_t)j * b + pos] = row[j];
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < b; i += blockDim.x) perm[i] = rid[i];
+}
+
+// T = R11^-1 R12 (truncated at the first dependent pivot), R/S/N lists, new active list.
+__global__ void __launch_bounds__(256) k_id_finish(GroupArgs g) {
+  const BoxDesc d = g.desc[blockIdx.x];
+  const int b = d.b, kp = d.kp, r = d.r;
+  const double* Rp = g.work + d.cp_off;
+  int32_t* perm = g.iwork + d.pv_off;
+  const int32_t* bn = g.iwork + d.bn_off;
+  double* T = g.fd + fd_T(d);
+  int32_t* Rl = g.fi + fi_R(d);
+  int32_t* Sl = g.fi + fi_S(d);
+  int32_t* Nl = g.fi + fi_N(d);
+  extern __shared__ int ism[];
+  int* rloc = ism;          // r: sorted redundant local indices
+  int* rcol = ism + r;      // r: column of T for permuted position kp+q
+  int* ssort = ism + 2 * r; // kp: skeleton local indices, ascending
+  __shared__ int s_j0;
+  // sorted R: rank of each redundant local index
+  for (int q = threadIdx.x; q < r; q += blockDim.x) {
+    int v = perm[kp + q], rank = 0;
+    for (int u = 0; u < r; ++u) rank += perm[kp + u] < v;
+    rloc[rank] = v;
+    rcol[q] = rank;
+  }
+  for (int q = threadIdx.x; q < kp; q += blockDim.x) {
+    int v = perm[q], rank = 0;
+    for (int u = 0; u < kp; ++u) rank += perm[u] < v;
+    ssort[rank] = v;
+  }
+  if (threadIdx.x == 0) {
+    double tau = 64.0 * DBL_EPSILON * (double)imax64(b, 2 * g.s);
+    double r00 = fabs(Rp[0]);
+    int j0 = kp;
+    for (int j = 0; j < kp; ++j)
+      if (fabs(Rp[(int64_t)j * b + j]) <= tau * r00) {
+        j0 = j;
+        break;
+      }
+    s_j0 = j0;
+  }
+  __syncthreads();
+  const int j0 = s_j0;
+  // back substitution, one thread per column of R12
+  for (int q = threadIdx.x; q < r; q += blockDim.x) {
+    const int col = rcol[q];
+    for (int j = kp - 1; j >= 0; --j) {
+      double v = 0.0;
+      if (j < j0) {
+        v = Rp[(int64_t)j * b + kp + q];
+        for (int u = j + 1; u < j0; ++u) v -= Rp[(int64_t)j * b + u] * T[(int64_t)u * r + col];
+        v /= Rp[(int64_t)j * b + j];
+      }
+      T[(int64_t)j * r + col] = v;
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < r; q += blockDim.x) {
+    Rl[q] = bn[rloc[q]];
+    perm[kp + q] = rloc[q];  // the tail of perm now holds R in ascending order
+  }
+  for (int q = threadIdx.x; q < kp; q += blockDim.x) {
+    Sl[q] = bn[perm[q]];
+    g.act[d.act_off + q] = bn[ssort[q]];
+  }
+  for (int q = threadIdx.x; q < d.n; q += blockDim.x) Nl[q] = bn[d.b + q];
+}
+
+// E and F on the sketches: Y_R -= T^T Y_S, Z_R -= T^T Z_S, Om_S += T Om_R, Ps_S += T Ps_R.
+struct CntEF {
+  int64_t s;
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const {
+    return (2 * cdv(d.r, TB) + 2 * cdv(d.kp, TB)) * cdv(s, TB);
+  }
+};
+__global__ void __launch_bounds__(NT) k_ef_update(GroupArgs g) {
+  int64_t loc;
+  int bi = find_item(g.desc, g.nbox, blockIdx.x, CntEF{g.s}, loc);
+  if (bi < 0) return;
+  const BoxDesc d = g.desc[bi];
+  const int64_t nt = cdv(g.s, TB);
+  const int64_t tr = cdv(d.r, TB), tk = cdv(d.kp, TB);
+  int64_t row_tile = loc / nt, tt = loc % nt;
+  const int32_t* Rl = g.fi + fi_R(d);
+  const int32_t* Sl = g.fi + fi_S(d);
+  const double* T = g.fd + fd_T(d);
+  int job;
+  if (row_tile < tr) job = 0;
+  else if (row_tile < 2 * tr) { job = 1; row_tile -= tr; }
+  else if (row_tile < 2 * tr + tk) { job = 2; row_tile -= 2 * tr; }
+  else { job = 3; row_tile -= 2 * tr + tk; }
+  if (job < 2) {
+    double* Mx = job == 0 ? g.Y : g.Z;
+    tile_acc(-1.0, MatA{T, d.r, true}, d.r, d.kp, Rows{Mx, g.s, Sl}, 0, RowsW{Mx, g.s, Rl}, 0, g.s,
+             row_tile * TB, tt * TB);
+  } else {
+    double* Mx = job == 2 ? g.Om : g.Ps;
+    tile_acc(1.0, MatA{T, d.r, false}, d.kp, d.r, Rows{Mx, g.s, Rl}, 0, RowsW{Mx, g.s, Sl}, 0, g.s,
+             row_tile * TB, tt * TB);
+  }
+}
+
+// Block extraction on the hatted sketches from the least-squares coefficients:
+// X_side = (C_R - T^T C_S) G_T^-1 with C the b x l coefficients of [Y_B ; Z_B] on W, V.
+constexpr int ER = 8;
+struct CntExtract {
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const { return 2 * cdv(d.r, ER); }
+};
+__global__ void __launch_bounds__(256) k_extract(GroupArgs g) {
+  int64_t loc;
+  int bi = find_item(g.desc, g.nbox, blockIdx.x, CntExtract(), loc);
+  if (bi < 0) return;
+  const BoxDesc d = g.desc[bi];
+  int64_t per = cdv(d.r, ER);
+  int side = (int)(loc / per);
+  int64_t i0 = (loc % per) * ER;
+  const int nr = (int)imin64(ER, d.r - i0);
+  const int kp = d.kp, r = d.r, l = d.l, b = d.b;
+  const int32_t* perm = g.iwork + d.pv_off;  // [S (pivot order) | R ascending]
+  const double* C = g.work + d.x_off + (int64_t)side * b * l;
+  const double* T = g.fd + fd_T(d);
+  double* E = g.work + d.cp_off + (int64_t)side * r * l;
+  // phase 1: Q = C_R - T^T C_S
+  for (int64_t e = threadIdx.x; e < (int64_t)nr * l; e += blockDim.x) {
+    int ii = (int)(e / l);
+    int64_t col = e % l;
+    int i = (int)i0 + ii;
+    double v = C[(int64_t)perm[kp + i] * l + col];
+    for (int q = 0; q < kp; ++q) v -= T[(int64_t)q * r + i] * C[(int64_t)perm[q] * l + col];
+    E[(int64_t)i * l + col] = v;
+  }
+  __syncthreads();
+  // phase 2: columns R -= columns S times T
+  for (int64_t e = threadIdx.x; e < (int64_t)nr * r; e += blockDim.x) {
+    int i = (int)i0 + (int)(e / r), u = (int)(e % r);
+    double v = E[(int64_t)i * l + perm[kp + u]];
+    for (int q = 0; q < kp; ++q) v -= E[(int64_t)i * l + perm[q]] * T[(int64_t)q * r + u];
+    E[(int64_t)i * l + perm[kp + u]] = v;
+  }
+  __syncthreads();
+  // phase 3: scatter into the factor blocks
+  const int64_t w = (int64_t)kp + d.n;
+  if (side == 0) {
+    double* XRR = g.fd + fd_XRR(d);
+    double* Uc = g.fd + fd_Uc(d);  // [X_RS X_RN] until the LU solve
+    for (int64_t e = threadIdx.x; e < (int64_t)nr * r; e += blockDim.x) {
+      int i = (int)i0 + (int)(e / r), u = (int)(e % r);
+      XRR[(int64_t)i * r + u] = E[(int64_t)i * l + perm[kp + u]];
+    }
+    for (int64_t e = threadIdx.x; e < (int64_t)nr * w; e += blockDim.x) {
+      int i = (int)i0 + (int)(e / w);
+      int64_t q = e % w;
+      int64_t col = q < kp ? perm[q] : b + (q - kp);
+      Uc[(int64_t)i * w + q] = E[(int64_t)i * l + col];
+    }
+  } else {
+    double* LcT = g.fd + fd_LcT(d);  // [X_SR^T X_NR^T] until the LU solve
+    for (int64_t e = threadIdx.x; e < (int64_t)nr * w; e += blockDim.x) {
+      int i = (int)i0 + (int)(e / w);
+      int64_t q = e % w;
+      int64_t col = q < kp ? perm[q] : b + (q - kp);
+      LcT[(int64_t)i * w + q] = E[(int64_t)i * l + col];
+    }
+  }
+}
+
+// LU with partial pivoting of X_RR (copied to the LU block), one CTA per box.
+__device__ void lu_inplace(double* A, int64_t n, int64_t lda, int32_t* piv, int* err) {
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int s_p;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t j = 0; j < n; ++j) {
+    double bv = -1.0;
+    int bp = -1;
+    for (int64_t i = j + threadIdx.x; i < n; i += blockDim.x) {
+      double v = fabs(A[i * lda + j]);
+      if (v > bv) {  // ascending i per thread: ties keep the lower row
+        bv = v;
+        bp = (int)i;
+      }
+    }
+    for (int o = 16; o; o >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      int op = __shfl_xor_sync(0xffffffffu, bp, o);
+      if (op >= 0 && (ov > bv || (ov == bv && (bp < 0 || op < bp)))) {
+        bv = ov;
+        bp = op;
+      }
+    }
+    if (lane == 0) {
+      red_v[warp] = bv;
+      red_i[warp] = bp;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double v0 = -1.0;
+      int p0 = (int)j;
+      for (int w = 0; w < nw; ++w)
+        if (red_i[w] >= 0 && (red_v[w] > v0 || (red_v[w] == v0 && red_i[w] < p0))) {
+          v0 = red_v[w];
+          p0 = red_i[w];
+        }
+      if (!(v0 > 0.0)) set_err(err, kDevSingular);
+      else if (!isfinite(v0)) set_err(err, kDevNonfinite);
+      s_p = p0;
+      piv[j] = p0;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != j)
+      for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+        double t = A[j * lda + c];
+        A[j * lda + c] = A[(int64_t)p * lda + c];
+        A[(int64_t)p * lda + c] = t;
+      }
+    __syncthreads();
+    double dj = A[j * lda + j];
+    if (dj == 0.0) dj = 1.0;
+    for (int64_t i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i * lda + j] /= dj;
+    __syncthreads();
+    const int64_t rem = n - j - 1;
+    for (int64_t e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+      int64_t i = j + 1 + e / rem, c = j + 1 + e % rem;
+      A[i * lda + c] -= A[i * lda + j] * A[j * lda + c];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(512) k_lu(GroupArgs g) {
+  const BoxDesc d = g.desc[blockIdx.x];
+  const double* X = g.fd + fd_XRR(d);
+  double* LU = g.fd + fd_LU(d);
+  for (int64_t e = threadIdx.x; e < (int64_t)d.r * d.r; e += blockDim.x) LU[e] = X[e];
+  __syncthreads();
+  lu_inplace(LU, d.r, d.r, g.fi + fi_piv(d), g.err);
+}
+
+// Solve X_RR Uc = [X_RS X_RN] and X_RR^T LcT = [X_SR^T X_NR^T] (one thread per column).
+constexpr int CW = 128;
+struct CntLuRhs {
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const { return 2 * cdv(d.kp + d.n, CW); }
+};
+__device__ void lu_solve_col(const double* LU, const int32_t* piv, int64_t n, double* x, int64_t stride,
+                             bool trans) {
+  if (!trans) {
+    for (int64_t j = 0; j < n; ++j) {
+      int p = piv[j];
+      if (p != j) {
+        double t = x[j * stride];
+        x[j * stride] = x[(int64_t)p * stride];
+        x[(int64_t)p * stride] = t;
+      }
+    }
+    for (int64_t i = 1; i < n; ++i) {
+      double v = x[i * stride];
+      for (int64_t q = 0; q < i; ++q) v -= LU[i * n + q] * x[q * stride];
+      x[i * stride] = v;
+    }
+    for (int64_t i = n - 1; i >= 0; --i) {
+      double v = x[i * stride];
+      for (int64_t q = i + 1; q < n; ++q) v -= LU[i * n + q] * x[q * stride];
+      x[i * stride] = v / LU[i * n + i];
+    }
+  } else {
+    for (int64_t i = 0; i < n; ++i) {  // U^T y = b
+      double v = x[i * stride];
+      for (int64_t q = 0; q < i; ++q) v -= LU[q * n + i] * x[q * stride];
+      x[i * stride] = v / LU[i * n + i];
+    }
+    for (int64_t i = n - 1; i >= 0; --i) {  // L^T z = y
+      double v = x[i * stride];
+      for (int64_t q = i + 1; q < n; ++q) v -= LU[q * n + i] * x[q * stride];
+      x[i * stride] = v;
+    }
+    for (int64_t j = n - 1; j >= 0; --j) {
+      int p = piv[j];
+      if (p != j) {
+        double t = x[j * stride];
+        x[j * stride] = x[(int64_t)p * stride];
+        x[(int64_t)p * stride] = t;
+      }
+    }
+  }
+}
+__global__ void __launch_bounds__(CW) k_lu_rhs(GroupArgs g) {
+  int64_t loc;
+  int bi = find_item(g.desc, g.nbox, blockIdx.x, CntLuRhs(), loc);
+  if (bi < 0) return;
+  const BoxDesc d = g.desc[bi];
+  const int64_t w = (int64_t)d.kp + d.n;
+  int64_t per = cdv(w, CW);
+  int side = (int)(loc / per);
+  int64_t col = (loc % per) * CW + threadIdx.x;
+  if (col >= w) return;
+  const double* LU = g.fd + fd_LU(d);
+  const int32_t* piv = g.fi + fi_piv(d);
+  double* B = g.fd + (side == 0 ? fd_Uc(d) : fd_LcT(d));
+  lu_solve_col(LU, piv, d.r, B + col, w, side == 1);
+}
+
+// Block elimination on the sketches: Y_SN -= Lc Y_R, Om_R += Uc Om_SN, Z_SN -= Uc^T Z_R,
+// Ps_R += Lc^T Ps_SN, with Lc = LcT^T stored r x (kp+n).
+struct CntSchur {
+  int64_t s;
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const {
+    return (2 * cdv(d.kp + d.n, TB) + 2 * cdv(d.r, TB)) * cdv(s, TB);
+  }
+};
+__global__ void __launch_bounds__(NT) k_schur(GroupArgs g) {
+  int64_t loc;
+  int bi = find_item(g.desc, g.nbox, blockIdx.x, CntSchur{g.s}, loc);
+  if (bi < 0) return;
+  const BoxDesc d = g.desc[bi];
+  const int64_t nt = cdv(g.s, TB);
+  const int64_t w = (int64_t)d.kp + d.n;
+  const int64_t tw = cdv(w, TB), tr = cdv(d.r, TB);
+  int64_t row_tile = loc / nt, tt = loc % nt;
+  const int32_t* Rl = g.fi + fi_R(d);
+  const int32_t* SN = g.fi + fi_S(d);
+  const double* LcT = g.fd + fd_LcT(d);
+  const double* Uc = g.fd + fd_Uc(d);
+  if (row_tile < tw) {
+    tile_acc(-1.0, MatA{LcT, w, true}, w, d.r, Rows{g.Y, g.s, Rl}, 0, RowsW{g.Y, g.s, SN}, 0, g.s,
+             row_tile * TB, tt * TB);
+  } else if (row_tile < tw + tr) {
+    row_tile -= tw;
+    tile_acc(1.0, MatA{Uc, w, false}, d.r, w, Rows{g.Om, g.s, SN}, 0, RowsW{g.Om, g.s, Rl}, 0, g.s,
+             row_tile * TB, tt * TB);
+  } else if (row_tile < 2 * tw + tr) {
+    row_tile -= tw + tr;
+    tile_acc(-1.0, MatA{Uc, w, true}, w, d.r, Rows{g.Z, g.s, Rl}, 0, RowsW{g.Z, g.s, SN}, 0, g.s,
+             row_tile * TB, tt * TB);
+  } else {
+    row_tile -= 2 * tw + tr;
+    tile_acc(1.0, MatA{LcT, w, false}, d.r, w, Rows{g.Ps, g.s, SN}, 0, RowsW{g.Ps, g.s, Rl}, 0, g.s,
+             row_tile * TB, tt * TB);
+  }
+}
+
+// Dense LU of the root block (single CTA) and its solve on gathered rows of F.
+__global__ void __launch_bounds__(1024) k_dense_lu(double* A, int64_t n, int32_t* piv, int* err) {
+  lu_inplace(A, n, n, piv, err);
+}
+__global__ void k_dense_lu_solve(const double* LU, const int32_t* piv, int64_t n, const int32_t* rows,
+                                 double* F, int nrhs, int adjoint) {
+  // one CTA per right-hand side; the column is staged in shared memory
+  extern __shared__ double col[];
+  const int c = blockIdx.x;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) col[i] = F[(int64_t)rows[i] * nrhs + c];
+  __syncthreads();
+  if (threadIdx.x == 0) lu_solve_col(LU, piv, n, col, 1, adjoint != 0);
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) F[(int64_t)rows[i] * nrhs + c] = col[i];
+}
+
+// ---- solve / apply sweeps ------------------------------------------------------
+// C rows += alpha * A(i, q) * B rows, nrhs columns of the row-major (tree order) block F.
+// Row sets: 0 = R, 1 = S, 2 = SN (S followed by N); matrices: 0 = T, 1 = LcT, 2 = Uc.
+struct SweepOp {
+  int cset, mat, trans, bset;
+  double alpha;
+};
+__device__ inline void sweep_set(const BoxDesc& d, const int32_t* fi, int set, const int32_t*& idx, int64_t& m) {
+  if (set == 0) { idx = fi + fi_R(d); m = d.r; }
+  else if (set == 1) { idx = fi + fi_S(d); m = d.kp; }
+  else { idx = fi + fi_S(d); m = (int64_t)d.kp + d.n; }
+}
+struct CntSweep {
+  int cset;
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const {
+    int64_t m = cset == 0 ? d.r : (cset == 1 ? d.kp : (int64_t)d.kp + d.n);
+    return cdv(m, 16);
+  }
+};
+__global__ void __launch_bounds__(256) k_sweep(SweepArgs a, SweepOp op) {
+  int64_t loc;
+  int bi = find_item(a.desc, a.nbox, blockIdx.x, CntSweep{op.cset}, loc);
+  if (bi < 0) return;
+  const BoxDesc d = a.desc[bi];
+  const int32_t *cidx, *bidx;
+  int64_t m, K;
+  sweep_set(d, a.fi, op.cset, cidx, m);
+  sweep_set(d, a.fi, op.bset, bidx, K);
+  const double* A;
+  int64_t lda;
+  if (op.mat == 0) { A = a.fd + fd_T(d); lda = d.r; }
+  else if (op.mat == 1) { A = a.fd + fd_LcT(d); lda = (int64_t)d.kp + d.n; }
+  else { A = a.fd + fd_Uc(d); lda = (int64_t)d.kp + d.n; }
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  const int64_t i = loc * 16 + ty;
+  __shared__ double Bs[64][17];
+  for (int c0 = 0; c0 < a.nrhs; c0 += 16) {
+    const int c = c0 + tx;
+    double acc = 0.0;
+    for (int64_t q0 = 0; q0 < K; q0 += 64) {
+      for (int e = threadIdx.x; e < 64 * 16; e += 256) {
+        int qq = e >> 4, cc = e & 15;
+        int64_t q = q0 + qq;
+        Bs[qq][cc] = (q < K && c0 + cc < a.nrhs) ? a.F[(int64_t)bidx[q] * a.nrhs + c0 + cc] : 0.0;
+      }
+      __syncthreads();
+      if (i < m) {
+        const int64_t qn = imin64(64, K - q0);
+        for (int64_t qq = 0; qq < qn; ++qq) {
+          int64_t q = q0 + qq;
+          double av = op.trans ? A[q * lda + i] : A[i * lda + q];
+          acc = fma(av, Bs[qq][tx], acc);
+        }
+      }
+      __syncthreads();
+    }
+    if (i < m && c < a.nrhs) a.F[(int64_t)cidx[i] * a.nrhs + c] += op.alpha * acc;
+  }
+}
+// f_R <- X_RR^-1 f_R (LU) or X_RR f_R; one CTA per (box, column).
+struct CntDiag {
+  int nrhs;
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const { return nrhs; }
+};
+__global__ void k_sweep_diag(SweepArgs a, int solve) {
+  int64_t loc;
+  int bi = find_item(a.desc, a.nbox, blockIdx.x, CntDiag{a.nrhs}, loc);
+  if (bi < 0) return;
+  const BoxDesc d = a.desc[bi];
+  const int c = (int)loc;
+  const int32_t* R = a.fi + fi_R(d);
+  extern __shared__ double col[];
+  double* out = col + d.r;
+  for (int64_t i = threadIdx.x; i < d.r; i += blockDim.x) col[i] = a.F[(int64_t)R[i] * a.nrhs + c];
+  __syncthreads();
+  if (solve) {
+    if (threadIdx.x == 0) lu_solve_col(a.fd + fd_LU(d), a.fi + fi_piv(d), d.r, col, 1, a.adjoint != 0);
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < d.r; i += blockDim.x) a.F[(int64_t)R[i] * a.nrhs + c] = col[i];
+  } else {
+    const double* X = a.fd + fd_XRR(d);
+    for (int64_t i = threadIdx.x; i < d.r; i += blockDim.x) {
+      double v = 0.0;
+      for (int64_t q = 0; q < d.r; ++q) v += (a.adjoint ? X[q * d.r + i] : X[i * d.r + q]) * col[q];
+      out[i] = v;
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < d.r; i += blockDim.x) a.F[(int64_t)R[i] * a.nrhs + c] = out[i];
+  }
+}
+// Dense root block times rows of F: F[rows] <- A F[rows] (or A^T), one CTA per column.
+__global__ void k_dense_apply(const double* A, int64_t n, const int32_t* rows, double* F, int nrhs, int adjoint) {
+  extern __shared__ double col[];
+  double* out = col + n;
+  const int c = blockIdx.x;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) col[i] = F[(int64_t)rows[i] * nrhs + c];
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    double v = 0.0;
+    for (int64_t q = 0; q < n; ++q) v += (adjoint ? A[q * n + i] : A[i * n + q]) * col[q];
+    out[i] = v;
+  }
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) F[(int64_t)rows[i] * nrhs + c] = out[i];
+}
+
+template <class K, class Cnt>
+int64_t items_of(const std::vector<BoxDesc>& h, Cnt cnt) {
+  int64_t t = 0;
+  for (const auto& d : h) t += cnt(d);
+  return t;
+}
+
+}  // namespace
+
+// ---- host wrappers -------------------------------------------------------------
+static inline void count_launch(Launch L) {
+  if (L.counter) ++*L.counter;
+}
+static inline unsigned grid1(int64_t items) { return (unsigned)items; }
+
+void launch_copy_segments(Launch L, const Seg* segs, int nseg, const int32_t* src, int32_t* dst) {
+  if (nseg <= 0) return;
+  k_copy_segments<<<nseg, 128, 0, L.st>>>(segs, nseg, src, dst);
+  count_launch(L);
+}
+void launch_gather_rows(Launch L, const double* in, int64_t ld_in, const int32_t* rows, int64_t m,
+                        int64_t ncols, double* out, int64_t ld_out) {
+  if (m <= 0) return;
+  k_gather_rows<<<(unsigned)m, 256, 0, L.st>>>(in, ld_in, rows, m, ncols, out, ld_out);
+  count_launch(L);
+}
+void launch_gram(Launch L, const GroupArgs& g, int64_t items) {
+  if (items <= 0) return;
+  k_gram<<<grid1(items), NT, 0, L.st>>>(g);
+  count_launch(L);
+}
+void launch_chol_panel(Launch L, const GroupArgs& g, int panel) {
+  // items = number of (box, side) with l > panel*64; the caller passes it through nbox scan
+  k_chol_panel<<<(unsigned)(2 * g.nbox), NT, 0, L.st>>>(g, panel);
+  count_launch(L);
+}
+void launch_chol_trsm(Launch L, const GroupArgs& g, int panel, int64_t items) {
+  if (items <= 0) return;
+  constexpr size_t smem = 2 * TB * (TB + 1) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_chol_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_chol_trsm<<<grid1(items), NT, smem, L.st>>>(g, panel);
+  count_launch(L);
+}
+void launch_chol_update(Launch L, const GroupArgs& g, int panel, int64_t items) {
+  if (items <= 0) return;
+  k_chol_update<<<grid1(items), NT, 0, L.st>>>(g, panel);
+  count_launch(L);
+}
+void launch_gather_box(Launch L, const GroupArgs& g, int64_t items) {
+  k_gather_box<<<grid1(items), 256, 0, L.st>>>(g);
+  count_launch(L);
+}
+void launch_proj_nt(Launch L, const GroupArgs& g, int pass, int64_t items) {
+  k_proj_nt<<<grid1(items), NT, 0, L.st>>>(g, pass);
+  count_launch(L);
+}
+void launch_proj_solve(Launch L, const GroupArgs& g, int pass, int64_t items) {
+  k_proj_solve<<<grid1(items), NT, 0, L.st>>>(g, pass);
+  count_launch(L);
+}
+void launch_proj_acc(Launch L, const GroupArgs& g, int pass, int64_t items) {
+  k_proj_acc<<<grid1(items), NT, 0, L.st>>>(g, pass);
+  count_launch(L);
+}
+void launch_cpqr(Launch L, const GroupArgs& g, int max_b) {
+  size_t smem = (size_t)max_b * (sizeof(double) + sizeof(int));
+  k_cpqr<<<(unsigned)g.nbox, 512, smem, L.st>>>(g);
+  count_launch(L);
+}
+void launch_id_finish(Launch L, const GroupArgs& g, int max_b) {
+  size_t smem = (size_t)(2 * max_b + max_b) * sizeof(int);
+  k_id_finish<<<(unsigned)g.nbox, 256, smem, L.st>>>(g);
+  count_launch(L);
+}
+void launch_ef_update(Launch L, const GroupArgs& g, int64_t items) {
+  if (items <= 0) return;
+  k_ef_update<<<grid1(items), NT, 0, L.st>>>(g);
+  count_launch(L);
+}
+void launch_extract(Launch L, const GroupArgs& g, int64_t items) {
+  if (items <= 0) return;
+  k_extract<<<grid1(items), 256, 0, L.st>>>(g);
+  count_launch(L);
+}
+void launch_lu(Launch L, const GroupArgs& g) {
+  k_lu<<<(unsigned)g.nbox, 512, 0, L.st>>>(g);
+  count_launch(L);
+}
+void launch_lu_rhs(Launch L, const GroupArgs& g, int64_t items) {
+  if (items <= 0) return;
+  k_lu_rhs<<<grid1(items), CW, 0, L.st>>>(g);
+  count_launch(L);
+}
+void launch_schur(Launch L, const GroupArgs& g, int64_t items) {
+  if (items <= 0) return;
+  k_schur<<<grid1(items), NT, 0, L.st>>>(g);
+  count_launch(L);
+}
+void launch_dense_lu(Launch L, double* A, int64_t n, int32_t* piv, int* err) {
+  k_dense_lu<<<1, 1024, 0, L.st>>>(A, n, piv, err);
+  count_launch(L);
+}
+void launch_dense_lu_solve(Launch L, const double* LU, const int32_t* piv, int64_t n, const int32_t* rows,
+                           double* F, int nrhs, int adjoint) {
+  k_dense_lu_solve<<<nrhs, 256, n * sizeof(double), L.st>>>(LU, piv, n, rows, F, nrhs, adjoint);
+  count_launch(L);
+}
+
+void launch_sweep_op(Launch L, const SweepArgs& a, int cset, int mat, int trans, int bset, double alpha,
+                     int64_t items) {
+  if (items <= 0) return;
+  k_sweep<<<grid1(items), 256, 0, L.st>>>(a, SweepOp{cset, mat, trans, bset, alpha});
+  count_launch(L);
+}
+void launch_sweep_diag(Launch L, const SweepArgs& a, int solve, int64_t items, int max_r) {
+  if (items <= 0) return;
+  k_sweep_diag<<<grid1(items), 128, 2 * (size_t)max_r * sizeof(double), L.st>>>(a, solve);
+  count_launch(L);
+}
+void launch_dense_apply(Launch L, const double* A, int64_t n, const int32_t* rows, double* F, int nrhs,
+                        int adjoint) {
+  k_dense_apply<<<nrhs, 256, 2 * n * sizeof(double), L.st>>>(A, n, rows, F, nrhs, adjoint);
+  count_launch(L);
+}
+
+// Item counts for host planning (same functors as the device decoding).
+int64_t items_sweep(const std::vector<BoxDesc>& h, int cset) { return items_of<void>(h, CntSweep{cset}); }
+int64_t items_diag(const std::vector<BoxDesc>& h, int nrhs) { return items_of<void>(h, CntDiag{nrhs}); }
+int64_t items_gram(const std::vector<BoxDesc>& h) { return items_of<void>(h, CntGram()); }
+int64_t items_chol_trsm(const std::vector<BoxDesc>& h, int p) { return items_of<void>(h, CntPanelRows{p}); }
+int64_t items_chol_update(const std::vector<BoxDesc>& h, int p) { return items_of<void>(h, CntUpdate{p}); }
+int64_t items_gather(const std::vector<BoxDesc>& h) { return items_of<void>(h, CntGather()); }
+int64_t items_proj_nt(const std::vector<BoxDesc>& h) { return items_of<void>(h, CntProjNT()); }
+int64_t items_proj_solve(const std::vector<BoxDesc>& h) { return items_of<void>(h, CntProjSolve()); }
+int64_t items_proj_acc(const std::vector<BoxDesc>& h, int64_t s) { return items_of<void>(h, CntProjAcc{s}); }
+int64_t items_ef(const std::vector<BoxDesc>& h, int64_t s) { return items_of<void>(h, CntEF{s}); }
+int64_t items_extract(const std::vector<BoxDesc>& h) { return items_of<void>(h, CntExtract()); }
+int64_t items_lu_rhs(const std::vector<BoxDesc>& h) { return items_of<void>(h, CntLuRhs()); }
+int64_t items_schur(const std::vector<BoxDesc>& h, int64_t s) { return items_of<void>(h, CntSchur{s}); }
+
+}  // namespace rsrs

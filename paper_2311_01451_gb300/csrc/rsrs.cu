@@ -1,0 +1,881 @@
+// librsrs: C ABI, build driver (Algorithm 1), solve/apply sweeps (eqs. Afact,
+// Ainvfact) and FP64 iterative refinement.
+//
+// All sizes of Algorithm 1 (|B_act|, |N_act|, k', r per box) follow from the
+// tree alone, so the whole launch sequence is planned on the host before any
+// device work: per (level, colour) group a descriptor table, the segment lists
+// that assemble active and near-field index lists on the device, and the
+// workspace offsets.  Only the identities of skeleton/redundant points are
+// data-dependent, and they stay on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace rsrs;
+
+struct rsrs_tree {
+  Tree t;
+};
+
+struct Group {
+  int level, colour;
+  int64_t desc_off;  // into desc_dev
+  std::vector<BoxDesc> h;
+  int64_t seg_off, nseg;  // bn-list segments
+  int max_panels, max_b, max_r;
+};
+
+struct rsrs_factor {
+  int64_t n = 0, s = 0, k = 0, p = 0;
+  int d = 2, precision = 0, kind = 0, passes = 2;
+  double shift = 0.0, scale = 0.0;
+  rsrs_matvec_fn fn = nullptr;
+  void* ctx = nullptr;
+  std::vector<int64_t> perm;  // tree position -> original index
+  int32_t* perm_dev = nullptr;
+  double* pts_dev = nullptr;
+  std::vector<Group> groups;
+  BoxDesc* desc_dev = nullptr;
+  double* fd = nullptr;
+  int32_t* fi = nullptr;
+  int64_t fd_n = 0, fi_n = 0;
+  int64_t root_size = 0;
+  int32_t* root_idx = nullptr;
+  double* root_A = nullptr;
+  double* root_LU = nullptr;
+  int32_t* root_piv = nullptr;
+  int max_r = 0;
+  double *Y = nullptr, *Z = nullptr, *Om = nullptr, *Ps = nullptr;  // kept sketches (optional)
+  rsrs_stats stats{};
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+rsrs_status fail(rsrs_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+#define CU(call)                                                                            \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail(e_ == cudaErrorMemoryAllocation ? RSRS_E_NOMEM : RSRS_E_CUDA,             \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                      \
+  } while (0)
+
+// Owning device buffer list, freed unless released into a factor.
+struct DevPool {
+  std::vector<void*> ptrs;
+  ~DevPool() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <class T>
+  cudaError_t alloc(T** p, int64_t count) {
+    *p = nullptr;
+    if (count <= 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, (size_t)count * sizeof(T));
+    if (e == cudaSuccess) ptrs.push_back(*p);
+    return e;
+  }
+  void release(void* p) { ptrs.erase(std::remove(ptrs.begin(), ptrs.end(), p), ptrs.end()); }
+};
+
+// ---- layout conversions at the boundary ---------------------------------------
+// rows (tree order, row-major n x c) <-> column-major original order with ld.
+__global__ void k_cm_to_rows(const double* F, int64_t ld, const int32_t* perm, int64_t n, int c, double* W) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * c) return;
+  int64_t t = e / c;
+  int j = (int)(e % c);
+  W[e] = F[(int64_t)perm[t] + (int64_t)j * ld];
+}
+__global__ void k_rows_to_cm(const double* W, const int32_t* perm, int64_t n, int c, double* F, int64_t ld) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * c) return;
+  int64_t t = e / c;
+  int j = (int)(e % c);
+  F[(int64_t)perm[t] + (int64_t)j * ld] = W[e];
+}
+__global__ void k_axpy(double* y, const double* x, double a, int64_t n) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) y[e] += a * x[e];
+}
+__global__ void k_sub(double* r, const double* b, const double* ax, int64_t n) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) r[e] = b[e] - ax[e];
+}
+// column sums of squares of a row-major n x c block (c <= 64), accumulated with atomics
+__global__ void k_colnorm2(const double* W, int64_t n, int c, double* out) {
+  __shared__ double part[64];
+  if (threadIdx.x < 64) part[threadIdx.x] = 0.0;
+  __syncthreads();
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * c; e += (int64_t)gridDim.x * blockDim.x) {
+    double v = W[e];
+    atomicAdd(&part[e % c], v * v);
+  }
+  __syncthreads();
+  if (threadIdx.x < c) atomicAdd(&out[threadIdx.x], part[threadIdx.x]);
+}
+
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// Seeded standard normal draws (splitmix64 + Box-Muller) for callers that pass no test matrices.
+void host_gaussian(uint64_t seed, int64_t count, double* out) {
+  uint64_t st = seed * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+  auto next = [&]() {
+    uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  for (int64_t i = 0; i < count; i += 2) {
+    double u1 = ((next() >> 11) + 1.0) * (1.0 / 9007199254740993.0);
+    double u2 = (next() >> 11) * (1.0 / 9007199254740992.0);
+    double rr = std::sqrt(-2.0 * std::log(u1));
+    out[i] = rr * std::cos(2.0 * M_PI * u2);
+    if (i + 1 < count) out[i + 1] = rr * std::sin(2.0 * M_PI * u2);
+  }
+}
+
+// Apply the operator to a tree-order row-major block: out = A in (adjoint for callbacks).
+rsrs_status op_apply(const rsrs_factor* f, Launch L, const double* in, double* out, int64_t ncols, int adjoint,
+                     int fp32, double* scratch_cm_in, double* scratch_cm_out) {
+  if (f->kind == RSRS_OP_CALLBACK) {
+    int64_t tot = f->n * ncols;
+    k_rows_to_cm<<<nblk(tot), 256, 0, L.st>>>(in, f->perm_dev, f->n, (int)ncols, scratch_cm_in, f->n);
+    int rc = f->fn(f->ctx, adjoint, f->n, (int32_t)ncols, scratch_cm_in, f->n, scratch_cm_out, f->n, (void*)L.st);
+    if (rc != 0) return fail(RSRS_E_CALLBACK, "matvec callback returned " + std::to_string(rc));
+    k_cm_to_rows<<<nblk(tot), 256, 0, L.st>>>(scratch_cm_out, f->n, f->perm_dev, f->n, (int)ncols, out);
+    CU(cudaGetLastError());
+    return RSRS_OK;
+  }
+  launch_kernel_matvec_prec(L, f->kind, f->pts_dev, f->d, f->n, f->shift, f->scale, in, ncols, out, ncols, ncols,
+                            fp32);
+  CU(cudaGetLastError());
+  return RSRS_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+const char* rsrs_status_string(rsrs_status st) {
+  switch (st) {
+    case RSRS_OK: return "ok";
+    case RSRS_E_INVAL: return "invalid argument";
+    case RSRS_E_UNDERSAMPLED: return "sample count below the bound s_req";
+    case RSRS_E_SINGULAR: return "singular pivot";
+    case RSRS_E_NONFINITE: return "non-finite value";
+    case RSRS_E_NOMEM: return "device out of memory";
+    case RSRS_E_CUDA: return "CUDA error";
+    case RSRS_E_CALLBACK: return "matvec callback failed";
+    case RSRS_E_TIMEOUT: return "device wait timed out";
+    case RSRS_E_NOT_CONVERGED: return "refinement did not converge";
+  }
+  return "unknown status";
+}
+
+const char* rsrs_last_error(void) { return g_last_error.c_str(); }
+
+rsrs_status rsrs_tree_build(const double* pts_host, int64_t n, int d, int leaf_cap, rsrs_tree** out) {
+  if (!out) return fail(RSRS_E_INVAL, "out is null");
+  *out = nullptr;
+  if (!pts_host || n <= 0 || (d != 2 && d != 3) || leaf_cap <= 0 || n > INT32_MAX)
+    return fail(RSRS_E_INVAL, "tree: need pts, n in [1, 2^31), d in {2,3}, leaf_cap > 0");
+  auto t = std::make_unique<rsrs_tree>();
+  if (!build_tree(pts_host, n, d, leaf_cap, t->t)) return fail(RSRS_E_INVAL, "tree: non-finite point");
+  *out = t.release();
+  return RSRS_OK;
+}
+
+void rsrs_tree_free(rsrs_tree* t) { delete t; }
+
+rsrs_status rsrs_tree_perm(const rsrs_tree* tree, int64_t* perm_host) {
+  if (!tree || !perm_host) return fail(RSRS_E_INVAL, "null argument");
+  std::memcpy(perm_host, tree->t.perm.data(), tree->t.perm.size() * sizeof(int64_t));
+  return RSRS_OK;
+}
+
+rsrs_status rsrs_tree_info(const rsrs_tree* tree, int k, int p, rsrs_tree_info_t* out) {
+  if (!tree || !out || k <= 0) return fail(RSRS_E_INVAL, "tree_info: null argument or k <= 0");
+  Schedule sc;
+  build_schedule(tree->t, k, p, sc);
+  out->d = tree->t.d;
+  out->depth = tree->t.depth;
+  out->n = tree->t.n;
+  out->n_boxes = (int64_t)tree->t.boxes.size();
+  out->n_leaves = 0;
+  for (auto& b : tree->t.boxes) out->n_leaves += b.leaf();
+  out->n_compress = (int64_t)sc.steps.size();
+  out->n_groups = 0;
+  for (auto& lv : sc.groups) out->n_groups += (int64_t)lv.size();
+  out->max_l = sc.max_l;
+  out->root_size = (int64_t)sc.root.size();
+  out->s_req = sc.s_req;
+  return RSRS_OK;
+}
+
+rsrs_status rsrs_tree_schedule(const rsrs_tree* tree, int k, int p, int64_t* rows) {
+  if (!tree || !rows || k <= 0) return fail(RSRS_E_INVAL, "tree_schedule: null argument");
+  Schedule sc;
+  build_schedule(tree->t, k, p, sc);
+  for (size_t i = 0; i < sc.steps.size(); ++i) {
+    const Step& st = sc.steps[i];
+    const Box& b = tree->t.boxes[st.box];
+    int64_t* r = rows + 6 * i;
+    r[0] = st.level;
+    r[1] = st.colour;
+    r[2] = (int64_t)b.morton;
+    r[3] = st.b;
+    r[4] = st.n;
+    r[5] = b.first_pos;
+  }
+  return RSRS_OK;
+}
+
+rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, int s, const rsrs_options* opts,
+                       void* stream, rsrs_factor** out) {
+  if (!out) return fail(RSRS_E_INVAL, "out is null");
+  *out = nullptr;
+  if (!tree || !op || k <= 0 || s <= 0) return fail(RSRS_E_INVAL, "build: null tree/op or k, s <= 0");
+  if (op->kind != RSRS_OP_LOG2D && op->kind != RSRS_OP_INVR3D && op->kind != RSRS_OP_CALLBACK)
+    return fail(RSRS_E_INVAL, "build: unknown operator kind");
+  if (op->kind == RSRS_OP_CALLBACK && !op->fn) return fail(RSRS_E_INVAL, "build: callback operator without fn");
+  const Tree& T = tree->t;
+  if (op->kind == RSRS_OP_LOG2D && T.d != 2) return fail(RSRS_E_INVAL, "build: log kernel needs 2D points");
+  if (op->kind == RSRS_OP_INVR3D && T.d != 3) return fail(RSRS_E_INVAL, "build: 1/r kernel needs 3D points");
+  rsrs_options o{};
+  o.p = -1;
+  if (opts) o = *opts;
+  if (o.precision != RSRS_PREC_FP64 && o.precision != RSRS_PREC_MIXED)
+    return fail(RSRS_E_INVAL, "build: unknown precision");
+  const int passes = o.proj_passes <= 0 ? 2 : std::min(o.proj_passes, 2);
+  Schedule sc;
+  build_schedule(T, k, o.p, sc);
+  if (s < sc.s_req)
+    return fail(RSRS_E_UNDERSAMPLED, "s=" + std::to_string(s) + " < s_req=" + std::to_string(sc.s_req));
+  cudaStream_t st = (cudaStream_t)stream;
+  auto f = std::make_unique<rsrs_factor>();
+  f->n = T.n;
+  f->s = s;
+  f->k = k;
+  f->p = sc.p;
+  f->d = T.d;
+  f->precision = o.precision;
+  f->kind = op->kind;
+  f->passes = passes;
+  f->shift = op->diag_shift;
+  f->scale = op->scale;
+  f->fn = op->fn;
+  f->ctx = op->ctx;
+  f->perm = T.perm;
+  const int64_t N = T.n;
+  const int nbox_tree = (int)T.boxes.size();
+
+  // ---- plan: active-list pool, groups, descriptors, offsets --------------------
+  std::vector<int64_t> act_off(nbox_tree, 0);
+  int64_t act_total = 0;
+  for (int i = 0; i < nbox_tree; ++i) {
+    act_off[i] = act_total;
+    act_total += sc.act0[i];
+  }
+  std::vector<int32_t> act_init(std::max<int64_t>(act_total, 1), 0);
+  for (int i = 0; i < nbox_tree; ++i)
+    if (T.boxes[i].leaf())
+      for (int64_t q = 0; q < sc.act0[i]; ++q) act_init[act_off[i] + q] = (int32_t)(T.boxes[i].first_pos + q);
+
+  std::vector<Seg> segs;
+  std::vector<std::pair<int64_t, int64_t>> level_seg(T.depth + 1, {0, 0});  // parent assembly per level
+  std::vector<BoxDesc> all_desc;
+  int64_t fd_total = 0, fi_total = 0, work_max = 0, iwork_max = 0;
+  for (int level = T.depth; level >= 1; --level) {
+    int64_t s0 = (int64_t)segs.size();
+    for (int b : T.levels[level])
+      if (!T.boxes[b].leaf()) {
+        int64_t dst = act_off[b];
+        for (int c : T.boxes[b].children) {
+          if (sc.act1[c] > 0) segs.push_back({act_off[c], dst, sc.act1[c]});
+          dst += sc.act1[c];
+        }
+      }
+    level_seg[level] = {s0, (int64_t)segs.size() - s0};
+    for (int col = 0; col < (int)sc.groups[level].size(); ++col) {
+      auto [first, last] = sc.groups[level][col];
+      if (first == last) continue;
+      Group g;
+      g.level = level;
+      g.colour = col;
+      g.desc_off = (int64_t)all_desc.size();
+      g.seg_off = (int64_t)segs.size();
+      g.max_panels = g.max_b = g.max_r = 0;
+      int64_t w = 0, iw = 0;
+      for (int si = first; si < last; ++si) {
+        const Step& stp = sc.steps[si];
+        BoxDesc d{};
+        d.b = (int32_t)stp.b;
+        d.n = (int32_t)stp.n;
+        d.l = (int32_t)(stp.b + stp.n);
+        d.kp = (int32_t)stp.kp;
+        d.r = (int32_t)stp.r;
+        d.bn_off = iw;
+        iw += d.l;
+        d.pv_off = iw;
+        iw += d.b;
+        d.g_off = w;
+        w += 2 * (int64_t)d.l * d.l;
+        d.x_off = w;
+        w += 2 * (int64_t)d.b * d.l;
+        d.x2_off = w;
+        if (passes > 1) w += 2 * (int64_t)d.b * d.l;
+        d.m_off = w;
+        w += (int64_t)d.b * 2 * s;
+        d.cp_off = w;
+        w += std::max<int64_t>((int64_t)d.kp * d.b, 2 * (int64_t)d.r * d.l);
+        d.fi_off = fi_total;
+        fi_total += fi_size(d.kp, d.r, d.n);
+        d.fd_off = fd_total;
+        fd_total += fd_size(d.kp, d.r, d.n);
+        d.act_off = act_off[stp.box];
+        // near-field list: own active points, then each neighbour's current active points
+        segs.push_back({act_off[stp.box], d.bn_off, stp.b});
+        int64_t pos = d.bn_off + stp.b;
+        for (size_t q = 0; q < stp.nbrs.size(); ++q) {
+          if (stp.nbr_len[q] > 0) segs.push_back({act_off[stp.nbrs[q]], pos, stp.nbr_len[q]});
+          pos += stp.nbr_len[q];
+        }
+        g.max_panels = std::max<int>(g.max_panels, (int)cdiv(d.l, kT));
+        g.max_b = std::max<int>(g.max_b, d.b);
+        g.max_r = std::max<int>(g.max_r, d.r);
+        g.h.push_back(d);
+        all_desc.push_back(d);
+      }
+      g.nseg = (int64_t)segs.size() - g.seg_off;
+      work_max = std::max(work_max, w);
+      iwork_max = std::max(iwork_max, iw);
+      f->max_r = std::max(f->max_r, g.max_r);
+      f->groups.push_back(std::move(g));
+    }
+  }
+  // root pseudo-box: B_t = what the level-1 boxes keep (or all points if the root is a leaf)
+  const int64_t nroot = (int64_t)sc.root.size();
+  f->root_size = nroot;
+  int64_t root_seg_off = (int64_t)segs.size();
+  BoxDesc rd{};
+  {
+    rd.b = rd.l = (int32_t)nroot;
+    rd.n = rd.kp = rd.r = 0;
+    rd.bn_off = 0;
+    rd.pv_off = nroot;
+    rd.g_off = 0;
+    rd.x_off = 2 * nroot * nroot;
+    rd.x2_off = rd.x_off;
+    rd.m_off = rd.x_off + 2 * nroot * nroot;
+    rd.cp_off = rd.m_off + nroot * 2 * s;
+    work_max = std::max(work_max, rd.cp_off + 1);
+    iwork_max = std::max(iwork_max, 2 * nroot);
+    if (T.depth == 0) {
+      segs.push_back({act_off[0], 0, nroot});
+    } else {
+      int64_t dst = 0;
+      for (int b : T.levels[1]) {
+        if (sc.act1[b] > 0) segs.push_back({act_off[b], dst, sc.act1[b]});
+        dst += sc.act1[b];
+      }
+    }
+  }
+  int64_t root_nseg = (int64_t)segs.size() - root_seg_off;
+  // root as a leaf: its pool slot is the whole point set
+  if (T.depth == 0)
+    for (int64_t q = 0; q < N; ++q) act_init[act_off[0] + q] = (int32_t)q;
+
+  // ---- device allocations --------------------------------------------------------
+  DevPool pool;
+  const int64_t NS = N * (int64_t)s;
+  double *Y, *Z, *Om, *Ps, *work;
+  int32_t *iwork, *act, *perm_dev;
+  Seg* segs_dev;
+  BoxDesc *desc_dev, *root_desc_dev;
+  int* err;
+  CU(pool.alloc(&Y, NS));
+  CU(pool.alloc(&Z, NS));
+  CU(pool.alloc(&Om, NS));
+  CU(pool.alloc(&Ps, NS));
+  CU(pool.alloc(&work, work_max));
+  CU(pool.alloc(&iwork, iwork_max));
+  CU(pool.alloc(&act, (int64_t)act_init.size()));
+  CU(pool.alloc(&segs_dev, (int64_t)segs.size()));
+  CU(pool.alloc(&desc_dev, (int64_t)all_desc.size()));
+  CU(pool.alloc(&root_desc_dev, 1));
+  CU(pool.alloc(&err, 1));
+  CU(pool.alloc(&perm_dev, N));
+  CU(pool.alloc(&f->pts_dev, N * T.d));
+  CU(pool.alloc(&f->fd, fd_total));
+  CU(pool.alloc(&f->fi, fi_total));
+  CU(pool.alloc(&f->root_idx, nroot));
+  CU(pool.alloc(&f->root_A, nroot * nroot));
+  CU(pool.alloc(&f->root_LU, nroot * nroot));
+  CU(pool.alloc(&f->root_piv, nroot));
+  f->fd_n = fd_total;
+  f->fi_n = fi_total;
+  f->desc_dev = desc_dev;
+  f->perm_dev = perm_dev;
+  {
+    std::vector<int32_t> p32(N);
+    for (int64_t q = 0; q < N; ++q) p32[q] = (int32_t)T.perm[q];
+    CU(cudaMemcpyAsync(perm_dev, p32.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(f->pts_dev, T.pts_tree.data(), N * T.d * sizeof(double), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(act, act_init.data(), act_init.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (!segs.empty())
+      CU(cudaMemcpyAsync(segs_dev, segs.data(), segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, st));
+    if (!all_desc.empty())
+      CU(cudaMemcpyAsync(desc_dev, all_desc.data(), all_desc.size() * sizeof(BoxDesc), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(root_desc_dev, &rd, sizeof(BoxDesc), cudaMemcpyHostToDevice, st));
+    CU(cudaMemsetAsync(err, 0, sizeof(int), st));
+    // test matrices: caller's (original order) or drawn here; stored in tree order
+    std::vector<double> host(NS);
+    std::vector<double> tree_order(NS);
+    for (int side = 0; side < 2; ++side) {
+      const double* src = side == 0 ? o.omega_host : o.psi_host;
+      if (!src) {
+        host_gaussian(o.seed * 2 + side + 1, NS, host.data());
+        src = host.data();
+      }
+      for (int64_t q = 0; q < N; ++q)
+        std::memcpy(&tree_order[q * s], &src[T.perm[q] * s], s * sizeof(double));
+      CU(cudaMemcpyAsync(side == 0 ? Om : Ps, tree_order.data(), NS * sizeof(double), cudaMemcpyHostToDevice, st));
+      CU(cudaStreamSynchronize(st));  // host staging buffers are reused
+    }
+  }
+
+  int64_t launches = 0;
+  Launch L{st, &launches};
+  cudaEvent_t ev[4];
+  for (auto& e : ev) CU(cudaEventCreate(&e));
+  CU(cudaEventRecord(ev[0], st));
+  // ---- a1: sampling Y = A Omega, Z = A* Psi -------------------------------------------
+  {
+    double *cm_in = nullptr, *cm_out = nullptr;
+    if (f->kind == RSRS_OP_CALLBACK) {
+      CU(pool.alloc(&cm_in, NS));
+      CU(pool.alloc(&cm_out, NS));
+    }
+    const int fp32 = (o.precision == RSRS_PREC_MIXED) ? 1 : 0;
+    rsrs_status r1 = op_apply(f.get(), L, Om, Y, s, 0, fp32, cm_in, cm_out);
+    if (r1 != RSRS_OK) return r1;
+    r1 = op_apply(f.get(), L, Ps, Z, s, 1, fp32, cm_in, cm_out);
+    if (r1 != RSRS_OK) return r1;
+  }
+  CU(cudaEventRecord(ev[1], st));
+  // ---- a2..a8: levels L..1, colour by colour ------------------------------------------
+  GroupArgs ga{};
+  ga.s = s;
+  ga.Y = Y;
+  ga.Z = Z;
+  ga.Om = Om;
+  ga.Ps = Ps;
+  ga.work = work;
+  ga.iwork = iwork;
+  ga.fd = f->fd;
+  ga.fi = f->fi;
+  ga.act = act;
+  ga.err = err;
+  size_t gi = 0;
+  for (int level = T.depth; level >= 1; --level) {
+    if (level_seg[level].second > 0)
+      launch_copy_segments(L, segs_dev + level_seg[level].first, (int)level_seg[level].second, act, act);
+    for (; gi < f->groups.size() && f->groups[gi].level == level; ++gi) {
+      const Group& g = f->groups[gi];
+      ga.desc = desc_dev + g.desc_off;
+      ga.nbox = (int)g.h.size();
+      launch_copy_segments(L, segs_dev + g.seg_off, (int)g.nseg, act, iwork);
+      launch_gram(L, ga, items_gram(g.h));
+      for (int p = 0; p < g.max_panels; ++p) {
+        launch_chol_panel(L, ga, p);
+        launch_chol_trsm(L, ga, p, items_chol_trsm(g.h, p));
+        launch_chol_update(L, ga, p, items_chol_update(g.h, p));
+      }
+      launch_gather_box(L, ga, items_gather(g.h));
+      for (int pass = 0; pass < passes; ++pass) {
+        launch_proj_nt(L, ga, pass, items_proj_nt(g.h));
+        launch_proj_solve(L, ga, pass, items_proj_solve(g.h));
+        launch_proj_acc(L, ga, pass, items_proj_acc(g.h, s));
+      }
+      launch_cpqr(L, ga, g.max_b);
+      launch_id_finish(L, ga, g.max_b);
+      launch_ef_update(L, ga, items_ef(g.h, s));
+      launch_extract(L, ga, items_extract(g.h));
+      launch_lu(L, ga);
+      launch_lu_rhs(L, ga, items_lu_rhs(g.h));
+      launch_schur(L, ga, items_schur(g.h, s));
+    }
+    CU(cudaGetLastError());
+  }
+  CU(cudaEventRecord(ev[2], st));
+  // ---- a9: root extraction A~_{Bt Bt} = Y_Bt pinv(Om_Bt), then LU ---------------------
+  if (nroot > 0) {
+    std::vector<BoxDesc> rh{rd};
+    ga.desc = root_desc_dev;
+    ga.nbox = 1;
+    launch_copy_segments(L, segs_dev + root_seg_off, (int)root_nseg, act, iwork);
+    launch_gram(L, ga, items_gram(rh));
+    for (int p = 0; p < (int)cdiv(nroot, kT); ++p) {
+      launch_chol_panel(L, ga, p);
+      launch_chol_trsm(L, ga, p, items_chol_trsm(rh, p));
+      launch_chol_update(L, ga, p, items_chol_update(rh, p));
+    }
+    launch_gather_box(L, ga, items_gather(rh));
+    launch_proj_nt(L, ga, 0, items_proj_nt(rh));
+    launch_proj_solve(L, ga, 0, items_proj_solve(rh));
+    CU(cudaMemcpyAsync(f->root_idx, iwork, nroot * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    CU(cudaMemcpyAsync(f->root_A, work + rd.x_off, nroot * nroot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CU(cudaMemcpyAsync(f->root_LU, work + rd.x_off, nroot * nroot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    launch_dense_lu(L, f->root_LU, nroot, f->root_piv, err);
+  }
+  CU(cudaEventRecord(ev[3], st));
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(st));
+  int herr = 0;
+  CU(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr == kDevSingular) return fail(RSRS_E_SINGULAR, "zero pivot in an LU factorization");
+  if (herr == kDevNonfinite) return fail(RSRS_E_NONFINITE, "non-finite or non-positive pivot");
+  float t01, t12, t23;
+  CU(cudaEventElapsedTime(&t01, ev[0], ev[1]));
+  CU(cudaEventElapsedTime(&t12, ev[1], ev[2]));
+  CU(cudaEventElapsedTime(&t23, ev[2], ev[3]));
+  for (auto& e : ev) cudaEventDestroy(e);
+  f->stats.n = N;
+  f->stats.s = s;
+  f->stats.k = k;
+  f->stats.n_boxes = (int64_t)all_desc.size();
+  f->stats.root_size = nroot;
+  f->stats.factor_bytes = fd_total * 8 + fi_total * 4 + nroot * nroot * 16 + nroot * 8;
+  f->stats.work_bytes = work_max * 8 + iwork_max * 4 + 4 * NS * 8;
+  f->stats.t_sample_ms = t01;
+  f->stats.t_compress_ms = t12;
+  f->stats.t_root_ms = t23;
+  f->stats.kernel_launches = launches;
+  // keep what the factor owns
+  for (void* p : {(void*)f->fd, (void*)f->fi, (void*)f->root_idx, (void*)f->root_A, (void*)f->root_LU,
+                  (void*)f->root_piv, (void*)f->desc_dev, (void*)f->perm_dev, (void*)f->pts_dev})
+    pool.release(p);
+  if (o.keep_sketches) {
+    f->Y = Y;
+    f->Z = Z;
+    f->Om = Om;
+    f->Ps = Ps;
+    for (void* p : {(void*)Y, (void*)Z, (void*)Om, (void*)Ps}) pool.release(p);
+  }
+  *out = f.release();
+  return RSRS_OK;
+}
+
+void rsrs_factor_free(rsrs_factor* f) {
+  if (!f) return;
+  for (void* p : {(void*)f->fd, (void*)f->fi, (void*)f->root_idx, (void*)f->root_A, (void*)f->root_LU,
+                  (void*)f->root_piv, (void*)f->desc_dev, (void*)f->perm_dev, (void*)f->pts_dev, (void*)f->Y,
+                  (void*)f->Z, (void*)f->Om, (void*)f->Ps})
+    if (p) cudaFree(p);
+  delete f;
+}
+
+}  // extern "C"
+
+// ---- sweeps on a tree-order row-major block ------------------------------------------
+namespace {
+
+rsrs_status sweep_solve(const rsrs_factor* f, Launch L, double* W, int nrhs, int adjoint) {
+  SweepArgs a{};
+  a.fd = f->fd;
+  a.fi = f->fi;
+  a.F = W;
+  a.nrhs = nrhs;
+  a.adjoint = adjoint;
+  // upward: V_1^-1 first (V^-1 = L E), or W^-* = U^* F^* for the adjoint
+  for (const Group& g : f->groups) {
+    a.desc = f->desc_dev + g.desc_off;
+    a.nbox = (int)g.h.size();
+    launch_sweep_op(L, a, /*C=R*/ 0, /*T*/ 0, /*trans*/ 1, /*B=S*/ 1, -1.0, items_sweep(g.h, 0));
+    if (!adjoint)
+      launch_sweep_op(L, a, 2, /*LcT*/ 1, 1, 0, -1.0, items_sweep(g.h, 2));
+    else
+      launch_sweep_op(L, a, 2, /*Uc*/ 2, 1, 0, -1.0, items_sweep(g.h, 2));
+  }
+  for (const Group& g : f->groups) {
+    a.desc = f->desc_dev + g.desc_off;
+    a.nbox = (int)g.h.size();
+    launch_sweep_diag(L, a, 1, items_diag(g.h, nrhs), g.max_r);
+  }
+  if (f->root_size > 0)
+    launch_dense_lu_solve(L, f->root_LU, f->root_piv, f->root_size, f->root_idx, W, nrhs, adjoint);
+  for (auto it = f->groups.rbegin(); it != f->groups.rend(); ++it) {
+    const Group& g = *it;
+    a.desc = f->desc_dev + g.desc_off;
+    a.nbox = (int)g.h.size();
+    if (!adjoint)
+      launch_sweep_op(L, a, 0, /*Uc*/ 2, 0, 2, -1.0, items_sweep(g.h, 0));
+    else
+      launch_sweep_op(L, a, 0, /*LcT*/ 1, 0, 2, -1.0, items_sweep(g.h, 0));
+    launch_sweep_op(L, a, /*C=S*/ 1, /*T*/ 0, 0, /*B=R*/ 0, -1.0, items_sweep(g.h, 1));
+  }
+  CU(cudaGetLastError());
+  return RSRS_OK;
+}
+
+rsrs_status sweep_apply(const rsrs_factor* f, Launch L, double* W, int nrhs, int adjoint) {
+  SweepArgs a{};
+  a.fd = f->fd;
+  a.fi = f->fi;
+  a.F = W;
+  a.nrhs = nrhs;
+  a.adjoint = adjoint;
+  for (const Group& g : f->groups) {  // W_1 first: F^-1 then U^-1 (or V^*: E^-* then L^-*)
+    a.desc = f->desc_dev + g.desc_off;
+    a.nbox = (int)g.h.size();
+    launch_sweep_op(L, a, 1, 0, 0, 0, 1.0, items_sweep(g.h, 1));
+    if (!adjoint)
+      launch_sweep_op(L, a, 0, 2, 0, 2, 1.0, items_sweep(g.h, 0));
+    else
+      launch_sweep_op(L, a, 0, 1, 0, 2, 1.0, items_sweep(g.h, 0));
+  }
+  for (const Group& g : f->groups) {
+    a.desc = f->desc_dev + g.desc_off;
+    a.nbox = (int)g.h.size();
+    launch_sweep_diag(L, a, 0, items_diag(g.h, nrhs), g.max_r);
+  }
+  if (f->root_size > 0) launch_dense_apply(L, f->root_A, f->root_size, f->root_idx, W, nrhs, adjoint);
+  for (auto it = f->groups.rbegin(); it != f->groups.rend(); ++it) {  // V_M first: L^-1 then E^-1
+    const Group& g = *it;
+    a.desc = f->desc_dev + g.desc_off;
+    a.nbox = (int)g.h.size();
+    if (!adjoint)
+      launch_sweep_op(L, a, 2, 1, 1, 0, 1.0, items_sweep(g.h, 2));
+    else
+      launch_sweep_op(L, a, 2, 2, 1, 0, 1.0, items_sweep(g.h, 2));
+    launch_sweep_op(L, a, 0, 0, 1, 1, 1.0, items_sweep(g.h, 0));
+  }
+  CU(cudaGetLastError());
+  return RSRS_OK;
+}
+
+rsrs_status check_block(const rsrs_factor* f, const void* F, int64_t ld, int32_t nrhs) {
+  if (!f || !F) return fail(RSRS_E_INVAL, "null factor or block");
+  if (nrhs <= 0 || nrhs > 4096 || ld < f->n) return fail(RSRS_E_INVAL, "need 0 < nrhs <= 4096 and ld >= N");
+  return RSRS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rsrs_status rsrs_solve(const rsrs_factor* f, double* F, int64_t ldf, int32_t nrhs, int adjoint, void* stream) {
+  rsrs_status r = check_block(f, F, ldf, nrhs);
+  if (r != RSRS_OK) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  Launch L{st, nullptr};
+  DevPool pool;
+  double* W;
+  CU(pool.alloc(&W, f->n * nrhs));
+  k_cm_to_rows<<<nblk(f->n * nrhs), 256, 0, st>>>(F, ldf, f->perm_dev, f->n, nrhs, W);
+  r = sweep_solve(f, L, W, nrhs, adjoint);
+  if (r != RSRS_OK) return r;
+  k_rows_to_cm<<<nblk(f->n * nrhs), 256, 0, st>>>(W, f->perm_dev, f->n, nrhs, F, ldf);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(st));
+  return RSRS_OK;
+}
+
+rsrs_status rsrs_apply(const rsrs_factor* f, double* F, int64_t ldf, int32_t nrhs, int adjoint, void* stream) {
+  rsrs_status r = check_block(f, F, ldf, nrhs);
+  if (r != RSRS_OK) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  Launch L{st, nullptr};
+  DevPool pool;
+  double* W;
+  CU(pool.alloc(&W, f->n * nrhs));
+  k_cm_to_rows<<<nblk(f->n * nrhs), 256, 0, st>>>(F, ldf, f->perm_dev, f->n, nrhs, W);
+  r = sweep_apply(f, L, W, nrhs, adjoint);
+  if (r != RSRS_OK) return r;
+  k_rows_to_cm<<<nblk(f->n * nrhs), 256, 0, st>>>(W, f->perm_dev, f->n, nrhs, F, ldf);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(st));
+  return RSRS_OK;
+}
+
+rsrs_status rsrs_matvec(const rsrs_factor* f, const double* X, double* Yout, int64_t ld, int32_t nrhs,
+                        void* stream) {
+  rsrs_status r = check_block(f, X, ld, nrhs);
+  if (r != RSRS_OK) return r;
+  if (!Yout) return fail(RSRS_E_INVAL, "null output");
+  cudaStream_t st = (cudaStream_t)stream;
+  Launch L{st, nullptr};
+  DevPool pool;
+  double *Wx, *Wy, *c1 = nullptr, *c2 = nullptr;
+  CU(pool.alloc(&Wx, f->n * nrhs));
+  CU(pool.alloc(&Wy, f->n * nrhs));
+  if (f->kind == RSRS_OP_CALLBACK) {
+    CU(pool.alloc(&c1, f->n * nrhs));
+    CU(pool.alloc(&c2, f->n * nrhs));
+  }
+  k_cm_to_rows<<<nblk(f->n * nrhs), 256, 0, st>>>(X, ld, f->perm_dev, f->n, nrhs, Wx);
+  r = op_apply(f, L, Wx, Wy, nrhs, 0, 0, c1, c2);
+  if (r != RSRS_OK) return r;
+  k_rows_to_cm<<<nblk(f->n * nrhs), 256, 0, st>>>(Wy, f->perm_dev, f->n, nrhs, Yout, ld);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(st));
+  return RSRS_OK;
+}
+
+rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_t ld, int32_t nrhs, double rtol,
+                        int maxit, void* stream, rsrs_refine_report* rep) {
+  rsrs_status r = check_block(f, B, ld, nrhs);
+  if (r != RSRS_OK) return r;
+  if (!X || nrhs > 64 || maxit < 0 || !(rtol >= 0.0)) return fail(RSRS_E_INVAL, "refine: bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  Launch L{st, nullptr};
+  DevPool pool;
+  const int64_t tot = f->n * nrhs;
+  double *Wb, *Wx, *Wr, *Wax, *nrm, *c1 = nullptr, *c2 = nullptr;
+  CU(pool.alloc(&Wb, tot));
+  CU(pool.alloc(&Wx, tot));
+  CU(pool.alloc(&Wr, tot));
+  CU(pool.alloc(&Wax, tot));
+  CU(pool.alloc(&nrm, 2 * 64));
+  if (f->kind == RSRS_OP_CALLBACK) {
+    CU(pool.alloc(&c1, tot));
+    CU(pool.alloc(&c2, tot));
+  }
+  k_cm_to_rows<<<nblk(tot), 256, 0, st>>>(B, ld, f->perm_dev, f->n, nrhs, Wb);
+  CU(cudaMemcpyAsync(Wx, Wb, tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  r = sweep_solve(f, L, Wx, nrhs, 0);
+  if (r != RSRS_OK) return r;
+  double hn[128];
+  CU(cudaMemsetAsync(nrm, 0, 64 * sizeof(double), st));
+  k_colnorm2<<<std::min<int64_t>(1024, nblk(tot)), 256, 0, st>>>(Wb, f->n, nrhs, nrm);
+  CU(cudaMemcpyAsync(hn, nrm, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  std::vector<double> bn(hn, hn + nrhs);
+  rsrs_refine_report rr{};
+  double rel = 0.0;
+  int it = 0;
+  for (;; ++it) {
+    r = op_apply(f, L, Wx, Wax, nrhs, 0, 0, c1, c2);
+    if (r != RSRS_OK) return r;
+    k_sub<<<nblk(tot), 256, 0, st>>>(Wr, Wb, Wax, tot);
+    CU(cudaMemsetAsync(nrm, 0, 64 * sizeof(double), st));
+    k_colnorm2<<<std::min<int64_t>(1024, nblk(tot)), 256, 0, st>>>(Wr, f->n, nrhs, nrm);
+    CU(cudaMemcpyAsync(hn, nrm, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    rel = 0.0;
+    for (int j = 0; j < nrhs; ++j) rel = std::max(rel, std::sqrt(hn[j]) / std::max(std::sqrt(bn[j]), 1e-300));
+    if (it < 64) rr.history[it] = rel;
+    if (!std::isfinite(rel)) return fail(RSRS_E_NONFINITE, "refine: non-finite residual");
+    if (rel <= rtol || it >= maxit) break;
+    r = sweep_solve(f, L, Wr, nrhs, 0);
+    if (r != RSRS_OK) return r;
+    k_axpy<<<nblk(tot), 256, 0, st>>>(Wx, Wr, 1.0, tot);
+  }
+  k_rows_to_cm<<<nblk(tot), 256, 0, st>>>(Wx, f->perm_dev, f->n, nrhs, X, ld);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(st));
+  rr.iterations = it;
+  rr.rel_residual = rel;
+  if (rep) *rep = rr;
+  if (rel > rtol) return fail(RSRS_E_NOT_CONVERGED, "refine: residual " + std::to_string(rel) + " > rtol");
+  return RSRS_OK;
+}
+
+rsrs_status rsrs_factor_stats(const rsrs_factor* f, rsrs_stats* out) {
+  if (!f || !out) return fail(RSRS_E_INVAL, "null argument");
+  *out = f->stats;
+  return RSRS_OK;
+}
+
+rsrs_status rsrs_factor_box(const rsrs_factor* f, int64_t i, rsrs_box_view* v) {
+  if (!f || !v || i < 0) return fail(RSRS_E_INVAL, "null argument");
+  int64_t acc = 0;
+  for (const Group& g : f->groups) {
+    if (i < acc + (int64_t)g.h.size()) {
+      const BoxDesc& d = g.h[i - acc];
+      v->level = g.level;
+      v->colour = g.colour;
+      v->b = d.b;
+      v->n = d.n;
+      v->kp = d.kp;
+      v->r = d.r;
+      const int64_t w = (int64_t)d.kp + d.n;
+      std::vector<int32_t> idx(fi_size(d.kp, d.r, d.n));
+      CU(cudaMemcpy(idx.data(), f->fi + d.fi_off, idx.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+      auto orig = [&](int32_t t) { return f->perm[t]; };
+      if (v->R)
+        for (int q = 0; q < d.r; ++q) v->R[q] = orig(idx[q]);
+      if (v->S)
+        for (int q = 0; q < d.kp; ++q) v->S[q] = orig(idx[d.r + q]);
+      if (v->N)
+        for (int q = 0; q < d.n; ++q) v->N[q] = orig(idx[d.r + d.kp + q]);
+      std::vector<double> fd(fd_size(d.kp, d.r, d.n));
+      CU(cudaMemcpy(fd.data(), f->fd + d.fd_off, fd.size() * sizeof(double), cudaMemcpyDeviceToHost));
+      const double* T = fd.data();
+      const double* XRR = T + (int64_t)d.kp * d.r;
+      const double* LcT = XRR + 2 * (int64_t)d.r * d.r;
+      const double* Uc = LcT + (int64_t)d.r * w;
+      if (v->T) std::memcpy(v->T, T, sizeof(double) * d.kp * d.r);
+      if (v->XRR) std::memcpy(v->XRR, XRR, sizeof(double) * d.r * d.r);
+      for (int64_t a = 0; a < d.r; ++a)
+        for (int64_t q = 0; q < w; ++q) {
+          double lc = LcT[a * w + q], uc = Uc[a * w + q];
+          if (q < d.kp) {
+            if (v->LcS) v->LcS[q * d.r + a] = lc;
+            if (v->UcS) v->UcS[a * d.kp + q] = uc;
+          } else {
+            if (v->LcN) v->LcN[(q - d.kp) * d.r + a] = lc;
+            if (v->UcN) v->UcN[a * d.n + (q - d.kp)] = uc;
+          }
+        }
+      return RSRS_OK;
+    }
+    acc += (int64_t)g.h.size();
+  }
+  return fail(RSRS_E_INVAL, "box index out of range");
+}
+
+rsrs_status rsrs_factor_root(const rsrs_factor* f, int64_t* idx, double* A, int64_t* size_out) {
+  if (!f) return fail(RSRS_E_INVAL, "null factor");
+  if (size_out) *size_out = f->root_size;
+  if (idx && f->root_size) {
+    std::vector<int32_t> t(f->root_size);
+    CU(cudaMemcpy(t.data(), f->root_idx, t.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    for (int64_t q = 0; q < f->root_size; ++q) idx[q] = f->perm[t[q]];
+  }
+  if (A && f->root_size)
+    CU(cudaMemcpy(A, f->root_A, f->root_size * f->root_size * sizeof(double), cudaMemcpyDeviceToHost));
+  return RSRS_OK;
+}
+
+rsrs_status rsrs_factor_sketches(const rsrs_factor* f, double* Yh, double* Zh, double* Omh, double* Psh) {
+  if (!f || !f->Y) return fail(RSRS_E_INVAL, "sketches were not kept (keep_sketches = 0)");
+  const int64_t N = f->n, s = f->s;
+  std::vector<double> tmp(N * s);
+  const double* src[4] = {f->Y, f->Z, f->Om, f->Ps};
+  double* dst[4] = {Yh, Zh, Omh, Psh};
+  for (int m = 0; m < 4; ++m) {
+    if (!dst[m]) continue;
+    CU(cudaMemcpy(tmp.data(), src[m], N * s * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int64_t q = 0; q < N; ++q) std::memcpy(dst[m] + f->perm[q] * s, &tmp[q * s], s * sizeof(double));
+  }
+  return RSRS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,172 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the same seeded inputs.
+
+Tolerances: the FP64 path follows a different but algebraically equivalent
+formulation (projector I - W^T (W W^T)^-1 W with two passes, least squares by
+Cholesky; the oracle uses an explicit null basis and QR-based pseudoinverses),
+so results agree to rounding amplified by the conditioning of the near-field
+test rows (cond([Om_B; Om_N]) ~ (sqrt s + sqrt l)/(sqrt s - sqrt l), about
+10..100 here): 1e-9 relative on factor blocks and 1e-10 on solutions.  Skeleton
+sets must be identical.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import operators as ops
+from oracle import refine as oref
+from oracle import rsrs as orsrs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+BLOCK_TOL = 1e-9
+SOLVE_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2311_01451_gb300 as pkg
+
+    return pkg
+
+
+def _gpu_factor(R, pr, s, precision=0, passes=0, keep=False):
+    t = R.Tree(pr.points, pr.leaf)
+    return R.Factor(t, R.kind_of(pr.kernel), pr.k, s, shift=pr.diag_shift, scale=pr.scale, precision=precision,
+                    omega=pr.omega(s), psi=pr.psi(s), passes=passes, keep_sketches=keep)
+
+
+def _to_gpu(b):
+    return torch.tensor(np.ascontiguousarray(np.asarray(b).T), device="cuda", dtype=torch.float64)
+
+
+def _from_gpu(x):
+    return x.cpu().numpy().T
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+CASES = {
+    "grid2d_1024": lambda: W.small_problem(n_side=32, leaf=16, k=8, nrhs=3),
+    "rand2d_3000": lambda: W.small_problem(n=3000, d=2, leaf=24, k=10, nrhs=2, seed_problem=3),
+    "rand3d_1500": lambda: W.small_problem(n=1500, d=3, kernel="invr3d", leaf=20, k=8, nrhs=2, seed_problem=4),
+    "clustered2d": lambda: W.kernel_problem(
+        90, "clustered", np.vstack([W.uniform_points(1200, 2, W.rng_for(90, 7, 0)) * 0.05 + 0.3,
+                                    W.uniform_points(800, 2, W.rng_for(90, 8, 0))]), "log2d", 16, 8, 0, 2),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request, R):
+    pr = CASES[request.param]()
+    tree, sched, fac, sk = orsrs.build(pr)
+    f = _gpu_factor(R, pr, fac.s, keep=True)
+    return pr, fac, f, sk
+
+
+def test_skeletons_and_blocks_match_oracle(case):
+    pr, fac, f, _ = case
+    assert f.stats().n_boxes == len(fac.boxes)
+    worst = 0.0
+    for i, bf in enumerate(fac.boxes):
+        g = f.box(i)
+        assert np.array_equal(g["S"], bf.S), f"box {i}: skeleton sets differ"
+        assert np.array_equal(g["R"], bf.R)
+        assert np.array_equal(g["N"], bf.N)
+        for nm, ref in (("T", bf.T), ("XRR", bf.XRR), ("LcS", bf.LcS), ("LcN", bf.LcN), ("UcS", bf.UcS),
+                        ("UcN", bf.UcN)):
+            if ref.size:
+                e = np.abs(g[nm] - ref).max() / max(np.abs(ref).max(), 1e-300)
+                worst = max(worst, e)
+                assert e < BLOCK_TOL, f"box {i} {nm}: {e:.2e}"
+    idx, a = f.root()
+    assert np.array_equal(idx, fac.root)
+    assert np.abs(a - fac.root_A).max() / np.abs(fac.root_A).max() < BLOCK_TOL
+
+
+def test_final_sketches_match_oracle(case):
+    pr, fac, f, _ = case
+    Y, Z, Om, Ps = f.sketches()
+    fin = fac.final
+    for a, b in ((Y, fin["Y"]), (Z, fin["Z"]), (Om, fin["Om"]), (Ps, fin["Ps"])):
+        assert np.abs(a - b).max() / np.abs(b).max() < BLOCK_TOL
+
+
+def test_solve_apply_match_oracle(case):
+    pr, fac, f, _ = case
+    b = pr.rhs()
+    for adj in (False, True):
+        x = _from_gpu(f.solve(_to_gpu(b), adjoint=adj))
+        assert _rel(x, orsrs.solve(fac, b, adjoint=adj)) < SOLVE_TOL
+        y = _from_gpu(f.apply(_to_gpu(b), adjoint=adj))
+        assert _rel(y, orsrs.apply(fac, b, adjoint=adj)) < SOLVE_TOL
+    # exact inverse pair on the device
+    z = f.apply(f.solve(_to_gpu(b)))
+    assert _rel(_from_gpu(z), b) < 1e-12
+
+
+def test_sampling_matvec_matches_dense(case):
+    pr, fac, f, sk = case
+    a = ops.make_operator(pr).dense()
+    x = np.random.default_rng(1).standard_normal((pr.n, 5))
+    y = _from_gpu(f.matvec(_to_gpu(x), torch.empty((5, pr.n), device="cuda", dtype=torch.float64)))
+    assert _rel(y, a @ x) < 1e-13
+
+
+def test_refine_fp64_reaches_dense_solution(case):
+    pr, fac, f, _ = case
+    b = pr.rhs()
+    xd = np.linalg.solve(ops.make_operator(pr).dense(), b)
+    X = torch.zeros_like(_to_gpu(b))
+    rep = f.refine(_to_gpu(b), X, rtol=1e-13, maxit=30)
+    assert rep.rel_residual <= 1e-13
+    assert _rel(_from_gpu(X), xd) < 1e-11
+
+
+def test_mixed_precision_refined_matches_fp64_oracle(R, case):
+    pr, fac, _, _ = case
+    fm = _gpu_factor(R, pr, fac.s, precision=R.RSRS_PREC_MIXED)
+    b = pr.rhs()
+    x_ref, hist = oref.refine(fac, ops.make_operator(pr), b, rtol=1e-14, maxit=40)
+    X = torch.zeros_like(_to_gpu(b))
+    rep = fm.refine(_to_gpu(b), X, rtol=1e-12, maxit=40)
+    assert rep.rel_residual <= 1e-12
+    assert _rel(_from_gpu(X), x_ref) < SOLVE_TOL
+
+
+def test_single_pass_projection_still_matches(R):
+    pr = CASES["grid2d_1024"]()
+    tree, sched, fac, _ = orsrs.build(pr)
+    f = _gpu_factor(R, pr, fac.s, passes=1)
+    for i, bf in enumerate(fac.boxes):
+        assert np.array_equal(f.box(i)["S"], bf.S)
+    b = pr.rhs()
+    assert _rel(_from_gpu(f.solve(_to_gpu(b))), orsrs.solve(fac, b)) < 1e-8
+
+
+def test_root_only_tree(R):
+    """Degenerate case: N <= leaf capacity, nothing is compressed, the factor is a dense LU."""
+    pr = W.small_problem(n=40, d=2, leaf=64, k=8, nrhs=2, seed_problem=9)
+    tree, sched, fac, _ = orsrs.build(pr)
+    assert not fac.boxes and len(fac.root) == 40
+    f = _gpu_factor(R, pr, fac.s)
+    b = pr.rhs()
+    assert _rel(_from_gpu(f.solve(_to_gpu(b))), np.linalg.solve(ops.make_operator(pr).dense(), b)) < 1e-12
+
+
+def test_workload_grid_64x64(R):
+    """The 64x64-grid workload (N=4096, leaf 64, k=32) at s = s_req, against the oracle."""
+    pr = W.config(0)[0]
+    tree, sched, fac, _ = orsrs.build(pr)
+    f = _gpu_factor(R, pr, fac.s)
+    for i, bf in enumerate(fac.boxes):
+        assert np.array_equal(f.box(i)["S"], bf.S)
+    b = pr.rhs()
+    assert _rel(_from_gpu(f.solve(_to_gpu(b))), orsrs.solve(fac, b)) < SOLVE_TOL

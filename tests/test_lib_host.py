@@ -1,0 +1,84 @@
+"""Host-side checks of librsrs (no GPU needed): symbols, tree parity with the oracle, argument errors."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.tree import Schedule as OSchedule
+from oracle.tree import Tree as OTree
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def R():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2311_01451_gb300 as pkg
+
+    return pkg
+
+
+def test_every_declared_symbol_is_exported(R):
+    hdr = open(os.path.join(ROOT, "include", "rsrs.h")).read()
+    declared = set(re.findall(r"\b(rsrs_[a-z_]+)\s*\(", hdr)) - {"rsrs_matvec_fn"}
+    lib = R.lib()
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    assert set(R.rsrs.EXPORTS) <= declared
+
+
+@pytest.mark.parametrize("case", ["grid2d", "rand2d", "rand3d", "clustered2d"])
+def test_tree_and_schedule_match_oracle(R, case):
+    if case == "grid2d":
+        pts, leaf, k = W.grid_points_2d(64), 64, 32
+    elif case == "rand2d":
+        pts, leaf, k = W.uniform_points(20000, 2, W.rng_for(96, 0, 0)), 64, 24
+    elif case == "rand3d":
+        pts, leaf, k = W.uniform_points(6000, 3, W.rng_for(96, 1, 0)), 32, 16
+    else:
+        pts = np.vstack([W.uniform_points(3000, 2, W.rng_for(96, 2, 0)) * 0.03 + 0.5,
+                         W.uniform_points(2000, 2, W.rng_for(96, 3, 0))])
+        leaf, k = 20, 8
+    t = R.Tree(pts, leaf)
+    ot = OTree(pts, leaf)
+    osc = OSchedule(ot, k)
+    info = t.info(k)
+    assert info.depth == ot.depth
+    assert np.array_equal(t.perm(), ot.perm)
+    assert info.s_req == osc.s_req and info.root_size == osc.root_size and info.max_l == osc.max_l
+    sch = t.schedule(k)
+    ref = np.array([[st["level"], st["colour"], st["b"], st["n"], st["box"].first_pos] for st in osc.steps])
+    assert np.array_equal(sch[:, [0, 1, 3, 4, 5]], ref)
+
+
+def test_sample_bound_matches_paper(R):
+    t = R.Tree(W.grid_points_2d(284), 160)
+    assert t.info(40).s_req == 1520  # 37k + p, Exp. 1
+
+
+def test_invalid_arguments(R):
+    lib = R.lib()
+    h = C.c_void_p()
+    assert lib.rsrs_tree_build(None, 10, 2, 4, C.byref(h)) == 1
+    pts = np.zeros((10, 4))
+    assert lib.rsrs_tree_build(pts.ctypes.data_as(C.c_void_p), 10, 4, 4, C.byref(h)) == 1
+    bad = W.uniform_points(10, 2, W.rng_for(97, 0, 0))
+    bad[3, 0] = np.nan
+    assert lib.rsrs_tree_build(bad.ctypes.data_as(C.c_void_p), 10, 2, 4, C.byref(h)) == 1
+    assert lib.rsrs_status_string(2) == b"sample count below the bound s_req"
+
+
+def test_undersampled_rejected_before_device_work(R):
+    t = R.Tree(W.grid_points_2d(64), 64)
+    s_req = t.info(32).s_req
+    with pytest.raises(R.RSRSError) as e:
+        R.Factor(t, R.RSRS_OP_LOG2D, 32, 400, shift=1.0, scale=1 / 4096)  # the literal s of the 64x64 workload
+    assert e.value.name == "RSRS_E_UNDERSAMPLED" and s_req > 400
+    with pytest.raises(R.RSRSError) as e:
+        R.Factor(t, R.RSRS_OP_INVR3D, 32, s_req)  # 3D kernel on 2D points
+    assert e.value.name == "RSRS_E_INVAL"
