@@ -11,9 +11,12 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
   by column-pivoted Householder QR of M^T stopped after k steps (Sec. 2.3:
   "standard pivoted QR with a greedy approach").  Column norms are recomputed
   from scratch every step; an exact tie goes to the lowest original column.
-  T = R11^-1 R12, with the rows from the first numerically dependent pivot
-  (|R_jj| <= tau |R_00|, so an all-zero sketch gives T = 0) on set to zero
-  (truncated back-substitution).
+  Once the largest remaining residual norm is <= tau |R_00| the remaining
+  columns are numerically dependent: the rest of the k skeletons are taken in
+  ascending original order (a choice among noise-level residuals would not be
+  reproducible), and T = R11^-1 R12 is computed with the rows of those
+  dependent pivots set to zero (truncated back-substitution; an all-zero sketch
+  gives T = 0).
 * ``lu`` -- LU with partial pivoting (LAPACK getrf via scipy).
 """
 from __future__ import annotations
@@ -46,16 +49,25 @@ def cpqr_id(m: np.ndarray, k: int, tau: float):
     a = np.array(m.T, dtype=np.float64, copy=True)  # c x b: pivot over columns = rows of m
     c, b = a.shape
     perm = np.arange(b)
+    r00 = None
+    j0 = k
     for j in range(k):
         norms = np.sqrt(np.sum(a[j:, j:] ** 2, axis=0))
         best = norms.max()
-        cand = np.nonzero(norms == best)[0]
-        p = j + cand[np.argmin(perm[j + cand])]
+        if r00 is not None and best <= tau * r00 or best == 0.0:
+            j0 = min(j0, j)
+        if j0 <= j:  # dependent: lowest remaining original index
+            p = j + int(np.argmin(perm[j:]))
+        else:
+            cand = np.nonzero(norms == best)[0]
+            p = j + cand[np.argmin(perm[j + cand])]
         if p != j:
             a[:, [j, p]] = a[:, [p, j]]
             perm[[j, p]] = perm[[p, j]]
         x = a[j:, j]
         alpha = np.linalg.norm(x)
+        if r00 is None:
+            r00 = alpha
         if alpha == 0.0:
             continue
         sign = 1.0 if x[0] >= 0 else -1.0
@@ -65,12 +77,6 @@ def cpqr_id(m: np.ndarray, k: int, tau: float):
         a[j:, j:] -= 2.0 * np.outer(v, v @ a[j:, j:])
     r11 = np.triu(a[:k, :k])
     r12 = a[:k, k:]
-    diag = np.abs(np.diag(r11))
-    j0 = k
-    if k > 0:
-        small = np.nonzero(diag <= tau * diag[0])[0]
-        if len(small):
-            j0 = int(small[0])
     t = np.zeros((k, b - k))
     if j0 > 0:
         t[:j0] = sla.solve_triangular(r11[:j0, :j0], r12[:j0], lower=False)

@@ -39,9 +39,17 @@ from .tree import Schedule, Tree
 EPS = np.finfo(np.float64).eps
 
 
+ID_FLOOR = 1e-10
+
+
 def id_tau(b: int, s: int) -> float:
-    """Relative threshold below which a CPQR pivot counts as numerically dependent."""
-    return 64.0 * EPS * max(b, 2 * s)
+    """Relative residual below which CPQR pivots count as numerically dependent.
+
+    The nullified sketch carries rounding of about 1e-12..1e-11 of its norm
+    (the near field it cancels is 1e2..1e4 times larger), so residuals below
+    1e-10 |R_00| cannot be ranked reproducibly in FP64; 64 eps max(b, 2s)
+    bounds the rounding of the Householder steps themselves."""
+    return max(ID_FLOOR, 64.0 * EPS * max(b, 2 * s))
 
 
 @dataclass
@@ -79,8 +87,11 @@ def _tree_sorted(idx: np.ndarray, pos: np.ndarray) -> np.ndarray:
     return idx[np.argsort(pos[idx], kind="stable")]
 
 
-def factor(tree: Tree, sched: Schedule, Y, Z, Om, Ps, trace=None) -> Factor:
-    """Algorithm 1 on copies of the sketch quartet.  ``trace`` (a list) receives per-box dumps."""
+def factor(tree: Tree, sched: Schedule, Y, Z, Om, Ps, trace=None, max_steps: int | None = None) -> Factor:
+    """Algorithm 1 on copies of the sketch quartet.  ``trace`` (a list) receives per-box dumps.
+
+    ``max_steps`` stops after that many compressed boxes and skips the root (used
+    only to time a bounded sample of a large workload)."""
     Y, Z, Om, Ps = (np.array(a, dtype=np.float64, copy=True) for a in (Y, Z, Om, Ps))
     n, s = Y.shape
     k = sched.k
@@ -94,6 +105,8 @@ def factor(tree: Tree, sched: Schedule, Y, Z, Om, Ps, trace=None) -> Factor:
             if not b.is_leaf:
                 act[b.id] = np.concatenate([act[c.id] for c in b.children])
         for st in steps_by_level.get(level, []):
+            if max_steps is not None and len(fac.boxes) >= max_steps:
+                return fac
             box = st["box"]
             Bact = act[box.id]
             Nact = (np.concatenate([act[c.id] for c in st["nbrs"]]) if st["nbrs"]
@@ -138,7 +151,7 @@ def factor(tree: Tree, sched: Schedule, Y, Z, Om, Ps, trace=None) -> Factor:
                            T=T, XRR=XRR, lu=f, LcS=LcS, LcN=LcN, UcS=UcS, UcN=UcN, XRR_z=Xz[:, red].T)
             fac.boxes.append(bf)
             if trace is not None:
-                trace.append(dict(box=bf, Yp=Yp, Zp=Zp, Y=Y.copy(), Z=Z.copy(), Om=Om.copy(), Ps=Ps.copy()))
+                trace.append(dict(box=bf, Yp=Yp, Zp=Zp))
     if tree.depth == 0:
         Bt = np.arange(n)
     else:
