@@ -82,10 +82,16 @@ typedef struct {
   int precision;          /* RSRS_PREC_*                                               */
   int p;                  /* oversampling; < 0 selects p = k (Sec. 5)                  */
   int proj_passes;        /* projection passes of the nullification (1 or 2; 0 -> 2)   */
-  uint64_t seed;          /* used only when omega/psi are NULL                         */
+  uint64_t seed;          /* key of the device Philox4x32-10 draws used when no test   */
+                          /* matrices are given: entry (i, c) of Omega (Psi) is member */
+                          /* (i*s+c) mod 2 of the Box-Muller pair from counter         */
+                          /* ((i*s+c)/2, stream 0 (1)), two 53-bit uniforms per pair   */
   const double* omega_host; /* optional caller test matrices, row-major N x s in        */
   const double* psi_host;   /* ORIGINAL point order (point i's samples contiguous)      */
+  const double* omega_dev;  /* same, in device memory (used when the host ones are NULL) */
+  const double* psi_dev;
   int keep_sketches;      /* keep the final Y, Z, Omega, Psi on the device (tests)     */
+  int profile;            /* record CUDA-event time per kernel class into rsrs_stats    */
 } rsrs_options;
 
 typedef struct {
@@ -101,6 +107,13 @@ typedef struct {
   int64_t s_req;          /* smallest admissible s: max(max_l + k + p, |B_t|)         */
 } rsrs_tree_info_t;
 
+/* Kernel classes of the build, for per-class timings and algorithmic FLOP counts. */
+enum {
+  RSRS_K_SAMPLE = 0, RSRS_K_LISTS, RSRS_K_GRAM, RSRS_K_CHOL, RSRS_K_GATHER, RSRS_K_PROJ_NT,
+  RSRS_K_PROJ_SOLVE, RSRS_K_PROJ_ACC, RSRS_K_CPQR, RSRS_K_ID, RSRS_K_EF, RSRS_K_EXTRACT, RSRS_K_LU,
+  RSRS_K_LU_RHS, RSRS_K_SCHUR, RSRS_K_ROOT, RSRS_NCLASS
+};
+
 typedef struct {
   int64_t n, s, k;
   int64_t n_boxes;        /* compressed boxes (factor blocks)                         */
@@ -109,7 +122,13 @@ typedef struct {
   int64_t work_bytes;     /* peak device workspace of the build                       */
   double t_sample_ms, t_compress_ms, t_root_ms;  /* stream-event timings of the build */
   int64_t kernel_launches; /* kernels launched by the last build                     */
+  double class_ms[RSRS_NCLASS];       /* CUDA-event time per class (opts.profile only)   */
+  double class_gflop[RSRS_NCLASS];    /* algorithmic GFLOP per class (always filled)     */
+  int64_t class_launches[RSRS_NCLASS];
 } rsrs_stats;
+
+/* Name of a kernel class ("gram", "schur", ...). */
+const char* rsrs_kernel_class_name(int cls);
 
 typedef struct {
   int iterations;         /* corrections applied after the first solve                */

@@ -24,7 +24,7 @@ struct BoxDesc {
   int64_t x2_off;   // double work: two b x l second-pass blocks
   int64_t m_off;    // double work: b x 2s projected sketches [Y' | Z']
   int64_t cp_off;   // double work: CPQR R rows, kp x b; then extraction blocks 2 x r x l
-  int64_t pv_off;   // int32 work: b CPQR local permutation
+  int64_t pv_off;   // int32 work: b CPQR local permutation, then the first dependent step
   int64_t fi_off;   // int32 factor: R (r), S (kp), N (n), LU pivots (r)
   int64_t fd_off;   // double factor: T (kp x r), XRR (r x r), LU (r x r), LcT (r x (kp+n)), Uc (r x (kp+n))
   int64_t act_off;  // int32 active-list pool slot of the box

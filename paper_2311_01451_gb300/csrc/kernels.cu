@@ -580,21 +580,31 @@ __global__ void __launch_bounds__(NT) k_proj_acc(GroupArgs g, int pass) {
 
 // Column-pivoted Householder QR of M^T (pivoting over the b rows of M), kp steps.
 // One CTA per box; the reflectors act on the 2s columns of M in place.
+// Once the largest remaining residual is <= tau |R_00| (tau = max(1e-10,
+// 64 eps max(b, 2s))) the remaining pivots are numerically dependent and are
+// taken in ascending local (tree) order; the first such step is stored after
+// the permutation for the interpolation matrix.
 __global__ void __launch_bounds__(512) k_cpqr(GroupArgs g) {
   const BoxDesc d = g.desc[blockIdx.x];
   const int b = d.b, kp = d.kp;
   const int64_t c = 2 * g.s;
   double* M = g.work + d.m_off;
-  double* Rp = g.work + d.cp_off;  // kp x b, Rp[j][pos]
+  double* Rp = g.work + d.cp_off;  // kp x b, Rp[j][local row id]: row j of R, columns by point
   int32_t* perm = g.iwork + d.pv_off;
   extern __shared__ double sm[];
   double* nrm = sm;                       // b
   int* rid = (int*)(sm + b);              // b
   __shared__ double red_v[32];
   __shared__ int red_i[32];
-  __shared__ double s_vn2;
+  __shared__ double s_vn2, s_r00;
+  __shared__ int s_j0;
+  const double tau = fmax(1e-10, 64.0 * DBL_EPSILON * (double)max(b, (int)(2 * g.s)));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = threadIdx.x; i < b; i += blockDim.x) rid[i] = i;
+  if (threadIdx.x == 0) {
+    s_r00 = -1.0;
+    s_j0 = kp;
+  }
   // initial squared row norms
   for (int i = warp; i < b; i += nw) {
     const double* row = M + (int64_t)i * c;
@@ -643,6 +653,12 @@ __global__ void __launch_bounds__(512) k_cpqr(GroupArgs g) {
         p0 = j;
         set_err(g.err, kDevNonfinite);
       }
+      if (s_j0 == kp && ((s_r00 >= 0.0 && sqrt(v0) <= tau * s_r00) || v0 == 0.0)) s_j0 = j;
+      if (s_j0 <= j) {  // dependent: lowest remaining local index
+        p0 = j;
+        for (int pos = j + 1; pos < b; ++pos)
+          if (rid[pos] < rid[p0]) p0 = pos;
+      }
       if (p0 != j) {
         int ti = rid[j];
         rid[j] = rid[p0];
@@ -668,7 +684,8 @@ __global__ void __launch_bounds__(512) k_cpqr(GroupArgs g) {
         double x0 = x[j];
         double sg = (x0 >= 0.0) ? 1.0 : -1.0;
         s_vn2 = 2.0 * alpha * (alpha + fabs(x0));
-        Rp[(int64_t)j * b + j] = -sg * alpha;
+        if (j == 0) s_r00 = alpha;
+        Rp[(int64_t)j * b + rid[j]] = -sg * alpha;
         x[j] = x0 + sg * alpha;
       }
       __syncthreads();
@@ -691,12 +708,13 @@ __global__ void __launch_bounds__(512) k_cpqr(GroupArgs g) {
       for (int o = 16; o; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
       if (lane == 0) {
         nrm[pos] = nn;
-        Rp[(int64_t)j * b + pos] = row[j];
+        Rp[(int64_t)j * b + rid[pos]] = row[j];
       }
     }
     __syncthreads();
   }
   for (int i = threadIdx.x; i < b; i += blockDim.x) perm[i] = rid[i];
+  if (threadIdx.x == 0) perm[b] = s_j0;
 }
 
 // T = R11^-1 R12 (truncated at the first dependent pivot), R/S/N lists, new active list.
@@ -727,17 +745,7 @@ __global__ void __launch_bounds__(256) k_id_finish(GroupArgs g) {
     for (int u = 0; u < kp; ++u) rank += perm[u] < v;
     ssort[rank] = v;
   }
-  if (threadIdx.x == 0) {
-    double tau = 64.0 * DBL_EPSILON * (double)imax64(b, 2 * g.s);
-    double r00 = fabs(Rp[0]);
-    int j0 = kp;
-    for (int j = 0; j < kp; ++j)
-      if (fabs(Rp[(int64_t)j * b + j]) <= tau * r00) {
-        j0 = j;
-        break;
-      }
-    s_j0 = j0;
-  }
+  if (threadIdx.x == 0) s_j0 = perm[b];  // first dependent pivot, from the CPQR
   __syncthreads();
   const int j0 = s_j0;
   // back substitution, one thread per column of R12
@@ -746,9 +754,9 @@ __global__ void __launch_bounds__(256) k_id_finish(GroupArgs g) {
     for (int j = kp - 1; j >= 0; --j) {
       double v = 0.0;
       if (j < j0) {
-        v = Rp[(int64_t)j * b + kp + q];
-        for (int u = j + 1; u < j0; ++u) v -= Rp[(int64_t)j * b + u] * T[(int64_t)u * r + col];
-        v /= Rp[(int64_t)j * b + j];
+        v = Rp[(int64_t)j * b + perm[kp + q]];
+        for (int u = j + 1; u < j0; ++u) v -= Rp[(int64_t)j * b + perm[u]] * T[(int64_t)u * r + col];
+        v /= Rp[(int64_t)j * b + perm[j]];
       }
       T[(int64_t)j * r + col] = v;
     }

@@ -108,6 +108,12 @@ __global__ void k_rows_to_cm(const double* W, const int32_t* perm, int64_t n, in
   int j = (int)(e % c);
   F[(int64_t)perm[t] + (int64_t)j * ld] = W[e];
 }
+__global__ void k_gather_orig(const double* in, const int32_t* perm, int64_t n, int64_t s, double* out) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * s) return;
+  int64_t t = e / s, c = e % s;
+  out[e] = in[(int64_t)perm[t] * s + c];
+}
 __global__ void k_axpy(double* y, const double* x, double a, int64_t n) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) y[e] += a * x[e];
@@ -131,22 +137,66 @@ __global__ void k_colnorm2(const double* W, int64_t n, int c, double* out) {
 
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
-// Seeded standard normal draws (splitmix64 + Box-Muller) for callers that pass no test matrices.
-void host_gaussian(uint64_t seed, int64_t count, double* out) {
-  uint64_t st = seed * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
-  auto next = [&]() {
-    uint64_t z = (st += 0x9E3779B97F4A7C15ull);
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-  };
-  for (int64_t i = 0; i < count; i += 2) {
-    double u1 = ((next() >> 11) + 1.0) * (1.0 / 9007199254740993.0);
-    double u2 = (next() >> 11) * (1.0 / 9007199254740992.0);
-    double rr = std::sqrt(-2.0 * std::log(u1));
-    out[i] = rr * std::cos(2.0 * M_PI * u2);
-    if (i + 1 < count) out[i + 1] = rr * std::sin(2.0 * M_PI * u2);
+// Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11): 10 rounds of the
+// multiply-xor round function with the published multipliers and Weyl key
+// increments, counter = (pair index lo, pair index hi, stream, 0), key = seed.
+__device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  for (int r = 0; r < 10; ++r) {
+    uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+    uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0;
+    uint32_t n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
+    c[1] = (uint32_t)p1;
+    c[3] = (uint32_t)p0;
+    c[0] = n0;
+    c[2] = n2;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
   }
+}
+// Standard normal pair number q of a stream: two 53-bit uniforms, Box-Muller.
+__device__ inline void normal_pair(uint64_t seed, uint32_t stream, uint64_t q, double& z0, double& z1) {
+  uint32_t c[4] = {(uint32_t)q, (uint32_t)(q >> 32), stream, 0u};
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  uint64_t a = ((uint64_t)c[0] << 32 | c[1]) >> 11, b = ((uint64_t)c[2] << 32 | c[3]) >> 11;
+  double u1 = ((double)a + 1.0) * (1.0 / 9007199254740992.0);  // (0, 1]
+  double u2 = (double)b * (1.0 / 9007199254740992.0);          // [0, 1)
+  double rr = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  z0 = rr * cs;
+  z1 = rr * sn;
+}
+// Omega (stream 0) or Psi (stream 1) in tree order: entry (t, c) is draw 2*(perm[t]*s + c) ...
+__global__ void k_gauss_tree(uint64_t seed, uint32_t stream, const int32_t* perm, int64_t n, int64_t s, double* out) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * s) return;
+  int64_t t = e / s, c = e % s;
+  int64_t g = (int64_t)perm[t] * s + c;
+  double z0, z1;
+  normal_pair(seed, stream, (uint64_t)(g >> 1), z0, z1);
+  out[e] = (g & 1) ? z1 : z0;
+}
+
+const char* kClassNames[RSRS_NCLASS] = {"sample", "lists", "gram", "chol", "gather", "proj_nt", "proj_solve",
+                                        "proj_acc", "cpqr", "id_finish", "ef_update", "extract", "lu", "lu_rhs",
+                                        "schur", "root"};
+
+// Algorithmic FLOPs of one box per kernel class (what the step must compute, not padded tiles).
+void box_flops(const BoxDesc& d, int64_t s, int passes, double* fl) {
+  const double b = d.b, l = d.l, kp = d.kp, r = d.r, w = d.kp + d.n, S = (double)s;
+  fl[RSRS_K_GRAM] += 2.0 * l * (l + 1) * S;              // two SYRKs l x s
+  fl[RSRS_K_CHOL] += 2.0 * l * l * l / 3.0;              // two Cholesky factorizations
+  fl[RSRS_K_PROJ_NT] += passes * 2.0 * 2.0 * b * l * S;  // [Y_B; Z_B] W^T per pass
+  fl[RSRS_K_PROJ_SOLVE] += passes * 2.0 * 2.0 * b * l * l;
+  fl[RSRS_K_PROJ_ACC] += passes * 2.0 * 2.0 * b * l * S;
+  fl[RSRS_K_CPQR] += 4.0 * (2.0 * S) * b * kp;
+  fl[RSRS_K_ID] += r * kp * kp;
+  fl[RSRS_K_EF] += 8.0 * r * kp * S;
+  fl[RSRS_K_EXTRACT] += 4.0 * r * kp * (l + r);
+  fl[RSRS_K_LU] += 2.0 * r * r * r / 3.0;
+  fl[RSRS_K_LU_RHS] += 2.0 * 2.0 * r * r * w;
+  fl[RSRS_K_SCHUR] += 8.0 * r * w * S;
 }
 
 // Apply the operator to a tree-order row-major block: out = A in (adjoint for callbacks).
@@ -189,6 +239,11 @@ const char* rsrs_status_string(rsrs_status st) {
 }
 
 const char* rsrs_last_error(void) { return g_last_error.c_str(); }
+
+const char* rsrs_kernel_class_name(int cls) {
+  if (cls < 0 || cls >= RSRS_NCLASS) return "";
+  return kClassNames[cls];
+}
 
 rsrs_status rsrs_tree_build(const double* pts_host, int64_t n, int d, int leaf_cap, rsrs_tree** out) {
   if (!out) return fail(RSRS_E_INVAL, "out is null");
@@ -333,7 +388,7 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
         d.bn_off = iw;
         iw += d.l;
         d.pv_off = iw;
-        iw += d.b;
+        iw += d.b + 1;  // CPQR permutation and the first dependent step
         d.g_off = w;
         w += 2 * (int64_t)d.l * d.l;
         d.x_off = w;
@@ -444,26 +499,63 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
       CU(cudaMemcpyAsync(desc_dev, all_desc.data(), all_desc.size() * sizeof(BoxDesc), cudaMemcpyHostToDevice, st));
     CU(cudaMemcpyAsync(root_desc_dev, &rd, sizeof(BoxDesc), cudaMemcpyHostToDevice, st));
     CU(cudaMemsetAsync(err, 0, sizeof(int), st));
-    // test matrices: caller's (original order) or drawn here; stored in tree order
-    std::vector<double> host(NS);
-    std::vector<double> tree_order(NS);
+    // test matrices: caller's host or device arrays (original order), or Philox draws; stored in tree order
     for (int side = 0; side < 2; ++side) {
-      const double* src = side == 0 ? o.omega_host : o.psi_host;
-      if (!src) {
-        host_gaussian(o.seed * 2 + side + 1, NS, host.data());
-        src = host.data();
+      double* dst = side == 0 ? Om : Ps;
+      const double* hsrc = side == 0 ? o.omega_host : o.psi_host;
+      const double* dsrc = side == 0 ? o.omega_dev : o.psi_dev;
+      if (hsrc) {
+        std::vector<double> tree_order(NS);
+        for (int64_t q = 0; q < N; ++q) std::memcpy(&tree_order[q * s], &hsrc[T.perm[q] * s], s * sizeof(double));
+        CU(cudaMemcpyAsync(dst, tree_order.data(), NS * sizeof(double), cudaMemcpyHostToDevice, st));
+        CU(cudaStreamSynchronize(st));  // the staging buffer goes out of scope
+      } else if (dsrc) {
+        k_gather_orig<<<nblk(NS), 256, 0, st>>>(dsrc, perm_dev, N, s, dst);
+      } else {
+        k_gauss_tree<<<nblk(NS), 256, 0, st>>>(o.seed, (uint32_t)side, perm_dev, N, s, dst);
       }
-      for (int64_t q = 0; q < N; ++q)
-        std::memcpy(&tree_order[q * s], &src[T.perm[q] * s], s * sizeof(double));
-      CU(cudaMemcpyAsync(side == 0 ? Om : Ps, tree_order.data(), NS * sizeof(double), cudaMemcpyHostToDevice, st));
-      CU(cudaStreamSynchronize(st));  // host staging buffers are reused
+      CU(cudaGetLastError());
     }
   }
 
   int64_t launches = 0;
   Launch L{st, &launches};
+  // per-class CUDA-event timing (opts.profile): one event pair around each class launch sequence
+  struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> evpool;
+  auto new_ev = [&]() {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    evpool.push_back(e);
+    return e;
+  };
+  auto timed = [&](int cls, auto&& fn) {
+    int64_t l0 = launches;
+    cudaEvent_t a = nullptr;
+    if (o.profile) {
+      a = new_ev();
+      cudaEventRecord(a, st);
+    }
+    fn();
+    if (o.profile) {
+      cudaEvent_t b = new_ev();
+      cudaEventRecord(b, st);
+      recs.push_back({cls, a, b});
+    }
+    f->stats.class_launches[cls] += launches - l0;
+  };
+  struct EvGuard {
+    std::vector<cudaEvent_t>& v;
+    ~EvGuard() {
+      for (auto e : v) cudaEventDestroy(e);
+    }
+  } evguard{evpool};
   cudaEvent_t ev[4];
-  for (auto& e : ev) CU(cudaEventCreate(&e));
+  for (auto& e : ev) e = new_ev();
   CU(cudaEventRecord(ev[0], st));
   // ---- a1: sampling Y = A Omega, Z = A* Psi -------------------------------------------
   {
@@ -473,10 +565,13 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
       CU(pool.alloc(&cm_out, NS));
     }
     const int fp32 = (o.precision == RSRS_PREC_MIXED) ? 1 : 0;
-    rsrs_status r1 = op_apply(f.get(), L, Om, Y, s, 0, fp32, cm_in, cm_out);
+    rsrs_status r1 = RSRS_OK;
+    timed(RSRS_K_SAMPLE, [&] {
+      r1 = op_apply(f.get(), L, Om, Y, s, 0, fp32, cm_in, cm_out);
+      if (r1 == RSRS_OK) r1 = op_apply(f.get(), L, Ps, Z, s, 1, fp32, cm_in, cm_out);
+    });
     if (r1 != RSRS_OK) return r1;
-    r1 = op_apply(f.get(), L, Ps, Z, s, 1, fp32, cm_in, cm_out);
-    if (r1 != RSRS_OK) return r1;
+    if (f->kind != RSRS_OP_CALLBACK) f->stats.class_gflop[RSRS_K_SAMPLE] = 4.0 * (double)N * N * s * 1e-9;
   }
   CU(cudaEventRecord(ev[1], st));
   // ---- a2..a8: levels L..1, colour by colour ------------------------------------------
@@ -492,57 +587,70 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
   ga.fi = f->fi;
   ga.act = act;
   ga.err = err;
+  double fl[RSRS_NCLASS] = {};
   size_t gi = 0;
   for (int level = T.depth; level >= 1; --level) {
     if (level_seg[level].second > 0)
-      launch_copy_segments(L, segs_dev + level_seg[level].first, (int)level_seg[level].second, act, act);
+      timed(RSRS_K_LISTS, [&] {
+        launch_copy_segments(L, segs_dev + level_seg[level].first, (int)level_seg[level].second, act, act);
+      });
     for (; gi < f->groups.size() && f->groups[gi].level == level; ++gi) {
       const Group& g = f->groups[gi];
       ga.desc = desc_dev + g.desc_off;
       ga.nbox = (int)g.h.size();
-      launch_copy_segments(L, segs_dev + g.seg_off, (int)g.nseg, act, iwork);
-      launch_gram(L, ga, items_gram(g.h));
-      for (int p = 0; p < g.max_panels; ++p) {
-        launch_chol_panel(L, ga, p);
-        launch_chol_trsm(L, ga, p, items_chol_trsm(g.h, p));
-        launch_chol_update(L, ga, p, items_chol_update(g.h, p));
-      }
-      launch_gather_box(L, ga, items_gather(g.h));
+      for (const BoxDesc& d : g.h) box_flops(d, s, passes, fl);
+      timed(RSRS_K_LISTS, [&] { launch_copy_segments(L, segs_dev + g.seg_off, (int)g.nseg, act, iwork); });
+      timed(RSRS_K_GRAM, [&] { launch_gram(L, ga, items_gram(g.h)); });
+      timed(RSRS_K_CHOL, [&] {
+        for (int p = 0; p < g.max_panels; ++p) {
+          launch_chol_panel(L, ga, p);
+          launch_chol_trsm(L, ga, p, items_chol_trsm(g.h, p));
+          launch_chol_update(L, ga, p, items_chol_update(g.h, p));
+        }
+      });
+      timed(RSRS_K_GATHER, [&] { launch_gather_box(L, ga, items_gather(g.h)); });
       for (int pass = 0; pass < passes; ++pass) {
-        launch_proj_nt(L, ga, pass, items_proj_nt(g.h));
-        launch_proj_solve(L, ga, pass, items_proj_solve(g.h));
-        launch_proj_acc(L, ga, pass, items_proj_acc(g.h, s));
+        timed(RSRS_K_PROJ_NT, [&] { launch_proj_nt(L, ga, pass, items_proj_nt(g.h)); });
+        timed(RSRS_K_PROJ_SOLVE, [&] { launch_proj_solve(L, ga, pass, items_proj_solve(g.h)); });
+        timed(RSRS_K_PROJ_ACC, [&] { launch_proj_acc(L, ga, pass, items_proj_acc(g.h, s)); });
       }
-      launch_cpqr(L, ga, g.max_b);
-      launch_id_finish(L, ga, g.max_b);
-      launch_ef_update(L, ga, items_ef(g.h, s));
-      launch_extract(L, ga, items_extract(g.h));
-      launch_lu(L, ga);
-      launch_lu_rhs(L, ga, items_lu_rhs(g.h));
-      launch_schur(L, ga, items_schur(g.h, s));
+      timed(RSRS_K_CPQR, [&] { launch_cpqr(L, ga, g.max_b); });
+      timed(RSRS_K_ID, [&] { launch_id_finish(L, ga, g.max_b); });
+      timed(RSRS_K_EF, [&] { launch_ef_update(L, ga, items_ef(g.h, s)); });
+      timed(RSRS_K_EXTRACT, [&] { launch_extract(L, ga, items_extract(g.h)); });
+      timed(RSRS_K_LU, [&] { launch_lu(L, ga); });
+      timed(RSRS_K_LU_RHS, [&] { launch_lu_rhs(L, ga, items_lu_rhs(g.h)); });
+      timed(RSRS_K_SCHUR, [&] { launch_schur(L, ga, items_schur(g.h, s)); });
     }
     CU(cudaGetLastError());
   }
+  for (int c = 0; c < RSRS_NCLASS; ++c)
+    if (c != RSRS_K_SAMPLE) f->stats.class_gflop[c] = fl[c] * 1e-9;
   CU(cudaEventRecord(ev[2], st));
   // ---- a9: root extraction A~_{Bt Bt} = Y_Bt pinv(Om_Bt), then LU ---------------------
   if (nroot > 0) {
     std::vector<BoxDesc> rh{rd};
     ga.desc = root_desc_dev;
     ga.nbox = 1;
-    launch_copy_segments(L, segs_dev + root_seg_off, (int)root_nseg, act, iwork);
-    launch_gram(L, ga, items_gram(rh));
-    for (int p = 0; p < (int)cdiv(nroot, kT); ++p) {
-      launch_chol_panel(L, ga, p);
-      launch_chol_trsm(L, ga, p, items_chol_trsm(rh, p));
-      launch_chol_update(L, ga, p, items_chol_update(rh, p));
-    }
-    launch_gather_box(L, ga, items_gather(rh));
-    launch_proj_nt(L, ga, 0, items_proj_nt(rh));
-    launch_proj_solve(L, ga, 0, items_proj_solve(rh));
+    timed(RSRS_K_ROOT, [&] {
+      launch_copy_segments(L, segs_dev + root_seg_off, (int)root_nseg, act, iwork);
+      launch_gram(L, ga, items_gram(rh));
+      for (int p = 0; p < (int)cdiv(nroot, kT); ++p) {
+        launch_chol_panel(L, ga, p);
+        launch_chol_trsm(L, ga, p, items_chol_trsm(rh, p));
+        launch_chol_update(L, ga, p, items_chol_update(rh, p));
+      }
+      launch_gather_box(L, ga, items_gather(rh));
+      launch_proj_nt(L, ga, 0, items_proj_nt(rh));
+      launch_proj_solve(L, ga, 0, items_proj_solve(rh));
+    });
     CU(cudaMemcpyAsync(f->root_idx, iwork, nroot * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
     CU(cudaMemcpyAsync(f->root_A, work + rd.x_off, nroot * nroot * sizeof(double), cudaMemcpyDeviceToDevice, st));
     CU(cudaMemcpyAsync(f->root_LU, work + rd.x_off, nroot * nroot * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    launch_dense_lu(L, f->root_LU, nroot, f->root_piv, err);
+    timed(RSRS_K_ROOT, [&] { launch_dense_lu(L, f->root_LU, nroot, f->root_piv, err); });
+    const double nr = (double)nroot;
+    f->stats.class_gflop[RSRS_K_ROOT] = (2.0 * nr * (nr + 1) * s + nr * nr * nr / 3.0 + 2.0 * nr * nr * s +
+                                         2.0 * nr * nr * nr + 2.0 * nr * nr * nr / 3.0) * 1e-9;
   }
   CU(cudaEventRecord(ev[3], st));
   CU(cudaGetLastError());
@@ -555,7 +663,11 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
   CU(cudaEventElapsedTime(&t01, ev[0], ev[1]));
   CU(cudaEventElapsedTime(&t12, ev[1], ev[2]));
   CU(cudaEventElapsedTime(&t23, ev[2], ev[3]));
-  for (auto& e : ev) cudaEventDestroy(e);
+  for (const Rec& rc : recs) {
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, rc.a, rc.b));
+    f->stats.class_ms[rc.cls] += ms;
+  }
   f->stats.n = N;
   f->stats.s = s;
   f->stats.k = k;

@@ -25,7 +25,7 @@ STATUS = {0: "RSRS_OK", 1: "RSRS_E_INVAL", 2: "RSRS_E_UNDERSAMPLED", 3: "RSRS_E_
 EXPORTS = ["rsrs_tree_build", "rsrs_tree_info", "rsrs_tree_perm", "rsrs_tree_schedule", "rsrs_tree_free",
            "rsrs_build", "rsrs_solve", "rsrs_apply", "rsrs_refine", "rsrs_matvec", "rsrs_factor_stats",
            "rsrs_factor_box", "rsrs_factor_root", "rsrs_factor_sketches", "rsrs_factor_free",
-           "rsrs_status_string", "rsrs_last_error"]
+           "rsrs_status_string", "rsrs_last_error", "rsrs_kernel_class_name"]
 
 MATVEC_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.c_int64, C.c_int32, C.c_void_p, C.c_int64,
                         C.c_void_p, C.c_int64, C.c_void_p)
@@ -38,7 +38,11 @@ class Operator(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("p", C.c_int), ("proj_passes", C.c_int), ("seed", C.c_uint64),
-                ("omega_host", C.c_void_p), ("psi_host", C.c_void_p), ("keep_sketches", C.c_int)]
+                ("omega_host", C.c_void_p), ("psi_host", C.c_void_p), ("omega_dev", C.c_void_p),
+                ("psi_dev", C.c_void_p), ("keep_sketches", C.c_int), ("profile", C.c_int)]
+
+
+NCLASS = 16
 
 
 class TreeInfo(C.Structure):
@@ -51,7 +55,8 @@ class Stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("s", C.c_int64), ("k", C.c_int64), ("n_boxes", C.c_int64),
                 ("root_size", C.c_int64), ("factor_bytes", C.c_int64), ("work_bytes", C.c_int64),
                 ("t_sample_ms", C.c_double), ("t_compress_ms", C.c_double), ("t_root_ms", C.c_double),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("class_ms", C.c_double * NCLASS),
+                ("class_gflop", C.c_double * NCLASS), ("class_launches", C.c_int64 * NCLASS)]
 
 
 class RefineReport(C.Structure):
@@ -100,6 +105,8 @@ def lib():
         L.rsrs_factor_free.restype = None
         L.rsrs_status_string.argtypes = [C.c_int]
         L.rsrs_status_string.restype = C.c_char_p
+        L.rsrs_kernel_class_name.argtypes = [C.c_int]
+        L.rsrs_kernel_class_name.restype = C.c_char_p
         L.rsrs_last_error.argtypes = []
         L.rsrs_last_error.restype = C.c_char_p
         _lib = L
@@ -179,7 +186,7 @@ class Factor:
     def __init__(self, tree: Tree, kind: int, k: int, s: int, shift: float = 1.0, scale: float = 0.0,
                  precision: int = RSRS_PREC_FP64, p: int = -1, omega: np.ndarray | None = None,
                  psi: np.ndarray | None = None, seed: int = 0, passes: int = 0, keep_sketches: bool = False,
-                 matvec=None, stream=None):
+                 matvec=None, stream=None, profile: bool = False):
         self.tree = tree
         self.n = tree.n
         self._cb = None
@@ -190,9 +197,13 @@ class Factor:
             self._cb = MATVEC_FN(matvec)
             op.fn = self._cb
         opts = Options(precision=precision, p=p, proj_passes=passes, seed=seed,
-                       keep_sketches=int(keep_sketches))
+                       keep_sketches=int(keep_sketches), profile=int(profile))
         self._om = self._ps = None
-        if omega is not None:
+        if omega is not None and hasattr(omega, "data_ptr"):  # device tensors (N, s), original order
+            self._om, self._ps = omega, psi
+            opts.omega_dev = C.c_void_p(omega.data_ptr())
+            opts.psi_dev = C.c_void_p(psi.data_ptr())
+        elif omega is not None:
             self._om = np.ascontiguousarray(omega, dtype=np.float64)
             self._ps = np.ascontiguousarray(psi, dtype=np.float64)
             assert self._om.shape == (self.n, s) and self._ps.shape == (self.n, s)
@@ -232,6 +243,12 @@ class Factor:
         out = Stats()
         _check(lib().rsrs_factor_stats(self._h, C.byref(out)))
         return out
+
+    def class_stats(self) -> dict:
+        """{class name: (ms, gflop, launches)} of the build (ms is 0 unless built with profile=True)."""
+        st = self.stats()
+        return {lib().rsrs_kernel_class_name(c).decode(): (st.class_ms[c], st.class_gflop[c], st.class_launches[c])
+                for c in range(NCLASS)}
 
     def box(self, i: int) -> dict:
         v = BoxView()
