@@ -83,14 +83,19 @@ class ClockSampler:
         sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if "Active" in r[4 + i]})
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def _problem(idx: int):
-    prs = W.config(idx)
-    return prs[0]
+def _problem(idx: int, n: int = 0):
+    """Workload ``idx``; ``n`` > 0 keeps its kind and sizes but draws n points (profiling runs)."""
+    pr = W.config(idx)[0]
+    if n and n != pr.n and pr.kernel != "stencil7":
+        pts = W.uniform_points(n, pr.d, W.rng_for(pr.cfg, 0, W.STREAM_POINTS))
+        pr = W.kernel_problem(pr.cfg, f"{pr.name.split('_')[0]}_N{n}_k{pr.k}", pts, pr.kernel, pr.leaf, pr.k,
+                              pr.s_cfg, pr.nrhs)
+    return pr
 
 
 def _cpu_baseline(pr, s: int, budget_s: float = 20.0) -> dict:
@@ -151,7 +156,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    pr = _problem(args.workload)
+    pr = _problem(args.workload, args.n)
     from oracle.tree import Schedule as OSched
     from oracle.tree import Tree as OTree
 
@@ -191,7 +196,7 @@ def run_gpu(args):
     __graft_entry__.build()
     import paper_2311_01451_gb300 as R
 
-    pr = _problem(args.workload)
+    pr = _problem(args.workload, args.n)
     tree = R.Tree(pr.points, pr.leaf)
     info = tree.info(pr.k)
     s = max(pr.s_cfg, info.s_req)
@@ -329,6 +334,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--workload", type=int, default=1, help="workload index (1: 2D N=65536, k=48)")
+    ap.add_argument("--n", type=int, default=0, help="override the number of points (profiling runs only)")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")

@@ -74,14 +74,17 @@ typedef struct {
 /* Arithmetic of the build and of the factor. */
 enum {
   RSRS_PREC_FP64 = 0,   /* every step in FP64                                               */
-  RSRS_PREC_MIXED = 1   /* sampling and Schur updates in FP32 SIMT; ID, LU, nullification,   */
-                        /* extraction and the refinement residual in FP64                   */
+  RSRS_PREC_MIXED = 1   /* FP32 arithmetic (FP64 storage) for the sampling product, the      */
+                        /* near-field Grams, Cholesky factors, projections and the E/F and  */
+                        /* Schur updates; FP64 for the CPQR pivots, extraction, the X_RR    */
+                        /* LU, the root, the solve and the refinement residual             */
 };
 
 typedef struct {
   int precision;          /* RSRS_PREC_*                                               */
   int p;                  /* oversampling; < 0 selects p = k (Sec. 5)                  */
-  int proj_passes;        /* projection passes of the nullification (1 or 2; 0 -> 2)   */
+  int proj_passes;        /* projection passes of the nullification, 1..4; 0 selects */
+                          /* 2 (FP64) or 3 (mixed)                                   */
   uint64_t seed;          /* key of the device Philox4x32-10 draws used when no test   */
                           /* matrices are given: entry (i, c) of Omega (Psi) is member */
                           /* (i*s+c) mod 2 of the Box-Muller pair from counter         */

@@ -26,7 +26,8 @@ struct BoxDesc {
   int64_t cp_off;   // double work: CPQR R rows, kp x b; then extraction blocks 2 x r x l
   int64_t pv_off;   // int32 work: b CPQR local permutation, then the first dependent step
   int64_t fi_off;   // int32 factor: R (r), S (kp), N (n), LU pivots (r)
-  int64_t fd_off;   // double factor: T (kp x r), XRR (r x r), LU (r x r), LcT (r x (kp+n)), Uc (r x (kp+n))
+  int64_t fd_off;   // double factor: T (kp x r), XRR (r x r), LU (r x r), LcT (r x (kp+n)), Uc (r x (kp+n)),
+                    //   XRR^-1 (r x r)
   int64_t act_off;  // int32 active-list pool slot of the box
 };
 
@@ -36,8 +37,9 @@ __host__ __device__ inline int64_t fd_XRR(const BoxDesc& d) { return d.fd_off + 
 __host__ __device__ inline int64_t fd_LU(const BoxDesc& d) { return fd_XRR(d) + (int64_t)d.r * d.r; }
 __host__ __device__ inline int64_t fd_LcT(const BoxDesc& d) { return fd_LU(d) + (int64_t)d.r * d.r; }
 __host__ __device__ inline int64_t fd_Uc(const BoxDesc& d) { return fd_LcT(d) + (int64_t)d.r * (d.kp + d.n); }
+__host__ __device__ inline int64_t fd_Xinv(const BoxDesc& d) { return fd_Uc(d) + (int64_t)d.r * (d.kp + d.n); }
 __host__ __device__ inline int64_t fd_size(int64_t kp, int64_t r, int64_t n) {
-  return kp * r + 2 * r * r + 2 * r * (kp + n);
+  return kp * r + 3 * r * r + 2 * r * (kp + n);
 }
 __host__ __device__ inline int64_t fi_R(const BoxDesc& d) { return d.fi_off; }
 __host__ __device__ inline int64_t fi_S(const BoxDesc& d) { return d.fi_off + d.r; }   // S then N: the "SN" list
@@ -86,6 +88,7 @@ struct GroupArgs {
   int32_t* fi;
   int32_t* act;
   int* err;
+  int fp32;  // arithmetic of the Gram, Cholesky, projection, E/F and Schur kernels: FP32 (1) or FP64 (0)
 };
 
 void launch_gram(Launch L, const GroupArgs& g, int64_t items);                    // G = W W^T
@@ -121,6 +124,7 @@ struct SweepArgs {
 // C rows += alpha * op(A) * B rows; row sets 0 = R, 1 = S, 2 = SN; matrices 0 = T, 1 = LcT, 2 = Uc.
 void launch_sweep_op(Launch L, const SweepArgs& a, int cset, int mat, int trans, int bset, double alpha,
                      int64_t items);
+// f_R <- X_RR^-1 f_R (solve, from the stored inverse) or X_RR f_R (apply), adjoint as requested.
 void launch_sweep_diag(Launch L, const SweepArgs& a, int solve, int64_t items, int max_r);
 void launch_dense_apply(Launch L, const double* A, int64_t n, const int32_t* rows, double* F, int nrhs,
                         int adjoint);
@@ -144,5 +148,7 @@ int64_t items_diag(const std::vector<BoxDesc>& h, int nrhs);
 void launch_dense_lu(Launch L, double* A, int64_t n, int32_t* piv, int* err);
 void launch_dense_lu_solve(Launch L, const double* LU, const int32_t* piv, int64_t n,
                            const int32_t* rows, double* F, int nrhs, int adjoint);
+// Explicit inverse of an LU-factored n x n matrix (one CTA per column).
+void launch_dense_inverse(Launch L, const double* LU, const int32_t* piv, int64_t n, double* inv);
 
 }  // namespace rsrs

@@ -10,6 +10,8 @@
 // these kernels are bound by the FP64 pipe as soon as a tile reuses its
 // operands a few times; 64x64 output tiles with 16-deep K slices in shared
 // memory are enough to keep the pipe busy.
+#include <cooperative_groups.h>
+
 #include <cfloat>
 #include <cmath>
 
@@ -59,6 +61,13 @@ __device__ inline int find_item(const BoxDesc* desc, int nbox, int64_t item, F c
   return s_box;
 }
 
+template <typename T>
+__device__ __forceinline__ T mad(T a, T b, T c);
+template <>
+__device__ __forceinline__ float mad<float>(float a, float b, float c) { return fmaf(a, b, c); }
+template <>
+__device__ __forceinline__ double mad<double>(double a, double b, double c) { return fma(a, b, c); }
+
 __device__ inline void set_err(int* err, int code) {
   if (err) atomicCAS(err, 0, code);
 }
@@ -79,10 +88,11 @@ struct RowsW {
 
 // C tile (64 x 64) = sum_t A[i][t] B[j][t] over t < K, rows gathered.  acc: 4 x 4 per thread,
 // rows ty + 16a, cols tx + 16c (a, c < 4).
+template <typename CT>
 __device__ void tile_nt(Rows A, int64_t ma, Rows B, int64_t mb, int64_t koff, int64_t K, int64_t i0,
-                        int64_t j0, double acc[4][4]) {
-  __shared__ double As[KC][TB + 1];
-  __shared__ double Bs[KC][TB + 1];
+                        int64_t j0, CT acc[4][4]) {
+  __shared__ CT As[KC][TB + 1];
+  __shared__ CT Bs[KC][TB + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int lr = tid >> 2, lk = (tid & 3) * 4;
@@ -92,13 +102,13 @@ __device__ void tile_nt(Rows A, int64_t ma, Rows B, int64_t mb, int64_t koff, in
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       int64_t k = k0 + lk + u;
-      As[lk + u][lr] = (arow && k < K) ? arow[k] : 0.0;
-      Bs[lk + u][lr] = (brow && k < K) ? brow[k] : 0.0;
+      As[lk + u][lr] = (arow && k < K) ? (CT)arow[k] : (CT)0;
+      Bs[lk + u][lr] = (brow && k < K) ? (CT)brow[k] : (CT)0;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < KC; ++kk) {
-      double a[4], b[4];
+      CT a[4], b[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         a[u] = As[kk][ty + 16 * u];
@@ -107,7 +117,7 @@ __device__ void tile_nt(Rows A, int64_t ma, Rows B, int64_t mb, int64_t koff, in
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        for (int v = 0; v < 4; ++v) acc[u][v] = mad<CT>(a[u], b[v], acc[u][v]);
     }
     __syncthreads();
   }
@@ -123,13 +133,14 @@ struct MatA {
 
 // C[crow(i)][coff + t] += alpha * sum_q A(i,q) B[brow(q)][t] for the 64 x 64 tile (i0, t0);
 // t ranges over ncols, q over K.
+template <typename CT>
 __device__ void tile_acc(double alpha, MatA A, int64_t m, int64_t K, Rows B, int64_t boff, RowsW C,
                          int64_t coff, int64_t ncols, int64_t i0, int64_t t0) {
-  __shared__ double As[KC][TB + 1];
-  __shared__ double Bs[KC][TB + 1];
+  __shared__ CT As[KC][TB + 1];
+  __shared__ CT Bs[KC][TB + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  double acc[4][4] = {};
+  CT acc[4][4] = {};
   for (int64_t q0 = 0; q0 < K; q0 += KC) {
     // A tile: 64 rows x 16 q
     if (!A.trans) {
@@ -137,14 +148,14 @@ __device__ void tile_acc(double alpha, MatA A, int64_t m, int64_t K, Rows B, int
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         int64_t i = i0 + lr, q = q0 + lq + u;
-        As[lq + u][lr] = (i < m && q < K) ? A.at(i, q) : 0.0;
+        As[lq + u][lr] = (i < m && q < K) ? (CT)A.at(i, q) : (CT)0;
       }
     } else {
       int lr = tid & 63, lq = (tid >> 6) * 4;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         int64_t i = i0 + lr, q = q0 + lq + u;
-        As[lq + u][lr] = (i < m && q < K) ? A.at(i, q) : 0.0;
+        As[lq + u][lr] = (i < m && q < K) ? (CT)A.at(i, q) : (CT)0;
       }
     }
     // B tile: 16 rows (q) x 64 cols (t)
@@ -155,13 +166,13 @@ __device__ void tile_acc(double alpha, MatA A, int64_t m, int64_t K, Rows B, int
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         int64_t t = t0 + lt + u;
-        Bs[lq][lt + u] = (brow && t < ncols) ? brow[t] : 0.0;
+        Bs[lq][lt + u] = (brow && t < ncols) ? (CT)brow[t] : (CT)0;
       }
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < KC; ++kk) {
-      double a[4], b[4];
+      CT a[4], b[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         a[u] = As[kk][ty + 16 * u];
@@ -170,7 +181,7 @@ __device__ void tile_acc(double alpha, MatA A, int64_t m, int64_t K, Rows B, int
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        for (int v = 0; v < 4; ++v) acc[u][v] = mad<CT>(a[u], b[v], acc[u][v]);
     }
     __syncthreads();
   }
@@ -182,7 +193,7 @@ __device__ void tile_acc(double alpha, MatA A, int64_t m, int64_t K, Rows B, int
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       int64_t t = t0 + tx + 16 * v;
-      if (t < ncols) crow[t] += alpha * acc[u][v];
+      if (t < ncols) crow[t] += alpha * (double)acc[u][v];
     }
   }
 }
@@ -208,6 +219,7 @@ __global__ void k_gather_rows(const double* in, int64_t ld_in, const int32_t* ro
 struct CntGram {
   __host__ __device__ int64_t operator()(const BoxDesc& d) const { return 2 * tri(cdv(d.l, TB)); }
 };
+template <typename CT>
 __global__ void __launch_bounds__(NT) k_gram(GroupArgs g) {
   int64_t loc;
   int bi = find_item(g.desc, g.nbox, blockIdx.x, CntGram(), loc);
@@ -219,8 +231,8 @@ __global__ void __launch_bounds__(NT) k_gram(GroupArgs g) {
   tri_decode(loc % per, ti, tj);
   const int32_t* bn = g.iwork + d.bn_off;
   Rows W{side ? g.Ps : g.Om, g.s, bn};
-  double acc[4][4] = {};
-  tile_nt(W, d.l, W, d.l, 0, g.s, ti * TB, tj * TB, acc);
+  CT acc[4][4] = {};
+  tile_nt<CT>(W, d.l, W, d.l, 0, g.s, ti * TB, tj * TB, acc);
   double* G = g.work + d.g_off + (int64_t)side * d.l * d.l;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
@@ -240,6 +252,7 @@ struct CntPanel {
   int p;
   __host__ __device__ int64_t operator()(const BoxDesc& d) const { return (d.l > (int64_t)p * TB) ? 2 : 0; }
 };
+template <typename CT>
 __global__ void __launch_bounds__(NT) k_chol_panel(GroupArgs g, int p) {
   int64_t loc;
   int bi = find_item(g.desc, g.nbox, blockIdx.x, CntPanel{p}, loc);
@@ -249,26 +262,26 @@ __global__ void __launch_bounds__(NT) k_chol_panel(GroupArgs g, int p) {
   double* G = g.work + d.g_off + (int64_t)side * d.l * d.l;
   const int64_t o = (int64_t)p * TB;
   const int nb = (int)imin64(TB, d.l - o);
-  __shared__ double S[TB][TB + 1];
+  __shared__ CT S[TB][TB + 1];
   __shared__ int s_bad;
   if (threadIdx.x == 0) s_bad = 0;
   for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
     int i = e / nb, j = e % nb;
-    S[i][j] = G[(o + i) * d.l + o + j];
+    S[i][j] = (CT)G[(o + i) * d.l + o + j];
   }
   __syncthreads();
   for (int c = 0; c < nb; ++c) {
     // column c: pivot, scale, rank-1 update of the trailing block (lower part)
     if (threadIdx.x == 0) {
-      double piv = S[c][c];
-      if (!(piv > 0.0) || !isfinite(piv)) {
+      CT piv = S[c][c];
+      if (!(piv > (CT)0) || !isfinite(piv)) {
         s_bad = 1;
-        piv = 1.0;
+        piv = (CT)1;
       }
       S[c][c] = sqrt(piv);
     }
     __syncthreads();
-    double dc = S[c][c];
+    CT dc = S[c][c];
     for (int i = c + 1 + threadIdx.x; i < nb; i += blockDim.x) S[i][c] /= dc;
     __syncthreads();
     int rem = nb - c - 1;
@@ -281,7 +294,7 @@ __global__ void __launch_bounds__(NT) k_chol_panel(GroupArgs g, int p) {
   if (threadIdx.x == 0 && s_bad) set_err(g.err, kDevNonfinite);
   for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
     int i = e / nb, j = e % nb;
-    G[(o + i) * d.l + o + j] = (j <= i) ? S[i][j] : 0.0;
+    G[(o + i) * d.l + o + j] = (j <= i) ? (double)S[i][j] : 0.0;
   }
 }
 
@@ -293,6 +306,7 @@ struct CntPanelRows {
   }
 };
 // L_ip = G_ip L_pp^-T for the 64-row tiles below the diagonal block of panel p.
+template <typename CT>
 __global__ void __launch_bounds__(NT) k_chol_trsm(GroupArgs g, int p) {
   int64_t loc;
   int bi = find_item(g.desc, g.nbox, blockIdx.x, CntPanelRows{p}, loc);
@@ -307,13 +321,14 @@ __global__ void __launch_bounds__(NT) k_chol_trsm(GroupArgs g, int p) {
   const int nb = (int)imin64(TB, d.l - o);
   const int64_t r0 = (int64_t)(p + 1) * TB + ti * TB;
   const int nr = (int)imin64(TB, d.l - r0);
-  extern __shared__ double trsm_sm[];
-  double(*Lp)[TB + 1] = reinterpret_cast<double(*)[TB + 1]>(trsm_sm);
-  double(*X)[TB + 1] = reinterpret_cast<double(*)[TB + 1]>(trsm_sm + TB * (TB + 1));
+  extern __shared__ __align__(16) unsigned char trsm_raw[];
+  CT* trsm_sm = reinterpret_cast<CT*>(trsm_raw);
+  CT(*Lp)[TB + 1] = reinterpret_cast<CT(*)[TB + 1]>(trsm_sm);
+  CT(*X)[TB + 1] = reinterpret_cast<CT(*)[TB + 1]>(trsm_sm + TB * (TB + 1));
   for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
     int i = e / TB, j = e % TB;
-    Lp[i][j] = (i < nb && j < nb) ? G[(o + i) * d.l + o + j] : 0.0;
-    X[i][j] = (i < nr && j < nb) ? G[(r0 + i) * d.l + o + j] : 0.0;
+    Lp[i][j] = (i < nb && j < nb) ? (CT)G[(o + i) * d.l + o + j] : (CT)0;
+    X[i][j] = (i < nr && j < nb) ? (CT)G[(r0 + i) * d.l + o + j] : (CT)0;
   }
   __syncthreads();
   // x L^T = g, column by column; threads over the rows of the tile (4 threads per row, 16 cols each)
@@ -328,7 +343,7 @@ __global__ void __launch_bounds__(NT) k_chol_trsm(GroupArgs g, int p) {
   }
   for (int e = threadIdx.x; e < nr * nb; e += blockDim.x) {
     int i = e / nb, j = e % nb;
-    G[(r0 + i) * d.l + o + j] = X[i][j];
+    G[(r0 + i) * d.l + o + j] = (double)X[i][j];
   }
 }
 
@@ -340,6 +355,7 @@ struct CntUpdate {
   }
 };
 // G_ij -= L_ip L_jp^T for trailing tiles i >= j > p.
+template <typename CT>
 __global__ void __launch_bounds__(NT) k_chol_update(GroupArgs g, int p) {
   int64_t loc;
   int bi = find_item(g.desc, g.nbox, blockIdx.x, CntUpdate{p}, loc);
@@ -356,8 +372,8 @@ __global__ void __launch_bounds__(NT) k_chol_update(GroupArgs g, int p) {
   const int64_t o = (int64_t)p * TB;
   const int64_t nb = imin64(TB, d.l - o);
   Rows L{G, d.l, nullptr};
-  double acc[4][4] = {};
-  tile_nt(L, d.l, L, d.l, o, nb, ti * TB, tj * TB, acc);
+  CT acc[4][4] = {};
+  tile_nt<CT>(L, d.l, L, d.l, o, nb, ti * TB, tj * TB, acc);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -398,6 +414,7 @@ __global__ void k_gather_box(GroupArgs g) {
 struct CntProjNT {
   __host__ __device__ int64_t operator()(const BoxDesc& d) const { return 2 * cdv(d.b, TB) * cdv(d.l, TB); }
 };
+template <typename CT>
 __global__ void __launch_bounds__(NT) k_proj_nt(GroupArgs g, int pass) {
   int64_t loc;
   int bi = find_item(g.desc, g.nbox, blockIdx.x, CntProjNT(), loc);
@@ -410,8 +427,8 @@ __global__ void __launch_bounds__(NT) k_proj_nt(GroupArgs g, int pass) {
   const int32_t* bn = g.iwork + d.bn_off;
   Rows M{g.work + d.m_off + (int64_t)side * g.s, 2 * g.s, nullptr};
   Rows W{side ? g.Ps : g.Om, g.s, bn};
-  double acc[4][4] = {};
-  tile_nt(M, d.b, W, d.l, 0, g.s, ti * TB, tj * TB, acc);
+  CT acc[4][4] = {};
+  tile_nt<CT>(M, d.b, W, d.l, 0, g.s, ti * TB, tj * TB, acc);
   double* X = g.work + (pass ? d.x2_off : d.x_off) + (int64_t)side * d.b * d.l;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
@@ -431,6 +448,7 @@ constexpr int SR = 16;
 struct CntProjSolve {
   __host__ __device__ int64_t operator()(const BoxDesc& d) const { return 2 * cdv(d.b, SR); }
 };
+template <typename CT>
 __global__ void __launch_bounds__(NT) k_proj_solve(GroupArgs g, int pass) {
   int64_t loc;
   int bi = find_item(g.desc, g.nbox, blockIdx.x, CntProjSolve(), loc);
@@ -444,41 +462,41 @@ __global__ void __launch_bounds__(NT) k_proj_solve(GroupArgs g, int pass) {
   double* X = g.work + (pass ? d.x2_off : d.x_off) + (int64_t)side * d.b * d.l + r0 * d.l;
   const int64_t l = d.l;
   const int64_t nblk = cdv(l, TB);
-  __shared__ double Ls[TB][TB + 1];
-  __shared__ double Xs[SR][TB + 1];
+  __shared__ CT Ls[TB][TB + 1];
+  __shared__ CT Xs[SR][TB + 1];
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;  // row ty, cols tx + 16u
   // forward: U L^T = X  (U[:, c] = (X[:, c] - sum_{q<c} U[:, q] L[c][q]) / L[c][c])
   for (int64_t jb = 0; jb < nblk; ++jb) {
     const int64_t c0 = jb * TB;
     const int nc = (int)imin64(TB, l - c0);
-    double acc[4];
+    CT acc[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       int c = tx + 16 * u;
-      acc[u] = (ty < nr && c < nc) ? X[ty * l + c0 + c] : 0.0;
+      acc[u] = (ty < nr && c < nc) ? (CT)X[ty * l + c0 + c] : (CT)0;
     }
     for (int64_t kb = 0; kb < jb; ++kb) {
       const int64_t q0 = kb * TB;
       for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
         int i = e / TB, j = e % TB;
-        Ls[i][j] = (i < nc) ? L[(c0 + i) * l + q0 + j] : 0.0;
+        Ls[i][j] = (i < nc) ? (CT)L[(c0 + i) * l + q0 + j] : (CT)0;
       }
       for (int e = threadIdx.x; e < SR * TB; e += blockDim.x) {
         int i = e / TB, j = e % TB;
-        Xs[i][j] = (i < nr) ? X[i * l + q0 + j] : 0.0;
+        Xs[i][j] = (i < nr) ? (CT)X[i * l + q0 + j] : (CT)0;
       }
       __syncthreads();
 #pragma unroll 8
       for (int q = 0; q < TB; ++q) {
-        double xv = Xs[ty][q];
+        CT xv = Xs[ty][q];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = fma(-xv, Ls[tx + 16 * u][q], acc[u]);
+        for (int u = 0; u < 4; ++u) acc[u] = mad<CT>(-xv, Ls[tx + 16 * u][q], acc[u]);
       }
       __syncthreads();
     }
     for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
       int i = e / TB, j = e % TB;
-      Ls[i][j] = (i < nc && j < nc) ? L[(c0 + i) * l + c0 + j] : 0.0;
+      Ls[i][j] = (i < nc && j < nc) ? (CT)L[(c0 + i) * l + c0 + j] : (CT)0;
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) Xs[ty][tx + 16 * u] = acc[u];
@@ -494,7 +512,7 @@ __global__ void __launch_bounds__(NT) k_proj_solve(GroupArgs g, int pass) {
     }
     for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
       int i = e / nc, j = e % nc;
-      X[i * l + c0 + j] = Xs[i][j];
+      X[i * l + c0 + j] = (double)Xs[i][j];
     }
     __syncthreads();
   }
@@ -502,35 +520,35 @@ __global__ void __launch_bounds__(NT) k_proj_solve(GroupArgs g, int pass) {
   for (int64_t jb = nblk - 1; jb >= 0; --jb) {
     const int64_t c0 = jb * TB;
     const int nc = (int)imin64(TB, l - c0);
-    double acc[4];
+    CT acc[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       int c = tx + 16 * u;
-      acc[u] = (ty < nr && c < nc) ? X[ty * l + c0 + c] : 0.0;
+      acc[u] = (ty < nr && c < nc) ? (CT)X[ty * l + c0 + c] : (CT)0;
     }
     for (int64_t kb = jb + 1; kb < nblk; ++kb) {
       const int64_t q0 = kb * TB;
       const int nq = (int)imin64(TB, l - q0);
       for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
         int i = e / TB, j = e % TB;  // Ls[i][j] = L[q0 + i][c0 + j]
-        Ls[i][j] = (i < nq && j < nc) ? L[(q0 + i) * l + c0 + j] : 0.0;
+        Ls[i][j] = (i < nq && j < nc) ? (CT)L[(q0 + i) * l + c0 + j] : (CT)0;
       }
       for (int e = threadIdx.x; e < SR * TB; e += blockDim.x) {
         int i = e / TB, j = e % TB;
-        Xs[i][j] = (i < nr && j < nq) ? X[i * l + q0 + j] : 0.0;
+        Xs[i][j] = (i < nr && j < nq) ? (CT)X[i * l + q0 + j] : (CT)0;
       }
       __syncthreads();
 #pragma unroll 8
       for (int q = 0; q < TB; ++q) {
-        double xv = Xs[ty][q];
+        CT xv = Xs[ty][q];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = fma(-xv, Ls[q][tx + 16 * u], acc[u]);
+        for (int u = 0; u < 4; ++u) acc[u] = mad<CT>(-xv, Ls[q][tx + 16 * u], acc[u]);
       }
       __syncthreads();
     }
     for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
       int i = e / TB, j = e % TB;
-      Ls[i][j] = (i < nc && j < nc) ? L[(c0 + i) * l + c0 + j] : 0.0;
+      Ls[i][j] = (i < nc && j < nc) ? (CT)L[(c0 + i) * l + c0 + j] : (CT)0;
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) Xs[ty][tx + 16 * u] = acc[u];
@@ -546,7 +564,7 @@ __global__ void __launch_bounds__(NT) k_proj_solve(GroupArgs g, int pass) {
     }
     for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
       int i = e / nc, j = e % nc;
-      X[i * l + c0 + j] = Xs[i][j];
+      X[i * l + c0 + j] = (double)Xs[i][j];
     }
     __syncthreads();
   }
@@ -561,6 +579,7 @@ struct CntProjAcc {
   int64_t s;
   __host__ __device__ int64_t operator()(const BoxDesc& d) const { return 2 * cdv(d.b, TB) * cdv(s, TB); }
 };
+template <typename CT>
 __global__ void __launch_bounds__(NT) k_proj_acc(GroupArgs g, int pass) {
   int64_t loc;
   int bi = find_item(g.desc, g.nbox, blockIdx.x, CntProjAcc{g.s}, loc);
@@ -575,7 +594,7 @@ __global__ void __launch_bounds__(NT) k_proj_acc(GroupArgs g, int pass) {
   MatA X{g.work + (pass ? d.x2_off : d.x_off) + (int64_t)side * d.b * d.l, d.l, false};
   Rows W{side ? g.Ps : g.Om, g.s, bn};
   RowsW M{g.work + d.m_off, 2 * g.s, nullptr};
-  tile_acc(-1.0, X, d.b, d.l, W, 0, M, (int64_t)side * g.s, g.s, ti * TB, tt * TB);
+  tile_acc<CT>(-1.0, X, d.b, d.l, W, 0, M, (int64_t)side * g.s, g.s, ti * TB, tt * TB);
 }
 
 // Column-pivoted Householder QR of M^T (pivoting over the b rows of M), kp steps.
@@ -717,6 +736,133 @@ __global__ void __launch_bounds__(512) k_cpqr(GroupArgs g) {
   if (threadIdx.x == 0) perm[b] = s_j0;
 }
 
+// Cluster version of the CPQR: CPQR_C CTAs per box (one thread-block cluster), CTA r owning the
+// columns [r*cs, (r+1)*cs) of M.  Per pivot step the row dot products with the Householder vector
+// and the updated row norms are summed over the cluster through distributed shared memory
+// (partials summed in rank order, so every CTA holds identical norms and picks the same pivot);
+// two hardware cluster barriers per step.  Same pivot rule as k_cpqr.
+constexpr int CPQR_C = 8;
+__global__ void __launch_bounds__(256) k_cpqr_cluster(GroupArgs g) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const BoxDesc d = g.desc[blockIdx.x / CPQR_C];
+  const int b = d.b, kp = d.kp;
+  const int64_t c = 2 * g.s;
+  const int64_t cs = ((c + CPQR_C - 1) / CPQR_C + 31) / 32 * 32;
+  const int64_t t_lo = imin64((int64_t)rank * cs, c), t_hi = imin64(t_lo + cs, c);
+  double* M = g.work + d.m_off;
+  double* Rp = g.work + d.cp_off;
+  int32_t* perm = g.iwork + d.pv_off;
+  extern __shared__ double csm[];
+  double* nrm = csm;            // b, replicated in every CTA
+  double* wpart = csm + b;      // b, this CTA's partial dot products
+  double* npart = csm + 2 * b;  // b, this CTA's partial norms
+  int* rid = (int*)(csm + 3 * b);
+  __shared__ double s_alpha, s_x0, s_vn2, s_r00;
+  __shared__ int s_j0, s_p;
+  const double tau = fmax(1e-10, 64.0 * DBL_EPSILON * (double)max(b, (int)c));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < b; i += blockDim.x) rid[i] = i;
+  if (threadIdx.x == 0) {
+    s_r00 = -1.0;
+    s_j0 = kp;
+  }
+  // initial squared row norms
+  for (int i = warp; i < b; i += nw) {
+    const double* row = M + (int64_t)i * c;
+    double acc = 0.0;
+    for (int64_t t = t_lo + lane; t < t_hi; t += 32) acc = fma(row[t], row[t], acc);
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) npart[i] = acc;
+  }
+  cluster.sync();
+  for (int i = threadIdx.x; i < b; i += blockDim.x) {
+    double v = 0.0;
+    for (int q = 0; q < CPQR_C; ++q) v += cluster.map_shared_rank(npart, q)[i];
+    nrm[i] = v;
+  }
+  __syncthreads();
+  for (int j = 0; j < kp; ++j) {
+    if (threadIdx.x == 0) {  // identical in every CTA: same norms, same order
+      double v0 = -1.0;
+      int p0 = -1;
+      for (int pos = j; pos < b; ++pos) {
+        double v = nrm[pos];
+        if (v > v0 || (v == v0 && p0 >= 0 && rid[pos] < rid[p0])) {
+          v0 = v;
+          p0 = pos;
+        }
+      }
+      if (p0 < 0) {
+        p0 = j;
+        if (rank == 0) set_err(g.err, kDevNonfinite);
+      }
+      if (s_j0 == kp && ((s_r00 >= 0.0 && sqrt(v0) <= tau * s_r00) || v0 == 0.0)) s_j0 = j;
+      if (s_j0 <= j) {
+        p0 = j;
+        for (int pos = j + 1; pos < b; ++pos)
+          if (rid[pos] < rid[p0]) p0 = pos;
+      }
+      if (p0 != j) {
+        int ti = rid[j];
+        rid[j] = rid[p0];
+        rid[p0] = ti;
+        double tv = nrm[j];
+        nrm[j] = nrm[p0];
+        nrm[p0] = tv;
+      }
+      const double alpha = sqrt(fmax(nrm[j], 0.0));
+      const double x0 = M[(int64_t)rid[j] * c + j];
+      const double sg = (x0 >= 0.0) ? 1.0 : -1.0;
+      s_alpha = alpha;
+      s_x0 = x0 + sg * alpha;  // v_j
+      s_vn2 = 2.0 * alpha * (alpha + fabs(x0));
+      if (j == 0) s_r00 = alpha;
+      if (rank == 0) Rp[(int64_t)j * b + rid[j]] = -sg * alpha;
+    }
+    __syncthreads();
+    const double vj = s_x0, vn2 = s_vn2;
+    const double* x = M + (int64_t)rid[j] * c;
+    // partial dot products of the remaining rows with v over this CTA's columns
+    for (int pos = j + 1 + warp; pos < b; pos += nw) {
+      const double* row = M + (int64_t)rid[pos] * c;
+      double w = 0.0;
+      for (int64_t t = imax64(t_lo, j) + lane; t < t_hi; t += 32) w = fma(row[t], t == j ? vj : x[t], w);
+      for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      if (lane == 0) wpart[pos] = w;
+    }
+    cluster.sync();
+    for (int pos = j + 1 + warp; pos < b; pos += nw) {
+      double w = 0.0;
+      for (int q = 0; q < CPQR_C; ++q) w += cluster.map_shared_rank(wpart, q)[pos];
+      const double f = (vn2 > 0.0) ? 2.0 * w / vn2 : 0.0;
+      double* row = M + (int64_t)rid[pos] * c;
+      double nn = 0.0;
+      for (int64_t t = imax64(t_lo, j) + lane; t < t_hi; t += 32) {
+        double v = fma(-f, t == j ? vj : x[t], row[t]);
+        row[t] = v;
+        if (t > j) nn = fma(v, v, nn);
+        else Rp[(int64_t)j * b + rid[pos]] = v;  // t == j lives in exactly one CTA
+      }
+      for (int o = 16; o; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+      if (lane == 0) npart[pos] = nn;
+    }
+    cluster.sync();
+    for (int pos = j + 1 + threadIdx.x; pos < b; pos += blockDim.x) {
+      double v = 0.0;
+      for (int q = 0; q < CPQR_C; ++q) v += cluster.map_shared_rank(npart, q)[pos];
+      nrm[pos] = v;
+    }
+    __syncthreads();
+  }
+  if (rank == 0) {
+    for (int i = threadIdx.x; i < b; i += blockDim.x) perm[i] = rid[i];
+    if (threadIdx.x == 0) perm[b] = s_j0;
+  }
+  cluster.sync();  // keep every CTA's shared memory alive until the last remote read
+}
+
 // T = R11^-1 R12 (truncated at the first dependent pivot), R/S/N lists, new active list.
 __global__ void __launch_bounds__(256) k_id_finish(GroupArgs g) {
   const BoxDesc d = g.desc[blockIdx.x];
@@ -780,6 +926,7 @@ struct CntEF {
     return (2 * cdv(d.r, TB) + 2 * cdv(d.kp, TB)) * cdv(s, TB);
   }
 };
+template <typename CT>
 __global__ void __launch_bounds__(NT) k_ef_update(GroupArgs g) {
   int64_t loc;
   int bi = find_item(g.desc, g.nbox, blockIdx.x, CntEF{g.s}, loc);
@@ -798,11 +945,11 @@ __global__ void __launch_bounds__(NT) k_ef_update(GroupArgs g) {
   else { job = 3; row_tile -= 2 * tr + tk; }
   if (job < 2) {
     double* Mx = job == 0 ? g.Y : g.Z;
-    tile_acc(-1.0, MatA{T, d.r, true}, d.r, d.kp, Rows{Mx, g.s, Sl}, 0, RowsW{Mx, g.s, Rl}, 0, g.s,
+    tile_acc<CT>(-1.0, MatA{T, d.r, true}, d.r, d.kp, Rows{Mx, g.s, Sl}, 0, RowsW{Mx, g.s, Rl}, 0, g.s,
              row_tile * TB, tt * TB);
   } else {
     double* Mx = job == 2 ? g.Om : g.Ps;
-    tile_acc(1.0, MatA{T, d.r, false}, d.kp, d.r, Rows{Mx, g.s, Rl}, 0, RowsW{Mx, g.s, Sl}, 0, g.s,
+    tile_acc<CT>(1.0, MatA{T, d.r, false}, d.kp, d.r, Rows{Mx, g.s, Rl}, 0, RowsW{Mx, g.s, Sl}, 0, g.s,
              row_tile * TB, tt * TB);
   }
 }
@@ -947,7 +1094,9 @@ __global__ void __launch_bounds__(512) k_lu(GroupArgs g) {
 // Solve X_RR Uc = [X_RS X_RN] and X_RR^T LcT = [X_SR^T X_NR^T] (one thread per column).
 constexpr int CW = 128;
 struct CntLuRhs {
-  __host__ __device__ int64_t operator()(const BoxDesc& d) const { return 2 * cdv(d.kp + d.n, CW); }
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const {
+    return 2 * cdv(d.kp + d.n, CW) + cdv(d.r, CW);
+  }
 };
 __device__ void lu_solve_col(const double* LU, const int32_t* piv, int64_t n, double* x, int64_t stride,
                              bool trans) {
@@ -998,11 +1147,19 @@ __global__ void __launch_bounds__(CW) k_lu_rhs(GroupArgs g) {
   const BoxDesc d = g.desc[bi];
   const int64_t w = (int64_t)d.kp + d.n;
   int64_t per = cdv(w, CW);
+  const double* LU = g.fd + fd_LU(d);
+  const int32_t* piv = g.fi + fi_piv(d);
+  if (loc >= 2 * per) {  // columns of X_RR^-1: solve against the identity
+    int64_t col = (loc - 2 * per) * CW + threadIdx.x;
+    if (col >= d.r) return;
+    double* B = g.fd + fd_Xinv(d);
+    for (int64_t i = 0; i < d.r; ++i) B[i * d.r + col] = (i == col) ? 1.0 : 0.0;
+    lu_solve_col(LU, piv, d.r, B + col, d.r, false);
+    return;
+  }
   int side = (int)(loc / per);
   int64_t col = (loc % per) * CW + threadIdx.x;
   if (col >= w) return;
-  const double* LU = g.fd + fd_LU(d);
-  const int32_t* piv = g.fi + fi_piv(d);
   double* B = g.fd + (side == 0 ? fd_Uc(d) : fd_LcT(d));
   lu_solve_col(LU, piv, d.r, B + col, w, side == 1);
 }
@@ -1015,6 +1172,7 @@ struct CntSchur {
     return (2 * cdv(d.kp + d.n, TB) + 2 * cdv(d.r, TB)) * cdv(s, TB);
   }
 };
+template <typename CT>
 __global__ void __launch_bounds__(NT) k_schur(GroupArgs g) {
   int64_t loc;
   int bi = find_item(g.desc, g.nbox, blockIdx.x, CntSchur{g.s}, loc);
@@ -1029,19 +1187,19 @@ __global__ void __launch_bounds__(NT) k_schur(GroupArgs g) {
   const double* LcT = g.fd + fd_LcT(d);
   const double* Uc = g.fd + fd_Uc(d);
   if (row_tile < tw) {
-    tile_acc(-1.0, MatA{LcT, w, true}, w, d.r, Rows{g.Y, g.s, Rl}, 0, RowsW{g.Y, g.s, SN}, 0, g.s,
+    tile_acc<CT>(-1.0, MatA{LcT, w, true}, w, d.r, Rows{g.Y, g.s, Rl}, 0, RowsW{g.Y, g.s, SN}, 0, g.s,
              row_tile * TB, tt * TB);
   } else if (row_tile < tw + tr) {
     row_tile -= tw;
-    tile_acc(1.0, MatA{Uc, w, false}, d.r, w, Rows{g.Om, g.s, SN}, 0, RowsW{g.Om, g.s, Rl}, 0, g.s,
+    tile_acc<CT>(1.0, MatA{Uc, w, false}, d.r, w, Rows{g.Om, g.s, SN}, 0, RowsW{g.Om, g.s, Rl}, 0, g.s,
              row_tile * TB, tt * TB);
   } else if (row_tile < 2 * tw + tr) {
     row_tile -= tw + tr;
-    tile_acc(-1.0, MatA{Uc, w, true}, w, d.r, Rows{g.Z, g.s, Rl}, 0, RowsW{g.Z, g.s, SN}, 0, g.s,
+    tile_acc<CT>(-1.0, MatA{Uc, w, true}, w, d.r, Rows{g.Z, g.s, Rl}, 0, RowsW{g.Z, g.s, SN}, 0, g.s,
              row_tile * TB, tt * TB);
   } else {
     row_tile -= 2 * tw + tr;
-    tile_acc(1.0, MatA{LcT, w, false}, d.r, w, Rows{g.Ps, g.s, SN}, 0, RowsW{g.Ps, g.s, Rl}, 0, g.s,
+    tile_acc<CT>(1.0, MatA{LcT, w, false}, d.r, w, Rows{g.Ps, g.s, SN}, 0, RowsW{g.Ps, g.s, Rl}, 0, g.s,
              row_tile * TB, tt * TB);
   }
 }
@@ -1121,36 +1279,97 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a, SweepOp op) {
     if (i < m && c < a.nrhs) a.F[(int64_t)cidx[i] * a.nrhs + c] += op.alpha * acc;
   }
 }
-// f_R <- X_RR^-1 f_R (LU) or X_RR f_R; one CTA per (box, column).
+// f_R <- M f_R with M = X_RR^-1 (solve) or X_RR (apply), or M^T for the adjoint; one CTA per
+// (box, group of DC columns): the rows R of F are staged in shared memory.
+constexpr int DC = 4;
 struct CntDiag {
   int nrhs;
-  __host__ __device__ int64_t operator()(const BoxDesc& d) const { return nrhs; }
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const { return cdv(nrhs, DC); }
 };
-__global__ void k_sweep_diag(SweepArgs a, int solve) {
+__global__ void __launch_bounds__(256) k_sweep_diag(SweepArgs a, int solve) {
   int64_t loc;
   int bi = find_item(a.desc, a.nbox, blockIdx.x, CntDiag{a.nrhs}, loc);
   if (bi < 0) return;
   const BoxDesc d = a.desc[bi];
-  const int c = (int)loc;
+  const int c0 = (int)loc * DC;
+  const int nc = min(DC, a.nrhs - c0);
+  const int64_t r = d.r;
   const int32_t* R = a.fi + fi_R(d);
-  extern __shared__ double col[];
-  double* out = col + d.r;
-  for (int64_t i = threadIdx.x; i < d.r; i += blockDim.x) col[i] = a.F[(int64_t)R[i] * a.nrhs + c];
-  __syncthreads();
-  if (solve) {
-    if (threadIdx.x == 0) lu_solve_col(a.fd + fd_LU(d), a.fi + fi_piv(d), d.r, col, 1, a.adjoint != 0);
-    __syncthreads();
-    for (int64_t i = threadIdx.x; i < d.r; i += blockDim.x) a.F[(int64_t)R[i] * a.nrhs + c] = col[i];
-  } else {
-    const double* X = a.fd + fd_XRR(d);
-    for (int64_t i = threadIdx.x; i < d.r; i += blockDim.x) {
-      double v = 0.0;
-      for (int64_t q = 0; q < d.r; ++q) v += (a.adjoint ? X[q * d.r + i] : X[i * d.r + q]) * col[q];
-      out[i] = v;
-    }
-    __syncthreads();
-    for (int64_t i = threadIdx.x; i < d.r; i += blockDim.x) a.F[(int64_t)R[i] * a.nrhs + c] = out[i];
+  const double* M = a.fd + (solve ? fd_Xinv(d) : fd_XRR(d));
+  extern __shared__ double dsm[];
+  double* in = dsm;  // r x DC
+  for (int64_t e = threadIdx.x; e < r * DC; e += blockDim.x) {
+    int64_t i = e / DC;
+    int c = (int)(e % DC);
+    in[e] = (c < nc) ? a.F[(int64_t)R[i] * a.nrhs + c0 + c] : 0.0;
   }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double out[DC];
+  if (!a.adjoint) {  // warp per row, lanes along the row (coalesced)
+    for (int64_t i = warp; i < r; i += nw) {
+#pragma unroll
+      for (int c = 0; c < DC; ++c) out[c] = 0.0;
+      for (int64_t q = lane; q < r; q += 32) {
+        double m = M[i * r + q];
+#pragma unroll
+        for (int c = 0; c < DC; ++c) out[c] = fma(m, in[q * DC + c], out[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < DC; ++c)
+        for (int o = 16; o; o >>= 1) out[c] += __shfl_xor_sync(0xffffffffu, out[c], o);
+      if (lane < nc) {
+        double v = out[0];
+#pragma unroll
+        for (int c = 1; c < DC; ++c)
+          if (lane == c) v = out[c];
+        a.F[(int64_t)R[i] * a.nrhs + c0 + lane] = v;
+      }
+    }
+  } else {  // thread per row, reading column i of M (coalesced across threads)
+    for (int64_t i = threadIdx.x; i < r; i += blockDim.x) {
+#pragma unroll
+      for (int c = 0; c < DC; ++c) out[c] = 0.0;
+      for (int64_t q = 0; q < r; ++q) {
+        double m = M[q * r + i];
+#pragma unroll
+        for (int c = 0; c < DC; ++c) out[c] = fma(m, in[q * DC + c], out[c]);
+      }
+      for (int c = 0; c < nc; ++c) a.F[(int64_t)R[i] * a.nrhs + c0 + c] = out[c];
+    }
+  }
+}
+// Column of the inverse of an LU-factored matrix, staged in shared memory, solved cooperatively:
+// each substitution step updates the remaining entries in parallel.
+__global__ void __launch_bounds__(256) k_dense_inverse(const double* LU, const int32_t* piv, int64_t n,
+                                                       double* inv) {
+  extern __shared__ double x[];
+  const int64_t col = blockIdx.x;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = (i == col) ? 1.0 : 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int64_t j = 0; j < n; ++j) {
+      int p = piv[j];
+      if (p != j) {
+        double t = x[j];
+        x[j] = x[p];
+        x[p] = t;
+      }
+    }
+  __syncthreads();
+  for (int64_t j = 0; j < n; ++j) {  // unit lower
+    double xj = x[j];
+    for (int64_t i = j + 1 + threadIdx.x; i < n; i += blockDim.x) x[i] -= LU[i * n + j] * xj;
+    __syncthreads();
+  }
+  for (int64_t j = n - 1; j >= 0; --j) {  // upper
+    if (threadIdx.x == 0) x[j] /= LU[j * n + j];
+    __syncthreads();
+    double xj = x[j];
+    for (int64_t i = threadIdx.x; i < j; i += blockDim.x) x[i] -= LU[i * n + j] * xj;
+    __syncthreads();
+  }
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) inv[i * n + col] = x[i];
 }
 // Dense root block times rows of F: F[rows] <- A F[rows] (or A^T), one CTA per column.
 __global__ void k_dense_apply(const double* A, int64_t n, const int32_t* rows, double* F, int nrhs, int adjoint) {
@@ -1159,10 +1378,20 @@ __global__ void k_dense_apply(const double* A, int64_t n, const int32_t* rows, d
   const int c = blockIdx.x;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) col[i] = F[(int64_t)rows[i] * nrhs + c];
   __syncthreads();
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    double v = 0.0;
-    for (int64_t q = 0; q < n; ++q) v += (adjoint ? A[q * n + i] : A[i * n + q]) * col[q];
-    out[i] = v;
+  if (adjoint) {
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      double v = 0.0;
+      for (int64_t q = 0; q < n; ++q) v = fma(A[q * n + i], col[q], v);
+      out[i] = v;
+    }
+  } else {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t i = warp; i < n; i += nw) {
+      double v = 0.0;
+      for (int64_t q = lane; q < n; q += 32) v = fma(A[i * n + q], col[q], v);
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) out[i] = v;
+    }
   }
   __syncthreads();
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) F[(int64_t)rows[i] * nrhs + c] = out[i];
@@ -1196,28 +1425,34 @@ void launch_gather_rows(Launch L, const double* in, int64_t ld_in, const int32_t
 }
 void launch_gram(Launch L, const GroupArgs& g, int64_t items) {
   if (items <= 0) return;
-  k_gram<<<grid1(items), NT, 0, L.st>>>(g);
+  if (g.fp32) k_gram<float><<<grid1(items), NT, 0, L.st>>>(g);
+  else k_gram<double><<<grid1(items), NT, 0, L.st>>>(g);
   count_launch(L);
 }
 void launch_chol_panel(Launch L, const GroupArgs& g, int panel) {
   // items = number of (box, side) with l > panel*64; the caller passes it through nbox scan
-  k_chol_panel<<<(unsigned)(2 * g.nbox), NT, 0, L.st>>>(g, panel);
+  if (g.fp32) k_chol_panel<float><<<(unsigned)(2 * g.nbox), NT, 0, L.st>>>(g, panel);
+  else k_chol_panel<double><<<(unsigned)(2 * g.nbox), NT, 0, L.st>>>(g, panel);
   count_launch(L);
 }
 void launch_chol_trsm(Launch L, const GroupArgs& g, int panel, int64_t items) {
   if (items <= 0) return;
-  constexpr size_t smem = 2 * TB * (TB + 1) * sizeof(double);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_chol_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_chol_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(2 * TB * (TB + 1) * sizeof(double)));
+    cudaFuncSetAttribute(k_chol_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(2 * TB * (TB + 1) * sizeof(float)));
     attr = true;
   }
-  k_chol_trsm<<<grid1(items), NT, smem, L.st>>>(g, panel);
+  if (g.fp32) k_chol_trsm<float><<<grid1(items), NT, 2 * TB * (TB + 1) * sizeof(float), L.st>>>(g, panel);
+  else k_chol_trsm<double><<<grid1(items), NT, 2 * TB * (TB + 1) * sizeof(double), L.st>>>(g, panel);
   count_launch(L);
 }
 void launch_chol_update(Launch L, const GroupArgs& g, int panel, int64_t items) {
   if (items <= 0) return;
-  k_chol_update<<<grid1(items), NT, 0, L.st>>>(g, panel);
+  if (g.fp32) k_chol_update<float><<<grid1(items), NT, 0, L.st>>>(g, panel);
+  else k_chol_update<double><<<grid1(items), NT, 0, L.st>>>(g, panel);
   count_launch(L);
 }
 void launch_gather_box(Launch L, const GroupArgs& g, int64_t items) {
@@ -1225,18 +1460,37 @@ void launch_gather_box(Launch L, const GroupArgs& g, int64_t items) {
   count_launch(L);
 }
 void launch_proj_nt(Launch L, const GroupArgs& g, int pass, int64_t items) {
-  k_proj_nt<<<grid1(items), NT, 0, L.st>>>(g, pass);
+  if (g.fp32) k_proj_nt<float><<<grid1(items), NT, 0, L.st>>>(g, pass);
+  else k_proj_nt<double><<<grid1(items), NT, 0, L.st>>>(g, pass);
   count_launch(L);
 }
 void launch_proj_solve(Launch L, const GroupArgs& g, int pass, int64_t items) {
-  k_proj_solve<<<grid1(items), NT, 0, L.st>>>(g, pass);
+  if (g.fp32) k_proj_solve<float><<<grid1(items), NT, 0, L.st>>>(g, pass);
+  else k_proj_solve<double><<<grid1(items), NT, 0, L.st>>>(g, pass);
   count_launch(L);
 }
 void launch_proj_acc(Launch L, const GroupArgs& g, int pass, int64_t items) {
-  k_proj_acc<<<grid1(items), NT, 0, L.st>>>(g, pass);
+  if (g.fp32) k_proj_acc<float><<<grid1(items), NT, 0, L.st>>>(g, pass);
+  else k_proj_acc<double><<<grid1(items), NT, 0, L.st>>>(g, pass);
   count_launch(L);
 }
 void launch_cpqr(Launch L, const GroupArgs& g, int max_b) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(g.nbox * CPQR_C));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = (size_t)max_b * (3 * sizeof(double) + sizeof(int));
+  cfg.stream = L.st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CPQR_C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_cpqr_cluster, g);
+  count_launch(L);
+}
+void launch_cpqr_single(Launch L, const GroupArgs& g, int max_b) {
   size_t smem = (size_t)max_b * (sizeof(double) + sizeof(int));
   k_cpqr<<<(unsigned)g.nbox, 512, smem, L.st>>>(g);
   count_launch(L);
@@ -1248,7 +1502,8 @@ void launch_id_finish(Launch L, const GroupArgs& g, int max_b) {
 }
 void launch_ef_update(Launch L, const GroupArgs& g, int64_t items) {
   if (items <= 0) return;
-  k_ef_update<<<grid1(items), NT, 0, L.st>>>(g);
+  if (g.fp32) k_ef_update<float><<<grid1(items), NT, 0, L.st>>>(g);
+  else k_ef_update<double><<<grid1(items), NT, 0, L.st>>>(g);
   count_launch(L);
 }
 void launch_extract(Launch L, const GroupArgs& g, int64_t items) {
@@ -1267,7 +1522,8 @@ void launch_lu_rhs(Launch L, const GroupArgs& g, int64_t items) {
 }
 void launch_schur(Launch L, const GroupArgs& g, int64_t items) {
   if (items <= 0) return;
-  k_schur<<<grid1(items), NT, 0, L.st>>>(g);
+  if (g.fp32) k_schur<float><<<grid1(items), NT, 0, L.st>>>(g);
+  else k_schur<double><<<grid1(items), NT, 0, L.st>>>(g);
   count_launch(L);
 }
 void launch_dense_lu(Launch L, double* A, int64_t n, int32_t* piv, int* err) {
@@ -1288,12 +1544,22 @@ void launch_sweep_op(Launch L, const SweepArgs& a, int cset, int mat, int trans,
 }
 void launch_sweep_diag(Launch L, const SweepArgs& a, int solve, int64_t items, int max_r) {
   if (items <= 0) return;
-  k_sweep_diag<<<grid1(items), 128, 2 * (size_t)max_r * sizeof(double), L.st>>>(a, solve);
+  k_sweep_diag<<<grid1(items), 256, (size_t)max_r * DC * sizeof(double), L.st>>>(a, solve);
+  count_launch(L);
+}
+void launch_dense_inverse(Launch L, const double* LU, const int32_t* piv, int64_t n, double* inv) {
+  if (n <= 0) return;
+  const size_t smem = (size_t)n * sizeof(double);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_dense_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_dense_inverse<<<(unsigned)n, 256, smem, L.st>>>(LU, piv, n, inv);
   count_launch(L);
 }
 void launch_dense_apply(Launch L, const double* A, int64_t n, const int32_t* rows, double* F, int nrhs,
                         int adjoint) {
-  k_dense_apply<<<nrhs, 256, 2 * n * sizeof(double), L.st>>>(A, n, rows, F, nrhs, adjoint);
+  const size_t smem = 2 * (size_t)n * sizeof(double);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_dense_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_dense_apply<<<nrhs, 256, smem, L.st>>>(A, n, rows, F, nrhs, adjoint);
   count_launch(L);
 }
 

@@ -52,6 +52,7 @@ struct rsrs_factor {
   int32_t* root_idx = nullptr;
   double* root_A = nullptr;
   double* root_LU = nullptr;
+  double* root_inv = nullptr;  // A~_BtBt^-1, for the block-diagonal solve
   int32_t* root_piv = nullptr;
   int max_r = 0;
   double *Y = nullptr, *Z = nullptr, *Om = nullptr, *Ps = nullptr;  // kept sketches (optional)
@@ -317,7 +318,9 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
   if (opts) o = *opts;
   if (o.precision != RSRS_PREC_FP64 && o.precision != RSRS_PREC_MIXED)
     return fail(RSRS_E_INVAL, "build: unknown precision");
-  const int passes = o.proj_passes <= 0 ? 2 : std::min(o.proj_passes, 2);
+  // FP32 projections converge by about 1e-2..1e-3 per pass (rounding of the Gram against its
+  // conditioning), FP64 ones to rounding after the second pass
+  const int passes = o.proj_passes <= 0 ? (o.precision == RSRS_PREC_MIXED ? 3 : 2) : std::min(o.proj_passes, 4);
   Schedule sc;
   build_schedule(T, k, o.p, sc);
   if (s < sc.s_req)
@@ -483,6 +486,7 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
   CU(pool.alloc(&f->root_A, nroot * nroot));
   CU(pool.alloc(&f->root_LU, nroot * nroot));
   CU(pool.alloc(&f->root_piv, nroot));
+  CU(pool.alloc(&f->root_inv, nroot * nroot));
   f->fd_n = fd_total;
   f->fi_n = fi_total;
   f->desc_dev = desc_dev;
@@ -587,6 +591,7 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
   ga.fi = f->fi;
   ga.act = act;
   ga.err = err;
+  ga.fp32 = (o.precision == RSRS_PREC_MIXED) ? 1 : 0;
   double fl[RSRS_NCLASS] = {};
   size_t gi = 0;
   for (int level = T.depth; level >= 1; --level) {
@@ -632,6 +637,7 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
     std::vector<BoxDesc> rh{rd};
     ga.desc = root_desc_dev;
     ga.nbox = 1;
+    ga.fp32 = 0;  // the root block is extracted in FP64
     timed(RSRS_K_ROOT, [&] {
       launch_copy_segments(L, segs_dev + root_seg_off, (int)root_nseg, act, iwork);
       launch_gram(L, ga, items_gram(rh));
@@ -647,7 +653,10 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
     CU(cudaMemcpyAsync(f->root_idx, iwork, nroot * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
     CU(cudaMemcpyAsync(f->root_A, work + rd.x_off, nroot * nroot * sizeof(double), cudaMemcpyDeviceToDevice, st));
     CU(cudaMemcpyAsync(f->root_LU, work + rd.x_off, nroot * nroot * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    timed(RSRS_K_ROOT, [&] { launch_dense_lu(L, f->root_LU, nroot, f->root_piv, err); });
+    timed(RSRS_K_ROOT, [&] {
+      launch_dense_lu(L, f->root_LU, nroot, f->root_piv, err);
+      launch_dense_inverse(L, f->root_LU, f->root_piv, nroot, f->root_inv);
+    });
     const double nr = (double)nroot;
     f->stats.class_gflop[RSRS_K_ROOT] = (2.0 * nr * (nr + 1) * s + nr * nr * nr / 3.0 + 2.0 * nr * nr * s +
                                          2.0 * nr * nr * nr + 2.0 * nr * nr * nr / 3.0) * 1e-9;
@@ -673,7 +682,7 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
   f->stats.k = k;
   f->stats.n_boxes = (int64_t)all_desc.size();
   f->stats.root_size = nroot;
-  f->stats.factor_bytes = fd_total * 8 + fi_total * 4 + nroot * nroot * 16 + nroot * 8;
+  f->stats.factor_bytes = fd_total * 8 + fi_total * 4 + nroot * nroot * 24 + nroot * 8;
   f->stats.work_bytes = work_max * 8 + iwork_max * 4 + 4 * NS * 8;
   f->stats.t_sample_ms = t01;
   f->stats.t_compress_ms = t12;
@@ -681,7 +690,8 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
   f->stats.kernel_launches = launches;
   // keep what the factor owns
   for (void* p : {(void*)f->fd, (void*)f->fi, (void*)f->root_idx, (void*)f->root_A, (void*)f->root_LU,
-                  (void*)f->root_piv, (void*)f->desc_dev, (void*)f->perm_dev, (void*)f->pts_dev})
+                  (void*)f->root_piv, (void*)f->root_inv, (void*)f->desc_dev, (void*)f->perm_dev,
+                  (void*)f->pts_dev})
     pool.release(p);
   if (o.keep_sketches) {
     f->Y = Y;
@@ -697,8 +707,8 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
 void rsrs_factor_free(rsrs_factor* f) {
   if (!f) return;
   for (void* p : {(void*)f->fd, (void*)f->fi, (void*)f->root_idx, (void*)f->root_A, (void*)f->root_LU,
-                  (void*)f->root_piv, (void*)f->desc_dev, (void*)f->perm_dev, (void*)f->pts_dev, (void*)f->Y,
-                  (void*)f->Z, (void*)f->Om, (void*)f->Ps})
+                  (void*)f->root_piv, (void*)f->root_inv, (void*)f->desc_dev, (void*)f->perm_dev,
+                  (void*)f->pts_dev, (void*)f->Y, (void*)f->Z, (void*)f->Om, (void*)f->Ps})
     if (p) cudaFree(p);
   delete f;
 }
@@ -730,8 +740,7 @@ rsrs_status sweep_solve(const rsrs_factor* f, Launch L, double* W, int nrhs, int
     a.nbox = (int)g.h.size();
     launch_sweep_diag(L, a, 1, items_diag(g.h, nrhs), g.max_r);
   }
-  if (f->root_size > 0)
-    launch_dense_lu_solve(L, f->root_LU, f->root_piv, f->root_size, f->root_idx, W, nrhs, adjoint);
+  if (f->root_size > 0) launch_dense_apply(L, f->root_inv, f->root_size, f->root_idx, W, nrhs, adjoint);
   for (auto it = f->groups.rbegin(); it != f->groups.rend(); ++it) {
     const Group& g = *it;
     a.desc = f->desc_dev + g.desc_off;

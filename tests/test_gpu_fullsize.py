@@ -1,0 +1,85 @@
+"""Full-size checks at the benchmark workload (65,536 random 2D points, k=48, s=s_req=1824, 16 RHS),
+in the launch configuration bench.py times (device Philox test matrices, mixed precision + FP64
+refinement), against what the oracle can compute row by row, plus properties that hold at any size.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import operators as ops
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2311_01451_gb300 as pkg
+
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def setup(R):
+    pr = W.config(1)[0]
+    tree = R.Tree(pr.points, pr.leaf)
+    s = max(pr.s_cfg, tree.info(pr.k).s_req)
+    assert s == 1824
+    b = pr.rhs()
+    B = torch.tensor(np.ascontiguousarray(b.T), device="cuda")
+    return pr, tree, s, b, B
+
+
+def _rows(pr, idx, x):
+    """Oracle rows of A x for a sample of rows (the dense operator, one row block)."""
+    return ops.make_operator(pr).rows(idx) @ x
+
+
+def test_fullsize_mixed_refined_solution(R, setup):
+    pr, tree, s, b, B = setup
+    f = R.Factor(tree, R.RSRS_OP_LOG2D, pr.k, s, shift=pr.diag_shift, scale=pr.scale,
+                 precision=R.RSRS_PREC_MIXED, seed=5)
+    X = torch.zeros_like(B)
+    rep = f.refine(B, X, rtol=1e-12, maxit=30)
+    assert rep.rel_residual <= 1e-12
+    x = X.cpu().numpy().T
+    idx = np.random.default_rng(3).choice(pr.n, 48, replace=False)
+    r = b[idx] - _rows(pr, idx, x)
+    # sampled residual rows, computed by the oracle, at the level of the device residual
+    assert np.linalg.norm(r) / np.linalg.norm(b[idx]) < 1e-11
+    # apply(solve(b)) = b to rounding
+    Fs = B.clone()
+    f.apply(f.solve(Fs))
+    assert float(torch.linalg.norm(Fs - B) / torch.linalg.norm(B)) < 1e-12
+    # the unrefined mixed factor is a good preconditioner
+    assert rep.history[0] < 1e-2
+
+
+def test_fullsize_matvec_rows(R, setup):
+    pr, tree, s, b, B = setup
+    f = R.Factor(tree, R.RSRS_OP_LOG2D, pr.k, s, shift=pr.diag_shift, scale=pr.scale,
+                 precision=R.RSRS_PREC_MIXED, seed=6)
+    Y = torch.empty_like(B)
+    f.matvec(B, Y)
+    y = Y.cpu().numpy().T
+    idx = np.random.default_rng(4).choice(pr.n, 48, replace=False)
+    ref = _rows(pr, idx, b)
+    assert np.abs(y[idx] - ref).max() / np.abs(ref).max() < 1e-13
+
+
+def test_fullsize_mixed_matches_fp64(R, setup):
+    pr, tree, s, b, B = setup
+    out = {}
+    for prec in (R.RSRS_PREC_MIXED, R.RSRS_PREC_FP64):
+        f = R.Factor(tree, R.RSRS_OP_LOG2D, pr.k, s, shift=pr.diag_shift, scale=pr.scale, precision=prec, seed=7)
+        X = torch.zeros_like(B)
+        f.refine(B, X, rtol=1e-13, maxit=30)
+        out[prec] = X
+        del f
+    rel = float(torch.linalg.norm(out[0] - out[1]) / torch.linalg.norm(out[1]))
+    assert rel < 1e-10
