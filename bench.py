@@ -209,7 +209,7 @@ def run_gpu(args):
 
     def step(seed, profile=False):
         f = R.Factor(tree, kind, pr.k, s, shift=pr.diag_shift, scale=pr.scale, precision=prec, seed=seed,
-                     profile=profile)
+                     profile=profile, sample_kernel=args.sample_kernel)
         rep = f.refine(B, X, rtol=RTOL, maxit=30)
         st = f.stats()
         cls = f.class_stats()
@@ -336,6 +336,7 @@ def main():
     ap.add_argument("--workload", type=int, default=1, help="workload index (1: 2D N=65536, k=48)")
     ap.add_argument("--n", type=int, default=0, help="override the number of points (profiling runs only)")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--sample-kernel", type=int, default=0, help="mixed sampling: 0 default, 1 FP32 SIMT, 2 tcgen05")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=20.0)

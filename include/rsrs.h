@@ -95,6 +95,11 @@ typedef struct {
   const double* psi_dev;
   int keep_sketches;      /* keep the final Y, Z, Omega, Psi on the device (tests)     */
   int profile;            /* record CUDA-event time per kernel class into rsrs_stats    */
+  int sample_kernel;      /* mixed precision, built-in kernels: 0 default, 1 FP32 SIMT,  */
+                          /* 2 3xTF32 on the tensor cores (tcgen05)                    */
+  int64_t residual_matrix_bytes; /* built-in kernels: rsrs_refine stores A in FP64 (N*N*8 */
+                          /* bytes, computed once per factor) when it fits this budget; */
+                          /* 0 selects 48 GiB, < 0 always evaluates A on the fly       */
 } rsrs_options;
 
 typedef struct {

@@ -12,7 +12,7 @@
 namespace rsrs {
 
 // Device error word: set (first writer wins) by kernels that meet a bad pivot.
-enum DevErr : int { kDevOk = 0, kDevSingular = 1, kDevNonfinite = 2 };
+enum DevErr : int { kDevOk = 0, kDevSingular = 1, kDevNonfinite = 2, kDevTimeout = 3 };
 
 // One compressed box of a (level, colour) group, as the device kernels see it.
 // All offsets are element offsets into the buffers named in the comments.
@@ -24,6 +24,7 @@ struct BoxDesc {
   int64_t x2_off;   // double work: two b x l second-pass blocks
   int64_t m_off;    // double work: b x 2s projected sketches [Y' | Z']
   int64_t cp_off;   // double work: CPQR R rows, kp x b; then extraction blocks 2 x r x l
+  int64_t li_off;   // double work: inverses of the 64 x 64 diagonal Cholesky blocks, 2 x nblk x 64 x 64
   int64_t pv_off;   // int32 work: b CPQR local permutation, then the first dependent step
   int64_t fi_off;   // int32 factor: R (r), S (kp), N (n), LU pivots (r)
   int64_t fd_off;   // double factor: T (kp x r), XRR (r x r), LU (r x r), LcT (r x (kp+n)), Uc (r x (kp+n)),
@@ -72,6 +73,17 @@ void launch_kernel_matvec(Launch L, int kind, const double* pts, int d, int64_t 
 void launch_kernel_matvec_prec(Launch L, int kind, const double* pts, int d, int64_t n, double shift,
                                double scale, const double* in, int64_t ld_in, double* out, int64_t ld_out,
                                int64_t ncols, int fp32);
+
+// Same product in 3xTF32 on the tensor cores (tcgen05, TMEM accumulators); a bounded wait that
+// expires records kDevTimeout in *err.
+void launch_kernel_matvec_tc(Launch L, int kind, const double* pts, int d, int64_t n, double shift, double scale,
+                             const double* in, int64_t ld_in, double* out, int64_t ld_out, int64_t ncols, int* err);
+
+// Operator matrix A = shift*I + scale*K stored in FP64 (tree order), and out = A in (few columns).
+void launch_operator_matrix(Launch L, int kind, const double* pts, int d, int64_t n, double shift, double scale,
+                            double* A);
+void launch_matrix_product(Launch L, const double* A, int64_t n, const double* in, int64_t ld_in, double* out,
+                           int64_t ld_out, int64_t ncols);
 
 // Group-batched kernels (descriptors of one (level, colour) group).
 struct GroupArgs {

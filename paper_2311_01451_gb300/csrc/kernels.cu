@@ -301,11 +301,14 @@ __global__ void __launch_bounds__(NT) k_chol_panel(GroupArgs g, int p) {
 struct CntPanelRows {
   int p;
   __host__ __device__ int64_t operator()(const BoxDesc& d) const {
+    if (d.l <= (int64_t)p * TB) return 0;
     int64_t below = d.l - (int64_t)(p + 1) * TB;
-    return below > 0 ? 2 * cdv(below, TB) : 0;
+    return 2 * ((below > 0 ? cdv(below, TB) : 0) + 1);
   }
 };
-// L_ip = G_ip L_pp^-T for the 64-row tiles below the diagonal block of panel p.
+// L_ip = G_ip L_pp^-T for the 64-row tiles below the diagonal block of panel p, and one more tile
+// with the identity as right-hand side, whose solution L_pp^-T gives the inverse of the diagonal
+// block (stored for the triangular solves of the projection).
 template <typename CT>
 __global__ void __launch_bounds__(NT) k_chol_trsm(GroupArgs g, int p) {
   int64_t loc;
@@ -313,14 +316,15 @@ __global__ void __launch_bounds__(NT) k_chol_trsm(GroupArgs g, int p) {
   if (bi < 0) return;
   const BoxDesc d = g.desc[bi];
   int64_t below = d.l - (int64_t)(p + 1) * TB;
-  int64_t per = cdv(below, TB);
+  int64_t per = (below > 0 ? cdv(below, TB) : 0) + 1;
   int side = (int)(loc / per);
   int64_t ti = loc % per;
+  const bool inv = (ti == per - 1);  // the identity tile
   double* G = g.work + d.g_off + (int64_t)side * d.l * d.l;
   const int64_t o = (int64_t)p * TB;
   const int nb = (int)imin64(TB, d.l - o);
   const int64_t r0 = (int64_t)(p + 1) * TB + ti * TB;
-  const int nr = (int)imin64(TB, d.l - r0);
+  const int nr = inv ? nb : (int)imin64(TB, d.l - r0);
   extern __shared__ __align__(16) unsigned char trsm_raw[];
   CT* trsm_sm = reinterpret_cast<CT*>(trsm_raw);
   CT(*Lp)[TB + 1] = reinterpret_cast<CT(*)[TB + 1]>(trsm_sm);
@@ -328,7 +332,10 @@ __global__ void __launch_bounds__(NT) k_chol_trsm(GroupArgs g, int p) {
   for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
     int i = e / TB, j = e % TB;
     Lp[i][j] = (i < nb && j < nb) ? (CT)G[(o + i) * d.l + o + j] : (CT)0;
-    X[i][j] = (i < nr && j < nb) ? (CT)G[(r0 + i) * d.l + o + j] : (CT)0;
+    if (inv)
+      X[i][j] = (i == j && i < nb) ? (CT)1 : (CT)0;
+    else
+      X[i][j] = (i < nr && j < nb) ? (CT)G[(r0 + i) * d.l + o + j] : (CT)0;
   }
   __syncthreads();
   // x L^T = g, column by column; threads over the rows of the tile (4 threads per row, 16 cols each)
@@ -340,6 +347,14 @@ __global__ void __launch_bounds__(NT) k_chol_trsm(GroupArgs g, int p) {
       X[i][j] -= X[i][c] * Lp[j][c];
     }
     __syncthreads();
+  }
+  if (inv) {  // X = L_pp^-T; store L_pp^-1 (zero padded to 64 x 64)
+    double* Li = g.work + d.li_off + ((int64_t)side * cdv(d.l, TB) + p) * TB * TB;
+    for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+      int i = e / TB, j = e % TB;
+      Li[e] = (i < nb && j < nb) ? (double)X[j][i] : 0.0;
+    }
+    return;
   }
   for (int e = threadIdx.x; e < nr * nb; e += blockDim.x) {
     int i = e / nb, j = e % nb;
@@ -459,6 +474,7 @@ __global__ void __launch_bounds__(NT) k_proj_solve(GroupArgs g, int pass) {
   int64_t r0 = (loc % per) * SR;
   const int nr = (int)imin64(SR, d.b - r0);
   const double* L = g.work + d.g_off + (int64_t)side * d.l * d.l;
+  const double* Linv = g.work + d.li_off + (int64_t)side * cdv(d.l, TB) * TB * TB;
   double* X = g.work + (pass ? d.x2_off : d.x_off) + (int64_t)side * d.b * d.l + r0 * d.l;
   const int64_t l = d.l;
   const int64_t nblk = cdv(l, TB);
@@ -494,25 +510,28 @@ __global__ void __launch_bounds__(NT) k_proj_solve(GroupArgs g, int pass) {
       }
       __syncthreads();
     }
+    // U_jb = acc L_jb^-T with the stored inverse of the diagonal block
+    const double* Li = Linv + jb * TB * TB;
     for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
       int i = e / TB, j = e % TB;
-      Ls[i][j] = (i < nc && j < nc) ? (CT)L[(c0 + i) * l + c0 + j] : (CT)0;
+      Ls[i][j] = (CT)Li[e];
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) Xs[ty][tx + 16 * u] = acc[u];
     __syncthreads();
-    for (int c = 0; c < nc; ++c) {
-      if (threadIdx.x < SR) Xs[threadIdx.x][c] /= Ls[c][c];
-      __syncthreads();
-      for (int e = threadIdx.x; e < SR * (nc - c - 1); e += blockDim.x) {
-        int i = e / (nc - c - 1), j = c + 1 + e % (nc - c - 1);
-        Xs[i][j] -= Xs[i][c] * Ls[j][c];
+    {
+      CT out[4] = {};
+#pragma unroll 8
+      for (int q = 0; q < TB; ++q) {
+        CT xv = Xs[ty][q];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) out[u] = mad<CT>(xv, Ls[tx + 16 * u][q], out[u]);
       }
-      __syncthreads();
-    }
-    for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
-      int i = e / nc, j = e % nc;
-      X[i * l + c0 + j] = (double)Xs[i][j];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        int c = tx + 16 * u;
+        if (ty < nr && c < nc) X[ty * l + c0 + c] = (double)out[u];
+      }
     }
     __syncthreads();
   }
@@ -546,25 +565,28 @@ __global__ void __launch_bounds__(NT) k_proj_solve(GroupArgs g, int pass) {
       }
       __syncthreads();
     }
+    // X_jb = acc L_jb^-1
+    const double* Li = Linv + jb * TB * TB;
     for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
       int i = e / TB, j = e % TB;
-      Ls[i][j] = (i < nc && j < nc) ? (CT)L[(c0 + i) * l + c0 + j] : (CT)0;
+      Ls[i][j] = (CT)Li[e];
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) Xs[ty][tx + 16 * u] = acc[u];
     __syncthreads();
-    for (int c = nc - 1; c >= 0; --c) {
-      if (threadIdx.x < SR) Xs[threadIdx.x][c] /= Ls[c][c];
-      __syncthreads();
-      for (int e = threadIdx.x; e < SR * c; e += blockDim.x) {
-        int i = e / c, j = e % c;
-        Xs[i][j] -= Xs[i][c] * Ls[c][j];
+    {
+      CT out[4] = {};
+#pragma unroll 8
+      for (int q = 0; q < TB; ++q) {
+        CT xv = Xs[ty][q];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) out[u] = mad<CT>(xv, Ls[q][tx + 16 * u], out[u]);
       }
-      __syncthreads();
-    }
-    for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
-      int i = e / nc, j = e % nc;
-      X[i * l + c0 + j] = (double)Xs[i][j];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        int c = tx + 16 * u;
+        if (ty < nr && c < nc) X[ty * l + c0 + c] = (double)out[u];
+      }
     }
     __syncthreads();
   }

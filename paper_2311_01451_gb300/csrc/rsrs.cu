@@ -56,6 +56,10 @@ struct rsrs_factor {
   int32_t* root_piv = nullptr;
   int max_r = 0;
   double *Y = nullptr, *Z = nullptr, *Om = nullptr, *Ps = nullptr;  // kept sketches (optional)
+  double* Amat = nullptr;  // FP64 operator matrix for refinement residuals (lazily, within budget)
+  int sample_kernel = 0;   // mixed sampling: 1 FP32 SIMT, 2 tcgen05 3xTF32
+  int* err_dev = nullptr;  // device status word of kernels run outside a build (sampling)
+  int64_t amat_budget = 0;
   rsrs_stats stats{};
 };
 
@@ -202,13 +206,23 @@ void box_flops(const BoxDesc& d, int64_t s, int passes, double* fl) {
 
 // Apply the operator to a tree-order row-major block: out = A in (adjoint for callbacks).
 rsrs_status op_apply(const rsrs_factor* f, Launch L, const double* in, double* out, int64_t ncols, int adjoint,
-                     int fp32, double* scratch_cm_in, double* scratch_cm_out) {
+                     int fp32, double* scratch_cm_in, double* scratch_cm_out, int* err = nullptr) {
   if (f->kind == RSRS_OP_CALLBACK) {
     int64_t tot = f->n * ncols;
     k_rows_to_cm<<<nblk(tot), 256, 0, L.st>>>(in, f->perm_dev, f->n, (int)ncols, scratch_cm_in, f->n);
     int rc = f->fn(f->ctx, adjoint, f->n, (int32_t)ncols, scratch_cm_in, f->n, scratch_cm_out, f->n, (void*)L.st);
     if (rc != 0) return fail(RSRS_E_CALLBACK, "matvec callback returned " + std::to_string(rc));
     k_cm_to_rows<<<nblk(tot), 256, 0, L.st>>>(scratch_cm_out, f->n, f->perm_dev, f->n, (int)ncols, out);
+    CU(cudaGetLastError());
+    return RSRS_OK;
+  }
+  if (fp32 && f->sample_kernel == 2) {
+    launch_kernel_matvec_tc(L, f->kind, f->pts_dev, f->d, f->n, f->shift, f->scale, in, ncols, out, ncols, ncols, err);
+    CU(cudaGetLastError());
+    return RSRS_OK;
+  }
+  if (f->Amat && !fp32 && ncols <= 16) {
+    launch_matrix_product(L, f->Amat, f->n, in, ncols, out, ncols, ncols);
     CU(cudaGetLastError());
     return RSRS_OK;
   }
@@ -340,6 +354,9 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
   f->fn = op->fn;
   f->ctx = op->ctx;
   f->perm = T.perm;
+  f->amat_budget = o.residual_matrix_bytes == 0 ? (int64_t)48 << 30 : o.residual_matrix_bytes;
+  if (o.sample_kernel < 0 || o.sample_kernel > 2) return fail(RSRS_E_INVAL, "build: unknown sample_kernel");
+  f->sample_kernel = o.sample_kernel == 0 ? 1 : o.sample_kernel;
   const int64_t N = T.n;
   const int nbox_tree = (int)T.boxes.size();
 
@@ -402,6 +419,8 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
         w += (int64_t)d.b * 2 * s;
         d.cp_off = w;
         w += std::max<int64_t>((int64_t)d.kp * d.b, 2 * (int64_t)d.r * d.l);
+        d.li_off = w;
+        w += 2 * cdiv(d.l, kT) * kT * kT;
         d.fi_off = fi_total;
         fi_total += fi_size(d.kp, d.r, d.n);
         d.fd_off = fd_total;
@@ -442,7 +461,8 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
     rd.x2_off = rd.x_off;
     rd.m_off = rd.x_off + 2 * nroot * nroot;
     rd.cp_off = rd.m_off + nroot * 2 * s;
-    work_max = std::max(work_max, rd.cp_off + 1);
+    rd.li_off = rd.cp_off + 1;
+    work_max = std::max(work_max, rd.li_off + 2 * cdiv(nroot, kT) * kT * kT);
     iwork_max = std::max(iwork_max, 2 * nroot);
     if (T.depth == 0) {
       segs.push_back({act_off[0], 0, nroot});
@@ -571,8 +591,8 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
     const int fp32 = (o.precision == RSRS_PREC_MIXED) ? 1 : 0;
     rsrs_status r1 = RSRS_OK;
     timed(RSRS_K_SAMPLE, [&] {
-      r1 = op_apply(f.get(), L, Om, Y, s, 0, fp32, cm_in, cm_out);
-      if (r1 == RSRS_OK) r1 = op_apply(f.get(), L, Ps, Z, s, 1, fp32, cm_in, cm_out);
+      r1 = op_apply(f.get(), L, Om, Y, s, 0, fp32, cm_in, cm_out, err);
+      if (r1 == RSRS_OK) r1 = op_apply(f.get(), L, Ps, Z, s, 1, fp32, cm_in, cm_out, err);
     });
     if (r1 != RSRS_OK) return r1;
     if (f->kind != RSRS_OP_CALLBACK) f->stats.class_gflop[RSRS_K_SAMPLE] = 4.0 * (double)N * N * s * 1e-9;
@@ -668,6 +688,7 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
   CU(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
   if (herr == kDevSingular) return fail(RSRS_E_SINGULAR, "zero pivot in an LU factorization");
   if (herr == kDevNonfinite) return fail(RSRS_E_NONFINITE, "non-finite or non-positive pivot");
+  if (herr == kDevTimeout) return fail(RSRS_E_TIMEOUT, "a bounded device wait expired");
   float t01, t12, t23;
   CU(cudaEventElapsedTime(&t01, ev[0], ev[1]));
   CU(cudaEventElapsedTime(&t12, ev[1], ev[2]));
@@ -708,7 +729,7 @@ void rsrs_factor_free(rsrs_factor* f) {
   if (!f) return;
   for (void* p : {(void*)f->fd, (void*)f->fi, (void*)f->root_idx, (void*)f->root_A, (void*)f->root_LU,
                   (void*)f->root_piv, (void*)f->root_inv, (void*)f->desc_dev, (void*)f->perm_dev,
-                  (void*)f->pts_dev, (void*)f->Y, (void*)f->Z, (void*)f->Om, (void*)f->Ps})
+                  (void*)f->pts_dev, (void*)f->Y, (void*)f->Z, (void*)f->Om, (void*)f->Ps, (void*)f->Amat})
     if (p) cudaFree(p);
   delete f;
 }
@@ -877,6 +898,18 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_
   if (f->kind == RSRS_OP_CALLBACK) {
     CU(pool.alloc(&c1, tot));
     CU(pool.alloc(&c2, tot));
+  }
+  // FP64 operator matrix for the residuals, once per factor, when it fits the budget
+  if (f->kind != RSRS_OP_CALLBACK && !f->Amat && nrhs <= 16 && f->amat_budget > 0 &&
+      (double)f->n * f->n * 8.0 <= (double)f->amat_budget) {
+    rsrs_factor* fm = const_cast<rsrs_factor*>(f);
+    if (cudaMalloc((void**)&fm->Amat, (size_t)f->n * f->n * sizeof(double)) == cudaSuccess) {
+      launch_operator_matrix(L, f->kind, f->pts_dev, f->d, f->n, f->shift, f->scale, fm->Amat);
+      CU(cudaGetLastError());
+    } else {
+      fm->Amat = nullptr;
+      cudaGetLastError();  // not enough memory: evaluate on the fly
+    }
   }
   k_cm_to_rows<<<nblk(tot), 256, 0, st>>>(B, ld, f->perm_dev, f->n, nrhs, Wb);
   CU(cudaMemcpyAsync(Wx, Wb, tot * sizeof(double), cudaMemcpyDeviceToDevice, st));

@@ -39,7 +39,8 @@ class Operator(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("p", C.c_int), ("proj_passes", C.c_int), ("seed", C.c_uint64),
                 ("omega_host", C.c_void_p), ("psi_host", C.c_void_p), ("omega_dev", C.c_void_p),
-                ("psi_dev", C.c_void_p), ("keep_sketches", C.c_int), ("profile", C.c_int)]
+                ("psi_dev", C.c_void_p), ("keep_sketches", C.c_int), ("profile", C.c_int),
+                ("sample_kernel", C.c_int), ("residual_matrix_bytes", C.c_int64)]
 
 
 NCLASS = 16
@@ -186,7 +187,8 @@ class Factor:
     def __init__(self, tree: Tree, kind: int, k: int, s: int, shift: float = 1.0, scale: float = 0.0,
                  precision: int = RSRS_PREC_FP64, p: int = -1, omega: np.ndarray | None = None,
                  psi: np.ndarray | None = None, seed: int = 0, passes: int = 0, keep_sketches: bool = False,
-                 matvec=None, stream=None, profile: bool = False):
+                 matvec=None, stream=None, profile: bool = False, residual_matrix_bytes: int = 0,
+                 sample_kernel: int = 0):
         self.tree = tree
         self.n = tree.n
         self._cb = None
@@ -197,7 +199,8 @@ class Factor:
             self._cb = MATVEC_FN(matvec)
             op.fn = self._cb
         opts = Options(precision=precision, p=p, proj_passes=passes, seed=seed,
-                       keep_sketches=int(keep_sketches), profile=int(profile))
+                       keep_sketches=int(keep_sketches), profile=int(profile),
+                       residual_matrix_bytes=residual_matrix_bytes, sample_kernel=sample_kernel)
         self._om = self._ps = None
         if omega is not None and hasattr(omega, "data_ptr"):  # device tensors (N, s), original order
             self._om, self._ps = omega, psi

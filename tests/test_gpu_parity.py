@@ -141,6 +141,20 @@ def test_refine_fp64_reaches_dense_solution(case):
     assert _rel(_from_gpu(X), xd) < 1e-11
 
 
+def test_refine_on_the_fly_residual(R):
+    """Refinement with the operator evaluated on the fly (no stored FP64 matrix)."""
+    pr = CASES["rand2d_3000"]()
+    tree, sched, fac, _ = orsrs.build(pr)
+    t = R.Tree(pr.points, pr.leaf)
+    f = R.Factor(t, R.kind_of(pr.kernel), pr.k, fac.s, shift=pr.diag_shift, scale=pr.scale,
+                 precision=R.RSRS_PREC_MIXED, omega=pr.omega(fac.s), psi=pr.psi(fac.s), residual_matrix_bytes=-1)
+    b = pr.rhs()
+    X = torch.zeros_like(_to_gpu(b))
+    rep = f.refine(_to_gpu(b), X, rtol=1e-13, maxit=30)
+    assert rep.rel_residual <= 1e-13
+    assert _rel(_from_gpu(X), np.linalg.solve(ops.make_operator(pr).dense(), b)) < 1e-11
+
+
 def test_mixed_precision_refined_matches_fp64_oracle(R, case):
     pr, fac, _, _, _ = case
     fm = _gpu_factor(R, pr, fac.s, precision=R.RSRS_PREC_MIXED)
