@@ -40,11 +40,13 @@ def pinv_right(y: np.ndarray, m: np.ndarray) -> np.ndarray:
     return sla.solve_triangular(r, (y @ q).T, lower=False).T
 
 
-def cpqr_id(m: np.ndarray, k: int, tau: float):
+def cpqr_id(m: np.ndarray, k: int, tau: float, record: dict | None = None):
     """Row ID of m (b x c): returns (skel, red, T) with m[red] ~= T^T m[skel].
 
     skel: k row indices in pivot order; red: the other rows, ascending;
-    T: k x (b-k) interpolation matrix.
+    T: k x (b-k) interpolation matrix.  ``record`` (a dict) receives, per pivot
+    step, the runner-up row and the gap between the two largest residual norms
+    relative to |R_00| (diagnostics for comparing implementations at near-ties).
     """
     a = np.array(m.T, dtype=np.float64, copy=True)  # c x b: pivot over columns = rows of m
     c, b = a.shape
@@ -61,6 +63,13 @@ def cpqr_id(m: np.ndarray, k: int, tau: float):
         else:
             cand = np.nonzero(norms == best)[0]
             p = j + cand[np.argmin(perm[j + cand])]
+        if record is not None:
+            order = np.argsort(-norms, kind="stable")
+            second = norms[order[1]] if len(order) > 1 else 0.0
+            ref = r00 if r00 else best
+            record.setdefault("gap", []).append((best - second) / ref if ref else 0.0)
+            record.setdefault("runner", []).append(int(perm[j + order[1]]) if len(order) > 1 else -1)
+            record.setdefault("dependent", []).append(bool(j0 <= j))
         if p != j:
             a[:, [j, p]] = a[:, [p, j]]
             perm[[j, p]] = perm[[p, j]]

@@ -69,7 +69,9 @@ class BoxFactor:
     UcS: np.ndarray  # X_RR^-1 X_RS   (r x k')
     UcN: np.ndarray  # X_RR^-1 X_RN   (r x n)
     XRR_z: np.ndarray = None  # X_RR as estimated from the Z side (diagnostic)
-    R11_diag: np.ndarray = None  # |R_jj| of the CPQR (diagnostic)
+    pivot_gap: np.ndarray = None  # per CPQR step: (largest - second residual norm) / |R_00|
+    pivot_runner: np.ndarray = None  # per CPQR step: the runner-up point
+    pivot_dependent: np.ndarray = None  # per CPQR step: taken by the dependent-pivot rule
 
 
 @dataclass
@@ -119,7 +121,8 @@ def factor(tree: Tree, sched: Schedule, Y, Z, Om, Ps, trace=None, max_steps: int
             Zp = Z[Bact] @ la.null(Ps[BN])
             # step 3: ID of the concatenation
             kp = min(k, b)
-            skel, red, T = la.cpqr_id(np.hstack([Yp, Zp]), kp, id_tau(b, s))
+            rec = {}
+            skel, red, T = la.cpqr_id(np.hstack([Yp, Zp]), kp, id_tau(b, s), record=rec)
             S, R = Bact[skel], Bact[red]
             # step 4: sparsification E, F
             Y[R] -= T.T @ Y[S]
@@ -148,7 +151,11 @@ def factor(tree: Tree, sched: Schedule, Y, Z, Om, Ps, trace=None, max_steps: int
             # step 7: R leaves the active set
             act[box.id] = _tree_sorted(S, tree.pos)
             bf = BoxFactor(box_id=box.id, level=level, colour=st["colour"], B=Bact, S=S, R=R, N=Nact,
-                           T=T, XRR=XRR, lu=f, LcS=LcS, LcN=LcN, UcS=UcS, UcN=UcN, XRR_z=Xz[:, red].T)
+                           T=T, XRR=XRR, lu=f, LcS=LcS, LcN=LcN, UcS=UcS, UcN=UcN, XRR_z=Xz[:, red].T,
+                           pivot_gap=np.array(rec.get("gap", [])),
+                           pivot_runner=Bact[np.array(rec.get("runner", []), dtype=np.int64)]
+                           if rec.get("runner") else np.zeros(0, dtype=np.int64),
+                           pivot_dependent=np.array(rec.get("dependent", []), dtype=bool))
             fac.boxes.append(bf)
             if trace is not None:
                 trace.append(dict(box=bf, Yp=Yp, Zp=Zp))
