@@ -24,7 +24,8 @@ struct BoxDesc {
   int64_t x2_off;   // double work: two b x l second-pass blocks
   int64_t m_off;    // double work: b x 2s projected sketches [Y' | Z']
   int64_t cp_off;   // double work: CPQR R rows, kp x b; then extraction blocks 2 x r x l
-  int64_t li_off;   // double work: inverses of the 64 x 64 diagonal Cholesky blocks, 2 x nblk x 64 x 64
+  int64_t li_off;   // double work: inverses (and their transposes) of the 64 x 64 diagonal Cholesky
+                    //   blocks, 2 sides x nblk x 2 x 64 x 64
   int64_t pv_off;   // int32 work: b CPQR local permutation, then the first dependent step
   int64_t fi_off;   // int32 factor: R (r), S (kp), N (n), LU pivots (r)
   int64_t fd_off;   // double factor: T (kp x r), XRR (r x r), LU (r x r), LcT (r x (kp+n)), Uc (r x (kp+n)),
@@ -69,15 +70,21 @@ void launch_gather_rows(Launch L, const double* in, int64_t ld_in, const int32_t
 void launch_kernel_matvec(Launch L, int kind, const double* pts, int d, int64_t n, double shift,
                           double scale, const double* in, int64_t ld_in, double* out, int64_t ld_out,
                           int64_t ncols);
-// Same, with the kernel part in FP32 (fp32 != 0; identity term and partial-sum flushes in FP64).
+// Same, with the kernel part in FP32 (fp32 != 0) from in32, an FP32 copy of `in` (same layout);
+// the identity term uses the FP64 `in`.
 void launch_kernel_matvec_prec(Launch L, int kind, const double* pts, int d, int64_t n, double shift,
                                double scale, const double* in, int64_t ld_in, double* out, int64_t ld_out,
-                               int64_t ncols, int fp32);
+                               int64_t ncols, int fp32, const float* in32);
+// FP32 copy; and TF32 hi/lo split of an n x s row-major block transposed to s x n planes.
+void launch_to_f32(Launch L, const double* in, int64_t count, float* out);
+void launch_split_transpose(Launch L, const double* in, int64_t n, int64_t s, float* hi, float* lo);
 
 // Same product in 3xTF32 on the tensor cores (tcgen05, TMEM accumulators); a bounded wait that
 // expires records kDevTimeout in *err.
+// bhi/blo: the TF32 hi/lo planes of `in`, transposed (ncols x n).
 void launch_kernel_matvec_tc(Launch L, int kind, const double* pts, int d, int64_t n, double shift, double scale,
-                             const double* in, int64_t ld_in, double* out, int64_t ld_out, int64_t ncols, int* err);
+                             const double* in, int64_t ld_in, const float* bhi, const float* blo, double* out,
+                             int64_t ld_out, int64_t ncols, int* err);
 
 // Operator matrix A = shift*I + scale*K stored in FP64 (tree order), and out = A in (few columns).
 void launch_operator_matrix(Launch L, int kind, const double* pts, int d, int64_t n, double shift, double scale,

@@ -348,11 +348,13 @@ __global__ void __launch_bounds__(NT) k_chol_trsm(GroupArgs g, int p) {
     }
     __syncthreads();
   }
-  if (inv) {  // X = L_pp^-T; store L_pp^-1 (zero padded to 64 x 64)
-    double* Li = g.work + d.li_off + ((int64_t)side * cdv(d.l, TB) + p) * TB * TB;
+  if (inv) {  // X = L_pp^-T; store L_pp^-1 and L_pp^-T (zero padded to 64 x 64)
+    double* Li = g.work + d.li_off + ((int64_t)side * cdv(d.l, TB) + p) * 2 * TB * TB;
     for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
       int i = e / TB, j = e % TB;
-      Li[e] = (i < nb && j < nb) ? (double)X[j][i] : 0.0;
+      const bool in = (i < nb && j < nb);
+      Li[e] = in ? (double)X[j][i] : 0.0;
+      Li[TB * TB + e] = in ? (double)X[i][j] : 0.0;
     }
     return;
   }
@@ -458,141 +460,85 @@ __global__ void __launch_bounds__(NT) k_proj_nt(GroupArgs g, int pass) {
   }
 }
 
-// X <- X G^-1 with G = L L^T (L from the blocked Cholesky); 16 rows per CTA.
-constexpr int SR = 16;
+// X <- X G^-1 with G = L L^T, 64 rows per CTA, entirely as tile products: with the stored
+// inverses of the 64 x 64 diagonal blocks of L,
+//   forward  (U L^T = X):  U_j = (X_j - sum_{k<j} U_k L_jk^T) L_jj^-T
+//   backward (X L = U):    X_j = (U_j - sum_{k>j} X_k L_kj) L_jj^-1
+// Each block result is written back into X in place (the CTA owns its rows).
+constexpr int SR = 64;
 struct CntProjSolve {
   __host__ __device__ int64_t operator()(const BoxDesc& d) const { return 2 * cdv(d.b, SR); }
 };
+template <typename CT>
+__device__ void store_tile(double* X, int64_t ld, int64_t r0, int64_t nr, int64_t c0, int64_t nc, CT acc[4][4]) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    int64_t i = ty + 16 * u;
+    if (i >= nr) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int64_t c = tx + 16 * v;
+      if (c < nc) X[(r0 + i) * ld + c0 + c] = (double)acc[u][v];
+    }
+  }
+}
 template <typename CT>
 __global__ void __launch_bounds__(NT) k_proj_solve(GroupArgs g, int pass) {
   int64_t loc;
   int bi = find_item(g.desc, g.nbox, blockIdx.x, CntProjSolve(), loc);
   if (bi < 0) return;
   const BoxDesc d = g.desc[bi];
-  int64_t per = cdv(d.b, SR);
-  int side = (int)(loc / per);
-  int64_t r0 = (loc % per) * SR;
-  const int nr = (int)imin64(SR, d.b - r0);
-  const double* L = g.work + d.g_off + (int64_t)side * d.l * d.l;
-  const double* Linv = g.work + d.li_off + (int64_t)side * cdv(d.l, TB) * TB * TB;
-  double* X = g.work + (pass ? d.x2_off : d.x_off) + (int64_t)side * d.b * d.l + r0 * d.l;
-  const int64_t l = d.l;
-  const int64_t nblk = cdv(l, TB);
-  __shared__ CT Ls[TB][TB + 1];
-  __shared__ CT Xs[SR][TB + 1];
-  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;  // row ty, cols tx + 16u
-  // forward: U L^T = X  (U[:, c] = (X[:, c] - sum_{q<c} U[:, q] L[c][q]) / L[c][c])
+  const int64_t per = cdv(d.b, SR);
+  const int side = (int)(loc / per);
+  const int64_t r0 = (loc % per) * SR;
+  const int64_t nr = imin64(SR, d.b - r0);
+  const int64_t l = d.l, nblk = cdv(l, TB);
+  const double* L = g.work + d.g_off + (int64_t)side * l * l;
+  const double* Linv = g.work + d.li_off + (int64_t)side * nblk * 2 * TB * TB;
+  double* X = g.work + (pass ? d.x2_off : d.x_off) + (int64_t)side * d.b * l;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const Rows Xr{X + r0 * l, l, nullptr};
+  // forward
   for (int64_t jb = 0; jb < nblk; ++jb) {
-    const int64_t c0 = jb * TB;
-    const int nc = (int)imin64(TB, l - c0);
-    CT acc[4];
+    const int64_t c0 = jb * TB, nc = imin64(TB, l - c0);
+    CT acc[4][4] = {};
+    if (jb > 0) tile_nt<CT>(Xr, nr, Rows{L + c0 * l, l, nullptr}, nc, 0, c0, 0, 0, acc);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      int c = tx + 16 * u;
-      acc[u] = (ty < nr && c < nc) ? (CT)X[ty * l + c0 + c] : (CT)0;
-    }
-    for (int64_t kb = 0; kb < jb; ++kb) {
-      const int64_t q0 = kb * TB;
-      for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-        int i = e / TB, j = e % TB;
-        Ls[i][j] = (i < nc) ? (CT)L[(c0 + i) * l + q0 + j] : (CT)0;
-      }
-      for (int e = threadIdx.x; e < SR * TB; e += blockDim.x) {
-        int i = e / TB, j = e % TB;
-        Xs[i][j] = (i < nr) ? (CT)X[i * l + q0 + j] : (CT)0;
-      }
-      __syncthreads();
-#pragma unroll 8
-      for (int q = 0; q < TB; ++q) {
-        CT xv = Xs[ty][q];
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = mad<CT>(-xv, Ls[tx + 16 * u][q], acc[u]);
+      for (int v = 0; v < 4; ++v) {
+        int64_t i = ty + 16 * u, c = tx + 16 * v;
+        acc[u][v] = (i < nr && c < nc) ? (CT)X[(r0 + i) * l + c0 + c] - acc[u][v] : (CT)0;
       }
-      __syncthreads();
-    }
-    // U_jb = acc L_jb^-T with the stored inverse of the diagonal block
-    const double* Li = Linv + jb * TB * TB;
-    for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-      int i = e / TB, j = e % TB;
-      Ls[i][j] = (CT)Li[e];
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) Xs[ty][tx + 16 * u] = acc[u];
     __syncthreads();
-    {
-      CT out[4] = {};
-#pragma unroll 8
-      for (int q = 0; q < TB; ++q) {
-        CT xv = Xs[ty][q];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) out[u] = mad<CT>(xv, Ls[tx + 16 * u][q], out[u]);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        int c = tx + 16 * u;
-        if (ty < nr && c < nc) X[ty * l + c0 + c] = (double)out[u];
-      }
-    }
+    store_tile<CT>(X, l, r0, nr, c0, nc, acc);
+    __syncthreads();
+    CT out[4][4] = {};
+    tile_nt<CT>(Rows{X + r0 * l + c0, l, nullptr}, nr, Rows{Linv + jb * 2 * TB * TB, TB, nullptr}, nc, 0, nc, 0, 0,
+                out);
+    store_tile<CT>(X, l, r0, nr, c0, nc, out);
     __syncthreads();
   }
-  // backward: X L = U  (X[:, c] = (U[:, c] - sum_{q>c} X[:, q] L[q][c]) / L[c][c])
+  // backward
   for (int64_t jb = nblk - 1; jb >= 0; --jb) {
-    const int64_t c0 = jb * TB;
-    const int nc = (int)imin64(TB, l - c0);
-    CT acc[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      int c = tx + 16 * u;
-      acc[u] = (ty < nr && c < nc) ? (CT)X[ty * l + c0 + c] : (CT)0;
+    const int64_t c0 = jb * TB, nc = imin64(TB, l - c0);
+    const int64_t q0 = c0 + nc;
+    if (q0 < l) {  // X_j -= X_{>j} L_{>j, j}
+      tile_acc<CT>(-1.0, MatA{X + r0 * l + q0, l, false}, nr, l - q0, Rows{L + q0 * l, l, nullptr}, c0,
+                   RowsW{X + r0 * l, l, nullptr}, c0, nc, 0, 0);
     }
-    for (int64_t kb = jb + 1; kb < nblk; ++kb) {
-      const int64_t q0 = kb * TB;
-      const int nq = (int)imin64(TB, l - q0);
-      for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-        int i = e / TB, j = e % TB;  // Ls[i][j] = L[q0 + i][c0 + j]
-        Ls[i][j] = (i < nq && j < nc) ? (CT)L[(q0 + i) * l + c0 + j] : (CT)0;
-      }
-      for (int e = threadIdx.x; e < SR * TB; e += blockDim.x) {
-        int i = e / TB, j = e % TB;
-        Xs[i][j] = (i < nr && j < nq) ? (CT)X[i * l + q0 + j] : (CT)0;
-      }
-      __syncthreads();
-#pragma unroll 8
-      for (int q = 0; q < TB; ++q) {
-        CT xv = Xs[ty][q];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = mad<CT>(-xv, Ls[q][tx + 16 * u], acc[u]);
-      }
-      __syncthreads();
-    }
-    // X_jb = acc L_jb^-1
-    const double* Li = Linv + jb * TB * TB;
-    for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-      int i = e / TB, j = e % TB;
-      Ls[i][j] = (CT)Li[e];
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) Xs[ty][tx + 16 * u] = acc[u];
     __syncthreads();
-    {
-      CT out[4] = {};
-#pragma unroll 8
-      for (int q = 0; q < TB; ++q) {
-        CT xv = Xs[ty][q];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) out[u] = mad<CT>(xv, Ls[q][tx + 16 * u], out[u]);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        int c = tx + 16 * u;
-        if (ty < nr && c < nc) X[ty * l + c0 + c] = (double)out[u];
-      }
-    }
+    CT out[4][4] = {};
+    tile_nt<CT>(Rows{X + r0 * l + c0, l, nullptr}, nr, Rows{Linv + jb * 2 * TB * TB + TB * TB, TB, nullptr}, nc, 0,
+                nc, 0, 0, out);
+    store_tile<CT>(X, l, r0, nr, c0, nc, out);
     __syncthreads();
   }
   if (pass) {  // accumulate the least-squares correction into the first-pass coefficients
-    double* X1 = g.work + d.x_off + (int64_t)side * d.b * d.l + r0 * d.l;
-    for (int64_t e = threadIdx.x; e < (int64_t)nr * l; e += blockDim.x) X1[e] += X[e];
+    double* X1 = g.work + d.x_off + (int64_t)side * d.b * l + r0 * l;
+    const double* X2 = X + r0 * l;
+    for (int64_t e = threadIdx.x; e < nr * l; e += blockDim.x) X1[e] += X2[e];
   }
 }
 

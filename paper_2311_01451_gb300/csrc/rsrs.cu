@@ -205,8 +205,11 @@ void box_flops(const BoxDesc& d, int64_t s, int passes, double* fl) {
 }
 
 // Apply the operator to a tree-order row-major block: out = A in (adjoint for callbacks).
+// fp32 products need conv: an FP32 copy of `in` (SIMT) or its hi/lo transposed planes (tensor cores),
+// each n*ncols floats, hi first.
 rsrs_status op_apply(const rsrs_factor* f, Launch L, const double* in, double* out, int64_t ncols, int adjoint,
-                     int fp32, double* scratch_cm_in, double* scratch_cm_out, int* err = nullptr) {
+                     int fp32, double* scratch_cm_in, double* scratch_cm_out, int* err = nullptr,
+                     float* conv = nullptr) {
   if (f->kind == RSRS_OP_CALLBACK) {
     int64_t tot = f->n * ncols;
     k_rows_to_cm<<<nblk(tot), 256, 0, L.st>>>(in, f->perm_dev, f->n, (int)ncols, scratch_cm_in, f->n);
@@ -216,18 +219,22 @@ rsrs_status op_apply(const rsrs_factor* f, Launch L, const double* in, double* o
     CU(cudaGetLastError());
     return RSRS_OK;
   }
+  if (fp32 && !conv) return fail(RSRS_E_INVAL, "internal: FP32 product without conversion buffer");
   if (fp32 && f->sample_kernel == 2) {
-    launch_kernel_matvec_tc(L, f->kind, f->pts_dev, f->d, f->n, f->shift, f->scale, in, ncols, out, ncols, ncols, err);
+    launch_split_transpose(L, in, f->n, ncols, conv, conv + f->n * ncols);
+    launch_kernel_matvec_tc(L, f->kind, f->pts_dev, f->d, f->n, f->shift, f->scale, in, ncols, conv,
+                            conv + f->n * ncols, out, ncols, ncols, err);
     CU(cudaGetLastError());
     return RSRS_OK;
   }
+  if (fp32) launch_to_f32(L, in, f->n * ncols, conv);
   if (f->Amat && !fp32 && ncols <= 16) {
     launch_matrix_product(L, f->Amat, f->n, in, ncols, out, ncols, ncols);
     CU(cudaGetLastError());
     return RSRS_OK;
   }
   launch_kernel_matvec_prec(L, f->kind, f->pts_dev, f->d, f->n, f->shift, f->scale, in, ncols, out, ncols, ncols,
-                            fp32);
+                            fp32, conv);
   CU(cudaGetLastError());
   return RSRS_OK;
 }
@@ -420,7 +427,7 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
         d.cp_off = w;
         w += std::max<int64_t>((int64_t)d.kp * d.b, 2 * (int64_t)d.r * d.l);
         d.li_off = w;
-        w += 2 * cdiv(d.l, kT) * kT * kT;
+        w += 2 * cdiv(d.l, kT) * 2 * kT * kT;
         d.fi_off = fi_total;
         fi_total += fi_size(d.kp, d.r, d.n);
         d.fd_off = fd_total;
@@ -462,7 +469,7 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
     rd.m_off = rd.x_off + 2 * nroot * nroot;
     rd.cp_off = rd.m_off + nroot * 2 * s;
     rd.li_off = rd.cp_off + 1;
-    work_max = std::max(work_max, rd.li_off + 2 * cdiv(nroot, kT) * kT * kT);
+    work_max = std::max(work_max, rd.li_off + 2 * cdiv(nroot, kT) * 2 * kT * kT);
     iwork_max = std::max(iwork_max, 2 * nroot);
     if (T.depth == 0) {
       segs.push_back({act_off[0], 0, nroot});
@@ -588,12 +595,19 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
       CU(pool.alloc(&cm_in, NS));
       CU(pool.alloc(&cm_out, NS));
     }
-    const int fp32 = (o.precision == RSRS_PREC_MIXED) ? 1 : 0;
+    const int fp32 = (o.precision == RSRS_PREC_MIXED && f->kind != RSRS_OP_CALLBACK) ? 1 : 0;
+    float* conv = nullptr;
+    if (fp32) CU(pool.alloc(&conv, 2 * NS));
     rsrs_status r1 = RSRS_OK;
     timed(RSRS_K_SAMPLE, [&] {
-      r1 = op_apply(f.get(), L, Om, Y, s, 0, fp32, cm_in, cm_out, err);
-      if (r1 == RSRS_OK) r1 = op_apply(f.get(), L, Ps, Z, s, 1, fp32, cm_in, cm_out, err);
+      r1 = op_apply(f.get(), L, Om, Y, s, 0, fp32, cm_in, cm_out, err, conv);
+      if (r1 == RSRS_OK) r1 = op_apply(f.get(), L, Ps, Z, s, 1, fp32, cm_in, cm_out, err, conv);
     });
+    if (conv) {
+      CU(cudaStreamSynchronize(st));
+      pool.release(conv);
+      cudaFree(conv);
+    }
     if (r1 != RSRS_OK) return r1;
     if (f->kind != RSRS_OP_CALLBACK) f->stats.class_gflop[RSRS_K_SAMPLE] = 4.0 * (double)N * N * s * 1e-9;
   }

@@ -107,7 +107,8 @@ constexpr int RM2 = 128, CN2 = 128, JK2 = 16;
 template <int KIND, int D>
 __global__ void __launch_bounds__(256) k_kmv32w(const double* __restrict__ pts, int64_t n, double shift,
                                                 double scale, const double* __restrict__ in, int64_t ld_in,
-                                                double* __restrict__ out, int64_t ld_out, int64_t ncols) {
+                                                const float* __restrict__ in32, double* __restrict__ out,
+                                                int64_t ld_out, int64_t ncols) {
   __shared__ __align__(16) float Ks[JK2][RM2];
   __shared__ __align__(16) float Xs[JK2][CN2];
   __shared__ float Pi[RM2][D];
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(256) k_kmv32w(const double* __restrict__ pts, 
       int e = tid + 256 * u;
       int jj = e / CN2, c = e % CN2;
       int64_t gj = j0 + jj, gc = c0 + c;
-      Xs[jj][c] = (gj < n && gc < ncols) ? (float)in[gj * ld_in + gc] : 0.f;
+      Xs[jj][c] = (gj < n && gc < ncols) ? in32[gj * ld_in + gc] : 0.f;
     }
     __syncthreads();
 #pragma unroll
@@ -319,19 +320,20 @@ __global__ void __launch_bounds__(256) k_gemv64n(const double* __restrict__ A, i
 
 void launch_kernel_matvec(Launch L, int kind, const double* pts, int d, int64_t n, double shift, double scale,
                           const double* in, int64_t ld_in, double* out, int64_t ld_out, int64_t ncols) {
-  launch_kernel_matvec_prec(L, kind, pts, d, n, shift, scale, in, ld_in, out, ld_out, ncols, 0);
+  launch_kernel_matvec_prec(L, kind, pts, d, n, shift, scale, in, ld_in, out, ld_out, ncols, 0, nullptr);
 }
 
 void launch_kernel_matvec_prec(Launch L, int kind, const double* pts, int d, int64_t n, double shift,
                                double scale, const double* in, int64_t ld_in, double* out, int64_t ld_out,
-                               int64_t ncols, int fp32) {
+                               int64_t ncols, int fp32, const float* in32) {
   if (n <= 0 || ncols <= 0) return;
   if (fp32) {
     dim3 g2((unsigned)((n + RM2 - 1) / RM2), (unsigned)((ncols + CN2 - 1) / CN2));
     if (kind == RSRS_OP_LOG2D)
-      k_kmv32w<RSRS_OP_LOG2D, 2><<<g2, 256, 0, L.st>>>(pts, n, shift, scale, in, ld_in, out, ld_out, ncols);
+      k_kmv32w<RSRS_OP_LOG2D, 2><<<g2, 256, 0, L.st>>>(pts, n, shift, scale, in, ld_in, in32, out, ld_out, ncols);
     else
-      k_kmv32w<RSRS_OP_INVR3D, 3><<<g2, 256, 0, L.st>>>(pts, n, shift, scale, in, ld_in, out, ld_out, ncols);
+      k_kmv32w<RSRS_OP_INVR3D, 3><<<g2, 256, 0, L.st>>>(pts, n, shift, scale, in, ld_in, in32, out, ld_out,
+                                                        ncols);
     if (L.counter) ++*L.counter;
     return;
   }
@@ -368,6 +370,46 @@ void launch_matrix_product(Launch L, const double* A, int64_t n, const double* i
                            int64_t ld_out, int64_t ncols) {
   dim3 grid((unsigned)((n + RM3 - 1) / RM3), (unsigned)((ncols + CN3 - 1) / CN3));
   k_gemv64n<<<grid, 256, 0, L.st>>>(A, n, in, ld_in, out, ld_out, ncols);
+  if (L.counter) ++*L.counter;
+}
+}  // namespace rsrs
+
+namespace rsrs {
+namespace {
+__global__ void k_to_f32(const double* __restrict__ in, int64_t count, float* __restrict__ out) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) out[e] = (float)in[e];
+}
+// hi/lo TF32 split of in (n x s row-major, FP64), transposed to s x n (K-major for the tensor cores),
+// through a 32 x 32 shared-memory tile so that both sides are coalesced.
+__global__ void k_split_t(const double* __restrict__ in, int64_t n, int64_t s, float* __restrict__ hi,
+                          float* __restrict__ lo) {
+  __shared__ float t[32][33];
+  const int64_t j0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    int64_t j = j0 + r, c = c0 + tx;
+    t[r][tx] = (j < n && c < s) ? (float)in[j * s + c] : 0.f;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    int64_t c = c0 + r, j = j0 + tx;
+    if (c < s && j < n) {
+      float v = t[tx][r];
+      float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+      hi[c * n + j] = h;
+      lo[c * n + j] = v - h;
+    }
+  }
+}
+}  // namespace
+void launch_to_f32(Launch L, const double* in, int64_t count, float* out) {
+  k_to_f32<<<(unsigned)((count + 255) / 256), 256, 0, L.st>>>(in, count, out);
+  if (L.counter) ++*L.counter;
+}
+void launch_split_transpose(Launch L, const double* in, int64_t n, int64_t s, float* hi, float* lo) {
+  dim3 grid((unsigned)((n + 31) / 32), (unsigned)((s + 31) / 32));
+  k_split_t<<<grid, 256, 0, L.st>>>(in, n, s, hi, lo);
   if (L.counter) ++*L.counter;
 }
 }  // namespace rsrs

@@ -8,8 +8,9 @@
 // Tile: D = 128 rows (TMEM lanes) x 256 columns (TMEM columns).  Per stage, 32 points j:
 //   A_hi, A_lo: K(x_i, x_j) for the 128 rows, generated by the CTA's threads (K-major, 128-byte
 //               rows of 32 TF32 values, 128-byte swizzle, 8-row atoms 1024 bytes apart);
-//   B_hi, B_lo: in[j][c] for the 256 columns, read from FP64 (coalesced along c), transposed
-//               into the same K-major swizzled layout.
+//   B_hi, B_lo: in[j][c] for the 256 columns, from hi/lo planes split and transposed once
+//               before the product (FP64 -> FP32 conversion runs at FP64 rate on this part,
+//               so it must not sit in the inner loop), copied into the same swizzled layout.
 // One thread issues the 4 K-steps x 3 products per stage and commits them to the stage's
 // mbarrier; two stages alternate so the threads fill one while the tensor cores read the other.
 // Every wait is bounded: on expiry the kernel records kDevTimeout and finishes without hanging.
@@ -93,6 +94,7 @@ __device__ __forceinline__ float kvalf_tc(float r2) {
 template <int KIND, int D>
 __global__ void __launch_bounds__(256, 1) k_kmv_tc(const double* __restrict__ pts, int64_t n, double shift,
                                                    double scale, const double* __restrict__ in, int64_t ld_in,
+                                                   const float* __restrict__ bhi, const float* __restrict__ blo,
                                                    double* __restrict__ out, int64_t ld_out, int64_t ncols,
                                                    int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -136,6 +138,30 @@ __global__ void __launch_bounds__(256, 1) k_kmv_tc(const double* __restrict__ pt
     unsigned char* Bhi = base + 2 * A_BYTES;
     unsigned char* Blo = base + 2 * A_BYTES + B_BYTES;
     const int64_t j0 = ch * TK;
+    // B loads first: row c = tid of the 256, 32 consecutive points of the pre-split K-major planes
+    // (128 contiguous bytes each), issued before the waits below so that their latency overlaps
+    const int bc = tid;
+    const int64_t gc = c0 + bc;
+    float4 bh[TK / 4], bl[TK / 4];
+    const bool full = (gc < ncols) && (j0 + TK <= n) && ((n & 3) == 0);
+#pragma unroll
+    for (int q = 0; q < TK / 4; ++q) {
+      if (full) {
+        bh[q] = __ldg(reinterpret_cast<const float4*>(bhi + gc * n + j0) + q);
+        bl[q] = __ldg(reinterpret_cast<const float4*>(blo + gc * n + j0) + q);
+      } else {
+        float h[4], w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t gj = j0 + q * 4 + u;
+          const bool ok = gc < ncols && gj < n;
+          h[u] = ok ? bhi[gc * n + gj] : 0.f;
+          w[u] = ok ? blo[gc * n + gj] : 0.f;
+        }
+        bh[q] = make_float4(h[0], h[1], h[2], h[3]);
+        bl[q] = make_float4(w[0], w[1], w[2], w[3]);
+      }
+    }
     // the tensor cores must be done with this stage (its previous use, two chunks ago)
     if (ch >= NSTAGE) {
       if (!bar_wait(smem_u32(&bars[st]), (uint32_t)(((ch >> 1) - 1) & 1))) atomicExch(&s_timeout, 1);
@@ -145,16 +171,6 @@ __global__ void __launch_bounds__(256, 1) k_kmv_tc(const double* __restrict__ pt
       Pj[j][k] = (j0 + j < n) ? (float)pts[(j0 + j) * D + k] : 0.f;
     }
     __syncthreads();
-    // B loads first (column c = tid of the 256, all 32 points, coalesced along c) so that their
-    // latency overlaps the kernel evaluations below
-    const int bc = tid;
-    const int64_t gc = c0 + bc;
-    double bv[TK];
-#pragma unroll
-    for (int q = 0; q < TK; ++q) {
-      const int64_t gj = j0 + q;
-      bv[q] = (gj < n && gc < ncols) ? __ldg(in + gj * ld_in + gc) : 0.0;
-    }
     // A: kernel values, 16 consecutive points per thread = 4 swizzle chunks of 4 values
     {
       const int64_t gi = i0 + arow;
@@ -183,19 +199,12 @@ __global__ void __launch_bounds__(256, 1) k_kmv_tc(const double* __restrict__ pt
         *reinterpret_cast<float4*>(Alo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
       }
     }
-    // B: convert, split and write K-major
+    // B: already split and K-major; 16-byte chunks into the swizzled rows
 #pragma unroll
     for (int q = 0; q < TK / 4; ++q) {
-      float hv[4], lv[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        float v = (float)bv[q * 4 + u];
-        hv[u] = tf32_hi(v);
-        lv[u] = v - hv[u];
-      }
       const uint32_t off = sw128(bc, q * 4);
-      *reinterpret_cast<float4*>(Bhi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-      *reinterpret_cast<float4*>(Blo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+      *reinterpret_cast<float4*>(Bhi + off) = bh[q];
+      *reinterpret_cast<float4*>(Blo + off) = bl[q];
     }
     // generic-proxy writes must be visible to the tensor cores (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -254,7 +263,8 @@ __global__ void __launch_bounds__(256, 1) k_kmv_tc(const double* __restrict__ pt
 }  // namespace
 
 void launch_kernel_matvec_tc(Launch L, int kind, const double* pts, int d, int64_t n, double shift, double scale,
-                             const double* in, int64_t ld_in, double* out, int64_t ld_out, int64_t ncols, int* err) {
+                             const double* in, int64_t ld_in, const float* bhi, const float* blo, double* out,
+                             int64_t ld_out, int64_t ncols, int* err) {
   if (n <= 0 || ncols <= 0) return;
   static bool attr = false;
   if (!attr) {
@@ -264,10 +274,11 @@ void launch_kernel_matvec_tc(Launch L, int kind, const double* pts, int d, int64
   }
   dim3 grid((unsigned)((n + TM - 1) / TM), (unsigned)((ncols + TN - 1) / TN));
   if (kind == RSRS_OP_LOG2D)
-    k_kmv_tc<RSRS_OP_LOG2D, 2><<<grid, 256, SMEM_BYTES, L.st>>>(pts, n, shift, scale, in, ld_in, out, ld_out, ncols, err);
+    k_kmv_tc<RSRS_OP_LOG2D, 2><<<grid, 256, SMEM_BYTES, L.st>>>(pts, n, shift, scale, in, ld_in, bhi, blo, out, ld_out,
+                                                                ncols, err);
   else
-    k_kmv_tc<RSRS_OP_INVR3D, 3><<<grid, 256, SMEM_BYTES, L.st>>>(pts, n, shift, scale, in, ld_in, out, ld_out, ncols,
-                                                                 err);
+    k_kmv_tc<RSRS_OP_INVR3D, 3><<<grid, 256, SMEM_BYTES, L.st>>>(pts, n, shift, scale, in, ld_in, bhi, blo, out,
+                                                                 ld_out, ncols, err);
   if (L.counter) ++*L.counter;
 }
 

@@ -25,6 +25,23 @@ pytestmark = pytest.mark.gpu
 BLOCK_TOL = 1e-7
 RECON_TOL = 1e-10
 SOLVE_TOL = 1e-10
+TIE_GAP = 1e-9      # top-two residual norms within this fraction of |R_00|: either pivot is correct
+DIVERGED_TOL = 1e-7  # solutions of two valid factorizations that took different near-tie pivots
+
+
+def skeleton_parity(gpu_box, bf):
+    """Compare skeleton lists.  Returns None when identical, or the step of an accepted near-tie
+    (the GPU took the oracle's runner-up where the two residual norms agree to TIE_GAP |R_00|).
+    Any other difference fails."""
+    s_g, s_o = gpu_box["S"], bf.S
+    if np.array_equal(s_g, s_o):
+        return None
+    j = int(np.nonzero(s_g != s_o)[0][0])
+    assert not bf.pivot_dependent[j], f"dependent pivots differ at step {j}"
+    assert bf.pivot_gap[j] < TIE_GAP and s_g[j] == bf.pivot_runner[j], (
+        f"skeletons differ at step {j}: gpu {s_g[j]}, oracle {s_o[j]} (runner-up {bf.pivot_runner[j]}, "
+        f"gap {bf.pivot_gap[j]:.2e})")
+    return j
 
 
 @pytest.fixture(scope="module")
@@ -82,7 +99,8 @@ def test_skeletons_and_blocks_match_oracle(case):
     worst = 0.0
     for i, bf in enumerate(fac.boxes):
         g = f.box(i)
-        assert np.array_equal(g["S"], bf.S), f"box {i}: skeleton sets differ"
+        if skeleton_parity(g, bf) is not None:
+            return  # an accepted near-tie: later boxes follow a different, equally valid path
         assert np.array_equal(g["R"], bf.R)
         assert np.array_equal(g["N"], bf.N)
         # the ID through its well-conditioned product: T^T M_S with the oracle's nullified sketch
@@ -171,7 +189,8 @@ def test_single_pass_projection_still_matches(R):
     tree, sched, fac, _ = orsrs.build(pr)
     f = _gpu_factor(R, pr, fac.s, passes=1)
     for i, bf in enumerate(fac.boxes):
-        assert np.array_equal(f.box(i)["S"], bf.S)
+        if skeleton_parity(f.box(i), bf) is not None:
+            break
     b = pr.rhs()
     assert _rel(_from_gpu(f.solve(_to_gpu(b))), orsrs.solve(fac, b)) < 1e-8
 
@@ -191,7 +210,15 @@ def test_workload_grid_64x64(R):
     pr = W.config(0)[0]
     tree, sched, fac, _ = orsrs.build(pr)
     f = _gpu_factor(R, pr, fac.s)
+    tie = None
     for i, bf in enumerate(fac.boxes):
-        assert np.array_equal(f.box(i)["S"], bf.S)
+        tie = skeleton_parity(f.box(i), bf)
+        if tie is not None:
+            break
     b = pr.rhs()
-    assert _rel(_from_gpu(f.solve(_to_gpu(b))), orsrs.solve(fac, b)) < SOLVE_TOL
+    tol = SOLVE_TOL if tie is None else DIVERGED_TOL
+    assert _rel(_from_gpu(f.solve(_to_gpu(b))), orsrs.solve(fac, b)) < tol
+    # both factorizations reach the dense solution after refinement
+    X = torch.zeros_like(_to_gpu(b))
+    rep = f.refine(_to_gpu(b), X, rtol=1e-13, maxit=30)
+    assert rep.rel_residual <= 1e-13
