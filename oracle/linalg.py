@@ -70,6 +70,9 @@ def cpqr_id(m: np.ndarray, k: int, tau: float, record: dict | None = None):
             record.setdefault("gap", []).append((best - second) / ref if ref else 0.0)
             record.setdefault("runner", []).append(int(perm[j + order[1]]) if len(order) > 1 else -1)
             record.setdefault("dependent", []).append(bool(j0 <= j))
+            shortfall = np.full(b, np.inf)  # (best - norm) / |R_00| of every remaining row
+            shortfall[perm[j:]] = (best - norms) / ref if ref else 0.0
+            record.setdefault("shortfall", []).append(shortfall)
         if p != j:
             a[:, [j, p]] = a[:, [p, j]]
             perm[[j, p]] = perm[[p, j]]

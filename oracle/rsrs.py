@@ -72,6 +72,7 @@ class BoxFactor:
     pivot_gap: np.ndarray = None  # per CPQR step: (largest - second residual norm) / |R_00|
     pivot_runner: np.ndarray = None  # per CPQR step: the runner-up point
     pivot_dependent: np.ndarray = None  # per CPQR step: taken by the dependent-pivot rule
+    pivot_shortfall: np.ndarray = None  # per CPQR step and box point: (largest - its residual) / |R_00|
 
 
 @dataclass
@@ -155,7 +156,8 @@ def factor(tree: Tree, sched: Schedule, Y, Z, Om, Ps, trace=None, max_steps: int
                            pivot_gap=np.array(rec.get("gap", [])),
                            pivot_runner=Bact[np.array(rec.get("runner", []), dtype=np.int64)]
                            if rec.get("runner") else np.zeros(0, dtype=np.int64),
-                           pivot_dependent=np.array(rec.get("dependent", []), dtype=bool))
+                           pivot_dependent=np.array(rec.get("dependent", []), dtype=bool),
+                           pivot_shortfall=np.array(rec.get("shortfall", [])))
             fac.boxes.append(bf)
             if trace is not None:
                 trace.append(dict(box=bf, Yp=Yp, Zp=Zp))
