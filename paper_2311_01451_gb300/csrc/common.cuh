@@ -16,15 +16,20 @@ enum DevErr : int { kDevOk = 0, kDevSingular = 1, kDevNonfinite = 2, kDevTimeout
 
 // One compressed box of a (level, colour) group, as the device kernels see it.
 // All offsets are element offsets into the buffers named in the comments.
+// Workspaces: `work` is FP64 (the CPQR input and R rows); `workc` holds the blocks of the
+// compute type (FP32 in the mixed path, FP64 otherwise); offsets count elements of each type.
 struct BoxDesc {
   int32_t b, n, l, kp, r, pad_;
   int64_t bn_off;   // int32 work: l tree positions [B_act | N_act]
-  int64_t g_off;    // double work: two l x l Grams (Omega side, then Psi side)
-  int64_t x_off;    // double work: two b x l least-squares coefficient blocks (Y, Z)
-  int64_t x2_off;   // double work: two b x l second-pass blocks
-  int64_t m_off;    // double work: b x 2s projected sketches [Y' | Z']
-  int64_t cp_off;   // double work: CPQR R rows, kp x b; then extraction blocks 2 x r x l
-  int64_t li_off;   // double work: inverses (and their transposes) of the 64 x 64 diagonal Cholesky
+  int64_t g_off;    // workc: two l x l Grams / Cholesky factors (Omega side, then Psi side)
+  int64_t x_off;    // workc: two b x l least-squares coefficient blocks (Y, Z)
+  int64_t x2_off;   // workc: two b x l correction-pass blocks
+  int64_t mc_off;   // workc: b x 2s sketches [Y_B | Z_B], projected in place
+  int64_t w_off;    // workc: near-field test rows W = Om[B u N], then V = Ps[B u N], l x s each
+  int64_t e_off;    // workc: extraction blocks, 2 x r x l
+  int64_t m_off;    // work (FP64): b x 2s projected sketches for the CPQR
+  int64_t cp_off;   // work (FP64): CPQR R rows, kp x b
+  int64_t li_off;   // workc: inverses (and their transposes) of the 64 x 64 diagonal Cholesky
                     //   blocks, 2 sides x nblk x 2 x 64 x 64
   int64_t pv_off;   // int32 work: b CPQR local permutation, then the first dependent step
   int64_t fi_off;   // int32 factor: R (r), S (kp), N (n), LU pivots (r)
@@ -102,6 +107,7 @@ struct GroupArgs {
   double* Om;
   double* Ps;
   double* work;
+  void* workc;
   int32_t* iwork;
   double* fd;
   int32_t* fi;
@@ -114,7 +120,8 @@ void launch_gram(Launch L, const GroupArgs& g, int64_t items);                  
 void launch_chol_panel(Launch L, const GroupArgs& g, int panel);                   // diag block
 void launch_chol_trsm(Launch L, const GroupArgs& g, int panel, int64_t items);     // below-diag panel
 void launch_chol_update(Launch L, const GroupArgs& g, int panel, int64_t items);   // trailing update
-void launch_gather_box(Launch L, const GroupArgs& g, int64_t items);               // M = [Y_B | Z_B]
+void launch_gather_box(Launch L, const GroupArgs& g, int64_t items);               // M, W, V rows
+void launch_m_finalize(Launch L, const GroupArgs& g, int64_t items);               // FP64 M for the CPQR
 void launch_proj_nt(Launch L, const GroupArgs& g, int pass, int64_t items);        // X = M W^T
 void launch_proj_solve(Launch L, const GroupArgs& g, int pass, int64_t items);     // X <- X G^-1
 void launch_proj_acc(Launch L, const GroupArgs& g, int pass, int64_t items);       // M -= X W
@@ -153,6 +160,7 @@ int64_t items_gram(const std::vector<BoxDesc>& h);
 int64_t items_chol_trsm(const std::vector<BoxDesc>& h, int p);
 int64_t items_chol_update(const std::vector<BoxDesc>& h, int p);
 int64_t items_gather(const std::vector<BoxDesc>& h);
+int64_t items_finalize(const std::vector<BoxDesc>& h);
 int64_t items_proj_nt(const std::vector<BoxDesc>& h);
 int64_t items_proj_solve(const std::vector<BoxDesc>& h);
 int64_t items_proj_acc(const std::vector<BoxDesc>& h, int64_t s);

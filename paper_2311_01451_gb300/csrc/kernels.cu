@@ -22,6 +22,7 @@ namespace rsrs {
 namespace {
 
 constexpr int TB = 64;   // output tile edge
+constexpr int TB_ = TB;
 constexpr int KC = 16;   // K slice
 constexpr int NT = 256;  // threads per tiled CTA (16 x 16), 4 x 4 outputs each
 
@@ -72,32 +73,36 @@ __device__ inline void set_err(int* err, int code) {
   if (err) atomicCAS(err, 0, code);
 }
 
-// Row source: row i of a row-major matrix, through an optional int32 index list.
-struct Rows {
-  const double* base;
+// Row source: row i of a row-major matrix of T, through an optional int32 index list.
+template <typename T>
+struct RowsT {
+  const T* base;
   int64_t ld;
   const int32_t* idx;  // may be null: row i -> base + i*ld
-  __device__ const double* row(int64_t i) const { return base + (idx ? (int64_t)idx[i] : i) * ld; }
+  __device__ const T* row(int64_t i) const { return base + (idx ? (int64_t)idx[i] : i) * ld; }
 };
-struct RowsW {
-  double* base;
+template <typename T>
+struct RowsWT {
+  T* base;
   int64_t ld;
   const int32_t* idx;
-  __device__ double* row(int64_t i) const { return base + (idx ? (int64_t)idx[i] : i) * ld; }
+  __device__ T* row(int64_t i) const { return base + (idx ? (int64_t)idx[i] : i) * ld; }
 };
+using Rows = RowsT<double>;
+using RowsW = RowsWT<double>;
 
 // C tile (64 x 64) = sum_t A[i][t] B[j][t] over t < K, rows gathered.  acc: 4 x 4 per thread,
-// rows ty + 16a, cols tx + 16c (a, c < 4).
-template <typename CT>
-__device__ void tile_nt(Rows A, int64_t ma, Rows B, int64_t mb, int64_t koff, int64_t K, int64_t i0,
+// rows ty + 16a, cols tx + 16c (a, c < 4).  Operands are read in their storage type and used in CT.
+template <typename CT, typename TA, typename TB>
+__device__ void tile_nt(RowsT<TA> A, int64_t ma, RowsT<TB> B, int64_t mb, int64_t koff, int64_t K, int64_t i0,
                         int64_t j0, CT acc[4][4]) {
-  __shared__ CT As[KC][TB + 1];
-  __shared__ CT Bs[KC][TB + 1];
+  __shared__ CT As[KC][TB_ + 1];
+  __shared__ CT Bs[KC][TB_ + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int lr = tid >> 2, lk = (tid & 3) * 4;
-  const double* arow = (i0 + lr < ma) ? A.row(i0 + lr) + koff : nullptr;
-  const double* brow = (j0 + lr < mb) ? B.row(j0 + lr) + koff : nullptr;
+  const TA* arow = (i0 + lr < ma) ? A.row(i0 + lr) + koff : nullptr;
+  const TB* brow = (j0 + lr < mb) ? B.row(j0 + lr) + koff : nullptr;
   for (int64_t k0 = 0; k0 < K; k0 += KC) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -124,20 +129,22 @@ __device__ void tile_nt(Rows A, int64_t ma, Rows B, int64_t mb, int64_t koff, in
 }
 
 // A operand of C += alpha A B: element (i, q) of an m x K matrix, row-major or transposed storage.
-struct MatA {
-  const double* p;
+template <typename T>
+struct MatAT {
+  const T* p;
   int64_t lda;
   bool trans;
-  __device__ double at(int64_t i, int64_t q) const { return trans ? p[q * lda + i] : p[i * lda + q]; }
+  __device__ T at(int64_t i, int64_t q) const { return trans ? p[q * lda + i] : p[i * lda + q]; }
 };
+using MatA = MatAT<double>;
 
 // C[crow(i)][coff + t] += alpha * sum_q A(i,q) B[brow(q)][t] for the 64 x 64 tile (i0, t0);
 // t ranges over ncols, q over K.
-template <typename CT>
-__device__ void tile_acc(double alpha, MatA A, int64_t m, int64_t K, Rows B, int64_t boff, RowsW C,
-                         int64_t coff, int64_t ncols, int64_t i0, int64_t t0) {
-  __shared__ CT As[KC][TB + 1];
-  __shared__ CT Bs[KC][TB + 1];
+template <typename CT, typename TA, typename TB, typename TC>
+__device__ void tile_acc(double alpha, MatAT<TA> A, int64_t m, int64_t K, RowsT<TB> B, int64_t boff,
+                         RowsWT<TC> C, int64_t coff, int64_t ncols, int64_t i0, int64_t t0) {
+  __shared__ CT As[KC][TB_ + 1];
+  __shared__ CT Bs[KC][TB_ + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   CT acc[4][4] = {};
@@ -162,7 +169,7 @@ __device__ void tile_acc(double alpha, MatA A, int64_t m, int64_t K, Rows B, int
     {
       int lq = tid >> 4, lt = (tid & 15) * 4;
       int64_t q = q0 + lq;
-      const double* brow = (q < K) ? B.row(q) + boff : nullptr;
+      const TB* brow = (q < K) ? B.row(q) + boff : nullptr;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         int64_t t = t0 + lt + u;
@@ -189,11 +196,16 @@ __device__ void tile_acc(double alpha, MatA A, int64_t m, int64_t K, Rows B, int
   for (int u = 0; u < 4; ++u) {
     int64_t i = i0 + ty + 16 * u;
     if (i >= m) continue;
-    double* crow = C.row(i) + coff;
+    TC* crow = C.row(i) + coff;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       int64_t t = t0 + tx + 16 * v;
-      if (t < ncols) crow[t] += alpha * (double)acc[u][v];
+      if (t < ncols) {
+        if constexpr (sizeof(TC) == 4)
+          crow[t] = crow[t] + (TC)alpha * (TC)acc[u][v];
+        else
+          crow[t] = crow[t] + alpha * (double)acc[u][v];
+      }
     }
   }
 }
@@ -229,11 +241,11 @@ __global__ void __launch_bounds__(NT) k_gram(GroupArgs g) {
   int side = (int)(loc / per);
   int64_t ti, tj;
   tri_decode(loc % per, ti, tj);
-  const int32_t* bn = g.iwork + d.bn_off;
-  Rows W{side ? g.Ps : g.Om, g.s, bn};
+  CT* wc = reinterpret_cast<CT*>(g.workc);
+  RowsT<CT> W{wc + d.w_off + (int64_t)side * d.l * g.s, g.s, nullptr};
   CT acc[4][4] = {};
   tile_nt<CT>(W, d.l, W, d.l, 0, g.s, ti * TB, tj * TB, acc);
-  double* G = g.work + d.g_off + (int64_t)side * d.l * d.l;
+  CT* G = wc + d.g_off + (int64_t)side * d.l * d.l;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -259,7 +271,7 @@ __global__ void __launch_bounds__(NT) k_chol_panel(GroupArgs g, int p) {
   if (bi < 0) return;
   const BoxDesc d = g.desc[bi];
   const int side = (int)loc;
-  double* G = g.work + d.g_off + (int64_t)side * d.l * d.l;
+  CT* G = reinterpret_cast<CT*>(g.workc) + d.g_off + (int64_t)side * d.l * d.l;
   const int64_t o = (int64_t)p * TB;
   const int nb = (int)imin64(TB, d.l - o);
   __shared__ CT S[TB][TB + 1];
@@ -267,7 +279,7 @@ __global__ void __launch_bounds__(NT) k_chol_panel(GroupArgs g, int p) {
   if (threadIdx.x == 0) s_bad = 0;
   for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
     int i = e / nb, j = e % nb;
-    S[i][j] = (CT)G[(o + i) * d.l + o + j];
+    S[i][j] = G[(o + i) * d.l + o + j];
   }
   __syncthreads();
   for (int c = 0; c < nb; ++c) {
@@ -294,7 +306,7 @@ __global__ void __launch_bounds__(NT) k_chol_panel(GroupArgs g, int p) {
   if (threadIdx.x == 0 && s_bad) set_err(g.err, kDevNonfinite);
   for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
     int i = e / nb, j = e % nb;
-    G[(o + i) * d.l + o + j] = (j <= i) ? (double)S[i][j] : 0.0;
+    G[(o + i) * d.l + o + j] = (j <= i) ? S[i][j] : (CT)0;
   }
 }
 
@@ -320,7 +332,7 @@ __global__ void __launch_bounds__(NT) k_chol_trsm(GroupArgs g, int p) {
   int side = (int)(loc / per);
   int64_t ti = loc % per;
   const bool inv = (ti == per - 1);  // the identity tile
-  double* G = g.work + d.g_off + (int64_t)side * d.l * d.l;
+  CT* G = reinterpret_cast<CT*>(g.workc) + d.g_off + (int64_t)side * d.l * d.l;
   const int64_t o = (int64_t)p * TB;
   const int nb = (int)imin64(TB, d.l - o);
   const int64_t r0 = (int64_t)(p + 1) * TB + ti * TB;
@@ -331,11 +343,11 @@ __global__ void __launch_bounds__(NT) k_chol_trsm(GroupArgs g, int p) {
   CT(*X)[TB + 1] = reinterpret_cast<CT(*)[TB + 1]>(trsm_sm + TB * (TB + 1));
   for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
     int i = e / TB, j = e % TB;
-    Lp[i][j] = (i < nb && j < nb) ? (CT)G[(o + i) * d.l + o + j] : (CT)0;
+    Lp[i][j] = (i < nb && j < nb) ? G[(o + i) * d.l + o + j] : (CT)0;
     if (inv)
       X[i][j] = (i == j && i < nb) ? (CT)1 : (CT)0;
     else
-      X[i][j] = (i < nr && j < nb) ? (CT)G[(r0 + i) * d.l + o + j] : (CT)0;
+      X[i][j] = (i < nr && j < nb) ? G[(r0 + i) * d.l + o + j] : (CT)0;
   }
   __syncthreads();
   // x L^T = g, column by column; threads over the rows of the tile (4 threads per row, 16 cols each)
@@ -349,18 +361,18 @@ __global__ void __launch_bounds__(NT) k_chol_trsm(GroupArgs g, int p) {
     __syncthreads();
   }
   if (inv) {  // X = L_pp^-T; store L_pp^-1 and L_pp^-T (zero padded to 64 x 64)
-    double* Li = g.work + d.li_off + ((int64_t)side * cdv(d.l, TB) + p) * 2 * TB * TB;
+    CT* Li = reinterpret_cast<CT*>(g.workc) + d.li_off + ((int64_t)side * cdv(d.l, TB) + p) * 2 * TB * TB;
     for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
       int i = e / TB, j = e % TB;
       const bool in = (i < nb && j < nb);
-      Li[e] = in ? (double)X[j][i] : 0.0;
-      Li[TB * TB + e] = in ? (double)X[i][j] : 0.0;
+      Li[e] = in ? X[j][i] : (CT)0;
+      Li[TB * TB + e] = in ? X[i][j] : (CT)0;
     }
     return;
   }
   for (int e = threadIdx.x; e < nr * nb; e += blockDim.x) {
     int i = e / nb, j = e % nb;
-    G[(r0 + i) * d.l + o + j] = (double)X[i][j];
+    G[(r0 + i) * d.l + o + j] = X[i][j];
   }
 }
 
@@ -385,10 +397,10 @@ __global__ void __launch_bounds__(NT) k_chol_update(GroupArgs g, int p) {
   tri_decode(loc % per, ti, tj);
   ti += p + 1;
   tj += p + 1;
-  double* G = g.work + d.g_off + (int64_t)side * d.l * d.l;
+  CT* G = reinterpret_cast<CT*>(g.workc) + d.g_off + (int64_t)side * d.l * d.l;
   const int64_t o = (int64_t)p * TB;
   const int64_t nb = imin64(TB, d.l - o);
-  Rows L{G, d.l, nullptr};
+  RowsT<CT> L{G, d.l, nullptr};
   CT acc[4][4] = {};
   tile_nt<CT>(L, d.l, L, d.l, o, nb, ti * TB, tj * TB, acc);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -404,26 +416,64 @@ __global__ void __launch_bounds__(NT) k_chol_update(GroupArgs g, int p) {
   }
 }
 
-// M = [Y_B | Z_B]: b rows, 4 rows per CTA.
+// Gather the box's rows once, in the compute type: M = [Y_B | Z_B] (b x 2s) and the near-field
+// test rows W = Om[B u N], V = Ps[B u N] (l x s each); 4 rows per CTA, M rows first.
 struct CntGather {
-  __host__ __device__ int64_t operator()(const BoxDesc& d) const { return cdv(d.b, 4); }
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const { return cdv(d.b, 4) + cdv(d.l, 4); }
 };
+template <typename CT>
 __global__ void k_gather_box(GroupArgs g) {
   int64_t loc;
   int bi = find_item(g.desc, g.nbox, blockIdx.x, CntGather(), loc);
   if (bi < 0) return;
   const BoxDesc d = g.desc[bi];
   const int32_t* bn = g.iwork + d.bn_off;
+  CT* wc = reinterpret_cast<CT*>(g.workc);
+  const int64_t mb = cdv(d.b, 4);
+  if (loc < mb) {
+    for (int rr = 0; rr < 4; ++rr) {
+      int64_t i = loc * 4 + rr;
+      if (i >= d.b) break;
+      const double* y = g.Y + (int64_t)bn[i] * g.s;
+      const double* z = g.Z + (int64_t)bn[i] * g.s;
+      CT* m = wc + d.mc_off + i * 2 * g.s;
+      for (int64_t c = threadIdx.x; c < g.s; c += blockDim.x) {
+        m[c] = (CT)y[c];
+        m[g.s + c] = (CT)z[c];
+      }
+    }
+  } else {
+    for (int rr = 0; rr < 4; ++rr) {
+      int64_t i = (loc - mb) * 4 + rr;
+      if (i >= d.l) break;
+      const double* w = g.Om + (int64_t)bn[i] * g.s;
+      const double* v = g.Ps + (int64_t)bn[i] * g.s;
+      CT* W = wc + d.w_off + i * g.s;
+      CT* V = wc + d.w_off + ((int64_t)d.l + i) * g.s;
+      for (int64_t c = threadIdx.x; c < g.s; c += blockDim.x) {
+        W[c] = (CT)w[c];
+        V[c] = (CT)v[c];
+      }
+    }
+  }
+}
+
+// M (FP64, for the CPQR) = the projected sketches from the compute-type workspace.
+struct CntFinal {
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const { return cdv(d.b, 4); }
+};
+template <typename CT>
+__global__ void k_m_finalize(GroupArgs g) {
+  int64_t loc;
+  int bi = find_item(g.desc, g.nbox, blockIdx.x, CntFinal(), loc);
+  if (bi < 0) return;
+  const BoxDesc d = g.desc[bi];
+  const CT* mc = reinterpret_cast<const CT*>(g.workc) + d.mc_off;
   for (int rr = 0; rr < 4; ++rr) {
     int64_t i = loc * 4 + rr;
     if (i >= d.b) break;
-    const double* y = g.Y + (int64_t)bn[i] * g.s;
-    const double* z = g.Z + (int64_t)bn[i] * g.s;
-    double* m = g.work + d.m_off + i * 2 * g.s;
-    for (int64_t c = threadIdx.x; c < g.s; c += blockDim.x) {
-      m[c] = y[c];
-      m[g.s + c] = z[c];
-    }
+    for (int64_t c = threadIdx.x; c < 2 * g.s; c += blockDim.x)
+      g.work[d.m_off + i * 2 * g.s + c] = (double)mc[i * 2 * g.s + c];
   }
 }
 
@@ -441,12 +491,12 @@ __global__ void __launch_bounds__(NT) k_proj_nt(GroupArgs g, int pass) {
   int side = (int)(loc / per);
   int64_t rem = loc % per;
   int64_t ti = rem / cdv(d.l, TB), tj = rem % cdv(d.l, TB);
-  const int32_t* bn = g.iwork + d.bn_off;
-  Rows M{g.work + d.m_off + (int64_t)side * g.s, 2 * g.s, nullptr};
-  Rows W{side ? g.Ps : g.Om, g.s, bn};
+  CT* wc = reinterpret_cast<CT*>(g.workc);
+  RowsT<CT> M{wc + d.mc_off + (int64_t)side * g.s, 2 * g.s, nullptr};
+  RowsT<CT> W{wc + d.w_off + (int64_t)side * d.l * g.s, g.s, nullptr};
   CT acc[4][4] = {};
   tile_nt<CT>(M, d.b, W, d.l, 0, g.s, ti * TB, tj * TB, acc);
-  double* X = g.work + (pass ? d.x2_off : d.x_off) + (int64_t)side * d.b * d.l;
+  CT* X = wc + (pass ? d.x2_off : d.x_off) + (int64_t)side * d.b * d.l;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -470,7 +520,7 @@ struct CntProjSolve {
   __host__ __device__ int64_t operator()(const BoxDesc& d) const { return 2 * cdv(d.b, SR); }
 };
 template <typename CT>
-__device__ void store_tile(double* X, int64_t ld, int64_t r0, int64_t nr, int64_t c0, int64_t nc, CT acc[4][4]) {
+__device__ void store_tile(CT* X, int64_t ld, int64_t r0, int64_t nr, int64_t c0, int64_t nc, CT acc[4][4]) {
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -479,7 +529,7 @@ __device__ void store_tile(double* X, int64_t ld, int64_t r0, int64_t nr, int64_
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       int64_t c = tx + 16 * v;
-      if (c < nc) X[(r0 + i) * ld + c0 + c] = (double)acc[u][v];
+      if (c < nc) X[(r0 + i) * ld + c0 + c] = acc[u][v];
     }
   }
 }
@@ -494,29 +544,30 @@ __global__ void __launch_bounds__(NT) k_proj_solve(GroupArgs g, int pass) {
   const int64_t r0 = (loc % per) * SR;
   const int64_t nr = imin64(SR, d.b - r0);
   const int64_t l = d.l, nblk = cdv(l, TB);
-  const double* L = g.work + d.g_off + (int64_t)side * l * l;
-  const double* Linv = g.work + d.li_off + (int64_t)side * nblk * 2 * TB * TB;
-  double* X = g.work + (pass ? d.x2_off : d.x_off) + (int64_t)side * d.b * l;
+  CT* wc = reinterpret_cast<CT*>(g.workc);
+  const CT* L = wc + d.g_off + (int64_t)side * l * l;
+  const CT* Linv = wc + d.li_off + (int64_t)side * nblk * 2 * TB * TB;
+  CT* X = wc + (pass ? d.x2_off : d.x_off) + (int64_t)side * d.b * l;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const Rows Xr{X + r0 * l, l, nullptr};
+  const RowsT<CT> Xr{X + r0 * l, l, nullptr};
   // forward
   for (int64_t jb = 0; jb < nblk; ++jb) {
     const int64_t c0 = jb * TB, nc = imin64(TB, l - c0);
     CT acc[4][4] = {};
-    if (jb > 0) tile_nt<CT>(Xr, nr, Rows{L + c0 * l, l, nullptr}, nc, 0, c0, 0, 0, acc);
+    if (jb > 0) tile_nt<CT>(Xr, nr, RowsT<CT>{L + c0 * l, l, nullptr}, nc, 0, c0, 0, 0, acc);
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         int64_t i = ty + 16 * u, c = tx + 16 * v;
-        acc[u][v] = (i < nr && c < nc) ? (CT)X[(r0 + i) * l + c0 + c] - acc[u][v] : (CT)0;
+        acc[u][v] = (i < nr && c < nc) ? X[(r0 + i) * l + c0 + c] - acc[u][v] : (CT)0;
       }
     __syncthreads();
     store_tile<CT>(X, l, r0, nr, c0, nc, acc);
     __syncthreads();
     CT out[4][4] = {};
-    tile_nt<CT>(Rows{X + r0 * l + c0, l, nullptr}, nr, Rows{Linv + jb * 2 * TB * TB, TB, nullptr}, nc, 0, nc, 0, 0,
-                out);
+    tile_nt<CT>(RowsT<CT>{X + r0 * l + c0, l, nullptr}, nr, RowsT<CT>{Linv + jb * 2 * TB * TB, TB, nullptr}, nc, 0,
+                nc, 0, 0, out);
     store_tile<CT>(X, l, r0, nr, c0, nc, out);
     __syncthreads();
   }
@@ -525,19 +576,20 @@ __global__ void __launch_bounds__(NT) k_proj_solve(GroupArgs g, int pass) {
     const int64_t c0 = jb * TB, nc = imin64(TB, l - c0);
     const int64_t q0 = c0 + nc;
     if (q0 < l) {  // X_j -= X_{>j} L_{>j, j}
-      tile_acc<CT>(-1.0, MatA{X + r0 * l + q0, l, false}, nr, l - q0, Rows{L + q0 * l, l, nullptr}, c0,
-                   RowsW{X + r0 * l, l, nullptr}, c0, nc, 0, 0);
+      tile_acc<CT>(-1.0, MatAT<CT>{X + r0 * l + q0, l, false}, nr, l - q0, RowsT<CT>{L + q0 * l, l, nullptr}, c0,
+                   RowsWT<CT>{X + r0 * l, l, nullptr}, c0, nc, 0, 0);
     }
     __syncthreads();
     CT out[4][4] = {};
-    tile_nt<CT>(Rows{X + r0 * l + c0, l, nullptr}, nr, Rows{Linv + jb * 2 * TB * TB + TB * TB, TB, nullptr}, nc, 0,
+    tile_nt<CT>(RowsT<CT>{X + r0 * l + c0, l, nullptr}, nr, RowsT<CT>{Linv + jb * 2 * TB * TB + TB * TB, TB, nullptr},
+                nc, 0,
                 nc, 0, 0, out);
     store_tile<CT>(X, l, r0, nr, c0, nc, out);
     __syncthreads();
   }
   if (pass) {  // accumulate the least-squares correction into the first-pass coefficients
-    double* X1 = g.work + d.x_off + (int64_t)side * d.b * l + r0 * l;
-    const double* X2 = X + r0 * l;
+    CT* X1 = wc + d.x_off + (int64_t)side * d.b * l + r0 * l;
+    const CT* X2 = X + r0 * l;
     for (int64_t e = threadIdx.x; e < nr * l; e += blockDim.x) X1[e] += X2[e];
   }
 }
@@ -558,10 +610,10 @@ __global__ void __launch_bounds__(NT) k_proj_acc(GroupArgs g, int pass) {
   int side = (int)(loc / per);
   int64_t rem = loc % per;
   int64_t ti = rem / nt, tt = rem % nt;
-  const int32_t* bn = g.iwork + d.bn_off;
-  MatA X{g.work + (pass ? d.x2_off : d.x_off) + (int64_t)side * d.b * d.l, d.l, false};
-  Rows W{side ? g.Ps : g.Om, g.s, bn};
-  RowsW M{g.work + d.m_off, 2 * g.s, nullptr};
+  CT* wc = reinterpret_cast<CT*>(g.workc);
+  MatAT<CT> X{wc + (pass ? d.x2_off : d.x_off) + (int64_t)side * d.b * d.l, d.l, false};
+  RowsT<CT> W{wc + d.w_off + (int64_t)side * d.l * g.s, g.s, nullptr};
+  RowsWT<CT> M{wc + d.mc_off, 2 * g.s, nullptr};
   tile_acc<CT>(-1.0, X, d.b, d.l, W, 0, M, (int64_t)side * g.s, g.s, ti * TB, tt * TB);
 }
 
@@ -928,6 +980,7 @@ constexpr int ER = 8;
 struct CntExtract {
   __host__ __device__ int64_t operator()(const BoxDesc& d) const { return 2 * cdv(d.r, ER); }
 };
+template <typename CT>
 __global__ void __launch_bounds__(256) k_extract(GroupArgs g) {
   int64_t loc;
   int bi = find_item(g.desc, g.nbox, blockIdx.x, CntExtract(), loc);
@@ -939,24 +992,31 @@ __global__ void __launch_bounds__(256) k_extract(GroupArgs g) {
   const int nr = (int)imin64(ER, d.r - i0);
   const int kp = d.kp, r = d.r, l = d.l, b = d.b;
   const int32_t* perm = g.iwork + d.pv_off;  // [S (pivot order) | R ascending]
-  const double* C = g.work + d.x_off + (int64_t)side * b * l;
+  CT* wc = reinterpret_cast<CT*>(g.workc);
+  const CT* C = wc + d.x_off + (int64_t)side * b * l;
   const double* T = g.fd + fd_T(d);
-  double* E = g.work + d.cp_off + (int64_t)side * r * l;
+  CT* E = wc + d.e_off + (int64_t)side * r * l;
+  __shared__ CT tcol[ER][128];  // columns i of T for this CTA's rows (kp <= 128)
+  for (int e = threadIdx.x; e < nr * kp; e += blockDim.x) {
+    int ii = e / kp, q = e % kp;
+    tcol[ii][q] = (CT)T[(int64_t)q * r + i0 + ii];
+  }
+  __syncthreads();
   // phase 1: Q = C_R - T^T C_S
   for (int64_t e = threadIdx.x; e < (int64_t)nr * l; e += blockDim.x) {
     int ii = (int)(e / l);
     int64_t col = e % l;
     int i = (int)i0 + ii;
-    double v = C[(int64_t)perm[kp + i] * l + col];
-    for (int q = 0; q < kp; ++q) v -= T[(int64_t)q * r + i] * C[(int64_t)perm[q] * l + col];
+    CT v = C[(int64_t)perm[kp + i] * l + col];
+    for (int q = 0; q < kp; ++q) v -= tcol[ii][q] * C[(int64_t)perm[q] * l + col];
     E[(int64_t)i * l + col] = v;
   }
   __syncthreads();
   // phase 2: columns R -= columns S times T
   for (int64_t e = threadIdx.x; e < (int64_t)nr * r; e += blockDim.x) {
     int i = (int)i0 + (int)(e / r), u = (int)(e % r);
-    double v = E[(int64_t)i * l + perm[kp + u]];
-    for (int q = 0; q < kp; ++q) v -= E[(int64_t)i * l + perm[q]] * T[(int64_t)q * r + u];
+    CT v = E[(int64_t)i * l + perm[kp + u]];
+    for (int q = 0; q < kp; ++q) v -= E[(int64_t)i * l + perm[q]] * (CT)T[(int64_t)q * r + u];
     E[(int64_t)i * l + perm[kp + u]] = v;
   }
   __syncthreads();
@@ -967,13 +1027,13 @@ __global__ void __launch_bounds__(256) k_extract(GroupArgs g) {
     double* Uc = g.fd + fd_Uc(d);  // [X_RS X_RN] until the LU solve
     for (int64_t e = threadIdx.x; e < (int64_t)nr * r; e += blockDim.x) {
       int i = (int)i0 + (int)(e / r), u = (int)(e % r);
-      XRR[(int64_t)i * r + u] = E[(int64_t)i * l + perm[kp + u]];
+      XRR[(int64_t)i * r + u] = (double)E[(int64_t)i * l + perm[kp + u]];
     }
     for (int64_t e = threadIdx.x; e < (int64_t)nr * w; e += blockDim.x) {
       int i = (int)i0 + (int)(e / w);
       int64_t q = e % w;
       int64_t col = q < kp ? perm[q] : b + (q - kp);
-      Uc[(int64_t)i * w + q] = E[(int64_t)i * l + col];
+      Uc[(int64_t)i * w + q] = (double)E[(int64_t)i * l + col];
     }
   } else {
     double* LcT = g.fd + fd_LcT(d);  // [X_SR^T X_NR^T] until the LU solve
@@ -981,7 +1041,7 @@ __global__ void __launch_bounds__(256) k_extract(GroupArgs g) {
       int i = (int)i0 + (int)(e / w);
       int64_t q = e % w;
       int64_t col = q < kp ? perm[q] : b + (q - kp);
-      LcT[(int64_t)i * w + q] = E[(int64_t)i * l + col];
+      LcT[(int64_t)i * w + q] = (double)E[(int64_t)i * l + col];
     }
   }
 }
@@ -1424,7 +1484,14 @@ void launch_chol_update(Launch L, const GroupArgs& g, int panel, int64_t items) 
   count_launch(L);
 }
 void launch_gather_box(Launch L, const GroupArgs& g, int64_t items) {
-  k_gather_box<<<grid1(items), 256, 0, L.st>>>(g);
+  if (g.fp32) k_gather_box<float><<<grid1(items), 256, 0, L.st>>>(g);
+  else k_gather_box<double><<<grid1(items), 256, 0, L.st>>>(g);
+  count_launch(L);
+}
+void launch_m_finalize(Launch L, const GroupArgs& g, int64_t items) {
+  if (items <= 0) return;
+  if (g.fp32) k_m_finalize<float><<<grid1(items), 256, 0, L.st>>>(g);
+  else k_m_finalize<double><<<grid1(items), 256, 0, L.st>>>(g);
   count_launch(L);
 }
 void launch_proj_nt(Launch L, const GroupArgs& g, int pass, int64_t items) {
@@ -1476,7 +1543,8 @@ void launch_ef_update(Launch L, const GroupArgs& g, int64_t items) {
 }
 void launch_extract(Launch L, const GroupArgs& g, int64_t items) {
   if (items <= 0) return;
-  k_extract<<<grid1(items), 256, 0, L.st>>>(g);
+  if (g.fp32) k_extract<float><<<grid1(items), 256, 0, L.st>>>(g);
+  else k_extract<double><<<grid1(items), 256, 0, L.st>>>(g);
   count_launch(L);
 }
 void launch_lu(Launch L, const GroupArgs& g) {
@@ -1538,6 +1606,7 @@ int64_t items_gram(const std::vector<BoxDesc>& h) { return items_of<void>(h, Cnt
 int64_t items_chol_trsm(const std::vector<BoxDesc>& h, int p) { return items_of<void>(h, CntPanelRows{p}); }
 int64_t items_chol_update(const std::vector<BoxDesc>& h, int p) { return items_of<void>(h, CntUpdate{p}); }
 int64_t items_gather(const std::vector<BoxDesc>& h) { return items_of<void>(h, CntGather()); }
+int64_t items_finalize(const std::vector<BoxDesc>& h) { return items_of<void>(h, CntFinal()); }
 int64_t items_proj_nt(const std::vector<BoxDesc>& h) { return items_of<void>(h, CntProjNT()); }
 int64_t items_proj_solve(const std::vector<BoxDesc>& h) { return items_of<void>(h, CntProjSolve()); }
 int64_t items_proj_acc(const std::vector<BoxDesc>& h, int64_t s) { return items_of<void>(h, CntProjAcc{s}); }

@@ -382,7 +382,7 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
   std::vector<Seg> segs;
   std::vector<std::pair<int64_t, int64_t>> level_seg(T.depth + 1, {0, 0});  // parent assembly per level
   std::vector<BoxDesc> all_desc;
-  int64_t fd_total = 0, fi_total = 0, work_max = 0, iwork_max = 0;
+  int64_t fd_total = 0, fi_total = 0, work_max = 0, workc_max = 0, iwork_max = 0;
   for (int level = T.depth; level >= 1; --level) {
     int64_t s0 = (int64_t)segs.size();
     for (int b : T.levels[level])
@@ -403,7 +403,7 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
       g.desc_off = (int64_t)all_desc.size();
       g.seg_off = (int64_t)segs.size();
       g.max_panels = g.max_b = g.max_r = 0;
-      int64_t w = 0, iw = 0;
+      int64_t w = 0, wc = 0, iw = 0;
       for (int si = first; si < last; ++si) {
         const Step& stp = sc.steps[si];
         BoxDesc d{};
@@ -416,18 +416,26 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
         iw += d.l;
         d.pv_off = iw;
         iw += d.b + 1;  // CPQR permutation and the first dependent step
-        d.g_off = w;
-        w += 2 * (int64_t)d.l * d.l;
-        d.x_off = w;
-        w += 2 * (int64_t)d.b * d.l;
-        d.x2_off = w;
-        if (passes > 1) w += 2 * (int64_t)d.b * d.l;
+        // compute-type workspace
+        d.g_off = wc;
+        wc += 2 * (int64_t)d.l * d.l;
+        d.x_off = wc;
+        wc += 2 * (int64_t)d.b * d.l;
+        d.x2_off = wc;
+        if (passes > 1) wc += 2 * (int64_t)d.b * d.l;
+        d.mc_off = wc;
+        wc += (int64_t)d.b * 2 * s;
+        d.w_off = wc;
+        wc += 2 * (int64_t)d.l * s;
+        d.e_off = wc;
+        wc += 2 * (int64_t)d.r * d.l;
+        d.li_off = wc;
+        wc += 2 * cdiv(d.l, kT) * 2 * kT * kT;
+        // FP64 workspace
         d.m_off = w;
         w += (int64_t)d.b * 2 * s;
         d.cp_off = w;
-        w += std::max<int64_t>((int64_t)d.kp * d.b, 2 * (int64_t)d.r * d.l);
-        d.li_off = w;
-        w += 2 * cdiv(d.l, kT) * 2 * kT * kT;
+        w += (int64_t)d.kp * d.b;
         d.fi_off = fi_total;
         fi_total += fi_size(d.kp, d.r, d.n);
         d.fd_off = fd_total;
@@ -448,6 +456,7 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
       }
       g.nseg = (int64_t)segs.size() - g.seg_off;
       work_max = std::max(work_max, w);
+      workc_max = std::max(workc_max, wc);
       iwork_max = std::max(iwork_max, iw);
       f->max_r = std::max(f->max_r, g.max_r);
       f->groups.push_back(std::move(g));
@@ -456,6 +465,7 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
   // root pseudo-box: B_t = what the level-1 boxes keep (or all points if the root is a leaf)
   const int64_t nroot = (int64_t)sc.root.size();
   f->root_size = nroot;
+  int64_t root_workc = 0;
   int64_t root_seg_off = (int64_t)segs.size();
   BoxDesc rd{};
   {
@@ -463,13 +473,17 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
     rd.n = rd.kp = rd.r = 0;
     rd.bn_off = 0;
     rd.pv_off = nroot;
+    // the root runs in FP64: its compute-type offsets count doubles
     rd.g_off = 0;
     rd.x_off = 2 * nroot * nroot;
     rd.x2_off = rd.x_off;
-    rd.m_off = rd.x_off + 2 * nroot * nroot;
-    rd.cp_off = rd.m_off + nroot * 2 * s;
-    rd.li_off = rd.cp_off + 1;
-    work_max = std::max(work_max, rd.li_off + 2 * cdiv(nroot, kT) * 2 * kT * kT);
+    rd.mc_off = rd.x_off + 2 * nroot * nroot;
+    rd.w_off = rd.mc_off + nroot * 2 * s;
+    rd.e_off = rd.w_off + 2 * nroot * s;
+    rd.li_off = rd.e_off;
+    root_workc = rd.li_off + 2 * cdiv(nroot, kT) * 2 * kT * kT;
+    rd.m_off = 0;
+    rd.cp_off = 0;
     iwork_max = std::max(iwork_max, 2 * nroot);
     if (T.depth == 0) {
       segs.push_back({act_off[0], 0, nroot});
@@ -499,6 +513,9 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
   CU(pool.alloc(&Om, NS));
   CU(pool.alloc(&Ps, NS));
   CU(pool.alloc(&work, work_max));
+  const size_t ct_bytes = (o.precision == RSRS_PREC_MIXED) ? sizeof(float) : sizeof(double);
+  unsigned char* workc;
+  CU(pool.alloc(&workc, (int64_t)std::max<size_t>(workc_max * ct_bytes, root_workc * sizeof(double))));
   CU(pool.alloc(&iwork, iwork_max));
   CU(pool.alloc(&act, (int64_t)act_init.size()));
   CU(pool.alloc(&segs_dev, (int64_t)segs.size()));
@@ -620,6 +637,7 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
   ga.Om = Om;
   ga.Ps = Ps;
   ga.work = work;
+  ga.workc = workc;
   ga.iwork = iwork;
   ga.fd = f->fd;
   ga.fi = f->fi;
@@ -653,6 +671,7 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
         timed(RSRS_K_PROJ_SOLVE, [&] { launch_proj_solve(L, ga, pass, items_proj_solve(g.h)); });
         timed(RSRS_K_PROJ_ACC, [&] { launch_proj_acc(L, ga, pass, items_proj_acc(g.h, s)); });
       }
+      timed(RSRS_K_GATHER, [&] { launch_m_finalize(L, ga, items_finalize(g.h)); });
       timed(RSRS_K_CPQR, [&] { launch_cpqr(L, ga, g.max_b); });
       timed(RSRS_K_ID, [&] { launch_id_finish(L, ga, g.max_b); });
       timed(RSRS_K_EF, [&] { launch_ef_update(L, ga, items_ef(g.h, s)); });
@@ -685,8 +704,9 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
       launch_proj_solve(L, ga, 0, items_proj_solve(rh));
     });
     CU(cudaMemcpyAsync(f->root_idx, iwork, nroot * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-    CU(cudaMemcpyAsync(f->root_A, work + rd.x_off, nroot * nroot * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    CU(cudaMemcpyAsync(f->root_LU, work + rd.x_off, nroot * nroot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    const double* xroot = reinterpret_cast<const double*>(workc) + rd.x_off;
+    CU(cudaMemcpyAsync(f->root_A, xroot, nroot * nroot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CU(cudaMemcpyAsync(f->root_LU, xroot, nroot * nroot * sizeof(double), cudaMemcpyDeviceToDevice, st));
     timed(RSRS_K_ROOT, [&] {
       launch_dense_lu(L, f->root_LU, nroot, f->root_piv, err);
       launch_dense_inverse(L, f->root_LU, f->root_piv, nroot, f->root_inv);
@@ -718,7 +738,7 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
   f->stats.n_boxes = (int64_t)all_desc.size();
   f->stats.root_size = nroot;
   f->stats.factor_bytes = fd_total * 8 + fi_total * 4 + nroot * nroot * 24 + nroot * 8;
-  f->stats.work_bytes = work_max * 8 + iwork_max * 4 + 4 * NS * 8;
+  f->stats.work_bytes = work_max * 8 + workc_max * (int64_t)ct_bytes + iwork_max * 4 + 4 * NS * 8;
   f->stats.t_sample_ms = t01;
   f->stats.t_compress_ms = t12;
   f->stats.t_root_ms = t23;
