@@ -657,6 +657,7 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
       ga.nbox = (int)g.h.size();
       for (const BoxDesc& d : g.h) box_flops(d, s, passes, fl);
       timed(RSRS_K_LISTS, [&] { launch_copy_segments(L, segs_dev + g.seg_off, (int)g.nseg, act, iwork); });
+      timed(RSRS_K_GATHER, [&] { launch_gather_box(L, ga, items_gather(g.h)); });
       timed(RSRS_K_GRAM, [&] { launch_gram(L, ga, items_gram(g.h)); });
       timed(RSRS_K_CHOL, [&] {
         for (int p = 0; p < g.max_panels; ++p) {
@@ -665,7 +666,6 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
           launch_chol_update(L, ga, p, items_chol_update(g.h, p));
         }
       });
-      timed(RSRS_K_GATHER, [&] { launch_gather_box(L, ga, items_gather(g.h)); });
       for (int pass = 0; pass < passes; ++pass) {
         timed(RSRS_K_PROJ_NT, [&] { launch_proj_nt(L, ga, pass, items_proj_nt(g.h)); });
         timed(RSRS_K_PROJ_SOLVE, [&] { launch_proj_solve(L, ga, pass, items_proj_solve(g.h)); });
@@ -693,13 +693,13 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
     ga.fp32 = 0;  // the root block is extracted in FP64
     timed(RSRS_K_ROOT, [&] {
       launch_copy_segments(L, segs_dev + root_seg_off, (int)root_nseg, act, iwork);
+      launch_gather_box(L, ga, items_gather(rh));
       launch_gram(L, ga, items_gram(rh));
       for (int p = 0; p < (int)cdiv(nroot, kT); ++p) {
         launch_chol_panel(L, ga, p);
         launch_chol_trsm(L, ga, p, items_chol_trsm(rh, p));
         launch_chol_update(L, ga, p, items_chol_update(rh, p));
       }
-      launch_gather_box(L, ga, items_gather(rh));
       launch_proj_nt(L, ga, 0, items_proj_nt(rh));
       launch_proj_solve(L, ga, 0, items_proj_solve(rh));
     });
