@@ -97,9 +97,10 @@ typedef struct {
   int profile;            /* record CUDA-event time per kernel class into rsrs_stats    */
   int sample_kernel;      /* mixed precision, built-in kernels: 0 default, 1 FP32 SIMT,  */
                           /* 2 3xTF32 on the tensor cores (tcgen05)                    */
-  int64_t residual_matrix_bytes; /* built-in kernels: rsrs_refine stores A in FP64 (N*N*8 */
-                          /* bytes, computed once per factor) when it fits this budget; */
-                          /* 0 selects 48 GiB, < 0 always evaluates A on the fly       */
+  int mixed_cpqr;         /* mixed precision: 0 default = FP32 reflectors on the sketch  */
+                          /* held in distributed shared memory (thread-block cluster of */
+                          /* up to 16 CTAs), pivots chosen on FP64 norm sums, when the  */
+                          /* box fits; 1 = FP64 CPQR in global memory (FP64 always)     */
 } rsrs_options;
 
 typedef struct {
@@ -166,6 +167,15 @@ void rsrs_tree_free(rsrs_tree* tree);
  * (before any device work) when s < s_req. */
 rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, int s,
                        const rsrs_options* opts, void* stream, rsrs_factor** out);
+
+/* Several independent problems in one set of launches (same k, s, options): the boxes of all
+ * problems at the same height above their deepest level and of the same colour share each
+ * launch, and the roots are extracted together.  out receives nprob factors that share device
+ * storage (freed with the last of them); each is used like a factor from rsrs_build.  Test
+ * matrices are drawn on the device (problem p uses key opts->seed + p); caller test matrices are
+ * refused with RSRS_E_INVAL. */
+rsrs_status rsrs_build_batched(int nprob, const rsrs_tree* const* trees, const rsrs_operator* ops, int k, int s,
+                               const rsrs_options* opts, void* stream, rsrs_factor** out);
 
 /* F <- A_approx^-1 F (eq. Ainvfact), or its adjoint; F_dev column-major N x nrhs. */
 rsrs_status rsrs_solve(const rsrs_factor* f, double* F_dev, int64_t ldf, int32_t nrhs,

@@ -23,8 +23,11 @@ Readings where the paper is silent:
   boxes conflict when their closed neighbourhoods intersect, and by ascending
   Morton key inside a colour;
 * s_req = max over compressed boxes of (b + n at processing time) + k + p,
-  and at least the size of the final active set B_t (its pseudoinverse needs
-  s >= |B_t|).
+  and at least |B_t| + p for the final active set B_t: its pseudoinverse needs
+  s >= |B_t| (Sec. 4.4), and the same oversampling p as the boxes' least-squares
+  problems keeps Omega_Bt well conditioned (a square Gaussian block has a
+  condition number in the 1e3..1e6 range, which turns sketch rounding into a
+  large error in the root block).
 """
 from __future__ import annotations
 
@@ -239,4 +242,4 @@ class Schedule:
         if tree.depth == 0:
             self.root_size = tree.n
         self.max_l = max((st["b"] + st["n"] for st in self.steps), default=0)
-        self.s_req = max(self.max_l + self.k + self.p if self.steps else 0, self.root_size)
+        self.s_req = max(self.max_l + self.k + self.p if self.steps else 0, self.root_size + self.p)

@@ -80,22 +80,24 @@ void launch_kernel_matvec(Launch L, int kind, const double* pts, int d, int64_t 
 void launch_kernel_matvec_prec(Launch L, int kind, const double* pts, int d, int64_t n, double shift,
                                double scale, const double* in, int64_t ld_in, double* out, int64_t ld_out,
                                int64_t ncols, int fp32, const float* in32);
-// FP32 copy; and TF32 hi/lo split of an n x s row-major block transposed to s x n planes.
+// FP32 copy; and TF32 hi/lo split of an n x s row-major block transposed to s x n planes with
+// row pitch ldp (>= n).
 void launch_to_f32(Launch L, const double* in, int64_t count, float* out);
-void launch_split_transpose(Launch L, const double* in, int64_t n, int64_t s, float* hi, float* lo);
+void launch_split_transpose(Launch L, const double* in, int64_t n, int64_t s, float* hi, float* lo, int64_t ldp);
 
-// Same product in 3xTF32 on the tensor cores (tcgen05, TMEM accumulators); a bounded wait that
-// expires records kDevTimeout in *err.
-// bhi/blo: the TF32 hi/lo planes of `in`, transposed (ncols x n).
-void launch_kernel_matvec_tc(Launch L, int kind, const double* pts, int d, int64_t n, double shift, double scale,
-                             const double* in, int64_t ld_in, const float* bhi, const float* blo, double* out,
-                             int64_t ld_out, int64_t ncols, int* err);
+// Same product in 3xTF32 on the tensor cores (tcgen05, TMEM accumulators, TMA-fed B operand).
+// p32: points in FP32 from launch_points_f32 (tc_points_len(n, d) floats); bhi/blo: TF32 hi/lo
+// planes of the input columns (ncols x n, row pitch ldp = tc_plane_ld(n), 16-byte aligned).
+// Columns [0, ncols0) come from in0 / go to out0, [ncols0, ncols) from in1 / to out1, all row-major
+// with leading dimension ld.  Returns false when the tensor maps cannot be made (no launch);
+// a bounded wait that expires records kDevTimeout in *err.
+int64_t tc_plane_ld(int64_t n);
+int64_t tc_points_len(int64_t n, int d);
+void launch_points_f32(Launch L, const double* pts, int64_t n, int d, float* out);
+bool launch_kernel_matvec_tc(Launch L, int kind, const float* p32, int64_t n, double shift, double scale,
+                             const double* in0, const double* in1, double* out0, double* out1, int64_t ld,
+                             int64_t ncols0, int64_t ncols, const float* bhi, const float* blo, int64_t ldp, int* err);
 
-// Operator matrix A = shift*I + scale*K stored in FP64 (tree order), and out = A in (few columns).
-void launch_operator_matrix(Launch L, int kind, const double* pts, int d, int64_t n, double shift, double scale,
-                            double* A);
-void launch_matrix_product(Launch L, const double* A, int64_t n, const double* in, int64_t ld_in, double* out,
-                           int64_t ld_out, int64_t ncols);
 
 // Group-batched kernels (descriptors of one (level, colour) group).
 struct GroupArgs {
@@ -126,6 +128,9 @@ void launch_proj_nt(Launch L, const GroupArgs& g, int pass, int64_t items);     
 void launch_proj_solve(Launch L, const GroupArgs& g, int pass, int64_t items);     // X <- X G^-1
 void launch_proj_acc(Launch L, const GroupArgs& g, int pass, int64_t items);       // M -= X W
 void launch_cpqr(Launch L, const GroupArgs& g, int max_b);                         // ID pivots + R
+// FP32 CPQR on the compute-type sketch held in distributed shared memory (mixed path); false when
+// the group's boxes do not fit a cluster of at most 16 CTAs (nothing launched).
+bool launch_cpqr32(Launch L, const GroupArgs& g, int max_b);
 void launch_id_finish(Launch L, const GroupArgs& g, int max_b);                    // T, R/S/N lists
 void launch_ef_update(Launch L, const GroupArgs& g, int64_t items);                // E, F on sketches
 void launch_extract(Launch L, const GroupArgs& g, int64_t items);                  // X blocks
@@ -143,17 +148,18 @@ struct SweepArgs {
   int nbox;
   const double* fd;
   const int32_t* fi;
-  double* F;  // N x nrhs row-major, tree order
+  double* F;  // N x nrhs row-major, tree order of one problem
   int nrhs;
   int adjoint;
+  int64_t row_base;  // index lists hold rows of the build's shared index space: row - row_base in F
 };
 // C rows += alpha * op(A) * B rows; row sets 0 = R, 1 = S, 2 = SN; matrices 0 = T, 1 = LcT, 2 = Uc.
 void launch_sweep_op(Launch L, const SweepArgs& a, int cset, int mat, int trans, int bset, double alpha,
                      int64_t items);
 // f_R <- X_RR^-1 f_R (solve, from the stored inverse) or X_RR f_R (apply), adjoint as requested.
 void launch_sweep_diag(Launch L, const SweepArgs& a, int solve, int64_t items, int max_r);
-void launch_dense_apply(Launch L, const double* A, int64_t n, const int32_t* rows, double* F, int nrhs,
-                        int adjoint);
+void launch_dense_apply(Launch L, const double* A, int64_t n, const int32_t* rows, int64_t row_base, double* F,
+                        int nrhs, int adjoint);
 
 // Item counts (host planning) matching the device decoding of each kernel.
 int64_t items_gram(const std::vector<BoxDesc>& h);

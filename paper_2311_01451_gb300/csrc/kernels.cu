@@ -883,6 +883,174 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(GroupArgs g) {
   cluster.sync();  // keep every CTA's shared memory alive until the last remote read
 }
 
+// Mixed-precision CPQR with the box's projected sketch resident in distributed shared memory: a
+// cluster of C CTAs (C = 1..16) per box, CTA r holding columns [r*cs, (r+1)*cs) of all b rows of
+// the FP32 sketch M, so the k' reflector steps never go back to global memory.  Products and
+// updates run in FP32 (M carries the FP32 rounding of the projections already); the dot products
+// and residual norms are summed over the cluster in FP64 and the pivot (largest residual, ties to
+// the lowest tree index, the dependent-pivot rule of k_cpqr) is chosen in FP64 on those sums.
+// Output as k_cpqr_cluster: R rows by point (FP64), permutation and first dependent step.
+__global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const BoxDesc d = g.desc[blockIdx.x / C];
+  const int b = d.b, kp = d.kp;
+  const int64_t c = 2 * g.s;
+  const int64_t t_lo = imin64((int64_t)rank * cs, c), t_hi = imin64(t_lo + cs, c);
+  const float* Mg = reinterpret_cast<const float*>(g.workc) + d.mc_off;
+  double* Rp = g.work + d.cp_off;
+  int32_t* perm = g.iwork + d.pv_off;
+  extern __shared__ double csm[];
+  double* nrm = csm;            // b, replicated in every CTA
+  double* wpart = csm + b;      // b, this CTA's partial dot products
+  double* npart = csm + 2 * b;  // b, this CTA's partial norms
+  int* rid = (int*)(csm + 3 * b);
+  float* S = reinterpret_cast<float*>(csm + 3 * b + (b + 1) / 2 + 1);  // b x cs slice of M
+  __shared__ double red_v[8];
+  __shared__ int red_i[8];
+  __shared__ double s_vj, s_vn2, s_r00;
+  __shared__ int s_j0;
+  const double tau = fmax(1e-10, 64.0 * DBL_EPSILON * (double)max(b, (int)c));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int wid = (int)(t_hi - t_lo);
+  for (int i = threadIdx.x; i < b; i += blockDim.x) rid[i] = i;
+  if (threadIdx.x == 0) {
+    s_r00 = -1.0;
+    s_j0 = kp;
+  }
+  // slice into shared memory; initial partial squared row norms
+  for (int i = warp; i < b; i += nw) {
+    const float* row = Mg + (int64_t)i * c + t_lo;
+    float* srow = S + (int64_t)i * cs;
+    float acc = 0.f;
+    for (int t = lane; t < wid; t += 32) {
+      const float v = row[t];
+      srow[t] = v;
+      acc = fmaf(v, v, acc);
+    }
+    double dacc = acc;
+    for (int o = 16; o; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+    if (lane == 0) npart[i] = dacc;
+  }
+  cluster.sync();
+  for (int i = warp; i < b; i += nw) {
+    double v = lane < C ? cluster.map_shared_rank(npart, lane)[i] : 0.0;
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) nrm[i] = v;
+  }
+  __syncthreads();
+  for (int j = 0; j < kp; ++j) {
+    // pivot: largest residual norm, ties to the lowest local index (identical in every CTA)
+    double bv = -1.0;
+    int bp = -1;
+    for (int pos = j + threadIdx.x; pos < b; pos += blockDim.x) {
+      const double v = nrm[pos];
+      if (v > bv || (v == bv && bp >= 0 && rid[pos] < rid[bp])) {
+        bv = v;
+        bp = pos;
+      }
+    }
+    for (int o = 16; o; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+      if (op >= 0 && (ov > bv || (ov == bv && (bp < 0 || rid[op] < rid[bp])))) {
+        bv = ov;
+        bp = op;
+      }
+    }
+    if (lane == 0) {
+      red_v[warp] = bv;
+      red_i[warp] = bp;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double v0 = -1.0;
+      int p0 = -1;
+      for (int w = 0; w < nw; ++w) {
+        const int op = red_i[w];
+        const double ov = red_v[w];
+        if (op >= 0 && (ov > v0 || (ov == v0 && (p0 < 0 || rid[op] < rid[p0])))) {
+          v0 = ov;
+          p0 = op;
+        }
+      }
+      if (p0 < 0) {
+        p0 = j;
+        if (rank == 0) set_err(g.err, kDevNonfinite);
+      }
+      if (s_j0 == kp && ((s_r00 >= 0.0 && sqrt(v0) <= tau * s_r00) || v0 == 0.0)) s_j0 = j;
+      if (s_j0 <= j) {
+        p0 = j;
+        for (int pos = j + 1; pos < b; ++pos)
+          if (rid[pos] < rid[p0]) p0 = pos;
+      }
+      if (p0 != j) {
+        const int ti = rid[j];
+        rid[j] = rid[p0];
+        rid[p0] = ti;
+        const double tv = nrm[j];
+        nrm[j] = nrm[p0];
+        nrm[p0] = tv;
+      }
+      // x0 = M[pivot][j] lives in the CTA that owns column j
+      const int owner = (int)(j / cs);
+      const double x0 = (double)cluster.map_shared_rank(S, owner)[(int64_t)rid[j] * cs + (j - (int64_t)owner * cs)];
+      const double alpha = sqrt(fmax(nrm[j], 0.0));
+      const double sg = (x0 >= 0.0) ? 1.0 : -1.0;
+      s_vj = x0 + sg * alpha;
+      s_vn2 = 2.0 * alpha * (alpha + fabs(x0));
+      if (j == 0) s_r00 = alpha;
+      if (rank == 0) Rp[(int64_t)j * b + rid[j]] = -sg * alpha;
+    }
+    __syncthreads();
+    const float vj = (float)s_vj;
+    const double vn2 = s_vn2;
+    const float* xs = S + (int64_t)rid[j] * cs;
+    const int t0 = (int)(imax64(t_lo, j) - t_lo);  // first local column of the reflector
+    const int tj = (int)(j - t_lo);                 // local index of column j (in range for its owner)
+    // partial dot products of the remaining rows with v over this CTA's columns
+    for (int pos = j + 1 + warp; pos < b; pos += nw) {
+      const float* row = S + (int64_t)rid[pos] * cs;
+      float w = 0.f;
+      for (int t = t0 + lane; t < wid; t += 32) w = fmaf(row[t], t == tj ? vj : xs[t], w);
+      double dw = w;
+      for (int o = 16; o; o >>= 1) dw += __shfl_xor_sync(0xffffffffu, dw, o);
+      if (lane == 0) wpart[pos] = dw;
+    }
+    cluster.sync();
+    for (int pos = j + 1 + warp; pos < b; pos += nw) {
+      double w = lane < C ? cluster.map_shared_rank(wpart, lane)[pos] : 0.0;
+      for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      const float f = (vn2 > 0.0) ? (float)(2.0 * w / vn2) : 0.f;
+      float* row = S + (int64_t)rid[pos] * cs;
+      float nn = 0.f;
+      for (int t = t0 + lane; t < wid; t += 32) {
+        const float v = fmaf(-f, t == tj ? vj : xs[t], row[t]);
+        row[t] = v;
+        if (t > tj) nn = fmaf(v, v, nn);
+        else Rp[(int64_t)j * b + rid[pos]] = (double)v;  // t == j lives in exactly one CTA
+      }
+      double dn = nn;
+      for (int o = 16; o; o >>= 1) dn += __shfl_xor_sync(0xffffffffu, dn, o);
+      if (lane == 0) npart[pos] = dn;
+    }
+    cluster.sync();
+    for (int pos = j + 1 + warp; pos < b; pos += nw) {
+      double v = lane < C ? cluster.map_shared_rank(npart, lane)[pos] : 0.0;
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) nrm[pos] = v;
+    }
+    __syncthreads();
+  }
+  if (rank == 0) {
+    for (int i = threadIdx.x; i < b; i += blockDim.x) perm[i] = rid[i];
+    if (threadIdx.x == 0) perm[b] = s_j0;
+  }
+  cluster.sync();  // keep every CTA's shared memory alive until the last remote read
+}
+
 // T = R11^-1 R12 (truncated at the first dependent pivot), R/S/N lists, new active list.
 __global__ void __launch_bounds__(256) k_id_finish(GroupArgs g) {
   const BoxDesc d = g.desc[blockIdx.x];
@@ -1291,7 +1459,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a, SweepOp op) {
       for (int e = threadIdx.x; e < 64 * 16; e += 256) {
         int qq = e >> 4, cc = e & 15;
         int64_t q = q0 + qq;
-        Bs[qq][cc] = (q < K && c0 + cc < a.nrhs) ? a.F[(int64_t)bidx[q] * a.nrhs + c0 + cc] : 0.0;
+        Bs[qq][cc] = (q < K && c0 + cc < a.nrhs) ? a.F[((int64_t)bidx[q] - a.row_base) * a.nrhs + c0 + cc] : 0.0;
       }
       __syncthreads();
       if (i < m) {
@@ -1304,7 +1472,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a, SweepOp op) {
       }
       __syncthreads();
     }
-    if (i < m && c < a.nrhs) a.F[(int64_t)cidx[i] * a.nrhs + c] += op.alpha * acc;
+    if (i < m && c < a.nrhs) a.F[((int64_t)cidx[i] - a.row_base) * a.nrhs + c] += op.alpha * acc;
   }
 }
 // f_R <- M f_R with M = X_RR^-1 (solve) or X_RR (apply), or M^T for the adjoint; one CTA per
@@ -1329,7 +1497,7 @@ __global__ void __launch_bounds__(256) k_sweep_diag(SweepArgs a, int solve) {
   for (int64_t e = threadIdx.x; e < r * DC; e += blockDim.x) {
     int64_t i = e / DC;
     int c = (int)(e % DC);
-    in[e] = (c < nc) ? a.F[(int64_t)R[i] * a.nrhs + c0 + c] : 0.0;
+    in[e] = (c < nc) ? a.F[((int64_t)R[i] - a.row_base) * a.nrhs + c0 + c] : 0.0;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -1351,7 +1519,7 @@ __global__ void __launch_bounds__(256) k_sweep_diag(SweepArgs a, int solve) {
 #pragma unroll
         for (int c = 1; c < DC; ++c)
           if (lane == c) v = out[c];
-        a.F[(int64_t)R[i] * a.nrhs + c0 + lane] = v;
+        a.F[((int64_t)R[i] - a.row_base) * a.nrhs + c0 + lane] = v;
       }
     }
   } else {  // thread per row, reading column i of M (coalesced across threads)
@@ -1363,7 +1531,7 @@ __global__ void __launch_bounds__(256) k_sweep_diag(SweepArgs a, int solve) {
 #pragma unroll
         for (int c = 0; c < DC; ++c) out[c] = fma(m, in[q * DC + c], out[c]);
       }
-      for (int c = 0; c < nc; ++c) a.F[(int64_t)R[i] * a.nrhs + c0 + c] = out[c];
+      for (int c = 0; c < nc; ++c) a.F[((int64_t)R[i] - a.row_base) * a.nrhs + c0 + c] = out[c];
     }
   }
 }
@@ -1400,11 +1568,12 @@ __global__ void __launch_bounds__(256) k_dense_inverse(const double* LU, const i
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) inv[i * n + col] = x[i];
 }
 // Dense root block times rows of F: F[rows] <- A F[rows] (or A^T), one CTA per column.
-__global__ void k_dense_apply(const double* A, int64_t n, const int32_t* rows, double* F, int nrhs, int adjoint) {
+__global__ void k_dense_apply(const double* A, int64_t n, const int32_t* rows, int64_t row_base, double* F, int nrhs,
+                              int adjoint) {
   extern __shared__ double col[];
   double* out = col + n;
   const int c = blockIdx.x;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) col[i] = F[(int64_t)rows[i] * nrhs + c];
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) col[i] = F[((int64_t)rows[i] - row_base) * nrhs + c];
   __syncthreads();
   if (adjoint) {
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -1422,7 +1591,7 @@ __global__ void k_dense_apply(const double* A, int64_t n, const int32_t* rows, d
     }
   }
   __syncthreads();
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) F[(int64_t)rows[i] * nrhs + c] = out[i];
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) F[((int64_t)rows[i] - row_base) * nrhs + c] = out[i];
 }
 
 template <class K, class Cnt>
@@ -1525,6 +1694,45 @@ void launch_cpqr(Launch L, const GroupArgs& g, int max_b) {
   cudaLaunchKernelEx(&cfg, k_cpqr_cluster, g);
   count_launch(L);
 }
+// Shared memory of k_cpqr32_cluster for boxes of up to max_b rows and slices of cs columns.
+static size_t cpqr32_smem(int max_b, int cs) {
+  return ((size_t)3 * max_b + (max_b + 1) / 2 + 1) * sizeof(double) + (size_t)max_b * cs * sizeof(float);
+}
+bool launch_cpqr32(Launch L, const GroupArgs& g, int max_b) {
+  const int64_t c = 2 * g.s;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_cpqr32_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_cpqr32_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  for (int C = 1; C <= 16; C *= 2) {
+    const int cs = (int)((cdiv(c, C) + 3) / 4 * 4);
+    const size_t smem = cpqr32_smem(max_b, cs);
+    if (smem > 200 * 1024) continue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(g.nbox * C));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = L.st;
+    cudaLaunchAttribute attr1[1];
+    attr1[0].id = cudaLaunchAttributeClusterDimension;
+    attr1[0].val.clusterDim.x = C;
+    attr1[0].val.clusterDim.y = 1;
+    attr1[0].val.clusterDim.z = 1;
+    cfg.attrs = attr1;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_cpqr32_cluster, &cfg) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();
+      return false;
+    }
+    cudaLaunchKernelEx(&cfg, k_cpqr32_cluster, g, cs);
+    count_launch(L);
+    return true;
+  }
+  return false;
+}
 void launch_cpqr_single(Launch L, const GroupArgs& g, int max_b) {
   size_t smem = (size_t)max_b * (sizeof(double) + sizeof(int));
   k_cpqr<<<(unsigned)g.nbox, 512, smem, L.st>>>(g);
@@ -1591,11 +1799,11 @@ void launch_dense_inverse(Launch L, const double* LU, const int32_t* piv, int64_
   k_dense_inverse<<<(unsigned)n, 256, smem, L.st>>>(LU, piv, n, inv);
   count_launch(L);
 }
-void launch_dense_apply(Launch L, const double* A, int64_t n, const int32_t* rows, double* F, int nrhs,
-                        int adjoint) {
+void launch_dense_apply(Launch L, const double* A, int64_t n, const int32_t* rows, int64_t row_base, double* F,
+                        int nrhs, int adjoint) {
   const size_t smem = 2 * (size_t)n * sizeof(double);
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_dense_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_dense_apply<<<nrhs, 256, smem, L.st>>>(A, n, rows, F, nrhs, adjoint);
+  k_dense_apply<<<nrhs, 256, smem, L.st>>>(A, n, rows, row_base, F, nrhs, adjoint);
   count_launch(L);
 }
 

@@ -26,40 +26,46 @@ struct rsrs_tree {
   Tree t;
 };
 
-struct Group {
+// One problem's boxes inside a (level, colour) launch group, in processing order.
+struct GroupView {
   int level, colour;
-  int64_t desc_off;  // into desc_dev
-  std::vector<BoxDesc> h;
-  int64_t seg_off, nseg;  // bn-list segments
-  int max_panels, max_b, max_r;
+  int64_t desc_off;        // first descriptor of this problem in the shared descriptor array
+  std::vector<BoxDesc> h;  // host copies
+  int max_r;
+};
+
+// Device memory shared by the factors of one build (one or several problems).
+struct Shared {
+  std::vector<void*> ptrs;
+  ~Shared() {
+    for (void* p : ptrs) cudaFree(p);
+  }
 };
 
 struct rsrs_factor {
+  std::shared_ptr<Shared> sh;
   int64_t n = 0, s = 0, k = 0, p = 0;
+  int64_t base = 0;  // first row of this problem in the build's tree-order index space
   int d = 2, precision = 0, kind = 0, passes = 2;
   double shift = 0.0, scale = 0.0;
   rsrs_matvec_fn fn = nullptr;
   void* ctx = nullptr;
-  std::vector<int64_t> perm;  // tree position -> original index
+  std::vector<int64_t> perm;  // tree position -> original index (both local to the problem)
   int32_t* perm_dev = nullptr;
-  double* pts_dev = nullptr;
-  std::vector<Group> groups;
+  double* pts_dev = nullptr;  // local tree order
+  std::vector<GroupView> groups;
   BoxDesc* desc_dev = nullptr;
   double* fd = nullptr;
   int32_t* fi = nullptr;
-  int64_t fd_n = 0, fi_n = 0;
   int64_t root_size = 0;
-  int32_t* root_idx = nullptr;
+  int32_t* root_idx = nullptr;  // shared index space
   double* root_A = nullptr;
   double* root_LU = nullptr;
   double* root_inv = nullptr;  // A~_BtBt^-1, for the block-diagonal solve
   int32_t* root_piv = nullptr;
   int max_r = 0;
-  double *Y = nullptr, *Z = nullptr, *Om = nullptr, *Ps = nullptr;  // kept sketches (optional)
-  double* Amat = nullptr;  // FP64 operator matrix for refinement residuals (lazily, within budget)
-  int sample_kernel = 0;   // mixed sampling: 1 FP32 SIMT, 2 tcgen05 3xTF32
-  int* err_dev = nullptr;  // device status word of kernels run outside a build (sampling)
-  int64_t amat_budget = 0;
+  double *Y = nullptr, *Z = nullptr, *Om = nullptr, *Ps = nullptr;  // kept sketches (shared, rows from base)
+  int sample_kernel = 0;  // mixed sampling: 1 FP32 SIMT, 2 tcgen05 3xTF32
   rsrs_stats stats{};
 };
 
@@ -220,19 +226,18 @@ rsrs_status op_apply(const rsrs_factor* f, Launch L, const double* in, double* o
     return RSRS_OK;
   }
   if (fp32 && !conv) return fail(RSRS_E_INVAL, "internal: FP32 product without conversion buffer");
-  if (fp32 && f->sample_kernel == 2) {
-    launch_split_transpose(L, in, f->n, ncols, conv, conv + f->n * ncols);
-    launch_kernel_matvec_tc(L, f->kind, f->pts_dev, f->d, f->n, f->shift, f->scale, in, ncols, conv,
-                            conv + f->n * ncols, out, ncols, ncols, err);
+  if (fp32 && f->sample_kernel == 2) {  // conv: hi and lo planes, then the FP32 points
+    const int64_t ldp = tc_plane_ld(f->n);
+    float *hi = conv, *lo = conv + ncols * ldp, *p32 = conv + 2 * ncols * ldp;
+    launch_points_f32(L, f->pts_dev, f->n, f->d, p32);
+    launch_split_transpose(L, in, f->n, ncols, hi, lo, ldp);
+    if (!launch_kernel_matvec_tc(L, f->kind, p32, f->n, f->shift, f->scale, in, in, out, out, ncols, ncols, ncols,
+                                 hi, lo, ldp, err))
+      return fail(RSRS_E_CUDA, "could not encode the TMA tensor maps of the sampling product");
     CU(cudaGetLastError());
     return RSRS_OK;
   }
   if (fp32) launch_to_f32(L, in, f->n * ncols, conv);
-  if (f->Amat && !fp32 && ncols <= 16) {
-    launch_matrix_product(L, f->Amat, f->n, in, ncols, out, ncols, ncols);
-    CU(cudaGetLastError());
-    return RSRS_OK;
-  }
   launch_kernel_matvec_prec(L, f->kind, f->pts_dev, f->d, f->n, f->shift, f->scale, in, ncols, out, ncols, ncols,
                             fp32, conv);
   CU(cudaGetLastError());
@@ -323,244 +328,348 @@ rsrs_status rsrs_tree_schedule(const rsrs_tree* tree, int k, int p, int64_t* row
   return RSRS_OK;
 }
 
-rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, int s, const rsrs_options* opts,
-                       void* stream, rsrs_factor** out) {
+}  // extern "C"
+
+namespace {
+
+// Algorithm 1 for a list of independent problems in one set of launches.  Boxes of all problems at
+// the same height above their deepest level and of the same colour share each launch (problems
+// never share rows, so any such merge is conflict-free); the roots form one more group.
+rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_operator* ops, int k, int s,
+                       const rsrs_options* opts, void* stream, rsrs_factor** out) {
   if (!out) return fail(RSRS_E_INVAL, "out is null");
-  *out = nullptr;
-  if (!tree || !op || k <= 0 || s <= 0) return fail(RSRS_E_INVAL, "build: null tree/op or k, s <= 0");
-  if (op->kind != RSRS_OP_LOG2D && op->kind != RSRS_OP_INVR3D && op->kind != RSRS_OP_CALLBACK)
-    return fail(RSRS_E_INVAL, "build: unknown operator kind");
-  if (op->kind == RSRS_OP_CALLBACK && !op->fn) return fail(RSRS_E_INVAL, "build: callback operator without fn");
-  const Tree& T = tree->t;
-  if (op->kind == RSRS_OP_LOG2D && T.d != 2) return fail(RSRS_E_INVAL, "build: log kernel needs 2D points");
-  if (op->kind == RSRS_OP_INVR3D && T.d != 3) return fail(RSRS_E_INVAL, "build: 1/r kernel needs 3D points");
+  for (int p = 0; p < nprob; ++p) out[p] = nullptr;
+  if (nprob <= 0 || !trees || !ops || k <= 0 || s <= 0)
+    return fail(RSRS_E_INVAL, "build: need problems, k > 0, s > 0");
   rsrs_options o{};
   o.p = -1;
   if (opts) o = *opts;
   if (o.precision != RSRS_PREC_FP64 && o.precision != RSRS_PREC_MIXED)
     return fail(RSRS_E_INVAL, "build: unknown precision");
+  if (o.sample_kernel < 0 || o.sample_kernel > 2) return fail(RSRS_E_INVAL, "build: unknown sample_kernel");
+  if (o.mixed_cpqr < 0 || o.mixed_cpqr > 1) return fail(RSRS_E_INVAL, "build: unknown mixed_cpqr");
+  if (nprob > 1 && (o.omega_host || o.psi_host || o.omega_dev || o.psi_dev))
+    return fail(RSRS_E_INVAL, "build: caller test matrices are for single-problem builds");
   // FP32 projections converge by about 1e-2..1e-3 per pass (rounding of the Gram against its
   // conditioning), FP64 ones to rounding after the second pass
   const int passes = o.proj_passes <= 0 ? (o.precision == RSRS_PREC_MIXED ? 3 : 2) : std::min(o.proj_passes, 4);
-  Schedule sc;
-  build_schedule(T, k, o.p, sc);
-  if (s < sc.s_req)
-    return fail(RSRS_E_UNDERSAMPLED, "s=" + std::to_string(s) + " < s_req=" + std::to_string(sc.s_req));
+  std::vector<Schedule> sc(nprob);
+  std::vector<int64_t> base(nprob + 1, 0);
+  int maxdepth = 0;
+  for (int p = 0; p < nprob; ++p) {
+    const rsrs_operator* op = &ops[p];
+    if (!trees[p]) return fail(RSRS_E_INVAL, "build: null tree");
+    if (op->kind != RSRS_OP_LOG2D && op->kind != RSRS_OP_INVR3D && op->kind != RSRS_OP_CALLBACK)
+      return fail(RSRS_E_INVAL, "build: unknown operator kind");
+    if (op->kind == RSRS_OP_CALLBACK && !op->fn) return fail(RSRS_E_INVAL, "build: callback operator without fn");
+    const Tree& T = trees[p]->t;
+    if (op->kind == RSRS_OP_LOG2D && T.d != 2) return fail(RSRS_E_INVAL, "build: log kernel needs 2D points");
+    if (op->kind == RSRS_OP_INVR3D && T.d != 3) return fail(RSRS_E_INVAL, "build: 1/r kernel needs 3D points");
+    build_schedule(T, k, o.p, sc[p]);
+    if (s < sc[p].s_req)
+      return fail(RSRS_E_UNDERSAMPLED, "problem " + std::to_string(p) + ": s=" + std::to_string(s) +
+                                           " < s_req=" + std::to_string(sc[p].s_req));
+    base[p + 1] = base[p] + T.n;
+    maxdepth = std::max(maxdepth, T.depth);
+  }
+  const int64_t Ntot = base[nprob];
+  if (Ntot > INT32_MAX) return fail(RSRS_E_INVAL, "build: more than 2^31 points in one build");
   cudaStream_t st = (cudaStream_t)stream;
-  auto f = std::make_unique<rsrs_factor>();
-  f->n = T.n;
-  f->s = s;
-  f->k = k;
-  f->p = sc.p;
-  f->d = T.d;
-  f->precision = o.precision;
-  f->kind = op->kind;
-  f->passes = passes;
-  f->shift = op->diag_shift;
-  f->scale = op->scale;
-  f->fn = op->fn;
-  f->ctx = op->ctx;
-  f->perm = T.perm;
-  f->amat_budget = o.residual_matrix_bytes == 0 ? (int64_t)48 << 30 : o.residual_matrix_bytes;
-  if (o.sample_kernel < 0 || o.sample_kernel > 2) return fail(RSRS_E_INVAL, "build: unknown sample_kernel");
-  f->sample_kernel = o.sample_kernel == 0 ? 1 : o.sample_kernel;
-  const int64_t N = T.n;
-  const int nbox_tree = (int)T.boxes.size();
+  auto sh = std::make_shared<Shared>();
+  auto dalloc = [&](auto** ptr, int64_t count) -> cudaError_t {
+    using T = std::remove_reference_t<decltype(**ptr)>;
+    *ptr = nullptr;
+    if (count <= 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)ptr, (size_t)count * sizeof(T));
+    if (e == cudaSuccess) sh->ptrs.push_back((void*)*ptr);
+    return e;
+  };
+  std::vector<std::unique_ptr<rsrs_factor>> F(nprob);
+  for (int p = 0; p < nprob; ++p) {
+    const Tree& T = trees[p]->t;
+    auto f = std::make_unique<rsrs_factor>();
+    f->sh = sh;
+    f->n = T.n;
+    f->base = base[p];
+    f->s = s;
+    f->k = k;
+    f->p = sc[p].p;
+    f->d = T.d;
+    f->precision = o.precision;
+    f->kind = ops[p].kind;
+    f->passes = passes;
+    f->shift = ops[p].diag_shift;
+    f->scale = ops[p].scale;
+    f->fn = ops[p].fn;
+    f->ctx = ops[p].ctx;
+    f->perm = T.perm;
+    f->sample_kernel = o.sample_kernel == 0 ? 1 : o.sample_kernel;
+    F[p] = std::move(f);
+  }
 
   // ---- plan: active-list pool, groups, descriptors, offsets --------------------
-  std::vector<int64_t> act_off(nbox_tree, 0);
+  std::vector<std::vector<int64_t>> act_off(nprob);
   int64_t act_total = 0;
-  for (int i = 0; i < nbox_tree; ++i) {
-    act_off[i] = act_total;
-    act_total += sc.act0[i];
+  for (int p = 0; p < nprob; ++p) {
+    const Tree& T = trees[p]->t;
+    act_off[p].assign(T.boxes.size(), 0);
+    for (size_t i = 0; i < T.boxes.size(); ++i) {
+      act_off[p][i] = act_total;
+      act_total += sc[p].act0[i];
+    }
   }
   std::vector<int32_t> act_init(std::max<int64_t>(act_total, 1), 0);
-  for (int i = 0; i < nbox_tree; ++i)
-    if (T.boxes[i].leaf())
-      for (int64_t q = 0; q < sc.act0[i]; ++q) act_init[act_off[i] + q] = (int32_t)(T.boxes[i].first_pos + q);
-
+  for (int p = 0; p < nprob; ++p) {
+    const Tree& T = trees[p]->t;
+    for (size_t i = 0; i < T.boxes.size(); ++i)
+      if (T.boxes[i].leaf())
+        for (int64_t q = 0; q < sc[p].act0[i]; ++q)
+          act_init[act_off[p][i] + q] = (int32_t)(base[p] + T.boxes[i].first_pos + q);
+    if (T.depth == 0)  // the root is a leaf: its slot holds every point
+      for (int64_t q = 0; q < T.n; ++q) act_init[act_off[p][0] + q] = (int32_t)(base[p] + q);
+  }
+  struct LaunchGroup {
+    int height, colour;
+    int64_t desc_off, seg_off, nseg;
+    std::vector<BoxDesc> h;
+    std::vector<std::pair<int, int64_t>> prob_first;  // (problem, first descriptor index in h)
+    int max_panels, max_b, max_r;
+  };
+  std::vector<LaunchGroup> groups;
   std::vector<Seg> segs;
-  std::vector<std::pair<int64_t, int64_t>> level_seg(T.depth + 1, {0, 0});  // parent assembly per level
+  std::vector<std::pair<int64_t, int64_t>> height_seg(std::max(maxdepth, 1), {0, 0});
   std::vector<BoxDesc> all_desc;
   int64_t fd_total = 0, fi_total = 0, work_max = 0, workc_max = 0, iwork_max = 0;
-  for (int level = T.depth; level >= 1; --level) {
+  for (int h = 0; h < maxdepth; ++h) {
     int64_t s0 = (int64_t)segs.size();
-    for (int b : T.levels[level])
-      if (!T.boxes[b].leaf()) {
-        int64_t dst = act_off[b];
-        for (int c : T.boxes[b].children) {
-          if (sc.act1[c] > 0) segs.push_back({act_off[c], dst, sc.act1[c]});
-          dst += sc.act1[c];
+    int ncol = 0;
+    for (int p = 0; p < nprob; ++p) {
+      const Tree& T = trees[p]->t;
+      const int level = T.depth - h;
+      if (level < 1) continue;
+      for (int b : T.levels[level])
+        if (!T.boxes[b].leaf()) {
+          int64_t dst = act_off[p][b];
+          for (int c : T.boxes[b].children) {
+            if (sc[p].act1[c] > 0) segs.push_back({act_off[p][c], dst, sc[p].act1[c]});
+            dst += sc[p].act1[c];
+          }
         }
-      }
-    level_seg[level] = {s0, (int64_t)segs.size() - s0};
-    for (int col = 0; col < (int)sc.groups[level].size(); ++col) {
-      auto [first, last] = sc.groups[level][col];
-      if (first == last) continue;
-      Group g;
-      g.level = level;
+      ncol = std::max(ncol, (int)sc[p].groups[level].size());
+    }
+    height_seg[h] = {s0, (int64_t)segs.size() - s0};
+    for (int col = 0; col < ncol; ++col) {
+      LaunchGroup g;
+      g.height = h;
       g.colour = col;
       g.desc_off = (int64_t)all_desc.size();
       g.seg_off = (int64_t)segs.size();
       g.max_panels = g.max_b = g.max_r = 0;
       int64_t w = 0, wc = 0, iw = 0;
-      for (int si = first; si < last; ++si) {
-        const Step& stp = sc.steps[si];
-        BoxDesc d{};
-        d.b = (int32_t)stp.b;
-        d.n = (int32_t)stp.n;
-        d.l = (int32_t)(stp.b + stp.n);
-        d.kp = (int32_t)stp.kp;
-        d.r = (int32_t)stp.r;
-        d.bn_off = iw;
-        iw += d.l;
-        d.pv_off = iw;
-        iw += d.b + 1;  // CPQR permutation and the first dependent step
-        // compute-type workspace
-        d.g_off = wc;
-        wc += 2 * (int64_t)d.l * d.l;
-        d.x_off = wc;
-        wc += 2 * (int64_t)d.b * d.l;
-        d.x2_off = wc;
-        if (passes > 1) wc += 2 * (int64_t)d.b * d.l;
-        d.mc_off = wc;
-        wc += (int64_t)d.b * 2 * s;
-        d.w_off = wc;
-        wc += 2 * (int64_t)d.l * s;
-        d.e_off = wc;
-        wc += 2 * (int64_t)d.r * d.l;
-        d.li_off = wc;
-        wc += 2 * cdiv(d.l, kT) * 2 * kT * kT;
-        // FP64 workspace
-        d.m_off = w;
-        w += (int64_t)d.b * 2 * s;
-        d.cp_off = w;
-        w += (int64_t)d.kp * d.b;
-        d.fi_off = fi_total;
-        fi_total += fi_size(d.kp, d.r, d.n);
-        d.fd_off = fd_total;
-        fd_total += fd_size(d.kp, d.r, d.n);
-        d.act_off = act_off[stp.box];
-        // near-field list: own active points, then each neighbour's current active points
-        segs.push_back({act_off[stp.box], d.bn_off, stp.b});
-        int64_t pos = d.bn_off + stp.b;
-        for (size_t q = 0; q < stp.nbrs.size(); ++q) {
-          if (stp.nbr_len[q] > 0) segs.push_back({act_off[stp.nbrs[q]], pos, stp.nbr_len[q]});
-          pos += stp.nbr_len[q];
+      for (int p = 0; p < nprob; ++p) {
+        const Tree& T = trees[p]->t;
+        const int level = T.depth - h;
+        if (level < 1 || col >= (int)sc[p].groups[level].size()) continue;
+        auto [first, last] = sc[p].groups[level][col];
+        if (first == last) continue;
+        g.prob_first.push_back({p, (int64_t)g.h.size()});
+        for (int si = first; si < last; ++si) {
+          const Step& stp = sc[p].steps[si];
+          BoxDesc d{};
+          d.b = (int32_t)stp.b;
+          d.n = (int32_t)stp.n;
+          d.l = (int32_t)(stp.b + stp.n);
+          d.kp = (int32_t)stp.kp;
+          d.r = (int32_t)stp.r;
+          d.bn_off = iw;
+          iw += d.l;
+          d.pv_off = iw;
+          iw += d.b + 1;  // CPQR permutation and the first dependent step
+          // compute-type workspace
+          d.g_off = wc;
+          wc += 2 * (int64_t)d.l * d.l;
+          d.x_off = wc;
+          wc += 2 * (int64_t)d.b * d.l;
+          d.x2_off = wc;
+          if (passes > 1) wc += 2 * (int64_t)d.b * d.l;
+          d.mc_off = wc;
+          wc += (int64_t)d.b * 2 * s;
+          d.w_off = wc;
+          wc += 2 * (int64_t)d.l * s;
+          d.e_off = wc;
+          wc += 2 * (int64_t)d.r * d.l;
+          d.li_off = wc;
+          wc += 2 * cdiv(d.l, kT) * 2 * kT * kT;
+          // FP64 workspace
+          d.m_off = w;
+          w += (int64_t)d.b * 2 * s;
+          d.cp_off = w;
+          w += (int64_t)d.kp * d.b;
+          d.fi_off = fi_total;
+          fi_total += fi_size(d.kp, d.r, d.n);
+          d.fd_off = fd_total;
+          fd_total += fd_size(d.kp, d.r, d.n);
+          d.act_off = act_off[p][stp.box];
+          // near-field list: own active points, then each neighbour's current active points
+          segs.push_back({act_off[p][stp.box], d.bn_off, stp.b});
+          int64_t pos = d.bn_off + stp.b;
+          for (size_t q = 0; q < stp.nbrs.size(); ++q) {
+            if (stp.nbr_len[q] > 0) segs.push_back({act_off[p][stp.nbrs[q]], pos, stp.nbr_len[q]});
+            pos += stp.nbr_len[q];
+          }
+          g.max_panels = std::max<int>(g.max_panels, (int)cdiv(d.l, kT));
+          g.max_b = std::max<int>(g.max_b, d.b);
+          g.max_r = std::max<int>(g.max_r, d.r);
+          g.h.push_back(d);
+          all_desc.push_back(d);
         }
-        g.max_panels = std::max<int>(g.max_panels, (int)cdiv(d.l, kT));
-        g.max_b = std::max<int>(g.max_b, d.b);
-        g.max_r = std::max<int>(g.max_r, d.r);
-        g.h.push_back(d);
-        all_desc.push_back(d);
       }
+      if (g.h.empty()) continue;
       g.nseg = (int64_t)segs.size() - g.seg_off;
       work_max = std::max(work_max, w);
       workc_max = std::max(workc_max, wc);
       iwork_max = std::max(iwork_max, iw);
-      f->max_r = std::max(f->max_r, g.max_r);
-      f->groups.push_back(std::move(g));
+      groups.push_back(std::move(g));
     }
   }
-  // root pseudo-box: B_t = what the level-1 boxes keep (or all points if the root is a leaf)
-  const int64_t nroot = (int64_t)sc.root.size();
-  f->root_size = nroot;
-  int64_t root_workc = 0;
-  int64_t root_seg_off = (int64_t)segs.size();
-  BoxDesc rd{};
-  {
+  // root group: one pseudo-box per problem, B_t = what its level-1 boxes keep (or all its points)
+  std::vector<BoxDesc> rh;
+  int64_t root_seg_off = (int64_t)segs.size(), root_workc = 0, root_iw = 0;
+  std::vector<int64_t> root_iw_off(nprob, 0);
+  for (int p = 0; p < nprob; ++p) {
+    const Tree& T = trees[p]->t;
+    const int64_t nroot = (int64_t)sc[p].root.size();
+    F[p]->root_size = nroot;
+    BoxDesc rd{};
     rd.b = rd.l = (int32_t)nroot;
     rd.n = rd.kp = rd.r = 0;
-    rd.bn_off = 0;
-    rd.pv_off = nroot;
+    rd.bn_off = root_iw;
+    root_iw_off[p] = root_iw;
+    root_iw += nroot;
+    rd.pv_off = root_iw;
+    root_iw += 1;
     // the root runs in FP64: its compute-type offsets count doubles
-    rd.g_off = 0;
-    rd.x_off = 2 * nroot * nroot;
-    rd.x2_off = rd.x_off;
-    rd.mc_off = rd.x_off + 2 * nroot * nroot;
-    rd.w_off = rd.mc_off + nroot * 2 * s;
-    rd.e_off = rd.w_off + 2 * nroot * s;
-    rd.li_off = rd.e_off;
-    root_workc = rd.li_off + 2 * cdiv(nroot, kT) * 2 * kT * kT;
-    rd.m_off = 0;
-    rd.cp_off = 0;
-    iwork_max = std::max(iwork_max, 2 * nroot);
+    rd.g_off = root_workc;
+    root_workc += 2 * nroot * nroot;
+    rd.x_off = root_workc;
+    root_workc += 2 * nroot * nroot;
+    rd.x2_off = root_workc;
+    root_workc += 2 * nroot * nroot;
+    rd.mc_off = root_workc;
+    root_workc += nroot * 2 * s;
+    rd.w_off = root_workc;
+    root_workc += 2 * nroot * s;
+    rd.e_off = root_workc;
+    rd.li_off = root_workc;
+    root_workc += 2 * cdiv(nroot, kT) * 2 * kT * kT;
+    rh.push_back(rd);
     if (T.depth == 0) {
-      segs.push_back({act_off[0], 0, nroot});
+      segs.push_back({act_off[p][0], rd.bn_off, nroot});
     } else {
-      int64_t dst = 0;
+      int64_t dst = rd.bn_off;
       for (int b : T.levels[1]) {
-        if (sc.act1[b] > 0) segs.push_back({act_off[b], dst, sc.act1[b]});
-        dst += sc.act1[b];
+        if (sc[p].act1[b] > 0) segs.push_back({act_off[p][b], dst, sc[p].act1[b]});
+        dst += sc[p].act1[b];
       }
     }
   }
-  int64_t root_nseg = (int64_t)segs.size() - root_seg_off;
-  // root as a leaf: its pool slot is the whole point set
-  if (T.depth == 0)
-    for (int64_t q = 0; q < N; ++q) act_init[act_off[0] + q] = (int32_t)q;
+  const int64_t root_nseg = (int64_t)segs.size() - root_seg_off;
+  iwork_max = std::max(iwork_max, root_iw);
+  int max_root_panels = 0;
+  for (const BoxDesc& d : rh) max_root_panels = std::max<int>(max_root_panels, (int)cdiv(d.l, kT));
 
   // ---- device allocations --------------------------------------------------------
-  DevPool pool;
-  const int64_t NS = N * (int64_t)s;
+  DevPool pool;  // build-only scratch
+  const int64_t NS = Ntot * (int64_t)s;
   double *Y, *Z, *Om, *Ps, *work;
-  int32_t *iwork, *act, *perm_dev;
+  int32_t *iwork, *act, *perm_all;
   Seg* segs_dev;
   BoxDesc *desc_dev, *root_desc_dev;
   int* err;
-  CU(pool.alloc(&Y, NS));
-  CU(pool.alloc(&Z, NS));
-  CU(pool.alloc(&Om, NS));
-  CU(pool.alloc(&Ps, NS));
-  CU(pool.alloc(&work, work_max));
   const size_t ct_bytes = (o.precision == RSRS_PREC_MIXED) ? sizeof(float) : sizeof(double);
   unsigned char* workc;
+  if (o.keep_sketches) {
+    CU(dalloc(&Y, NS));
+    CU(dalloc(&Z, NS));
+    CU(dalloc(&Om, NS));
+    CU(dalloc(&Ps, NS));
+  } else {
+    CU(pool.alloc(&Y, NS));
+    CU(pool.alloc(&Z, NS));
+    CU(pool.alloc(&Om, NS));
+    CU(pool.alloc(&Ps, NS));
+  }
+  CU(pool.alloc(&work, work_max));
   CU(pool.alloc(&workc, (int64_t)std::max<size_t>(workc_max * ct_bytes, root_workc * sizeof(double))));
   CU(pool.alloc(&iwork, iwork_max));
   CU(pool.alloc(&act, (int64_t)act_init.size()));
   CU(pool.alloc(&segs_dev, (int64_t)segs.size()));
-  CU(pool.alloc(&desc_dev, (int64_t)all_desc.size()));
-  CU(pool.alloc(&root_desc_dev, 1));
+  CU(pool.alloc(&root_desc_dev, nprob));
   CU(pool.alloc(&err, 1));
-  CU(pool.alloc(&perm_dev, N));
-  CU(pool.alloc(&f->pts_dev, N * T.d));
-  CU(pool.alloc(&f->fd, fd_total));
-  CU(pool.alloc(&f->fi, fi_total));
-  CU(pool.alloc(&f->root_idx, nroot));
-  CU(pool.alloc(&f->root_A, nroot * nroot));
-  CU(pool.alloc(&f->root_LU, nroot * nroot));
-  CU(pool.alloc(&f->root_piv, nroot));
-  CU(pool.alloc(&f->root_inv, nroot * nroot));
-  f->fd_n = fd_total;
-  f->fi_n = fi_total;
-  f->desc_dev = desc_dev;
-  f->perm_dev = perm_dev;
+  CU(dalloc(&desc_dev, (int64_t)all_desc.size()));
+  double* fd;
+  int32_t* fi;
+  CU(dalloc(&fd, fd_total));
+  CU(dalloc(&fi, fi_total));
+  CU(dalloc(&perm_all, Ntot));
+  double* pts_all;
   {
-    std::vector<int32_t> p32(N);
-    for (int64_t q = 0; q < N; ++q) p32[q] = (int32_t)T.perm[q];
-    CU(cudaMemcpyAsync(perm_dev, p32.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(f->pts_dev, T.pts_tree.data(), N * T.d * sizeof(double), cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(act, act_init.data(), act_init.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    if (!segs.empty())
-      CU(cudaMemcpyAsync(segs_dev, segs.data(), segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, st));
-    if (!all_desc.empty())
-      CU(cudaMemcpyAsync(desc_dev, all_desc.data(), all_desc.size() * sizeof(BoxDesc), cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(root_desc_dev, &rd, sizeof(BoxDesc), cudaMemcpyHostToDevice, st));
-    CU(cudaMemsetAsync(err, 0, sizeof(int), st));
-    // test matrices: caller's host or device arrays (original order), or Philox draws; stored in tree order
+    int64_t npts = 0;
+    for (int p = 0; p < nprob; ++p) npts += trees[p]->t.n * trees[p]->t.d;
+    CU(dalloc(&pts_all, npts));
+    int64_t po = 0;
+    for (int p = 0; p < nprob; ++p) {
+      const Tree& T = trees[p]->t;
+      F[p]->pts_dev = pts_all + po;
+      F[p]->perm_dev = perm_all + base[p];
+      CU(cudaMemcpyAsync(F[p]->pts_dev, T.pts_tree.data(), T.n * T.d * sizeof(double), cudaMemcpyHostToDevice, st));
+      po += T.n * T.d;
+      std::vector<int32_t> p32(T.n);
+      for (int64_t q = 0; q < T.n; ++q) p32[q] = (int32_t)T.perm[q];
+      CU(cudaMemcpyAsync(F[p]->perm_dev, p32.data(), T.n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+      CU(cudaStreamSynchronize(st));  // p32 goes out of scope
+      const int64_t nroot = F[p]->root_size;
+      CU(dalloc(&F[p]->root_idx, nroot));
+      CU(dalloc(&F[p]->root_A, nroot * nroot));
+      CU(dalloc(&F[p]->root_LU, nroot * nroot));
+      CU(dalloc(&F[p]->root_piv, nroot));
+      CU(dalloc(&F[p]->root_inv, nroot * nroot));
+      F[p]->desc_dev = desc_dev;
+      F[p]->fd = fd;
+      F[p]->fi = fi;
+      if (o.keep_sketches) {
+        F[p]->Y = Y;
+        F[p]->Z = Z;
+        F[p]->Om = Om;
+        F[p]->Ps = Ps;
+      }
+    }
+  }
+  CU(cudaMemcpyAsync(act, act_init.data(), act_init.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  if (!segs.empty())
+    CU(cudaMemcpyAsync(segs_dev, segs.data(), segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, st));
+  if (!all_desc.empty())
+    CU(cudaMemcpyAsync(desc_dev, all_desc.data(), all_desc.size() * sizeof(BoxDesc), cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(root_desc_dev, rh.data(), rh.size() * sizeof(BoxDesc), cudaMemcpyHostToDevice, st));
+  CU(cudaMemsetAsync(err, 0, sizeof(int), st));
+  // test matrices: caller's host or device arrays (original order, single problem), or Philox draws
+  // (problem p uses key seed + p); stored in tree order
+  for (int p = 0; p < nprob; ++p) {
+    const Tree& T = trees[p]->t;
+    const int64_t n = T.n, ns = n * s;
     for (int side = 0; side < 2; ++side) {
-      double* dst = side == 0 ? Om : Ps;
+      double* dst = (side == 0 ? Om : Ps) + base[p] * s;
       const double* hsrc = side == 0 ? o.omega_host : o.psi_host;
       const double* dsrc = side == 0 ? o.omega_dev : o.psi_dev;
       if (hsrc) {
-        std::vector<double> tree_order(NS);
-        for (int64_t q = 0; q < N; ++q) std::memcpy(&tree_order[q * s], &hsrc[T.perm[q] * s], s * sizeof(double));
-        CU(cudaMemcpyAsync(dst, tree_order.data(), NS * sizeof(double), cudaMemcpyHostToDevice, st));
+        std::vector<double> tree_order(ns);
+        for (int64_t q = 0; q < n; ++q) std::memcpy(&tree_order[q * s], &hsrc[T.perm[q] * s], s * sizeof(double));
+        CU(cudaMemcpyAsync(dst, tree_order.data(), ns * sizeof(double), cudaMemcpyHostToDevice, st));
         CU(cudaStreamSynchronize(st));  // the staging buffer goes out of scope
       } else if (dsrc) {
-        k_gather_orig<<<nblk(NS), 256, 0, st>>>(dsrc, perm_dev, N, s, dst);
+        k_gather_orig<<<nblk(ns), 256, 0, st>>>(dsrc, F[p]->perm_dev, n, s, dst);
       } else {
-        k_gauss_tree<<<nblk(NS), 256, 0, st>>>(o.seed, (uint32_t)side, perm_dev, N, s, dst);
+        k_gauss_tree<<<nblk(ns), 256, 0, st>>>(o.seed + (uint64_t)p, (uint32_t)side, F[p]->perm_dev, n, s, dst);
       }
       CU(cudaGetLastError());
     }
@@ -568,6 +677,7 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
 
   int64_t launches = 0;
   Launch L{st, &launches};
+  rsrs_stats bst{};
   // per-class CUDA-event timing (opts.profile): one event pair around each class launch sequence
   struct Rec {
     int cls;
@@ -594,7 +704,7 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
       cudaEventRecord(b, st);
       recs.push_back({cls, a, b});
     }
-    f->stats.class_launches[cls] += launches - l0;
+    bst.class_launches[cls] += launches - l0;
   };
   struct EvGuard {
     std::vector<cudaEvent_t>& v;
@@ -605,31 +715,59 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
   cudaEvent_t ev[4];
   for (auto& e : ev) e = new_ev();
   CU(cudaEventRecord(ev[0], st));
-  // ---- a1: sampling Y = A Omega, Z = A* Psi -------------------------------------------
+  // ---- a1: sampling Y = A Omega, Z = A* Psi, problem by problem --------------------------
   {
+    int64_t nmax = 0;
+    for (int p = 0; p < nprob; ++p) nmax = std::max(nmax, F[p]->n);
+    const int64_t nsmax = nmax * s;
     double *cm_in = nullptr, *cm_out = nullptr;
-    if (f->kind == RSRS_OP_CALLBACK) {
-      CU(pool.alloc(&cm_in, NS));
-      CU(pool.alloc(&cm_out, NS));
-    }
-    const int fp32 = (o.precision == RSRS_PREC_MIXED && f->kind != RSRS_OP_CALLBACK) ? 1 : 0;
     float* conv = nullptr;
-    if (fp32) CU(pool.alloc(&conv, 2 * NS));
+    bool any_cb = false, any_builtin = false;
+    for (int p = 0; p < nprob; ++p) (F[p]->kind == RSRS_OP_CALLBACK ? any_cb : any_builtin) = true;
+    if (any_cb) {
+      CU(pool.alloc(&cm_in, nsmax));
+      CU(pool.alloc(&cm_out, nsmax));
+    }
+    const bool mixed = o.precision == RSRS_PREC_MIXED;
+    const bool tc = mixed && F[0]->sample_kernel == 2;
+    // tensor-core path: hi/lo planes of [Omega Psi] (2s x N each) and the FP32 points; SIMT path:
+    // an FP32 copy of one side
+    if (mixed && any_builtin)
+      CU(pool.alloc(&conv, tc ? 4 * s * tc_plane_ld(nmax) + tc_points_len(nmax, 3) : nsmax));
     rsrs_status r1 = RSRS_OK;
     timed(RSRS_K_SAMPLE, [&] {
-      r1 = op_apply(f.get(), L, Om, Y, s, 0, fp32, cm_in, cm_out, err, conv);
-      if (r1 == RSRS_OK) r1 = op_apply(f.get(), L, Ps, Z, s, 1, fp32, cm_in, cm_out, err, conv);
+      for (int p = 0; p < nprob && r1 == RSRS_OK; ++p) {
+        const rsrs_factor* fp = F[p].get();
+        const int fp32 = (mixed && fp->kind != RSRS_OP_CALLBACK) ? 1 : 0;
+        const int64_t off = base[p] * s;
+        if (fp32 && tc) {
+          // the built-in kernels are symmetric, so Y = A Omega and Z = A* Psi are one product with
+          // the 2s columns [Omega Psi]
+          const int64_t ldp = tc_plane_ld(fp->n);
+          float *hi = conv, *lo = conv + 2 * s * ldp, *p32 = conv + 4 * s * ldp;
+          launch_points_f32(L, fp->pts_dev, fp->n, fp->d, p32);
+          launch_split_transpose(L, Om + off, fp->n, s, hi, lo, ldp);
+          launch_split_transpose(L, Ps + off, fp->n, s, hi + s * ldp, lo + s * ldp, ldp);
+          if (!launch_kernel_matvec_tc(L, fp->kind, p32, fp->n, fp->shift, fp->scale, Om + off, Ps + off, Y + off,
+                                       Z + off, s, s, 2 * s, hi, lo, ldp, err))
+            r1 = fail(RSRS_E_CUDA, "could not encode the TMA tensor maps of the sampling product");
+          continue;
+        }
+        r1 = op_apply(fp, L, Om + off, Y + off, s, 0, fp32, cm_in, cm_out, err, conv);
+        if (r1 == RSRS_OK) r1 = op_apply(fp, L, Ps + off, Z + off, s, 1, fp32, cm_in, cm_out, err, conv);
+      }
     });
+    if (r1 != RSRS_OK) return r1;
+    for (int p = 0; p < nprob; ++p)
+      if (F[p]->kind != RSRS_OP_CALLBACK) bst.class_gflop[RSRS_K_SAMPLE] += 4.0 * (double)F[p]->n * F[p]->n * s * 1e-9;
     if (conv) {
       CU(cudaStreamSynchronize(st));
       pool.release(conv);
       cudaFree(conv);
     }
-    if (r1 != RSRS_OK) return r1;
-    if (f->kind != RSRS_OP_CALLBACK) f->stats.class_gflop[RSRS_K_SAMPLE] = 4.0 * (double)N * N * s * 1e-9;
   }
   CU(cudaEventRecord(ev[1], st));
-  // ---- a2..a8: levels L..1, colour by colour ------------------------------------------
+  // ---- a2..a8: heights 0.. (levels L..1 of each problem), colour by colour ------------------
   GroupArgs ga{};
   ga.s = s;
   ga.Y = Y;
@@ -639,20 +777,20 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
   ga.work = work;
   ga.workc = workc;
   ga.iwork = iwork;
-  ga.fd = f->fd;
-  ga.fi = f->fi;
+  ga.fd = fd;
+  ga.fi = fi;
   ga.act = act;
   ga.err = err;
   ga.fp32 = (o.precision == RSRS_PREC_MIXED) ? 1 : 0;
   double fl[RSRS_NCLASS] = {};
   size_t gi = 0;
-  for (int level = T.depth; level >= 1; --level) {
-    if (level_seg[level].second > 0)
+  for (int h = 0; h < maxdepth; ++h) {
+    if (height_seg[h].second > 0)
       timed(RSRS_K_LISTS, [&] {
-        launch_copy_segments(L, segs_dev + level_seg[level].first, (int)level_seg[level].second, act, act);
+        launch_copy_segments(L, segs_dev + height_seg[h].first, (int)height_seg[h].second, act, act);
       });
-    for (; gi < f->groups.size() && f->groups[gi].level == level; ++gi) {
-      const Group& g = f->groups[gi];
+    for (; gi < groups.size() && groups[gi].height == h; ++gi) {
+      const LaunchGroup& g = groups[gi];
       ga.desc = desc_dev + g.desc_off;
       ga.nbox = (int)g.h.size();
       for (const BoxDesc& d : g.h) box_flops(d, s, passes, fl);
@@ -660,10 +798,10 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
       timed(RSRS_K_GATHER, [&] { launch_gather_box(L, ga, items_gather(g.h)); });
       timed(RSRS_K_GRAM, [&] { launch_gram(L, ga, items_gram(g.h)); });
       timed(RSRS_K_CHOL, [&] {
-        for (int p = 0; p < g.max_panels; ++p) {
-          launch_chol_panel(L, ga, p);
-          launch_chol_trsm(L, ga, p, items_chol_trsm(g.h, p));
-          launch_chol_update(L, ga, p, items_chol_update(g.h, p));
+        for (int pn = 0; pn < g.max_panels; ++pn) {
+          launch_chol_panel(L, ga, pn);
+          launch_chol_trsm(L, ga, pn, items_chol_trsm(g.h, pn));
+          launch_chol_update(L, ga, pn, items_chol_update(g.h, pn));
         }
       });
       for (int pass = 0; pass < passes; ++pass) {
@@ -671,8 +809,12 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
         timed(RSRS_K_PROJ_SOLVE, [&] { launch_proj_solve(L, ga, pass, items_proj_solve(g.h)); });
         timed(RSRS_K_PROJ_ACC, [&] { launch_proj_acc(L, ga, pass, items_proj_acc(g.h, s)); });
       }
-      timed(RSRS_K_GATHER, [&] { launch_m_finalize(L, ga, items_finalize(g.h)); });
-      timed(RSRS_K_CPQR, [&] { launch_cpqr(L, ga, g.max_b); });
+      bool cpqr_done = false;
+      if (ga.fp32 && o.mixed_cpqr == 0) timed(RSRS_K_CPQR, [&] { cpqr_done = launch_cpqr32(L, ga, g.max_b); });
+      if (!cpqr_done) {
+        timed(RSRS_K_GATHER, [&] { launch_m_finalize(L, ga, items_finalize(g.h)); });
+        timed(RSRS_K_CPQR, [&] { launch_cpqr(L, ga, g.max_b); });
+      }
       timed(RSRS_K_ID, [&] { launch_id_finish(L, ga, g.max_b); });
       timed(RSRS_K_EF, [&] { launch_ef_update(L, ga, items_ef(g.h, s)); });
       timed(RSRS_K_EXTRACT, [&] { launch_extract(L, ga, items_extract(g.h)); });
@@ -683,37 +825,51 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
     CU(cudaGetLastError());
   }
   for (int c = 0; c < RSRS_NCLASS; ++c)
-    if (c != RSRS_K_SAMPLE) f->stats.class_gflop[c] = fl[c] * 1e-9;
+    if (c != RSRS_K_SAMPLE) bst.class_gflop[c] = fl[c] * 1e-9;
   CU(cudaEventRecord(ev[2], st));
-  // ---- a9: root extraction A~_{Bt Bt} = Y_Bt pinv(Om_Bt), then LU ---------------------
-  if (nroot > 0) {
-    std::vector<BoxDesc> rh{rd};
+  // ---- a9: root extraction A~_{Bt Bt} = Y_Bt pinv(Om_Bt) for every problem, then LU ----------
+  {
     ga.desc = root_desc_dev;
-    ga.nbox = 1;
-    ga.fp32 = 0;  // the root block is extracted in FP64
-    timed(RSRS_K_ROOT, [&] {
-      launch_copy_segments(L, segs_dev + root_seg_off, (int)root_nseg, act, iwork);
-      launch_gather_box(L, ga, items_gather(rh));
-      launch_gram(L, ga, items_gram(rh));
-      for (int p = 0; p < (int)cdiv(nroot, kT); ++p) {
-        launch_chol_panel(L, ga, p);
-        launch_chol_trsm(L, ga, p, items_chol_trsm(rh, p));
-        launch_chol_update(L, ga, p, items_chol_update(rh, p));
-      }
-      launch_proj_nt(L, ga, 0, items_proj_nt(rh));
-      launch_proj_solve(L, ga, 0, items_proj_solve(rh));
-    });
-    CU(cudaMemcpyAsync(f->root_idx, iwork, nroot * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-    const double* xroot = reinterpret_cast<const double*>(workc) + rd.x_off;
-    CU(cudaMemcpyAsync(f->root_A, xroot, nroot * nroot * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    CU(cudaMemcpyAsync(f->root_LU, xroot, nroot * nroot * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    timed(RSRS_K_ROOT, [&] {
-      launch_dense_lu(L, f->root_LU, nroot, f->root_piv, err);
-      launch_dense_inverse(L, f->root_LU, f->root_piv, nroot, f->root_inv);
-    });
-    const double nr = (double)nroot;
-    f->stats.class_gflop[RSRS_K_ROOT] = (2.0 * nr * (nr + 1) * s + nr * nr * nr / 3.0 + 2.0 * nr * nr * s +
-                                         2.0 * nr * nr * nr + 2.0 * nr * nr * nr / 3.0) * 1e-9;
+    ga.nbox = nprob;
+    ga.fp32 = 0;  // the root blocks are extracted in FP64
+    bool any = false;
+    for (const BoxDesc& d : rh) any = any || d.l > 0;
+    if (any) {
+      timed(RSRS_K_ROOT, [&] {
+        launch_copy_segments(L, segs_dev + root_seg_off, (int)root_nseg, act, iwork);
+        launch_gather_box(L, ga, items_gather(rh));
+        launch_gram(L, ga, items_gram(rh));
+        for (int pn = 0; pn < max_root_panels; ++pn) {
+          launch_chol_panel(L, ga, pn);
+          launch_chol_trsm(L, ga, pn, items_chol_trsm(rh, pn));
+          launch_chol_update(L, ga, pn, items_chol_update(rh, pn));
+        }
+        // two least-squares passes: the second solves for the residual of the first, so that the
+        // normal equations' squared conditioning (Om_Bt can be square when s = |B_t|) is corrected
+        launch_proj_nt(L, ga, 0, items_proj_nt(rh));
+        launch_proj_solve(L, ga, 0, items_proj_solve(rh));
+        launch_proj_acc(L, ga, 0, items_proj_acc(rh, s));
+        launch_proj_nt(L, ga, 1, items_proj_nt(rh));
+        launch_proj_solve(L, ga, 1, items_proj_solve(rh));
+      });
+    }
+    for (int p = 0; p < nprob; ++p) {
+      const int64_t nroot = F[p]->root_size;
+      if (nroot == 0) continue;
+      const double* xroot = reinterpret_cast<const double*>(workc) + rh[p].x_off;
+      CU(cudaMemcpyAsync(F[p]->root_idx, iwork + root_iw_off[p], nroot * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                         st));
+      CU(cudaMemcpyAsync(F[p]->root_A, xroot, nroot * nroot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      CU(cudaMemcpyAsync(F[p]->root_LU, xroot, nroot * nroot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      timed(RSRS_K_ROOT, [&] {
+        launch_dense_lu(L, F[p]->root_LU, nroot, F[p]->root_piv, err);
+        launch_dense_inverse(L, F[p]->root_LU, F[p]->root_piv, nroot, F[p]->root_inv);
+      });
+      const double nr = (double)nroot;
+      bst.class_gflop[RSRS_K_ROOT] += (2.0 * nr * (nr + 1) * s + nr * nr * nr / 3.0 + 2.0 * nr * nr * s +
+                                       2.0 * nr * nr * nr + 2.0 * nr * nr * nr / 3.0 + 2.0 * nr * nr * nr) *
+                                      1e-9;
+    }
   }
   CU(cudaEventRecord(ev[3], st));
   CU(cudaGetLastError());
@@ -730,42 +886,70 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
   for (const Rec& rc : recs) {
     float ms = 0.f;
     CU(cudaEventElapsedTime(&ms, rc.a, rc.b));
-    f->stats.class_ms[rc.cls] += ms;
+    bst.class_ms[rc.cls] += ms;
   }
-  f->stats.n = N;
-  f->stats.s = s;
-  f->stats.k = k;
-  f->stats.n_boxes = (int64_t)all_desc.size();
-  f->stats.root_size = nroot;
-  f->stats.factor_bytes = fd_total * 8 + fi_total * 4 + nroot * nroot * 24 + nroot * 8;
-  f->stats.work_bytes = work_max * 8 + workc_max * (int64_t)ct_bytes + iwork_max * 4 + 4 * NS * 8;
-  f->stats.t_sample_ms = t01;
-  f->stats.t_compress_ms = t12;
-  f->stats.t_root_ms = t23;
-  f->stats.kernel_launches = launches;
-  // keep what the factor owns
-  for (void* p : {(void*)f->fd, (void*)f->fi, (void*)f->root_idx, (void*)f->root_A, (void*)f->root_LU,
-                  (void*)f->root_piv, (void*)f->root_inv, (void*)f->desc_dev, (void*)f->perm_dev,
-                  (void*)f->pts_dev})
-    pool.release(p);
-  if (o.keep_sketches) {
-    f->Y = Y;
-    f->Z = Z;
-    f->Om = Om;
-    f->Ps = Ps;
-    for (void* p : {(void*)Y, (void*)Z, (void*)Om, (void*)Ps}) pool.release(p);
+  bst.s = s;
+  bst.k = k;
+  bst.t_sample_ms = t01;
+  bst.t_compress_ms = t12;
+  bst.t_root_ms = t23;
+  bst.kernel_launches = launches;
+  bst.work_bytes = work_max * 8 + workc_max * (int64_t)ct_bytes + iwork_max * 4 + 4 * NS * 8;
+  // per-problem views of the launch groups
+  for (const LaunchGroup& g : groups)
+    for (size_t q = 0; q < g.prob_first.size(); ++q) {
+      const int p = g.prob_first[q].first;
+      const int64_t a0 = g.prob_first[q].second;
+      const int64_t a1 = (q + 1 < g.prob_first.size()) ? g.prob_first[q + 1].second : (int64_t)g.h.size();
+      GroupView v;
+      v.level = trees[p]->t.depth - g.height;
+      v.colour = g.colour;
+      v.desc_off = g.desc_off + a0;
+      v.h.assign(g.h.begin() + a0, g.h.begin() + a1);
+      v.max_r = 0;
+      for (const BoxDesc& d : v.h) v.max_r = std::max<int>(v.max_r, d.r);
+      F[p]->max_r = std::max(F[p]->max_r, v.max_r);
+      F[p]->groups.push_back(std::move(v));
+    }
+  for (int p = 0; p < nprob; ++p) {
+    rsrs_factor* f = F[p].get();
+    f->stats = bst;
+    f->stats.n = f->n;
+    f->stats.root_size = f->root_size;
+    int64_t nb = 0, fdb = 0, fib = 0;
+    for (const GroupView& v : f->groups)
+      for (const BoxDesc& d : v.h) {
+        ++nb;
+        fdb += fd_size(d.kp, d.r, d.n);
+        fib += fi_size(d.kp, d.r, d.n);
+      }
+    f->stats.n_boxes = nb;
+    f->stats.factor_bytes = fdb * 8 + fib * 4 + f->root_size * f->root_size * 24 + f->root_size * 8;
+    out[p] = F[p].release();
   }
-  *out = f.release();
   return RSRS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, int s, const rsrs_options* opts,
+                       void* stream, rsrs_factor** out) {
+  if (!out) return fail(RSRS_E_INVAL, "out is null");
+  *out = nullptr;
+  if (!tree || !op) return fail(RSRS_E_INVAL, "build: null tree or operator");
+  return build_impl(1, &tree, op, k, s, opts, stream, out);
+}
+
+rsrs_status rsrs_build_batched(int nprob, const rsrs_tree* const* trees, const rsrs_operator* ops, int k, int s,
+                               const rsrs_options* opts, void* stream, rsrs_factor** out) {
+  return build_impl(nprob, trees, ops, k, s, opts, stream, out);
 }
 
 void rsrs_factor_free(rsrs_factor* f) {
   if (!f) return;
-  for (void* p : {(void*)f->fd, (void*)f->fi, (void*)f->root_idx, (void*)f->root_A, (void*)f->root_LU,
-                  (void*)f->root_piv, (void*)f->root_inv, (void*)f->desc_dev, (void*)f->perm_dev,
-                  (void*)f->pts_dev, (void*)f->Y, (void*)f->Z, (void*)f->Om, (void*)f->Ps, (void*)f->Amat})
-    if (p) cudaFree(p);
-  delete f;
+  delete f;  // shared device storage goes with the last factor of its build
 }
 
 }  // extern "C"
@@ -780,8 +964,9 @@ rsrs_status sweep_solve(const rsrs_factor* f, Launch L, double* W, int nrhs, int
   a.F = W;
   a.nrhs = nrhs;
   a.adjoint = adjoint;
+  a.row_base = f->base;
   // upward: V_1^-1 first (V^-1 = L E), or W^-* = U^* F^* for the adjoint
-  for (const Group& g : f->groups) {
+  for (const GroupView& g : f->groups) {
     a.desc = f->desc_dev + g.desc_off;
     a.nbox = (int)g.h.size();
     launch_sweep_op(L, a, /*C=R*/ 0, /*T*/ 0, /*trans*/ 1, /*B=S*/ 1, -1.0, items_sweep(g.h, 0));
@@ -790,14 +975,14 @@ rsrs_status sweep_solve(const rsrs_factor* f, Launch L, double* W, int nrhs, int
     else
       launch_sweep_op(L, a, 2, /*Uc*/ 2, 1, 0, -1.0, items_sweep(g.h, 2));
   }
-  for (const Group& g : f->groups) {
+  for (const GroupView& g : f->groups) {
     a.desc = f->desc_dev + g.desc_off;
     a.nbox = (int)g.h.size();
     launch_sweep_diag(L, a, 1, items_diag(g.h, nrhs), g.max_r);
   }
-  if (f->root_size > 0) launch_dense_apply(L, f->root_inv, f->root_size, f->root_idx, W, nrhs, adjoint);
+  if (f->root_size > 0) launch_dense_apply(L, f->root_inv, f->root_size, f->root_idx, f->base, W, nrhs, adjoint);
   for (auto it = f->groups.rbegin(); it != f->groups.rend(); ++it) {
-    const Group& g = *it;
+    const GroupView& g = *it;
     a.desc = f->desc_dev + g.desc_off;
     a.nbox = (int)g.h.size();
     if (!adjoint)
@@ -817,7 +1002,8 @@ rsrs_status sweep_apply(const rsrs_factor* f, Launch L, double* W, int nrhs, int
   a.F = W;
   a.nrhs = nrhs;
   a.adjoint = adjoint;
-  for (const Group& g : f->groups) {  // W_1 first: F^-1 then U^-1 (or V^*: E^-* then L^-*)
+  a.row_base = f->base;
+  for (const GroupView& g : f->groups) {  // W_1 first: F^-1 then U^-1 (or V^*: E^-* then L^-*)
     a.desc = f->desc_dev + g.desc_off;
     a.nbox = (int)g.h.size();
     launch_sweep_op(L, a, 1, 0, 0, 0, 1.0, items_sweep(g.h, 1));
@@ -826,14 +1012,14 @@ rsrs_status sweep_apply(const rsrs_factor* f, Launch L, double* W, int nrhs, int
     else
       launch_sweep_op(L, a, 0, 1, 0, 2, 1.0, items_sweep(g.h, 0));
   }
-  for (const Group& g : f->groups) {
+  for (const GroupView& g : f->groups) {
     a.desc = f->desc_dev + g.desc_off;
     a.nbox = (int)g.h.size();
     launch_sweep_diag(L, a, 0, items_diag(g.h, nrhs), g.max_r);
   }
-  if (f->root_size > 0) launch_dense_apply(L, f->root_A, f->root_size, f->root_idx, W, nrhs, adjoint);
+  if (f->root_size > 0) launch_dense_apply(L, f->root_A, f->root_size, f->root_idx, f->base, W, nrhs, adjoint);
   for (auto it = f->groups.rbegin(); it != f->groups.rend(); ++it) {  // V_M first: L^-1 then E^-1
-    const Group& g = *it;
+    const GroupView& g = *it;
     a.desc = f->desc_dev + g.desc_off;
     a.nbox = (int)g.h.size();
     if (!adjoint)
@@ -933,18 +1119,6 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_
     CU(pool.alloc(&c1, tot));
     CU(pool.alloc(&c2, tot));
   }
-  // FP64 operator matrix for the residuals, once per factor, when it fits the budget
-  if (f->kind != RSRS_OP_CALLBACK && !f->Amat && nrhs <= 16 && f->amat_budget > 0 &&
-      (double)f->n * f->n * 8.0 <= (double)f->amat_budget) {
-    rsrs_factor* fm = const_cast<rsrs_factor*>(f);
-    if (cudaMalloc((void**)&fm->Amat, (size_t)f->n * f->n * sizeof(double)) == cudaSuccess) {
-      launch_operator_matrix(L, f->kind, f->pts_dev, f->d, f->n, f->shift, f->scale, fm->Amat);
-      CU(cudaGetLastError());
-    } else {
-      fm->Amat = nullptr;
-      cudaGetLastError();  // not enough memory: evaluate on the fly
-    }
-  }
   k_cm_to_rows<<<nblk(tot), 256, 0, st>>>(B, ld, f->perm_dev, f->n, nrhs, Wb);
   CU(cudaMemcpyAsync(Wx, Wb, tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
   r = sweep_solve(f, L, Wx, nrhs, 0);
@@ -994,7 +1168,7 @@ rsrs_status rsrs_factor_stats(const rsrs_factor* f, rsrs_stats* out) {
 rsrs_status rsrs_factor_box(const rsrs_factor* f, int64_t i, rsrs_box_view* v) {
   if (!f || !v || i < 0) return fail(RSRS_E_INVAL, "null argument");
   int64_t acc = 0;
-  for (const Group& g : f->groups) {
+  for (const GroupView& g : f->groups) {
     if (i < acc + (int64_t)g.h.size()) {
       const BoxDesc& d = g.h[i - acc];
       v->level = g.level;
@@ -1006,7 +1180,7 @@ rsrs_status rsrs_factor_box(const rsrs_factor* f, int64_t i, rsrs_box_view* v) {
       const int64_t w = (int64_t)d.kp + d.n;
       std::vector<int32_t> idx(fi_size(d.kp, d.r, d.n));
       CU(cudaMemcpy(idx.data(), f->fi + d.fi_off, idx.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
-      auto orig = [&](int32_t t) { return f->perm[t]; };
+      auto orig = [&](int32_t t) { return f->perm[t - f->base]; };
       if (v->R)
         for (int q = 0; q < d.r; ++q) v->R[q] = orig(idx[q]);
       if (v->S)
@@ -1045,7 +1219,7 @@ rsrs_status rsrs_factor_root(const rsrs_factor* f, int64_t* idx, double* A, int6
   if (idx && f->root_size) {
     std::vector<int32_t> t(f->root_size);
     CU(cudaMemcpy(t.data(), f->root_idx, t.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    for (int64_t q = 0; q < f->root_size; ++q) idx[q] = f->perm[t[q]];
+    for (int64_t q = 0; q < f->root_size; ++q) idx[q] = f->perm[t[q] - f->base];
   }
   if (A && f->root_size)
     CU(cudaMemcpy(A, f->root_A, f->root_size * f->root_size * sizeof(double), cudaMemcpyDeviceToHost));
@@ -1056,7 +1230,8 @@ rsrs_status rsrs_factor_sketches(const rsrs_factor* f, double* Yh, double* Zh, d
   if (!f || !f->Y) return fail(RSRS_E_INVAL, "sketches were not kept (keep_sketches = 0)");
   const int64_t N = f->n, s = f->s;
   std::vector<double> tmp(N * s);
-  const double* src[4] = {f->Y, f->Z, f->Om, f->Ps};
+  const int64_t off = f->base * s;
+  const double* src[4] = {f->Y + off, f->Z + off, f->Om + off, f->Ps + off};
   double* dst[4] = {Yh, Zh, Omh, Psh};
   for (int m = 0; m < 4; ++m) {
     if (!dst[m]) continue;

@@ -247,74 +247,6 @@ __global__ void __launch_bounds__(256) k_kmv64n(const double* __restrict__ pts, 
   }
 }
 
-// The operator matrix A = shift*I + scale*K materialized in FP64, row-major in tree order.
-template <int KIND, int D>
-__global__ void __launch_bounds__(256) k_amat64(const double* __restrict__ pts, int64_t n, double shift,
-                                                double scale, double* __restrict__ A) {
-  const int64_t j = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
-  const int64_t i0 = (int64_t)blockIdx.y * 32;
-  if (j >= n) return;
-  double pj[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) pj[k] = pts[j * D + k];
-  for (int ii = threadIdx.x >> 5; ii < 32; ii += 8) {
-    const int64_t i = i0 + ii;
-    if (i >= n) break;
-    double v;
-    if (i == j) {
-      v = shift;
-    } else {
-      double r2 = 0.0;
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        double dd = pts[i * D + k] - pj[k];
-        r2 = fma(dd, dd, r2);
-      }
-      v = scale * kval<KIND>(r2);
-    }
-    A[i * n + j] = v;
-  }
-}
-
-// out = A x for a stored FP64 matrix and at most 16 columns: 128 rows x 16 columns per CTA.
-__global__ void __launch_bounds__(256) k_gemv64n(const double* __restrict__ A, int64_t n,
-                                                 const double* __restrict__ in, int64_t ld_in,
-                                                 double* __restrict__ out, int64_t ld_out, int64_t ncols) {
-  __shared__ double As[JK3][RM3 + 1];
-  __shared__ double Xs[JK3][CN3];
-  const int tid = threadIdx.x, tc = tid & 15, tr = tid >> 4;
-  const int64_t i0 = (int64_t)blockIdx.x * RM3, c0 = (int64_t)blockIdx.y * CN3;
-  double acc[8] = {};
-  for (int64_t j0 = 0; j0 < n; j0 += JK3) {
-#pragma unroll
-    for (int u = 0; u < (RM3 * JK3) / 256; ++u) {
-      int e = tid + 256 * u;
-      int i = e / JK3, jj = e % JK3;  // 32 consecutive columns of one row per 32 threads
-      int64_t gi = i0 + i, gj = j0 + jj;
-      As[jj][i] = (gi < n && gj < n) ? A[gi * n + gj] : 0.0;
-    }
-    for (int e = tid; e < JK3 * CN3; e += 256) {
-      int jj = e / CN3, c = e % CN3;
-      int64_t gj = j0 + jj, gc = c0 + c;
-      Xs[jj][c] = (gj < n && gc < ncols) ? in[gj * ld_in + gc] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int jj = 0; jj < JK3; ++jj) {
-      double x = Xs[jj][tc];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) acc[u] = fma(As[jj][tr + 16 * u], x, acc[u]);
-    }
-    __syncthreads();
-  }
-  const int64_t gc = c0 + tc;
-  if (gc >= ncols) return;
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    int64_t gi = i0 + tr + 16 * u;
-    if (gi < n) out[gi * ld_out + gc] = acc[u];
-  }
-}
 
 }  // namespace
 
@@ -357,21 +289,6 @@ void launch_kernel_matvec_prec(Launch L, int kind, const double* pts, int d, int
 }  // namespace rsrs
 
 namespace rsrs {
-void launch_operator_matrix(Launch L, int kind, const double* pts, int d, int64_t n, double shift, double scale,
-                            double* A) {
-  dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
-  if (kind == RSRS_OP_LOG2D)
-    k_amat64<RSRS_OP_LOG2D, 2><<<grid, 256, 0, L.st>>>(pts, n, shift, scale, A);
-  else
-    k_amat64<RSRS_OP_INVR3D, 3><<<grid, 256, 0, L.st>>>(pts, n, shift, scale, A);
-  if (L.counter) ++*L.counter;
-}
-void launch_matrix_product(Launch L, const double* A, int64_t n, const double* in, int64_t ld_in, double* out,
-                           int64_t ld_out, int64_t ncols) {
-  dim3 grid((unsigned)((n + RM3 - 1) / RM3), (unsigned)((ncols + CN3 - 1) / CN3));
-  k_gemv64n<<<grid, 256, 0, L.st>>>(A, n, in, ld_in, out, ld_out, ncols);
-  if (L.counter) ++*L.counter;
-}
 }  // namespace rsrs
 
 namespace rsrs {
@@ -383,7 +300,7 @@ __global__ void k_to_f32(const double* __restrict__ in, int64_t count, float* __
 // hi/lo TF32 split of in (n x s row-major, FP64), transposed to s x n (K-major for the tensor cores),
 // through a 32 x 32 shared-memory tile so that both sides are coalesced.
 __global__ void k_split_t(const double* __restrict__ in, int64_t n, int64_t s, float* __restrict__ hi,
-                          float* __restrict__ lo) {
+                          float* __restrict__ lo, int64_t ldp) {
   __shared__ float t[32][33];
   const int64_t j0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
@@ -397,8 +314,8 @@ __global__ void k_split_t(const double* __restrict__ in, int64_t n, int64_t s, f
     if (c < s && j < n) {
       float v = t[tx][r];
       float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-      hi[c * n + j] = h;
-      lo[c * n + j] = v - h;
+      hi[c * ldp + j] = h;
+      lo[c * ldp + j] = v - h;
     }
   }
 }
@@ -407,9 +324,9 @@ void launch_to_f32(Launch L, const double* in, int64_t count, float* out) {
   k_to_f32<<<(unsigned)((count + 255) / 256), 256, 0, L.st>>>(in, count, out);
   if (L.counter) ++*L.counter;
 }
-void launch_split_transpose(Launch L, const double* in, int64_t n, int64_t s, float* hi, float* lo) {
+void launch_split_transpose(Launch L, const double* in, int64_t n, int64_t s, float* hi, float* lo, int64_t ldp) {
   dim3 grid((unsigned)((n + 31) / 32), (unsigned)((s + 31) / 32));
-  k_split_t<<<grid, 256, 0, L.st>>>(in, n, s, hi, lo);
+  k_split_t<<<grid, 256, 0, L.st>>>(in, n, s, hi, lo, ldp);
   if (L.counter) ++*L.counter;
 }
 }  // namespace rsrs

@@ -5,16 +5,23 @@
 // tensor memory.  The split follows Ootomo & Yokota (2022); products are then accurate to about
 // 2^-21 relative, the level of the FP32 arithmetic of the rest of the mixed path.
 //
-// Tile: D = 128 rows (TMEM lanes) x 256 columns (TMEM columns).  Per stage, 32 points j:
-//   A_hi, A_lo: K(x_i, x_j) for the 128 rows, generated by the CTA's threads (K-major, 128-byte
-//               rows of 32 TF32 values, 128-byte swizzle, 8-row atoms 1024 bytes apart);
-//   B_hi, B_lo: in[j][c] for the 256 columns, from hi/lo planes split and transposed once
-//               before the product (FP64 -> FP32 conversion runs at FP64 rate on this part,
-//               so it must not sit in the inner loop), copied into the same swizzled layout.
-// One thread issues the 4 K-steps x 3 products per stage and commits them to the stage's
-// mbarrier; two stages alternate so the threads fill one while the tensor cores read the other.
-// Every wait is bounded: on expiry the kernel records kDevTimeout and finishes without hanging.
+// Tile: D = 128 rows (TMEM lanes) x up to 256 columns (TMEM columns); 32 points j per stage.
+//   A_hi, A_lo: K(x_i, x_j) for the 128 rows, generated by 8 producer warps (K-major, 128-byte rows
+//               of 32 TF32 values, 128-byte swizzle, 8-row atoms 1024 bytes apart);
+//   B_hi, B_lo: in[j][c] for the tile's columns, from hi/lo planes split and transposed once
+//               before the product (FP64 -> FP32 conversion runs at FP64 rate on this part, so it
+//               must not sit in the inner loop), fetched by TMA straight into the same swizzled
+//               layout (the tensor map's 128-byte swizzle is the canonical K-major one).
+// A ninth warp issues, from one thread, the TMA copies and the 4 K-steps x 3 products per stage.
+// Two stages; per stage three mbarriers: A written (256 arrivals), B landed (TMA transaction
+// bytes) and stage free (tcgen05.commit of the products that read it).  The products of chunk c
+// are issued before the copies for chunk c+1 are armed, so the tensor pipe has work queued while
+// the next stage fills.  Every wait is bounded: on expiry the kernel records kDevTimeout, waits
+// (bounded) for its own copies still in flight, frees its TMEM and returns.
+#include <cuda.h>
+
 #include <cstdint>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -28,6 +35,8 @@ constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;     // 96 KB: A_hi, A_lo,
 constexpr int NSTAGE = 2;
 constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024;   // + alignment slack
 constexpr uint32_t TMEM_COLS = 256;
+constexpr int NPROD = 256;                                // producer threads (warps 0..7)
+constexpr int NTHREADS = NPROD + 32;                      // + the TMA / MMA warp
 constexpr long long WAIT_LIMIT = 1ll << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -53,19 +62,31 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 
 // Instruction descriptor, kind::tf32: D FP32 (bits 4..5 = 1), A and B TF32 (bits 7..9, 10..12 = 2),
 // both K-major, N >> 3 at bits 17..22, M >> 4 at bits 24..28.
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) |
-                           ((uint32_t)(TM >> 4) << 24);
+__device__ __forceinline__ uint32_t idesc_tf32(int nmma) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nmma >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate));
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
+}
+
+__device__ __forceinline__ void bar_init(uint32_t bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void bar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
 // Bounded wait for the completion of the mbarrier phase with the given parity; false on expiry.
@@ -83,6 +104,15 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
+// 2D tiled TMA load of box (TK points x TN columns) at (x = first point, y = first column).
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
 __device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
 
 template <int KIND>
@@ -91,25 +121,33 @@ __device__ __forceinline__ float kvalf_tc(float r2) {
   return rsqrtf(r2);
 }
 
+// p32: the points in FP32, n rounded up to a multiple of TK and zero padded (so that every
+// producer load of a chunk stays in bounds).  Columns [0, ncols0) read in0 / write out0, columns
+// [ncols0, ncols) read in1 / write out1 (column c - ncols0); all four are row-major with ld.
 template <int KIND, int D>
-__global__ void __launch_bounds__(256, 1) k_kmv_tc(const double* __restrict__ pts, int64_t n, double shift,
-                                                   double scale, const double* __restrict__ in, int64_t ld_in,
-                                                   const float* __restrict__ bhi, const float* __restrict__ blo,
-                                                   double* __restrict__ out, int64_t ld_out, int64_t ncols,
-                                                   int* err) {
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_kmv_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
+             const float* __restrict__ p32, int64_t n, double shift, double scale, const double* __restrict__ in0,
+             const double* __restrict__ in1, double* __restrict__ out0, double* __restrict__ out1, int64_t ld,
+             int64_t ncols0, int64_t ncols, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[NSTAGE];
+  __shared__ __align__(8) uint64_t full_a[NSTAGE], full_b[NSTAGE], empty[NSTAGE];
   __shared__ uint32_t s_tmem;
-  __shared__ float Pj[TK][D];
   __shared__ int s_timeout;
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t i0 = (int64_t)blockIdx.x * TM, c0 = (int64_t)blockIdx.y * TN;
+  const int ntile = (int)(ncols - c0 < TN ? ncols - c0 : TN);
+  const int nmma = (ntile + 15) & ~15;  // MMA N: a multiple of 16 in [16, 256]
+  const int64_t nchunk = (n + TK - 1) / TK;
 
   if (tid == 0) {
     s_timeout = 0;
-    for (int s = 0; s < NSTAGE; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[s])) : "memory");
+    for (int s = 0; s < NSTAGE; ++s) {
+      bar_init(smem_u32(&full_a[s]), NPROD);
+      bar_init(smem_u32(&full_b[s]), 1);
+      bar_init(smem_u32(&empty[s]), 1);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -123,118 +161,120 @@ __global__ void __launch_bounds__(256, 1) k_kmv_tc(const double* __restrict__ pt
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
 
-  // this thread's kernel row (A producer: row tid/2, 16 of the 32 points)
-  const int arow = tid >> 1, akh = (tid & 1) * 16;
-  float pi[D];
+  if (warp < NPROD / 32) {
+    // ---- producers: kernel values of row arow, points akh..akh+15 of each chunk ----
+    const int arow = tid >> 1, akh = (tid & 1) * 16;
+    const int64_t gi = i0 + arow;
+    float pi[D];
 #pragma unroll
-  for (int k = 0; k < D; ++k) pi[k] = (i0 + arow < n) ? (float)pts[(i0 + arow) * D + k] : 0.f;
-
-  const int64_t nchunk = (n + TK - 1) / TK;
-  for (int64_t ch = 0; ch < nchunk; ++ch) {
-    const int st = (int)(ch & 1);
-    unsigned char* base = smem + st * STAGE_BYTES;
-    unsigned char* Ahi = base;
-    unsigned char* Alo = base + A_BYTES;
-    unsigned char* Bhi = base + 2 * A_BYTES;
-    unsigned char* Blo = base + 2 * A_BYTES + B_BYTES;
-    const int64_t j0 = ch * TK;
-    // B loads first: row c = tid of the 256, 32 consecutive points of the pre-split K-major planes
-    // (128 contiguous bytes each), issued before the waits below so that their latency overlaps
-    const int bc = tid;
-    const int64_t gc = c0 + bc;
-    float4 bh[TK / 4], bl[TK / 4];
-    const bool full = (gc < ncols) && (j0 + TK <= n) && ((n & 3) == 0);
+    for (int k = 0; k < D; ++k) pi[k] = (gi < n) ? p32[gi * D + k] : 0.f;
+    for (int64_t ch = 0; ch < nchunk; ++ch) {
+      const int st = (int)(ch & 1);
+      const int64_t u = ch >> 1;
+      unsigned char* Ahi = smem + st * STAGE_BYTES;
+      unsigned char* Alo = Ahi + A_BYTES;
+      const int64_t j0 = ch * TK + akh;
+      float pj[16 * D];
+      const float4* src = reinterpret_cast<const float4*>(p32 + j0 * D);
 #pragma unroll
-    for (int q = 0; q < TK / 4; ++q) {
-      if (full) {
-        bh[q] = __ldg(reinterpret_cast<const float4*>(bhi + gc * n + j0) + q);
-        bl[q] = __ldg(reinterpret_cast<const float4*>(blo + gc * n + j0) + q);
-      } else {
-        float h[4], w[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int64_t gj = j0 + q * 4 + u;
-          const bool ok = gc < ncols && gj < n;
-          h[u] = ok ? bhi[gc * n + gj] : 0.f;
-          w[u] = ok ? blo[gc * n + gj] : 0.f;
-        }
-        bh[q] = make_float4(h[0], h[1], h[2], h[3]);
-        bl[q] = make_float4(w[0], w[1], w[2], w[3]);
+      for (int q = 0; q < 4 * D; ++q) {
+        const float4 v = __ldg(src + q);
+        pj[4 * q] = v.x;
+        pj[4 * q + 1] = v.y;
+        pj[4 * q + 2] = v.z;
+        pj[4 * q + 3] = v.w;
       }
-    }
-    // the tensor cores must be done with this stage (its previous use, two chunks ago)
-    if (ch >= NSTAGE) {
-      if (!bar_wait(smem_u32(&bars[st]), (uint32_t)(((ch >> 1) - 1) & 1))) atomicExch(&s_timeout, 1);
-    }
-    if (tid < TK * D) {
-      int j = tid / D, k = tid % D;
-      Pj[j][k] = (j0 + j < n) ? (float)pts[(j0 + j) * D + k] : 0.f;
-    }
-    __syncthreads();
-    // A: kernel values, 16 consecutive points per thread = 4 swizzle chunks of 4 values
-    {
-      const int64_t gi = i0 + arow;
+      // the products of chunk ch - 2 must be done with this stage
+      if (ch >= NSTAGE && !bar_wait(smem_u32(&empty[st]), (uint32_t)((u - 1) & 1))) s_timeout = 1;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         float hv[4], lv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int kk = akh + q * 4 + u;
+        for (int w = 0; w < 4; ++w) {
+          const int kk = q * 4 + w;
           const int64_t gj = j0 + kk;
           float v = 0.f;
           if (gi < n && gj < n && gi != gj) {
             float r2 = 0.f;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-              float dd = pi[k] - Pj[kk][k];
+              const float dd = pi[k] - pj[kk * D + k];
               r2 = fmaf(dd, dd, r2);
             }
             v = kvalf_tc<KIND>(r2);
           }
-          hv[u] = tf32_hi(v);
-          lv[u] = v - hv[u];
+          hv[w] = tf32_hi(v);
+          lv[w] = v - hv[w];
         }
         const uint32_t off = sw128(arow, akh + q * 4);
         *reinterpret_cast<float4*>(Ahi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
         *reinterpret_cast<float4*>(Alo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
       }
+      // generic-proxy writes must be visible to the tensor cores (async proxy)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bar_arrive(smem_u32(&full_a[st]));
     }
-    // B: already split and K-major; 16-byte chunks into the swizzled rows
-#pragma unroll
-    for (int q = 0; q < TK / 4; ++q) {
-      const uint32_t off = sw128(bc, q * 4);
-      *reinterpret_cast<float4*>(Bhi + off) = bh[q];
-      *reinterpret_cast<float4*>(Blo + off) = bl[q];
-    }
-    // generic-proxy writes must be visible to the tensor cores (async proxy)
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+  } else if (lane == 0) {
+    // ---- TMA + MMA issue ----
+    const uint32_t idesc = idesc_tf32(nmma);
+    bool armed[NSTAGE] = {false, false};
+    uint32_t armed_par[NSTAGE] = {0u, 0u};
+    bool ok = true;
+    auto arm = [&](int64_t ch) {
+      const int st = (int)(ch & 1);
+      unsigned char* Bhi = smem + st * STAGE_BYTES + 2 * A_BYTES;
+      const uint32_t bar = smem_u32(&full_b[st]);
+      bar_expect_tx(bar, 2u * B_BYTES);
+      tma_load_2d(smem_u32(Bhi), &tm_hi, (int)(ch * TK), (int)c0, bar);
+      tma_load_2d(smem_u32(Bhi + B_BYTES), &tm_lo, (int)(ch * TK), (int)c0, bar);
+      armed[st] = true;
+      armed_par[st] = (uint32_t)((ch >> 1) & 1);
+    };
+    if (nchunk > 0) arm(0);
+    for (int64_t ch = 0; ch < nchunk; ++ch) {
+      const int st = (int)(ch & 1);
+      const uint32_t par = (uint32_t)((ch >> 1) & 1);
+      if (!bar_wait(smem_u32(&full_b[st]), par)) ok = false;
+      else armed[st] = false;
+      if (!bar_wait(smem_u32(&full_a[st]), par)) ok = false;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a_hi = smem_u32(Ahi), a_lo = smem_u32(Alo), b_hi = smem_u32(Bhi), b_lo = smem_u32(Blo);
+      unsigned char* base = smem + st * STAGE_BYTES;
+      const uint32_t a_hi = smem_u32(base), a_lo = a_hi + A_BYTES;
+      const uint32_t b_hi = a_hi + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
 #pragma unroll
       for (int kk = 0; kk < TK / 8; ++kk) {  // K = 8 TF32 values (32 bytes) per instruction
         const uint32_t ko = kk * 32;
-        mma_tf32(tmem, smem_desc(a_hi + ko), smem_desc(b_hi + ko), (ch > 0 || kk > 0) ? 1u : 0u);
-        mma_tf32(tmem, smem_desc(a_hi + ko), smem_desc(b_lo + ko), 1u);
-        mma_tf32(tmem, smem_desc(a_lo + ko), smem_desc(b_hi + ko), 1u);
+        mma_tf32(tmem, smem_desc(a_hi + ko), smem_desc(b_hi + ko), idesc, (ch > 0 || kk > 0) ? 1u : 0u);
+        mma_tf32(tmem, smem_desc(a_hi + ko), smem_desc(b_lo + ko), idesc, 1u);
+        mma_tf32(tmem, smem_desc(a_lo + ko), smem_desc(b_hi + ko), idesc, 1u);
       }
-      mma_commit(smem_u32(&bars[st]));
+      mma_commit(smem_u32(&empty[st]));
+      if (ch + 1 < nchunk) {
+        // the other stage is free once the products of chunk ch - 1 are done
+        if (ch >= 1 && !bar_wait(smem_u32(&empty[st ^ 1]), (uint32_t)(((ch - 1) >> 1) & 1))) ok = false;
+        arm(ch + 1);
+      }
+    }
+    if (!ok) {
+      s_timeout = 1;
+      for (int s = 0; s < NSTAGE; ++s)  // copies still in flight must land before the CTA exits
+        if (armed[s]) bar_wait(smem_u32(&full_b[s]), armed_par[s]);
     }
   }
-  // wait for the last stage's products (commits complete in issue order)
+  if (warp == NPROD / 32) __syncwarp();  // lanes 1..31 of the issuing warp wait here, not spinning
+  // every thread: the last commit completes after all earlier products
   if (nchunk > 0) {
     const int64_t last = nchunk - 1;
-    if (!bar_wait(smem_u32(&bars[last & 1]), (uint32_t)((last >> 1) & 1))) atomicExch(&s_timeout, 1);
+    if (!bar_wait(smem_u32(&empty[last & 1]), (uint32_t)((last >> 1) & 1))) s_timeout = 1;
   }
-  __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  // epilogue: warp w reads TMEM lanes 32*(w%4).. (its rows), columns (w/4)*128 .. +128
-  {
+  if (warp < NPROD / 32 && nchunk > 0) {
+    // epilogue: warp w reads TMEM lanes 32*(w%4).. (its rows), columns (w/4)*128 .. +128
     const int row = 32 * (warp & 3) + lane;
     const int64_t gi = i0 + row;
     const int colbase = (warp >> 2) * 128;
     for (int cc = 0; cc < 128; cc += 16) {
+      if (colbase + cc >= nmma) break;  // warp-uniform
       uint32_t r[16];
       const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(colbase + cc);
       asm volatile(
@@ -249,7 +289,13 @@ __global__ void __launch_bounds__(256, 1) k_kmv_tc(const double* __restrict__ pt
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           const int64_t gc = c0 + colbase + cc + q;
-          if (gc < ncols) out[gi * ld_out + gc] = shift * in[gi * ld_in + gc] + scale * (double)__uint_as_float(r[q]);
+          if (gc < ncols) {
+            const bool first = gc < ncols0;
+            const int64_t c = first ? gc : gc - ncols0;
+            const double* in = first ? in0 : in1;
+            double* out = first ? out0 : out1;
+            out[gi * ld + c] = shift * in[gi * ld + c] + scale * (double)__uint_as_float(r[q]);
+          }
         }
       }
     }
@@ -260,26 +306,77 @@ __global__ void __launch_bounds__(256, 1) k_kmv_tc(const double* __restrict__ pt
   if (tid == 0 && s_timeout && err) atomicCAS(err, 0, kDevTimeout);
 }
 
+// Points in FP32, zero padded to a multiple of TK points.
+__global__ void k_points_f32(const double* __restrict__ pts, int64_t n, int d, int64_t npad, float* __restrict__ out) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= npad * d) return;
+  out[e] = e < n * d ? (float)pts[e] : 0.f;
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+  static EncodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  });
+  return fn;
+}
+
+// Tensor map of one plane: ncols rows of n FP32 values, row pitch ldp values (ldp % 4 == 0 so that
+// the pitch is a multiple of 16 bytes); box = TK values x TN rows, 128-byte swizzle, zero fill
+// outside [0, n) x [0, ncols).
+bool plane_map(CUtensorMap* m, const float* base, int64_t n, int64_t ncols, int64_t ldp) {
+  EncodeTiled enc = encode_fn();
+  if (!enc || (ldp & 3) || ((uintptr_t)base & 15)) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)ncols};
+  cuuint64_t strides[1] = {(cuuint64_t)ldp * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)TN};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
-void launch_kernel_matvec_tc(Launch L, int kind, const double* pts, int d, int64_t n, double shift, double scale,
-                             const double* in, int64_t ld_in, const float* bhi, const float* blo, double* out,
-                             int64_t ld_out, int64_t ncols, int* err) {
-  if (n <= 0 || ncols <= 0) return;
-  static bool attr = false;
-  if (!attr) {
+int64_t tc_plane_ld(int64_t n) { return (n + 3) & ~(int64_t)3; }
+int64_t tc_points_len(int64_t n, int d) { return ((n + TK - 1) / TK) * TK * d; }
+
+void launch_points_f32(Launch L, const double* pts, int64_t n, int d, float* out) {
+  const int64_t npad = (n + TK - 1) / TK * TK;
+  k_points_f32<<<(unsigned)((npad * d + 255) / 256), 256, 0, L.st>>>(pts, n, d, npad, out);
+  if (L.counter) ++*L.counter;
+}
+
+bool launch_kernel_matvec_tc(Launch L, int kind, const float* p32, int64_t n, double shift, double scale,
+                             const double* in0, const double* in1, double* out0, double* out1, int64_t ld,
+                             int64_t ncols0, int64_t ncols, const float* bhi, const float* blo, int64_t ldp, int* err) {
+  if (n <= 0 || ncols <= 0) return true;
+  CUtensorMap mh, ml;
+  if (!plane_map(&mh, bhi, n, ncols, ldp) || !plane_map(&ml, blo, n, ncols, ldp)) return false;
+  static std::once_flag attr;
+  std::call_once(attr, [] {
     cudaFuncSetAttribute(k_kmv_tc<RSRS_OP_LOG2D, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     cudaFuncSetAttribute(k_kmv_tc<RSRS_OP_INVR3D, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    attr = true;
-  }
+  });
   dim3 grid((unsigned)((n + TM - 1) / TM), (unsigned)((ncols + TN - 1) / TN));
   if (kind == RSRS_OP_LOG2D)
-    k_kmv_tc<RSRS_OP_LOG2D, 2><<<grid, 256, SMEM_BYTES, L.st>>>(pts, n, shift, scale, in, ld_in, bhi, blo, out, ld_out,
-                                                                ncols, err);
+    k_kmv_tc<RSRS_OP_LOG2D, 2><<<grid, NTHREADS, SMEM_BYTES, L.st>>>(mh, ml, p32, n, shift, scale, in0, in1, out0,
+                                                                     out1, ld, ncols0, ncols, err);
   else
-    k_kmv_tc<RSRS_OP_INVR3D, 3><<<grid, 256, SMEM_BYTES, L.st>>>(pts, n, shift, scale, in, ld_in, bhi, blo, out,
-                                                                 ld_out, ncols, err);
+    k_kmv_tc<RSRS_OP_INVR3D, 3><<<grid, NTHREADS, SMEM_BYTES, L.st>>>(mh, ml, p32, n, shift, scale, in0, in1, out0,
+                                                                      out1, ld, ncols0, ncols, err);
   if (L.counter) ++*L.counter;
+  return true;
 }
 
 }  // namespace rsrs

@@ -12,7 +12,8 @@
 //    field is not empty; same-level boxes are processed colour by colour, the
 //    colours from a greedy colouring in Morton order where boxes with
 //    intersecting closed neighbourhoods conflict; Morton order inside a colour;
-//  * s_req = max(max over compressed boxes of b + n + k + p, |B_t|).
+//  * s_req = max(max over compressed boxes of b + n + k + p, |B_t| + p): the root's least-squares
+//    problem is oversampled by p like the boxes', which keeps Omega_Bt well conditioned.
 #include "tree.h"
 
 #include <algorithm>
@@ -280,7 +281,7 @@ void build_schedule(const Tree& t, int k, int p, Schedule& s) {
     for (int b : t.levels[1]) root_size += s.act1[b];
   else
     root_size = t.n;
-  s.s_req = std::max<int64_t>(s.steps.empty() ? 0 : s.max_l + s.k + s.p, root_size);
+  s.s_req = std::max<int64_t>(s.steps.empty() ? 0 : s.max_l + s.k + s.p, root_size + s.p);
   s.root.resize(root_size);  // filled with tree positions by the device build
 }
 

@@ -23,7 +23,7 @@ STATUS = {0: "RSRS_OK", 1: "RSRS_E_INVAL", 2: "RSRS_E_UNDERSAMPLED", 3: "RSRS_E_
           8: "RSRS_E_TIMEOUT", 9: "RSRS_E_NOT_CONVERGED"}
 
 EXPORTS = ["rsrs_tree_build", "rsrs_tree_info", "rsrs_tree_perm", "rsrs_tree_schedule", "rsrs_tree_free",
-           "rsrs_build", "rsrs_solve", "rsrs_apply", "rsrs_refine", "rsrs_matvec", "rsrs_factor_stats",
+           "rsrs_build", "rsrs_build_batched", "rsrs_solve", "rsrs_apply", "rsrs_refine", "rsrs_matvec", "rsrs_factor_stats",
            "rsrs_factor_box", "rsrs_factor_root", "rsrs_factor_sketches", "rsrs_factor_free",
            "rsrs_status_string", "rsrs_last_error", "rsrs_kernel_class_name"]
 
@@ -40,7 +40,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("p", C.c_int), ("proj_passes", C.c_int), ("seed", C.c_uint64),
                 ("omega_host", C.c_void_p), ("psi_host", C.c_void_p), ("omega_dev", C.c_void_p),
                 ("psi_dev", C.c_void_p), ("keep_sketches", C.c_int), ("profile", C.c_int),
-                ("sample_kernel", C.c_int), ("residual_matrix_bytes", C.c_int64)]
+                ("sample_kernel", C.c_int), ("mixed_cpqr", C.c_int)]
 
 
 NCLASS = 16
@@ -87,6 +87,8 @@ def lib():
             "rsrs_tree_perm": [vp, vp],
             "rsrs_tree_schedule": [vp, C.c_int, C.c_int, vp],
             "rsrs_build": [vp, C.POINTER(Operator), C.c_int, C.c_int, C.POINTER(Options), vp, C.POINTER(vp)],
+            "rsrs_build_batched": [C.c_int, C.POINTER(vp), C.POINTER(Operator), C.c_int, C.c_int, C.POINTER(Options),
+                                   vp, C.POINTER(vp)],
             "rsrs_solve": [vp, vp, i64, i32, C.c_int, vp],
             "rsrs_apply": [vp, vp, i64, i32, C.c_int, vp],
             "rsrs_refine": [vp, vp, vp, i64, i32, dbl, C.c_int, vp, C.POINTER(RefineReport)],
@@ -187,8 +189,8 @@ class Factor:
     def __init__(self, tree: Tree, kind: int, k: int, s: int, shift: float = 1.0, scale: float = 0.0,
                  precision: int = RSRS_PREC_FP64, p: int = -1, omega: np.ndarray | None = None,
                  psi: np.ndarray | None = None, seed: int = 0, passes: int = 0, keep_sketches: bool = False,
-                 matvec=None, stream=None, profile: bool = False, residual_matrix_bytes: int = 0,
-                 sample_kernel: int = 0):
+                 matvec=None, stream=None, profile: bool = False,
+                 sample_kernel: int = 0, mixed_cpqr: int = 0):
         self.tree = tree
         self.n = tree.n
         self._cb = None
@@ -200,7 +202,8 @@ class Factor:
             op.fn = self._cb
         opts = Options(precision=precision, p=p, proj_passes=passes, seed=seed,
                        keep_sketches=int(keep_sketches), profile=int(profile),
-                       residual_matrix_bytes=residual_matrix_bytes, sample_kernel=sample_kernel)
+                       sample_kernel=sample_kernel,
+                       mixed_cpqr=mixed_cpqr)
         self._om = self._ps = None
         if omega is not None and hasattr(omega, "data_ptr"):  # device tensors (N, s), original order
             self._om, self._ps = omega, psi
@@ -284,6 +287,32 @@ class Factor:
         if getattr(self, "_h", None) and _lib is not None:
             _lib.rsrs_factor_free(self._h)
             self._h = None
+
+
+def build_batched(trees, kinds, k: int, s: int, shifts, scales, precision: int = RSRS_PREC_FP64, p: int = -1,
+                  seed: int = 0, passes: int = 0, profile: bool = False, sample_kernel: int = 0,
+                  keep_sketches: bool = False, mixed_cpqr: int = 0,
+                  stream=None) -> list:
+    """rsrs_build_batched: factors of independent problems built in one set of launches."""
+    n = len(trees)
+    ops = (Operator * n)()
+    for i in range(n):
+        ops[i].kind = kinds[i]
+        ops[i].diag_shift = shifts[i]
+        ops[i].scale = scales[i]
+    handles = (C.c_void_p * n)(*[t._h for t in trees])
+    outs = (C.c_void_p * n)()
+    opts = Options(precision=precision, p=p, proj_passes=passes, seed=seed, profile=int(profile),
+                   sample_kernel=sample_kernel,
+                   keep_sketches=int(keep_sketches), mixed_cpqr=mixed_cpqr)
+    _check(lib().rsrs_build_batched(n, handles, ops, k, s, C.byref(opts), _stream_ptr(stream), outs))
+    res = []
+    for i in range(n):
+        f = Factor.__new__(Factor)
+        f.tree, f.n, f._cb, f._om, f._ps = trees[i], trees[i].n, None, None, None
+        f._h, f.s, f.k = C.c_void_p(outs[i]), s, k
+        res.append(f)
+    return res
 
 
 def kind_of(kernel: str) -> int:

@@ -162,12 +162,12 @@ def test_refine_fp64_reaches_dense_solution(case):
 
 
 def test_refine_on_the_fly_residual(R):
-    """Refinement with the operator evaluated on the fly (no stored FP64 matrix)."""
+    """Mixed factor refined with the FP64 residual evaluated on the fly."""
     pr = CASES["rand2d_3000"]()
     tree, sched, fac, _ = orsrs.build(pr)
     t = R.Tree(pr.points, pr.leaf)
     f = R.Factor(t, R.kind_of(pr.kernel), pr.k, fac.s, shift=pr.diag_shift, scale=pr.scale,
-                 precision=R.RSRS_PREC_MIXED, omega=pr.omega(fac.s), psi=pr.psi(fac.s), residual_matrix_bytes=-1)
+                 precision=R.RSRS_PREC_MIXED, omega=pr.omega(fac.s), psi=pr.psi(fac.s))
     b = pr.rhs()
     X = torch.zeros_like(_to_gpu(b))
     rep = f.refine(_to_gpu(b), X, rtol=1e-13, maxit=30)

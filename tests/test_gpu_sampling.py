@@ -3,7 +3,8 @@
 A tree whose root is a leaf compresses nothing, so the kept sketches are exactly the sampled
 Y = A Omega and Z = A* Psi.  The FP32 SIMT and the 3xTF32 tensor-core kernels must agree with
 the FP64 kernel on the kernel part A - I to FP32-level accuracy (1e-5 relative), on ragged
-sizes (rows not a multiple of 128, points not a multiple of 32, columns not a multiple of 256).
+sizes (rows not a multiple of 128, points not a multiple of 32 or of 4, a single partial chunk of
+points, and 2s columns [Omega Psi] ending in a partial tile of every width class).
 """
 import numpy as np
 import pytest
@@ -26,7 +27,8 @@ def R():
     return pkg
 
 
-@pytest.mark.parametrize("d,kind,n,s", [(2, "log2d", 1000, 1100), (3, "invr3d", 777, 800), (2, "log2d", 257, 300)])
+@pytest.mark.parametrize("d,kind,n,s", [(2, "log2d", 1000, 1100), (3, "invr3d", 777, 800), (2, "log2d", 257, 300),
+                                        (2, "log2d", 21, 40), (3, "invr3d", 120, 132)])
 @pytest.mark.parametrize("kernel", [1, 2])
 def test_mixed_sampling_matches_fp64(R, d, kind, n, s, kernel):
     pts = W.uniform_points(n, d, W.rng_for(98, n, 0))

@@ -211,3 +211,31 @@ def test_power_iteration_metrics_match_dense_norms():
     es_dense = np.linalg.norm(np.eye(pr.n) - _dense_of(rsrs.solve, fac, pr.n) @ a, 2)
     assert 0.5 * rel_dense <= refine.relerr(fac, op, iters=60) <= 1.01 * rel_dense
     assert 0.5 * es_dense <= refine.errsolve(fac, op, iters=60) <= 1.0001 * es_dense
+
+
+def test_root_bound_keeps_the_root_block_well_conditioned():
+    """A problem whose s_req is set by the root (|B_t| + p).  With s = |B_t| the final Omega_Bt is
+    square (Sec. 4.4 needs only s >= |B_t|) and ill conditioned, so sketch rounding at FP32 level
+    (1e-7 relative) spoils the root block; oversampled by p its condition number stays near the
+    Gaussian estimate (sqrt s + sqrt m) / (sqrt s - sqrt m), m = |B_t|, and the factor remains a
+    good preconditioner."""
+    pr = W.small_problem(n=1100, d=3, kernel="invr3d", leaf=20, k=8, nrhs=2, seed_problem=12)
+    tree = Tree(pr.points, pr.leaf)
+    sc = Schedule(tree, pr.k)
+    assert sc.s_req == sc.root_size + sc.p  # the root sets the bound here
+    a = ops.make_operator(pr).dense()
+    b = pr.rhs()
+    m = sc.root_size
+    cond, res = {}, {}
+    for s in (m, sc.s_req):
+        om, ps = pr.omega(s), pr.psi(s)
+        noise = np.random.default_rng(0)
+        y = (a @ om) * (1 + 1e-7 * noise.standard_normal((pr.n, s)))
+        z = (a.T @ ps) * (1 + 1e-7 * noise.standard_normal((pr.n, s)))
+        fac = rsrs.factor(tree, sc, y, z, om, ps)
+        cond[s] = np.linalg.cond(fac.final["Om"][fac.root])
+        res[s] = np.linalg.norm(b - a @ rsrs.solve(fac, b)) / np.linalg.norm(b)
+    s = sc.s_req
+    est = (np.sqrt(s) + np.sqrt(m)) / (np.sqrt(s) - np.sqrt(m))
+    assert cond[s] < 2 * est < 20 * est < cond[m]
+    assert res[s] < 2e-3 and res[s] < res[m]

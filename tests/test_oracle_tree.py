@@ -96,7 +96,7 @@ def test_sizes_and_root():
     tr = Tree(W.grid_points_2d(64), 64)
     sc = Schedule(tr, 32)
     assert sc.root_size == 16 * 32  # 16 level-2 boxes keep k skeletons each
-    assert sc.s_req >= sc.root_size
+    assert sc.s_req >= sc.root_size + sc.p
     # sizes are consistent: b = sum of children's k', r = b - k'
     for st in sc.steps:
         assert st["r"] == st["b"] - st["kp"] and st["kp"] == min(32, st["b"])

@@ -148,3 +148,48 @@ def small_problem(n_side: int = 0, n: int = 0, d: int = 2, kernel: str = "log2d"
         pts = uniform_points(n, d, rng_for(cfg, seed_problem, STREAM_POINTS))
     return kernel_problem(cfg, f"small_{kernel}_{pts.shape[0]}", pts, kernel, leaf, k, 0, nrhs,
                           problem=seed_problem)
+
+
+# ---- counter-based draws matching the library's device generator ---------------------------
+# Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of the multiply-xor round with
+# multipliers 0xD2511F53, 0xCD9E8D57 and key increments 0x9E3779B9, 0xBB67AE85.  Counter =
+# (q mod 2^32, q >> 32, stream, 0), key = (seed mod 2^32, seed >> 32).  Each output block gives two
+# 53-bit uniforms u1 = (a + 1) 2^-53 in (0, 1] and u2 = b 2^-53 from its two 64-bit halves, and the
+# Box-Muller pair r cos(2 pi u2), r sin(2 pi u2) with r = sqrt(-2 log u1).  Entry (i, c) of an
+# N x s test matrix is member (i*s + c) mod 2 of pair (i*s + c) // 2 (stream 0: Omega, 1: Psi).
+
+def _philox4x32_10(c0, c1, c2, c3, k0, k1):
+    m0, m1 = np.uint64(0xD2511F53), np.uint64(0xCD9E8D57)
+    w0, w1 = np.uint32(0x9E3779B9), np.uint32(0xBB67AE85)
+    mask = np.uint64(0xFFFFFFFF)
+    for _ in range(10):
+        p0 = m0 * c0.astype(np.uint64)
+        p1 = m1 * c2.astype(np.uint64)
+        n0 = (p1 >> np.uint64(32)).astype(np.uint32) ^ c1 ^ k0
+        n2 = (p0 >> np.uint64(32)).astype(np.uint32) ^ c3 ^ k1
+        c1 = (p1 & mask).astype(np.uint32)
+        c3 = (p0 & mask).astype(np.uint32)
+        c0, c2 = n0, n2
+        k0 = np.uint32((int(k0) + int(w0)) & 0xFFFFFFFF)
+        k1 = np.uint32((int(k1) + int(w1)) & 0xFFFFFFFF)
+    return c0, c1, c2, c3
+
+
+def philox_gaussian(n: int, s: int, seed: int, stream: int) -> np.ndarray:
+    """The N x s standard normal test matrix the library draws on the device for (seed, stream)."""
+    g = np.arange(n * s, dtype=np.uint64)
+    q = g >> np.uint64(1)
+    c0 = (q & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    c1 = (q >> np.uint64(32)).astype(np.uint32)
+    c2 = np.full_like(c0, np.uint32(stream))
+    c3 = np.zeros_like(c0)
+    k0 = np.uint32(seed & 0xFFFFFFFF)
+    k1 = np.uint32((seed >> 32) & 0xFFFFFFFF)
+    o0, o1, o2, o3 = _philox4x32_10(c0, c1, c2, c3, k0, k1)
+    a = ((o0.astype(np.uint64) << np.uint64(32)) | o1.astype(np.uint64)) >> np.uint64(11)
+    b = ((o2.astype(np.uint64) << np.uint64(32)) | o3.astype(np.uint64)) >> np.uint64(11)
+    u1 = (a.astype(np.float64) + 1.0) * 2.0 ** -53
+    u2 = b.astype(np.float64) * 2.0 ** -53
+    r = np.sqrt(-2.0 * np.log(u1))
+    z = np.where((g & np.uint64(1)) == 0, r * np.cos(2.0 * np.pi * u2), r * np.sin(2.0 * np.pi * u2))
+    return z.reshape(n, s)
