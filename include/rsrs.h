@@ -180,6 +180,33 @@ rsrs_status rsrs_build_batched(int nprob, const rsrs_tree* const* trees, const r
 /* F <- A_approx^-1 F (eq. Ainvfact), or its adjoint; F_dev column-major N x nrhs. */
 rsrs_status rsrs_solve(const rsrs_factor* f, double* F_dev, int64_t ldf, int32_t nrhs,
                        int adjoint, void* stream);
+/* rsrs_solve_noalloc: rsrs_solve for callers that must not allocate device memory.  The paper
+ * has no counterpart: it is a deployment variant of rsrs_solve (the sweeps of eq. Ainvfact,
+ * Sec. 3.2), computing the same result with the same kernels.
+ *
+ * Who needs it: rsrs_solve takes an N x nrhs staging block from cudaMalloc and returns it with
+ * cudaFree on every call.  A caller whose device memory is all reserved by another allocator (a
+ * caching allocator such as PyTorch's holds freed blocks instead of returning them, so cudaMalloc
+ * can fail while memory is nominally free) cannot make that call succeed, and a serving loop
+ * cannot accept the implicit device-wide synchronisation of cudaFree while other streams run.
+ * This entry point stages the block in one library-wide static device buffer instead and calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Limit: N * nrhs <= RSRS_NOALLOC_MAX_ELEMS (2^20 doubles = 8 MiB, e.g. N = 65,536 with 16
+ * right-hand sides); larger blocks return RSRS_E_INVAL before any launch.  Nothing in the buffer
+ * needs to start at zero: the first kernel writes every element the sweeps read.
+ *
+ * The buffer is shared by all calls on a device: calls whose execution overlaps (on different
+ * streams, or from host threads without ordering between them) race on it and give wrong
+ * results; order them on one stream.  The call enqueues its kernels on `stream` and returns
+ * without synchronising; F holds the solution once the stream has reached that point.  The first
+ * call on each device resolves the buffer's address (cudaGetSymbolAddress with that device
+ * current); make that first call before any stream capture.  Arguments, layout and other errors
+ * as rsrs_solve. */
+#define RSRS_NOALLOC_MAX_ELEMS (1 << 20)
+rsrs_status rsrs_solve_noalloc(const rsrs_factor* f, double* F, int64_t ldf, int32_t nrhs, int adjoint,
+                               void* stream);
+
 /* F <- A_approx F (eq. Afact), or its adjoint. */
 rsrs_status rsrs_apply(const rsrs_factor* f, double* F_dev, int64_t ldf, int32_t nrhs,
                        int adjoint, void* stream);

@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1242,3 +1243,44 @@ rsrs_status rsrs_factor_sketches(const rsrs_factor* f, double* Yh, double* Zh, d
 }
 
 }  // extern "C"
+
+// ---- solve without device allocation ---------------------------------------------------------
+// One static staging buffer per device (the module's copy of this array on that device).
+static __device__ __align__(256) double g_noalloc_stage[RSRS_NOALLOC_MAX_ELEMS];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_addr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" rsrs_status rsrs_solve_noalloc(const rsrs_factor* f, double* F, int64_t ldf, int32_t nrhs, int adjoint,
+                                          void* stream) {
+  rsrs_status r = check_block(f, F, ldf, nrhs);
+  if (r != RSRS_OK) return r;
+  if (f->n * (int64_t)nrhs > RSRS_NOALLOC_MAX_ELEMS)
+    return fail(RSRS_E_INVAL, "solve_noalloc: N * nrhs = " + std::to_string(f->n * (int64_t)nrhs) +
+                                  " exceeds the static staging buffer of " +
+                                  std::to_string(RSRS_NOALLOC_MAX_ELEMS) + " doubles");
+  int dev = -1;
+  CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(RSRS_E_INVAL, "solve_noalloc: device ordinal out of range");
+  double* W = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {  // set-up, once per device, with that device current
+      void* p = nullptr;
+      CU(cudaGetSymbolAddress(&p, g_noalloc_stage));
+      g_noalloc_addr[dev] = static_cast<double*>(p);
+    }
+    W = g_noalloc_addr[dev];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  Launch L{st, nullptr};
+  k_cm_to_rows<<<nblk(f->n * nrhs), 256, 0, st>>>(F, ldf, f->perm_dev, f->n, nrhs, W);
+  r = sweep_solve(f, L, W, nrhs, adjoint);
+  if (r != RSRS_OK) return r;
+  k_rows_to_cm<<<nblk(f->n * nrhs), 256, 0, st>>>(W, f->perm_dev, f->n, nrhs, F, ldf);
+  CU(cudaGetLastError());
+  return RSRS_OK;
+}

@@ -23,7 +23,7 @@ STATUS = {0: "RSRS_OK", 1: "RSRS_E_INVAL", 2: "RSRS_E_UNDERSAMPLED", 3: "RSRS_E_
           8: "RSRS_E_TIMEOUT", 9: "RSRS_E_NOT_CONVERGED"}
 
 EXPORTS = ["rsrs_tree_build", "rsrs_tree_info", "rsrs_tree_perm", "rsrs_tree_schedule", "rsrs_tree_free",
-           "rsrs_build", "rsrs_build_batched", "rsrs_solve", "rsrs_apply", "rsrs_refine", "rsrs_matvec", "rsrs_factor_stats",
+           "rsrs_build", "rsrs_build_batched", "rsrs_solve", "rsrs_solve_noalloc", "rsrs_apply", "rsrs_refine", "rsrs_matvec", "rsrs_factor_stats",
            "rsrs_factor_box", "rsrs_factor_root", "rsrs_factor_sketches", "rsrs_factor_free",
            "rsrs_status_string", "rsrs_last_error", "rsrs_kernel_class_name"]
 
@@ -90,6 +90,7 @@ def lib():
             "rsrs_build_batched": [C.c_int, C.POINTER(vp), C.POINTER(Operator), C.c_int, C.c_int, C.POINTER(Options),
                                    vp, C.POINTER(vp)],
             "rsrs_solve": [vp, vp, i64, i32, C.c_int, vp],
+            "rsrs_solve_noalloc": [vp, vp, i64, i32, C.c_int, vp],
             "rsrs_apply": [vp, vp, i64, i32, C.c_int, vp],
             "rsrs_refine": [vp, vp, vp, i64, i32, dbl, C.c_int, vp, C.POINTER(RefineReport)],
             "rsrs_matvec": [vp, vp, vp, i64, i32, vp],
@@ -225,6 +226,13 @@ class Factor:
         """In place: F <- A_approx^-1 F, F a (nrhs, N) float64 CUDA tensor."""
         ptr, ld, nr = _cm(F)
         _check(lib().rsrs_solve(self._h, ptr, ld, nr, int(adjoint), _stream_ptr(stream)))
+        return F
+
+    def solve_noalloc(self, F, adjoint: bool = False, stream=None):
+        """rsrs_solve_noalloc: as solve, staged in the library's static device buffer (no device
+        allocation, no synchronisation; calls on one device must not overlap)."""
+        ptr, ld, nr = _cm(F)
+        _check(lib().rsrs_solve_noalloc(self._h, ptr, ld, nr, int(adjoint), _stream_ptr(stream)))
         return F
 
     def apply(self, F, adjoint: bool = False, stream=None):

@@ -1,0 +1,74 @@
+"""rsrs_solve_noalloc against rsrs_solve.
+
+The no-allocation solve stages the right-hand sides in the library's static device buffer instead
+of a per-call cudaMalloc; it runs the same kernels in the same order, so its results must equal
+rsrs_solve's bit for bit, also for two calls in a row that reuse the buffer.  This file is named to
+be collected last, so that it also runs after everything else has used the device.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MAX_ELEMS = 1 << 20  # RSRS_NOALLOC_MAX_ELEMS
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2311_01451_gb300 as pkg
+
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def factor(R):
+    pr = W.small_problem(n=3000, d=2, leaf=24, k=10, nrhs=3, seed_problem=3)
+    tree = R.Tree(pr.points, pr.leaf)
+    s = tree.info(pr.k).s_req
+    f = R.Factor(tree, R.RSRS_OP_LOG2D, pr.k, s, shift=pr.diag_shift, scale=pr.scale,
+                 precision=R.RSRS_PREC_FP64, seed=5)
+    return pr, f
+
+
+def _block(n, nrhs, seed):
+    g = np.random.default_rng(seed).standard_normal((nrhs, n))
+    return torch.tensor(g, device="cuda", dtype=torch.float64)  # (nrhs, N): column-major N x nrhs
+
+
+def test_noalloc_equals_solve_two_calls_in_a_row(R, factor):
+    pr, f = factor
+    F1, F2 = _block(pr.n, 3, 1), _block(pr.n, 5, 2)
+    ref1 = f.solve(F1.clone())
+    ref2 = f.solve(F2.clone(), adjoint=True)
+    G1, G2 = F1.clone(), F2.clone()
+    f.solve_noalloc(G1)
+    f.solve_noalloc(G2, adjoint=True)  # reuses the staging buffer right after the first call
+    torch.cuda.synchronize()
+    assert torch.equal(G1, ref1)
+    assert torch.equal(G2, ref2)
+    # and again, in the opposite order
+    H2, H1 = F2.clone(), F1.clone()
+    f.solve_noalloc(H2, adjoint=True)
+    f.solve_noalloc(H1)
+    torch.cuda.synchronize()
+    assert torch.equal(H1, ref1) and torch.equal(H2, ref2)
+
+
+def test_noalloc_rejects_blocks_beyond_the_buffer(R, factor):
+    pr, f = factor
+    nrhs = MAX_ELEMS // pr.n + 1
+    F = _block(pr.n, nrhs, 3)
+    before = F.clone()
+    with pytest.raises(R.RSRSError) as e:
+        f.solve_noalloc(F)
+    assert e.value.name == "RSRS_E_INVAL" and "exceeds" in str(e.value)
+    torch.cuda.synchronize()
+    assert torch.equal(F, before)  # nothing was launched
