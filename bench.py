@@ -35,6 +35,43 @@ FP64_TFLOPS_NOMINAL = 1.25  # GB300 FP64 (recipe table); cuBLAS DGEMM measured 1
 FP32_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.070e-3  # SMs x FP32 lanes x 2 x max SM clock (GHz) -> TFLOP/s
 
 
+# Kernel classes that run in FP32 arithmetic in the mixed path (the rest stay FP64).
+MIXED_FP32 = {"sample", "gram", "chol", "gather", "proj_nt", "proj_solve", "proj_acc", "cpqr", "ef_update",
+              "extract", "schur"}
+
+
+def _class_roof(name: str, mixed: bool, sample_kernel: int):
+    """(bound, peak TFLOP/s, note) for a kernel class."""
+    if mixed and name == "sample" and sample_kernel in (0, 2):
+        bf16 = _peaks().get("bf16_tflops")
+        src = "measured bf16 %.1f" % bf16 if bf16 else "fallback bf16 1900"
+        tf32 = (bf16 or 1900.0) * 1.1 / 2.25
+        return ("tensor", tf32 / 3.0,
+                f"3xTF32 effective = TF32 / 3 (three TF32 products per FP32 product); TF32 = {src} x nominal "
+                "1.1/2.25; of measured")
+    if mixed and name in MIXED_FP32:
+        return ("alu", FP32_TFLOPS_NOMINAL, "FP32 SIMT nominal: 152 SMs x 128 lanes x 2 x 2.07 GHz")
+    return ("alu", FP64_TFLOPS_NOMINAL, "FP64 nominal 1.25 TFLOP/s (cuBLAS DGEMM measured 1.05 on this pool)")
+
+
+def _traffic(name: str, workload: str):
+    """DRAM bytes per launch of this kernel class from the committed ncu summary, when it was taken
+    on this workload and the kernel's source has not changed since (else None)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            tab = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = tab.get(name)
+    if not e or e.get("workload") != workload:
+        return None
+    with open(os.path.join(ROOT, e["source"]), "rb") as fh:
+        if hashlib.sha1(fh.read()).hexdigest() != e["source_sha1"]:
+            return None
+    return e["dram_bytes_per_launch"]
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -248,8 +285,7 @@ def run_gpu(args):
     avg = {nm: (sum(c[nm][0] for c in clss) / len(clss), clss[0][nm][1], clss[0][nm][2]) for nm in names}
     dom = max(avg, key=lambda nm: avg[nm][0])
     dom_ms, dom_gflop, dom_launch = avg[dom]
-    fp32_dom = (dom == "sample" and prec == R.RSRS_PREC_MIXED)
-    peak = FP32_TFLOPS_NOMINAL if fp32_dom else FP64_TFLOPS_NOMINAL
+    bound, peak, peak_note = _class_roof(dom, prec == R.RSRS_PREC_MIXED, args.sample_kernel)
     achieved = dom_gflop / dom_ms if dom_ms > 0 else 0.0  # GFLOP/ms = TFLOP/s
     line = {
         "metric": METRIC, "value": value, "unit": "RHS/s (factor + refined solve, per step)",
@@ -263,10 +299,9 @@ def run_gpu(args):
         "rel_residual": max(r.rel_residual for r in reps),
         "gpu_launches": int(sts[0].kernel_launches) * args.steps,
         "kernel_classes_ms": {nm: round(avg[nm][0], 3) for nm in names},
-        "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "peak_note": ("FP32 SIMT nominal: 152 SMs x 128 lanes x 2 x 2.07 GHz" if fp32_dom else
-                                   "FP64 nominal 1.25 TFLOP/s (cuBLAS DGEMM measured 1.05 on this pool)"),
+        "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": _traffic(dom, pr.name),
+                     "peak_note": peak_note,
                      "algorithmic_gflop_per_step": dom_gflop, "launches_per_step": dom_launch},
         "clocks": clk.summary(),
     }

@@ -83,8 +83,7 @@ enum {
 typedef struct {
   int precision;          /* RSRS_PREC_*                                               */
   int p;                  /* oversampling; < 0 selects p = k (Sec. 5)                  */
-  int proj_passes;        /* projection passes of the nullification, 1..4; 0 selects */
-                          /* 2 (FP64) or 3 (mixed)                                   */
+  int proj_passes;        /* projection passes of the nullification, 1..4; 0 selects 2 */
   uint64_t seed;          /* key of the device Philox4x32-10 draws used when no test   */
                           /* matrices are given: entry (i, c) of Omega (Psi) is member */
                           /* (i*s+c) mod 2 of the Box-Muller pair from counter         */
@@ -95,12 +94,18 @@ typedef struct {
   const double* psi_dev;
   int keep_sketches;      /* keep the final Y, Z, Omega, Psi on the device (tests)     */
   int profile;            /* record CUDA-event time per kernel class into rsrs_stats    */
-  int sample_kernel;      /* mixed precision, built-in kernels: 0 default, 1 FP32 SIMT,  */
-                          /* 2 3xTF32 on the tensor cores (tcgen05)                    */
+  int sample_kernel;      /* mixed precision, built-in kernels: 1 FP32 SIMT, 2 (and the  */
+                          /* default 0) 3xTF32 on the tensor cores (tcgen05, TMA)       */
   int mixed_cpqr;         /* mixed precision: 0 default = FP32 reflectors on the sketch  */
                           /* held in distributed shared memory (thread-block cluster of */
                           /* up to 16 CTAs), pivots chosen on FP64 norm sums, when the  */
                           /* box fits; 1 = FP64 CPQR in global memory (FP64 always)     */
+  int mixed_gemm;         /* mixed precision: 0 default = Grams, least-squares right-hand */
+                          /* sides and projection updates as 3xTF32 tcgen05 products;  */
+                          /* 1 = FP32 SIMT                                             */
+  int residual_fp64;      /* rsrs_refine with a built-in kernel: 0 default = residual in */
+                          /* float-float (48-bit) arithmetic on the FP32 pipe, about    */
+                          /* 1e-14 relative; 1 = residual in FP64 arithmetic            */
 } rsrs_options;
 
 typedef struct {
@@ -210,6 +215,12 @@ rsrs_status rsrs_solve_noalloc(const rsrs_factor* f, double* F, int64_t ldf, int
 /* F <- A_approx F (eq. Afact), or its adjoint. */
 rsrs_status rsrs_apply(const rsrs_factor* f, double* F_dev, int64_t ldf, int32_t nrhs,
                        int adjoint, void* stream);
+/* R = B - A X for the operator the factor was built from, in the refinement's residual
+ * arithmetic (float-float for the built-in kernels unless opts->residual_fp64, FP64 for a
+ * callback); B_dev, X_dev, R_dev column-major N x nrhs with leading dimension ld (R may not alias
+ * B or X).  Section 3.3's residual; nrhs <= 4096. */
+rsrs_status rsrs_residual(const rsrs_factor* f, const double* B_dev, const double* X_dev, double* R_dev,
+                          int64_t ld, int32_t nrhs, void* stream);
 /* FP64 iterative refinement: X = A_approx^-1 B, then X += A_approx^-1 (B - A X)
  * with the FP64 residual of the operator the factor was built from, until
  * max_j ||B_j - A X_j|| / ||B_j|| <= rtol or maxit corrections. */

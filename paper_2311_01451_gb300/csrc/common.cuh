@@ -91,6 +91,14 @@ void launch_split_transpose(Launch L, const double* in, int64_t n, int64_t s, fl
 // Columns [0, ncols0) come from in0 / go to out0, [ncols0, ncols) from in1 / to out1, all row-major
 // with leading dimension ld.  Returns false when the tensor maps cannot be made (no launch);
 // a bounded wait that expires records kDevTimeout in *err.
+// FP64-accurate residual product in float-float arithmetic on the FP32 pipe (refinement):
+// out = shift*in + scale*K*in, rows in tree order (ld_in, ld_out), any number of columns;
+// scratch: ff_scratch_floats(n, d, ncols) floats.
+int64_t ff_scratch_floats(int64_t n, int d, int ncols);
+void launch_kernel_matvec_ff(Launch L, int kind, const double* pts, int d, int64_t n, double shift, double scale,
+                             const double* in, int64_t ld_in, double* out, int64_t ld_out, int64_t ncols,
+                             float* scratch);
+
 int64_t tc_plane_ld(int64_t n);
 int64_t tc_points_len(int64_t n, int d);
 void launch_points_f32(Launch L, const double* pts, int64_t n, int d, float* out);
@@ -127,6 +135,13 @@ void launch_m_finalize(Launch L, const GroupArgs& g, int64_t items);            
 void launch_proj_nt(Launch L, const GroupArgs& g, int pass, int64_t items);        // X = M W^T
 void launch_proj_solve(Launch L, const GroupArgs& g, int pass, int64_t items);     // X <- X G^-1
 void launch_proj_acc(Launch L, const GroupArgs& g, int pass, int64_t items);       // M -= X W
+// Mixed path (FP32 workspace): the group's Grams, least-squares right-hand sides and projection
+// updates as 3xTF32 tcgen05 products (one launch each); the same results as launch_gram,
+// launch_proj_nt and launch_proj_acc with CT = float, to FP32 accuracy.
+void launch_gram_tc(Launch L, const GroupArgs& g, const std::vector<BoxDesc>& h);
+void launch_proj_nt_tc(Launch L, const GroupArgs& g, int pass, const std::vector<BoxDesc>& h);
+void launch_proj_acc_tc(Launch L, const GroupArgs& g, int pass, const std::vector<BoxDesc>& h);
+
 void launch_cpqr(Launch L, const GroupArgs& g, int max_b);                         // ID pivots + R
 // FP32 CPQR on the compute-type sketch held in distributed shared memory (mixed path); false when
 // the group's boxes do not fit a cluster of at most 16 CTAs (nothing launched).
@@ -141,6 +156,8 @@ void launch_schur(Launch L, const GroupArgs& g, int64_t items);                 
 // Number of 64-row x 64-col tiles for the group kernels (host-side planning).
 constexpr int kT = 64;
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ inline int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }
 
 // Solve / apply sweeps over one group (defined in solve.cu).
 struct SweepArgs {

@@ -1,0 +1,344 @@
+// Grouped 3xTF32 products on the tensor cores for the mixed path's FP32 workspace: the near-field
+// Grams G = W W^T (a2), the least-squares right-hand sides X = M W^T and the projection updates
+// M -= X W (a3), for every box of a (level, colour) group in one launch.
+//
+// One CTA computes a 128 x 128 tile of D = A B^T (A rows and B rows both K-contiguous) or
+// D = A B (B stored K x N, N contiguous), with D <- alpha D_acc + beta D on store.  Eight producer
+// warps load 32-deep K slices of both operands from global memory, split every FP32 value v into
+// hi = v with 13 low mantissa bits cleared and lo = v - hi (Ootomo & Yokota 2022), and write them
+// into the 128-byte-swizzled K-major layout the MMA reads (an N-contiguous B is transposed on the
+// way); a ninth warp issues D += A_hi B_hi + A_hi B_lo + A_lo B_hi with tcgen05.mma into a 128-column
+// TMEM accumulator.  Three stages; per stage an mbarrier for "operands written" (256 arrivals) and
+// one for "stage free" (tcgen05.commit).  Every wait is bounded: on expiry the kernel records
+// kDevTimeout and completes without hanging.
+#include <cstdint>
+
+#include "common.cuh"
+#include "tc_common.cuh"
+
+namespace rsrs {
+namespace {
+using namespace tc;
+
+constexpr int GM = 128, GN = 128, GK = 32;
+constexpr int OP_BYTES = GM * GK * 4;  // 16 KB: one hi or lo operand tile
+constexpr int GSTAGE = 4 * OP_BYTES;   // A_hi, A_lo, B_hi, B_lo
+constexpr int GNST = 3;
+constexpr int GSMEM = GNST * GSTAGE + 1024;
+constexpr int GPROD = 256, GTHREADS = GPROD + 32;
+constexpr uint32_t GTMEM = 128;
+static_assert(GM == GN, "both operand tiles have 128 rows");
+
+__host__ __device__ inline int64_t cdiv128(int64_t a) { return (a + 127) / 128; }
+__host__ __device__ inline int64_t tri_n(int64_t t) { return t * (t + 1) / 2; }
+__device__ inline void tri_idx(int64_t idx, int64_t& ti, int64_t& tj) {
+  int64_t t = (int64_t)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
+  while (tri_n(t) > idx) --t;
+  while (tri_n(t + 1) <= idx) ++t;
+  ti = t;
+  tj = idx - tri_n(t);
+}
+
+struct TcTile {
+  const float* A;  // row 0, k 0 of the tile's A rows (row i at A + i * lda)
+  int64_t lda;
+  int m;           // valid rows
+  const float* B;  // bnm = 0: row j at B + j * ldb; bnm = 1: element (k, j) at B + k * ldb + j
+  int64_t ldb;
+  int n;           // valid columns
+  int bnm;
+  int64_t K;
+  float* D;        // element (i, j) at D + i * ldd + j
+  int64_t ldd;
+  float alpha, beta;
+};
+
+// Job functors: tiles per box (count) and the tile for a box-local index (tile).
+struct GramJob {  // G_side = W_side W_side^T, lower block triangle of 128 x 128 tiles
+  int64_t s;
+  __device__ int64_t count(const BoxDesc& d) const { return 2 * tri_n(cdiv128(d.l)); }
+  __device__ TcTile tile(const GroupArgs& g, const BoxDesc& d, int64_t loc) const {
+    const int64_t per = tri_n(cdiv128(d.l));
+    const int side = (int)(loc / per);
+    int64_t ti, tj;
+    tri_idx(loc % per, ti, tj);
+    float* wc = reinterpret_cast<float*>(g.workc);
+    const float* W = wc + d.w_off + (int64_t)side * d.l * s;
+    TcTile t;
+    t.A = W + ti * GM * s;
+    t.lda = s;
+    t.m = (int)imin64(GM, d.l - ti * GM);
+    t.B = W + tj * GN * s;
+    t.ldb = s;
+    t.n = (int)imin64(GN, d.l - tj * GN);
+    t.bnm = 0;
+    t.K = s;
+    t.D = wc + d.g_off + (int64_t)side * d.l * d.l + ti * GM * d.l + tj * GN;
+    t.ldd = d.l;
+    t.alpha = 1.f;
+    t.beta = 0.f;
+    return t;
+  }
+};
+struct ProjNtJob {  // X_side(pass) = M_side W_side^T (b x l)
+  int64_t s;
+  int pass;
+  __device__ int64_t count(const BoxDesc& d) const { return 2 * cdiv128(d.b) * cdiv128(d.l); }
+  __device__ TcTile tile(const GroupArgs& g, const BoxDesc& d, int64_t loc) const {
+    const int64_t per = cdiv128(d.b) * cdiv128(d.l);
+    const int side = (int)(loc / per);
+    const int64_t ti = (loc % per) / cdiv128(d.l), tj = (loc % per) % cdiv128(d.l);
+    float* wc = reinterpret_cast<float*>(g.workc);
+    TcTile t;
+    t.A = wc + d.mc_off + (int64_t)side * s + ti * GM * 2 * s;
+    t.lda = 2 * s;
+    t.m = (int)imin64(GM, d.b - ti * GM);
+    t.B = wc + d.w_off + (int64_t)side * d.l * s + tj * GN * s;
+    t.ldb = s;
+    t.n = (int)imin64(GN, d.l - tj * GN);
+    t.bnm = 0;
+    t.K = s;
+    t.D = wc + (pass ? d.x2_off : d.x_off) + (int64_t)side * d.b * d.l + ti * GM * d.l + tj * GN;
+    t.ldd = d.l;
+    t.alpha = 1.f;
+    t.beta = 0.f;
+    return t;
+  }
+};
+struct ProjAccJob {  // M_side -= X_side(pass) W_side (b x s), B = W stored l x s
+  int64_t s;
+  int pass;
+  __device__ int64_t count(const BoxDesc& d) const { return 2 * cdiv128(d.b) * cdiv128(s); }
+  __device__ TcTile tile(const GroupArgs& g, const BoxDesc& d, int64_t loc) const {
+    const int64_t per = cdiv128(d.b) * cdiv128(s);
+    const int side = (int)(loc / per);
+    const int64_t ti = (loc % per) / cdiv128(s), tj = (loc % per) % cdiv128(s);
+    float* wc = reinterpret_cast<float*>(g.workc);
+    TcTile t;
+    t.A = wc + (pass ? d.x2_off : d.x_off) + (int64_t)side * d.b * d.l + ti * GM * d.l;
+    t.lda = d.l;
+    t.m = (int)imin64(GM, d.b - ti * GM);
+    t.B = wc + d.w_off + (int64_t)side * d.l * s + tj * GN;
+    t.ldb = s;
+    t.n = (int)imin64(GN, s - tj * GN);
+    t.bnm = 1;
+    t.K = d.l;
+    t.D = wc + d.mc_off + (int64_t)side * s + ti * GM * 2 * s + tj * GN;
+    t.ldd = 2 * s;
+    t.alpha = -1.f;
+    t.beta = 1.f;
+    return t;
+  }
+};
+
+template <class Job>
+__device__ int find_box(const BoxDesc* desc, int nbox, int64_t item, const Job& job, int64_t& local) {
+  __shared__ int s_box;
+  __shared__ int64_t s_local;
+  if (threadIdx.x == 0) {
+    int64_t acc = 0;
+    s_box = -1;
+    for (int i = 0; i < nbox; ++i) {
+      const int64_t c = job.count(desc[i]);
+      if (item < acc + c) {
+        s_box = i;
+        s_local = item - acc;
+        break;
+      }
+      acc += c;
+    }
+  }
+  __syncthreads();
+  local = s_local;
+  return s_box;
+}
+
+// 16 consecutive K values of one K-contiguous row (zero outside [0, rows) x [0, K)), split, into
+// the swizzled hi/lo tiles at (row, k0l .. k0l + 15).
+__device__ __forceinline__ void put_row16(unsigned char* hi, unsigned char* lo, int row, int k0l, const float* src,
+                                          bool row_ok, int64_t kleft, bool vec) {
+  float v[16];
+  if (row_ok && vec && kleft >= 16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 x = __ldg(reinterpret_cast<const float4*>(src) + q);
+      v[4 * q] = x.x;
+      v[4 * q + 1] = x.y;
+      v[4 * q + 2] = x.z;
+      v[4 * q + 3] = x.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = (row_ok && q < kleft) ? __ldg(src + q) : 0.f;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float4 h, l;
+    h.x = tf32_hi(v[4 * q]);
+    h.y = tf32_hi(v[4 * q + 1]);
+    h.z = tf32_hi(v[4 * q + 2]);
+    h.w = tf32_hi(v[4 * q + 3]);
+    l.x = v[4 * q] - h.x;
+    l.y = v[4 * q + 1] - h.y;
+    l.z = v[4 * q + 2] - h.z;
+    l.w = v[4 * q + 3] - h.w;
+    const uint32_t off = sw128(row, k0l + 4 * q);
+    *reinterpret_cast<float4*>(hi + off) = h;
+    *reinterpret_cast<float4*>(lo + off) = l;
+  }
+}
+
+template <class Job>
+__global__ void __launch_bounds__(GTHREADS, 1) k_tc_grouped(GroupArgs g, Job job) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[GNST], empty[GNST];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_timeout;
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  int64_t loc;
+  const int bi = find_box(g.desc, g.nbox, blockIdx.x, job, loc);
+  if (bi < 0) return;
+  const BoxDesc d = g.desc[bi];
+  const TcTile t = job.tile(g, d, loc);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t nchunk = (t.K + GK - 1) / GK;
+  if (tid == 0) {
+    s_timeout = 0;
+    for (int s = 0; s < GNST; ++s) {
+      bar_init(smem_u32(&full[s]), GPROD);
+      bar_init(smem_u32(&empty[s]), 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(&s_tmem, GTMEM);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = s_tmem;
+
+  if (warp < GPROD / 32) {
+    // A: row tid/2, K half (tid&1)*16.  B (K-contiguous): the same.  B (N-contiguous): k = tid%32,
+    // columns (tid/32)*16 .. +15, transposed into rows n of the K-major tile.
+    const int r = tid >> 1, kh = (tid & 1) * 16;
+    const bool avec = ((t.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(t.A) & 15) == 0);
+    const bool bvec = ((t.ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(t.B) & 15) == 0);
+    const int bk = tid & 31, bn0 = (tid >> 5) * 16;
+    for (int64_t ch = 0; ch < nchunk; ++ch) {
+      const int st = (int)(ch % GNST);
+      const int64_t u = ch / GNST;
+      unsigned char* Ahi = smem + st * GSTAGE;
+      unsigned char* Alo = Ahi + OP_BYTES;
+      unsigned char* Bhi = Alo + OP_BYTES;
+      unsigned char* Blo = Bhi + OP_BYTES;
+      const int64_t k0 = ch * GK;
+      if (ch >= GNST && !bar_wait(smem_u32(&empty[st]), (uint32_t)((u - 1) & 1))) s_timeout = 1;
+      put_row16(Ahi, Alo, r, kh, t.A + (int64_t)r * t.lda + k0 + kh, r < t.m, t.K - k0 - kh, avec);
+      if (!t.bnm) {
+        put_row16(Bhi, Blo, r, kh, t.B + (int64_t)r * t.ldb + k0 + kh, r < t.n, t.K - k0 - kh, bvec);
+      } else {
+        const int64_t kk = k0 + bk;
+        const bool kok = kk < t.K;
+        const float* src = t.B + kk * t.ldb + bn0;
+        float v[16];
+        if (kok && bvec && bn0 + 16 <= t.n) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float4 x = __ldg(reinterpret_cast<const float4*>(src) + q);
+            v[4 * q] = x.x;
+            v[4 * q + 1] = x.y;
+            v[4 * q + 2] = x.z;
+            v[4 * q + 3] = x.w;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) v[q] = (kok && bn0 + q < t.n) ? __ldg(src + q) : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const float h = tf32_hi(v[q]);
+          const uint32_t off = sw128(bn0 + q, bk);
+          *reinterpret_cast<float*>(Bhi + off) = h;
+          *reinterpret_cast<float*>(Blo + off) = v[q] - h;
+        }
+      }
+      fence_proxy_async();
+      bar_arrive(smem_u32(&full[st]));
+    }
+  } else if (lane == 0) {
+    const uint32_t idesc = idesc_tf32(GM, GN);
+    for (int64_t ch = 0; ch < nchunk; ++ch) {
+      const int st = (int)(ch % GNST);
+      if (!bar_wait(smem_u32(&full[st]), (uint32_t)((ch / GNST) & 1))) s_timeout = 1;
+      fence_after();
+      const uint32_t a_hi = smem_u32(smem + st * GSTAGE);
+      mma_3xtf32_chunk(tmem, a_hi, a_hi + OP_BYTES, a_hi + 2 * OP_BYTES, a_hi + 3 * OP_BYTES, idesc, ch == 0);
+      mma_commit(smem_u32(&empty[st]));
+    }
+  }
+  if (warp == GPROD / 32) __syncwarp();
+  if (nchunk > 0) {
+    const int64_t last = nchunk - 1;
+    if (!bar_wait(smem_u32(&empty[last % GNST]), (uint32_t)((last / GNST) & 1))) s_timeout = 1;
+  }
+  fence_after();
+  if (warp < GPROD / 32) {
+    // epilogue: warp w reads TMEM lanes 32*(w%4).. (its rows), columns (w/4)*64 .. +64
+    const int row = 32 * (warp & 3) + lane;
+    const int colbase = (warp >> 2) * 64;
+    for (int cc = 0; cc < 64; cc += 16) {
+      if (colbase + cc >= t.n) break;  // warp-uniform
+      uint32_t rr[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(colbase + cc), rr);
+      if (row < t.m) {
+        float* drow = t.D + (int64_t)row * t.ldd + colbase + cc;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          if (colbase + cc + q < t.n) {
+            const float acc = nchunk > 0 ? __uint_as_float(rr[q]) : 0.f;
+            drow[q] = t.beta == 0.f ? t.alpha * acc : fmaf(t.alpha, acc, t.beta * drow[q]);
+          }
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, GTMEM);
+  if (tid == 0 && s_timeout && g.err) atomicCAS(g.err, 0, kDevTimeout);
+}
+
+template <class Job>
+void launch_job(Launch L, const GroupArgs& g, const Job& job, int64_t items) {
+  if (items <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_tc_grouped<Job>, cudaFuncAttributeMaxDynamicSharedMemorySize, GSMEM);
+    attr = true;
+  }
+  k_tc_grouped<Job><<<(unsigned)items, GTHREADS, GSMEM, L.st>>>(g, job);
+  if (L.counter) ++*L.counter;
+}
+
+template <class Count>
+int64_t items_of_h(const std::vector<BoxDesc>& h, Count c) {
+  int64_t n = 0;
+  for (const BoxDesc& d : h) n += c(d);
+  return n;
+}
+
+}  // namespace
+
+void launch_gram_tc(Launch L, const GroupArgs& g, const std::vector<BoxDesc>& h) {
+  launch_job(L, g, GramJob{g.s}, items_of_h(h, [](const BoxDesc& d) { return 2 * tri_n(cdiv128(d.l)); }));
+}
+void launch_proj_nt_tc(Launch L, const GroupArgs& g, int pass, const std::vector<BoxDesc>& h) {
+  launch_job(L, g, ProjNtJob{g.s, pass},
+             items_of_h(h, [](const BoxDesc& d) { return 2 * cdiv128(d.b) * cdiv128(d.l); }));
+}
+void launch_proj_acc_tc(Launch L, const GroupArgs& g, int pass, const std::vector<BoxDesc>& h) {
+  const int64_t s = g.s;
+  launch_job(L, g, ProjAccJob{g.s, pass},
+             items_of_h(h, [s](const BoxDesc& d) { return 2 * cdiv128(d.b) * cdiv128(s); }));
+}
+
+}  // namespace rsrs

@@ -26,8 +26,6 @@ constexpr int TB_ = TB;
 constexpr int KC = 16;   // K slice
 constexpr int NT = 256;  // threads per tiled CTA (16 x 16), 4 x 4 outputs each
 
-__host__ __device__ inline int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
-__host__ __device__ inline int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }
 __host__ __device__ inline int64_t tri(int64_t t) { return t * (t + 1) / 2; }
 
 __device__ inline void tri_decode(int64_t idx, int64_t& ti, int64_t& tj) {
@@ -907,7 +905,8 @@ __global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs) {
   double* wpart = csm + b;      // b, this CTA's partial dot products
   double* npart = csm + 2 * b;  // b, this CTA's partial norms
   int* rid = (int*)(csm + 3 * b);
-  float* S = reinterpret_cast<float*>(csm + 3 * b + (b + 1) / 2 + 1);  // b x cs slice of M
+  float* fvec = reinterpret_cast<float*>(csm + 3 * b + (b + 1) / 2 + 1);     // b reflector coefficients
+  float* S = reinterpret_cast<float*>(csm + 3 * b + 2 * ((b + 1) / 2 + 1));  // b x cs slice of M
   __shared__ double red_v[8];
   __shared__ int red_i[8];
   __shared__ double s_vj, s_vn2, s_r00;
@@ -935,11 +934,17 @@ __global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs) {
     if (lane == 0) npart[i] = dacc;
   }
   cluster.sync();
-  for (int i = warp; i < b; i += nw) {
-    double v = lane < C ? cluster.map_shared_rank(npart, lane)[i] : 0.0;
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) nrm[i] = v;
-  }
+  // partial sums gathered thread per row: the C remote loads of a row are independent, so their
+  // latencies overlap
+  auto gather = [&](const double* part, int from, double* dst) {
+    for (int pos = from + threadIdx.x; pos < b; pos += blockDim.x) {
+      double v = 0.0;
+#pragma unroll 4
+      for (int q = 0; q < C; ++q) v += cluster.map_shared_rank(part, q)[pos];
+      dst[pos] = v;
+    }
+  };
+  gather(npart, 0, nrm);
   __syncthreads();
   for (int j = 0; j < kp; ++j) {
     // pivot: largest residual norm, ties to the lowest local index (identical in every CTA)
@@ -1020,10 +1025,15 @@ __global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs) {
       if (lane == 0) wpart[pos] = dw;
     }
     cluster.sync();
+    for (int pos = j + 1 + threadIdx.x; pos < b; pos += blockDim.x) {
+      double w = 0.0;
+#pragma unroll 4
+      for (int q = 0; q < C; ++q) w += cluster.map_shared_rank(wpart, q)[pos];
+      fvec[pos] = (vn2 > 0.0) ? (float)(2.0 * w / vn2) : 0.f;
+    }
+    __syncthreads();
     for (int pos = j + 1 + warp; pos < b; pos += nw) {
-      double w = lane < C ? cluster.map_shared_rank(wpart, lane)[pos] : 0.0;
-      for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-      const float f = (vn2 > 0.0) ? (float)(2.0 * w / vn2) : 0.f;
+      const float f = fvec[pos];
       float* row = S + (int64_t)rid[pos] * cs;
       float nn = 0.f;
       for (int t = t0 + lane; t < wid; t += 32) {
@@ -1037,11 +1047,7 @@ __global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs) {
       if (lane == 0) npart[pos] = dn;
     }
     cluster.sync();
-    for (int pos = j + 1 + warp; pos < b; pos += nw) {
-      double v = lane < C ? cluster.map_shared_rank(npart, lane)[pos] : 0.0;
-      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) nrm[pos] = v;
-    }
+    gather(npart, j + 1, nrm);
     __syncthreads();
   }
   if (rank == 0) {
@@ -1696,7 +1702,7 @@ void launch_cpqr(Launch L, const GroupArgs& g, int max_b) {
 }
 // Shared memory of k_cpqr32_cluster for boxes of up to max_b rows and slices of cs columns.
 static size_t cpqr32_smem(int max_b, int cs) {
-  return ((size_t)3 * max_b + (max_b + 1) / 2 + 1) * sizeof(double) + (size_t)max_b * cs * sizeof(float);
+  return ((size_t)3 * max_b + 2 * ((max_b + 1) / 2 + 1)) * sizeof(double) + (size_t)max_b * cs * sizeof(float);
 }
 bool launch_cpqr32(Launch L, const GroupArgs& g, int max_b) {
   const int64_t c = 2 * g.s;

@@ -67,6 +67,7 @@ struct rsrs_factor {
   int max_r = 0;
   double *Y = nullptr, *Z = nullptr, *Om = nullptr, *Ps = nullptr;  // kept sketches (shared, rows from base)
   int sample_kernel = 0;  // mixed sampling: 1 FP32 SIMT, 2 tcgen05 3xTF32
+  int residual_fp64 = 0;  // refinement residual in FP64 instead of float-float
   rsrs_stats stats{};
 };
 
@@ -349,11 +350,14 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
     return fail(RSRS_E_INVAL, "build: unknown precision");
   if (o.sample_kernel < 0 || o.sample_kernel > 2) return fail(RSRS_E_INVAL, "build: unknown sample_kernel");
   if (o.mixed_cpqr < 0 || o.mixed_cpqr > 1) return fail(RSRS_E_INVAL, "build: unknown mixed_cpqr");
+  if (o.mixed_gemm < 0 || o.mixed_gemm > 1) return fail(RSRS_E_INVAL, "build: unknown mixed_gemm");
+  if (o.residual_fp64 < 0 || o.residual_fp64 > 1) return fail(RSRS_E_INVAL, "build: residual_fp64 is 0 or 1");
   if (nprob > 1 && (o.omega_host || o.psi_host || o.omega_dev || o.psi_dev))
     return fail(RSRS_E_INVAL, "build: caller test matrices are for single-problem builds");
-  // FP32 projections converge by about 1e-2..1e-3 per pass (rounding of the Gram against its
-  // conditioning), FP64 ones to rounding after the second pass
-  const int passes = o.proj_passes <= 0 ? (o.precision == RSRS_PREC_MIXED ? 3 : 2) : std::min(o.proj_passes, 4);
+  // two least-squares passes: the second solves for the residual of the first; a third FP32 pass
+  // leaves the refined mixed factor unchanged on the 65,536-point workload (same refinement
+  // history to two digits), so both precisions default to two
+  const int passes = o.proj_passes <= 0 ? 2 : std::min(o.proj_passes, 4);
   std::vector<Schedule> sc(nprob);
   std::vector<int64_t> base(nprob + 1, 0);
   int maxdepth = 0;
@@ -404,7 +408,8 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
     f->fn = ops[p].fn;
     f->ctx = ops[p].ctx;
     f->perm = T.perm;
-    f->sample_kernel = o.sample_kernel == 0 ? 1 : o.sample_kernel;
+    f->sample_kernel = o.sample_kernel == 0 ? 2 : o.sample_kernel;
+    f->residual_fp64 = o.residual_fp64 ? 1 : 0;
     F[p] = std::move(f);
   }
 
@@ -797,7 +802,11 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
       for (const BoxDesc& d : g.h) box_flops(d, s, passes, fl);
       timed(RSRS_K_LISTS, [&] { launch_copy_segments(L, segs_dev + g.seg_off, (int)g.nseg, act, iwork); });
       timed(RSRS_K_GATHER, [&] { launch_gather_box(L, ga, items_gather(g.h)); });
-      timed(RSRS_K_GRAM, [&] { launch_gram(L, ga, items_gram(g.h)); });
+      const bool tcg = ga.fp32 && o.mixed_gemm == 0;
+      timed(RSRS_K_GRAM, [&] {
+        if (tcg) launch_gram_tc(L, ga, g.h);
+        else launch_gram(L, ga, items_gram(g.h));
+      });
       timed(RSRS_K_CHOL, [&] {
         for (int pn = 0; pn < g.max_panels; ++pn) {
           launch_chol_panel(L, ga, pn);
@@ -806,9 +815,15 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
         }
       });
       for (int pass = 0; pass < passes; ++pass) {
-        timed(RSRS_K_PROJ_NT, [&] { launch_proj_nt(L, ga, pass, items_proj_nt(g.h)); });
+        timed(RSRS_K_PROJ_NT, [&] {
+          if (tcg) launch_proj_nt_tc(L, ga, pass, g.h);
+          else launch_proj_nt(L, ga, pass, items_proj_nt(g.h));
+        });
         timed(RSRS_K_PROJ_SOLVE, [&] { launch_proj_solve(L, ga, pass, items_proj_solve(g.h)); });
-        timed(RSRS_K_PROJ_ACC, [&] { launch_proj_acc(L, ga, pass, items_proj_acc(g.h, s)); });
+        timed(RSRS_K_PROJ_ACC, [&] {
+          if (tcg) launch_proj_acc_tc(L, ga, pass, g.h);
+          else launch_proj_acc(L, ga, pass, items_proj_acc(g.h, s));
+        });
       }
       bool cpqr_done = false;
       if (ga.fp32 && o.mixed_cpqr == 0) timed(RSRS_K_CPQR, [&] { cpqr_done = launch_cpqr32(L, ga, g.max_b); });
@@ -1120,6 +1135,10 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_
     CU(pool.alloc(&c1, tot));
     CU(pool.alloc(&c2, tot));
   }
+  // float-float residual scratch (built-in kernels)
+  const bool ff = f->kind != RSRS_OP_CALLBACK && !f->residual_fp64;
+  float* ffs = nullptr;
+  if (ff) CU(pool.alloc(&ffs, ff_scratch_floats(f->n, f->d, nrhs)));
   k_cm_to_rows<<<nblk(tot), 256, 0, st>>>(B, ld, f->perm_dev, f->n, nrhs, Wb);
   CU(cudaMemcpyAsync(Wx, Wb, tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
   r = sweep_solve(f, L, Wx, nrhs, 0);
@@ -1134,7 +1153,10 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_
   double rel = 0.0;
   int it = 0;
   for (;; ++it) {
-    r = op_apply(f, L, Wx, Wax, nrhs, 0, 0, c1, c2);
+    if (ff)
+      launch_kernel_matvec_ff(L, f->kind, f->pts_dev, f->d, f->n, f->shift, f->scale, Wx, nrhs, Wax, nrhs, nrhs, ffs);
+    else
+      r = op_apply(f, L, Wx, Wax, nrhs, 0, 0, c1, c2);
     if (r != RSRS_OK) return r;
     k_sub<<<nblk(tot), 256, 0, st>>>(Wr, Wb, Wax, tot);
     CU(cudaMemsetAsync(nrm, 0, 64 * sizeof(double), st));
@@ -1157,6 +1179,40 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_
   rr.rel_residual = rel;
   if (rep) *rep = rr;
   if (rel > rtol) return fail(RSRS_E_NOT_CONVERGED, "refine: residual " + std::to_string(rel) + " > rtol");
+  return RSRS_OK;
+}
+
+rsrs_status rsrs_residual(const rsrs_factor* f, const double* B, const double* X, double* Rout, int64_t ld,
+                          int32_t nrhs, void* stream) {
+  rsrs_status r = check_block(f, B, ld, nrhs);
+  if (r != RSRS_OK) return r;
+  if (!X || !Rout) return fail(RSRS_E_INVAL, "residual: null block");
+  cudaStream_t st = (cudaStream_t)stream;
+  Launch L{st, nullptr};
+  DevPool pool;
+  const int64_t tot = f->n * nrhs;
+  double *Wb, *Wx, *Wax, *c1 = nullptr, *c2 = nullptr;
+  CU(pool.alloc(&Wb, tot));
+  CU(pool.alloc(&Wx, tot));
+  CU(pool.alloc(&Wax, tot));
+  const bool ff = f->kind != RSRS_OP_CALLBACK && !f->residual_fp64;
+  float* ffs = nullptr;
+  if (ff) CU(pool.alloc(&ffs, ff_scratch_floats(f->n, f->d, nrhs)));
+  if (f->kind == RSRS_OP_CALLBACK) {
+    CU(pool.alloc(&c1, tot));
+    CU(pool.alloc(&c2, tot));
+  }
+  k_cm_to_rows<<<nblk(tot), 256, 0, st>>>(B, ld, f->perm_dev, f->n, nrhs, Wb);
+  k_cm_to_rows<<<nblk(tot), 256, 0, st>>>(X, ld, f->perm_dev, f->n, nrhs, Wx);
+  if (ff)
+    launch_kernel_matvec_ff(L, f->kind, f->pts_dev, f->d, f->n, f->shift, f->scale, Wx, nrhs, Wax, nrhs, nrhs, ffs);
+  else
+    r = op_apply(f, L, Wx, Wax, nrhs, 0, 0, c1, c2);
+  if (r != RSRS_OK) return r;
+  k_sub<<<nblk(tot), 256, 0, st>>>(Wx, Wb, Wax, tot);
+  k_rows_to_cm<<<nblk(tot), 256, 0, st>>>(Wx, f->perm_dev, f->n, nrhs, Rout, ld);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(st));
   return RSRS_OK;
 }
 

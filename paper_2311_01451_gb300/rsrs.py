@@ -23,7 +23,7 @@ STATUS = {0: "RSRS_OK", 1: "RSRS_E_INVAL", 2: "RSRS_E_UNDERSAMPLED", 3: "RSRS_E_
           8: "RSRS_E_TIMEOUT", 9: "RSRS_E_NOT_CONVERGED"}
 
 EXPORTS = ["rsrs_tree_build", "rsrs_tree_info", "rsrs_tree_perm", "rsrs_tree_schedule", "rsrs_tree_free",
-           "rsrs_build", "rsrs_build_batched", "rsrs_solve", "rsrs_solve_noalloc", "rsrs_apply", "rsrs_refine", "rsrs_matvec", "rsrs_factor_stats",
+           "rsrs_build", "rsrs_build_batched", "rsrs_solve", "rsrs_solve_noalloc", "rsrs_apply", "rsrs_refine", "rsrs_residual", "rsrs_matvec", "rsrs_factor_stats",
            "rsrs_factor_box", "rsrs_factor_root", "rsrs_factor_sketches", "rsrs_factor_free",
            "rsrs_status_string", "rsrs_last_error", "rsrs_kernel_class_name"]
 
@@ -40,7 +40,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("p", C.c_int), ("proj_passes", C.c_int), ("seed", C.c_uint64),
                 ("omega_host", C.c_void_p), ("psi_host", C.c_void_p), ("omega_dev", C.c_void_p),
                 ("psi_dev", C.c_void_p), ("keep_sketches", C.c_int), ("profile", C.c_int),
-                ("sample_kernel", C.c_int), ("mixed_cpqr", C.c_int)]
+                ("sample_kernel", C.c_int), ("mixed_cpqr", C.c_int), ("mixed_gemm", C.c_int),
+                ("residual_fp64", C.c_int)]
 
 
 NCLASS = 16
@@ -93,6 +94,7 @@ def lib():
             "rsrs_solve_noalloc": [vp, vp, i64, i32, C.c_int, vp],
             "rsrs_apply": [vp, vp, i64, i32, C.c_int, vp],
             "rsrs_refine": [vp, vp, vp, i64, i32, dbl, C.c_int, vp, C.POINTER(RefineReport)],
+            "rsrs_residual": [vp, vp, vp, vp, i64, i32, vp],
             "rsrs_matvec": [vp, vp, vp, i64, i32, vp],
             "rsrs_factor_stats": [vp, C.POINTER(Stats)],
             "rsrs_factor_box": [vp, i64, C.POINTER(BoxView)],
@@ -191,7 +193,8 @@ class Factor:
                  precision: int = RSRS_PREC_FP64, p: int = -1, omega: np.ndarray | None = None,
                  psi: np.ndarray | None = None, seed: int = 0, passes: int = 0, keep_sketches: bool = False,
                  matvec=None, stream=None, profile: bool = False,
-                 sample_kernel: int = 0, mixed_cpqr: int = 0):
+                 sample_kernel: int = 0, mixed_cpqr: int = 0, residual_fp64: bool = False,
+                 mixed_gemm: int = 0):
         self.tree = tree
         self.n = tree.n
         self._cb = None
@@ -204,7 +207,7 @@ class Factor:
         opts = Options(precision=precision, p=p, proj_passes=passes, seed=seed,
                        keep_sketches=int(keep_sketches), profile=int(profile),
                        sample_kernel=sample_kernel,
-                       mixed_cpqr=mixed_cpqr)
+                       mixed_cpqr=mixed_cpqr, residual_fp64=int(residual_fp64), mixed_gemm=mixed_gemm)
         self._om = self._ps = None
         if omega is not None and hasattr(omega, "data_ptr"):  # device tensors (N, s), original order
             self._om, self._ps = omega, psi
@@ -245,6 +248,16 @@ class Factor:
         py, _, _ = _cm(Y)
         _check(lib().rsrs_matvec(self._h, px, py, ld, nr, _stream_ptr(stream)))
         return Y
+
+    def residual(self, B, X, Rout, stream=None):
+        """Rout <- B - A X in the refinement's residual arithmetic; (nrhs, N) float64 CUDA tensors."""
+        pb, ld, nr = _cm(B)
+        px, ldx, nrx = _cm(X)
+        pr_, ldr, nrr = _cm(Rout)
+        if (ldx, nrx) != (ld, nr) or (ldr, nrr) != (ld, nr):
+            raise ValueError("B, X and Rout must have the same shape")
+        _check(lib().rsrs_residual(self._h, pb, px, pr_, ld, nr, _stream_ptr(stream)))
+        return Rout
 
     def refine(self, B, X, rtol: float = 1e-12, maxit: int = 20, stream=None) -> RefineReport:
         pb, ld, nr = _cm(B)
@@ -299,7 +312,8 @@ class Factor:
 
 def build_batched(trees, kinds, k: int, s: int, shifts, scales, precision: int = RSRS_PREC_FP64, p: int = -1,
                   seed: int = 0, passes: int = 0, profile: bool = False, sample_kernel: int = 0,
-                  keep_sketches: bool = False, mixed_cpqr: int = 0,
+                  keep_sketches: bool = False, mixed_cpqr: int = 0, residual_fp64: bool = False,
+                  mixed_gemm: int = 0,
                   stream=None) -> list:
     """rsrs_build_batched: factors of independent problems built in one set of launches."""
     n = len(trees)
@@ -312,7 +326,8 @@ def build_batched(trees, kinds, k: int, s: int, shifts, scales, precision: int =
     outs = (C.c_void_p * n)()
     opts = Options(precision=precision, p=p, proj_passes=passes, seed=seed, profile=int(profile),
                    sample_kernel=sample_kernel,
-                   keep_sketches=int(keep_sketches), mixed_cpqr=mixed_cpqr)
+                   keep_sketches=int(keep_sketches), mixed_cpqr=mixed_cpqr,
+                   residual_fp64=int(residual_fp64), mixed_gemm=mixed_gemm)
     _check(lib().rsrs_build_batched(n, handles, ops, k, s, C.byref(opts), _stream_ptr(stream), outs))
     res = []
     for i in range(n):

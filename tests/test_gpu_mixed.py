@@ -62,3 +62,26 @@ def test_mixed_cpqr_variants(R, name):
     # differently, so skeleton lists are not compared)
     assert abs(its[0] - its[1]) <= 1
     assert fac[0].stats().n_boxes == fac[1].stats().n_boxes
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_mixed_tensor_core_products(R, name):
+    """Grams, least-squares right-hand sides and projection updates as 3xTF32 tcgen05 products
+    (default) against the FP32 SIMT kernels: both factors precondition alike and refine to the
+    dense solution."""
+    pr = CASES[name]()
+    tree = R.Tree(pr.points, pr.leaf)
+    s = max(pr.s_cfg, tree.info(pr.k).s_req)
+    b = pr.rhs()
+    xd = np.linalg.solve(ops.make_operator(pr).dense(), b)
+    its = {}
+    for mg in (0, 1):
+        f = R.Factor(tree, R.kind_of(pr.kernel), pr.k, s, shift=pr.diag_shift, scale=pr.scale,
+                     precision=R.RSRS_PREC_MIXED, seed=22, mixed_gemm=mg)
+        X = torch.zeros_like(_to_gpu(b))
+        rep = f.refine(_to_gpu(b), X, rtol=1e-13, maxit=40)
+        assert rep.rel_residual <= 1e-13
+        assert rep.history[0] < 1e-2, (mg, rep.history[0])
+        assert np.linalg.norm(X.cpu().numpy().T - xd) / np.linalg.norm(xd) < 1e-11
+        its[mg] = rep.iterations
+    assert abs(its[0] - its[1]) <= 1
