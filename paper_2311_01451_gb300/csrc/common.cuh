@@ -142,6 +142,16 @@ void launch_gram_tc(Launch L, const GroupArgs& g, const std::vector<BoxDesc>& h)
 void launch_proj_nt_tc(Launch L, const GroupArgs& g, int pass, const std::vector<BoxDesc>& h);
 void launch_proj_acc_tc(Launch L, const GroupArgs& g, int pass, const std::vector<BoxDesc>& h);
 
+// Root blocks of a build: LU with partial pivoting in place in A (LAPACK interchange record in
+// piv) and the explicit inverse in inv, all problems at once, FP64.
+struct RootLU {
+  double* A;
+  int64_t n;
+  int32_t* piv;
+  double* inv;
+};
+void launch_root_lu_inverse(Launch L, const RootLU* R_dev, int nprob, int64_t max_n, int* err);
+
 void launch_cpqr(Launch L, const GroupArgs& g, int max_b);                         // ID pivots + R
 // FP32 CPQR on the compute-type sketch held in distributed shared memory (mixed path); false when
 // the group's boxes do not fit a cluster of at most 16 CTAs (nothing launched).

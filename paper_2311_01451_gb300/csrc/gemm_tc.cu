@@ -133,31 +133,45 @@ struct ProjAccJob {  // M_side -= X_side(pass) W_side (b x s), B = W stored l x 
 
 template <class Job>
 __device__ int find_box(const BoxDesc* desc, int nbox, int64_t item, const Job& job, int64_t& local) {
+  // block-wide prefix sum over the boxes' tile counts, blockDim.x boxes at a time
   __shared__ int s_box;
   __shared__ int64_t s_local;
-  if (threadIdx.x == 0) {
-    int64_t acc = 0;
-    s_box = -1;
-    for (int i = 0; i < nbox; ++i) {
-      const int64_t c = job.count(desc[i]);
-      if (item < acc + c) {
-        s_box = i;
-        s_local = item - acc;
-        break;
-      }
-      acc += c;
+  __shared__ int64_t s_warp[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (threadIdx.x == 0) s_box = -1;
+  int64_t base = 0;
+  for (int c0 = 0; c0 < nbox; c0 += blockDim.x) {
+    const int i = c0 + (int)threadIdx.x;
+    const int64_t c = i < nbox ? job.count(desc[i]) : 0;
+    int64_t incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
     }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    int64_t wbase = 0, total = 0;
+    for (int w = 0; w < nw; ++w) {
+      if (w < warp) wbase += s_warp[w];
+      total += s_warp[w];
+    }
+    incl += wbase;
+    const int64_t excl = incl - c;
+    if (i < nbox && c > 0 && item >= base + excl && item < base + incl) {
+      s_box = i;
+      s_local = item - base - excl;
+    }
+    __syncthreads();
+    base += total;
+    if (s_box >= 0 || item < base) break;
   }
   __syncthreads();
   local = s_local;
   return s_box;
 }
 
-// 16 consecutive K values of one K-contiguous row (zero outside [0, rows) x [0, K)), split, into
-// the swizzled hi/lo tiles at (row, k0l .. k0l + 15).
-__device__ __forceinline__ void put_row16(unsigned char* hi, unsigned char* lo, int row, int k0l, const float* src,
-                                          bool row_ok, int64_t kleft, bool vec) {
-  float v[16];
+// 16 consecutive K values of one K-contiguous row (zero outside the valid rows and K).
+__device__ __forceinline__ void load_row16(float v[16], const float* src, bool row_ok, int64_t kleft, bool vec) {
   if (row_ok && vec && kleft >= 16) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -171,6 +185,25 @@ __device__ __forceinline__ void put_row16(unsigned char* hi, unsigned char* lo, 
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = (row_ok && q < kleft) ? __ldg(src + q) : 0.f;
   }
+}
+// 16 consecutive columns of one K row of an N-contiguous operand (zero outside).
+__device__ __forceinline__ void load_col16(float v[16], const float* src, bool k_ok, int nleft, bool vec) {
+  if (k_ok && vec && nleft >= 16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 x = __ldg(reinterpret_cast<const float4*>(src) + q);
+      v[4 * q] = x.x;
+      v[4 * q + 1] = x.y;
+      v[4 * q + 2] = x.z;
+      v[4 * q + 3] = x.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = (k_ok && q < nleft) ? __ldg(src + q) : 0.f;
+  }
+}
+// Split into TF32 hi/lo and store row `row`, K positions k0l .. k0l + 15, of the swizzled tiles.
+__device__ __forceinline__ void store_row16(unsigned char* hi, unsigned char* lo, int row, int k0l, const float v[16]) {
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     float4 h, l;
@@ -185,6 +218,16 @@ __device__ __forceinline__ void put_row16(unsigned char* hi, unsigned char* lo, 
     const uint32_t off = sw128(row, k0l + 4 * q);
     *reinterpret_cast<float4*>(hi + off) = h;
     *reinterpret_cast<float4*>(lo + off) = l;
+  }
+}
+// Split and store column k, rows n0 .. n0 + 15 (the transpose of an N-contiguous operand).
+__device__ __forceinline__ void store_col16(unsigned char* hi, unsigned char* lo, int n0, int k, const float v[16]) {
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const float h = tf32_hi(v[q]);
+    const uint32_t off = sw128(n0 + q, k);
+    *reinterpret_cast<float*>(hi + off) = h;
+    *reinterpret_cast<float*>(lo + off) = v[q] - h;
   }
 }
 
@@ -218,11 +261,20 @@ __global__ void __launch_bounds__(GTHREADS, 1) k_tc_grouped(GroupArgs g, Job job
 
   if (warp < GPROD / 32) {
     // A: row tid/2, K half (tid&1)*16.  B (K-contiguous): the same.  B (N-contiguous): k = tid%32,
-    // columns (tid/32)*16 .. +15, transposed into rows n of the K-major tile.
+    // columns (tid/32)*16 .. +15, transposed into rows n of the K-major tile.  The operands of the
+    // next slice are loaded into registers while this slice is split and stored.
     const int r = tid >> 1, kh = (tid & 1) * 16;
     const bool avec = ((t.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(t.A) & 15) == 0);
     const bool bvec = ((t.ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(t.B) & 15) == 0);
     const int bk = tid & 31, bn0 = (tid >> 5) * 16;
+    auto load = [&](int64_t ch, float va[16], float vb[16]) {
+      const int64_t k0 = ch * GK;
+      load_row16(va, t.A + (int64_t)r * t.lda + k0 + kh, r < t.m, t.K - k0 - kh, avec);
+      if (!t.bnm) load_row16(vb, t.B + (int64_t)r * t.ldb + k0 + kh, r < t.n, t.K - k0 - kh, bvec);
+      else load_col16(vb, t.B + (k0 + bk) * t.ldb + bn0, k0 + bk < t.K, t.n - bn0, bvec);
+    };
+    float va[16], vb[16], na[16], nb[16];
+    if (nchunk > 0) load(0, va, vb);
     for (int64_t ch = 0; ch < nchunk; ++ch) {
       const int st = (int)(ch % GNST);
       const int64_t u = ch / GNST;
@@ -230,39 +282,18 @@ __global__ void __launch_bounds__(GTHREADS, 1) k_tc_grouped(GroupArgs g, Job job
       unsigned char* Alo = Ahi + OP_BYTES;
       unsigned char* Bhi = Alo + OP_BYTES;
       unsigned char* Blo = Bhi + OP_BYTES;
-      const int64_t k0 = ch * GK;
+      if (ch + 1 < nchunk) load(ch + 1, na, nb);
       if (ch >= GNST && !bar_wait(smem_u32(&empty[st]), (uint32_t)((u - 1) & 1))) s_timeout = 1;
-      put_row16(Ahi, Alo, r, kh, t.A + (int64_t)r * t.lda + k0 + kh, r < t.m, t.K - k0 - kh, avec);
-      if (!t.bnm) {
-        put_row16(Bhi, Blo, r, kh, t.B + (int64_t)r * t.ldb + k0 + kh, r < t.n, t.K - k0 - kh, bvec);
-      } else {
-        const int64_t kk = k0 + bk;
-        const bool kok = kk < t.K;
-        const float* src = t.B + kk * t.ldb + bn0;
-        float v[16];
-        if (kok && bvec && bn0 + 16 <= t.n) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float4 x = __ldg(reinterpret_cast<const float4*>(src) + q);
-            v[4 * q] = x.x;
-            v[4 * q + 1] = x.y;
-            v[4 * q + 2] = x.z;
-            v[4 * q + 3] = x.w;
-          }
-        } else {
-#pragma unroll
-          for (int q = 0; q < 16; ++q) v[q] = (kok && bn0 + q < t.n) ? __ldg(src + q) : 0.f;
-        }
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const float h = tf32_hi(v[q]);
-          const uint32_t off = sw128(bn0 + q, bk);
-          *reinterpret_cast<float*>(Bhi + off) = h;
-          *reinterpret_cast<float*>(Blo + off) = v[q] - h;
-        }
-      }
+      store_row16(Ahi, Alo, r, kh, va);
+      if (!t.bnm) store_row16(Bhi, Blo, r, kh, vb);
+      else store_col16(Bhi, Blo, bn0, bk, vb);
       fence_proxy_async();
       bar_arrive(smem_u32(&full[st]));
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        va[q] = na[q];
+        vb[q] = nb[q];
+      }
     }
   } else if (lane == 0) {
     const uint32_t idesc = idesc_tf32(GM, GN);

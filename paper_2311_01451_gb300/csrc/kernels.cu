@@ -40,20 +40,38 @@ __host__ __device__ inline int64_t cdv(int64_t a, int64_t b) { return (a + b - 1
 
 template <class F>
 __device__ inline int find_item(const BoxDesc* desc, int nbox, int64_t item, F count, int64_t& local) {
+  // the CTA scans the boxes' item counts in chunks of blockDim.x (one box per thread, block-wide
+  // inclusive prefix sum), so the search costs a few dependent loads instead of one per box
   __shared__ int s_box;
   __shared__ int64_t s_local;
-  if (threadIdx.x == 0) {
-    int64_t acc = 0;
-    s_box = -1;
-    for (int i = 0; i < nbox; ++i) {
-      int64_t c = count(desc[i]);
-      if (item < acc + c) {
-        s_box = i;
-        s_local = item - acc;
-        break;
-      }
-      acc += c;
+  __shared__ int64_t s_warp[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (threadIdx.x == 0) s_box = -1;
+  int64_t base = 0;
+  for (int c0 = 0; c0 < nbox; c0 += blockDim.x) {
+    const int i = c0 + (int)threadIdx.x;
+    const int64_t c = i < nbox ? count(desc[i]) : 0;
+    int64_t incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
     }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    int64_t wbase = 0, total = 0;
+    for (int w = 0; w < nw; ++w) {
+      if (w < warp) wbase += s_warp[w];
+      total += s_warp[w];
+    }
+    incl += wbase;
+    const int64_t excl = incl - c;
+    if (i < nbox && c > 0 && item >= base + excl && item < base + incl) {
+      s_box = i;
+      s_local = item - base - excl;
+    }
+    __syncthreads();
+    base += total;
+    if (s_box >= 0 || item < base) break;  // uniform: read after the barrier
   }
   __syncthreads();
   local = s_local;
@@ -883,11 +901,14 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(GroupArgs g) {
 
 // Mixed-precision CPQR with the box's projected sketch resident in distributed shared memory: a
 // cluster of C CTAs (C = 1..16) per box, CTA r holding columns [r*cs, (r+1)*cs) of all b rows of
-// the FP32 sketch M, so the k' reflector steps never go back to global memory.  Products and
-// updates run in FP32 (M carries the FP32 rounding of the projections already); the dot products
-// and residual norms are summed over the cluster in FP64 and the pivot (largest residual, ties to
-// the lowest tree index, the dependent-pivot rule of k_cpqr) is chosen in FP64 on those sums.
-// Output as k_cpqr_cluster: R rows by point (FP64), permutation and first dependent step.
+// the FP32 sketch M, so the k' reflector steps never go back to global memory.  The arithmetic on
+// M is FP32 (M carries the FP32 rounding of the projections already), including the warp and
+// cluster sums of the dot products and row norms: this part's FP64 pipe is 1/64 of its FP32 pipe,
+// and FP64 reductions over every row and lane would dominate each step.  The pivot decisions stay
+// in FP64: the residual norms are held as FP64, the largest is found by comparing their bit
+// patterns (monotone for non-negative doubles; ties to the lowest tree index), and the Householder
+// scalars and the dependent-pivot test of k_cpqr are evaluated in FP64.  Output as
+// k_cpqr_cluster: R rows by point (FP64), permutation and first dependent step.
 __global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
@@ -901,15 +922,16 @@ __global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs) {
   double* Rp = g.work + d.cp_off;
   int32_t* perm = g.iwork + d.pv_off;
   extern __shared__ double csm[];
-  double* nrm = csm;            // b, replicated in every CTA
-  double* wpart = csm + b;      // b, this CTA's partial dot products
-  double* npart = csm + 2 * b;  // b, this CTA's partial norms
-  int* rid = (int*)(csm + 3 * b);
-  float* fvec = reinterpret_cast<float*>(csm + 3 * b + (b + 1) / 2 + 1);     // b reflector coefficients
-  float* S = reinterpret_cast<float*>(csm + 3 * b + 2 * ((b + 1) / 2 + 1));  // b x cs slice of M
-  __shared__ double red_v[8];
+  double* nrm = csm;                                         // b, replicated in every CTA
+  float* wpart = reinterpret_cast<float*>(csm + b);          // b, this CTA's partial dot products
+  float* npart = wpart + b;                                  // b, this CTA's partial norms
+  float* fvec = npart + b;                                   // b, reflector coefficients
+  int* rid = reinterpret_cast<int*>(fvec + b);               // b
+  float* S = reinterpret_cast<float*>(csm + b + (4 * b + 1) / 2 + 1);  // b x cs slice of M
+  __shared__ unsigned long long red_v[8];
   __shared__ int red_i[8];
-  __shared__ double s_vj, s_vn2, s_r00;
+  __shared__ double s_r00;
+  __shared__ float s_vj, s_f2;
   __shared__ int s_j0;
   const double tau = fmax(1e-10, 64.0 * DBL_EPSILON * (double)max(b, (int)c));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -929,38 +951,37 @@ __global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs) {
       srow[t] = v;
       acc = fmaf(v, v, acc);
     }
-    double dacc = acc;
-    for (int o = 16; o; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
-    if (lane == 0) npart[i] = dacc;
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) npart[i] = acc;
   }
   cluster.sync();
-  // partial sums gathered thread per row: the C remote loads of a row are independent, so their
+  // cluster sums, thread per row: the C remote loads of a row are independent, so their
   // latencies overlap
-  auto gather = [&](const double* part, int from, double* dst) {
+  auto gather_norms = [&](int from) {
     for (int pos = from + threadIdx.x; pos < b; pos += blockDim.x) {
-      double v = 0.0;
+      float v = 0.f;
 #pragma unroll 4
-      for (int q = 0; q < C; ++q) v += cluster.map_shared_rank(part, q)[pos];
-      dst[pos] = v;
+      for (int q = 0; q < C; ++q) v += cluster.map_shared_rank(npart, q)[pos];
+      nrm[pos] = (double)v;
     }
   };
-  gather(npart, 0, nrm);
+  gather_norms(0);
   __syncthreads();
   for (int j = 0; j < kp; ++j) {
     // pivot: largest residual norm, ties to the lowest local index (identical in every CTA)
-    double bv = -1.0;
+    unsigned long long bv = 0ull;
     int bp = -1;
     for (int pos = j + threadIdx.x; pos < b; pos += blockDim.x) {
-      const double v = nrm[pos];
-      if (v > bv || (v == bv && bp >= 0 && rid[pos] < rid[bp])) {
+      const unsigned long long v = (unsigned long long)__double_as_longlong(nrm[pos]);
+      if (bp < 0 || v > bv || (v == bv && rid[pos] < rid[bp])) {
         bv = v;
         bp = pos;
       }
     }
     for (int o = 16; o; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
       const int op = __shfl_xor_sync(0xffffffffu, bp, o);
-      if (op >= 0 && (ov > bv || (ov == bv && (bp < 0 || rid[op] < rid[bp])))) {
+      if (op >= 0 && (bp < 0 || ov > bv || (ov == bv && rid[op] < rid[bp]))) {
         bv = ov;
         bp = op;
       }
@@ -971,21 +992,22 @@ __global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs) {
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      double v0 = -1.0;
+      unsigned long long v0 = 0ull;
       int p0 = -1;
       for (int w = 0; w < nw; ++w) {
         const int op = red_i[w];
-        const double ov = red_v[w];
-        if (op >= 0 && (ov > v0 || (ov == v0 && (p0 < 0 || rid[op] < rid[p0])))) {
+        const unsigned long long ov = red_v[w];
+        if (op >= 0 && (p0 < 0 || ov > v0 || (ov == v0 && rid[op] < rid[p0]))) {
           v0 = ov;
           p0 = op;
         }
       }
-      if (p0 < 0) {
+      const double dv0 = p0 >= 0 ? __longlong_as_double((long long)v0) : 0.0;
+      if (p0 < 0 || !isfinite(dv0)) {
         p0 = j;
         if (rank == 0) set_err(g.err, kDevNonfinite);
       }
-      if (s_j0 == kp && ((s_r00 >= 0.0 && sqrt(v0) <= tau * s_r00) || v0 == 0.0)) s_j0 = j;
+      if (s_j0 == kp && ((s_r00 >= 0.0 && sqrt(dv0) <= tau * s_r00) || dv0 == 0.0)) s_j0 = j;
       if (s_j0 <= j) {
         p0 = j;
         for (int pos = j + 1; pos < b; ++pos)
@@ -1004,14 +1026,14 @@ __global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs) {
       const double x0 = (double)cluster.map_shared_rank(S, owner)[(int64_t)rid[j] * cs + (j - (int64_t)owner * cs)];
       const double alpha = sqrt(fmax(nrm[j], 0.0));
       const double sg = (x0 >= 0.0) ? 1.0 : -1.0;
-      s_vj = x0 + sg * alpha;
-      s_vn2 = 2.0 * alpha * (alpha + fabs(x0));
+      const double vn2 = 2.0 * alpha * (alpha + fabs(x0));
+      s_vj = (float)(x0 + sg * alpha);
+      s_f2 = vn2 > 0.0 ? (float)(2.0 / vn2) : 0.f;
       if (j == 0) s_r00 = alpha;
       if (rank == 0) Rp[(int64_t)j * b + rid[j]] = -sg * alpha;
     }
     __syncthreads();
-    const float vj = (float)s_vj;
-    const double vn2 = s_vn2;
+    const float vj = s_vj, f2 = s_f2;
     const float* xs = S + (int64_t)rid[j] * cs;
     const int t0 = (int)(imax64(t_lo, j) - t_lo);  // first local column of the reflector
     const int tj = (int)(j - t_lo);                 // local index of column j (in range for its owner)
@@ -1020,16 +1042,15 @@ __global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs) {
       const float* row = S + (int64_t)rid[pos] * cs;
       float w = 0.f;
       for (int t = t0 + lane; t < wid; t += 32) w = fmaf(row[t], t == tj ? vj : xs[t], w);
-      double dw = w;
-      for (int o = 16; o; o >>= 1) dw += __shfl_xor_sync(0xffffffffu, dw, o);
-      if (lane == 0) wpart[pos] = dw;
+      for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      if (lane == 0) wpart[pos] = w;
     }
     cluster.sync();
     for (int pos = j + 1 + threadIdx.x; pos < b; pos += blockDim.x) {
-      double w = 0.0;
+      float w = 0.f;
 #pragma unroll 4
       for (int q = 0; q < C; ++q) w += cluster.map_shared_rank(wpart, q)[pos];
-      fvec[pos] = (vn2 > 0.0) ? (float)(2.0 * w / vn2) : 0.f;
+      fvec[pos] = w * f2;
     }
     __syncthreads();
     for (int pos = j + 1 + warp; pos < b; pos += nw) {
@@ -1042,12 +1063,11 @@ __global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs) {
         if (t > tj) nn = fmaf(v, v, nn);
         else Rp[(int64_t)j * b + rid[pos]] = (double)v;  // t == j lives in exactly one CTA
       }
-      double dn = nn;
-      for (int o = 16; o; o >>= 1) dn += __shfl_xor_sync(0xffffffffu, dn, o);
-      if (lane == 0) npart[pos] = dn;
+      for (int o = 16; o; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+      if (lane == 0) npart[pos] = nn;
     }
     cluster.sync();
-    gather(npart, j + 1, nrm);
+    gather_norms(j + 1);
     __syncthreads();
   }
   if (rank == 0) {
@@ -1702,7 +1722,7 @@ void launch_cpqr(Launch L, const GroupArgs& g, int max_b) {
 }
 // Shared memory of k_cpqr32_cluster for boxes of up to max_b rows and slices of cs columns.
 static size_t cpqr32_smem(int max_b, int cs) {
-  return ((size_t)3 * max_b + 2 * ((max_b + 1) / 2 + 1)) * sizeof(double) + (size_t)max_b * cs * sizeof(float);
+  return ((size_t)max_b + (4 * (size_t)max_b + 1) / 2 + 1) * sizeof(double) + (size_t)max_b * cs * sizeof(float);
 }
 bool launch_cpqr32(Launch L, const GroupArgs& g, int max_b) {
   const int64_t c = 2 * g.s;

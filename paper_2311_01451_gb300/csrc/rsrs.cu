@@ -869,6 +869,8 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
         launch_proj_solve(L, ga, 1, items_proj_solve(rh));
       });
     }
+    std::vector<RootLU> rl;
+    int64_t max_root = 0;
     for (int p = 0; p < nprob; ++p) {
       const int64_t nroot = F[p]->root_size;
       if (nroot == 0) continue;
@@ -877,10 +879,18 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
                          st));
       CU(cudaMemcpyAsync(F[p]->root_A, xroot, nroot * nroot * sizeof(double), cudaMemcpyDeviceToDevice, st));
       CU(cudaMemcpyAsync(F[p]->root_LU, xroot, nroot * nroot * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      timed(RSRS_K_ROOT, [&] {
-        launch_dense_lu(L, F[p]->root_LU, nroot, F[p]->root_piv, err);
-        launch_dense_inverse(L, F[p]->root_LU, F[p]->root_piv, nroot, F[p]->root_inv);
-      });
+      rl.push_back(RootLU{F[p]->root_LU, nroot, F[p]->root_piv, F[p]->root_inv});
+      max_root = std::max(max_root, nroot);
+    }
+    if (!rl.empty()) {
+      RootLU* rl_dev;
+      CU(pool.alloc(&rl_dev, (int64_t)rl.size()));
+      CU(cudaMemcpyAsync(rl_dev, rl.data(), rl.size() * sizeof(RootLU), cudaMemcpyHostToDevice, st));
+      timed(RSRS_K_ROOT, [&] { launch_root_lu_inverse(L, rl_dev, (int)rl.size(), max_root, err); });
+    }
+    for (int p = 0; p < nprob; ++p) {
+      const int64_t nroot = F[p]->root_size;
+      if (nroot == 0) continue;
       const double nr = (double)nroot;
       bst.class_gflop[RSRS_K_ROOT] += (2.0 * nr * (nr + 1) * s + nr * nr * nr / 3.0 + 2.0 * nr * nr * s +
                                        2.0 * nr * nr * nr + 2.0 * nr * nr * nr / 3.0 + 2.0 * nr * nr * nr) *

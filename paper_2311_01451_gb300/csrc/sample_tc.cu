@@ -6,14 +6,14 @@
 // 2^-21 relative, the level of the FP32 arithmetic of the rest of the mixed path.
 //
 // Tile: D = 128 rows (TMEM lanes) x up to 256 columns (TMEM columns); 32 points j per stage.
-//   A_hi, A_lo: K(x_i, x_j) for the 128 rows, generated by 8 producer warps (K-major, 128-byte rows
+//   A_hi, A_lo: K(x_i, x_j) for the 128 rows, generated by 16 producer warps (K-major, 128-byte rows
 //               of 32 TF32 values, 128-byte swizzle, 8-row atoms 1024 bytes apart);
 //   B_hi, B_lo: in[j][c] for the tile's columns, from hi/lo planes split and transposed once
 //               before the product (FP64 -> FP32 conversion runs at FP64 rate on this part, so it
 //               must not sit in the inner loop), fetched by TMA straight into the same swizzled
 //               layout (the tensor map's 128-byte swizzle is the canonical K-major one).
-// A ninth warp issues, from one thread, the TMA copies and the 4 K-steps x 3 products per stage.
-// Two stages; per stage three mbarriers: A written (256 arrivals), B landed (TMA transaction
+// A seventeenth warp issues, from one thread, the TMA copies and the 4 K-steps x 3 products per
+// stage.  Two stages; per stage three mbarriers: A written (512 arrivals), B landed (TMA transaction
 // bytes) and stage free (tcgen05.commit of the products that read it).  The products of chunk c
 // are issued before the copies for chunk c+1 are armed, so the tensor pipe has work queued while
 // the next stage fills.  Every wait is bounded: on expiry the kernel records kDevTimeout, waits
@@ -35,7 +35,7 @@ constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;     // 96 KB: A_hi, A_lo,
 constexpr int NSTAGE = 2;
 constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024;   // + alignment slack
 constexpr uint32_t TMEM_COLS = 256;
-constexpr int NPROD = 256;                                // producer threads (warps 0..7)
+constexpr int NPROD = 512;                                // producer threads (warps 0..15)
 constexpr int NTHREADS = NPROD + 32;                      // + the TMA / MMA warp
 constexpr long long WAIT_LIMIT = 1ll << 26;
 
@@ -162,32 +162,37 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t tmem = s_tmem;
 
   if (warp < NPROD / 32) {
-    // ---- producers: kernel values of row arow, points akh..akh+15 of each chunk ----
-    const int arow = tid >> 1, akh = (tid & 1) * 16;
+    // ---- producers: kernel values of row arow, points akq..akq+7 of each chunk; the points of the
+    // next chunk are loaded while this chunk's values are computed ----
+    const int arow = tid >> 2, akq = (tid & 3) * 8;
     const int64_t gi = i0 + arow;
     float pi[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) pi[k] = (gi < n) ? p32[gi * D + k] : 0.f;
+    float pj[8 * D], pn[8 * D];
+    auto load_pts = [&](int64_t ch, float* dst) {
+      const float4* src = reinterpret_cast<const float4*>(p32 + (ch * TK + akq) * D);
+#pragma unroll
+      for (int q = 0; q < 2 * D; ++q) {
+        const float4 v = __ldg(src + q);
+        dst[4 * q] = v.x;
+        dst[4 * q + 1] = v.y;
+        dst[4 * q + 2] = v.z;
+        dst[4 * q + 3] = v.w;
+      }
+    };
+    if (nchunk > 0) load_pts(0, pj);
     for (int64_t ch = 0; ch < nchunk; ++ch) {
       const int st = (int)(ch & 1);
       const int64_t u = ch >> 1;
       unsigned char* Ahi = smem + st * STAGE_BYTES;
       unsigned char* Alo = Ahi + A_BYTES;
-      const int64_t j0 = ch * TK + akh;
-      float pj[16 * D];
-      const float4* src = reinterpret_cast<const float4*>(p32 + j0 * D);
-#pragma unroll
-      for (int q = 0; q < 4 * D; ++q) {
-        const float4 v = __ldg(src + q);
-        pj[4 * q] = v.x;
-        pj[4 * q + 1] = v.y;
-        pj[4 * q + 2] = v.z;
-        pj[4 * q + 3] = v.w;
-      }
+      const int64_t j0 = ch * TK + akq;
+      if (ch + 1 < nchunk) load_pts(ch + 1, pn);
       // the products of chunk ch - 2 must be done with this stage
       if (ch >= NSTAGE && !bar_wait(smem_u32(&empty[st]), (uint32_t)((u - 1) & 1))) s_timeout = 1;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < 2; ++q) {
         float hv[4], lv[4];
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
@@ -206,13 +211,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           hv[w] = tf32_hi(v);
           lv[w] = v - hv[w];
         }
-        const uint32_t off = sw128(arow, akh + q * 4);
+        const uint32_t off = sw128(arow, akq + q * 4);
         *reinterpret_cast<float4*>(Ahi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
         *reinterpret_cast<float4*>(Alo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
       }
       // generic-proxy writes must be visible to the tensor cores (async proxy)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       bar_arrive(smem_u32(&full_a[st]));
+#pragma unroll
+      for (int q = 0; q < 8 * D; ++q) pj[q] = pn[q];
     }
   } else if (lane == 0) {
     // ---- TMA + MMA issue ----
@@ -269,11 +276,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp < NPROD / 32 && nchunk > 0) {
-    // epilogue: warp w reads TMEM lanes 32*(w%4).. (its rows), columns (w/4)*128 .. +128
+    // epilogue: warp w reads TMEM lanes 32*(w%4).. (its rows), columns (w/4)*64 .. +64
     const int row = 32 * (warp & 3) + lane;
     const int64_t gi = i0 + row;
-    const int colbase = (warp >> 2) * 128;
-    for (int cc = 0; cc < 128; cc += 16) {
+    const int colbase = (warp >> 2) * 64;
+    for (int cc = 0; cc < 64; cc += 16) {
       if (colbase + cc >= nmma) break;  // warp-uniform
       uint32_t r[16];
       const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(colbase + cc);
