@@ -103,6 +103,9 @@ typedef struct {
   int mixed_gemm;         /* mixed precision: 0 default = Grams, least-squares right-hand */
                           /* sides and projection updates as 3xTF32 tcgen05 products;  */
                           /* 1 = FP32 SIMT                                             */
+  int use_graph;          /* 1: capture the build's launch sequence as one CUDA graph    */
+                          /* kept with the factors, so rsrs_refactor can replay it;    */
+                          /* needs device-drawn test matrices; no per-class timings   */
   int residual_fp64;      /* rsrs_refine with a built-in kernel: 0 default = residual in */
                           /* float-float (48-bit) arithmetic on the FP32 pipe, about    */
                           /* 1e-14 relative; 1 = residual in FP64 arithmetic            */
@@ -118,7 +121,10 @@ typedef struct {
   int64_t n_groups;       /* (level, colour) groups = launches per step                */
   int64_t max_l;          /* largest |B_act| + |N_act| at processing time             */
   int64_t root_size;      /* |B_t|                                                    */
-  int64_t s_req;          /* smallest admissible s: max(max_l + k + p, |B_t|)         */
+  int64_t s_req;          /* smallest admissible s: max(max_l + k + p, |B_t| + p)     */
+  int64_t s_req_mixed;    /* smallest s for RSRS_PREC_MIXED: also keeps every box's   */
+                          /* near-field Gram W W^T well conditioned in FP32 (mixed  */
+                          /* builds with s below it return RSRS_E_UNDERSAMPLED)     */
 } rsrs_tree_info_t;
 
 /* Kernel classes of the build, for per-class timings and algorithmic FLOP counts. */
@@ -173,6 +179,22 @@ void rsrs_tree_free(rsrs_tree* tree);
 rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, int s,
                        const rsrs_options* opts, void* stream, rsrs_factor** out);
 
+/* A 7-point variable-coefficient operator on an m x m x m cell grid, usable as the matvec callback
+ * of an RSRS_OP_CALLBACK operator (fn = rsrs_stencil7_matvec, ctx = the object).  Cell-centred
+ * finite volumes: (A u)_i = sum over the faces (i, j) between neighbouring cells of
+ * beta_ij (u_i - u_j), beta_ij = 2 b_i b_j / (b_i + b_j), plus 2 b_i u_i for every boundary face of
+ * cell i (Dirichlet wall half a cell away); no h^-2 scaling.  Symmetric positive definite.  Not
+ * part of the paper's method: it stands in for the paper's PDE-derived operators (Sec. 5, Exp. 3).
+ * coef_host: m^3 positive finite coefficients b, cells ordered x fastest, then y, then z (copied;
+ * the face coefficients are formed in FP64).  RSRS_E_INVAL on bad arguments, RSRS_E_NOMEM when the
+ * device copy fails.  The matvec returns 0, or non-zero (which rsrs_build reports as
+ * RSRS_E_CALLBACK) on a size mismatch or a launch error; it enqueues on `stream` only. */
+typedef struct rsrs_stencil7 rsrs_stencil7;
+rsrs_status rsrs_stencil7_create(const double* coef_host, int m, rsrs_stencil7** out);
+int rsrs_stencil7_matvec(void* ctx, int adjoint, int64_t n, int32_t ncols, const double* X_dev, int64_t ldx,
+                         double* Y_dev, int64_t ldy, void* stream);
+void rsrs_stencil7_free(rsrs_stencil7* s);
+
 /* Several independent problems in one set of launches (same k, s, options): the boxes of all
  * problems at the same height above their deepest level and of the same colour share each
  * launch, and the roots are extracted together.  out receives nprob factors that share device
@@ -181,6 +203,16 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
  * refused with RSRS_E_INVAL. */
 rsrs_status rsrs_build_batched(int nprob, const rsrs_tree* const* trees, const rsrs_operator* ops, int k, int s,
                                const rsrs_options* opts, void* stream, rsrs_factor** out);
+
+/* Rebuilds in place every factor of the build that f belongs to (all problems of a batched
+ * build) from new test matrices drawn with key `seed` (problem p: seed + p), by replaying the
+ * launch sequence captured when it was built with opts.use_graph = 1: same trees, operators, k,
+ * s and options, one graph launch instead of thousands of kernel launches.  A callback operator's
+ * work was captured at build time, so its matvec is not called again (its kernels rerun on
+ * whatever device data they read).  The factors must not be in use meanwhile.  Per-class timings
+ * are not recorded.  RSRS_E_INVAL when the build did not use use_graph; device-detected
+ * conditions as for rsrs_build. */
+rsrs_status rsrs_refactor(rsrs_factor* f, uint64_t seed, void* stream);
 
 /* F <- A_approx^-1 F (eq. Ainvfact), or its adjoint; F_dev column-major N x nrhs. */
 rsrs_status rsrs_solve(const rsrs_factor* f, double* F_dev, int64_t ldf, int32_t nrhs,

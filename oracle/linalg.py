@@ -40,8 +40,12 @@ def pinv_right(y: np.ndarray, m: np.ndarray) -> np.ndarray:
     return sla.solve_triangular(r, (y @ q).T, lower=False).T
 
 
-def cpqr_id(m: np.ndarray, k: int, tau: float, record: dict | None = None):
+def cpqr_id(m: np.ndarray, k: int, tau: float, record: dict | None = None, floor: float = 0.0):
     """Row ID of m (b x c): returns (skel, red, T) with m[red] ~= T^T m[skel].
+
+    Pivots whose residual norm is <= tau |R_00| or <= ``floor`` (an absolute noise level) are
+    numerically dependent: they are taken in ascending original order and their rows of T are
+    zero (truncated back-substitution).
 
     skel: k row indices in pivot order; red: the other rows, ascending;
     T: k x (b-k) interpolation matrix.  ``record`` (a dict) receives, per pivot
@@ -56,7 +60,7 @@ def cpqr_id(m: np.ndarray, k: int, tau: float, record: dict | None = None):
     for j in range(k):
         norms = np.sqrt(np.sum(a[j:, j:] ** 2, axis=0))
         best = norms.max()
-        if r00 is not None and best <= tau * r00 or best == 0.0:
+        if best <= floor or (r00 is not None and best <= tau * r00) or best == 0.0:
             j0 = min(j0, j)
         if j0 <= j:  # dependent: lowest remaining original index
             p = j + int(np.argmin(perm[j:]))

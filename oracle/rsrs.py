@@ -123,7 +123,12 @@ def factor(tree: Tree, sched: Schedule, Y, Z, Om, Ps, trace=None, max_steps: int
             # step 3: ID of the concatenation
             kp = min(k, b)
             rec = {}
-            skel, red, T = la.cpqr_id(np.hstack([Yp, Zp]), kp, id_tau(b, s), record=rec)
+            # residuals below tau times the largest row of [Y_B | Z_B] are at the rounding level of
+            # the near field the nullification cancelled (a sparse operator's box has no far field)
+            tau = id_tau(b, s)
+            scale2 = np.sum(Y[Bact] ** 2, axis=1) + np.sum(Z[Bact] ** 2, axis=1)
+            floor = tau * np.sqrt(np.max(scale2))
+            skel, red, T = la.cpqr_id(np.hstack([Yp, Zp]), kp, tau, record=rec, floor=floor)
             S, R = Bact[skel], Bact[red]
             # step 4: sparsification E, F
             Y[R] -= T.T @ Y[S]
@@ -160,7 +165,7 @@ def factor(tree: Tree, sched: Schedule, Y, Z, Om, Ps, trace=None, max_steps: int
                            pivot_shortfall=np.array(rec.get("shortfall", [])))
             fac.boxes.append(bf)
             if trace is not None:
-                trace.append(dict(box=bf, Yp=Yp, Zp=Zp))
+                trace.append(dict(box=bf, Yp=Yp, Zp=Zp, scale2=scale2))
     if tree.depth == 0:
         Bt = np.arange(n)
     else:

@@ -4,7 +4,7 @@ The computation lives in ``librsrs.so`` (CUDA kernels behind the C ABI of
 ``include/rsrs.h``); this package only builds it and marshals arguments.
 """
 from .rsrs import (RSRS_OP_CALLBACK, RSRS_OP_INVR3D, RSRS_OP_LOG2D, RSRS_PREC_FP64, RSRS_PREC_MIXED, Factor,
-                   RSRSError, Tree, build_batched, kind_of, lib)
+                   RSRSError, Stencil7, Tree, build_batched, kind_of, lib)
 
-__all__ = ["Tree", "Factor", "build_batched", "RSRSError", "lib", "kind_of", "RSRS_OP_LOG2D", "RSRS_OP_INVR3D",
+__all__ = ["Tree", "Factor", "Stencil7", "build_batched", "RSRSError", "lib", "kind_of", "RSRS_OP_LOG2D", "RSRS_OP_INVR3D",
            "RSRS_OP_CALLBACK", "RSRS_PREC_FP64", "RSRS_PREC_MIXED"]

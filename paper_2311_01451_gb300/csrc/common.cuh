@@ -29,6 +29,7 @@ struct BoxDesc {
   int64_t e_off;    // workc: extraction blocks, 2 x r x l
   int64_t m_off;    // work (FP64): b x 2s projected sketches for the CPQR
   int64_t cp_off;   // work (FP64): CPQR R rows, kp x b
+  int64_t sn_off;   // work (FP64): b squared row norms of [Y_B | Z_B] before nullification
   int64_t li_off;   // workc: inverses (and their transposes) of the 64 x 64 diagonal Cholesky
                     //   blocks, 2 sides x nblk x 2 x 64 x 64
   int64_t pv_off;   // int32 work: b CPQR local permutation, then the first dependent step

@@ -447,16 +447,30 @@ __global__ void k_gather_box(GroupArgs g) {
   CT* wc = reinterpret_cast<CT*>(g.workc);
   const int64_t mb = cdv(d.b, 4);
   if (loc < mb) {
+    __shared__ CT red[32];
     for (int rr = 0; rr < 4; ++rr) {
       int64_t i = loc * 4 + rr;
-      if (i >= d.b) break;
+      if (i >= d.b) break;  // uniform
       const double* y = g.Y + (int64_t)bn[i] * g.s;
       const double* z = g.Z + (int64_t)bn[i] * g.s;
       CT* m = wc + d.mc_off + i * 2 * g.s;
+      CT acc = 0;
       for (int64_t c = threadIdx.x; c < g.s; c += blockDim.x) {
-        m[c] = (CT)y[c];
-        m[g.s + c] = (CT)z[c];
+        const CT a = (CT)y[c], bz = (CT)z[c];
+        m[c] = a;
+        m[g.s + c] = bz;
+        acc = mad(a, a, mad(bz, bz, acc));
       }
+      // squared row norm before nullification: the ID's noise floor
+      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        CT t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        g.work[d.sn_off + i] = (double)t;
+      }
+      __syncthreads();
     }
   } else {
     for (int rr = 0; rr < 4; ++rr) {
@@ -633,12 +647,23 @@ __global__ void __launch_bounds__(NT) k_proj_acc(GroupArgs g, int pass) {
   tile_acc<CT>(-1.0, X, d.b, d.l, W, 0, M, (int64_t)side * g.s, g.s, ti * TB, tt * TB);
 }
 
+// Largest row norm of the box's sketch [Y_B | Z_B] before nullification.  A residual below tau
+// times it is at the rounding level of the near field the nullification cancelled: such pivots
+// (all of them when the box has no numerically significant far field, as for a sparse operator)
+// count as dependent.
+__device__ inline double id_scale(const double* sn, int b) {
+  double m = 0.0;
+  for (int i = 0; i < b; ++i) m = fmax(m, sn[i]);
+  return sqrt(m);
+}
+
 // Column-pivoted Householder QR of M^T (pivoting over the b rows of M), kp steps.
 // One CTA per box; the reflectors act on the 2s columns of M in place.
-// Once the largest remaining residual is <= tau |R_00| (tau = max(1e-10,
-// 64 eps max(b, 2s))) the remaining pivots are numerically dependent and are
-// taken in ascending local (tree) order; the first such step is stored after
-// the permutation for the interpolation matrix.
+// Once the largest remaining residual is <= tau |R_00| or <= tau max_i |[Y_B Z_B]_i|
+// (tau = max(1e-10, 64 eps max(b, 2s)); the second bound is the rounding level of the
+// near field the nullification cancelled) the remaining pivots are numerically dependent
+// and are taken in ascending local (tree) order; the first such step is stored after the
+// permutation for the interpolation matrix.
 __global__ void __launch_bounds__(512) k_cpqr(GroupArgs g) {
   const BoxDesc d = g.desc[blockIdx.x];
   const int b = d.b, kp = d.kp;
@@ -654,6 +679,7 @@ __global__ void __launch_bounds__(512) k_cpqr(GroupArgs g) {
   __shared__ double s_vn2, s_r00;
   __shared__ int s_j0;
   const double tau = fmax(1e-10, 64.0 * DBL_EPSILON * (double)max(b, (int)(2 * g.s)));
+  const double floor_abs = tau * id_scale(g.work + d.sn_off, b);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = threadIdx.x; i < b; i += blockDim.x) rid[i] = i;
   if (threadIdx.x == 0) {
@@ -708,7 +734,7 @@ __global__ void __launch_bounds__(512) k_cpqr(GroupArgs g) {
         p0 = j;
         set_err(g.err, kDevNonfinite);
       }
-      if (s_j0 == kp && ((s_r00 >= 0.0 && sqrt(v0) <= tau * s_r00) || v0 == 0.0)) s_j0 = j;
+      if (s_j0 == kp && (sqrt(v0) <= floor_abs || (s_r00 >= 0.0 && sqrt(v0) <= tau * s_r00) || v0 == 0.0)) s_j0 = j;
       if (s_j0 <= j) {  // dependent: lowest remaining local index
         p0 = j;
         for (int pos = j + 1; pos < b; ++pos)
@@ -798,6 +824,7 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(GroupArgs g) {
   __shared__ double s_alpha, s_x0, s_vn2, s_r00;
   __shared__ int s_j0, s_p;
   const double tau = fmax(1e-10, 64.0 * DBL_EPSILON * (double)max(b, (int)c));
+  const double floor_abs = tau * id_scale(g.work + d.sn_off, b);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = threadIdx.x; i < b; i += blockDim.x) rid[i] = i;
   if (threadIdx.x == 0) {
@@ -834,7 +861,7 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(GroupArgs g) {
         p0 = j;
         if (rank == 0) set_err(g.err, kDevNonfinite);
       }
-      if (s_j0 == kp && ((s_r00 >= 0.0 && sqrt(v0) <= tau * s_r00) || v0 == 0.0)) s_j0 = j;
+      if (s_j0 == kp && (sqrt(v0) <= floor_abs || (s_r00 >= 0.0 && sqrt(v0) <= tau * s_r00) || v0 == 0.0)) s_j0 = j;
       if (s_j0 <= j) {
         p0 = j;
         for (int pos = j + 1; pos < b; ++pos)
@@ -909,7 +936,7 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(GroupArgs g) {
 // patterns (monotone for non-negative doubles; ties to the lowest tree index), and the Householder
 // scalars and the dependent-pivot test of k_cpqr are evaluated in FP64.  Output as
 // k_cpqr_cluster: R rows by point (FP64), permutation and first dependent step.
-__global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs) {
+__global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs, int in_global) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
@@ -918,7 +945,7 @@ __global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs) {
   const int b = d.b, kp = d.kp;
   const int64_t c = 2 * g.s;
   const int64_t t_lo = imin64((int64_t)rank * cs, c), t_hi = imin64(t_lo + cs, c);
-  const float* Mg = reinterpret_cast<const float*>(g.workc) + d.mc_off;
+  float* Mg = reinterpret_cast<float*>(g.workc) + d.mc_off;
   double* Rp = g.work + d.cp_off;
   int32_t* perm = g.iwork + d.pv_off;
   extern __shared__ double csm[];
@@ -927,13 +954,17 @@ __global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs) {
   float* npart = wpart + b;                                  // b, this CTA's partial norms
   float* fvec = npart + b;                                   // b, reflector coefficients
   int* rid = reinterpret_cast<int*>(fvec + b);               // b
-  float* S = reinterpret_cast<float*>(csm + b + (4 * b + 1) / 2 + 1);  // b x cs slice of M
+  // this CTA's b x (t_hi - t_lo) slice of M: in shared memory (row pitch cs), or in place in the
+  // workspace when the box is too large for the cluster's shared memory (row pitch 2s)
+  float* S = in_global ? Mg + t_lo : reinterpret_cast<float*>(csm + b + (4 * b + 1) / 2 + 1);
+  const int64_t lds = in_global ? c : (int64_t)cs;
   __shared__ unsigned long long red_v[8];
   __shared__ int red_i[8];
   __shared__ double s_r00;
   __shared__ float s_vj, s_f2;
   __shared__ int s_j0;
   const double tau = fmax(1e-10, 64.0 * DBL_EPSILON * (double)max(b, (int)c));
+  const double floor_abs = tau * id_scale(g.work + d.sn_off, b);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int wid = (int)(t_hi - t_lo);
   for (int i = threadIdx.x; i < b; i += blockDim.x) rid[i] = i;
@@ -944,11 +975,11 @@ __global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs) {
   // slice into shared memory; initial partial squared row norms
   for (int i = warp; i < b; i += nw) {
     const float* row = Mg + (int64_t)i * c + t_lo;
-    float* srow = S + (int64_t)i * cs;
+    float* srow = S + (int64_t)i * lds;
     float acc = 0.f;
     for (int t = lane; t < wid; t += 32) {
       const float v = row[t];
-      srow[t] = v;
+      if (!in_global) srow[t] = v;
       acc = fmaf(v, v, acc);
     }
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -1007,7 +1038,8 @@ __global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs) {
         p0 = j;
         if (rank == 0) set_err(g.err, kDevNonfinite);
       }
-      if (s_j0 == kp && ((s_r00 >= 0.0 && sqrt(dv0) <= tau * s_r00) || dv0 == 0.0)) s_j0 = j;
+      if (s_j0 == kp && (sqrt(dv0) <= floor_abs || (s_r00 >= 0.0 && sqrt(dv0) <= tau * s_r00) || dv0 == 0.0))
+        s_j0 = j;
       if (s_j0 <= j) {
         p0 = j;
         for (int pos = j + 1; pos < b; ++pos)
@@ -1023,7 +1055,9 @@ __global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs) {
       }
       // x0 = M[pivot][j] lives in the CTA that owns column j
       const int owner = (int)(j / cs);
-      const double x0 = (double)cluster.map_shared_rank(S, owner)[(int64_t)rid[j] * cs + (j - (int64_t)owner * cs)];
+      const double x0 = in_global ? (double)Mg[(int64_t)rid[j] * c + j]
+                                  : (double)cluster.map_shared_rank(S, owner)[(int64_t)rid[j] * cs +
+                                                                              (j - (int64_t)owner * cs)];
       const double alpha = sqrt(fmax(nrm[j], 0.0));
       const double sg = (x0 >= 0.0) ? 1.0 : -1.0;
       const double vn2 = 2.0 * alpha * (alpha + fabs(x0));
@@ -1034,12 +1068,12 @@ __global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs) {
     }
     __syncthreads();
     const float vj = s_vj, f2 = s_f2;
-    const float* xs = S + (int64_t)rid[j] * cs;
+    const float* xs = S + (int64_t)rid[j] * lds;
     const int t0 = (int)(imax64(t_lo, j) - t_lo);  // first local column of the reflector
     const int tj = (int)(j - t_lo);                 // local index of column j (in range for its owner)
     // partial dot products of the remaining rows with v over this CTA's columns
     for (int pos = j + 1 + warp; pos < b; pos += nw) {
-      const float* row = S + (int64_t)rid[pos] * cs;
+      const float* row = S + (int64_t)rid[pos] * lds;
       float w = 0.f;
       for (int t = t0 + lane; t < wid; t += 32) w = fmaf(row[t], t == tj ? vj : xs[t], w);
       for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
@@ -1055,7 +1089,7 @@ __global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs) {
     __syncthreads();
     for (int pos = j + 1 + warp; pos < b; pos += nw) {
       const float f = fvec[pos];
-      float* row = S + (int64_t)rid[pos] * cs;
+      float* row = S + (int64_t)rid[pos] * lds;
       float nn = 0.f;
       for (int t = t0 + lane; t < wid; t += 32) {
         const float v = fmaf(-f, t == tj ? vj : xs[t], row[t]);
@@ -1732,32 +1766,37 @@ bool launch_cpqr32(Launch L, const GroupArgs& g, int max_b) {
     cudaFuncSetAttribute(k_cpqr32_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  for (int C = 1; C <= 16; C *= 2) {
-    const int cs = (int)((cdiv(c, C) + 3) / 4 * 4);
-    const size_t smem = cpqr32_smem(max_b, cs);
-    if (smem > 200 * 1024) continue;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(g.nbox * C));
-    cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = L.st;
-    cudaLaunchAttribute attr1[1];
-    attr1[0].id = cudaLaunchAttributeClusterDimension;
-    attr1[0].val.clusterDim.x = C;
-    attr1[0].val.clusterDim.y = 1;
-    attr1[0].val.clusterDim.z = 1;
-    cfg.attrs = attr1;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, k_cpqr32_cluster, &cfg) != cudaSuccess || nclusters < 1) {
-      cudaGetLastError();
-      return false;
+  // smallest cluster whose shared memory holds the slices; otherwise 16 CTAs on slices in place
+  int C = 16, in_global = 1;
+  for (int q = 1; q <= 16; q *= 2)
+    if (cpqr32_smem(max_b, (int)((cdiv(c, q) + 3) / 4 * 4)) <= 200 * 1024) {
+      C = q;
+      in_global = 0;
+      break;
     }
-    cudaLaunchKernelEx(&cfg, k_cpqr32_cluster, g, cs);
-    count_launch(L);
-    return true;
+  const int cs = (int)((cdiv(c, C) + 3) / 4 * 4);
+  const size_t smem = in_global ? cpqr32_smem(max_b, 0) : cpqr32_smem(max_b, cs);
+  if (smem > 200 * 1024) return false;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(g.nbox * C));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = L.st;
+  cudaLaunchAttribute attr1[1];
+  attr1[0].id = cudaLaunchAttributeClusterDimension;
+  attr1[0].val.clusterDim.x = C;
+  attr1[0].val.clusterDim.y = 1;
+  attr1[0].val.clusterDim.z = 1;
+  cfg.attrs = attr1;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, k_cpqr32_cluster, &cfg) != cudaSuccess || nclusters < 1) {
+    cudaGetLastError();
+    return false;
   }
-  return false;
+  cudaLaunchKernelEx(&cfg, k_cpqr32_cluster, g, cs, in_global);
+  count_launch(L);
+  return true;
 }
 void launch_cpqr_single(Launch L, const GroupArgs& g, int max_b) {
   size_t smem = (size_t)max_b * (sizeof(double) + sizeof(int));

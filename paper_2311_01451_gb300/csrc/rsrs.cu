@@ -38,7 +38,13 @@ struct GroupView {
 // Device memory shared by the factors of one build (one or several problems).
 struct Shared {
   std::vector<void*> ptrs;
+  // builds with opts.use_graph: the captured launch sequence (replayed by rsrs_refactor), the
+  // device word its Philox draws take their key from, and its status word
+  cudaGraphExec_t exec = nullptr;
+  uint64_t* seed_dev = nullptr;
+  int* err_dev = nullptr;
   ~Shared() {
+    if (exec) cudaGraphExecDestroy(exec);
     for (void* p : ptrs) cudaFree(p);
   }
 };
@@ -127,6 +133,11 @@ __global__ void k_gather_orig(const double* in, const int32_t* perm, int64_t n, 
   int64_t t = e / s, c = e % s;
   out[e] = in[(int64_t)perm[t] * s + c];
 }
+__global__ void k_set_u64(uint64_t* p, uint64_t v) { *p = v; }
+__global__ void k_f32_to_f64(const float* in, int64_t n, double* out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = (double)in[e];
+}
 __global__ void k_axpy(double* y, const double* x, double a, int64_t n) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) y[e] += a * x[e];
@@ -181,9 +192,11 @@ __device__ inline void normal_pair(uint64_t seed, uint32_t stream, uint64_t q, d
   z1 = rr * sn;
 }
 // Omega (stream 0) or Psi (stream 1) in tree order: entry (t, c) is draw 2*(perm[t]*s + c) ...
-__global__ void k_gauss_tree(uint64_t seed, uint32_t stream, const int32_t* perm, int64_t n, int64_t s, double* out) {
+__global__ void k_gauss_tree(const uint64_t* seed_dev, uint64_t add, uint32_t stream, const int32_t* perm, int64_t n,
+                             int64_t s, double* out) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n * s) return;
+  const uint64_t seed = *seed_dev + add;
   int64_t t = e / s, c = e % s;
   int64_t g = (int64_t)perm[t] * s + c;
   double z0, z1;
@@ -293,6 +306,28 @@ rsrs_status rsrs_tree_perm(const rsrs_tree* tree, int64_t* perm_host) {
   return RSRS_OK;
 }
 
+// Smallest s >= s_min for which an l-row Gaussian-like test block W (l x s) keeps its Gram
+// W W^T positive definite under FP32 rounding: with cond(W) ~ (sqrt s + sqrt l) / (sqrt s - sqrt l)
+// (the extreme singular values of a Gaussian matrix) the Gram's rounding, about sqrt(s) 2^-24 of
+// its norm, must stay below a tenth of its smallest eigenvalue.
+int64_t mixed_sample_bound(int64_t s_min, int64_t max_l) {
+  auto ok = [&](int64_t s) {
+    const double rs = std::sqrt((double)s), rl = std::sqrt((double)max_l);
+    if (rs <= rl) return false;
+    const double c = (rs + rl) / (rs - rl);
+    return c * c * rs * std::ldexp(1.0, -24) <= 0.1;
+  };
+  int64_t s = std::max<int64_t>(s_min, 1);
+  if (ok(s)) return s;
+  int64_t lo = s, hi = s;
+  while (!ok(hi)) hi *= 2;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) / 2;
+    (ok(mid) ? hi : lo) = mid;
+  }
+  return hi;
+}
+
 rsrs_status rsrs_tree_info(const rsrs_tree* tree, int k, int p, rsrs_tree_info_t* out) {
   if (!tree || !out || k <= 0) return fail(RSRS_E_INVAL, "tree_info: null argument or k <= 0");
   Schedule sc;
@@ -309,6 +344,7 @@ rsrs_status rsrs_tree_info(const rsrs_tree* tree, int k, int p, rsrs_tree_info_t
   out->max_l = sc.max_l;
   out->root_size = (int64_t)sc.root.size();
   out->s_req = sc.s_req;
+  out->s_req_mixed = sc.steps.empty() ? sc.s_req : mixed_sample_bound(sc.s_req, sc.max_l);
   return RSRS_OK;
 }
 
@@ -354,6 +390,10 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
   if (o.residual_fp64 < 0 || o.residual_fp64 > 1) return fail(RSRS_E_INVAL, "build: residual_fp64 is 0 or 1");
   if (nprob > 1 && (o.omega_host || o.psi_host || o.omega_dev || o.psi_dev))
     return fail(RSRS_E_INVAL, "build: caller test matrices are for single-problem builds");
+  const bool graph = o.use_graph != 0;
+  if (graph && (o.omega_host || o.psi_host || o.omega_dev || o.psi_dev))
+    return fail(RSRS_E_INVAL, "build: a graph build draws its test matrices on the device");
+  if (graph) o.profile = 0;  // per-class event timing is not part of a captured graph
   // two least-squares passes: the second solves for the residual of the first; a third FP32 pass
   // leaves the refined mixed factor unchanged on the 65,536-point workload (same refinement
   // history to two digits), so both precisions default to two
@@ -374,12 +414,33 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
     if (s < sc[p].s_req)
       return fail(RSRS_E_UNDERSAMPLED, "problem " + std::to_string(p) + ": s=" + std::to_string(s) +
                                            " < s_req=" + std::to_string(sc[p].s_req));
+    if (o.precision == RSRS_PREC_MIXED && !sc[p].steps.empty()) {
+      const int64_t sm = mixed_sample_bound(sc[p].s_req, sc[p].max_l);
+      if (s < sm)
+        return fail(RSRS_E_UNDERSAMPLED,
+                    "problem " + std::to_string(p) + ": mixed precision needs s >= " + std::to_string(sm) +
+                        " (near-field Grams of up to " + std::to_string(sc[p].max_l) +
+                        " rows must stay positive definite in FP32); s=" + std::to_string(s));
+    }
     base[p + 1] = base[p] + T.n;
     maxdepth = std::max(maxdepth, T.depth);
   }
   const int64_t Ntot = base[nprob];
   if (Ntot > INT32_MAX) return fail(RSRS_E_INVAL, "build: more than 2^31 points in one build");
   cudaStream_t st = (cudaStream_t)stream;
+  // a graph build records its launches on a private stream (the legacy default stream cannot be
+  // captured); everything it enqueues is synchronised before the build returns
+  struct OwnStream {
+    cudaStream_t s = nullptr;
+    ~OwnStream() {
+      if (s) cudaStreamDestroy(s);
+    }
+  } own;
+  if (o.use_graph) {
+    CU(cudaStreamSynchronize(st));
+    CU(cudaStreamCreateWithFlags(&own.s, cudaStreamNonBlocking));
+    st = own.s;
+  }
   auto sh = std::make_shared<Shared>();
   auto dalloc = [&](auto** ptr, int64_t count) -> cudaError_t {
     using T = std::remove_reference_t<decltype(**ptr)>;
@@ -511,6 +572,8 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
           w += (int64_t)d.b * 2 * s;
           d.cp_off = w;
           w += (int64_t)d.kp * d.b;
+          d.sn_off = w;
+          w += d.b;
           d.fi_off = fi_total;
           fi_total += fi_size(d.kp, d.r, d.n);
           d.fd_off = fd_total;
@@ -540,7 +603,7 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
   }
   // root group: one pseudo-box per problem, B_t = what its level-1 boxes keep (or all its points)
   std::vector<BoxDesc> rh;
-  int64_t root_seg_off = (int64_t)segs.size(), root_workc = 0, root_iw = 0;
+  int64_t root_seg_off = (int64_t)segs.size(), root_workc = 0, root_iw = 0, root_work = 0;
   std::vector<int64_t> root_iw_off(nprob, 0);
   for (int p = 0; p < nprob; ++p) {
     const Tree& T = trees[p]->t;
@@ -554,6 +617,8 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
     root_iw += nroot;
     rd.pv_off = root_iw;
     root_iw += 1;
+    rd.sn_off = root_work;  // FP64 work: the gather's row norms (unused by the root)
+    root_work += nroot;
     // the root runs in FP64: its compute-type offsets count doubles
     rd.g_off = root_workc;
     root_workc += 2 * nroot * nroot;
@@ -605,7 +670,7 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
     CU(pool.alloc(&Om, NS));
     CU(pool.alloc(&Ps, NS));
   }
-  CU(pool.alloc(&work, work_max));
+  CU(pool.alloc(&work, std::max(work_max, root_work)));
   CU(pool.alloc(&workc, (int64_t)std::max<size_t>(workc_max * ct_bytes, root_workc * sizeof(double))));
   CU(pool.alloc(&iwork, iwork_max));
   CU(pool.alloc(&act, (int64_t)act_init.size()));
@@ -651,12 +716,85 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
       }
     }
   }
-  CU(cudaMemcpyAsync(act, act_init.data(), act_init.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  int32_t* act_init_dev;
+  CU(pool.alloc(&act_init_dev, (int64_t)act_init.size()));
+  CU(cudaMemcpyAsync(act_init_dev, act_init.data(), act_init.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  uint64_t* seed_dev;
+  CU(pool.alloc(&seed_dev, 1));
+  k_set_u64<<<1, 1, 0, st>>>(seed_dev, o.seed);
   if (!segs.empty())
     CU(cudaMemcpyAsync(segs_dev, segs.data(), segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, st));
   if (!all_desc.empty())
     CU(cudaMemcpyAsync(desc_dev, all_desc.data(), all_desc.size() * sizeof(BoxDesc), cudaMemcpyHostToDevice, st));
   CU(cudaMemcpyAsync(root_desc_dev, rh.data(), rh.size() * sizeof(BoxDesc), cudaMemcpyHostToDevice, st));
+  // scratch of the launch sequence, allocated before it so that it can be captured as a graph
+  int64_t nmax = 0;
+  for (int p = 0; p < nprob; ++p) nmax = std::max(nmax, F[p]->n);
+  const int64_t nsmax = nmax * s;
+  double *cm_in = nullptr, *cm_out = nullptr;
+  float* conv = nullptr;
+  bool any_cb = false, any_builtin = false;
+  for (int p = 0; p < nprob; ++p) (F[p]->kind == RSRS_OP_CALLBACK ? any_cb : any_builtin) = true;
+  if (any_cb) {
+    CU(pool.alloc(&cm_in, nsmax));
+    CU(pool.alloc(&cm_out, nsmax));
+  }
+  const bool mixed = o.precision == RSRS_PREC_MIXED;
+  const bool tc = mixed && F[0]->sample_kernel == 2;
+  bool root32 = mixed && o.mixed_gemm == 0;
+  for (int p = 0; p < nprob; ++p)
+    if (F[p]->root_size > 0 && mixed_sample_bound(0, F[p]->root_size) > s) root32 = false;
+  // tensor-core path: hi/lo planes of [Omega Psi] (2s x N each) and the FP32 points; SIMT path:
+  // an FP32 copy of one side
+  if (mixed && any_builtin)
+    CU(pool.alloc(&conv, tc ? 4 * s * tc_plane_ld(nmax) + tc_points_len(nmax, 3) : nsmax));
+  std::vector<RootLU> rl;
+  int64_t max_root = 0;
+  for (int p = 0; p < nprob; ++p)
+    if (F[p]->root_size > 0) {
+      rl.push_back(RootLU{F[p]->root_LU, F[p]->root_size, F[p]->root_piv, F[p]->root_inv});
+      max_root = std::max(max_root, F[p]->root_size);
+    }
+  RootLU* rl_dev = nullptr;
+  if (!rl.empty()) {
+    CU(pool.alloc(&rl_dev, (int64_t)rl.size()));
+    CU(cudaMemcpyAsync(rl_dev, rl.data(), rl.size() * sizeof(RootLU), cudaMemcpyHostToDevice, st));
+  }
+  // caller test matrices from host memory are staged before the launch sequence
+  for (int p = 0; p < nprob; ++p) {
+    const Tree& T = trees[p]->t;
+    const int64_t n = T.n, ns = n * s;
+    for (int side = 0; side < 2; ++side) {
+      double* dst = (side == 0 ? Om : Ps) + base[p] * s;
+      const double* hsrc = side == 0 ? o.omega_host : o.psi_host;
+      if (hsrc) {
+        std::vector<double> tree_order(ns);
+        for (int64_t q = 0; q < n; ++q) std::memcpy(&tree_order[q * s], &hsrc[T.perm[q] * s], s * sizeof(double));
+        CU(cudaMemcpyAsync(dst, tree_order.data(), ns * sizeof(double), cudaMemcpyHostToDevice, st));
+        CU(cudaStreamSynchronize(st));  // the staging buffer goes out of scope
+      }
+    }
+  }
+  CU(cudaStreamSynchronize(st));  // uploads done; rl and the host tables may go
+  cudaGraph_t cgraph = nullptr;
+  // ends an unfinished capture on every early return, so the caller's stream stays usable
+  struct CaptureGuard {
+    cudaStream_t st;
+    bool active = false;
+    ~CaptureGuard() {
+      if (!active) return;
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(st, &g);
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+    }
+  } capture{st};
+  if (graph) {
+    CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    capture.active = true;
+  }
+  // ---- the launch sequence (captured as a graph when opts.use_graph) ------------------------
+  CU(cudaMemcpyAsync(act, act_init_dev, act_init.size() * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   CU(cudaMemsetAsync(err, 0, sizeof(int), st));
   // test matrices: caller's host or device arrays (original order, single problem), or Philox draws
   // (problem p uses key seed + p); stored in tree order
@@ -668,14 +806,11 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
       const double* hsrc = side == 0 ? o.omega_host : o.psi_host;
       const double* dsrc = side == 0 ? o.omega_dev : o.psi_dev;
       if (hsrc) {
-        std::vector<double> tree_order(ns);
-        for (int64_t q = 0; q < n; ++q) std::memcpy(&tree_order[q * s], &hsrc[T.perm[q] * s], s * sizeof(double));
-        CU(cudaMemcpyAsync(dst, tree_order.data(), ns * sizeof(double), cudaMemcpyHostToDevice, st));
-        CU(cudaStreamSynchronize(st));  // the staging buffer goes out of scope
+        // staged above
       } else if (dsrc) {
         k_gather_orig<<<nblk(ns), 256, 0, st>>>(dsrc, F[p]->perm_dev, n, s, dst);
       } else {
-        k_gauss_tree<<<nblk(ns), 256, 0, st>>>(o.seed + (uint64_t)p, (uint32_t)side, F[p]->perm_dev, n, s, dst);
+        k_gauss_tree<<<nblk(ns), 256, 0, st>>>(seed_dev, (uint64_t)p, (uint32_t)side, F[p]->perm_dev, n, s, dst);
       }
       CU(cudaGetLastError());
     }
@@ -720,26 +855,9 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
   } evguard{evpool};
   cudaEvent_t ev[4];
   for (auto& e : ev) e = new_ev();
-  CU(cudaEventRecord(ev[0], st));
+  if (!graph) CU(cudaEventRecord(ev[0], st));
   // ---- a1: sampling Y = A Omega, Z = A* Psi, problem by problem --------------------------
   {
-    int64_t nmax = 0;
-    for (int p = 0; p < nprob; ++p) nmax = std::max(nmax, F[p]->n);
-    const int64_t nsmax = nmax * s;
-    double *cm_in = nullptr, *cm_out = nullptr;
-    float* conv = nullptr;
-    bool any_cb = false, any_builtin = false;
-    for (int p = 0; p < nprob; ++p) (F[p]->kind == RSRS_OP_CALLBACK ? any_cb : any_builtin) = true;
-    if (any_cb) {
-      CU(pool.alloc(&cm_in, nsmax));
-      CU(pool.alloc(&cm_out, nsmax));
-    }
-    const bool mixed = o.precision == RSRS_PREC_MIXED;
-    const bool tc = mixed && F[0]->sample_kernel == 2;
-    // tensor-core path: hi/lo planes of [Omega Psi] (2s x N each) and the FP32 points; SIMT path:
-    // an FP32 copy of one side
-    if (mixed && any_builtin)
-      CU(pool.alloc(&conv, tc ? 4 * s * tc_plane_ld(nmax) + tc_points_len(nmax, 3) : nsmax));
     rsrs_status r1 = RSRS_OK;
     timed(RSRS_K_SAMPLE, [&] {
       for (int p = 0; p < nprob && r1 == RSRS_OK; ++p) {
@@ -766,13 +884,8 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
     if (r1 != RSRS_OK) return r1;
     for (int p = 0; p < nprob; ++p)
       if (F[p]->kind != RSRS_OP_CALLBACK) bst.class_gflop[RSRS_K_SAMPLE] += 4.0 * (double)F[p]->n * F[p]->n * s * 1e-9;
-    if (conv) {
-      CU(cudaStreamSynchronize(st));
-      pool.release(conv);
-      cudaFree(conv);
-    }
   }
-  CU(cudaEventRecord(ev[1], st));
+  if (!graph) CU(cudaEventRecord(ev[1], st));
   // ---- a2..a8: heights 0.. (levels L..1 of each problem), colour by colour ------------------
   GroupArgs ga{};
   ga.s = s;
@@ -842,19 +955,23 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
   }
   for (int c = 0; c < RSRS_NCLASS; ++c)
     if (c != RSRS_K_SAMPLE) bst.class_gflop[c] = fl[c] * 1e-9;
-  CU(cudaEventRecord(ev[2], st));
+  if (!graph) CU(cudaEventRecord(ev[2], st));
   // ---- a9: root extraction A~_{Bt Bt} = Y_Bt pinv(Om_Bt) for every problem, then LU ----------
   {
     ga.desc = root_desc_dev;
     ga.nbox = nprob;
-    ga.fp32 = 0;  // the root blocks are extracted in FP64
+    // the mixed path extracts the root blocks like its boxes (FP32 workspace, 3xTF32 products) when
+    // Omega_Bt is well conditioned for that (s comfortably above |B_t|); otherwise in FP64.  The
+    // root LU and its inverse are FP64 either way.
+    ga.fp32 = root32 ? 1 : 0;
     bool any = false;
     for (const BoxDesc& d : rh) any = any || d.l > 0;
     if (any) {
       timed(RSRS_K_ROOT, [&] {
         launch_copy_segments(L, segs_dev + root_seg_off, (int)root_nseg, act, iwork);
         launch_gather_box(L, ga, items_gather(rh));
-        launch_gram(L, ga, items_gram(rh));
+        if (root32) launch_gram_tc(L, ga, rh);
+        else launch_gram(L, ga, items_gram(rh));
         for (int pn = 0; pn < max_root_panels; ++pn) {
           launch_chol_panel(L, ga, pn);
           launch_chol_trsm(L, ga, pn, items_chol_trsm(rh, pn));
@@ -862,32 +979,33 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
         }
         // two least-squares passes: the second solves for the residual of the first, so that the
         // normal equations' squared conditioning (Om_Bt can be square when s = |B_t|) is corrected
-        launch_proj_nt(L, ga, 0, items_proj_nt(rh));
-        launch_proj_solve(L, ga, 0, items_proj_solve(rh));
-        launch_proj_acc(L, ga, 0, items_proj_acc(rh, s));
-        launch_proj_nt(L, ga, 1, items_proj_nt(rh));
-        launch_proj_solve(L, ga, 1, items_proj_solve(rh));
+        for (int pass = 0; pass < 2; ++pass) {
+          if (pass) {
+            if (root32) launch_proj_acc_tc(L, ga, 0, rh);
+            else launch_proj_acc(L, ga, 0, items_proj_acc(rh, s));
+          }
+          if (root32) launch_proj_nt_tc(L, ga, pass, rh);
+          else launch_proj_nt(L, ga, pass, items_proj_nt(rh));
+          launch_proj_solve(L, ga, pass, items_proj_solve(rh));
+        }
       });
     }
-    std::vector<RootLU> rl;
-    int64_t max_root = 0;
     for (int p = 0; p < nprob; ++p) {
       const int64_t nroot = F[p]->root_size;
       if (nroot == 0) continue;
-      const double* xroot = reinterpret_cast<const double*>(workc) + rh[p].x_off;
       CU(cudaMemcpyAsync(F[p]->root_idx, iwork + root_iw_off[p], nroot * sizeof(int32_t), cudaMemcpyDeviceToDevice,
                          st));
-      CU(cudaMemcpyAsync(F[p]->root_A, xroot, nroot * nroot * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      CU(cudaMemcpyAsync(F[p]->root_LU, xroot, nroot * nroot * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      rl.push_back(RootLU{F[p]->root_LU, nroot, F[p]->root_piv, F[p]->root_inv});
-      max_root = std::max(max_root, nroot);
+      if (root32) {
+        const float* xroot = reinterpret_cast<const float*>(workc) + rh[p].x_off;
+        k_f32_to_f64<<<nblk(nroot * nroot), 256, 0, st>>>(xroot, nroot * nroot, F[p]->root_A);
+        ++launches;
+      } else {
+        const double* xroot = reinterpret_cast<const double*>(workc) + rh[p].x_off;
+        CU(cudaMemcpyAsync(F[p]->root_A, xroot, nroot * nroot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      }
+      CU(cudaMemcpyAsync(F[p]->root_LU, F[p]->root_A, nroot * nroot * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
-    if (!rl.empty()) {
-      RootLU* rl_dev;
-      CU(pool.alloc(&rl_dev, (int64_t)rl.size()));
-      CU(cudaMemcpyAsync(rl_dev, rl.data(), rl.size() * sizeof(RootLU), cudaMemcpyHostToDevice, st));
-      timed(RSRS_K_ROOT, [&] { launch_root_lu_inverse(L, rl_dev, (int)rl.size(), max_root, err); });
-    }
+    if (rl_dev) timed(RSRS_K_ROOT, [&] { launch_root_lu_inverse(L, rl_dev, (int)rl.size(), max_root, err); });
     for (int p = 0; p < nprob; ++p) {
       const int64_t nroot = F[p]->root_size;
       if (nroot == 0) continue;
@@ -897,18 +1015,35 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
                                       1e-9;
     }
   }
-  CU(cudaEventRecord(ev[3], st));
+  if (!graph) CU(cudaEventRecord(ev[3], st));
   CU(cudaGetLastError());
+  if (graph) {
+    capture.active = false;
+    CU(cudaStreamEndCapture(st, &cgraph));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, cgraph, 0);
+    cudaGraphDestroy(cgraph);
+    CU(ie);
+    sh->exec = exec;
+    sh->seed_dev = seed_dev;
+    sh->err_dev = err;
+    // the workspace stays with the factors: replays write to the same addresses
+    for (void* q : pool.ptrs) sh->ptrs.push_back(q);
+    pool.ptrs.clear();
+    CU(cudaGraphLaunch(exec, st));
+  }
   CU(cudaStreamSynchronize(st));
   int herr = 0;
   CU(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
   if (herr == kDevSingular) return fail(RSRS_E_SINGULAR, "zero pivot in an LU factorization");
   if (herr == kDevNonfinite) return fail(RSRS_E_NONFINITE, "non-finite or non-positive pivot");
   if (herr == kDevTimeout) return fail(RSRS_E_TIMEOUT, "a bounded device wait expired");
-  float t01, t12, t23;
-  CU(cudaEventElapsedTime(&t01, ev[0], ev[1]));
-  CU(cudaEventElapsedTime(&t12, ev[1], ev[2]));
-  CU(cudaEventElapsedTime(&t23, ev[2], ev[3]));
+  float t01 = 0.f, t12 = 0.f, t23 = 0.f;
+  if (!graph) {
+    CU(cudaEventElapsedTime(&t01, ev[0], ev[1]));
+    CU(cudaEventElapsedTime(&t12, ev[1], ev[2]));
+    CU(cudaEventElapsedTime(&t23, ev[2], ev[3]));
+  }
   for (const Rec& rc : recs) {
     float ms = 0.f;
     CU(cudaEventElapsedTime(&ms, rc.a, rc.b));
@@ -971,6 +1106,23 @@ rsrs_status rsrs_build(const rsrs_tree* tree, const rsrs_operator* op, int k, in
 rsrs_status rsrs_build_batched(int nprob, const rsrs_tree* const* trees, const rsrs_operator* ops, int k, int s,
                                const rsrs_options* opts, void* stream, rsrs_factor** out) {
   return build_impl(nprob, trees, ops, k, s, opts, stream, out);
+}
+
+rsrs_status rsrs_refactor(rsrs_factor* f, uint64_t seed, void* stream) {
+  if (!f) return fail(RSRS_E_INVAL, "refactor: null factor");
+  Shared* sh = f->sh.get();
+  if (!sh || !sh->exec) return fail(RSRS_E_INVAL, "refactor: the factor was built without use_graph");
+  cudaStream_t st = (cudaStream_t)stream;
+  k_set_u64<<<1, 1, 0, st>>>(sh->seed_dev, seed);
+  CU(cudaGetLastError());
+  CU(cudaGraphLaunch(sh->exec, st));
+  CU(cudaStreamSynchronize(st));
+  int herr = 0;
+  CU(cudaMemcpy(&herr, sh->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr == kDevSingular) return fail(RSRS_E_SINGULAR, "zero pivot in an LU factorization");
+  if (herr == kDevNonfinite) return fail(RSRS_E_NONFINITE, "non-finite or non-positive pivot");
+  if (herr == kDevTimeout) return fail(RSRS_E_TIMEOUT, "a bounded device wait expired");
+  return RSRS_OK;
 }
 
 void rsrs_factor_free(rsrs_factor* f) {

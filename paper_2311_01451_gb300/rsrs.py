@@ -23,9 +23,9 @@ STATUS = {0: "RSRS_OK", 1: "RSRS_E_INVAL", 2: "RSRS_E_UNDERSAMPLED", 3: "RSRS_E_
           8: "RSRS_E_TIMEOUT", 9: "RSRS_E_NOT_CONVERGED"}
 
 EXPORTS = ["rsrs_tree_build", "rsrs_tree_info", "rsrs_tree_perm", "rsrs_tree_schedule", "rsrs_tree_free",
-           "rsrs_build", "rsrs_build_batched", "rsrs_solve", "rsrs_solve_noalloc", "rsrs_apply", "rsrs_refine", "rsrs_residual", "rsrs_matvec", "rsrs_factor_stats",
+           "rsrs_build", "rsrs_build_batched", "rsrs_refactor", "rsrs_solve", "rsrs_solve_noalloc", "rsrs_apply", "rsrs_refine", "rsrs_residual", "rsrs_matvec", "rsrs_factor_stats",
            "rsrs_factor_box", "rsrs_factor_root", "rsrs_factor_sketches", "rsrs_factor_free",
-           "rsrs_status_string", "rsrs_last_error", "rsrs_kernel_class_name"]
+           "rsrs_status_string", "rsrs_last_error", "rsrs_kernel_class_name", "rsrs_stencil7_create", "rsrs_stencil7_matvec", "rsrs_stencil7_free"]
 
 MATVEC_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.c_int64, C.c_int32, C.c_void_p, C.c_int64,
                         C.c_void_p, C.c_int64, C.c_void_p)
@@ -41,7 +41,7 @@ class Options(C.Structure):
                 ("omega_host", C.c_void_p), ("psi_host", C.c_void_p), ("omega_dev", C.c_void_p),
                 ("psi_dev", C.c_void_p), ("keep_sketches", C.c_int), ("profile", C.c_int),
                 ("sample_kernel", C.c_int), ("mixed_cpqr", C.c_int), ("mixed_gemm", C.c_int),
-                ("residual_fp64", C.c_int)]
+                ("use_graph", C.c_int), ("residual_fp64", C.c_int)]
 
 
 NCLASS = 16
@@ -50,7 +50,8 @@ NCLASS = 16
 class TreeInfo(C.Structure):
     _fields_ = [("d", C.c_int), ("depth", C.c_int), ("n", C.c_int64), ("n_boxes", C.c_int64),
                 ("n_leaves", C.c_int64), ("n_compress", C.c_int64), ("n_groups", C.c_int64),
-                ("max_l", C.c_int64), ("root_size", C.c_int64), ("s_req", C.c_int64)]
+                ("max_l", C.c_int64), ("root_size", C.c_int64), ("s_req", C.c_int64),
+                ("s_req_mixed", C.c_int64)]
 
 
 class Stats(C.Structure):
@@ -91,6 +92,7 @@ def lib():
             "rsrs_build_batched": [C.c_int, C.POINTER(vp), C.POINTER(Operator), C.c_int, C.c_int, C.POINTER(Options),
                                    vp, C.POINTER(vp)],
             "rsrs_solve": [vp, vp, i64, i32, C.c_int, vp],
+            "rsrs_refactor": [vp, C.c_uint64, vp],
             "rsrs_solve_noalloc": [vp, vp, i64, i32, C.c_int, vp],
             "rsrs_apply": [vp, vp, i64, i32, C.c_int, vp],
             "rsrs_refine": [vp, vp, vp, i64, i32, dbl, C.c_int, vp, C.POINTER(RefineReport)],
@@ -100,6 +102,8 @@ def lib():
             "rsrs_factor_box": [vp, i64, C.POINTER(BoxView)],
             "rsrs_factor_root": [vp, vp, vp, C.POINTER(i64)],
             "rsrs_factor_sketches": [vp, vp, vp, vp, vp],
+            "rsrs_stencil7_create": [vp, C.c_int, C.POINTER(vp)],
+            "rsrs_stencil7_matvec": [vp, C.c_int, i64, i32, vp, i64, vp, i64, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -109,6 +113,8 @@ def lib():
         L.rsrs_tree_free.restype = None
         L.rsrs_factor_free.argtypes = [vp]
         L.rsrs_factor_free.restype = None
+        L.rsrs_stencil7_free.argtypes = [vp]
+        L.rsrs_stencil7_free.restype = None
         L.rsrs_status_string.argtypes = [C.c_int]
         L.rsrs_status_string.restype = C.c_char_p
         L.rsrs_kernel_class_name.argtypes = [C.c_int]
@@ -186,6 +192,36 @@ class Tree:
             self._h = None
 
 
+class Stencil7:
+    """rsrs_stencil7: the 7-point variable-coefficient operator on an m^3 cell grid as a device
+    matvec callback (pass it as ``matvec`` with ``kind=RSRS_OP_CALLBACK``)."""
+
+    def __init__(self, coef: np.ndarray, m: int):
+        b = np.ascontiguousarray(coef, dtype=np.float64).reshape(-1)
+        if b.size != m ** 3:
+            raise ValueError("need m^3 coefficients")
+        h = C.c_void_p()
+        _check(lib().rsrs_stencil7_create(b.ctypes.data_as(C.c_void_p), m, C.byref(h)))
+        self._h = h
+        self.m = m
+        self.n = m ** 3
+        self.fn = C.cast(lib().rsrs_stencil7_matvec, MATVEC_FN)
+
+    def matvec(self, X, Y, stream=None):
+        """Y <- A X for (ncols, N) float64 CUDA tensors (column-major N x ncols)."""
+        px, ld, nc = _cm(X)
+        py, ldy, ncy = _cm(Y)
+        rc = lib().rsrs_stencil7_matvec(self._h, 0, self.n, nc, px, ld, py, ldy, _stream_ptr(stream))
+        if rc != 0:
+            raise RSRSError(7, f"stencil matvec returned {rc}")
+        return Y
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.rsrs_stencil7_free(self._h)
+            self._h = None
+
+
 class Factor:
     """rsrs_build result: the invertible factorization of eq. (Afact)."""
 
@@ -194,7 +230,7 @@ class Factor:
                  psi: np.ndarray | None = None, seed: int = 0, passes: int = 0, keep_sketches: bool = False,
                  matvec=None, stream=None, profile: bool = False,
                  sample_kernel: int = 0, mixed_cpqr: int = 0, residual_fp64: bool = False,
-                 mixed_gemm: int = 0):
+                 mixed_gemm: int = 0, use_graph: bool = False):
         self.tree = tree
         self.n = tree.n
         self._cb = None
@@ -202,12 +238,18 @@ class Factor:
         if kind == RSRS_OP_CALLBACK:
             if matvec is None:
                 raise ValueError("callback operator needs matvec")
-            self._cb = MATVEC_FN(matvec)
-            op.fn = self._cb
+            if isinstance(matvec, Stencil7):  # a library-side device matvec: no Python in the loop
+                self._cb = matvec
+                op.fn = matvec.fn
+                op.ctx = matvec._h
+            else:
+                self._cb = MATVEC_FN(matvec)
+                op.fn = self._cb
         opts = Options(precision=precision, p=p, proj_passes=passes, seed=seed,
                        keep_sketches=int(keep_sketches), profile=int(profile),
                        sample_kernel=sample_kernel,
-                       mixed_cpqr=mixed_cpqr, residual_fp64=int(residual_fp64), mixed_gemm=mixed_gemm)
+                       mixed_cpqr=mixed_cpqr, residual_fp64=int(residual_fp64), mixed_gemm=mixed_gemm,
+                       use_graph=int(use_graph))
         self._om = self._ps = None
         if omega is not None and hasattr(omega, "data_ptr"):  # device tensors (N, s), original order
             self._om, self._ps = omega, psi
@@ -224,6 +266,12 @@ class Factor:
         self._h = h
         self.s = s
         self.k = k
+
+    def refactor(self, seed: int, stream=None):
+        """rsrs_refactor: rebuild in place from new test matrices (key ``seed``) by replaying the
+        build's captured graph (the factor must have been built with ``use_graph=True``)."""
+        _check(lib().rsrs_refactor(self._h, seed, _stream_ptr(stream)))
+        return self
 
     def solve(self, F, adjoint: bool = False, stream=None):
         """In place: F <- A_approx^-1 F, F a (nrhs, N) float64 CUDA tensor."""
@@ -313,7 +361,7 @@ class Factor:
 def build_batched(trees, kinds, k: int, s: int, shifts, scales, precision: int = RSRS_PREC_FP64, p: int = -1,
                   seed: int = 0, passes: int = 0, profile: bool = False, sample_kernel: int = 0,
                   keep_sketches: bool = False, mixed_cpqr: int = 0, residual_fp64: bool = False,
-                  mixed_gemm: int = 0,
+                  mixed_gemm: int = 0, use_graph: bool = False,
                   stream=None) -> list:
     """rsrs_build_batched: factors of independent problems built in one set of launches."""
     n = len(trees)
@@ -327,7 +375,7 @@ def build_batched(trees, kinds, k: int, s: int, shifts, scales, precision: int =
     opts = Options(precision=precision, p=p, proj_passes=passes, seed=seed, profile=int(profile),
                    sample_kernel=sample_kernel,
                    keep_sketches=int(keep_sketches), mixed_cpqr=mixed_cpqr,
-                   residual_fp64=int(residual_fp64), mixed_gemm=mixed_gemm)
+                   residual_fp64=int(residual_fp64), mixed_gemm=mixed_gemm, use_graph=int(use_graph))
     _check(lib().rsrs_build_batched(n, handles, ops, k, s, C.byref(opts), _stream_ptr(stream), outs))
     res = []
     for i in range(n):

@@ -25,7 +25,7 @@ def R():
 
 def test_every_declared_symbol_is_exported(R):
     hdr = open(os.path.join(ROOT, "include", "rsrs.h")).read()
-    declared = set(re.findall(r"\b(rsrs_[a-z_]+)\s*\(", hdr)) - {"rsrs_matvec_fn"}
+    declared = set(re.findall(r"\b(rsrs_[a-z0-9_]+)\s*\(", hdr)) - {"rsrs_matvec_fn"}
     lib = R.lib()
     for name in sorted(declared):
         assert hasattr(lib, name), name
@@ -51,6 +51,7 @@ def test_tree_and_schedule_match_oracle(R, case):
     assert info.depth == ot.depth
     assert np.array_equal(t.perm(), ot.perm)
     assert info.s_req == osc.s_req and info.root_size == osc.root_size and info.max_l == osc.max_l
+    assert info.s_req_mixed >= info.s_req
     sch = t.schedule(k)
     ref = np.array([[st["level"], st["colour"], st["b"], st["n"], st["box"].first_pos] for st in osc.steps])
     assert np.array_equal(sch[:, [0, 1, 3, 4, 5]], ref)

@@ -109,3 +109,16 @@ def test_stencil7_closed_forms():
     coef[0], coef[1] = 1.0, 3.0
     a2 = ops.Stencil7Operator(m, coef).dense()
     assert math.isclose(-a2[0, 1], 2 * 1.0 * 3.0 / 4.0)
+
+
+def test_cpqr_rows_below_the_absolute_floor_are_dependent():
+    """A sketch at the rounding level of what was cancelled (floor): every pivot is dependent, the
+    skeletons are the first k rows in original order and T = 0."""
+    rng = np.random.default_rng(11)
+    m = 1e-17 * rng.standard_normal((12, 40))
+    skel, red, t = la.cpqr_id(m, 5, 1e-10, floor=1e-10)
+    assert list(skel) == [0, 1, 2, 3, 4] and list(red) == list(range(5, 12))
+    assert not t.any()
+    # without the floor the same matrix is ranked by its noise
+    skel2, _, t2 = la.cpqr_id(m, 5, 1e-10)
+    assert list(skel2) != [0, 1, 2, 3, 4] and t2.any()

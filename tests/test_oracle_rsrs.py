@@ -239,3 +239,22 @@ def test_root_bound_keeps_the_root_block_well_conditioned():
     est = (np.sqrt(s) + np.sqrt(m)) / (np.sqrt(s) - np.sqrt(m))
     assert cond[s] < 2 * est < 20 * est < cond[m]
     assert res[s] < 2e-3 and res[s] < res[m]
+
+
+def test_sparse_operator_boxes_have_no_far_field():
+    """For the 7-point operator a box's far-field block is exactly zero until eliminations next to
+    it create fill, so for the first colour of the finest level the nullified sketch is at the
+    rounding level of the near field it cancelled: the ID takes every pivot as dependent (skeletons
+    in tree order, T = 0).  Later colours see fill from their eliminated neighbours and compress
+    genuinely.  The factorization stays an exact inverse pair."""
+    pr = W.Problem(name="st8", cfg=4, problem=0, d=3, kernel="stencil7", points=W.grid_points_3d(8), leaf=8,
+                   k=4, s_cfg=0, nrhs=2, diag_shift=0.0, scale=1.0, grid_side=8)
+    tree, sched, fac, _ = rsrs.build(pr)
+    first = [bf for bf in fac.boxes if bf.level == tree.depth and bf.colour == 0]
+    assert first and any(not bf.pivot_dependent[0] for bf in fac.boxes)
+    for bf in first:
+        assert bf.pivot_dependent[0]
+        assert not bf.T.any()
+        assert np.array_equal(bf.S, np.sort(bf.B)[: len(bf.S)]) or np.array_equal(bf.S, bf.B[: len(bf.S)])
+    b = pr.rhs()
+    assert np.allclose(rsrs.apply(fac, rsrs.solve(fac, b)), b, rtol=0, atol=1e-12 * np.abs(b).max())
