@@ -1,6 +1,6 @@
 """The remaining named workloads at full size, in the mixed precision the benchmark runs them in:
 64 independent 2D problems with N ~ U{2048..16384} built together (rsrs_build_batched), and
-32,768 uniform random 3D points with the 1/r kernel (k = 64, s = the mixed-precision sample bound).  The oracle cannot factor
+32,768 uniform random 3D points with the 1/r kernel (k = 64, s = the mixed sample bound).  The oracle cannot factor
 these in a test's time, so each refined solution is checked through residual rows the oracle's
 operator computes exactly, and the refinement history shows the factor is a good preconditioner.
 """
