@@ -936,7 +936,7 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(GroupArgs g) {
 // patterns (monotone for non-negative doubles; ties to the lowest tree index), and the Householder
 // scalars and the dependent-pivot test of k_cpqr are evaluated in FP64.  Output as
 // k_cpqr_cluster: R rows by point (FP64), permutation and first dependent step.
-__global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs, int in_global) {
+__global__ void __launch_bounds__(1024, 1) k_cpqr32_cluster(GroupArgs g, int cs, int in_global) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
@@ -958,8 +958,8 @@ __global__ void __launch_bounds__(256) k_cpqr32_cluster(GroupArgs g, int cs, int
   // workspace when the box is too large for the cluster's shared memory (row pitch 2s)
   float* S = in_global ? Mg + t_lo : reinterpret_cast<float*>(csm + b + (4 * b + 1) / 2 + 1);
   const int64_t lds = in_global ? c : (int64_t)cs;
-  __shared__ unsigned long long red_v[8];
-  __shared__ int red_i[8];
+  __shared__ unsigned long long red_v[32];
+  __shared__ int red_i[32];
   __shared__ double s_r00;
   __shared__ float s_vj, s_f2;
   __shared__ int s_j0;
@@ -1779,7 +1779,7 @@ bool launch_cpqr32(Launch L, const GroupArgs& g, int max_b) {
   if (smem > 200 * 1024) return false;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(g.nbox * C));
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(1024);  // one CTA per SM: many warps to hide the shared-memory latency of each step
   cfg.dynamicSmemBytes = smem;
   cfg.stream = L.st;
   cudaLaunchAttribute attr1[1];

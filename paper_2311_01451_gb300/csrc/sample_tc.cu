@@ -78,6 +78,14 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
 }
+// The completion of this CTA's issued products arrives on the mbarrier at the same offset in every
+// CTA of the cluster pair (both read the stage's B tile halves that the pair loaded together).
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"((uint16_t)3)
+      : "memory");
+}
 
 __device__ __forceinline__ void bar_init(uint32_t bar, int count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
@@ -104,13 +112,22 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
-// 2D tiled TMA load of box (TK points x TN columns) at (x = first point, y = first column).
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+// 2D tiled TMA load of box (TK points x TN/2 columns) at (x = first point, y = first column),
+// multicast to the same shared-memory offset (and mbarrier) in both CTAs of the cluster pair.
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, "
+      "%3}], [%4], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"((uint16_t)3)
       : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
@@ -146,7 +163,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int s = 0; s < NSTAGE; ++s) {
       bar_init(smem_u32(&full_a[s]), NPROD);
       bar_init(smem_u32(&full_b[s]), 1);
-      bar_init(smem_u32(&empty[s]), 1);
+      bar_init(smem_u32(&empty[s]), 2);  // the products of both CTAs of the pair
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -160,6 +177,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
+  const uint32_t crank = cluster_rank();
+  // the partner must have initialised its barriers before any multicast reaches them
+  cluster_sync_all();
 
   if (warp < NPROD / 32) {
     // ---- producers: kernel values of row arow, points akq..akq+7 of each chunk; the points of the
@@ -231,9 +251,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int st = (int)(ch & 1);
       unsigned char* Bhi = smem + st * STAGE_BYTES + 2 * A_BYTES;
       const uint32_t bar = smem_u32(&full_b[st]);
+      // this CTA loads half of the columns of the B tile for both CTAs of the pair; the stage's
+      // barrier counts the bytes of both halves of both planes
       bar_expect_tx(bar, 2u * B_BYTES);
-      tma_load_2d(smem_u32(Bhi), &tm_hi, (int)(ch * TK), (int)c0, bar);
-      tma_load_2d(smem_u32(Bhi + B_BYTES), &tm_lo, (int)(ch * TK), (int)c0, bar);
+      const uint32_t half = crank * (B_BYTES / 2);
+      tma_load_2d_pair(smem_u32(Bhi) + half, &tm_hi, (int)(ch * TK), (int)(c0 + crank * (TN / 2)), bar);
+      tma_load_2d_pair(smem_u32(Bhi + B_BYTES) + half, &tm_lo, (int)(ch * TK), (int)(c0 + crank * (TN / 2)), bar);
       armed[st] = true;
       armed_par[st] = (uint32_t)((ch >> 1) & 1);
     };
@@ -255,7 +278,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mma_tf32(tmem, smem_desc(a_hi + ko), smem_desc(b_lo + ko), idesc, 1u);
         mma_tf32(tmem, smem_desc(a_lo + ko), smem_desc(b_hi + ko), idesc, 1u);
       }
-      mma_commit(smem_u32(&empty[st]));
+      mma_commit_pair(smem_u32(&empty[st]));
       if (ch + 1 < nchunk) {
         // the other stage is free once the products of chunk ch - 1 are done
         if (ch >= 1 && !bar_wait(smem_u32(&empty[st ^ 1]), (uint32_t)(((ch - 1) >> 1) & 1))) ok = false;
@@ -309,6 +332,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  // neither CTA leaves while its partner may still signal its barriers
+  cluster_sync_all();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   if (tid == 0 && s_timeout && err) atomicCAS(err, 0, kDevTimeout);
 }
@@ -346,7 +371,7 @@ bool plane_map(CUtensorMap* m, const float* base, int64_t n, int64_t ncols, int6
   if (!enc || (ldp & 3) || ((uintptr_t)base & 15)) return false;
   cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)ncols};
   cuuint64_t strides[1] = {(cuuint64_t)ldp * sizeof(float)};
-  cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)TN};
+  cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)(TN / 2)};
   cuuint32_t estr[2] = {1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -375,13 +400,26 @@ bool launch_kernel_matvec_tc(Launch L, int kind, const float* p32, int64_t n, do
     cudaFuncSetAttribute(k_kmv_tc<RSRS_OP_LOG2D, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     cudaFuncSetAttribute(k_kmv_tc<RSRS_OP_INVR3D, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   });
-  dim3 grid((unsigned)((n + TM - 1) / TM), (unsigned)((ncols + TN - 1) / TN));
+  // row tiles in pairs (one thread-block cluster each) that share the B tile of their column tile
+  const unsigned gx = (unsigned)(((n + TM - 1) / TM + 1) / 2 * 2);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(gx, (unsigned)((ncols + TN - 1) / TN));
+  cfg.blockDim = dim3(NTHREADS);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = L.st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
   if (kind == RSRS_OP_LOG2D)
-    k_kmv_tc<RSRS_OP_LOG2D, 2><<<grid, NTHREADS, SMEM_BYTES, L.st>>>(mh, ml, p32, n, shift, scale, in0, in1, out0,
-                                                                     out1, ld, ncols0, ncols, err);
+    cudaLaunchKernelEx(&cfg, k_kmv_tc<RSRS_OP_LOG2D, 2>, mh, ml, p32, n, shift, scale, in0, in1, out0, out1, ld, ncols0,
+                       ncols, err);
   else
-    k_kmv_tc<RSRS_OP_INVR3D, 3><<<grid, NTHREADS, SMEM_BYTES, L.st>>>(mh, ml, p32, n, shift, scale, in0, in1, out0,
-                                                                      out1, ld, ncols0, ncols, err);
+    cudaLaunchKernelEx(&cfg, k_kmv_tc<RSRS_OP_INVR3D, 3>, mh, ml, p32, n, shift, scale, in0, in1, out0, out1, ld,
+                       ncols0, ncols, err);
   if (L.counter) ++*L.counter;
   return true;
 }
