@@ -244,9 +244,11 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     prec = R.RSRS_PREC_MIXED if args.precision == "mixed" else R.RSRS_PREC_FP64
 
+    tune, tune_info = _autotune(args, R, tree, kind, pr.k, s, pr.diag_shift, pr.scale, prec)
+
     def step(seed, profile=False):
         f = R.Factor(tree, kind, pr.k, s, shift=pr.diag_shift, scale=pr.scale, precision=prec, seed=seed,
-                     profile=profile, sample_kernel=args.sample_kernel)
+                     profile=profile, sample_kernel=args.sample_kernel, tune=tune)
         rep = f.refine(B, X, rtol=RTOL, maxit=30)
         st = f.stats()
         cls = f.class_stats()
@@ -304,9 +306,10 @@ def run_gpu(args):
                      "peak_note": peak_note,
                      "algorithmic_gflop_per_step": dom_gflop, "launches_per_step": dom_launch},
         "clocks": clk.summary(),
+        "autotune": tune_info,
     }
     # solves/s with the factor reused (refined and plain), and the FP64 comparison
-    f = R.Factor(tree, kind, pr.k, s, shift=pr.diag_shift, scale=pr.scale, precision=prec, seed=7)
+    f = R.Factor(tree, kind, pr.k, s, shift=pr.diag_shift, scale=pr.scale, precision=prec, seed=7, tune=tune)
     torch.cuda.synchronize()
     a0 = time.perf_counter()
     rep = f.refine(B, X, rtol=RTOL, maxit=30)
@@ -344,7 +347,7 @@ def run_gpu(args):
     t2 = R.Tree(pr.points, pr.leaf)
     Bd = b_pin.to("cuda", non_blocking=True)
     Xd = torch.zeros_like(Bd)
-    f = R.Factor(t2, kind, pr.k, s, shift=pr.diag_shift, scale=pr.scale, precision=prec, seed=11)
+    f = R.Factor(t2, kind, pr.k, s, shift=pr.diag_shift, scale=pr.scale, precision=prec, seed=11, tune=tune)
     f.refine(Bd, Xd, rtol=RTOL, maxit=30)
     x_pin.copy_(Xd, non_blocking=True)
     torch.cuda.synchronize()
@@ -384,9 +387,13 @@ def run_gpu_batched(args):
     Xs = [torch.zeros_like(b) for b in Bs]
     stream = torch.cuda.current_stream()
 
+    tune, tune_info = _autotune(args, R, trees, kinds, k, s, [p.diag_shift for p in prs], [p.scale for p in prs],
+                                prec)
+
     def step(seed, profile=False):
         fs = R.build_batched(trees, kinds, k, s, [p.diag_shift for p in prs], [p.scale for p in prs],
-                             precision=prec, seed=seed, profile=profile, sample_kernel=args.sample_kernel)
+                             precision=prec, seed=seed, profile=profile, sample_kernel=args.sample_kernel,
+                             tune=tune)
         its = [f.refine(b, x, rtol=RTOL, maxit=30).iterations for f, b, x in zip(fs, Bs, Xs)]
         st, cls = fs[0].stats(), fs[0].class_stats()
         del fs
@@ -432,8 +439,23 @@ def run_gpu_batched(args):
                      "frac": achieved / peak, "traffic": None, "peak_note": peak_note,
                      "algorithmic_gflop_per_step": dom_gflop, "launches_per_step": dom_launch},
         "clocks": clk.summary(),
+        "autotune": tune_info,
     }
     print(json.dumps(line), flush=True)
+
+
+def _autotune(args, R, trees, kinds, k, s, shifts, scales, prec):
+    """Launch shapes from the library's autotuner (before the warm-up; cached per device and
+    workload in the temporary directory), or the defaults with --tune none."""
+    if args.tune == "none":
+        return None, None
+    import tempfile
+    cache = os.path.join(tempfile.gettempdir(), "rsrs_tune_cache.txt")
+    t0 = time.perf_counter()
+    tune, rep = R.autotune(trees, kinds, k, s, shifts, scales, precision=prec, reps=1, cache=cache,
+                           sample_kernel=args.sample_kernel)
+    rep["seconds"] = round(time.perf_counter() - t0, 2)
+    return tune, {"tune": tune, **rep}
 
 
 def main():
@@ -448,6 +470,8 @@ def main():
     ap.add_argument("--sample-kernel", type=int, default=0, help="mixed sampling: 0 default, 1 FP32 SIMT, 2 tcgen05")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--tune", choices=["auto", "none"], default="auto",
+                    help="launch shapes: the library's autotuner (cached) or the defaults")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -80,6 +80,30 @@ enum {
                         /* LU, the root, the solve and the refinement residual             */
 };
 
+/* Tile shapes of the tensor-core sampling product: column tile x pipeline stages. */
+enum {
+  RSRS_SAMPLE_TILE_DEFAULT = 0,  /* the library's choice (256 x 2)                               */
+  RSRS_SAMPLE_TILE_256x2 = 1,    /* 256 columns per CTA, two stages                              */
+  RSRS_SAMPLE_TILE_128x3 = 2,    /* 128 columns, three stages                                    */
+  RSRS_SAMPLE_TILE_192x2 = 3     /* 192 columns, two stages                                      */
+};
+
+/* Launch shapes of the kernels whose best shape depends on the problem and the device; all zero
+ * selects the library's defaults.  Every value computes the same quantities (the shapes change at
+ * most the grouping of floating-point sums: the sampling tiles not even that), so a tuned
+ * configuration can be reused for any problem of its kind.  rsrs_autotune picks one by timing.
+ * Not in the paper (a property of this GPU implementation). */
+typedef struct {
+  int32_t sample_tile;     /* RSRS_SAMPLE_TILE_*                                            */
+  int32_t cpqr_cluster;    /* mixed path's cluster CPQR: CTAs per box, 0 = the fewest whose  */
+                           /* distributed shared memory holds the sketch; 2, 4, 8 or 16     */
+                           /* (never below that fewest)                                     */
+  int32_t cpqr_threads;    /* threads per CTA of that CPQR: 0 = 1024; 256, 512 or 1024      */
+  int32_t residual_split;  /* point-range splits of the float-float refinement residual:    */
+                           /* 0 = enough CTAs for four per SM; 1..16                        */
+  int32_t reserved[4];     /* zero                                                          */
+} rsrs_tune_t;
+
 typedef struct {
   int precision;          /* RSRS_PREC_*                                               */
   int p;                  /* oversampling; < 0 selects p = k (Sec. 5)                  */
@@ -98,17 +122,19 @@ typedef struct {
                           /* default 0) 3xTF32 on the tensor cores (tcgen05, TMA)       */
   int mixed_cpqr;         /* mixed precision: 0 default = FP32 reflectors on the sketch  */
                           /* held in distributed shared memory (thread-block cluster of */
-                          /* up to 16 CTAs), pivots chosen on FP64 norm sums, when the  */
-                          /* box fits; 1 = FP64 CPQR in global memory (FP64 always)     */
-  int mixed_gemm;         /* mixed precision: 0 default = Grams, least-squares right-hand */
-                          /* sides and projection updates as 3xTF32 tcgen05 products;  */
-                          /* 1 = FP32 SIMT                                             */
+                          /* up to 16 CTAs), pivots chosen on FP64 residual norms, when */
+                          /* the box fits; 1 = FP64 CPQR in global memory (FP64 always) */
+  int mixed_gemm;         /* mixed precision: 0 default = Grams, their blocked Cholesky   */
+                          /* factors and L^-T, least-squares right-hand sides, solves  */
+                          /* and projection updates as 3xTF32 tcgen05 products;        */
+                          /* 1 = FP32 SIMT (Cholesky and substitution)                 */
   int use_graph;          /* 1: capture the build's launch sequence as one CUDA graph    */
                           /* kept with the factors, so rsrs_refactor can replay it;    */
                           /* needs device-drawn test matrices; no per-class timings   */
   int residual_fp64;      /* rsrs_refine with a built-in kernel: 0 default = residual in */
                           /* float-float (48-bit) arithmetic on the FP32 pipe, about    */
                           /* 1e-14 relative; 1 = residual in FP64 arithmetic            */
+  rsrs_tune_t tune;       /* launch shapes (zero: defaults); kept with the factor       */
 } rsrs_options;
 
 typedef struct {
@@ -203,6 +229,29 @@ void rsrs_stencil7_free(rsrs_stencil7* s);
  * refused with RSRS_E_INVAL. */
 rsrs_status rsrs_build_batched(int nprob, const rsrs_tree* const* trees, const rsrs_operator* ops, int k, int s,
                                const rsrs_options* opts, void* stream, rsrs_factor** out);
+
+typedef struct {
+  int candidates;         /* builds (and residual products) timed                      */
+  int from_cache;         /* 1: the configuration came from the cache file, nothing timed */
+  double default_ms;      /* device time of the tuned kernel classes with all-zero tune */
+  double tuned_ms;        /* the same with the configuration returned                  */
+} rsrs_tune_report;
+
+/* Autotuner (not in the paper: picks launch shapes of this implementation).  Builds the given
+ * problem(s) (arguments as rsrs_build_batched; opts->tune is the starting point) once per
+ * candidate value of one rsrs_tune_t field at a time, the others held at the best found so far,
+ * and keeps the value with the smallest device time of the kernel class the field governs (best
+ * of `reps` builds, CUDA events): sample_tile on the sampling product (mixed precision, built-in
+ * kernels), cpqr_cluster and cpqr_threads on the CPQR (mixed precision, cluster CPQR), and
+ * residual_split on one float-float refinement residual of 16 columns (built-in kernels).  Fields
+ * that do not apply stay 0.  cache_path (optional): a text file with one line per tuned
+ * configuration, keyed by the device name, operator kind, number of problems, total N, d, k, s
+ * and precision; a matching line is returned without timing (report->from_cache = 1), otherwise
+ * the result is appended.  Build errors of a candidate are returned as from rsrs_build; no factor
+ * is kept.  out receives the configuration; report (optional) the counts and times. */
+rsrs_status rsrs_autotune(int nprob, const rsrs_tree* const* trees, const rsrs_operator* ops, int k, int s,
+                          const rsrs_options* opts, int reps, const char* cache_path, void* stream,
+                          rsrs_tune_t* out, rsrs_tune_report* report);
 
 /* Rebuilds in place every factor of the build that f belongs to (all problems of a batched
  * build) from new test matrices drawn with key `seed` (problem p: seed + p), by replaying the

@@ -21,7 +21,10 @@ enum DevErr : int { kDevOk = 0, kDevSingular = 1, kDevNonfinite = 2, kDevTimeout
 struct BoxDesc {
   int32_t b, n, l, kp, r, pad_;
   int64_t bn_off;   // int32 work: l tree positions [B_act | N_act]
-  int64_t g_off;    // workc: two l x l Grams / Cholesky factors (Omega side, then Psi side)
+  int64_t g_off;    // workc: two l x l Grams / Cholesky factors (Omega side, then Psi side); row
+                    //   pitch and side stride l and l * l on the SIMT path, gram_ld(l) and
+                    //   l * gram_ld(l) on the tensor-core path (room for 2 l gram_ld(l))
+  int64_t t_off;    // workc (tensor-core path): two b x gram_ld(l) blocks X L^-T of the projection
   int64_t x_off;    // workc: two b x l least-squares coefficient blocks (Y, Z)
   int64_t x2_off;   // workc: two b x l correction-pass blocks
   int64_t mc_off;   // workc: b x 2s sketches [Y_B | Z_B], projected in place
@@ -31,7 +34,8 @@ struct BoxDesc {
   int64_t cp_off;   // work (FP64): CPQR R rows, kp x b
   int64_t sn_off;   // work (FP64): b squared row norms of [Y_B | Z_B] before nullification
   int64_t li_off;   // workc: inverses (and their transposes) of the 64 x 64 diagonal Cholesky
-                    //   blocks, 2 sides x nblk x 2 x 64 x 64
+                    //   blocks, 2 sides x nblk x 2 x 64 x 64 (SIMT path); inverses of the
+                    //   128 x 128 diagonal blocks, 2 sides x nblk128 x 128 x 128 (tensor-core path)
   int64_t pv_off;   // int32 work: b CPQR local permutation, then the first dependent step
   int64_t fi_off;   // int32 factor: R (r), S (kp), N (n), LU pivots (r)
   int64_t fd_off;   // double factor: T (kp x r), XRR (r x r), LU (r x r), LcT (r x (kp+n)), Uc (r x (kp+n)),
@@ -94,18 +98,21 @@ void launch_split_transpose(Launch L, const double* in, int64_t n, int64_t s, fl
 // a bounded wait that expires records kDevTimeout in *err.
 // FP64-accurate residual product in float-float arithmetic on the FP32 pipe (refinement):
 // out = shift*in + scale*K*in, rows in tree order (ld_in, ld_out), any number of columns;
-// scratch: ff_scratch_floats(n, d, ncols) floats.
-int64_t ff_scratch_floats(int64_t n, int d, int ncols);
+// scratch: ff_scratch_floats(n, d, ncols, split) floats.  split: point-range splits of the sums
+// (partials added in a second kernel), 0 = enough CTAs for four per SM, else 1..16.
+int64_t ff_scratch_floats(int64_t n, int d, int ncols, int split);
 void launch_kernel_matvec_ff(Launch L, int kind, const double* pts, int d, int64_t n, double shift, double scale,
                              const double* in, int64_t ld_in, double* out, int64_t ld_out, int64_t ncols,
-                             float* scratch);
+                             float* scratch, int split);
 
 int64_t tc_plane_ld(int64_t n);
 int64_t tc_points_len(int64_t n, int d);
 void launch_points_f32(Launch L, const double* pts, int64_t n, int d, float* out);
+// variant: RSRS_SAMPLE_TILE_* (column tile x stages).
 bool launch_kernel_matvec_tc(Launch L, int kind, const float* p32, int64_t n, double shift, double scale,
                              const double* in0, const double* in1, double* out0, double* out1, int64_t ld,
-                             int64_t ncols0, int64_t ncols, const float* bhi, const float* blo, int64_t ldp, int* err);
+                             int64_t ncols0, int64_t ncols, const float* bhi, const float* blo, int64_t ldp, int* err,
+                             int variant);
 
 
 // Group-batched kernels (descriptors of one (level, colour) group).
@@ -142,6 +149,14 @@ void launch_proj_acc(Launch L, const GroupArgs& g, int pass, int64_t items);    
 void launch_gram_tc(Launch L, const GroupArgs& g, const std::vector<BoxDesc>& h);
 void launch_proj_nt_tc(Launch L, const GroupArgs& g, int pass, const std::vector<BoxDesc>& h);
 void launch_proj_acc_tc(Launch L, const GroupArgs& g, int pass, const std::vector<BoxDesc>& h);
+// Tensor-core path of the Gram factorisation and the projection solve (FP32 workspace, Gram from
+// launch_gram_tc): blocked Cholesky G = L L^T with 128-wide panels (diagonal blocks factored and
+// inverted by one CTA each, panel and trailing products in 3xTF32), then U = L^-T by blocked
+// substitution, stored in the upper block triangle of G (lower: L~_ik = L_ii^-1 L_ik).
+// launch_solve_tc: X <- X G^-1 = (X U) U^T for the pass's coefficients (pass 1 also adds the
+// result into the pass-0 coefficients).
+void launch_chol_tc(Launch L, const GroupArgs& g, const std::vector<BoxDesc>& h);
+void launch_solve_tc(Launch L, const GroupArgs& g, int pass, const std::vector<BoxDesc>& h);
 
 // Root blocks of a build: LU with partial pivoting in place in A (LAPACK interchange record in
 // piv) and the explicit inverse in inv, all problems at once, FP64.
@@ -156,7 +171,8 @@ void launch_root_lu_inverse(Launch L, const RootLU* R_dev, int nprob, int64_t ma
 void launch_cpqr(Launch L, const GroupArgs& g, int max_b);                         // ID pivots + R
 // FP32 CPQR on the compute-type sketch held in distributed shared memory (mixed path); false when
 // the group's boxes do not fit a cluster of at most 16 CTAs (nothing launched).
-bool launch_cpqr32(Launch L, const GroupArgs& g, int max_b);
+// cluster: CTAs per box (0 = the fewest that hold the sketch; never fewer); threads: per CTA (0 = 1024).
+bool launch_cpqr32(Launch L, const GroupArgs& g, int max_b, int cluster, int threads);
 void launch_id_finish(Launch L, const GroupArgs& g, int max_b);                    // T, R/S/N lists
 void launch_ef_update(Launch L, const GroupArgs& g, int64_t items);                // E, F on sketches
 void launch_extract(Launch L, const GroupArgs& g, int64_t items);                  // X blocks
@@ -167,6 +183,15 @@ void launch_schur(Launch L, const GroupArgs& g, int64_t items);                 
 // Number of 64-row x 64-col tiles for the group kernels (host-side planning).
 constexpr int kT = 64;
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+// Tensor-core path: 128-wide Cholesky panels; the Gram's row pitch is padded to 4 elements so that
+// its rows start 16-byte aligned for the operand loads.
+constexpr int kTB = 128;
+__host__ __device__ inline int64_t gram_ld(int64_t l) { return (l + 3) & ~(int64_t)3; }
+// Compute-type elements of one box's diagonal-inverse area (both sides), either path.
+inline int64_t li_elems(int64_t l) {
+  const int64_t a = 2 * cdiv(l, kT) * 2 * kT * kT, b = 2 * cdiv(l, kTB) * kTB * kTB;
+  return a > b ? a : b;
+}
 __host__ __device__ inline int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 __host__ __device__ inline int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }
 

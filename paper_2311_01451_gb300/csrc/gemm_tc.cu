@@ -11,6 +11,7 @@
 // TMEM accumulator.  Three stages; per stage an mbarrier for "operands written" (256 arrivals) and
 // one for "stage free" (tcgen05.commit).  Every wait is bounded: on expiry the kernel records
 // kDevTimeout and completes without hanging.
+#include <algorithm>
 #include <cstdint>
 
 #include "common.cuh"
@@ -51,10 +52,11 @@ struct TcTile {
   float* D;        // element (i, j) at D + i * ldd + j
   int64_t ldd;
   float alpha, beta;
+  float* D2 = nullptr;  // when set, also D2(i, j) += alpha * acc (same ldd)
 };
 
 // Job functors: tiles per box (count) and the tile for a box-local index (tile).
-struct GramJob {  // G_side = W_side W_side^T, lower block triangle of 128 x 128 tiles
+struct GramJob {  // G_side = W_side W_side^T, lower block triangle of 128 x 128 tiles (row pitch gram_ld(l))
   int64_t s;
   __device__ int64_t count(const BoxDesc& d) const { return 2 * tri_n(cdiv128(d.l)); }
   __device__ TcTile tile(const GroupArgs& g, const BoxDesc& d, int64_t loc) const {
@@ -73,8 +75,9 @@ struct GramJob {  // G_side = W_side W_side^T, lower block triangle of 128 x 128
     t.n = (int)imin64(GN, d.l - tj * GN);
     t.bnm = 0;
     t.K = s;
-    t.D = wc + d.g_off + (int64_t)side * d.l * d.l + ti * GM * d.l + tj * GN;
-    t.ldd = d.l;
+    const int64_t lg = gram_ld(d.l);
+    t.D = wc + d.g_off + (int64_t)side * d.l * lg + ti * GM * lg + tj * GN;
+    t.ldd = lg;
     t.alpha = 1.f;
     t.beta = 0.f;
     return t;
@@ -127,6 +130,178 @@ struct ProjAccJob {  // M_side -= X_side(pass) W_side (b x s), B = W stored l x 
     t.ldd = 2 * s;
     t.alpha = -1.f;
     t.beta = 1.f;
+    return t;
+  }
+};
+
+
+// ---- blocked Cholesky and inverse on the tensor-core path (128-wide blocks, G row pitch lg) ----
+// Block (i, j) of side `side` of the box's Gram area starts at gblk(...) + i*128*lg + j*128.
+__device__ inline float* gram_side(const GroupArgs& g, const BoxDesc& d, int side) {
+  return reinterpret_cast<float*>(g.workc) + d.g_off + (int64_t)side * d.l * gram_ld(d.l);
+}
+// Inverse of diagonal block p (128 x 128 row-major, zero padded).
+__device__ inline float* dinv_blk(const GroupArgs& g, const BoxDesc& d, int side, int64_t p) {
+  return reinterpret_cast<float*>(g.workc) + d.li_off + ((int64_t)side * cdiv128(d.l) + p) * GM * GM;
+}
+__device__ inline int rows_of(int64_t l, int64_t blk) { return (int)imin64(GM, l - blk * GM); }
+
+struct CholPanelJob {  // L_ip = G_ip L_pp^-T for the blocks i > p below the diagonal block p
+  int p;
+  __device__ int64_t count(const BoxDesc& d) const {
+    const int64_t t = cdiv128(d.l) - p - 1;
+    return t > 0 ? 2 * t : 0;
+  }
+  __device__ TcTile tile(const GroupArgs& g, const BoxDesc& d, int64_t loc) const {
+    const int64_t per = cdiv128(d.l) - p - 1, lg = gram_ld(d.l);
+    const int side = (int)(loc / per);
+    const int64_t i = p + 1 + loc % per;
+    float* G = gram_side(g, d, side);
+    TcTile t;
+    t.A = G + i * GM * lg + (int64_t)p * GM;
+    t.lda = lg;
+    t.m = rows_of(d.l, i);
+    t.B = dinv_blk(g, d, side, p);
+    t.ldb = GM;
+    t.n = GM;
+    t.bnm = 0;
+    t.K = GM;
+    t.D = G + i * GM * lg + (int64_t)p * GM;  // in place: the tile's own A, read before the epilogue
+    t.ldd = lg;
+    t.alpha = 1.f;
+    t.beta = 0.f;
+    return t;
+  }
+};
+struct CholUpdJob {  // G_ij -= L_ip L_jp^T for i >= j > p
+  int p;
+  __device__ int64_t count(const BoxDesc& d) const {
+    const int64_t t = cdiv128(d.l) - p - 1;
+    return t > 0 ? 2 * tri_n(t) : 0;
+  }
+  __device__ TcTile tile(const GroupArgs& g, const BoxDesc& d, int64_t loc) const {
+    const int64_t per = tri_n(cdiv128(d.l) - p - 1), lg = gram_ld(d.l);
+    const int side = (int)(loc / per);
+    int64_t ti, tj;
+    tri_idx(loc % per, ti, tj);
+    const int64_t i = p + 1 + ti, j = p + 1 + tj;
+    float* G = gram_side(g, d, side);
+    TcTile t;
+    t.A = G + i * GM * lg + (int64_t)p * GM;
+    t.lda = lg;
+    t.m = rows_of(d.l, i);
+    t.B = G + j * GM * lg + (int64_t)p * GM;
+    t.ldb = lg;
+    t.n = rows_of(d.l, j);
+    t.bnm = 0;
+    t.K = GM;
+    t.D = G + i * GM * lg + j * GM;
+    t.ldd = lg;
+    t.alpha = -1.f;
+    t.beta = 1.f;
+    return t;
+  }
+};
+struct LtildeJob {  // L~_ik = L_ii^-1 L_ik for k < i, in place
+  __device__ int64_t count(const BoxDesc& d) const {
+    const int64_t nb = cdiv128(d.l);
+    return nb > 1 ? 2 * tri_n(nb - 1) : 0;
+  }
+  __device__ TcTile tile(const GroupArgs& g, const BoxDesc& d, int64_t loc) const {
+    const int64_t per = tri_n(cdiv128(d.l) - 1), lg = gram_ld(d.l);
+    const int side = (int)(loc / per);
+    int64_t ti, tj;
+    tri_idx(loc % per, ti, tj);
+    const int64_t i = ti + 1, k = tj;
+    float* G = gram_side(g, d, side);
+    TcTile t;
+    t.A = dinv_blk(g, d, side, i);
+    t.lda = GM;
+    t.m = rows_of(d.l, i);
+    t.B = G + i * GM * lg + k * GM;  // K x N = rows of block i x columns of block k, N contiguous
+    t.ldb = lg;
+    t.n = GM;
+    t.bnm = 1;
+    t.K = rows_of(d.l, i);
+    t.D = G + i * GM * lg + k * GM;  // in place: the tile's own B, read before the epilogue
+    t.ldd = lg;
+    t.alpha = 1.f;
+    t.beta = 0.f;
+    return t;
+  }
+};
+struct InvColJob {  // U_ji = -sum_{k=j}^{i-1} U_jk L~_ik^T for j < i (block column i of U = L^-T)
+  int i;
+  __device__ int64_t count(const BoxDesc& d) const { return cdiv128(d.l) > i ? 2 * (int64_t)i : 0; }
+  __device__ TcTile tile(const GroupArgs& g, const BoxDesc& d, int64_t loc) const {
+    const int64_t lg = gram_ld(d.l);
+    const int side = (int)(loc / i);
+    const int64_t j = loc % i;
+    float* G = gram_side(g, d, side);
+    TcTile t;
+    t.A = G + j * GM * lg + j * GM;  // row block j of U from column block j (U_jj on the diagonal)
+    t.lda = lg;
+    t.m = GM;
+    t.B = G + (int64_t)i * GM * lg + j * GM;  // row block i of L~ from column block j
+    t.ldb = lg;
+    t.n = rows_of(d.l, i);
+    t.bnm = 0;
+    t.K = ((int64_t)i - j) * GM;
+    t.D = G + j * GM * lg + (int64_t)i * GM;
+    t.ldd = lg;
+    t.alpha = -1.f;
+    t.beta = 0.f;
+    return t;
+  }
+};
+struct SolveTJob {  // T = X U (U upper: column block j needs rows < 128 (j + 1))
+  int pass;
+  __device__ int64_t count(const BoxDesc& d) const { return 2 * cdiv128(d.b) * cdiv128(d.l); }
+  __device__ TcTile tile(const GroupArgs& g, const BoxDesc& d, int64_t loc) const {
+    const int64_t nb = cdiv128(d.l), per = cdiv128(d.b) * nb, lg = gram_ld(d.l);
+    const int side = (int)(loc / per);
+    const int64_t a = (loc % per) / nb, j = (loc % per) % nb;
+    float* wc = reinterpret_cast<float*>(g.workc);
+    TcTile t;
+    t.A = wc + (pass ? d.x2_off : d.x_off) + (int64_t)side * d.b * d.l + a * GM * d.l;
+    t.lda = d.l;
+    t.m = rows_of(d.b, a);
+    t.B = gram_side(g, d, side) + j * GM;  // element (k, n) at B + k * lg + n
+    t.ldb = lg;
+    t.n = rows_of(d.l, j);
+    t.bnm = 1;
+    t.K = imin64(d.l, (j + 1) * GM);
+    t.D = wc + d.t_off + (int64_t)side * d.b * lg + a * GM * lg + j * GM;
+    t.ldd = lg;
+    t.alpha = 1.f;
+    t.beta = 0.f;
+    return t;
+  }
+};
+struct SolveCJob {  // X = T U^T (U upper: column block j needs columns >= 128 j of T); pass 1 adds into X_0
+  int pass;
+  __device__ int64_t count(const BoxDesc& d) const { return 2 * cdiv128(d.b) * cdiv128(d.l); }
+  __device__ TcTile tile(const GroupArgs& g, const BoxDesc& d, int64_t loc) const {
+    const int64_t nb = cdiv128(d.l), per = cdiv128(d.b) * nb, lg = gram_ld(d.l);
+    const int side = (int)(loc / per);
+    const int64_t a = (loc % per) / nb, j = (loc % per) % nb;
+    float* wc = reinterpret_cast<float*>(g.workc);
+    float* G = gram_side(g, d, side);
+    TcTile t;
+    t.A = wc + d.t_off + (int64_t)side * d.b * lg + a * GM * lg + j * GM;
+    t.lda = lg;
+    t.m = rows_of(d.b, a);
+    t.B = G + j * GM * lg + j * GM;
+    t.ldb = lg;
+    t.n = rows_of(d.l, j);
+    t.bnm = 0;
+    t.K = d.l - j * GM;
+    const int64_t xo = (int64_t)side * d.b * d.l + a * GM * d.l + j * GM;
+    t.D = wc + (pass ? d.x2_off : d.x_off) + xo;
+    t.ldd = d.l;
+    t.alpha = 1.f;
+    t.beta = 0.f;
+    if (pass) t.D2 = wc + d.x_off + xo;
     return t;
   }
 };
@@ -327,6 +502,7 @@ __global__ void __launch_bounds__(GTHREADS, 1) k_tc_grouped(GroupArgs g, Job job
           if (colbase + cc + q < t.n) {
             const float acc = nchunk > 0 ? __uint_as_float(rr[q]) : 0.f;
             drow[q] = t.beta == 0.f ? t.alpha * acc : fmaf(t.alpha, acc, t.beta * drow[q]);
+            if (t.D2) t.D2[(int64_t)row * t.ldd + colbase + cc + q] += t.alpha * acc;
           }
         }
       }
@@ -336,6 +512,103 @@ __global__ void __launch_bounds__(GTHREADS, 1) k_tc_grouped(GroupArgs g, Job job
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, GTMEM);
   if (tid == 0 && s_timeout && g.err) atomicCAS(g.err, 0, kDevTimeout);
+}
+
+
+// Diagonal block p of the blocked Cholesky, one CTA per (box, side) with l > 128 p: G_pp = L L^T
+// in shared memory (right-looking, one barrier per column: column c's rank-1 update uses the
+// unscaled column and 1 / a_cc, and column c is scaled by sqrt(a_cc) during step c + 1, when no
+// thread reads it), then X = L^-1 by row-oriented forward substitution on the identity (row i's
+// scaling by 1 / L_ii deferred the same way), X held transposed in the strict upper triangle of the
+// same array and its diagonal apart.  Rows beyond the box's l are padded with the identity.
+// Writes X (lower, zero padded) to the block's inverse area and U_pp = X^T (upper, zeros below) to
+// the diagonal block of G.  A pivot that is not positive and finite records kDevNonfinite.
+constexpr int DB = 128, DLD = DB + 1, DTHREADS = 512;
+constexpr int DSMEM = DB * DLD * 4;
+struct DiagCount {
+  int p;
+  __device__ int64_t count(const BoxDesc& d) const { return d.l > (int64_t)p * DB ? 2 : 0; }
+};
+__global__ void __launch_bounds__(DTHREADS) k_chol_diag_tc(GroupArgs g, int p) {
+  extern __shared__ float S[];  // DB x DLD
+  __shared__ float pd[DB];      // L_cc
+  __shared__ float xd[DB];      // X_ii
+  __shared__ int s_bad;
+  int64_t loc;
+  const DiagCount cnt{p};
+  const int bi = find_box(g.desc, g.nbox, blockIdx.x, cnt, loc);
+  if (bi < 0) return;
+  const BoxDesc d = g.desc[bi];
+  const int side = (int)loc;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int64_t lg = gram_ld(d.l), o = (int64_t)p * DB;
+  const int nbp = (int)imin64(DB, d.l - o);
+  float* G = gram_side(g, d, side) + o * lg + o;
+  if (tid == 0) s_bad = 0;
+  for (int e = tid; e < DB * DB; e += DTHREADS) {
+    const int i = e / DB, j = e % DB;
+    float v = (i == j) ? 1.f : 0.f;
+    if (j <= i && i < nbp) v = G[(int64_t)i * lg + j];
+    S[i * DLD + j] = v;
+  }
+  for (int i = tid; i < DB; i += DTHREADS) xd[i] = 1.f;
+  __syncthreads();
+  // ---- Cholesky ----
+  for (int c = 0; c < DB; ++c) {
+    float a = S[c * DLD + c];
+    const bool bad = !(a > 0.f) || !isfinite(a);
+    if (bad) a = 1.f;
+    const float inv = 1.f / a;
+    if (c > 0) {
+      const float dp = pd[c - 1];
+      for (int i = c + tid; i < DB; i += DTHREADS) S[i * DLD + c - 1] /= dp;
+      if (tid == DTHREADS - 1) S[(c - 1) * DLD + c - 1] = dp;
+    }
+    for (int i = c + 1 + ty; i < DB; i += DTHREADS / 32) {
+      const float f = S[i * DLD + c] * inv;
+      for (int j = c + 1 + tx; j <= i; j += 32) S[i * DLD + j] -= f * S[j * DLD + c];
+    }
+    if (tid == 0) {
+      pd[c] = sqrtf(a);
+      if (bad) s_bad = 1;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) S[(DB - 1) * DLD + DB - 1] = pd[DB - 1];
+  __syncthreads();
+  // ---- X = L^-1: X[r][j] (j < r) at S[j][r], X[i][i] in xd ----
+  for (int i = 0; i < DB; ++i) {
+    const float lii = S[i * DLD + i];
+    if (i > 0) {
+      const float lp = S[(i - 1) * DLD + i - 1];
+      for (int j = tid; j < i - 1; j += DTHREADS) S[j * DLD + i - 1] /= lp;
+      if (tid == DTHREADS - 1) xd[i - 1] /= lp;
+    }
+    const float xi = xd[i];
+    for (int r = i + 1 + tx; r < DB; r += 32) {
+      const float f = S[r * DLD + i] / lii;
+      for (int j = ty; j <= i; j += DTHREADS / 32) S[j * DLD + r] -= f * (j < i ? S[j * DLD + i] : xi);
+    }
+    __syncthreads();
+  }
+  {
+    const float lp = S[(DB - 1) * DLD + DB - 1];
+    for (int j = tid; j < DB - 1; j += DTHREADS) S[j * DLD + DB - 1] /= lp;
+    if (tid == DTHREADS - 1) xd[DB - 1] /= lp;
+  }
+  __syncthreads();
+  float* Xo = dinv_blk(g, d, side, p);
+  for (int e = tid; e < DB * DB; e += DTHREADS) {
+    const int i = e / DB, j = e % DB;
+    float v = 0.f;
+    if (i < nbp && j < nbp) v = (j < i) ? S[j * DLD + i] : (j == i ? xd[i] : 0.f);
+    Xo[e] = v;
+  }
+  for (int e = tid; e < nbp * nbp; e += DTHREADS) {
+    const int i = e / nbp, j = e % nbp;
+    G[(int64_t)i * lg + j] = (j > i) ? S[i * DLD + j] : (j == i ? xd[i] : 0.f);
+  }
+  if (tid == 0 && s_bad && g.err) atomicCAS(g.err, 0, (int)kDevNonfinite);
 }
 
 template <class Job>
@@ -370,6 +643,43 @@ void launch_proj_acc_tc(Launch L, const GroupArgs& g, int pass, const std::vecto
   const int64_t s = g.s;
   launch_job(L, g, ProjAccJob{g.s, pass},
              items_of_h(h, [s](const BoxDesc& d) { return 2 * cdiv128(d.b) * cdiv128(s); }));
+}
+
+void launch_chol_tc(Launch L, const GroupArgs& g, const std::vector<BoxDesc>& h) {
+  int64_t nbmax = 0;
+  for (const BoxDesc& d : h) nbmax = std::max<int64_t>(nbmax, cdiv128(d.l));
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_chol_diag_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, DSMEM);
+    attr = true;
+  }
+  for (int p = 0; p < (int)nbmax; ++p) {
+    const int64_t nd = items_of_h(h, [p](const BoxDesc& d) { return d.l > (int64_t)p * DB ? 2 : 0; });
+    if (nd > 0) {
+      k_chol_diag_tc<<<(unsigned)nd, DTHREADS, DSMEM, L.st>>>(g, p);
+      if (L.counter) ++*L.counter;
+    }
+    launch_job(L, g, CholPanelJob{p}, items_of_h(h, [p](const BoxDesc& d) {
+                 const int64_t t = cdiv128(d.l) - p - 1;
+                 return t > 0 ? 2 * t : (int64_t)0;
+               }));
+    launch_job(L, g, CholUpdJob{p}, items_of_h(h, [p](const BoxDesc& d) {
+                 const int64_t t = cdiv128(d.l) - p - 1;
+                 return t > 0 ? 2 * tri_n(t) : (int64_t)0;
+               }));
+  }
+  launch_job(L, g, LtildeJob{}, items_of_h(h, [](const BoxDesc& d) {
+               const int64_t nb = cdiv128(d.l);
+               return nb > 1 ? 2 * tri_n(nb - 1) : (int64_t)0;
+             }));
+  for (int i = 1; i < (int)nbmax; ++i)
+    launch_job(L, g, InvColJob{i},
+               items_of_h(h, [i](const BoxDesc& d) { return cdiv128(d.l) > i ? 2 * (int64_t)i : (int64_t)0; }));
+}
+void launch_solve_tc(Launch L, const GroupArgs& g, int pass, const std::vector<BoxDesc>& h) {
+  const int64_t items = items_of_h(h, [](const BoxDesc& d) { return 2 * cdiv128(d.b) * cdiv128(d.l); });
+  launch_job(L, g, SolveTJob{pass}, items);
+  launch_job(L, g, SolveCJob{pass}, items);
 }
 
 }  // namespace rsrs

@@ -930,12 +930,18 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(GroupArgs g) {
 // cluster of C CTAs (C = 1..16) per box, CTA r holding columns [r*cs, (r+1)*cs) of all b rows of
 // the FP32 sketch M, so the k' reflector steps never go back to global memory.  The arithmetic on
 // M is FP32 (M carries the FP32 rounding of the projections already), including the warp and
-// cluster sums of the dot products and row norms: this part's FP64 pipe is 1/64 of its FP32 pipe,
-// and FP64 reductions over every row and lane would dominate each step.  The pivot decisions stay
-// in FP64: the residual norms are held as FP64, the largest is found by comparing their bit
-// patterns (monotone for non-negative doubles; ties to the lowest tree index), and the Householder
-// scalars and the dependent-pivot test of k_cpqr are evaluated in FP64.  Output as
-// k_cpqr_cluster: R rows by point (FP64), permutation and first dependent step.
+// cluster sums of the dot products and row norms and the Householder scalars: this part's FP64
+// pipe is 1/64 of its FP32 pipe, and FP64 work on the serial path of every step would dominate it.
+// The pivot decisions stay in FP64: the residual norms are held as FP64, the largest is found by
+// comparing their bit patterns (monotone for non-negative doubles; ties to the lowest tree index),
+// and the dependent-pivot test of k_cpqr is evaluated on them (squared, no square roots).  The two
+// cluster sums of every step are pushed: each CTA stores its partial sums into a slot of every
+// CTA's shared memory (remote stores, no round trips) and, after the cluster barrier, adds its C
+// local slots in rank order.  Output as k_cpqr_cluster: R rows by point (FP64), permutation and
+// first dependent step.
+__host__ __device__ inline size_t cpqr32_head_bytes(int b, int C) {
+  return (((size_t)b * 8 + (size_t)2 * C * b * 4 + (size_t)b * 4 + (size_t)b * 4) + 15) & ~(size_t)15;
+}
 __global__ void __launch_bounds__(1024, 1) k_cpqr32_cluster(GroupArgs g, int cs, int in_global) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
@@ -950,23 +956,34 @@ __global__ void __launch_bounds__(1024, 1) k_cpqr32_cluster(GroupArgs g, int cs,
   int32_t* perm = g.iwork + d.pv_off;
   extern __shared__ double csm[];
   double* nrm = csm;                                         // b, replicated in every CTA
-  float* wpart = reinterpret_cast<float*>(csm + b);          // b, this CTA's partial dot products
-  float* npart = wpart + b;                                  // b, this CTA's partial norms
-  float* fvec = npart + b;                                   // b, reflector coefficients
+  float* wbuf = reinterpret_cast<float*>(csm + b);          // C x b: partial dot products, slot per CTA
+  float* nbuf = wbuf + (size_t)C * b;                        // C x b: partial squared norms, slot per CTA
+  float* fvec = nbuf + (size_t)C * b;                        // b, reflector coefficients
   int* rid = reinterpret_cast<int*>(fvec + b);               // b
   // this CTA's b x (t_hi - t_lo) slice of M: in shared memory (row pitch cs), or in place in the
   // workspace when the box is too large for the cluster's shared memory (row pitch 2s)
-  float* S = in_global ? Mg + t_lo : reinterpret_cast<float*>(csm + b + (4 * b + 1) / 2 + 1);
+  float* S = in_global ? Mg + t_lo
+                       : reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(csm) + cpqr32_head_bytes(b, C));
   const int64_t lds = in_global ? c : (int64_t)cs;
   __shared__ unsigned long long red_v[32];
-  __shared__ int red_i[32];
+  __shared__ int red_i[32], red_m[32];
   __shared__ double s_r00;
   __shared__ float s_vj, s_f2;
   __shared__ int s_j0;
   const double tau = fmax(1e-10, 64.0 * DBL_EPSILON * (double)max(b, (int)c));
   const double floor_abs = tau * id_scale(g.work + d.sn_off, b);
+  const double floor2 = floor_abs * floor_abs, tau2 = tau * tau;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int wid = (int)(t_hi - t_lo);
+  // a warp-reduced partial sum of row pos goes to slot `rank` of every CTA's buffer (lane q -> CTA q)
+  auto push = [&](float* buf, int pos, float v) {
+    if (lane < C) cluster.map_shared_rank(buf, lane)[(size_t)rank * b + pos] = v;
+  };
+  auto sum_slots = [&](const float* buf, int pos) {
+    float v = 0.f;
+    for (int q = 0; q < C; ++q) v += buf[(size_t)q * b + pos];
+    return v;
+  };
   for (int i = threadIdx.x; i < b; i += blockDim.x) rid[i] = i;
   if (threadIdx.x == 0) {
     s_r00 = -1.0;
@@ -983,68 +1000,68 @@ __global__ void __launch_bounds__(1024, 1) k_cpqr32_cluster(GroupArgs g, int cs,
       acc = fmaf(v, v, acc);
     }
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) npart[i] = acc;
+    push(nbuf, i, acc);
   }
   cluster.sync();
-  // cluster sums, thread per row: the C remote loads of a row are independent, so their
-  // latencies overlap
-  auto gather_norms = [&](int from) {
-    for (int pos = from + threadIdx.x; pos < b; pos += blockDim.x) {
-      float v = 0.f;
-#pragma unroll 4
-      for (int q = 0; q < C; ++q) v += cluster.map_shared_rank(npart, q)[pos];
-      nrm[pos] = (double)v;
-    }
-  };
-  gather_norms(0);
+  for (int pos = threadIdx.x; pos < b; pos += blockDim.x) nrm[pos] = (double)sum_slots(nbuf, pos);
   __syncthreads();
+  // candidate order: larger norm bits first, then the lower tree index
+  auto better = [&](unsigned long long v, int p, unsigned long long bv, int bp) {
+    return p >= 0 && (bp < 0 || v > bv || (v == bv && rid[p] < rid[bp]));
+  };
   for (int j = 0; j < kp; ++j) {
-    // pivot: largest residual norm, ties to the lowest local index (identical in every CTA)
+    // pivot candidates (identical in every CTA): the largest residual norm, and the lowest tree
+    // index (taken once the remaining pivots are numerically dependent)
     unsigned long long bv = 0ull;
-    int bp = -1;
+    int bp = -1, mp = -1;
     for (int pos = j + threadIdx.x; pos < b; pos += blockDim.x) {
       const unsigned long long v = (unsigned long long)__double_as_longlong(nrm[pos]);
-      if (bp < 0 || v > bv || (v == bv && rid[pos] < rid[bp])) {
+      if (better(v, pos, bv, bp)) {
         bv = v;
         bp = pos;
       }
+      if (mp < 0 || rid[pos] < rid[mp]) mp = pos;
     }
     for (int o = 16; o; o >>= 1) {
       const unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
       const int op = __shfl_xor_sync(0xffffffffu, bp, o);
-      if (op >= 0 && (bp < 0 || ov > bv || (ov == bv && rid[op] < rid[bp]))) {
+      const int om = __shfl_xor_sync(0xffffffffu, mp, o);
+      if (better(ov, op, bv, bp)) {
         bv = ov;
         bp = op;
       }
+      if (om >= 0 && (mp < 0 || rid[om] < rid[mp])) mp = om;
     }
     if (lane == 0) {
       red_v[warp] = bv;
       red_i[warp] = bp;
+      red_m[warp] = mp;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned long long v0 = 0ull;
-      int p0 = -1;
-      for (int w = 0; w < nw; ++w) {
-        const int op = red_i[w];
-        const unsigned long long ov = red_v[w];
-        if (op >= 0 && (p0 < 0 || ov > v0 || (ov == v0 && rid[op] < rid[p0]))) {
-          v0 = ov;
-          p0 = op;
+    if (warp == 0) {
+      bv = lane < nw ? red_v[lane] : 0ull;
+      bp = lane < nw ? red_i[lane] : -1;
+      mp = lane < nw ? red_m[lane] : -1;
+      for (int o = 16; o; o >>= 1) {
+        const unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+        const int om = __shfl_xor_sync(0xffffffffu, mp, o);
+        if (better(ov, op, bv, bp)) {
+          bv = ov;
+          bp = op;
         }
+        if (om >= 0 && (mp < 0 || rid[om] < rid[mp])) mp = om;
       }
-      const double dv0 = p0 >= 0 ? __longlong_as_double((long long)v0) : 0.0;
+    }
+    if (threadIdx.x == 0) {
+      int p0 = bp;
+      const double dv0 = p0 >= 0 ? __longlong_as_double((long long)bv) : 0.0;
       if (p0 < 0 || !isfinite(dv0)) {
         p0 = j;
         if (rank == 0) set_err(g.err, kDevNonfinite);
       }
-      if (s_j0 == kp && (sqrt(dv0) <= floor_abs || (s_r00 >= 0.0 && sqrt(dv0) <= tau * s_r00) || dv0 == 0.0))
-        s_j0 = j;
-      if (s_j0 <= j) {
-        p0 = j;
-        for (int pos = j + 1; pos < b; ++pos)
-          if (rid[pos] < rid[p0]) p0 = pos;
-      }
+      if (s_j0 == kp && (dv0 <= floor2 || (s_r00 >= 0.0 && dv0 <= tau2 * s_r00 * s_r00) || dv0 == 0.0)) s_j0 = j;
+      if (s_j0 <= j) p0 = mp >= 0 ? mp : j;
       if (p0 != j) {
         const int ti = rid[j];
         rid[j] = rid[p0];
@@ -1055,16 +1072,15 @@ __global__ void __launch_bounds__(1024, 1) k_cpqr32_cluster(GroupArgs g, int cs,
       }
       // x0 = M[pivot][j] lives in the CTA that owns column j
       const int owner = (int)(j / cs);
-      const double x0 = in_global ? (double)Mg[(int64_t)rid[j] * c + j]
-                                  : (double)cluster.map_shared_rank(S, owner)[(int64_t)rid[j] * cs +
-                                                                              (j - (int64_t)owner * cs)];
-      const double alpha = sqrt(fmax(nrm[j], 0.0));
-      const double sg = (x0 >= 0.0) ? 1.0 : -1.0;
-      const double vn2 = 2.0 * alpha * (alpha + fabs(x0));
-      s_vj = (float)(x0 + sg * alpha);
-      s_f2 = vn2 > 0.0 ? (float)(2.0 / vn2) : 0.f;
-      if (j == 0) s_r00 = alpha;
-      if (rank == 0) Rp[(int64_t)j * b + rid[j]] = -sg * alpha;
+      const float x0 = in_global ? Mg[(int64_t)rid[j] * c + j]
+                                 : cluster.map_shared_rank(S, owner)[(int64_t)rid[j] * cs + (j - (int64_t)owner * cs)];
+      const float alpha = sqrtf((float)fmax(nrm[j], 0.0));
+      const float sg = (x0 >= 0.f) ? 1.f : -1.f;
+      const float vn2 = 2.f * alpha * (alpha + fabsf(x0));
+      s_vj = x0 + sg * alpha;
+      s_f2 = vn2 > 0.f ? 2.f / vn2 : 0.f;
+      if (j == 0) s_r00 = (double)alpha;
+      if (rank == 0) Rp[(int64_t)j * b + rid[j]] = (double)(-sg * alpha);
     }
     __syncthreads();
     const float vj = s_vj, f2 = s_f2;
@@ -1077,15 +1093,10 @@ __global__ void __launch_bounds__(1024, 1) k_cpqr32_cluster(GroupArgs g, int cs,
       float w = 0.f;
       for (int t = t0 + lane; t < wid; t += 32) w = fmaf(row[t], t == tj ? vj : xs[t], w);
       for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-      if (lane == 0) wpart[pos] = w;
+      push(wbuf, pos, w);
     }
     cluster.sync();
-    for (int pos = j + 1 + threadIdx.x; pos < b; pos += blockDim.x) {
-      float w = 0.f;
-#pragma unroll 4
-      for (int q = 0; q < C; ++q) w += cluster.map_shared_rank(wpart, q)[pos];
-      fvec[pos] = w * f2;
-    }
+    for (int pos = j + 1 + threadIdx.x; pos < b; pos += blockDim.x) fvec[pos] = sum_slots(wbuf, pos) * f2;
     __syncthreads();
     for (int pos = j + 1 + warp; pos < b; pos += nw) {
       const float f = fvec[pos];
@@ -1098,17 +1109,17 @@ __global__ void __launch_bounds__(1024, 1) k_cpqr32_cluster(GroupArgs g, int cs,
         else Rp[(int64_t)j * b + rid[pos]] = (double)v;  // t == j lives in exactly one CTA
       }
       for (int o = 16; o; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
-      if (lane == 0) npart[pos] = nn;
+      push(nbuf, pos, nn);
     }
     cluster.sync();
-    gather_norms(j + 1);
+    for (int pos = j + 1 + threadIdx.x; pos < b; pos += blockDim.x) nrm[pos] = (double)sum_slots(nbuf, pos);
     __syncthreads();
   }
   if (rank == 0) {
     for (int i = threadIdx.x; i < b; i += blockDim.x) perm[i] = rid[i];
     if (threadIdx.x == 0) perm[b] = s_j0;
   }
-  cluster.sync();  // keep every CTA's shared memory alive until the last remote read
+  cluster.sync();  // keep every CTA's shared memory alive until the last remote access
 }
 
 // T = R11^-1 R12 (truncated at the first dependent pivot), R/S/N lists, new active list.
@@ -1754,32 +1765,38 @@ void launch_cpqr(Launch L, const GroupArgs& g, int max_b) {
   cudaLaunchKernelEx(&cfg, k_cpqr_cluster, g);
   count_launch(L);
 }
-// Shared memory of k_cpqr32_cluster for boxes of up to max_b rows and slices of cs columns.
-static size_t cpqr32_smem(int max_b, int cs) {
-  return ((size_t)max_b + (4 * (size_t)max_b + 1) / 2 + 1) * sizeof(double) + (size_t)max_b * cs * sizeof(float);
+// Shared memory of k_cpqr32_cluster for boxes of up to max_b rows, C CTAs and slices of cs columns.
+static size_t cpqr32_smem(int max_b, int cs, int C) {
+  return cpqr32_head_bytes(max_b, C) + (size_t)max_b * cs * sizeof(float);
 }
-bool launch_cpqr32(Launch L, const GroupArgs& g, int max_b) {
+constexpr size_t kCpqr32MaxSmem = 220 * 1024;
+bool launch_cpqr32(Launch L, const GroupArgs& g, int max_b, int cluster, int threads) {
   const int64_t c = 2 * g.s;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_cpqr32_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaFuncSetAttribute(k_cpqr32_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_cpqr32_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCpqr32MaxSmem);
     attr = true;
   }
+  auto slice = [c](int q) { return (int)((cdiv(c, q) + 3) / 4 * 4); };
   // smallest cluster whose shared memory holds the slices; otherwise 16 CTAs on slices in place
   int C = 16, in_global = 1;
   for (int q = 1; q <= 16; q *= 2)
-    if (cpqr32_smem(max_b, (int)((cdiv(c, q) + 3) / 4 * 4)) <= 200 * 1024) {
+    if (cpqr32_smem(max_b, slice(q), q) <= kCpqr32MaxSmem) {
       C = q;
       in_global = 0;
       break;
     }
-  const int cs = (int)((cdiv(c, C) + 3) / 4 * 4);
-  const size_t smem = in_global ? cpqr32_smem(max_b, 0) : cpqr32_smem(max_b, cs);
-  if (smem > 200 * 1024) return false;
+  if (!in_global && cluster > C && cluster <= 16 && (cluster & (cluster - 1)) == 0 &&
+      cpqr32_smem(max_b, slice(cluster), cluster) <= kCpqr32MaxSmem)
+    C = cluster;
+  const int cs = slice(C);
+  const size_t smem = in_global ? cpqr32_smem(max_b, 0, C) : cpqr32_smem(max_b, cs, C);
+  if (smem > kCpqr32MaxSmem) return false;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(g.nbox * C));
-  cfg.blockDim = dim3(1024);  // one CTA per SM: many warps to hide the shared-memory latency of each step
+  // one CTA per SM: many warps hide the shared-memory latency of each step
+  cfg.blockDim = dim3((threads == 256 || threads == 512) ? (unsigned)threads : 1024u);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = L.st;
   cudaLaunchAttribute attr1[1];

@@ -316,25 +316,25 @@ int ff_group(int ncols) {
   while (nc < ncols && nc < 16) nc *= 2;
   return nc;
 }
-int ff_splits(int64_t n) {
+int ff_splits(int64_t n, int split) {
   const int64_t blocks = cdiv(n, RT);
-  int64_t ks = cdiv(4 * 152, blocks);
+  int64_t ks = (split >= 1 && split <= 16) ? split : cdiv(4 * 152, blocks);
   ks = imax64(1, imin64(ks, cdiv(n, (int64_t)FOLD * JT)));
   return (int)ks;
 }
 
 }  // namespace
 
-int64_t ff_scratch_floats(int64_t n, int d, int ncols) {
+int64_t ff_scratch_floats(int64_t n, int d, int ncols, int split) {
   const int nc = ff_group(ncols);
-  return 4 * ((3 * n * d + 3) / 4) + 2 * (n * nc + (int64_t)ff_splits(n) * n * nc);
+  return 4 * ((3 * n * d + 3) / 4) + 2 * (n * nc + (int64_t)ff_splits(n, split) * n * nc);
 }
 
 void launch_kernel_matvec_ff(Launch L, int kind, const double* pts, int d, int64_t n, double shift, double scale,
                              const double* in, int64_t ld_in, double* out, int64_t ld_out, int64_t ncols,
-                             float* scratch) {
+                             float* scratch, int split) {
   if (n <= 0 || ncols <= 0) return;
-  const int ksplit = ff_splits(n);
+  const int ksplit = ff_splits(n, split);
   // a split covers whole folds of tiles
   const int64_t jspan = cdiv(cdiv(n, ksplit), (int64_t)FOLD * JT) * FOLD * JT;
   for (int64_t c0 = 0; c0 < ncols; c0 += 16) {

@@ -74,6 +74,7 @@ struct rsrs_factor {
   double *Y = nullptr, *Z = nullptr, *Om = nullptr, *Ps = nullptr;  // kept sketches (shared, rows from base)
   int sample_kernel = 0;  // mixed sampling: 1 FP32 SIMT, 2 tcgen05 3xTF32
   int residual_fp64 = 0;  // refinement residual in FP64 instead of float-float
+  rsrs_tune_t tune{};     // launch shapes of the build and of the refinement residual
   rsrs_stats stats{};
 };
 
@@ -84,6 +85,16 @@ thread_local std::string g_last_error;
 rsrs_status fail(rsrs_status st, const std::string& msg) {
   g_last_error = msg;
   return st;
+}
+
+bool tune_valid(const rsrs_tune_t& t) {
+  const int c = t.cpqr_cluster, th = t.cpqr_threads;
+  bool ok = t.sample_tile >= 0 && t.sample_tile <= RSRS_SAMPLE_TILE_192x2;
+  ok = ok && (c == 0 || c == 2 || c == 4 || c == 8 || c == 16);
+  ok = ok && (th == 0 || th == 256 || th == 512 || th == 1024);
+  ok = ok && t.residual_split >= 0 && t.residual_split <= 16;
+  for (int r : t.reserved) ok = ok && r == 0;
+  return ok;
 }
 
 #define CU(call)                                                                            \
@@ -247,7 +258,7 @@ rsrs_status op_apply(const rsrs_factor* f, Launch L, const double* in, double* o
     launch_points_f32(L, f->pts_dev, f->n, f->d, p32);
     launch_split_transpose(L, in, f->n, ncols, hi, lo, ldp);
     if (!launch_kernel_matvec_tc(L, f->kind, p32, f->n, f->shift, f->scale, in, in, out, out, ncols, ncols, ncols,
-                                 hi, lo, ldp, err))
+                                 hi, lo, ldp, err, f->tune.sample_tile))
       return fail(RSRS_E_CUDA, "could not encode the TMA tensor maps of the sampling product");
     CU(cudaGetLastError());
     return RSRS_OK;
@@ -387,6 +398,7 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
   if (o.sample_kernel < 0 || o.sample_kernel > 2) return fail(RSRS_E_INVAL, "build: unknown sample_kernel");
   if (o.mixed_cpqr < 0 || o.mixed_cpqr > 1) return fail(RSRS_E_INVAL, "build: unknown mixed_cpqr");
   if (o.mixed_gemm < 0 || o.mixed_gemm > 1) return fail(RSRS_E_INVAL, "build: unknown mixed_gemm");
+  if (!tune_valid(o.tune)) return fail(RSRS_E_INVAL, "build: tune values out of range");
   if (o.residual_fp64 < 0 || o.residual_fp64 > 1) return fail(RSRS_E_INVAL, "build: residual_fp64 is 0 or 1");
   if (nprob > 1 && (o.omega_host || o.psi_host || o.omega_dev || o.psi_dev))
     return fail(RSRS_E_INVAL, "build: caller test matrices are for single-problem builds");
@@ -398,6 +410,8 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
   // leaves the refined mixed factor unchanged on the 65,536-point workload (same refinement
   // history to two digits), so both precisions default to two
   const int passes = o.proj_passes <= 0 ? 2 : std::min(o.proj_passes, 4);
+  // tensor-core Gram factorisation and projection solve (mixed path with tcgen05 products)
+  const bool tc_path = o.precision == RSRS_PREC_MIXED && o.mixed_gemm == 0;
   std::vector<Schedule> sc(nprob);
   std::vector<int64_t> base(nprob + 1, 0);
   int maxdepth = 0;
@@ -471,6 +485,7 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
     f->perm = T.perm;
     f->sample_kernel = o.sample_kernel == 0 ? 2 : o.sample_kernel;
     f->residual_fp64 = o.residual_fp64 ? 1 : 0;
+    f->tune = o.tune;
     F[p] = std::move(f);
   }
 
@@ -554,7 +569,9 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
           iw += d.b + 1;  // CPQR permutation and the first dependent step
           // compute-type workspace
           d.g_off = wc;
-          wc += 2 * (int64_t)d.l * d.l;
+          wc += 2 * (int64_t)d.l * gram_ld(d.l);
+          d.t_off = wc;
+          if (tc_path) wc += 2 * (int64_t)d.b * gram_ld(d.l);
           d.x_off = wc;
           wc += 2 * (int64_t)d.b * d.l;
           d.x2_off = wc;
@@ -566,7 +583,7 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
           d.e_off = wc;
           wc += 2 * (int64_t)d.r * d.l;
           d.li_off = wc;
-          wc += 2 * cdiv(d.l, kT) * 2 * kT * kT;
+          wc += li_elems(d.l);
           // FP64 workspace
           d.m_off = w;
           w += (int64_t)d.b * 2 * s;
@@ -621,7 +638,9 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
     root_work += nroot;
     // the root runs in FP64: its compute-type offsets count doubles
     rd.g_off = root_workc;
-    root_workc += 2 * nroot * nroot;
+    root_workc += 2 * nroot * gram_ld(nroot);
+    rd.t_off = root_workc;
+    if (tc_path) root_workc += 2 * nroot * gram_ld(nroot);
     rd.x_off = root_workc;
     root_workc += 2 * nroot * nroot;
     rd.x2_off = root_workc;
@@ -632,7 +651,7 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
     root_workc += 2 * nroot * s;
     rd.e_off = root_workc;
     rd.li_off = root_workc;
-    root_workc += 2 * cdiv(nroot, kT) * 2 * kT * kT;
+    root_workc += li_elems(nroot);
     rh.push_back(rd);
     if (T.depth == 0) {
       segs.push_back({act_off[p][0], rd.bn_off, nroot});
@@ -873,7 +892,7 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
           launch_split_transpose(L, Om + off, fp->n, s, hi, lo, ldp);
           launch_split_transpose(L, Ps + off, fp->n, s, hi + s * ldp, lo + s * ldp, ldp);
           if (!launch_kernel_matvec_tc(L, fp->kind, p32, fp->n, fp->shift, fp->scale, Om + off, Ps + off, Y + off,
-                                       Z + off, s, s, 2 * s, hi, lo, ldp, err))
+                                       Z + off, s, s, 2 * s, hi, lo, ldp, err, o.tune.sample_tile))
             r1 = fail(RSRS_E_CUDA, "could not encode the TMA tensor maps of the sampling product");
           continue;
         }
@@ -921,6 +940,10 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
         else launch_gram(L, ga, items_gram(g.h));
       });
       timed(RSRS_K_CHOL, [&] {
+        if (tcg) {
+          launch_chol_tc(L, ga, g.h);
+          return;
+        }
         for (int pn = 0; pn < g.max_panels; ++pn) {
           launch_chol_panel(L, ga, pn);
           launch_chol_trsm(L, ga, pn, items_chol_trsm(g.h, pn));
@@ -932,14 +955,17 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
           if (tcg) launch_proj_nt_tc(L, ga, pass, g.h);
           else launch_proj_nt(L, ga, pass, items_proj_nt(g.h));
         });
-        timed(RSRS_K_PROJ_SOLVE, [&] { launch_proj_solve(L, ga, pass, items_proj_solve(g.h)); });
+        timed(RSRS_K_PROJ_SOLVE, [&] {
+          if (tcg) launch_solve_tc(L, ga, pass, g.h);
+          else launch_proj_solve(L, ga, pass, items_proj_solve(g.h));
+        });
         timed(RSRS_K_PROJ_ACC, [&] {
           if (tcg) launch_proj_acc_tc(L, ga, pass, g.h);
           else launch_proj_acc(L, ga, pass, items_proj_acc(g.h, s));
         });
       }
       bool cpqr_done = false;
-      if (ga.fp32 && o.mixed_cpqr == 0) timed(RSRS_K_CPQR, [&] { cpqr_done = launch_cpqr32(L, ga, g.max_b); });
+      if (ga.fp32 && o.mixed_cpqr == 0) timed(RSRS_K_CPQR, [&] { cpqr_done = launch_cpqr32(L, ga, g.max_b, o.tune.cpqr_cluster, o.tune.cpqr_threads); });
       if (!cpqr_done) {
         timed(RSRS_K_GATHER, [&] { launch_m_finalize(L, ga, items_finalize(g.h)); });
         timed(RSRS_K_CPQR, [&] { launch_cpqr(L, ga, g.max_b); });
@@ -970,12 +996,16 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
       timed(RSRS_K_ROOT, [&] {
         launch_copy_segments(L, segs_dev + root_seg_off, (int)root_nseg, act, iwork);
         launch_gather_box(L, ga, items_gather(rh));
-        if (root32) launch_gram_tc(L, ga, rh);
-        else launch_gram(L, ga, items_gram(rh));
-        for (int pn = 0; pn < max_root_panels; ++pn) {
-          launch_chol_panel(L, ga, pn);
-          launch_chol_trsm(L, ga, pn, items_chol_trsm(rh, pn));
-          launch_chol_update(L, ga, pn, items_chol_update(rh, pn));
+        if (root32) {
+          launch_gram_tc(L, ga, rh);
+          launch_chol_tc(L, ga, rh);
+        } else {
+          launch_gram(L, ga, items_gram(rh));
+          for (int pn = 0; pn < max_root_panels; ++pn) {
+            launch_chol_panel(L, ga, pn);
+            launch_chol_trsm(L, ga, pn, items_chol_trsm(rh, pn));
+            launch_chol_update(L, ga, pn, items_chol_update(rh, pn));
+          }
         }
         // two least-squares passes: the second solves for the residual of the first, so that the
         // normal equations' squared conditioning (Om_Bt can be square when s = |B_t|) is corrected
@@ -984,9 +1014,13 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
             if (root32) launch_proj_acc_tc(L, ga, 0, rh);
             else launch_proj_acc(L, ga, 0, items_proj_acc(rh, s));
           }
-          if (root32) launch_proj_nt_tc(L, ga, pass, rh);
-          else launch_proj_nt(L, ga, pass, items_proj_nt(rh));
-          launch_proj_solve(L, ga, pass, items_proj_solve(rh));
+          if (root32) {
+            launch_proj_nt_tc(L, ga, pass, rh);
+            launch_solve_tc(L, ga, pass, rh);
+          } else {
+            launch_proj_nt(L, ga, pass, items_proj_nt(rh));
+            launch_proj_solve(L, ga, pass, items_proj_solve(rh));
+          }
         }
       });
     }
@@ -1131,6 +1165,216 @@ void rsrs_factor_free(rsrs_factor* f) {
 }
 
 }  // extern "C"
+
+// ---- autotuner ----------------------------------------------------------------------------
+namespace {
+
+// Cache key: device name (blanks as '_'), operator kind, problems, total N, d, k, s, precision.
+std::string tune_key(int nprob, const rsrs_tree* const* trees, const rsrs_operator* ops, int k, int s, int prec) {
+  int dev = 0;
+  cudaDeviceProp prop{};
+  std::string name = "unknown";
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+  cudaGetLastError();
+  for (char& c : name)
+    if (c == ' ' || c == '\t') c = '_';
+  int64_t ntot = 0;
+  for (int p = 0; p < nprob; ++p) ntot += trees[p]->t.n;
+  char buf[256];
+  std::snprintf(buf, sizeof buf, " %d %d %lld %d %d %d %d", ops[0].kind, nprob, (long long)ntot, trees[0]->t.d, k, s,
+                prec);
+  return name + buf;
+}
+
+bool tune_cache_find(const char* path, const std::string& key, rsrs_tune_t* out) {
+  FILE* fh = std::fopen(path, "r");
+  if (!fh) return false;
+  char line[512];
+  bool found = false;
+  while (std::fgets(line, sizeof line, fh)) {
+    const size_t kl = key.size();
+    if (std::strncmp(line, key.c_str(), kl) != 0 || line[kl] != ' ') continue;
+    rsrs_tune_t t{};
+    if (std::sscanf(line + kl, " %d %d %d %d", &t.sample_tile, &t.cpqr_cluster, &t.cpqr_threads,
+                    &t.residual_split) == 4 &&
+        tune_valid(t)) {
+      *out = t;  // the last matching line wins
+      found = true;
+    }
+  }
+  std::fclose(fh);
+  return found;
+}
+
+void tune_cache_add(const char* path, const std::string& key, const rsrs_tune_t& t) {
+  FILE* fh = std::fopen(path, "a");
+  if (!fh) return;
+  std::fprintf(fh, "%s %d %d %d %d\n", key.c_str(), t.sample_tile, t.cpqr_cluster, t.cpqr_threads, t.residual_split);
+  std::fclose(fh);
+}
+
+}  // namespace
+
+extern "C" rsrs_status rsrs_autotune(int nprob, const rsrs_tree* const* trees, const rsrs_operator* ops, int k,
+                                     int s, const rsrs_options* opts, int reps, const char* cache_path, void* stream,
+                                     rsrs_tune_t* out, rsrs_tune_report* report) {
+  if (!out || nprob < 1 || !trees || !ops) return fail(RSRS_E_INVAL, "autotune: null argument");
+  for (int p = 0; p < nprob; ++p)
+    if (!trees[p]) return fail(RSRS_E_INVAL, "autotune: null tree");
+  rsrs_options o{};
+  if (opts) o = *opts;
+  if (!tune_valid(o.tune)) return fail(RSRS_E_INVAL, "autotune: tune values out of range");
+  reps = std::max(1, std::min(reps, 10));
+  rsrs_tune_report rep{};
+  const std::string key = tune_key(nprob, trees, ops, k, s, o.precision);
+  if (cache_path && tune_cache_find(cache_path, key, out)) {
+    rep.from_cache = 1;
+    if (report) *report = rep;
+    return RSRS_OK;
+  }
+  o.profile = 1;
+  o.use_graph = 0;
+  o.keep_sketches = 0;
+  const bool mixed = o.precision == RSRS_PREC_MIXED;
+  bool builtin = true;
+  for (int p = 0; p < nprob; ++p) builtin = builtin && ops[p].kind != RSRS_OP_CALLBACK;
+  const bool tune_sample = mixed && builtin && (o.sample_kernel == 0 || o.sample_kernel == 2);
+  const bool tune_cpqr = mixed && o.mixed_cpqr == 0;
+  const bool tune_resid = builtin && !o.residual_fp64;
+
+  // best-of-reps device time per kernel class of one build configuration
+  auto time_build = [&](const rsrs_tune_t& t, double* cls) -> rsrs_status {
+    for (int c = 0; c < RSRS_NCLASS; ++c) cls[c] = 1e300;
+    o.tune = t;
+    for (int r = 0; r < reps; ++r) {
+      std::vector<rsrs_factor*> F(nprob, nullptr);
+      const rsrs_status st = build_impl(nprob, trees, ops, k, s, &o, stream, F.data());
+      if (st != RSRS_OK) return st;
+      for (int c = 0; c < RSRS_NCLASS; ++c) cls[c] = std::min(cls[c], F[0]->stats.class_ms[c]);
+      for (rsrs_factor* f : F) rsrs_factor_free(f);
+    }
+    ++rep.candidates;
+    return RSRS_OK;
+  };
+  // keep a candidate only when it is at least 1% faster (ties keep the earlier, default-first value)
+  auto better = [](double t, double best) { return t < 0.99 * best; };
+
+  rsrs_tune_t best = o.tune;
+  double cls[RSRS_NCLASS], def[RSRS_NCLASS];
+  rsrs_status st = time_build(rsrs_tune_t{}, def);
+  if (st != RSRS_OK) return st;
+  double cur[RSRS_NCLASS];
+  bool start_zero = true;
+  {
+    const rsrs_tune_t z{};
+    start_zero = std::memcmp(&best, &z, sizeof z) == 0;
+  }
+  if (start_zero) {
+    std::copy(def, def + RSRS_NCLASS, cur);
+  } else {
+    st = time_build(best, cur);
+    if (st != RSRS_OK) return st;
+  }
+  if (tune_sample) {
+    double bt = cur[RSRS_K_SAMPLE];
+    const int cand[] = {RSRS_SAMPLE_TILE_256x2, RSRS_SAMPLE_TILE_128x3, RSRS_SAMPLE_TILE_192x2};
+    for (int v : cand) {
+      if (v == best.sample_tile || (v == RSRS_SAMPLE_TILE_256x2 && best.sample_tile == 0)) continue;
+      rsrs_tune_t t = best;
+      t.sample_tile = v;
+      st = time_build(t, cls);
+      if (st != RSRS_OK) return st;
+      if (better(cls[RSRS_K_SAMPLE], bt)) {
+        bt = cls[RSRS_K_SAMPLE];
+        best = t;
+        std::copy(cls, cls + RSRS_NCLASS, cur);
+      }
+    }
+  }
+  if (tune_cpqr) {
+    double bt = cur[RSRS_K_CPQR];
+    for (int c : {2, 4, 8, 16}) {
+      if (c == best.cpqr_cluster) continue;
+      rsrs_tune_t t = best;
+      t.cpqr_cluster = c;
+      st = time_build(t, cls);
+      if (st != RSRS_OK) return st;
+      if (better(cls[RSRS_K_CPQR], bt)) {
+        bt = cls[RSRS_K_CPQR];
+        best = t;
+        std::copy(cls, cls + RSRS_NCLASS, cur);
+      }
+    }
+    for (int th : {512, 256}) {
+      if (th == best.cpqr_threads) continue;
+      rsrs_tune_t t = best;
+      t.cpqr_threads = th;
+      st = time_build(t, cls);
+      if (st != RSRS_OK) return st;
+      if (better(cls[RSRS_K_CPQR], bt)) {
+        bt = cls[RSRS_K_CPQR];
+        best = t;
+        std::copy(cls, cls + RSRS_NCLASS, cur);
+      }
+    }
+  }
+  rep.default_ms = (tune_sample ? def[RSRS_K_SAMPLE] : 0.0) + (tune_cpqr ? def[RSRS_K_CPQR] : 0.0);
+  rep.tuned_ms = (tune_sample ? cur[RSRS_K_SAMPLE] : 0.0) + (tune_cpqr ? cur[RSRS_K_CPQR] : 0.0);
+  if (tune_resid) {
+    // one float-float residual product of 16 columns on the first problem, per split value
+    o.tune = best;
+    o.profile = 0;
+    std::vector<rsrs_factor*> F(nprob, nullptr);
+    st = build_impl(nprob, trees, ops, k, s, &o, stream, F.data());
+    if (st != RSRS_OK) return st;
+    const rsrs_factor* f = F[0];
+    cudaStream_t cs = (cudaStream_t)stream;
+    Launch L{cs, nullptr};
+    DevPool pool;
+    const int nc = 16;
+    double *Wx = nullptr, *Wax = nullptr;
+    float* scr = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int64_t need = 0;
+    for (int sp : {0, 1, 2, 4, 8, 16}) need = std::max(need, ff_scratch_floats(f->n, f->d, nc, sp));
+    cudaError_t ce = pool.alloc(&Wx, f->n * nc);
+    if (ce == cudaSuccess) ce = pool.alloc(&Wax, f->n * nc);
+    if (ce == cudaSuccess) ce = pool.alloc(&scr, need);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(Wx, 0, (size_t)f->n * nc * sizeof(double), cs);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    double def_ms = 0.0, best_ms = 1e300;
+    for (int sp : {0, 1, 2, 4, 8, 16}) {
+      if (ce != cudaSuccess) break;
+      double tmin = 1e300;
+      for (int r = 0; r < reps + 1 && ce == cudaSuccess; ++r) {  // the first run warms up
+        cudaEventRecord(e0, cs);
+        launch_kernel_matvec_ff(L, f->kind, f->pts_dev, f->d, f->n, f->shift, f->scale, Wx, nc, Wax, nc, nc, scr, sp);
+        cudaEventRecord(e1, cs);
+        ce = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) tmin = std::min(tmin, (double)ms);
+      }
+      ++rep.candidates;
+      if (sp == 0) def_ms = tmin;
+      if (sp == 0 || better(tmin, best_ms)) {
+        best_ms = tmin;
+        best.residual_split = sp;
+      }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (rsrs_factor* ff : F) rsrs_factor_free(ff);
+    if (ce != cudaSuccess) return fail(RSRS_E_CUDA, std::string("autotune: ") + cudaGetErrorString(ce));
+    rep.default_ms += def_ms;
+    rep.tuned_ms += best_ms;
+  }
+  *out = best;
+  if (cache_path) tune_cache_add(cache_path, key, best);
+  if (report) *report = rep;
+  return RSRS_OK;
+}
 
 // ---- sweeps on a tree-order row-major block ------------------------------------------
 namespace {
@@ -1300,7 +1544,7 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_
   // float-float residual scratch (built-in kernels)
   const bool ff = f->kind != RSRS_OP_CALLBACK && !f->residual_fp64;
   float* ffs = nullptr;
-  if (ff) CU(pool.alloc(&ffs, ff_scratch_floats(f->n, f->d, nrhs)));
+  if (ff) CU(pool.alloc(&ffs, ff_scratch_floats(f->n, f->d, nrhs, f->tune.residual_split)));
   k_cm_to_rows<<<nblk(tot), 256, 0, st>>>(B, ld, f->perm_dev, f->n, nrhs, Wb);
   CU(cudaMemcpyAsync(Wx, Wb, tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
   r = sweep_solve(f, L, Wx, nrhs, 0);
@@ -1316,7 +1560,8 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_
   int it = 0;
   for (;; ++it) {
     if (ff)
-      launch_kernel_matvec_ff(L, f->kind, f->pts_dev, f->d, f->n, f->shift, f->scale, Wx, nrhs, Wax, nrhs, nrhs, ffs);
+      launch_kernel_matvec_ff(L, f->kind, f->pts_dev, f->d, f->n, f->shift, f->scale, Wx, nrhs, Wax, nrhs, nrhs, ffs,
+                              f->tune.residual_split);
     else
       r = op_apply(f, L, Wx, Wax, nrhs, 0, 0, c1, c2);
     if (r != RSRS_OK) return r;
@@ -1359,7 +1604,7 @@ rsrs_status rsrs_residual(const rsrs_factor* f, const double* B, const double* X
   CU(pool.alloc(&Wax, tot));
   const bool ff = f->kind != RSRS_OP_CALLBACK && !f->residual_fp64;
   float* ffs = nullptr;
-  if (ff) CU(pool.alloc(&ffs, ff_scratch_floats(f->n, f->d, nrhs)));
+  if (ff) CU(pool.alloc(&ffs, ff_scratch_floats(f->n, f->d, nrhs, f->tune.residual_split)));
   if (f->kind == RSRS_OP_CALLBACK) {
     CU(pool.alloc(&c1, tot));
     CU(pool.alloc(&c2, tot));
@@ -1367,7 +1612,8 @@ rsrs_status rsrs_residual(const rsrs_factor* f, const double* B, const double* X
   k_cm_to_rows<<<nblk(tot), 256, 0, st>>>(B, ld, f->perm_dev, f->n, nrhs, Wb);
   k_cm_to_rows<<<nblk(tot), 256, 0, st>>>(X, ld, f->perm_dev, f->n, nrhs, Wx);
   if (ff)
-    launch_kernel_matvec_ff(L, f->kind, f->pts_dev, f->d, f->n, f->shift, f->scale, Wx, nrhs, Wax, nrhs, nrhs, ffs);
+    launch_kernel_matvec_ff(L, f->kind, f->pts_dev, f->d, f->n, f->shift, f->scale, Wx, nrhs, Wax, nrhs, nrhs, ffs,
+                              f->tune.residual_split);
   else
     r = op_apply(f, L, Wx, Wax, nrhs, 0, 0, c1, c2);
   if (r != RSRS_OK) return r;

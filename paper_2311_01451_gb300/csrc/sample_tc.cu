@@ -28,14 +28,20 @@
 namespace rsrs {
 namespace {
 
-constexpr int TM = 128, TN = 256, TK = 32;
+constexpr int TM = 128, TK = 32;
 constexpr int A_BYTES = TM * TK * 4;                      // 16 KB
-constexpr int B_BYTES = TN * TK * 4;                      // 32 KB
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;     // 96 KB: A_hi, A_lo, B_hi, B_lo
-constexpr int NSTAGE = 2;
-constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024;   // + alignment slack
-constexpr uint32_t TMEM_COLS = 256;
 constexpr int NPROD = 512;                                // producer threads (warps 0..15)
+// Column tile TN and pipeline depth NST of one variant: B_hi and B_lo tiles of TN columns, stages
+// of A_hi, A_lo, B_hi, B_lo; the TMEM accumulator takes the next power of two >= TN columns.
+template <int TN, int NST>
+struct Tile {
+  static constexpr int B_BYTES = TN * TK * 4;
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int SMEM_BYTES = NST * STAGE_BYTES + 1024;  // + alignment slack
+  static constexpr uint32_t TMEM_COLS = TN <= 32 ? 32 : TN <= 64 ? 64 : TN <= 128 ? 128 : 256;
+  static_assert(TN % 32 == 0 && TN >= 32 && TN <= 256, "MMA N and the multicast halves");
+  static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per CTA");
+};
 constexpr int NTHREADS = NPROD + 32;                      // + the TMA / MMA warp
 constexpr long long WAIT_LIMIT = 1ll << 26;
 
@@ -112,7 +118,7 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
-// 2D tiled TMA load of box (TK points x TN/2 columns) at (x = first point, y = first column),
+// 2D tiled TMA load of box (TK points x half a column tile) at (x = first point, y = first column),
 // multicast to the same shared-memory offset (and mbarrier) in both CTAs of the cluster pair.
 __device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
   asm volatile(
@@ -141,26 +147,29 @@ __device__ __forceinline__ float kvalf_tc(float r2) {
 // p32: the points in FP32, n rounded up to a multiple of TK and zero padded (so that every
 // producer load of a chunk stays in bounds).  Columns [0, ncols0) read in0 / write out0, columns
 // [ncols0, ncols) read in1 / write out1 (column c - ncols0); all four are row-major with ld.
-template <int KIND, int D>
+template <int KIND, int D, int TN, int NST>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_kmv_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
              const float* __restrict__ p32, int64_t n, double shift, double scale, const double* __restrict__ in0,
              const double* __restrict__ in1, double* __restrict__ out0, double* __restrict__ out1, int64_t ld,
              int64_t ncols0, int64_t ncols, int* err) {
+  using C = Tile<TN, NST>;
+  constexpr int B_BYTES = C::B_BYTES, STAGE_BYTES = C::STAGE_BYTES;
+  constexpr uint32_t TMEM_COLS = C::TMEM_COLS;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full_a[NSTAGE], full_b[NSTAGE], empty[NSTAGE];
+  __shared__ __align__(8) uint64_t full_a[NST], full_b[NST], empty[NST];
   __shared__ uint32_t s_tmem;
   __shared__ int s_timeout;
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t i0 = (int64_t)blockIdx.x * TM, c0 = (int64_t)blockIdx.y * TN;
   const int ntile = (int)(ncols - c0 < TN ? ncols - c0 : TN);
-  const int nmma = (ntile + 15) & ~15;  // MMA N: a multiple of 16 in [16, 256]
+  const int nmma = (ntile + 15) & ~15;  // MMA N: a multiple of 16 in [16, TN]
   const int64_t nchunk = (n + TK - 1) / TK;
 
   if (tid == 0) {
     s_timeout = 0;
-    for (int s = 0; s < NSTAGE; ++s) {
+    for (int s = 0; s < NST; ++s) {
       bar_init(smem_u32(&full_a[s]), NPROD);
       bar_init(smem_u32(&full_b[s]), 1);
       bar_init(smem_u32(&empty[s]), 2);  // the products of both CTAs of the pair
@@ -203,14 +212,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     };
     if (nchunk > 0) load_pts(0, pj);
     for (int64_t ch = 0; ch < nchunk; ++ch) {
-      const int st = (int)(ch & 1);
-      const int64_t u = ch >> 1;
+      const int st = (int)(ch % NST);
+      const int64_t u = ch / NST;
       unsigned char* Ahi = smem + st * STAGE_BYTES;
       unsigned char* Alo = Ahi + A_BYTES;
       const int64_t j0 = ch * TK + akq;
       if (ch + 1 < nchunk) load_pts(ch + 1, pn);
-      // the products of chunk ch - 2 must be done with this stage
-      if (ch >= NSTAGE && !bar_wait(smem_u32(&empty[st]), (uint32_t)((u - 1) & 1))) s_timeout = 1;
+      // the products of chunk ch - NST must be done with this stage
+      if (ch >= NST && !bar_wait(smem_u32(&empty[st]), (uint32_t)((u - 1) & 1))) s_timeout = 1;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         float hv[4], lv[4];
@@ -244,11 +253,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else if (lane == 0) {
     // ---- TMA + MMA issue ----
     const uint32_t idesc = idesc_tf32(nmma);
-    bool armed[NSTAGE] = {false, false};
-    uint32_t armed_par[NSTAGE] = {0u, 0u};
+    bool armed[NST];
+    uint32_t armed_par[NST];
+#pragma unroll
+    for (int q = 0; q < NST; ++q) {
+      armed[q] = false;
+      armed_par[q] = 0u;
+    }
     bool ok = true;
     auto arm = [&](int64_t ch) {
-      const int st = (int)(ch & 1);
+      const int st = (int)(ch % NST);
       unsigned char* Bhi = smem + st * STAGE_BYTES + 2 * A_BYTES;
       const uint32_t bar = smem_u32(&full_b[st]);
       // this CTA loads half of the columns of the B tile for both CTAs of the pair; the stage's
@@ -258,12 +272,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       tma_load_2d_pair(smem_u32(Bhi) + half, &tm_hi, (int)(ch * TK), (int)(c0 + crank * (TN / 2)), bar);
       tma_load_2d_pair(smem_u32(Bhi + B_BYTES) + half, &tm_lo, (int)(ch * TK), (int)(c0 + crank * (TN / 2)), bar);
       armed[st] = true;
-      armed_par[st] = (uint32_t)((ch >> 1) & 1);
+      armed_par[st] = (uint32_t)((ch / NST) & 1);
     };
-    if (nchunk > 0) arm(0);
+    for (int64_t c = 0; c < NST - 1 && c < nchunk; ++c) arm(c);
     for (int64_t ch = 0; ch < nchunk; ++ch) {
-      const int st = (int)(ch & 1);
-      const uint32_t par = (uint32_t)((ch >> 1) & 1);
+      const int st = (int)(ch % NST);
+      const uint32_t par = (uint32_t)((ch / NST) & 1);
       if (!bar_wait(smem_u32(&full_b[st]), par)) ok = false;
       else armed[st] = false;
       if (!bar_wait(smem_u32(&full_a[st]), par)) ok = false;
@@ -279,15 +293,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mma_tf32(tmem, smem_desc(a_lo + ko), smem_desc(b_hi + ko), idesc, 1u);
       }
       mma_commit_pair(smem_u32(&empty[st]));
-      if (ch + 1 < nchunk) {
-        // the other stage is free once the products of chunk ch - 1 are done
-        if (ch >= 1 && !bar_wait(smem_u32(&empty[st ^ 1]), (uint32_t)(((ch - 1) >> 1) & 1))) ok = false;
-        arm(ch + 1);
+      const int64_t nxt = ch + NST - 1;
+      if (nxt < nchunk) {
+        // chunk nxt reuses the stage of chunk ch - 1: free once that chunk's products are done
+        if (ch >= 1 && !bar_wait(smem_u32(&empty[(ch - 1) % NST]), (uint32_t)(((ch - 1) / NST) & 1))) ok = false;
+        arm(nxt);
       }
     }
     if (!ok) {
       s_timeout = 1;
-      for (int s = 0; s < NSTAGE; ++s)  // copies still in flight must land before the CTA exits
+      for (int s = 0; s < NST; ++s)  // copies still in flight must land before the CTA exits
         if (armed[s]) bar_wait(smem_u32(&full_b[s]), armed_par[s]);
     }
   }
@@ -295,7 +310,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   // every thread: the last commit completes after all earlier products
   if (nchunk > 0) {
     const int64_t last = nchunk - 1;
-    if (!bar_wait(smem_u32(&empty[last & 1]), (uint32_t)((last >> 1) & 1))) s_timeout = 1;
+    if (!bar_wait(smem_u32(&empty[last % NST]), (uint32_t)((last / NST) & 1))) s_timeout = 1;
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp < NPROD / 32 && nchunk > 0) {
@@ -364,18 +379,50 @@ EncodeTiled encode_fn() {
 }
 
 // Tensor map of one plane: ncols rows of n FP32 values, row pitch ldp values (ldp % 4 == 0 so that
-// the pitch is a multiple of 16 bytes); box = TK values x TN rows, 128-byte swizzle, zero fill
-// outside [0, n) x [0, ncols).
-bool plane_map(CUtensorMap* m, const float* base, int64_t n, int64_t ncols, int64_t ldp) {
+// the pitch is a multiple of 16 bytes); box = TK values x half a column tile (each CTA of a pair
+// loads one half), 128-byte swizzle, zero fill outside [0, n) x [0, ncols).
+bool plane_map(CUtensorMap* m, const float* base, int64_t n, int64_t ncols, int64_t ldp, int tn) {
   EncodeTiled enc = encode_fn();
   if (!enc || (ldp & 3) || ((uintptr_t)base & 15)) return false;
   cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)ncols};
   cuuint64_t strides[1] = {(cuuint64_t)ldp * sizeof(float)};
-  cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)(TN / 2)};
+  cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)(tn / 2)};
   cuuint32_t estr[2] = {1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int TN, int NST>
+void launch_variant(cudaStream_t st, int kind, const CUtensorMap& mh, const CUtensorMap& ml, const float* p32,
+                    int64_t n, double shift, double scale, const double* in0, const double* in1, double* out0,
+                    double* out1, int64_t ld, int64_t ncols0, int64_t ncols, int* err) {
+  constexpr int SMEM = Tile<TN, NST>::SMEM_BYTES;
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_kmv_tc<RSRS_OP_LOG2D, 2, TN, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    cudaFuncSetAttribute(k_kmv_tc<RSRS_OP_INVR3D, 3, TN, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+  });
+  // row tiles in pairs (one thread-block cluster each) that share the B tile of their column tile
+  const unsigned gx = (unsigned)(((n + TM - 1) / TM + 1) / 2 * 2);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(gx, (unsigned)((ncols + TN - 1) / TN));
+  cfg.blockDim = dim3(NTHREADS);
+  cfg.dynamicSmemBytes = SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (kind == RSRS_OP_LOG2D)
+    cudaLaunchKernelEx(&cfg, k_kmv_tc<RSRS_OP_LOG2D, 2, TN, NST>, mh, ml, p32, n, shift, scale, in0, in1, out0, out1,
+                       ld, ncols0, ncols, err);
+  else
+    cudaLaunchKernelEx(&cfg, k_kmv_tc<RSRS_OP_INVR3D, 3, TN, NST>, mh, ml, p32, n, shift, scale, in0, in1, out0, out1,
+                       ld, ncols0, ncols, err);
 }
 
 }  // namespace
@@ -389,37 +436,32 @@ void launch_points_f32(Launch L, const double* pts, int64_t n, int d, float* out
   if (L.counter) ++*L.counter;
 }
 
+int sample_tile_tn(int variant) {
+  switch (variant) {
+    case RSRS_SAMPLE_TILE_128x3: return 128;
+    case RSRS_SAMPLE_TILE_192x2: return 192;
+    default: return 256;
+  }
+}
+
 bool launch_kernel_matvec_tc(Launch L, int kind, const float* p32, int64_t n, double shift, double scale,
                              const double* in0, const double* in1, double* out0, double* out1, int64_t ld,
-                             int64_t ncols0, int64_t ncols, const float* bhi, const float* blo, int64_t ldp, int* err) {
+                             int64_t ncols0, int64_t ncols, const float* bhi, const float* blo, int64_t ldp, int* err,
+                             int variant) {
   if (n <= 0 || ncols <= 0) return true;
+  const int tn = sample_tile_tn(variant);
   CUtensorMap mh, ml;
-  if (!plane_map(&mh, bhi, n, ncols, ldp) || !plane_map(&ml, blo, n, ncols, ldp)) return false;
-  static std::once_flag attr;
-  std::call_once(attr, [] {
-    cudaFuncSetAttribute(k_kmv_tc<RSRS_OP_LOG2D, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    cudaFuncSetAttribute(k_kmv_tc<RSRS_OP_INVR3D, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-  });
-  // row tiles in pairs (one thread-block cluster each) that share the B tile of their column tile
-  const unsigned gx = (unsigned)(((n + TM - 1) / TM + 1) / 2 * 2);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(gx, (unsigned)((ncols + TN - 1) / TN));
-  cfg.blockDim = dim3(NTHREADS);
-  cfg.dynamicSmemBytes = SMEM_BYTES;
-  cfg.stream = L.st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 2;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  if (kind == RSRS_OP_LOG2D)
-    cudaLaunchKernelEx(&cfg, k_kmv_tc<RSRS_OP_LOG2D, 2>, mh, ml, p32, n, shift, scale, in0, in1, out0, out1, ld, ncols0,
-                       ncols, err);
-  else
-    cudaLaunchKernelEx(&cfg, k_kmv_tc<RSRS_OP_INVR3D, 3>, mh, ml, p32, n, shift, scale, in0, in1, out0, out1, ld,
-                       ncols0, ncols, err);
+  if (!plane_map(&mh, bhi, n, ncols, ldp, tn) || !plane_map(&ml, blo, n, ncols, ldp, tn)) return false;
+  switch (variant) {
+    case RSRS_SAMPLE_TILE_128x3:
+      launch_variant<128, 3>(L.st, kind, mh, ml, p32, n, shift, scale, in0, in1, out0, out1, ld, ncols0, ncols, err);
+      break;
+    case RSRS_SAMPLE_TILE_192x2:
+      launch_variant<192, 2>(L.st, kind, mh, ml, p32, n, shift, scale, in0, in1, out0, out1, ld, ncols0, ncols, err);
+      break;
+    default:
+      launch_variant<256, 2>(L.st, kind, mh, ml, p32, n, shift, scale, in0, in1, out0, out1, ld, ncols0, ncols, err);
+  }
   if (L.counter) ++*L.counter;
   return true;
 }

@@ -25,7 +25,7 @@ STATUS = {0: "RSRS_OK", 1: "RSRS_E_INVAL", 2: "RSRS_E_UNDERSAMPLED", 3: "RSRS_E_
 EXPORTS = ["rsrs_tree_build", "rsrs_tree_info", "rsrs_tree_perm", "rsrs_tree_schedule", "rsrs_tree_free",
            "rsrs_build", "rsrs_build_batched", "rsrs_refactor", "rsrs_solve", "rsrs_solve_noalloc", "rsrs_apply", "rsrs_refine", "rsrs_residual", "rsrs_matvec", "rsrs_factor_stats",
            "rsrs_factor_box", "rsrs_factor_root", "rsrs_factor_sketches", "rsrs_factor_free",
-           "rsrs_status_string", "rsrs_last_error", "rsrs_kernel_class_name", "rsrs_stencil7_create", "rsrs_stencil7_matvec", "rsrs_stencil7_free"]
+           "rsrs_status_string", "rsrs_last_error", "rsrs_kernel_class_name", "rsrs_stencil7_create", "rsrs_stencil7_matvec", "rsrs_stencil7_free", "rsrs_autotune"]
 
 MATVEC_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.c_int64, C.c_int32, C.c_void_p, C.c_int64,
                         C.c_void_p, C.c_int64, C.c_void_p)
@@ -36,12 +36,39 @@ class Operator(C.Structure):
                 ("fn", MATVEC_FN), ("ctx", C.c_void_p)]
 
 
+RSRS_SAMPLE_TILE_DEFAULT, RSRS_SAMPLE_TILE_256x2, RSRS_SAMPLE_TILE_128x3, RSRS_SAMPLE_TILE_192x2 = 0, 1, 2, 3
+
+
+class Tune(C.Structure):
+    """rsrs_tune_t: launch shapes (all zero = library defaults)."""
+    _fields_ = [("sample_tile", C.c_int32), ("cpqr_cluster", C.c_int32), ("cpqr_threads", C.c_int32),
+                ("residual_split", C.c_int32), ("reserved", C.c_int32 * 4)]
+
+    def as_dict(self) -> dict:
+        return {nm: int(getattr(self, nm)) for nm in ("sample_tile", "cpqr_cluster", "cpqr_threads",
+                                                       "residual_split")}
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("candidates", C.c_int), ("from_cache", C.c_int), ("default_ms", C.c_double),
+                ("tuned_ms", C.c_double)]
+
+
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("p", C.c_int), ("proj_passes", C.c_int), ("seed", C.c_uint64),
                 ("omega_host", C.c_void_p), ("psi_host", C.c_void_p), ("omega_dev", C.c_void_p),
                 ("psi_dev", C.c_void_p), ("keep_sketches", C.c_int), ("profile", C.c_int),
                 ("sample_kernel", C.c_int), ("mixed_cpqr", C.c_int), ("mixed_gemm", C.c_int),
-                ("use_graph", C.c_int), ("residual_fp64", C.c_int)]
+                ("use_graph", C.c_int), ("residual_fp64", C.c_int), ("tune", Tune)]
+
+
+def _tune(t) -> Tune:
+    """A Tune from None, a Tune or a dict of its fields."""
+    if t is None:
+        return Tune()
+    if isinstance(t, Tune):
+        return t
+    return Tune(**{k: int(v) for k, v in dict(t).items()})
 
 
 NCLASS = 16
@@ -104,6 +131,8 @@ def lib():
             "rsrs_factor_sketches": [vp, vp, vp, vp, vp],
             "rsrs_stencil7_create": [vp, C.c_int, C.POINTER(vp)],
             "rsrs_stencil7_matvec": [vp, C.c_int, i64, i32, vp, i64, vp, i64, vp],
+            "rsrs_autotune": [C.c_int, C.POINTER(vp), C.POINTER(Operator), C.c_int, C.c_int, C.POINTER(Options),
+                              C.c_int, C.c_char_p, vp, C.POINTER(Tune), C.POINTER(TuneReport)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -230,7 +259,7 @@ class Factor:
                  psi: np.ndarray | None = None, seed: int = 0, passes: int = 0, keep_sketches: bool = False,
                  matvec=None, stream=None, profile: bool = False,
                  sample_kernel: int = 0, mixed_cpqr: int = 0, residual_fp64: bool = False,
-                 mixed_gemm: int = 0, use_graph: bool = False):
+                 mixed_gemm: int = 0, use_graph: bool = False, tune=None):
         self.tree = tree
         self.n = tree.n
         self._cb = None
@@ -249,7 +278,7 @@ class Factor:
                        keep_sketches=int(keep_sketches), profile=int(profile),
                        sample_kernel=sample_kernel,
                        mixed_cpqr=mixed_cpqr, residual_fp64=int(residual_fp64), mixed_gemm=mixed_gemm,
-                       use_graph=int(use_graph))
+                       use_graph=int(use_graph), tune=_tune(tune))
         self._om = self._ps = None
         if omega is not None and hasattr(omega, "data_ptr"):  # device tensors (N, s), original order
             self._om, self._ps = omega, psi
@@ -361,21 +390,18 @@ class Factor:
 def build_batched(trees, kinds, k: int, s: int, shifts, scales, precision: int = RSRS_PREC_FP64, p: int = -1,
                   seed: int = 0, passes: int = 0, profile: bool = False, sample_kernel: int = 0,
                   keep_sketches: bool = False, mixed_cpqr: int = 0, residual_fp64: bool = False,
-                  mixed_gemm: int = 0, use_graph: bool = False,
+                  mixed_gemm: int = 0, use_graph: bool = False, tune=None,
                   stream=None) -> list:
     """rsrs_build_batched: factors of independent problems built in one set of launches."""
     n = len(trees)
-    ops = (Operator * n)()
-    for i in range(n):
-        ops[i].kind = kinds[i]
-        ops[i].diag_shift = shifts[i]
-        ops[i].scale = scales[i]
+    ops = _operators(kinds, shifts, scales)
     handles = (C.c_void_p * n)(*[t._h for t in trees])
     outs = (C.c_void_p * n)()
     opts = Options(precision=precision, p=p, proj_passes=passes, seed=seed, profile=int(profile),
                    sample_kernel=sample_kernel,
                    keep_sketches=int(keep_sketches), mixed_cpqr=mixed_cpqr,
-                   residual_fp64=int(residual_fp64), mixed_gemm=mixed_gemm, use_graph=int(use_graph))
+                   residual_fp64=int(residual_fp64), mixed_gemm=mixed_gemm, use_graph=int(use_graph),
+                   tune=_tune(tune))
     _check(lib().rsrs_build_batched(n, handles, ops, k, s, C.byref(opts), _stream_ptr(stream), outs))
     res = []
     for i in range(n):
@@ -384,6 +410,36 @@ def build_batched(trees, kinds, k: int, s: int, shifts, scales, precision: int =
         f._h, f.s, f.k = C.c_void_p(outs[i]), s, k
         res.append(f)
     return res
+
+
+def _operators(kinds, shifts, scales):
+    n = len(kinds)
+    ops = (Operator * n)()
+    for i in range(n):
+        ops[i].kind = kinds[i]
+        ops[i].diag_shift = shifts[i]
+        ops[i].scale = scales[i]
+    return ops
+
+
+def autotune(trees, kinds, k: int, s: int, shifts, scales, precision: int = RSRS_PREC_MIXED, p: int = -1,
+             seed: int = 0, reps: int = 2, cache: str | None = None, stream=None, **options):
+    """rsrs_autotune on built-in-kernel problems (one tree, or a list for a batched build): returns
+    (tune dict, report dict).  options: the build options of Factor / build_batched."""
+    if not isinstance(trees, (list, tuple)):
+        trees, kinds, shifts, scales = [trees], [kinds], [shifts], [scales]
+    n = len(trees)
+    ops = _operators(kinds, shifts, scales)
+    handles = (C.c_void_p * n)(*[t._h for t in trees])
+    opts = Options(precision=precision, p=p, seed=seed,
+                   proj_passes=options.pop("passes", 0), tune=_tune(options.pop("tune", None)))
+    for key, val in options.items():
+        setattr(opts, key, int(val))
+    out, rep = Tune(), TuneReport()
+    _check(lib().rsrs_autotune(n, handles, ops, k, s, C.byref(opts), reps,
+                               cache.encode() if cache else None, _stream_ptr(stream), C.byref(out), C.byref(rep)))
+    return out.as_dict(), {"candidates": rep.candidates, "from_cache": bool(rep.from_cache),
+                           "default_ms": rep.default_ms, "tuned_ms": rep.tuned_ms}
 
 
 def kind_of(kernel: str) -> int:

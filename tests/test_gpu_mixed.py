@@ -66,8 +66,9 @@ def test_mixed_cpqr_variants(R, name):
 
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_mixed_tensor_core_products(R, name):
-    """Grams, least-squares right-hand sides and projection updates as 3xTF32 tcgen05 products
-    (default) against the FP32 SIMT kernels: both factors precondition alike and refine to the
+    """Grams, their blocked Cholesky factors and L^-T, least-squares right-hand sides, projection
+    solves and updates as 3xTF32 tcgen05 products (default) against the FP32 SIMT kernels
+    (substitution with the Cholesky factor): both factors precondition alike and refine to the
     dense solution."""
     pr = CASES[name]()
     tree = R.Tree(pr.points, pr.leaf)

@@ -83,3 +83,31 @@ def test_undersampled_rejected_before_device_work(R):
     with pytest.raises(R.RSRSError) as e:
         R.Factor(t, R.RSRS_OP_INVR3D, 32, s_req)  # 3D kernel on 2D points
     assert e.value.name == "RSRS_E_INVAL"
+
+
+@pytest.mark.parametrize("tune", [{"sample_tile": 4}, {"cpqr_cluster": 3}, {"cpqr_threads": 100},
+                                  {"residual_split": 17}, {"sample_tile": -1}])
+def test_tune_values_validated_before_device_work(R, tune):
+    t = R.Tree(W.grid_points_2d(64), 64)
+    with pytest.raises(R.RSRSError) as e:
+        R.Factor(t, R.RSRS_OP_LOG2D, 32, t.info(32).s_req, shift=1.0, scale=1 / 4096, tune=tune)
+    assert e.value.name == "RSRS_E_INVAL"
+
+
+def test_autotune_cache_hit_needs_no_device(R, tmp_path):
+    """A cache line for the problem's key is returned as is, without a build (so also here)."""
+    t = R.Tree(W.grid_points_2d(64), 64)
+    s = t.info(32).s_req_mixed
+    cache = tmp_path / "tune.txt"
+    # the key starts with the device name; without a device the library reports "unknown"
+    name = "unknown"
+    try:
+        import torch
+        if torch.cuda.is_available():
+            name = torch.cuda.get_device_name(0).replace(" ", "_")
+    except ImportError:
+        pass
+    cache.write_text(f"{name} {R.RSRS_OP_LOG2D} 1 4096 2 32 {s} {R.RSRS_PREC_MIXED} 2 4 512 8\n")
+    tune, rep = R.autotune(t, R.RSRS_OP_LOG2D, 32, s, 1.0, 1 / 4096, cache=str(cache))
+    assert rep["from_cache"] and rep["candidates"] == 0
+    assert tune == {"sample_tile": 2, "cpqr_cluster": 4, "cpqr_threads": 512, "residual_split": 8}
