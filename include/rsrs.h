@@ -308,6 +308,20 @@ rsrs_status rsrs_residual(const rsrs_factor* f, const double* B_dev, const doubl
 rsrs_status rsrs_refine(const rsrs_factor* f, const double* B_dev, double* X_dev, int64_t ld,
                         int32_t nrhs, double rtol, int maxit, void* stream,
                         rsrs_refine_report* out);
+/* Restarted GMRES(restart) (Saad and Schultz 1986) on A X = B with the factor as right
+ * preconditioner, A (A_approx)^-1 Y = B, X = (A_approx)^-1 Y: the Krylov method Sec. 6 pairs
+ * with the factorization, against iterative refinement.  Every column is its own GMRES run (its
+ * own Arnoldi basis, classical Gram-Schmidt applied twice, Givens rotations); the columns share
+ * the launches.  Products with A in the refinement's residual arithmetic (float-float for the
+ * built-in kernels unless opts->residual_fp64, the callback otherwise); X starts at 0 (its input
+ * is ignored).  Stops when the true residual max_j ||B_j - A X_j|| / ||B_j|| <= rtol (checked
+ * when the Arnoldi estimate reaches rtol, at each restart and at the end) or after maxit
+ * iterations in total.  out: iterations = Krylov iterations (preconditioner solves),
+ * history = the initial relative residual, then each iteration's estimate (max over columns)
+ * and each restart's true residual, rel_residual = the last true residual.  restart 1..64,
+ * nrhs <= 64; device memory (2 restart + 5) N nrhs doubles.  RSRS_E_NOT_CONVERGED after maxit. */
+rsrs_status rsrs_gmres(const rsrs_factor* f, const double* B_dev, double* X_dev, int64_t ld, int32_t nrhs,
+                       double rtol, int restart, int maxit, void* stream, rsrs_refine_report* out);
 /* Y = A X with the factor's operator in FP64 (the residual product of rsrs_refine). */
 rsrs_status rsrs_matvec(const rsrs_factor* f, const double* X_dev, double* Y_dev, int64_t ld,
                         int32_t nrhs, void* stream);

@@ -11,7 +11,8 @@ Modules:
     operators  -- the matrices A (kernel, 7-point) and the sketches Y, Z (eq. rand_sample_setting)
     linalg     -- null, pseudoinverse, CPQR-based ID, LU (Sec. 2)
     rsrs       -- Algorithm 1, its factorization, solve and apply (eqs. Afact, Ainvfact)
-    refine     -- FP64 iterative refinement and the metrics of eq. (error)
+    refine     -- FP64 iterative refinement, GMRES with the factor as preconditioner, and the
+                  metrics of eq. (error)
 
 Parity status: every function is pinned by tests/test_oracle_*.py against
 closed forms, invariants, brute force at tiny N and the paper's printed sample

@@ -9,6 +9,8 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
   (eq. error), spectral norms estimated by power iteration on B^* B with a
   seeded start block (30 iterations or 1e-3 relative change).
 * ``solve_error_bound``: the right side of eq. (err_solve_cond).
+* ``gmres``: restarted, right-preconditioned GMRES with the factor as preconditioner (the Krylov
+  method of the paper's experiments, Sec. 6), one right-hand side.
 """
 from __future__ import annotations
 
@@ -67,3 +69,52 @@ def errsolve(fac, op, iters=30):
 def solve_error_bound(eps: float, cond: float) -> float:
     """Bound of eq. (err_solve_cond) on ||x - x~|| / ||x|| when relerr <= eps."""
     return 2.0 * eps * cond / (1.0 - eps * cond)
+
+
+def gmres(matvec, precond, b: np.ndarray, rtol: float = 1e-12, restart: int = 30, maxit: int = 60):
+    """Restarted GMRES(restart) (Saad and Schultz 1986) for A x = b with a right preconditioner:
+    solve A M^-1 y = b by Arnoldi on A M^-1 (modified Gram-Schmidt), minimise ||beta e1 - H y||
+    with Givens rotations, x = x0 + M^-1 V y; restart from the true residual.  The factor is the
+    preconditioner (M^-1 = A_approx^-1) as in the paper's experiments, which report GMRES iteration
+    counts.  One right-hand side; returns x, the number of iterations (applications of M^-1) and
+    the history [initial relative residual, per-iteration estimates, true residual per restart]."""
+    b = np.asarray(b, dtype=np.float64)
+    n = b.shape[0]
+    x = np.zeros(n)
+    bn = np.linalg.norm(b)
+    hist = []
+    total = 0
+    while True:
+        r = b - matvec(x) if total else b.copy()
+        beta = np.linalg.norm(r)
+        hist.append(beta / bn)
+        if beta / bn <= rtol or total >= maxit:
+            return x, total, hist
+        V = np.zeros((n, restart + 1))
+        H = np.zeros((restart + 1, restart))
+        V[:, 0] = r / beta
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        cs, sn = np.zeros(restart), np.zeros(restart)
+        k = 0
+        while k < restart and total < maxit:
+            w = matvec(precond(V[:, k]))
+            for i in range(k + 1):
+                H[i, k] = V[:, i] @ w
+                w = w - H[i, k] * V[:, i]
+            H[k + 1, k] = np.linalg.norm(w)
+            V[:, k + 1] = w / H[k + 1, k] if H[k + 1, k] > 0 else 0.0
+            for i in range(k):
+                a, c2 = H[i, k], H[i + 1, k]
+                H[i, k], H[i + 1, k] = cs[i] * a + sn[i] * c2, -sn[i] * a + cs[i] * c2
+            rho = np.hypot(H[k, k], H[k + 1, k])
+            cs[k], sn[k] = (H[k, k] / rho, H[k + 1, k] / rho) if rho > 0 else (1.0, 0.0)
+            H[k, k], H[k + 1, k] = rho, 0.0
+            g[k + 1], g[k] = -sn[k] * g[k], cs[k] * g[k]
+            k += 1
+            total += 1
+            hist.append(abs(g[k]) / bn)
+            if abs(g[k]) / bn <= rtol:
+                break
+        y = np.linalg.solve(np.triu(H[:k, :k]), g[:k]) if k else np.zeros(0)
+        x = x + precond(V[:, :k] @ y)

@@ -516,23 +516,33 @@ __global__ void __launch_bounds__(GTHREADS, 1) k_tc_grouped(GroupArgs g, Job job
 
 
 // Diagonal block p of the blocked Cholesky, one CTA per (box, side) with l > 128 p: G_pp = L L^T
-// in shared memory (right-looking, one barrier per column: column c's rank-1 update uses the
-// unscaled column and 1 / a_cc, and column c is scaled by sqrt(a_cc) during step c + 1, when no
-// thread reads it), then X = L^-1 by row-oriented forward substitution on the identity (row i's
-// scaling by 1 / L_ii deferred the same way), X held transposed in the strict upper triangle of the
-// same array and its diagonal apart.  Rows beyond the box's l are padded with the identity.
-// Writes X (lower, zero padded) to the block's inverse area and U_pp = X^T (upper, zeros below) to
-// the diagonal block of G.  A pivot that is not positive and finite records kDevNonfinite.
+// (right-looking, column by column) and X = L^-1 (forward substitution on the identity, row by row),
+// with the 128 x 128 block held in registers: thread (ty, tx) of 16 x 32 owns the elements
+// (ty + 16u, tx + 32v), u < 8, v < 4, of both L and X.  Each step publishes one column of the
+// trailing matrix (Cholesky) or one row of X and one column of L (inverse) through a
+// double-buffered shared vector, so one barrier per step suffices, and every thread updates its
+// 32 elements from the published values (independent FMAs; blocks of rows and columns that the
+// step no longer touches are skipped warp-uniformly).  Rows beyond the box's l are padded with the
+// identity.  Writes X (lower, zero padded) to the block's inverse area and U_pp = X^T (upper,
+// zeros below, staged through shared memory for coalesced rows) to the diagonal block of G.  A
+// pivot that is not positive and finite records kDevNonfinite.
 constexpr int DB = 128, DLD = DB + 1, DTHREADS = 512;
 constexpr int DSMEM = DB * DLD * 4;
+// Register selects with a run-time index written as value selects, so the arrays stay in registers.
+__device__ __forceinline__ float sel4(float a0, float a1, float a2, float a3, int k) {
+  return k == 0 ? a0 : k == 1 ? a1 : k == 2 ? a2 : a3;
+}
+__device__ __forceinline__ float sel8(float a0, float a1, float a2, float a3, float a4, float a5, float a6, float a7,
+                                      int k) {
+  return k < 4 ? sel4(a0, a1, a2, a3, k) : sel4(a4, a5, a6, a7, k - 4);
+}
 struct DiagCount {
   int p;
   __device__ int64_t count(const BoxDesc& d) const { return d.l > (int64_t)p * DB ? 2 : 0; }
 };
-__global__ void __launch_bounds__(DTHREADS) k_chol_diag_tc(GroupArgs g, int p) {
-  extern __shared__ float S[];  // DB x DLD
-  __shared__ float pd[DB];      // L_cc
-  __shared__ float xd[DB];      // X_ii
+__global__ void __launch_bounds__(DTHREADS, 1) k_chol_diag_tc(GroupArgs g, int p) {
+  extern __shared__ float T[];  // DB x DLD staging for the transposed store
+  __shared__ float vec0[2][DB], vec1[2][DB];
   __shared__ int s_bad;
   int64_t loc;
   const DiagCount cnt{p};
@@ -545,68 +555,106 @@ __global__ void __launch_bounds__(DTHREADS) k_chol_diag_tc(GroupArgs g, int p) {
   const int nbp = (int)imin64(DB, d.l - o);
   float* G = gram_side(g, d, side) + o * lg + o;
   if (tid == 0) s_bad = 0;
-  for (int e = tid; e < DB * DB; e += DTHREADS) {
-    const int i = e / DB, j = e % DB;
-    float v = (i == j) ? 1.f : 0.f;
-    if (j <= i && i < nbp) v = G[(int64_t)i * lg + j];
-    S[i * DLD + j] = v;
-  }
-  for (int i = tid; i < DB; i += DTHREADS) xd[i] = 1.f;
-  __syncthreads();
-  // ---- Cholesky ----
+  float A[8][4], X[8][4];
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = ty + 16 * u, j = tx + 32 * v;
+      float a = (i == j) ? 1.f : 0.f;
+      if (j <= i && i < nbp) a = G[(int64_t)i * lg + j];
+      A[u][v] = a;
+      X[u][v] = (i == j) ? 1.f : 0.f;
+    }
+  // ---- Cholesky: column c of the trailing matrix published in vec0[c & 1] ----
   for (int c = 0; c < DB; ++c) {
-    float a = S[c * DLD + c];
+    float* cb = vec0[c & 1];
+    if (tx == (c & 31)) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (ty + 16 * u >= c) cb[ty + 16 * u] = sel4(A[u][0], A[u][1], A[u][2], A[u][3], c >> 5);
+    }
+    __syncthreads();
+    float a = cb[c];
     const bool bad = !(a > 0.f) || !isfinite(a);
     if (bad) a = 1.f;
-    const float inv = 1.f / a;
-    if (c > 0) {
-      const float dp = pd[c - 1];
-      for (int i = c + tid; i < DB; i += DTHREADS) S[i * DLD + c - 1] /= dp;
-      if (tid == DTHREADS - 1) S[(c - 1) * DLD + c - 1] = dp;
+    const float inv = 1.f / a, dg = sqrtf(a);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = ty + 16 * u;
+      if (i <= c) continue;  // warp-uniform
+      const float fi = cb[i] * inv;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int j = tx + 32 * v;
+        if (32 * v + 31 <= c) continue;  // warp-uniform
+        if (j > c && j <= i) A[u][v] = fmaf(-fi, cb[j], A[u][v]);
+      }
     }
-    for (int i = c + 1 + ty; i < DB; i += DTHREADS / 32) {
-      const float f = S[i * DLD + c] * inv;
-      for (int j = c + 1 + tx; j <= i; j += 32) S[i * DLD + j] -= f * S[j * DLD + c];
+    if (tx == (c & 31)) {  // column c becomes column c of L
+      const float rdg = 1.f / dg;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = ty + 16 * u;
+        const float nv = (i == c) ? dg : cb[i < DB ? i : 0] * rdg;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) A[u][v] = (v == (c >> 5) && i >= c) ? nv : A[u][v];
+      }
     }
-    if (tid == 0) {
-      pd[c] = sqrtf(a);
-      if (bad) s_bad = 1;
-    }
-    __syncthreads();
+    if (tid == 0 && bad) s_bad = 1;
   }
-  if (tid == 0) S[(DB - 1) * DLD + DB - 1] = pd[DB - 1];
-  __syncthreads();
-  // ---- X = L^-1: X[r][j] (j < r) at S[j][r], X[i][i] in xd ----
+  // ---- X = L^-1: row i of X (unscaled) in vec0[i & 1], column i of L in vec1[i & 1] ----
   for (int i = 0; i < DB; ++i) {
-    const float lii = S[i * DLD + i];
-    if (i > 0) {
-      const float lp = S[(i - 1) * DLD + i - 1];
-      for (int j = tid; j < i - 1; j += DTHREADS) S[j * DLD + i - 1] /= lp;
-      if (tid == DTHREADS - 1) xd[i - 1] /= lp;
+    float* rb = vec0[i & 1];
+    float* lc = vec1[i & 1];
+    if (ty == (i & 15)) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        if (tx + 32 * v <= i)
+          rb[tx + 32 * v] = sel8(X[0][v], X[1][v], X[2][v], X[3][v], X[4][v], X[5][v], X[6][v], X[7][v], i >> 4);
     }
-    const float xi = xd[i];
-    for (int r = i + 1 + tx; r < DB; r += 32) {
-      const float f = S[r * DLD + i] / lii;
-      for (int j = ty; j <= i; j += DTHREADS / 32) S[j * DLD + r] -= f * (j < i ? S[j * DLD + i] : xi);
+    if (tx == (i & 31)) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (ty + 16 * u >= i) lc[ty + 16 * u] = sel4(A[u][0], A[u][1], A[u][2], A[u][3], i >> 5);
     }
     __syncthreads();
+    const float rl = 1.f / lc[i];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int r = ty + 16 * u;
+      if (r <= i) continue;  // warp-uniform
+      const float fr = lc[r] * rl;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int j = tx + 32 * v;
+        if (32 * v > i) continue;  // warp-uniform
+        if (j <= i) X[u][v] = fmaf(-fr, rb[j], X[u][v]);
+      }
+    }
+    if (ty == (i & 15)) {  // row i is final once scaled by 1 / L_ii
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float sc = (u == (i >> 4)) ? rl : 1.f;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) X[u][v] *= sc;
+      }
+    }
   }
-  {
-    const float lp = S[(DB - 1) * DLD + DB - 1];
-    for (int j = tid; j < DB - 1; j += DTHREADS) S[j * DLD + DB - 1] /= lp;
-    if (tid == DTHREADS - 1) xd[DB - 1] /= lp;
-  }
-  __syncthreads();
   float* Xo = dinv_blk(g, d, side, p);
-  for (int e = tid; e < DB * DB; e += DTHREADS) {
-    const int i = e / DB, j = e % DB;
-    float v = 0.f;
-    if (i < nbp && j < nbp) v = (j < i) ? S[j * DLD + i] : (j == i ? xd[i] : 0.f);
-    Xo[e] = v;
-  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = ty + 16 * u, j = tx + 32 * v;
+      const bool in = i < nbp && j < nbp && j <= i;
+      Xo[i * DB + j] = in ? X[u][v] : 0.f;
+      T[j * DLD + i] = in ? X[u][v] : 0.f;  // U = X^T
+    }
+  __syncthreads();
   for (int e = tid; e < nbp * nbp; e += DTHREADS) {
     const int i = e / nbp, j = e % nbp;
-    G[(int64_t)i * lg + j] = (j > i) ? S[i * DLD + j] : (j == i ? xd[i] : 0.f);
+    G[(int64_t)i * lg + j] = T[i * DLD + j];
   }
   if (tid == 0 && s_bad && g.err) atomicCAS(g.err, 0, (int)kDevNonfinite);
 }

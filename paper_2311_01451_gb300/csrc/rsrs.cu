@@ -1624,6 +1624,248 @@ rsrs_status rsrs_residual(const rsrs_factor* f, const double* B, const double* X
   return RSRS_OK;
 }
 
+}  // extern "C"
+
+// ---- GMRES with the factor as right preconditioner ----------------------------------------
+namespace {
+
+// Krylov blocks are n x c row-major (c = nrhs <= 64), block i of a basis at base + i * n * c.
+// Partial column dot products of w with blocks 0..kk-1 of V: grid (row chunks, kk); thread
+// (col, lane) sums its column over the chunk's rows, the lanes are added in a fixed order.
+constexpr int kDotRows = 2048;
+__global__ void k_vdot_part(const double* __restrict__ V, const double* __restrict__ w, int64_t n, int c,
+                            double* __restrict__ part) {
+  __shared__ double red[256];
+  const int col = threadIdx.x % c, lane = threadIdx.x / c, nl = blockDim.x / c;
+  const int i = blockIdx.y;
+  const double* v = V + (int64_t)i * n * c;
+  const int64_t r0 = (int64_t)blockIdx.x * kDotRows, r1 = imin64(r0 + kDotRows, n);
+  double acc = 0.0;
+  if (lane < nl)
+    for (int64_t r = r0 + lane; r < r1; r += nl) acc = fma(v[r * c + col], w[r * c + col], acc);
+  red[threadIdx.x] = (lane < nl) ? acc : 0.0;
+  __syncthreads();
+  if (threadIdx.x < c) {
+    double t = 0.0;
+    for (int q = 0; q < nl; ++q) t += red[q * c + threadIdx.x];
+    part[((int64_t)i * gridDim.x + blockIdx.x) * c + threadIdx.x] = t;
+  }
+}
+// h[i][col] = sum over chunks (in order) of the partials.
+__global__ void k_vdot_final(const double* __restrict__ part, int nchunk, int kk, int c, double* __restrict__ h) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= kk * c) return;
+  const int i = e / c, col = e % c;
+  double t = 0.0;
+  for (int q = 0; q < nchunk; ++q) t += part[((int64_t)i * nchunk + q) * c + col];
+  h[e] = t;
+}
+// w[r][col] += sign * sum_i V_i[r][col] h[i][col]
+__global__ void k_vcomb(double* __restrict__ w, const double* __restrict__ V, const double* __restrict__ h, int kk,
+                        int64_t n, int c, double sign) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * c) return;
+  const int col = (int)(e % c);
+  double t = 0.0;
+  for (int i = 0; i < kk; ++i) t = fma(V[(int64_t)i * n * c + e], h[i * c + col], t);
+  w[e] += sign * t;
+}
+// out[r][col] = in[r][col] * s[col]
+__global__ void k_colscale(const double* __restrict__ in, const double* __restrict__ sc, int64_t n, int c,
+                           double* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n * c) out[e] = in[e] * sc[e % c];
+}
+
+struct Gmres {
+  cudaStream_t st;
+  int64_t n;
+  int c;
+  double *part, *h_dev;
+  int nchunk;
+  // h[0..kk)[col] = V_i^T w, copied to the host
+  rsrs_status dots(const double* V, int kk, const double* w, double* h_host) {
+    const int threads = (256 / c) * c;
+    k_vdot_part<<<dim3((unsigned)nchunk, (unsigned)kk), threads, 0, st>>>(V, w, n, c, part);
+    k_vdot_final<<<nblk((int64_t)kk * c), 256, 0, st>>>(part, nchunk, kk, c, h_dev);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(h_host, h_dev, (size_t)kk * c * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return RSRS_OK;
+  }
+  rsrs_status comb(double* w, const double* V, const double* h_host, int kk, double sign) {
+    CU(cudaMemcpyAsync(h_dev, h_host, (size_t)kk * c * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_vcomb<<<nblk(n * c), 256, 0, st>>>(w, V, h_dev, kk, n, c, sign);
+    CU(cudaGetLastError());
+    return RSRS_OK;
+  }
+  rsrs_status scale(const double* in, const double* s_host, double* out) {
+    CU(cudaMemcpyAsync(h_dev, s_host, (size_t)c * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_colscale<<<nblk(n * c), 256, 0, st>>>(in, h_dev, n, c, out);
+    CU(cudaGetLastError());
+    return RSRS_OK;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+rsrs_status rsrs_gmres(const rsrs_factor* f, const double* B, double* X, int64_t ld, int32_t nrhs, double rtol,
+                       int restart, int maxit, void* stream, rsrs_refine_report* rep) {
+  rsrs_status r = check_block(f, B, ld, nrhs);
+  if (r != RSRS_OK) return r;
+  if (!X || nrhs > 64 || restart < 1 || restart > 64 || maxit < 1 || !(rtol >= 0.0))
+    return fail(RSRS_E_INVAL, "gmres: bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  Launch L{st, nullptr};
+  DevPool pool;
+  const int c = nrhs, m = restart;
+  const int64_t n = f->n, tot = n * c;
+  double *Wb, *Wx, *Ww, *V, *Z, *c1 = nullptr, *c2 = nullptr;
+  Gmres gm{st, n, c, nullptr, nullptr, (int)cdiv(n, kDotRows)};
+  CU(pool.alloc(&Wb, tot));
+  CU(pool.alloc(&Wx, tot));
+  CU(pool.alloc(&Ww, tot));
+  CU(pool.alloc(&V, (int64_t)(m + 1) * tot));
+  CU(pool.alloc(&Z, (int64_t)m * tot));
+  CU(pool.alloc(&gm.part, (int64_t)(m + 1) * gm.nchunk * c));
+  CU(pool.alloc(&gm.h_dev, (int64_t)(m + 1) * c));
+  if (f->kind == RSRS_OP_CALLBACK) {
+    CU(pool.alloc(&c1, tot));
+    CU(pool.alloc(&c2, tot));
+  }
+  const bool ff = f->kind != RSRS_OP_CALLBACK && !f->residual_fp64;
+  float* ffs = nullptr;
+  if (ff) CU(pool.alloc(&ffs, ff_scratch_floats(n, f->d, c, f->tune.residual_split)));
+  // A y in the refinement's residual arithmetic
+  auto apply_A = [&](const double* in, double* out) -> rsrs_status {
+    if (ff) {
+      launch_kernel_matvec_ff(L, f->kind, f->pts_dev, f->d, n, f->shift, f->scale, in, c, out, c, c, ffs,
+                              f->tune.residual_split);
+      CU(cudaGetLastError());
+      return RSRS_OK;
+    }
+    return op_apply(f, L, in, out, c, 0, 0, c1, c2);
+  };
+  k_cm_to_rows<<<nblk(tot), 256, 0, st>>>(B, ld, f->perm_dev, n, c, Wb);
+  CU(cudaMemsetAsync(Wx, 0, tot * sizeof(double), st));
+  std::vector<double> bn(c), beta(c), hcol((size_t)(m + 1) * c), h2((size_t)(m + 1) * c), sc(c);
+  r = gm.dots(Wb, 1, Wb, bn.data());
+  if (r != RSRS_OK) return r;
+  for (double& v : bn) v = std::sqrt(v);
+  // per column: Hessenberg columns (m+1) x m, Givens rotations, least-squares right-hand side
+  std::vector<double> H((size_t)c * (m + 1) * m), cs((size_t)c * m), sn((size_t)c * m), g((size_t)c * (m + 1));
+  rsrs_refine_report rr{};
+  int total = 0, hist = 0;
+  double rel = 0.0;
+  bool first = true;
+  for (;;) {
+    // residual of the current iterate (the first one is b itself: x = 0)
+    if (first) {
+      CU(cudaMemcpyAsync(Ww, Wb, tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+      r = apply_A(Wx, Ww);
+      if (r != RSRS_OK) return r;
+      k_sub<<<nblk(tot), 256, 0, st>>>(Ww, Wb, Ww, tot);
+      CU(cudaGetLastError());
+    }
+    first = false;
+    r = gm.dots(Ww, 1, Ww, beta.data());
+    if (r != RSRS_OK) return r;
+    rel = 0.0;
+    for (int j = 0; j < c; ++j) {
+      beta[j] = std::sqrt(beta[j]);
+      rel = std::max(rel, beta[j] / std::max(bn[j], 1e-300));
+    }
+    if (!std::isfinite(rel)) return fail(RSRS_E_NONFINITE, "gmres: non-finite residual");
+    if (hist < 64) rr.history[hist++] = rel;
+    if (rel <= rtol || total >= maxit) break;
+    for (int j = 0; j < c; ++j) sc[j] = beta[j] > 0.0 ? 1.0 / beta[j] : 0.0;
+    r = gm.scale(Ww, sc.data(), V);
+    if (r != RSRS_OK) return r;
+    std::fill(g.begin(), g.end(), 0.0);
+    for (int j = 0; j < c; ++j) g[(size_t)j * (m + 1)] = beta[j];
+    int k = 0;
+    for (; k < m && total < maxit; ++k) {
+      double* Vk = V + (int64_t)k * tot;
+      double* Zk = Z + (int64_t)k * tot;
+      CU(cudaMemcpyAsync(Zk, Vk, tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      r = sweep_solve(f, L, Zk, c, 0);  // z_k = M^-1 v_k
+      if (r != RSRS_OK) return r;
+      r = apply_A(Zk, Ww);              // w = A z_k
+      if (r != RSRS_OK) return r;
+      // classical Gram-Schmidt, twice
+      r = gm.dots(V, k + 1, Ww, hcol.data());
+      if (r == RSRS_OK) r = gm.comb(Ww, V, hcol.data(), k + 1, -1.0);
+      if (r == RSRS_OK) r = gm.dots(V, k + 1, Ww, h2.data());
+      if (r == RSRS_OK) r = gm.comb(Ww, V, h2.data(), k + 1, -1.0);
+      if (r != RSRS_OK) return r;
+      for (size_t e = 0; e < (size_t)(k + 1) * c; ++e) hcol[e] += h2[e];
+      std::vector<double> hn(c);
+      r = gm.dots(Ww, 1, Ww, hn.data());
+      if (r != RSRS_OK) return r;
+      double est = 0.0;
+      for (int j = 0; j < c; ++j) {
+        hn[j] = std::sqrt(hn[j]);
+        double* Hj = H.data() + (size_t)j * (m + 1) * m + (size_t)k * (m + 1);  // column k of H_j
+        for (int i = 0; i <= k; ++i) Hj[i] = hcol[(size_t)i * c + j];
+        Hj[k + 1] = hn[j];
+        // previous rotations, then a new one that zeroes H[k+1][k]
+        for (int i = 0; i < k; ++i) {
+          const double a = Hj[i], b2 = Hj[i + 1];
+          Hj[i] = cs[(size_t)j * m + i] * a + sn[(size_t)j * m + i] * b2;
+          Hj[i + 1] = -sn[(size_t)j * m + i] * a + cs[(size_t)j * m + i] * b2;
+        }
+        const double a = Hj[k], b2 = Hj[k + 1];
+        const double rho = std::hypot(a, b2);
+        const double cc = rho > 0.0 ? a / rho : 1.0, ss = rho > 0.0 ? b2 / rho : 0.0;
+        cs[(size_t)j * m + k] = cc;
+        sn[(size_t)j * m + k] = ss;
+        Hj[k] = rho;
+        Hj[k + 1] = 0.0;
+        double* gj = g.data() + (size_t)j * (m + 1);
+        gj[k + 1] = -ss * gj[k];
+        gj[k] = cc * gj[k];
+        est = std::max(est, std::fabs(gj[k + 1]) / std::max(bn[j], 1e-300));
+        sc[j] = hn[j] > 0.0 ? 1.0 / hn[j] : 0.0;
+      }
+      ++total;
+      if (hist < 64) rr.history[hist++] = est;
+      r = gm.scale(Ww, sc.data(), V + (int64_t)(k + 1) * tot);
+      if (r != RSRS_OK) return r;
+      if (est <= rtol) {
+        ++k;
+        break;
+      }
+    }
+    // x += Z y with H y = g (upper triangular k x k per column)
+    std::vector<double> y((size_t)k * c, 0.0);
+    for (int j = 0; j < c; ++j) {
+      const double* Hj = H.data() + (size_t)j * (m + 1) * m;
+      const double* gj = g.data() + (size_t)j * (m + 1);
+      for (int i = k - 1; i >= 0; --i) {
+        double t = gj[i];
+        for (int q = i + 1; q < k; ++q) t -= Hj[(size_t)q * (m + 1) + i] * y[(size_t)q * c + j];
+        const double d = Hj[(size_t)i * (m + 1) + i];
+        y[(size_t)i * c + j] = d != 0.0 ? t / d : 0.0;
+      }
+    }
+    if (k > 0) {
+      r = gm.comb(Wx, Z, y.data(), k, 1.0);
+      if (r != RSRS_OK) return r;
+    }
+  }
+  k_rows_to_cm<<<nblk(tot), 256, 0, st>>>(Wx, f->perm_dev, n, c, X, ld);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(st));
+  rr.iterations = total;
+  rr.rel_residual = rel;
+  if (rep) *rep = rr;
+  if (rel > rtol) return fail(RSRS_E_NOT_CONVERGED, "gmres: residual " + std::to_string(rel) + " > rtol");
+  return RSRS_OK;
+}
+
 rsrs_status rsrs_factor_stats(const rsrs_factor* f, rsrs_stats* out) {
   if (!f || !out) return fail(RSRS_E_INVAL, "null argument");
   *out = f->stats;

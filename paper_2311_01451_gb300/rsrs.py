@@ -25,7 +25,7 @@ STATUS = {0: "RSRS_OK", 1: "RSRS_E_INVAL", 2: "RSRS_E_UNDERSAMPLED", 3: "RSRS_E_
 EXPORTS = ["rsrs_tree_build", "rsrs_tree_info", "rsrs_tree_perm", "rsrs_tree_schedule", "rsrs_tree_free",
            "rsrs_build", "rsrs_build_batched", "rsrs_refactor", "rsrs_solve", "rsrs_solve_noalloc", "rsrs_apply", "rsrs_refine", "rsrs_residual", "rsrs_matvec", "rsrs_factor_stats",
            "rsrs_factor_box", "rsrs_factor_root", "rsrs_factor_sketches", "rsrs_factor_free",
-           "rsrs_status_string", "rsrs_last_error", "rsrs_kernel_class_name", "rsrs_stencil7_create", "rsrs_stencil7_matvec", "rsrs_stencil7_free", "rsrs_autotune"]
+           "rsrs_status_string", "rsrs_last_error", "rsrs_kernel_class_name", "rsrs_stencil7_create", "rsrs_stencil7_matvec", "rsrs_stencil7_free", "rsrs_autotune", "rsrs_gmres"]
 
 MATVEC_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.c_int64, C.c_int32, C.c_void_p, C.c_int64,
                         C.c_void_p, C.c_int64, C.c_void_p)
@@ -123,6 +123,7 @@ def lib():
             "rsrs_solve_noalloc": [vp, vp, i64, i32, C.c_int, vp],
             "rsrs_apply": [vp, vp, i64, i32, C.c_int, vp],
             "rsrs_refine": [vp, vp, vp, i64, i32, dbl, C.c_int, vp, C.POINTER(RefineReport)],
+            "rsrs_gmres": [vp, vp, vp, i64, i32, dbl, C.c_int, C.c_int, vp, C.POINTER(RefineReport)],
             "rsrs_residual": [vp, vp, vp, vp, i64, i32, vp],
             "rsrs_matvec": [vp, vp, vp, i64, i32, vp],
             "rsrs_factor_stats": [vp, C.POINTER(Stats)],
@@ -335,6 +336,16 @@ class Factor:
             raise ValueError("B, X and Rout must have the same shape")
         _check(lib().rsrs_residual(self._h, pb, px, pr_, ld, nr, _stream_ptr(stream)))
         return Rout
+
+    def gmres(self, B, X, rtol: float = 1e-12, restart: int = 30, maxit: int = 60, stream=None) -> RefineReport:
+        """rsrs_gmres: X = A^-1 B by GMRES with this factor as right preconditioner."""
+        pb, ld, nr = _cm(B)
+        px, ldx, nrx = _cm(X)
+        if (ldx, nrx) != (ld, nr):
+            raise ValueError("B and X must have the same shape")
+        rep = RefineReport()
+        _check(lib().rsrs_gmres(self._h, pb, px, ld, nr, rtol, restart, maxit, _stream_ptr(stream), C.byref(rep)))
+        return rep
 
     def refine(self, B, X, rtol: float = 1e-12, maxit: int = 20, stream=None) -> RefineReport:
         pb, ld, nr = _cm(B)
