@@ -80,12 +80,15 @@ enum {
                         /* LU, the root, the solve and the refinement residual             */
 };
 
-/* Tile shapes of the tensor-core sampling product: column tile x pipeline stages. */
+/* Tile shapes of the tensor-core sampling product: column tile x pipeline stages (of 32 points
+ * unless stated). */
 enum {
-  RSRS_SAMPLE_TILE_DEFAULT = 0,  /* the library's choice (256 x 2)                               */
+  RSRS_SAMPLE_TILE_DEFAULT = 0,  /* the library's choice (256 x 4 of 16 points)                 */
   RSRS_SAMPLE_TILE_256x2 = 1,    /* 256 columns per CTA, two stages                              */
   RSRS_SAMPLE_TILE_128x3 = 2,    /* 128 columns, three stages                                    */
-  RSRS_SAMPLE_TILE_192x2 = 3     /* 192 columns, two stages                                      */
+  RSRS_SAMPLE_TILE_192x2 = 3,    /* 192 columns, two stages                                      */
+  RSRS_SAMPLE_TILE_256x4_K16 = 4, /* 256 columns, four stages of 16 points (64-byte swizzle)     */
+  RSRS_SAMPLE_TILE_192x5_K16 = 5  /* 192 columns, five stages of 16 points                       */
 };
 
 /* Launch shapes of the kernels whose best shape depends on the problem and the device; all zero

@@ -150,8 +150,8 @@ void launch_gram_tc(Launch L, const GroupArgs& g, const std::vector<BoxDesc>& h)
 void launch_proj_nt_tc(Launch L, const GroupArgs& g, int pass, const std::vector<BoxDesc>& h);
 void launch_proj_acc_tc(Launch L, const GroupArgs& g, int pass, const std::vector<BoxDesc>& h);
 // Tensor-core path of the Gram factorisation and the projection solve (FP32 workspace, Gram from
-// launch_gram_tc): blocked Cholesky G = L L^T with 128-wide panels (diagonal blocks factored and
-// inverted by one CTA each, panel and trailing products in 3xTF32), then U = L^-T by blocked
+// launch_gram_tc): left-looking blocked Cholesky G = L L^T with 128-wide panels (diagonal blocks
+// factored and inverted by one CTA each, column-block and panel products in 3xTF32), then U = L^-T by blocked
 // substitution, stored in the upper block triangle of G (lower: L~_ik = L_ii^-1 L_ik).
 // launch_solve_tc: X <- X G^-1 = (X U) U^T for the pass's coefficients (pass 1 also adds the
 // result into the pass-0 coefficients).

@@ -173,29 +173,27 @@ struct CholPanelJob {  // L_ip = G_ip L_pp^-T for the blocks i > p below the dia
     return t;
   }
 };
-struct CholUpdJob {  // G_ij -= L_ip L_jp^T for i >= j > p
+struct CholLeftJob {  // G_ip -= L_{i,0:p} L_{p,0:p}^T for i >= p (left-looking: column block p, K = 128 p)
   int p;
   __device__ int64_t count(const BoxDesc& d) const {
-    const int64_t t = cdiv128(d.l) - p - 1;
-    return t > 0 ? 2 * tri_n(t) : 0;
+    const int64_t t = cdiv128(d.l) - p;
+    return t > 0 ? 2 * t : 0;
   }
   __device__ TcTile tile(const GroupArgs& g, const BoxDesc& d, int64_t loc) const {
-    const int64_t per = tri_n(cdiv128(d.l) - p - 1), lg = gram_ld(d.l);
+    const int64_t per = cdiv128(d.l) - p, lg = gram_ld(d.l);
     const int side = (int)(loc / per);
-    int64_t ti, tj;
-    tri_idx(loc % per, ti, tj);
-    const int64_t i = p + 1 + ti, j = p + 1 + tj;
+    const int64_t i = p + loc % per;
     float* G = gram_side(g, d, side);
     TcTile t;
-    t.A = G + i * GM * lg + (int64_t)p * GM;
+    t.A = G + i * GM * lg;
     t.lda = lg;
     t.m = rows_of(d.l, i);
-    t.B = G + j * GM * lg + (int64_t)p * GM;
+    t.B = G + (int64_t)p * GM * lg;
     t.ldb = lg;
-    t.n = rows_of(d.l, j);
+    t.n = rows_of(d.l, p);
     t.bnm = 0;
-    t.K = GM;
-    t.D = G + i * GM * lg + j * GM;
+    t.K = (int64_t)p * GM;
+    t.D = G + i * GM * lg + (int64_t)p * GM;  // column block p: disjoint from the columns read
     t.ldd = lg;
     t.alpha = -1.f;
     t.beta = 1.f;
@@ -516,33 +514,25 @@ __global__ void __launch_bounds__(GTHREADS, 1) k_tc_grouped(GroupArgs g, Job job
 
 
 // Diagonal block p of the blocked Cholesky, one CTA per (box, side) with l > 128 p: G_pp = L L^T
-// (right-looking, column by column) and X = L^-1 (forward substitution on the identity, row by row),
-// with the 128 x 128 block held in registers: thread (ty, tx) of 16 x 32 owns the elements
-// (ty + 16u, tx + 32v), u < 8, v < 4, of both L and X.  Each step publishes one column of the
-// trailing matrix (Cholesky) or one row of X and one column of L (inverse) through a
-// double-buffered shared vector, so one barrier per step suffices, and every thread updates its
-// 32 elements from the published values (independent FMAs; blocks of rows and columns that the
-// step no longer touches are skipped warp-uniformly).  Rows beyond the box's l are padded with the
-// identity.  Writes X (lower, zero padded) to the block's inverse area and U_pp = X^T (upper,
-// zeros below, staged through shared memory for coalesced rows) to the diagonal block of G.  A
-// pivot that is not positive and finite records kDevNonfinite.
-constexpr int DB = 128, DLD = DB + 1, DTHREADS = 512;
-constexpr int DSMEM = DB * DLD * 4;
-// Register selects with a run-time index written as value selects, so the arrays stay in registers.
-__device__ __forceinline__ float sel4(float a0, float a1, float a2, float a3, int k) {
-  return k == 0 ? a0 : k == 1 ? a1 : k == 2 ? a2 : a3;
-}
-__device__ __forceinline__ float sel8(float a0, float a1, float a2, float a3, float a4, float a5, float a6, float a7,
-                                      int k) {
-  return k < 4 ? sel4(a0, a1, a2, a3, k) : sel4(a4, a5, a6, a7, k - 4);
-}
+// and X = L^-1, both blocked by 16.  Cholesky, right-looking over eight 16-column panels: one warp
+// factors the panel (rows in registers, 16 column steps with shuffles, no block barrier), then all
+// warps apply its rank-16 update to the trailing lower triangle.  Inverse: the eight 16 x 16
+// diagonal blocks by one warp each (a column of X per lane, forward substitution), then block row
+// by block row X_ij = -X_ii sum_{j<=k<i} L_ik X_kj.  Rows beyond the box's l are padded with the
+// identity.  Writes X (lower, zero padded) to the block's inverse area and U_pp = X^T (upper, zeros
+// below) to the diagonal block of G.  A pivot that is not positive and finite records
+// kDevNonfinite (and is replaced by 1 so that the factorisation completes).
+constexpr int DB = 128, DLD = DB + 1, DTHREADS = 512, DW = 16;
+constexpr int DSMEM = (2 * DB * DLD + DW * DB) * 4;
 struct DiagCount {
   int p;
   __device__ int64_t count(const BoxDesc& d) const { return d.l > (int64_t)p * DB ? 2 : 0; }
 };
 __global__ void __launch_bounds__(DTHREADS, 1) k_chol_diag_tc(GroupArgs g, int p) {
-  extern __shared__ float T[];  // DB x DLD staging for the transposed store
-  __shared__ float vec0[2][DB], vec1[2][DB];
+  extern __shared__ float dsm[];
+  float* S = dsm;                // DB x DLD: G_pp, then L (lower)
+  float* Xs = S + DB * DLD;      // DB x DLD: X = L^-1 (lower)
+  float* Tb = Xs + DB * DLD;     // DW x DB: partial products of one block row
   __shared__ int s_bad;
   int64_t loc;
   const DiagCount cnt{p};
@@ -550,111 +540,123 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_chol_diag_tc(GroupArgs g, int p
   if (bi < 0) return;
   const BoxDesc d = g.desc[bi];
   const int side = (int)loc;
-  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t lg = gram_ld(d.l), o = (int64_t)p * DB;
   const int nbp = (int)imin64(DB, d.l - o);
   float* G = gram_side(g, d, side) + o * lg + o;
   if (tid == 0) s_bad = 0;
-  float A[8][4], X[8][4];
-#pragma unroll
-  for (int u = 0; u < 8; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int i = ty + 16 * u, j = tx + 32 * v;
-      float a = (i == j) ? 1.f : 0.f;
-      if (j <= i && i < nbp) a = G[(int64_t)i * lg + j];
-      A[u][v] = a;
-      X[u][v] = (i == j) ? 1.f : 0.f;
-    }
-  // ---- Cholesky: column c of the trailing matrix published in vec0[c & 1] ----
-  for (int c = 0; c < DB; ++c) {
-    float* cb = vec0[c & 1];
-    if (tx == (c & 31)) {
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (ty + 16 * u >= c) cb[ty + 16 * u] = sel4(A[u][0], A[u][1], A[u][2], A[u][3], c >> 5);
-    }
-    __syncthreads();
-    float a = cb[c];
-    const bool bad = !(a > 0.f) || !isfinite(a);
-    if (bad) a = 1.f;
-    const float inv = 1.f / a, dg = sqrtf(a);
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int i = ty + 16 * u;
-      if (i <= c) continue;  // warp-uniform
-      const float fi = cb[i] * inv;
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const int j = tx + 32 * v;
-        if (32 * v + 31 <= c) continue;  // warp-uniform
-        if (j > c && j <= i) A[u][v] = fmaf(-fi, cb[j], A[u][v]);
-      }
-    }
-    if (tx == (c & 31)) {  // column c becomes column c of L
-      const float rdg = 1.f / dg;
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int i = ty + 16 * u;
-        const float nv = (i == c) ? dg : cb[i < DB ? i : 0] * rdg;
-#pragma unroll
-        for (int v = 0; v < 4; ++v) A[u][v] = (v == (c >> 5) && i >= c) ? nv : A[u][v];
-      }
-    }
-    if (tid == 0 && bad) s_bad = 1;
+  for (int e = tid; e < DB * DB; e += DTHREADS) {
+    const int i = e / DB, j = e % DB;
+    float v = (i == j) ? 1.f : 0.f;
+    if (j <= i && i < nbp) v = G[(int64_t)i * lg + j];
+    S[i * DLD + j] = v;
   }
-  // ---- X = L^-1: row i of X (unscaled) in vec0[i & 1], column i of L in vec1[i & 1] ----
-  for (int i = 0; i < DB; ++i) {
-    float* rb = vec0[i & 1];
-    float* lc = vec1[i & 1];
-    if (ty == (i & 15)) {
+  __syncthreads();
+  // ---- Cholesky ----
+  for (int c0 = 0; c0 < DB; c0 += DW) {
+    if (warp == 0) {
+      // panel rows c0 + lane + 32 q, columns c0 .. c0 + 15
+      float P[4][DW];
 #pragma unroll
-      for (int v = 0; v < 4; ++v)
-        if (tx + 32 * v <= i)
-          rb[tx + 32 * v] = sel8(X[0][v], X[1][v], X[2][v], X[3][v], X[4][v], X[5][v], X[6][v], X[7][v], i >> 4);
-    }
-    if (tx == (i & 31)) {
+      for (int q = 0; q < 4; ++q)
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (ty + 16 * u >= i) lc[ty + 16 * u] = sel4(A[u][0], A[u][1], A[u][2], A[u][3], i >> 5);
+        for (int cc = 0; cc < DW; ++cc) {
+          const int r = c0 + lane + 32 * q;
+          P[q][cc] = r < DB ? S[r * DLD + c0 + cc] : 0.f;
+        }
+      bool bad = false;
+#pragma unroll
+      for (int cc = 0; cc < DW; ++cc) {
+        float a = __shfl_sync(0xffffffffu, P[0][cc], cc);  // row c0 + cc lives in lane cc, q = 0
+        if (!(a > 0.f) || !isfinite(a)) {
+          bad = true;
+          a = 1.f;
+        }
+        const float dg = __fsqrt_rn(a), rd = __frcp_rn(dg);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int ri = lane + 32 * q;
+          P[q][cc] = ri == cc ? dg : (ri > cc ? P[q][cc] * rd : P[q][cc]);
+        }
+#pragma unroll
+        for (int c2 = 1; c2 < DW; ++c2) {
+          if (c2 <= cc) continue;  // compile-time
+          const float lc = __shfl_sync(0xffffffffu, P[0][cc], c2);  // L[c0 + c2][c0 + cc]
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (lane + 32 * q >= c2) P[q][c2] = fmaf(-P[q][cc], lc, P[q][c2]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int cc = 0; cc < DW; ++cc) {
+          const int r = c0 + lane + 32 * q;
+          if (r < DB) S[r * DLD + c0 + cc] = P[q][cc];
+        }
+      if (lane == 0 && bad) s_bad = 1;
     }
     __syncthreads();
-    const float rl = 1.f / lc[i];
+    // rank-16 update of the trailing lower triangle
+    const int c1 = c0 + DW;
+    if (c1 < DB) {
+      const int ty = warp, tx = lane;
+      for (int i = c1 + ty; i < DB; i += DTHREADS / 32) {
+        float pi[DW];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int r = ty + 16 * u;
-      if (r <= i) continue;  // warp-uniform
-      const float fr = lc[r] * rl;
+        for (int k = 0; k < DW; ++k) pi[k] = S[i * DLD + c0 + k];
+        for (int j = c1 + tx; j <= i; j += 32) {
+          float acc = 0.f;
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const int j = tx + 32 * v;
-        if (32 * v > i) continue;  // warp-uniform
-        if (j <= i) X[u][v] = fmaf(-fr, rb[j], X[u][v]);
+          for (int k = 0; k < DW; ++k) acc = fmaf(pi[k], S[j * DLD + c0 + k], acc);
+          S[i * DLD + j] -= acc;
+        }
       }
     }
-    if (ty == (i & 15)) {  // row i is final once scaled by 1 / L_ii
+    __syncthreads();
+  }
+  // ---- X = L^-1: diagonal 16 x 16 blocks, one warp each, a column per lane ----
+  if (warp < DB / DW && lane < DW) {
+    const int k0 = warp * DW, j = lane;
+    float x[DW];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const float sc = (u == (i >> 4)) ? rl : 1.f;
+    for (int r = 0; r < DW; ++r) {
+      float acc = (r == j) ? 1.f : 0.f;
 #pragma unroll
-        for (int v = 0; v < 4; ++v) X[u][v] *= sc;
-      }
+      for (int t = 0; t < r; ++t) acc = fmaf(-S[(k0 + r) * DLD + k0 + t], x[t], acc);
+      x[r] = r >= j ? acc / S[(k0 + r) * DLD + k0 + r] : 0.f;
     }
+#pragma unroll
+    for (int r = 0; r < DW; ++r) Xs[(k0 + r) * DLD + k0 + j] = x[r];
+  }
+  __syncthreads();
+  // block rows i = 1..7: T_ij = sum_{j<=k<i} L_ik X_kj, then X_ij = -X_ii T_ij
+  for (int ib = 1; ib < DB / DW; ++ib) {
+    const int i0 = ib * DW;
+    for (int e = tid; e < DW * i0; e += DTHREADS) {  // T: DW rows x (columns of blocks j < i)
+      const int a = e / i0, col = e % i0, jb = col / DW;
+      float acc = 0.f;
+      for (int k = jb * DW; k < i0; ++k) acc = fmaf(S[(i0 + a) * DLD + k], Xs[k * DLD + col], acc);
+      Tb[a * DB + col] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < DW * i0; e += DTHREADS) {
+      const int a = e / i0, col = e % i0;
+      float acc = 0.f;
+#pragma unroll
+      for (int c = 0; c < DW; ++c) acc = fmaf(Xs[(i0 + a) * DLD + i0 + c], Tb[c * DB + col], acc);
+      Xs[(i0 + a) * DLD + col] = -acc;
+    }
+    __syncthreads();
   }
   float* Xo = dinv_blk(g, d, side, p);
-#pragma unroll
-  for (int u = 0; u < 8; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int i = ty + 16 * u, j = tx + 32 * v;
-      const bool in = i < nbp && j < nbp && j <= i;
-      Xo[i * DB + j] = in ? X[u][v] : 0.f;
-      T[j * DLD + i] = in ? X[u][v] : 0.f;  // U = X^T
-    }
-  __syncthreads();
+  for (int e = tid; e < DB * DB; e += DTHREADS) {
+    const int i = e / DB, j = e % DB;
+    Xo[e] = (i < nbp && j < nbp && j <= i) ? Xs[i * DLD + j] : 0.f;
+  }
   for (int e = tid; e < nbp * nbp; e += DTHREADS) {
     const int i = e / nbp, j = e % nbp;
-    G[(int64_t)i * lg + j] = T[i * DLD + j];
+    G[(int64_t)i * lg + j] = (j >= i) ? Xs[j * DLD + i] : 0.f;  // U = X^T
   }
   if (tid == 0 && s_bad && g.err) atomicCAS(g.err, 0, (int)kDevNonfinite);
 }
@@ -701,7 +703,14 @@ void launch_chol_tc(Launch L, const GroupArgs& g, const std::vector<BoxDesc>& h)
     cudaFuncSetAttribute(k_chol_diag_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, DSMEM);
     attr = true;
   }
+  // left-looking: column block p takes all earlier panels in one product (K = 128 p), then its
+  // diagonal block is factored and inverted and the blocks below it are scaled
   for (int p = 0; p < (int)nbmax; ++p) {
+    if (p > 0)
+      launch_job(L, g, CholLeftJob{p}, items_of_h(h, [p](const BoxDesc& d) {
+                   const int64_t t = cdiv128(d.l) - p;
+                   return t > 0 ? 2 * t : (int64_t)0;
+                 }));
     const int64_t nd = items_of_h(h, [p](const BoxDesc& d) { return d.l > (int64_t)p * DB ? 2 : 0; });
     if (nd > 0) {
       k_chol_diag_tc<<<(unsigned)nd, DTHREADS, DSMEM, L.st>>>(g, p);
@@ -710,10 +719,6 @@ void launch_chol_tc(Launch L, const GroupArgs& g, const std::vector<BoxDesc>& h)
     launch_job(L, g, CholPanelJob{p}, items_of_h(h, [p](const BoxDesc& d) {
                  const int64_t t = cdiv128(d.l) - p - 1;
                  return t > 0 ? 2 * t : (int64_t)0;
-               }));
-    launch_job(L, g, CholUpdJob{p}, items_of_h(h, [p](const BoxDesc& d) {
-                 const int64_t t = cdiv128(d.l) - p - 1;
-                 return t > 0 ? 2 * tri_n(t) : (int64_t)0;
                }));
   }
   launch_job(L, g, LtildeJob{}, items_of_h(h, [](const BoxDesc& d) {

@@ -5,41 +5,71 @@
 // tensor memory.  The split follows Ootomo & Yokota (2022); products are then accurate to about
 // 2^-21 relative, the level of the FP32 arithmetic of the rest of the mixed path.
 //
-// Tile: D = 128 rows (TMEM lanes) x up to 256 columns (TMEM columns); 32 points j per stage.
-//   A_hi, A_lo: K(x_i, x_j) for the 128 rows, generated by 16 producer warps (K-major, 128-byte rows
-//               of 32 TF32 values, 128-byte swizzle, 8-row atoms 1024 bytes apart);
+// Tile: D = 128 rows (TMEM lanes) x TN <= 256 columns (TMEM columns); KT points j per stage.
+//   A_hi, A_lo: K(x_i, x_j) for the 128 rows, generated by 16 producer warps (K-major rows of KT
+//               TF32 values: 128-byte rows with the 128-byte swizzle for KT = 32, 64-byte rows
+//               with the 64-byte swizzle for KT = 16);
 //   B_hi, B_lo: in[j][c] for the tile's columns, from hi/lo planes split and transposed once
 //               before the product (FP64 -> FP32 conversion runs at FP64 rate on this part, so it
 //               must not sit in the inner loop), fetched by TMA straight into the same swizzled
-//               layout (the tensor map's 128-byte swizzle is the canonical K-major one).
-// A seventeenth warp issues, from one thread, the TMA copies and the 4 K-steps x 3 products per
-// stage.  Two stages; per stage three mbarriers: A written (512 arrivals), B landed (TMA transaction
-// bytes) and stage free (tcgen05.commit of the products that read it).  The products of chunk c
-// are issued before the copies for chunk c+1 are armed, so the tensor pipe has work queued while
-// the next stage fills.  Every wait is bounded: on expiry the kernel records kDevTimeout, waits
-// (bounded) for its own copies still in flight, frees its TMEM and returns.
+//               layout (the tensor map's swizzle is the canonical K-major one); the two CTAs of a
+//               cluster each load half of the columns and multicast it to both.
+// A seventeenth warp issues, from one thread, the TMA copies and the KT/8 K-steps x 3 products per
+// stage.  NST stages (default: TN = 256, KT = 16, four stages); per stage three mbarriers: A
+// written (512 arrivals), B landed (TMA transaction bytes) and stage free (tcgen05.commit of the
+// products of both CTAs that read it).  The copies of chunk c + NST - 1 are armed once the
+// products of chunk c - 1 are done, so the B tiles arrive NST - 1 products ahead.  Chunks that
+// overlap the row tile (K_ii = 0) or hold the last points test indices; the others do not.  Every
+// wait is bounded: on expiry the kernel records kDevTimeout, waits (bounded) for its own copies
+// still in flight, frees its TMEM and returns.
 #include <cuda.h>
 
 #include <cstdint>
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 
 namespace rsrs {
 namespace {
 
-constexpr int TM = 128, TK = 32;
-constexpr int A_BYTES = TM * TK * 4;                      // 16 KB
+constexpr int TM = 128;
+constexpr int TK = 32;                                    // point padding of p32 (a multiple of every KT)
 constexpr int NPROD = 512;                                // producer threads (warps 0..15)
-// Column tile TN and pipeline depth NST of one variant: B_hi and B_lo tiles of TN columns, stages
-// of A_hi, A_lo, B_hi, B_lo; the TMEM accumulator takes the next power of two >= TN columns.
-template <int TN, int NST>
+// K-major operand tiles with KT TF32 values (4 KT bytes) per row: KT = 32 uses the 128-byte swizzle
+// (8-row atoms of 1024 bytes), KT = 16 the 64-byte swizzle (8-row atoms of 512 bytes).  In both, the
+// 16-byte chunk index of a row is XOR-ed with address bits 7.. of the row start, which is what
+// the TMA writes with the matching tensor-map swizzle and the MMA reads with the matching
+// descriptor layout.
+template <int KT>
+struct Lay;
+template <>
+struct Lay<32> {
+  static constexpr uint32_t SBO = 1024, MODE = 2;  // descriptor layout: 128-byte swizzle
+  static constexpr CUtensorMapSwizzle TMA_SWIZZLE = CU_TENSOR_MAP_SWIZZLE_128B;
+  __device__ static uint32_t off(int row, int k) {
+    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + (((k >> 2) ^ (row & 7)) << 4) + (k & 3) * 4);
+  }
+};
+template <>
+struct Lay<16> {
+  static constexpr uint32_t SBO = 512, MODE = 4;  // descriptor layout: 64-byte swizzle
+  static constexpr CUtensorMapSwizzle TMA_SWIZZLE = CU_TENSOR_MAP_SWIZZLE_64B;
+  __device__ static uint32_t off(int row, int k) {
+    return (uint32_t)(row * 64 + (((k >> 2) ^ ((row >> 1) & 3)) << 4) + (k & 3) * 4);
+  }
+};
+// One variant: column tile TN, points per stage KT and pipeline depth NST: stages of A_hi, A_lo
+// (128 x KT) and B_hi, B_lo (TN x KT); the TMEM accumulator takes the next power of two >= TN.
+template <int TN, int KT, int NST>
 struct Tile {
-  static constexpr int B_BYTES = TN * TK * 4;
+  static constexpr int A_BYTES = TM * KT * 4;
+  static constexpr int B_BYTES = TN * KT * 4;
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
   static constexpr int SMEM_BYTES = NST * STAGE_BYTES + 1024;  // + alignment slack
   static constexpr uint32_t TMEM_COLS = TN <= 32 ? 32 : TN <= 64 ? 64 : TN <= 128 ? 128 : 256;
   static_assert(TN % 32 == 0 && TN >= 32 && TN <= 256, "MMA N and the multicast halves");
+  static_assert(KT == 16 || KT == 32, "K-slice of one stage");
   static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per CTA");
 };
 constexpr int NTHREADS = NPROD + 32;                      // + the TMA / MMA warp
@@ -47,22 +77,16 @@ constexpr long long WAIT_LIMIT = 1ll << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Byte offset of element (row, k) of a K-major tile with 128-byte rows and the 128-byte swizzle:
-// the 16-byte chunk index (bits 4..6) is XOR-ed with the row inside the 8-row atom (bits 7..9).
-__device__ __forceinline__ uint32_t sw128(int row, int k) {
-  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + (((k >> 2) ^ (row & 7)) << 4) + (k & 3) * 4);
-}
-
 // Shared-memory matrix descriptor: start address >> 4 (bits 0..13), leading byte offset (bits
-// 16..29, not used by swizzled K-major layouts), stride byte offset >> 4 = 1024 B between 8-row
-// atoms (bits 32..45), descriptor version 1 (bits 46..47), base offset 0, 128-byte swizzle (= 2,
-// bits 61..63).
+// 16..29, not used by swizzled K-major layouts), stride byte offset >> 4 between 8-row atoms
+// (bits 32..45), descriptor version 1 (bits 46..47), base offset 0, layout type (bits 61..63).
+template <int KT>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
   d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)(Lay<KT>::SBO >> 4) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
+  d |= (uint64_t)Lay<KT>::MODE << 61;
   return d;
 }
 
@@ -147,14 +171,15 @@ __device__ __forceinline__ float kvalf_tc(float r2) {
 // p32: the points in FP32, n rounded up to a multiple of TK and zero padded (so that every
 // producer load of a chunk stays in bounds).  Columns [0, ncols0) read in0 / write out0, columns
 // [ncols0, ncols) read in1 / write out1 (column c - ncols0); all four are row-major with ld.
-template <int KIND, int D, int TN, int NST>
+template <int KIND, int D, int TN, int KT, int NST>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_kmv_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
              const float* __restrict__ p32, int64_t n, double shift, double scale, const double* __restrict__ in0,
              const double* __restrict__ in1, double* __restrict__ out0, double* __restrict__ out1, int64_t ld,
              int64_t ncols0, int64_t ncols, int* err) {
-  using C = Tile<TN, NST>;
-  constexpr int B_BYTES = C::B_BYTES, STAGE_BYTES = C::STAGE_BYTES;
+  using C = Tile<TN, KT, NST>;
+  constexpr int A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES, STAGE_BYTES = C::STAGE_BYTES;
+  constexpr int VPT = KT / 4;  // kernel values per producer thread and stage
   constexpr uint32_t TMEM_COLS = C::TMEM_COLS;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_a[NST], full_b[NST], empty[NST];
@@ -165,7 +190,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int64_t i0 = (int64_t)blockIdx.x * TM, c0 = (int64_t)blockIdx.y * TN;
   const int ntile = (int)(ncols - c0 < TN ? ncols - c0 : TN);
   const int nmma = (ntile + 15) & ~15;  // MMA N: a multiple of 16 in [16, TN]
-  const int64_t nchunk = (n + TK - 1) / TK;
+  const int64_t nchunk = (n + KT - 1) / KT;
 
   if (tid == 0) {
     s_timeout = 0;
@@ -193,16 +218,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp < NPROD / 32) {
     // ---- producers: kernel values of row arow, points akq..akq+7 of each chunk; the points of the
     // next chunk are loaded while this chunk's values are computed ----
-    const int arow = tid >> 2, akq = (tid & 3) * 8;
+    const int arow = tid >> 2, akq = (tid & 3) * VPT;
     const int64_t gi = i0 + arow;
+    const int gi32 = (int)gi;
     float pi[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) pi[k] = (gi < n) ? p32[gi * D + k] : 0.f;
-    float pj[8 * D], pn[8 * D];
+    float pj[VPT * D], pn[VPT * D];
     auto load_pts = [&](int64_t ch, float* dst) {
-      const float4* src = reinterpret_cast<const float4*>(p32 + (ch * TK + akq) * D);
+      const float4* src = reinterpret_cast<const float4*>(p32 + (ch * KT + akq) * D);
 #pragma unroll
-      for (int q = 0; q < 2 * D; ++q) {
+      for (int q = 0; q < VPT * D / 4; ++q) {
         const float4 v = __ldg(src + q);
         dst[4 * q] = v.x;
         dst[4 * q + 1] = v.y;
@@ -216,39 +242,49 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int64_t u = ch / NST;
       unsigned char* Ahi = smem + st * STAGE_BYTES;
       unsigned char* Alo = Ahi + A_BYTES;
-      const int64_t j0 = ch * TK + akq;
+      const int64_t j0 = ch * KT + akq;
       if (ch + 1 < nchunk) load_pts(ch + 1, pn);
       // the products of chunk ch - NST must be done with this stage
       if (ch >= NST && !bar_wait(smem_u32(&empty[st]), (uint32_t)((u - 1) & 1))) s_timeout = 1;
+      // K_ii = 0 and the zero padding beyond n only concern the chunks that overlap the row tile
+      // or hold the last points (block-uniform); rows beyond n are never stored, so their values
+      // need no check
+      const int64_t jc = ch * KT;
+      const bool check = (jc < i0 + TM && jc + KT > i0) || jc + KT > n;
+      auto gen = [&](auto check_tag) {
+        constexpr bool CHECK = decltype(check_tag)::value;
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        float hv[4], lv[4];
+        for (int q = 0; q < VPT / 4; ++q) {
+          float hv[4], lv[4];
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          const int kk = q * 4 + w;
-          const int64_t gj = j0 + kk;
-          float v = 0.f;
-          if (gi < n && gj < n && gi != gj) {
+          for (int w = 0; w < 4; ++w) {
+            const int kk = q * 4 + w;
             float r2 = 0.f;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
               const float dd = pi[k] - pj[kk * D + k];
               r2 = fmaf(dd, dd, r2);
             }
-            v = kvalf_tc<KIND>(r2);
+            float v = kvalf_tc<KIND>(r2);
+            if (CHECK) {
+              const int gj = (int)j0 + kk;
+              if (gj >= (int)n || gj == gi32) v = 0.f;
+            }
+            hv[w] = tf32_hi(v);
+            lv[w] = v - hv[w];
           }
-          hv[w] = tf32_hi(v);
-          lv[w] = v - hv[w];
+          const uint32_t off = Lay<KT>::off(arow, akq + q * 4);
+          *reinterpret_cast<float4*>(Ahi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+          *reinterpret_cast<float4*>(Alo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
         }
-        const uint32_t off = sw128(arow, akq + q * 4);
-        *reinterpret_cast<float4*>(Ahi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-        *reinterpret_cast<float4*>(Alo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
-      }
+      };
+      if (check) gen(std::true_type{});
+      else gen(std::false_type{});
       // generic-proxy writes must be visible to the tensor cores (async proxy)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       bar_arrive(smem_u32(&full_a[st]));
 #pragma unroll
-      for (int q = 0; q < 8 * D; ++q) pj[q] = pn[q];
+      for (int q = 0; q < VPT * D; ++q) pj[q] = pn[q];
     }
   } else if (lane == 0) {
     // ---- TMA + MMA issue ----
@@ -269,8 +305,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // barrier counts the bytes of both halves of both planes
       bar_expect_tx(bar, 2u * B_BYTES);
       const uint32_t half = crank * (B_BYTES / 2);
-      tma_load_2d_pair(smem_u32(Bhi) + half, &tm_hi, (int)(ch * TK), (int)(c0 + crank * (TN / 2)), bar);
-      tma_load_2d_pair(smem_u32(Bhi + B_BYTES) + half, &tm_lo, (int)(ch * TK), (int)(c0 + crank * (TN / 2)), bar);
+      tma_load_2d_pair(smem_u32(Bhi) + half, &tm_hi, (int)(ch * KT), (int)(c0 + crank * (TN / 2)), bar);
+      tma_load_2d_pair(smem_u32(Bhi + B_BYTES) + half, &tm_lo, (int)(ch * KT), (int)(c0 + crank * (TN / 2)), bar);
       armed[st] = true;
       armed_par[st] = (uint32_t)((ch / NST) & 1);
     };
@@ -286,11 +322,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const uint32_t a_hi = smem_u32(base), a_lo = a_hi + A_BYTES;
       const uint32_t b_hi = a_hi + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
 #pragma unroll
-      for (int kk = 0; kk < TK / 8; ++kk) {  // K = 8 TF32 values (32 bytes) per instruction
+      for (int kk = 0; kk < KT / 8; ++kk) {  // K = 8 TF32 values (32 bytes) per instruction
         const uint32_t ko = kk * 32;
-        mma_tf32(tmem, smem_desc(a_hi + ko), smem_desc(b_hi + ko), idesc, (ch > 0 || kk > 0) ? 1u : 0u);
-        mma_tf32(tmem, smem_desc(a_hi + ko), smem_desc(b_lo + ko), idesc, 1u);
-        mma_tf32(tmem, smem_desc(a_lo + ko), smem_desc(b_hi + ko), idesc, 1u);
+        mma_tf32(tmem, smem_desc<KT>(a_hi + ko), smem_desc<KT>(b_hi + ko), idesc, (ch > 0 || kk > 0) ? 1u : 0u);
+        mma_tf32(tmem, smem_desc<KT>(a_hi + ko), smem_desc<KT>(b_lo + ko), idesc, 1u);
+        mma_tf32(tmem, smem_desc<KT>(a_lo + ko), smem_desc<KT>(b_hi + ko), idesc, 1u);
       }
       mma_commit_pair(smem_u32(&empty[st]));
       const int64_t nxt = ch + NST - 1;
@@ -381,27 +417,32 @@ EncodeTiled encode_fn() {
 // Tensor map of one plane: ncols rows of n FP32 values, row pitch ldp values (ldp % 4 == 0 so that
 // the pitch is a multiple of 16 bytes); box = TK values x half a column tile (each CTA of a pair
 // loads one half), 128-byte swizzle, zero fill outside [0, n) x [0, ncols).
-bool plane_map(CUtensorMap* m, const float* base, int64_t n, int64_t ncols, int64_t ldp, int tn) {
+bool plane_map(CUtensorMap* m, const float* base, int64_t n, int64_t ncols, int64_t ldp, int tn, int kt,
+               CUtensorMapSwizzle swz) {
   EncodeTiled enc = encode_fn();
   if (!enc || (ldp & 3) || ((uintptr_t)base & 15)) return false;
   cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)ncols};
   cuuint64_t strides[1] = {(cuuint64_t)ldp * sizeof(float)};
-  cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)(tn / 2)};
+  cuuint32_t box[2] = {(cuuint32_t)kt, (cuuint32_t)(tn / 2)};
   cuuint32_t estr[2] = {1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int TN, int NST>
-void launch_variant(cudaStream_t st, int kind, const CUtensorMap& mh, const CUtensorMap& ml, const float* p32,
-                    int64_t n, double shift, double scale, const double* in0, const double* in1, double* out0,
-                    double* out1, int64_t ld, int64_t ncols0, int64_t ncols, int* err) {
-  constexpr int SMEM = Tile<TN, NST>::SMEM_BYTES;
+template <int TN, int KT, int NST>
+bool launch_variant(cudaStream_t st, int kind, const float* p32, int64_t n, double shift, double scale,
+                    const double* in0, const double* in1, double* out0, double* out1, int64_t ld, int64_t ncols0,
+                    int64_t ncols, const float* bhi, const float* blo, int64_t ldp, int* err) {
+  CUtensorMap mh, ml;
+  if (!plane_map(&mh, bhi, n, ncols, ldp, TN, KT, Lay<KT>::TMA_SWIZZLE) ||
+      !plane_map(&ml, blo, n, ncols, ldp, TN, KT, Lay<KT>::TMA_SWIZZLE))
+    return false;
+  constexpr int SMEM = Tile<TN, KT, NST>::SMEM_BYTES;
   static std::once_flag attr;
   std::call_once(attr, [] {
-    cudaFuncSetAttribute(k_kmv_tc<RSRS_OP_LOG2D, 2, TN, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-    cudaFuncSetAttribute(k_kmv_tc<RSRS_OP_INVR3D, 3, TN, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    cudaFuncSetAttribute(k_kmv_tc<RSRS_OP_LOG2D, 2, TN, KT, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    cudaFuncSetAttribute(k_kmv_tc<RSRS_OP_INVR3D, 3, TN, KT, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
   });
   // row tiles in pairs (one thread-block cluster each) that share the B tile of their column tile
   const unsigned gx = (unsigned)(((n + TM - 1) / TM + 1) / 2 * 2);
@@ -418,11 +459,12 @@ void launch_variant(cudaStream_t st, int kind, const CUtensorMap& mh, const CUte
   cfg.attrs = at;
   cfg.numAttrs = 1;
   if (kind == RSRS_OP_LOG2D)
-    cudaLaunchKernelEx(&cfg, k_kmv_tc<RSRS_OP_LOG2D, 2, TN, NST>, mh, ml, p32, n, shift, scale, in0, in1, out0, out1,
-                       ld, ncols0, ncols, err);
+    cudaLaunchKernelEx(&cfg, k_kmv_tc<RSRS_OP_LOG2D, 2, TN, KT, NST>, mh, ml, p32, n, shift, scale, in0, in1, out0,
+                       out1, ld, ncols0, ncols, err);
   else
-    cudaLaunchKernelEx(&cfg, k_kmv_tc<RSRS_OP_INVR3D, 3, TN, NST>, mh, ml, p32, n, shift, scale, in0, in1, out0, out1,
-                       ld, ncols0, ncols, err);
+    cudaLaunchKernelEx(&cfg, k_kmv_tc<RSRS_OP_INVR3D, 3, TN, KT, NST>, mh, ml, p32, n, shift, scale, in0, in1, out0,
+                       out1, ld, ncols0, ncols, err);
+  return true;
 }
 
 }  // namespace
@@ -436,34 +478,35 @@ void launch_points_f32(Launch L, const double* pts, int64_t n, int d, float* out
   if (L.counter) ++*L.counter;
 }
 
-int sample_tile_tn(int variant) {
-  switch (variant) {
-    case RSRS_SAMPLE_TILE_128x3: return 128;
-    case RSRS_SAMPLE_TILE_192x2: return 192;
-    default: return 256;
-  }
-}
-
 bool launch_kernel_matvec_tc(Launch L, int kind, const float* p32, int64_t n, double shift, double scale,
                              const double* in0, const double* in1, double* out0, double* out1, int64_t ld,
                              int64_t ncols0, int64_t ncols, const float* bhi, const float* blo, int64_t ldp, int* err,
                              int variant) {
   if (n <= 0 || ncols <= 0) return true;
-  const int tn = sample_tile_tn(variant);
-  CUtensorMap mh, ml;
-  if (!plane_map(&mh, bhi, n, ncols, ldp, tn) || !plane_map(&ml, blo, n, ncols, ldp, tn)) return false;
+  bool ok;
   switch (variant) {
     case RSRS_SAMPLE_TILE_128x3:
-      launch_variant<128, 3>(L.st, kind, mh, ml, p32, n, shift, scale, in0, in1, out0, out1, ld, ncols0, ncols, err);
+      ok = launch_variant<128, 32, 3>(L.st, kind, p32, n, shift, scale, in0, in1, out0, out1, ld, ncols0, ncols, bhi,
+                                      blo, ldp, err);
       break;
     case RSRS_SAMPLE_TILE_192x2:
-      launch_variant<192, 2>(L.st, kind, mh, ml, p32, n, shift, scale, in0, in1, out0, out1, ld, ncols0, ncols, err);
+      ok = launch_variant<192, 32, 2>(L.st, kind, p32, n, shift, scale, in0, in1, out0, out1, ld, ncols0, ncols, bhi,
+                                      blo, ldp, err);
       break;
-    default:
-      launch_variant<256, 2>(L.st, kind, mh, ml, p32, n, shift, scale, in0, in1, out0, out1, ld, ncols0, ncols, err);
+    case RSRS_SAMPLE_TILE_256x2:
+      ok = launch_variant<256, 32, 2>(L.st, kind, p32, n, shift, scale, in0, in1, out0, out1, ld, ncols0, ncols, bhi,
+                                      blo, ldp, err);
+      break;
+    case RSRS_SAMPLE_TILE_192x5_K16:
+      ok = launch_variant<192, 16, 5>(L.st, kind, p32, n, shift, scale, in0, in1, out0, out1, ld, ncols0, ncols, bhi,
+                                      blo, ldp, err);
+      break;
+    default:  // RSRS_SAMPLE_TILE_256x4_K16: four stages keep the B-tile copies two products ahead
+      ok = launch_variant<256, 16, 4>(L.st, kind, p32, n, shift, scale, in0, in1, out0, out1, ld, ncols0, ncols, bhi,
+                                      blo, ldp, err);
   }
-  if (L.counter) ++*L.counter;
-  return true;
+  if (ok && L.counter) ++*L.counter;
+  return ok;
 }
 
 }  // namespace rsrs

@@ -37,6 +37,7 @@ class Operator(C.Structure):
 
 
 RSRS_SAMPLE_TILE_DEFAULT, RSRS_SAMPLE_TILE_256x2, RSRS_SAMPLE_TILE_128x3, RSRS_SAMPLE_TILE_192x2 = 0, 1, 2, 3
+RSRS_SAMPLE_TILE_256x4_K16, RSRS_SAMPLE_TILE_192x5_K16 = 4, 5
 
 
 class Tune(C.Structure):
