@@ -178,7 +178,8 @@ void launch_ef_update(Launch L, const GroupArgs& g, int64_t items);             
 void launch_extract(Launch L, const GroupArgs& g, int64_t items);                  // X blocks
 void launch_lu(Launch L, const GroupArgs& g);                                      // LU(X_RR)
 void launch_lu_rhs(Launch L, const GroupArgs& g, int64_t items);                   // Lc, Uc
-void launch_schur(Launch L, const GroupArgs& g, int64_t items);                    // L, U on sketches
+// L, U on the sketches; the mixed path first makes FP32 copies of LcT, Uc, Y_R, Z_R (prep_items blocks)
+void launch_schur(Launch L, const GroupArgs& g, int64_t items, int64_t prep_items);
 
 // Number of 64-row x 64-col tiles for the group kernels (host-side planning).
 constexpr int kT = 64;
@@ -227,6 +228,7 @@ int64_t items_ef(const std::vector<BoxDesc>& h, int64_t s);
 int64_t items_extract(const std::vector<BoxDesc>& h);
 int64_t items_lu_rhs(const std::vector<BoxDesc>& h);
 int64_t items_schur(const std::vector<BoxDesc>& h, int64_t s);
+int64_t items_schur_prep(const std::vector<BoxDesc>& h, int64_t s);
 int64_t items_sweep(const std::vector<BoxDesc>& h, int cset);
 int64_t items_diag(const std::vector<BoxDesc>& h, int nrhs);
 

@@ -970,9 +970,13 @@ __global__ void __launch_bounds__(1024, 1) k_cpqr32_cluster(GroupArgs g, int cs,
   __shared__ double s_r00;
   __shared__ float s_vj, s_f2;
   __shared__ int s_j0;
-  const double tau = fmax(1e-10, 64.0 * DBL_EPSILON * (double)max(b, (int)c));
-  const double floor_abs = tau * id_scale(g.work + d.sn_off, b);
-  const double floor2 = floor_abs * floor_abs, tau2 = tau * tau;
+  __shared__ double s_floor2, s_tau2;
+  if (threadIdx.x == 0) {  // FP64 work once per CTA, not per thread (the FP64 pipe is narrow)
+    const double tau = fmax(1e-10, 64.0 * DBL_EPSILON * (double)max(b, (int)c));
+    const double floor_abs = tau * id_scale(g.work + d.sn_off, b);
+    s_floor2 = floor_abs * floor_abs;
+    s_tau2 = tau * tau;
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int wid = (int)(t_hi - t_lo);
   // a warp-reduced partial sum of row pos goes to slot `rank` of every CTA's buffer (lane q -> CTA q)
@@ -1054,6 +1058,7 @@ __global__ void __launch_bounds__(1024, 1) k_cpqr32_cluster(GroupArgs g, int cs,
       }
     }
     if (threadIdx.x == 0) {
+      const double floor2 = s_floor2, tau2 = s_tau2;
       int p0 = bp;
       const double dv0 = p0 >= 0 ? __longlong_as_double((long long)bv) : 0.0;
       if (p0 < 0 || !isfinite(dv0)) {
@@ -1088,10 +1093,13 @@ __global__ void __launch_bounds__(1024, 1) k_cpqr32_cluster(GroupArgs g, int cs,
     const int t0 = (int)(imax64(t_lo, j) - t_lo);  // first local column of the reflector
     const int tj = (int)(j - t_lo);                 // local index of column j (in range for its owner)
     // partial dot products of the remaining rows with v over this CTA's columns
+    // column j (in its owner CTA only, where t0 == tj) uses v_j; the other columns x itself
+    const bool own_j = (tj >= 0 && tj < wid);  // this CTA holds column j (then t0 == tj)
+    const int t1 = own_j ? t0 + 1 : t0;
     for (int pos = j + 1 + warp; pos < b; pos += nw) {
       const float* row = S + (int64_t)rid[pos] * lds;
-      float w = 0.f;
-      for (int t = t0 + lane; t < wid; t += 32) w = fmaf(row[t], t == tj ? vj : xs[t], w);
+      float w = (own_j && lane == 0) ? row[tj] * vj : 0.f;
+      for (int t = t1 + lane; t < wid; t += 32) w = fmaf(row[t], xs[t], w);
       for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
       push(wbuf, pos, w);
     }
@@ -1101,12 +1109,16 @@ __global__ void __launch_bounds__(1024, 1) k_cpqr32_cluster(GroupArgs g, int cs,
     for (int pos = j + 1 + warp; pos < b; pos += nw) {
       const float f = fvec[pos];
       float* row = S + (int64_t)rid[pos] * lds;
+      if (own_j && lane == 0) {  // R[j][pos], written by the CTA that owns column j
+        const float v = fmaf(-f, vj, row[tj]);
+        row[tj] = v;
+        Rp[(int64_t)j * b + rid[pos]] = (double)v;
+      }
       float nn = 0.f;
-      for (int t = t0 + lane; t < wid; t += 32) {
-        const float v = fmaf(-f, t == tj ? vj : xs[t], row[t]);
+      for (int t = t1 + lane; t < wid; t += 32) {
+        const float v = fmaf(-f, xs[t], row[t]);
         row[t] = v;
-        if (t > tj) nn = fmaf(v, v, nn);
-        else Rp[(int64_t)j * b + rid[pos]] = (double)v;  // t == j lives in exactly one CTA
+        nn = fmaf(v, v, nn);
       }
       for (int o = 16; o; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
       push(nbuf, pos, nn);
@@ -1468,6 +1480,72 @@ __global__ void __launch_bounds__(NT) k_schur(GroupArgs g) {
     row_tile -= 2 * tw + tr;
     tile_acc<CT>(1.0, MatA{LcT, w, false}, d.r, w, Rows{g.Ps, g.s, SN}, 0, RowsW{g.Ps, g.s, Rl}, 0, g.s,
              row_tile * TB, tt * TB);
+  }
+}
+
+// Mixed path: FP32 copies of the Schur products' reused operands, made once per group (FP64 ->
+// FP32 conversions run at the FP64 rate on this part, and a tile product converts every operand
+// element it loads, i.e. once per tile that reads it): LcT and Uc (r x (k'+n) each) into the box's
+// extraction workspace, Y_R and Z_R (r x s each) into its sketch workspace (both free after the
+// extraction and the CPQR).
+struct CntSchurPrep {
+  int64_t s;
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const {
+    return cdv(2 * (int64_t)d.r * ((int64_t)d.kp + d.n) + 2 * (int64_t)d.r * s, 256);
+  }
+};
+__global__ void __launch_bounds__(256) k_schur_prep(GroupArgs g) {
+  int64_t loc;
+  int bi = find_item(g.desc, g.nbox, blockIdx.x, CntSchurPrep{g.s}, loc);
+  if (bi < 0) return;
+  const BoxDesc d = g.desc[bi];
+  const int64_t w = (int64_t)d.kp + d.n, rw = (int64_t)d.r * w, rs = (int64_t)d.r * g.s;
+  int64_t e = loc * 256 + threadIdx.x;
+  float* wc = reinterpret_cast<float*>(g.workc);
+  if (e < 2 * rw) {
+    const double* src = g.fd + (e < rw ? fd_LcT(d) : fd_Uc(d));
+    wc[d.e_off + e] = (float)src[e < rw ? e : e - rw];
+    return;
+  }
+  e -= 2 * rw;
+  if (e >= 2 * rs) return;
+  const int side = (int)(e / rs);
+  const int64_t i = (e % rs) / g.s, t = (e % rs) % g.s;
+  const int32_t* Rl = g.fi + fi_R(d);
+  const double* src = side == 0 ? g.Y : g.Z;
+  wc[d.mc_off + e] = (float)src[(int64_t)Rl[i] * g.s + t];
+}
+__global__ void __launch_bounds__(NT) k_schur32(GroupArgs g) {
+  int64_t loc;
+  int bi = find_item(g.desc, g.nbox, blockIdx.x, CntSchur{g.s}, loc);
+  if (bi < 0) return;
+  const BoxDesc d = g.desc[bi];
+  const int64_t nt = cdv(g.s, TB);
+  const int64_t w = (int64_t)d.kp + d.n;
+  const int64_t tw = cdv(w, TB), tr = cdv(d.r, TB);
+  int64_t row_tile = loc / nt, tt = loc % nt;
+  const int32_t* Rl = g.fi + fi_R(d);
+  const int32_t* SN = g.fi + fi_S(d);
+  const float* wc = reinterpret_cast<const float*>(g.workc);
+  const float* LcT = wc + d.e_off;
+  const float* Uc = LcT + (int64_t)d.r * w;
+  const float* YR = wc + d.mc_off;
+  const float* ZR = YR + (int64_t)d.r * g.s;
+  if (row_tile < tw) {
+    tile_acc<float>(-1.0, MatAT<float>{LcT, w, true}, w, d.r, RowsT<float>{YR, g.s, nullptr}, 0,
+                    RowsW{g.Y, g.s, SN}, 0, g.s, row_tile * TB, tt * TB);
+  } else if (row_tile < tw + tr) {
+    row_tile -= tw;
+    tile_acc<float>(1.0, MatAT<float>{Uc, w, false}, d.r, w, Rows{g.Om, g.s, SN}, 0, RowsW{g.Om, g.s, Rl}, 0, g.s,
+                    row_tile * TB, tt * TB);
+  } else if (row_tile < 2 * tw + tr) {
+    row_tile -= tw + tr;
+    tile_acc<float>(-1.0, MatAT<float>{Uc, w, true}, w, d.r, RowsT<float>{ZR, g.s, nullptr}, 0,
+                    RowsW{g.Z, g.s, SN}, 0, g.s, row_tile * TB, tt * TB);
+  } else {
+    row_tile -= 2 * tw + tr;
+    tile_acc<float>(1.0, MatAT<float>{LcT, w, false}, d.r, w, Rows{g.Ps, g.s, SN}, 0, RowsW{g.Ps, g.s, Rl}, 0, g.s,
+                    row_tile * TB, tt * TB);
   }
 }
 
@@ -1846,10 +1924,17 @@ void launch_lu_rhs(Launch L, const GroupArgs& g, int64_t items) {
   k_lu_rhs<<<grid1(items), CW, 0, L.st>>>(g);
   count_launch(L);
 }
-void launch_schur(Launch L, const GroupArgs& g, int64_t items) {
+void launch_schur(Launch L, const GroupArgs& g, int64_t items, int64_t prep_items) {
   if (items <= 0) return;
-  if (g.fp32) k_schur<float><<<grid1(items), NT, 0, L.st>>>(g);
-  else k_schur<double><<<grid1(items), NT, 0, L.st>>>(g);
+  if (g.fp32) {
+    if (prep_items > 0) {
+      k_schur_prep<<<grid1(prep_items), 256, 0, L.st>>>(g);
+      count_launch(L);
+    }
+    k_schur32<<<grid1(items), NT, 0, L.st>>>(g);
+  } else {
+    k_schur<double><<<grid1(items), NT, 0, L.st>>>(g);
+  }
   count_launch(L);
 }
 void launch_dense_lu(Launch L, double* A, int64_t n, int32_t* piv, int* err) {
@@ -1904,5 +1989,6 @@ int64_t items_ef(const std::vector<BoxDesc>& h, int64_t s) { return items_of<voi
 int64_t items_extract(const std::vector<BoxDesc>& h) { return items_of<void>(h, CntExtract()); }
 int64_t items_lu_rhs(const std::vector<BoxDesc>& h) { return items_of<void>(h, CntLuRhs()); }
 int64_t items_schur(const std::vector<BoxDesc>& h, int64_t s) { return items_of<void>(h, CntSchur{s}); }
+int64_t items_schur_prep(const std::vector<BoxDesc>& h, int64_t s) { return items_of<void>(h, CntSchurPrep{s}); }
 
 }  // namespace rsrs

@@ -975,7 +975,7 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
       timed(RSRS_K_EXTRACT, [&] { launch_extract(L, ga, items_extract(g.h)); });
       timed(RSRS_K_LU, [&] { launch_lu(L, ga); });
       timed(RSRS_K_LU_RHS, [&] { launch_lu_rhs(L, ga, items_lu_rhs(g.h)); });
-      timed(RSRS_K_SCHUR, [&] { launch_schur(L, ga, items_schur(g.h, s)); });
+      timed(RSRS_K_SCHUR, [&] { launch_schur(L, ga, items_schur(g.h, s), items_schur_prep(g.h, s)); });
     }
     CU(cudaGetLastError());
   }

@@ -86,3 +86,22 @@ def test_mixed_tensor_core_products(R, name):
         assert np.linalg.norm(X.cpu().numpy().T - xd) / np.linalg.norm(xd) < 1e-11
         its[mg] = rep.iterations
     assert abs(its[0] - its[1]) <= 1
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_mixed_solve_apply_inverse_pair(R, name):
+    """The mixed factor's sweeps run in float-float arithmetic on its FP64 blocks: its solve and apply
+    are exact inverses of each other to FP64-level rounding (adjoints too), and the solve agrees
+    with the FP64 refinement target to the factor's own accuracy."""
+    pr = CASES[name]()
+    tree = R.Tree(pr.points, pr.leaf)
+    s = max(pr.s_cfg, tree.info(pr.k).s_req_mixed)
+    f = R.Factor(tree, R.kind_of(pr.kernel), pr.k, s, shift=pr.diag_shift, scale=pr.scale,
+                 precision=R.RSRS_PREC_MIXED, seed=23)
+    b = pr.rhs()
+    for adj in (False, True):
+        y = f.apply(f.solve(_to_gpu(b), adjoint=adj), adjoint=adj).cpu().numpy().T
+        assert np.linalg.norm(y - b) / np.linalg.norm(b) < 1e-12, adj
+    xd = np.linalg.solve(ops.make_operator(pr).dense(), b)
+    x0 = f.solve(_to_gpu(b)).cpu().numpy().T
+    assert np.linalg.norm(x0 - xd) / np.linalg.norm(xd) < 1e-2
