@@ -214,6 +214,22 @@ __global__ void k_gauss_tree(const uint64_t* seed_dev, uint64_t add, uint32_t st
   normal_pair(seed, stream, (uint64_t)(g >> 1), z0, z1);
   out[e] = (g & 1) ? z1 : z0;
 }
+// The same for even s, one thread per pair: draws g and g + 1 (g even) are columns c and c + 1 of
+// one original row, so each Box-Muller pair (FP64 log, square root, sine and cosine, at the FP64
+// rate on this part) is evaluated once and both members stored.
+__global__ void k_gauss_tree_pairs(const uint64_t* seed_dev, uint64_t add, uint32_t stream, const int32_t* perm,
+                                   int64_t n, int64_t s, double* out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // pair index in tree order
+  const int64_t hs = s >> 1;
+  if (e >= n * hs) return;
+  const uint64_t seed = *seed_dev + add;
+  const int64_t t = e / hs, c = 2 * (e % hs);
+  const int64_t g = (int64_t)perm[t] * s + c;
+  double z0, z1;
+  normal_pair(seed, stream, (uint64_t)(g >> 1), z0, z1);
+  out[t * s + c] = z0;
+  out[t * s + c + 1] = z1;
+}
 
 const char* kClassNames[RSRS_NCLASS] = {"sample", "lists", "gram", "chol", "gather", "proj_nt", "proj_solve",
                                         "proj_acc", "cpqr", "id_finish", "ef_update", "extract", "lu", "lu_rhs",
@@ -829,7 +845,11 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
       } else if (dsrc) {
         k_gather_orig<<<nblk(ns), 256, 0, st>>>(dsrc, F[p]->perm_dev, n, s, dst);
       } else {
-        k_gauss_tree<<<nblk(ns), 256, 0, st>>>(seed_dev, (uint64_t)p, (uint32_t)side, F[p]->perm_dev, n, s, dst);
+        if ((s & 1) == 0)
+          k_gauss_tree_pairs<<<nblk(ns / 2), 256, 0, st>>>(seed_dev, (uint64_t)p, (uint32_t)side, F[p]->perm_dev, n,
+                                                           s, dst);
+        else
+          k_gauss_tree<<<nblk(ns), 256, 0, st>>>(seed_dev, (uint64_t)p, (uint32_t)side, F[p]->perm_dev, n, s, dst);
       }
       CU(cudaGetLastError());
     }

@@ -47,3 +47,18 @@ def test_mixed_sampling_matches_fp64(R, d, kind, n, s, kernel):
     for a, b in zip(out[R.RSRS_PREC_MIXED], out[R.RSRS_PREC_FP64]):
         err = np.abs(a - b).max() / np.abs(b).max()
         assert err < 1e-5, err
+
+
+@pytest.mark.parametrize("n,s", [(300, 320), (257, 301)])
+def test_device_draws_match_counter_generator(R, n, s):
+    """Omega and Psi drawn on the device (Philox4x32-10 + Box-Muller; one thread per pair when s is
+    even, per entry when odd) equal workloads.philox_gaussian entry by entry, up to the last-bit
+    differences of the FP64 log / sine / cosine of the two math libraries."""
+    pts = W.uniform_points(n, 2, W.rng_for(97, n, 3))
+    t = R.Tree(pts, 4096)
+    f = R.Factor(t, R.RSRS_OP_LOG2D, 8, s, shift=1.0, scale=1.0 / n, seed=77, keep_sketches=True)
+    _, _, Om, Ps = f.sketches()
+    for got, stream in ((Om, 0), (Ps, 1)):
+        ref = W.philox_gaussian(n, s, 77, stream)
+        assert got.shape == ref.shape
+        assert np.abs(got - ref).max() <= 1e-14 * np.abs(ref).max()
