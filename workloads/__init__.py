@@ -106,6 +106,24 @@ def kernel_problem(cfg: int, name: str, points: np.ndarray, kernel: str, leaf: i
                    diag_shift=1.0, scale=1.0 / n)
 
 
+def cell_log_mean(h: float) -> float:
+    """Mean of log|x| over the square cell [-h/2, h/2]^2: log(h/sqrt(2)) - 3/2 + pi/4 (from
+    int_0^a int_0^a log(x^2 + y^2) dx dy = a^2 (log(2 a^2) - 3 + pi/2) with a = h/2)."""
+    return float(np.log(h / np.sqrt(2.0)) - 1.5 + np.pi / 4.0)
+
+
+def exp1_problem(n_side: int = 284, k: int = 40, nrhs: int = 1) -> Problem:
+    """The matrix of the paper's Experiment 1 (Sec. 6.1, eq. Aentries_exp1): collocation points on
+    the uniform n_side x n_side grid of the unit square (cell centres), A_ij = log|x_i - x_j| / N for
+    i != j and A_ii = the integral of log|x| over the point's cell (h^2 = 1/N times the cell mean),
+    leaf m = 4k (c_cap = 4) and n_samples = s of the sample bound (1520 at N = 80,656, k = 40)."""
+    pts = grid_points_2d(n_side)
+    n = pts.shape[0]
+    h = 1.0 / n_side
+    return Problem(name=f"exp1_grid{n_side}_k{k}", cfg=91, problem=0, d=2, kernel="log2d", points=pts,
+                   leaf=4 * k, k=k, s_cfg=0, nrhs=nrhs, diag_shift=cell_log_mean(h) / n, scale=1.0 / n)
+
+
 def config(idx: int) -> list[Problem]:
     """The five named workloads (0-based), each a list of problems.
 
