@@ -322,6 +322,15 @@ def run_gpu(args):
     t_sol = time.perf_counter() - a0
     line["solves_per_s_refined"] = pr.nrhs / t_ref
     line["solves_per_s_unrefined"] = pr.nrhs / t_sol
+    # GMRES with the same factor as preconditioner (the paper's solver), to 1e-10 as in its tables
+    Xg = torch.zeros_like(B)
+    torch.cuda.synchronize()
+    a0 = time.perf_counter()
+    gm = f.gmres(B, Xg, rtol=1e-10, restart=30, maxit=30)
+    torch.cuda.synchronize()
+    t_gm = time.perf_counter() - a0
+    line["gmres"] = {"rtol": 1e-10, "iterations": gm.iterations, "rel_residual": gm.rel_residual,
+                     "solves_per_s": pr.nrhs / t_gm}
     del f
     if not args.no_compare and rank == 0:
         a0 = time.perf_counter()
