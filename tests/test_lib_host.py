@@ -111,3 +111,13 @@ def test_autotune_cache_hit_needs_no_device(R, tmp_path):
     tune, rep = R.autotune(t, R.RSRS_OP_LOG2D, 32, s, 1.0, 1 / 4096, cache=str(cache))
     assert rep["from_cache"] and rep["candidates"] == 0
     assert tune == {"sample_tile": 2, "cpqr_cluster": 4, "cpqr_threads": 512, "residual_split": 8}
+
+
+def test_autotune_validates_before_device_work(R):
+    t = R.Tree(W.grid_points_2d(64), 64)
+    s = t.info(32).s_req_mixed
+    with pytest.raises(R.RSRSError) as e:
+        R.autotune(t, R.RSRS_OP_LOG2D, 32, s, 1.0, 1 / 4096, tune={"cpqr_threads": 7})
+    assert e.value.name == "RSRS_E_INVAL"
+    lib = R.lib()
+    assert lib.rsrs_autotune(1, None, None, 32, s, None, 1, None, None, None, None) == 1
