@@ -1,6 +1,8 @@
-// Grouped 3xTF32 products on the tensor cores for the mixed path's FP32 workspace: the near-field
-// Grams G = W W^T (a2), the least-squares right-hand sides X = M W^T and the projection updates
-// M -= X W (a3), for every box of a (level, colour) group in one launch.
+// Grouped 3xTF32 products on the tensor cores for the mixed path's FP32 workspace, for every box
+// of a (level, colour) group in one launch: the near-field Grams G = W W^T, their blocked
+// Cholesky factors and U = L^-T (with the diagonal-block kernel below), the least-squares
+// right-hand sides X = M W^T, the solves X G^-1 = (X U) U^T and the projection updates M -= X W of
+// the nullification (Algorithm 1, the null-space projection of the sketches).
 //
 // One CTA computes a 128 x 128 tile of D = A B^T (A rows and B rows both K-contiguous) or
 // D = A B (B stored K x N, N contiguous), with D <- alpha D_acc + beta D on store.  Eight producer
