@@ -189,9 +189,39 @@ def _cpu_baseline(pr, s: int, budget_s: float = 20.0) -> dict:
             "est_factor_s": t_sample + t_factor}
 
 
+def _rank_env():
+    """(world size, rank, local rank) from the launcher's environment; torchrun sets all three."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def _barrier():
+    """Barrier over the ranks of the process group, when one is initialised (N > 1)."""
+    import torch.distributed as dist
+
+    if dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+def _job_time(ms, units, device):
+    """Whole-job time and work over the ranks.  Every rank runs its own replica of the path with
+    no exchange between them, so the job takes the slowest rank's time (MAX) and has processed
+    every rank's units (SUM).  Without a process group (one GPU) both pass through unchanged."""
+    import torch
+    import torch.distributed as dist
+
+    if not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms, units
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(u.item()))
+
+
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    _, rank, _ = _rank_env()
+    if rank != 0:  # the CPU oracle runs once, on rank 0; the other ranks exit without work
         return
     pr = _problem(args.workload, args.n)
     from oracle.tree import Schedule as OSched
@@ -222,12 +252,10 @@ def run_gpu(args):
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
+    world, rank, local = _rank_env()
     torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import __graft_entry__
 
     __graft_entry__.build()
@@ -258,8 +286,7 @@ def run_gpu(args):
     for w in range(args.warmup):
         step(1000 + w)
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    _barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     reps, sts, clss = [], [], []
@@ -273,12 +300,8 @@ def run_gpu(args):
             clss.append(cls)
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    total_rhs = pr.nrhs * args.steps * world
+        _barrier()
+    ms, total_rhs = _job_time(e0.elapsed_time(e1), pr.nrhs * args.steps, "cuda")
     value = total_rhs / (ms / 1e3)
     x_mixed = X.clone()
 
@@ -379,7 +402,12 @@ def run_gpu_batched(args):
     rsrs_build_batched (one launch per (height, colour) group across problems, batched roots), then
     each problem's right-hand sides refined to RTOL.  value = all problems' RHS per step / time."""
     import torch
+    import torch.distributed as dist
 
+    world, rank, local = _rank_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import __graft_entry__
 
     __graft_entry__.build()
@@ -411,17 +439,18 @@ def run_gpu_batched(args):
     for w in range(args.warmup):
         step(2000 + w)
     torch.cuda.synchronize()
+    _barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     res = []
-    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+    with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         e0.record(stream)
         for i in range(args.steps):
-            res.append(step(3000 + i, profile=True))
+            res.append(step(3000 + rank * 100003 + i, profile=True))
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    nrhs = sum(p.nrhs for p in prs)
+        _barrier()
+    ms, total_rhs = _job_time(e0.elapsed_time(e1), sum(p.nrhs for p in prs) * args.steps, "cuda")
     clss = [r[2] for r in res]
     names = list(clss[0].keys())
     avg = {nm: (sum(c[nm][0] for c in clss) / len(clss), clss[0][nm][1], clss[0][nm][2]) for nm in names}
@@ -431,8 +460,8 @@ def run_gpu_batched(args):
     achieved = dom_gflop / dom_ms if dom_ms > 0 else 0.0
     st = res[0][1]
     line = {
-        "metric": METRIC, "value": nrhs * args.steps / (ms / 1e3), "unit": "RHS/s (factor + refined solve, per step)",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "metric": METRIC, "value": total_rhs / (ms / 1e3), "unit": "RHS/s (factor + refined solve, per step)",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64 (mixed)" if prec == R.RSRS_PREC_MIXED else "f64",
         "data": "synthetic (seeded uniform points, device Philox test matrices, Gaussian RHS)",
@@ -450,7 +479,10 @@ def run_gpu_batched(args):
         "clocks": clk.summary(),
         "autotune": tune_info,
     }
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def _autotune(args, R, trees, kinds, k, s, shifts, scales, prec):
