@@ -361,6 +361,16 @@ const char* rsrs_status_string(rsrs_status st);
 /* Message of the last failed call on this thread (empty string if none). */
 const char* rsrs_last_error(void);
 
+/* Failure-detection self-test (no counterpart in the paper).  Every wait of the tensor-core kernels
+ * on an mbarrier is bounded: after a fixed number of polls it records a timeout in the device
+ * status word, the kernel releases what it holds and returns, and the call reports
+ * RSRS_E_TIMEOUT with the context still usable.  This launches one CTA that initialises an
+ * mbarrier expecting one arrival, makes that arrival only when arrive = 1, and waits for it
+ * through the same bounded wait with at most `polls` polls (1..2^26).  Returns RSRS_E_TIMEOUT
+ * when the wait expired (always, for arrive = 0), RSRS_OK when it completed, RSRS_E_INVAL for
+ * arguments out of range.  Synchronises `stream`; allocates and frees one device int. */
+rsrs_status rsrs_wait_selftest(int64_t polls, int arrive, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -157,6 +157,10 @@ void launch_proj_acc_tc(Launch L, const GroupArgs& g, int pass, const std::vecto
 // result into the pass-0 coefficients).
 void launch_chol_tc(Launch L, const GroupArgs& g, const std::vector<BoxDesc>& h);
 void launch_solve_tc(Launch L, const GroupArgs& g, int pass, const std::vector<BoxDesc>& h);
+// One CTA waits, through the tcgen05 kernels' bounded mbarrier wait, for a barrier that receives
+// its arrival only when `arrive` is set; at most `polls` polls (clamped to 1..2^26).  An expired
+// wait records kDevTimeout in *err (device int) and the kernel returns.
+void launch_wait_selftest(Launch L, long long polls, int arrive, int* err);
 
 // Root blocks of a build: LU with partial pivoting in place in A (LAPACK interchange record in
 // piv) and the explicit inverse in inv, all problems at once, FP64.

@@ -682,7 +682,27 @@ int64_t items_of_h(const std::vector<BoxDesc>& h, Count c) {
   return n;
 }
 
+// Self-test of the bounded mbarrier wait every kernel here uses: one CTA initialises a barrier
+// that expects one arrival, makes that arrival only when `arrive` is set, and waits for the phase
+// with at most `polls` polls.  With no arrival the wait must expire and record kDevTimeout; the
+// kernel then returns normally, so the context stays usable.
+__global__ void __launch_bounds__(32) k_wait_selftest(long long polls, int arrive, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t b = tc::smem_u32(&bar);
+  if (threadIdx.x == 0) tc::bar_init(b, 1);
+  __syncthreads();
+  if (threadIdx.x == 0 && arrive) tc::bar_arrive(b);
+  __syncthreads();
+  if (threadIdx.x == 0 && !tc::bar_wait(b, 0, polls)) atomicCAS(err, 0, (int)kDevTimeout);
+}
+
 }  // namespace
+
+void launch_wait_selftest(Launch L, long long polls, int arrive, int* err) {
+  polls = std::min(std::max(polls, 1ll), tc::kWaitLimit);
+  k_wait_selftest<<<1, 32, 0, L.st>>>(polls, arrive, err);
+  if (L.counter) ++*L.counter;
+}
 
 void launch_gram_tc(Launch L, const GroupArgs& g, const std::vector<BoxDesc>& h) {
   launch_job(L, g, GramJob{g.s}, items_of_h(h, [](const BoxDesc& d) { return 2 * tri_n(cdiv128(d.l)); }));

@@ -2011,3 +2011,21 @@ extern "C" rsrs_status rsrs_solve_noalloc(const rsrs_factor* f, double* F, int64
   CU(cudaGetLastError());
   return RSRS_OK;
 }
+
+extern "C" rsrs_status rsrs_wait_selftest(int64_t polls, int arrive, void* stream) {
+  if (polls <= 0 || polls > ((int64_t)1 << 26) || (arrive != 0 && arrive != 1))
+    return fail(RSRS_E_INVAL, "wait_selftest: polls outside 1..2^26 or arrive not 0/1");
+  cudaStream_t st = (cudaStream_t)stream;
+  DevPool pool;
+  int* err = nullptr;
+  CU(pool.alloc(&err, 1));
+  CU(cudaMemsetAsync(err, 0, sizeof(int), st));
+  launch_wait_selftest(Launch{st, nullptr}, (long long)polls, arrive, err);
+  CU(cudaGetLastError());
+  int herr = 0;
+  CU(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (herr == kDevTimeout) return fail(RSRS_E_TIMEOUT, "wait_selftest: the bounded wait expired");
+  if (herr != 0) return fail(RSRS_E_CUDA, "wait_selftest: unexpected device status " + std::to_string(herr));
+  return RSRS_OK;
+}

@@ -72,9 +72,10 @@ __device__ __forceinline__ void bar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-// Bounded wait for the completion of the mbarrier phase with the given parity; false on expiry.
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
-  for (long long it = 0; it < kWaitLimit; ++it) {
+// Bounded wait for the completion of the mbarrier phase with the given parity: at most `limit`
+// polls; false on expiry.
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, long long limit = kWaitLimit) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"

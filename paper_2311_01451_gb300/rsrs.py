@@ -23,7 +23,7 @@ STATUS = {0: "RSRS_OK", 1: "RSRS_E_INVAL", 2: "RSRS_E_UNDERSAMPLED", 3: "RSRS_E_
           8: "RSRS_E_TIMEOUT", 9: "RSRS_E_NOT_CONVERGED"}
 
 EXPORTS = ["rsrs_tree_build", "rsrs_tree_info", "rsrs_tree_perm", "rsrs_tree_schedule", "rsrs_tree_free",
-           "rsrs_build", "rsrs_build_batched", "rsrs_refactor", "rsrs_solve", "rsrs_solve_noalloc", "rsrs_apply", "rsrs_refine", "rsrs_residual", "rsrs_matvec", "rsrs_factor_stats",
+           "rsrs_build", "rsrs_build_batched", "rsrs_refactor", "rsrs_solve", "rsrs_solve_noalloc", "rsrs_wait_selftest", "rsrs_apply", "rsrs_refine", "rsrs_residual", "rsrs_matvec", "rsrs_factor_stats",
            "rsrs_factor_box", "rsrs_factor_root", "rsrs_factor_sketches", "rsrs_factor_free",
            "rsrs_status_string", "rsrs_last_error", "rsrs_kernel_class_name", "rsrs_stencil7_create", "rsrs_stencil7_matvec", "rsrs_stencil7_free", "rsrs_autotune", "rsrs_gmres"]
 
@@ -135,6 +135,7 @@ def lib():
             "rsrs_stencil7_matvec": [vp, C.c_int, i64, i32, vp, i64, vp, i64, vp],
             "rsrs_autotune": [C.c_int, C.POINTER(vp), C.POINTER(Operator), C.c_int, C.c_int, C.POINTER(Options),
                               C.c_int, C.c_char_p, vp, C.POINTER(Tune), C.POINTER(TuneReport)],
+            "rsrs_wait_selftest": [i64, C.c_int, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -154,6 +155,13 @@ def lib():
         L.rsrs_last_error.restype = C.c_char_p
         _lib = L
     return _lib
+
+
+def wait_selftest(polls: int, arrive: bool, stream=None):
+    """rsrs_wait_selftest: one CTA waits, through the kernels' bounded mbarrier wait (at most
+    ``polls`` polls), for an arrival made only when ``arrive`` is true.  Raises RSRSError
+    (RSRS_E_TIMEOUT) when the wait expired; returns None when it completed."""
+    _check(lib().rsrs_wait_selftest(int(polls), int(bool(arrive)), _stream_ptr(stream)))
 
 
 class RSRSError(RuntimeError):
