@@ -821,8 +821,8 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(GroupArgs g) {
   double* wpart = csm + b;      // b, this CTA's partial dot products
   double* npart = csm + 2 * b;  // b, this CTA's partial norms
   int* rid = (int*)(csm + 3 * b);
-  __shared__ double s_alpha, s_x0, s_vn2, s_r00;
-  __shared__ int s_j0, s_p;
+  __shared__ double s_x0, s_vn2, s_r00;
+  __shared__ int s_j0;
   const double tau = fmax(1e-10, 64.0 * DBL_EPSILON * (double)max(b, (int)c));
   const double floor_abs = tau * id_scale(g.work + d.sn_off, b);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -878,7 +878,6 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(GroupArgs g) {
       const double alpha = sqrt(fmax(nrm[j], 0.0));
       const double x0 = M[(int64_t)rid[j] * c + j];
       const double sg = (x0 >= 0.0) ? 1.0 : -1.0;
-      s_alpha = alpha;
       s_x0 = x0 + sg * alpha;  // v_j
       s_vn2 = 2.0 * alpha * (alpha + fabs(x0));
       if (j == 0) s_r00 = alpha;

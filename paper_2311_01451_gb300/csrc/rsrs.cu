@@ -105,7 +105,8 @@ bool tune_valid(const rsrs_tune_t& t) {
                   std::string(#call) + ": " + cudaGetErrorString(e_));                      \
   } while (0)
 
-// Owning device buffer list, freed unless released into a factor.
+// Owning device buffer list, freed when the pool goes out of scope (a graph build moves the list
+// into its factors, whose replays write to the same addresses).
 struct DevPool {
   std::vector<void*> ptrs;
   ~DevPool() {
@@ -119,7 +120,6 @@ struct DevPool {
     if (e == cudaSuccess) ptrs.push_back(*p);
     return e;
   }
-  void release(void* p) { ptrs.erase(std::remove(ptrs.begin(), ptrs.end(), p), ptrs.end()); }
 };
 
 // ---- layout conversions at the boundary ---------------------------------------
