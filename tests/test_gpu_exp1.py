@@ -3,12 +3,15 @@ first-kind log-kernel matrix on the 284 x 284 grid (N = 80,656, cond(A) = 1.2e5)
 n_samples = 1520, FP64 path.  relerr = ||A - A_approx|| / ||A|| and errsolve = ||I - A_approx^-1 A||
 (eq. error) by power iteration on the device (30 iterations or 1e-3 relative change, seeded start,
 the oracle's settings), and GMRES with the factor as preconditioner.  The paper reports relerr
-2.0e-7, errsolve 9.8e-4 and 3 GMRES iterations (other randomness, other hardware): the checks
-below ask for the same orders of magnitude, not the same digits."""
+2.0e-7, errsolve 9.8e-4 and 3 GMRES iterations (other randomness, other hardware; the printed
+table is ``tests/golden/exp1_tables.txt``): the checks below ask for the same orders of magnitude,
+not the same digits, and for errsolve within the bound of eq. (err_solve_cond) that relerr and
+the printed cond(A) give."""
 import numpy as np
 import pytest
 
 import workloads as W
+from test_golden_exp1 import load_exp1_tables
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -66,12 +69,16 @@ def test_exp1_accuracy_and_gmres(R):
     norm_a = _power(A, A, n)  # A is symmetric
     relerr = _power(lambda v: A(v) - Aapp(v), lambda w: A(w) - Aapp(w, True), n) / norm_a
     errsolve = _power(lambda v: v - Ainv(A(v)), lambda w: w - A(Ainv(w, True)), n)
-    print(f"\nExp. 1, N = {n}, k = 40, s = {s}: relerr {relerr:.2e} (paper 2.0e-07), "
-          f"errsolve {errsolve:.2e} (paper 9.8e-04)")
+    paper = next(r for r in load_exp1_tables() if r["N"] == n)
+    print(f"\nExp. 1, N = {n}, k = 40, s = {s}: relerr {relerr:.2e} (paper {paper['relerr40']:.1e}), "
+          f"errsolve {errsolve:.2e} (paper {paper['errsolve40']:.1e})")
     assert 1e-9 < relerr < 2e-6
     assert errsolve < 1e-2
+    rc = relerr * paper["cond"]  # eq. (err_solve_cond): errsolve <= 2 relerr cond / (1 - relerr cond)
+    assert rc < 0.5 and errsolve <= 2 * rc / (1 - rc)
     b = torch.tensor(np.ascontiguousarray(pr.rhs().T), device="cuda")
     X = torch.zeros_like(b)
     rep = f.gmres(b, X, rtol=1e-10, restart=30, maxit=30)
-    print(f"GMRES to 1e-10 with the factor as preconditioner: {rep.iterations} iterations (paper 3)")
+    print(f"GMRES to 1e-10 with the factor as preconditioner: {rep.iterations} iterations "
+          f"(paper {paper['it40']})")
     assert rep.rel_residual <= 1e-10 and rep.iterations <= 5
