@@ -23,6 +23,7 @@ import oracle.operators
 import oracle.refine
 import oracle.rsrs
 import oracle.tree
+import test_golden_exp1 as tgold
 import test_oracle_gmres as tg
 import test_oracle_linalg as tl
 import test_oracle_rsrs as tr
@@ -44,7 +45,8 @@ TREE_PINS = [lambda: tt.test_tree_partition_and_balance(lambda: W.grid_points_2d
                                     W.uniform_points(500, 2, W.rng_for(93, 1, 0))]), 12),
              tt.test_uniform_grid_neighbour_counts,
              lambda: tt.test_colouring_is_conflict_free(16, 4),
-             tt.test_uniform_3d_sample_count, tt.test_sizes_and_root]
+             tt.test_uniform_3d_sample_count, tt.test_sizes_and_root,
+             lambda: tgold.test_oracle_sample_count_matches_table(tgold.ROWS[0], 40)]
 GMRES_PINS = [lambda: tg.test_terminates_after_distinct_eigenvalue_count(3), tg.test_exact_preconditioner_one_iteration,
               tg.test_estimates_monotone_and_true_residual, tg.test_restarts_converge_to_dense_solution,
               tg.test_preconditioned_matches_refinement_fixed_point]
@@ -105,6 +107,7 @@ MUTANTS = [
            "t = np.all((lo < bhi[0]) & (blo[0] < hi), axis=1)"),
     Mutant("colouring_checks_first_member_only", "tree", "for o in members[c.id]:", "for o in members[c.id][:1]:"),
     Mutant("sample_bound_without_k", "tree", "self.max_l + self.k + self.p", "self.max_l + self.p"),
+    Mutant("sample_bound_without_p", "tree", "self.max_l + self.k + self.p", "self.max_l + self.k"),
     Mutant("position_map_not_inverted", "tree", "self.pos[self.perm] = np.arange(self.n)", "self.pos[:] = self.perm"),
     Mutant("balance_allows_two_levels", "tree", "deep = lvl >= a.level + 2", "deep = lvl >= a.level + 3"),
     # refinement and GMRES (oracle/refine.py)
@@ -146,7 +149,7 @@ def _swap_in(monkeypatch, module: str, mod: types.ModuleType):
     for k, v in vars(mod).items():
         if isinstance(v, (types.FunctionType, type)) and getattr(v, "__module__", None) == mod.__name__:
             swap[id(getattr(real, k))] = v
-    holders = list(MODULES.values()) + [tg, tl, tr, tt]
+    holders = list(MODULES.values()) + [tg, tgold, tl, tr, tt]
     for h in holders:
         for k, v in list(vars(h).items()):
             if id(v) in swap:
