@@ -32,18 +32,36 @@ def test_every_declared_symbol_is_exported(R):
     assert set(R.rsrs.EXPORTS) <= declared
 
 
-@pytest.mark.parametrize("case", ["grid2d", "rand2d", "rand3d", "clustered2d"])
+@pytest.mark.parametrize("case", ["grid2d", "rand2d", "rand3d", "clustered2d", "collinear2d", "coincident2d",
+                                  "single", "outside_unit3d", "planar3d"])
 def test_tree_and_schedule_match_oracle(R, case):
+    """Same tree, order and schedule as the oracle's, including degenerate geometry: points on a
+    line or a plane (empty children are never made), 100 coincident points (subdivision stops at the
+    2^20 binning grid's depth), one point (a root-only tree), and points outside the unit cube (the
+    root is their bounding cube)."""
     if case == "grid2d":
         pts, leaf, k = W.grid_points_2d(64), 64, 32
     elif case == "rand2d":
         pts, leaf, k = W.uniform_points(20000, 2, W.rng_for(96, 0, 0)), 64, 24
     elif case == "rand3d":
         pts, leaf, k = W.uniform_points(6000, 3, W.rng_for(96, 1, 0)), 32, 16
-    else:
+    elif case == "clustered2d":
         pts = np.vstack([W.uniform_points(3000, 2, W.rng_for(96, 2, 0)) * 0.03 + 0.5,
                          W.uniform_points(2000, 2, W.rng_for(96, 3, 0))])
         leaf, k = 20, 8
+    elif case == "collinear2d":
+        pts = np.stack([W.uniform_points(3000, 1, W.rng_for(96, 4, 0))[:, 0], np.full(3000, 0.25)], 1)
+        leaf, k = 24, 8
+    elif case == "coincident2d":
+        pts = np.vstack([np.full((100, 2), 0.3), W.uniform_points(400, 2, W.rng_for(96, 5, 0))])
+        leaf, k = 16, 8
+    elif case == "single":
+        pts, leaf, k = np.array([[0.5, 0.5]]), 16, 8
+    elif case == "outside_unit3d":
+        pts, leaf, k = W.uniform_points(3000, 3, W.rng_for(96, 6, 0)) * 8.0 - 3.0, 32, 12
+    else:
+        pts = np.hstack([W.uniform_points(4000, 2, W.rng_for(96, 7, 0)), np.full((4000, 1), 0.5)])
+        leaf, k = 32, 12
     t = R.Tree(pts, leaf)
     ot = OTree(pts, leaf)
     osc = OSchedule(ot, k)
@@ -54,7 +72,11 @@ def test_tree_and_schedule_match_oracle(R, case):
     assert info.s_req_mixed >= info.s_req
     sch = t.schedule(k)
     ref = np.array([[st["level"], st["colour"], st["b"], st["n"], st["box"].first_pos] for st in osc.steps])
-    assert np.array_equal(sch[:, [0, 1, 3, 4, 5]], ref)
+    assert np.array_equal(sch[:, [0, 1, 3, 4, 5]], ref.reshape(-1, 5))
+    if case == "coincident2d":
+        assert info.depth == 20
+    if case == "single":
+        assert info.n_compress == 0 and info.root_size == 1
 
 
 def test_sample_bound_matches_paper(R):
