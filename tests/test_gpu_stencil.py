@@ -13,6 +13,7 @@ import pytest
 import workloads as W
 from oracle import operators as ops
 from oracle import rsrs as orsrs
+from test_gpu_parity import id_amplification
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -62,23 +63,6 @@ def test_stencil_rejects_bad_coefficients(R):
         R.Stencil7(np.full(27, -1.0), 3)
 
 
-def _id_amplification(fac, trace, Y0, Z0):
-    """max over boxes of |[Y_B Z_B]|_rowmax / (smallest accepted pivot residual): how much an ID of
-    a weak far field amplifies the rounding of the nullified sketch.  On the stencil some boxes see
-    only a little fill from eliminated neighbours (far fields at 1e-10..1e-4 of the near field), so
-    two correct FP64 implementations agree only to about 1e-14 times this factor."""
-    amp = 1.0
-    for bf, tr in zip(fac.boxes, trace):
-        nd = int(np.sum(~np.asarray(bf.pivot_dependent)))
-        if nd == 0:
-            continue
-        m = np.hstack([tr["Yp"], tr["Zp"]])
-        r = np.linalg.qr(m[[list(bf.B).index(v) for v in bf.S[:nd]]].T, mode="r")
-        scale = np.sqrt(np.max(tr["scale2"]))
-        amp = max(amp, scale / np.abs(np.diag(r)).min())
-    return amp
-
-
 def test_stencil_fp64_matches_oracle(R):
     pr = _stencil_problem(12, 27, 8)
     trace = []
@@ -100,7 +84,9 @@ def test_stencil_fp64_matches_oracle(R):
     b = pr.rhs()
     x = _from_gpu(f.solve(_to_gpu(b)))
     ref = orsrs.solve(fac, b)
-    tol = max(SOLVE_TOL, 1e-14 * _id_amplification(fac, trace, None, None))
+    # some boxes see only a little fill from eliminated neighbours (far fields at 1e-10..1e-4 of
+    # the near field), whose IDs amplify the nullified sketch's rounding
+    tol = max(SOLVE_TOL, 1e-14 * id_amplification(fac, trace))
     assert np.linalg.norm(x - ref) / np.linalg.norm(ref) < (tol if same else 1e-3)
     # the pair is an exact inverse on the device
     y = _from_gpu(f.apply(f.solve(_to_gpu(b))))
