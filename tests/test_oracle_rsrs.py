@@ -131,11 +131,16 @@ def test_sketch_pair_invariant():
     assert np.abs(fin["Z"] - at.T @ fin["Ps"]).max() < 1e-12 * np.abs(Z).max()
 
 
-@pytest.mark.parametrize("case", ["grid2d", "rand3d"])
+@pytest.mark.parametrize("case", ["grid2d", "rand3d", "collinear2d"])
 def test_brute_force_against_dense_lu(case):
-    """P7: solve vs numpy dense LU; eq. (err_solve_cond); errors fall with k."""
+    """P7: solve vs numpy dense LU; eq. (err_solve_cond); errors fall with k.  The collinear set
+    (1,200 points on one line) is degenerate geometry: two neighbours per box in a row."""
     if case == "grid2d":
         mk = lambda k: W.small_problem(n_side=32, leaf=16, k=k)
+        ks = [4, 8, 12]
+    elif case == "collinear2d":
+        line = np.stack([W.uniform_points(1200, 1, W.rng_for(95, 0, 0))[:, 0], np.full(1200, 0.25)], 1)
+        mk = lambda k: W.kernel_problem(95, "collinear", line, "log2d", 16, k, 0, 1)
         ks = [4, 8, 12]
     else:
         # a 1024-point octree is too shallow for the error to fall monotonically in k;
@@ -158,7 +163,7 @@ def test_brute_force_against_dense_lu(case):
             assert fe <= refine.solve_error_bound(eps, cond)
         rel.append(eps)
         es.append(np.linalg.norm(np.eye(pr.n) - _dense_of(rsrs.solve, fac, pr.n) @ a, 2))
-    if case == "grid2d":
+    if case != "rand3d":
         assert all(r1 > r2 for r1, r2 in zip(rel, rel[1:]))
         assert all(e1 > e2 for e1, e2 in zip(es, es[1:]))
     assert max(rel) < 0.1
