@@ -322,7 +322,7 @@ def run_gpu(args):
         "factor_ms": statistics.mean(x.t_sample_ms + x.t_compress_ms + x.t_root_ms for x in sts),
         "refine_iterations": [r.iterations for r in reps],
         "rel_residual": max(r.rel_residual for r in reps),
-        "gpu_launches": int(sts[0].kernel_launches) * args.steps,
+        "gpu_launches": sum(int(x.kernel_launches) + int(rp.kernel_launches) for rp, x in zip(reps, sts)),
         "kernel_classes_ms": {nm: round(avg[nm][0], 3) for nm in names},
         "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": _traffic(dom, pr.name),
@@ -431,10 +431,11 @@ def run_gpu_batched(args):
         fs = R.build_batched(trees, kinds, k, s, [p.diag_shift for p in prs], [p.scale for p in prs],
                              precision=prec, seed=seed, profile=profile, sample_kernel=args.sample_kernel,
                              tune=tune)
-        its = [f.refine(b, x, rtol=RTOL, maxit=30).iterations for f, b, x in zip(fs, Bs, Xs)]
+        reps = [f.refine(b, x, rtol=RTOL, maxit=30) for f, b, x in zip(fs, Bs, Xs)]
+        its = [r.iterations for r in reps]
         st, cls = fs[0].stats(), fs[0].class_stats()
         del fs
-        return its, st, cls
+        return its, st, cls, sum(int(r.kernel_launches) for r in reps)
 
     for w in range(args.warmup):
         step(2000 + w)
@@ -471,7 +472,7 @@ def run_gpu_batched(args):
                    "l2": "inputs larger than L2"},
         "factor_ms": st.t_sample_ms + st.t_compress_ms + st.t_root_ms,
         "refine_iterations_max": max(max(r[0]) for r in res),
-        "gpu_launches": int(st.kernel_launches) * args.steps,
+        "gpu_launches": sum(int(r[1].kernel_launches) + r[3] for r in res),
         "kernel_classes_ms": {nm: round(avg[nm][0], 3) for nm in names},
         "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None, "peak_note": peak_note,

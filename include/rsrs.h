@@ -183,6 +183,8 @@ typedef struct {
   int iterations;         /* corrections applied after the first solve                */
   double rel_residual;    /* final max over columns of ||b - A x|| / ||b||            */
   double history[64];     /* relative residual after each step                        */
+  int64_t kernel_launches; /* kernels of this library the call launched (a matvec
+                              callback's own launches are not counted)                */
 } rsrs_refine_report;
 
 /* ---- tree (Sec. 3: quad/octree, adjacency, 2:1 balance) --------------------

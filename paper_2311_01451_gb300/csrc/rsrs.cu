@@ -261,9 +261,11 @@ rsrs_status op_apply(const rsrs_factor* f, Launch L, const double* in, double* o
   if (f->kind == RSRS_OP_CALLBACK) {
     int64_t tot = f->n * ncols;
     k_rows_to_cm<<<nblk(tot), 256, 0, L.st>>>(in, f->perm_dev, f->n, (int)ncols, scratch_cm_in, f->n);
+    if (L.counter) ++*L.counter;
     int rc = f->fn(f->ctx, adjoint, f->n, (int32_t)ncols, scratch_cm_in, f->n, scratch_cm_out, f->n, (void*)L.st);
     if (rc != 0) return fail(RSRS_E_CALLBACK, "matvec callback returned " + std::to_string(rc));
     k_cm_to_rows<<<nblk(tot), 256, 0, L.st>>>(scratch_cm_out, f->n, f->perm_dev, f->n, (int)ncols, out);
+    if (L.counter) ++*L.counter;
     CU(cudaGetLastError());
     return RSRS_OK;
   }
@@ -1549,7 +1551,8 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_
   if (r != RSRS_OK) return r;
   if (!X || nrhs > 64 || maxit < 0 || !(rtol >= 0.0)) return fail(RSRS_E_INVAL, "refine: bad arguments");
   cudaStream_t st = (cudaStream_t)stream;
-  Launch L{st, nullptr};
+  int64_t nl = 0;  // kernels launched, for the report
+  Launch L{st, &nl};
   DevPool pool;
   const int64_t tot = f->n * nrhs;
   double *Wb, *Wx, *Wr, *Wax, *nrm, *c1 = nullptr, *c2 = nullptr;
@@ -1567,12 +1570,14 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_
   float* ffs = nullptr;
   if (ff) CU(pool.alloc(&ffs, ff_scratch_floats(f->n, f->d, nrhs, f->tune.residual_split)));
   k_cm_to_rows<<<nblk(tot), 256, 0, st>>>(B, ld, f->perm_dev, f->n, nrhs, Wb);
+  ++nl;
   CU(cudaMemcpyAsync(Wx, Wb, tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
   r = sweep_solve(f, L, Wx, nrhs, 0);
   if (r != RSRS_OK) return r;
   double hn[128];
   CU(cudaMemsetAsync(nrm, 0, 64 * sizeof(double), st));
   k_colnorm2<<<std::min<int64_t>(1024, nblk(tot)), 256, 0, st>>>(Wb, f->n, nrhs, nrm);
+  ++nl;
   CU(cudaMemcpyAsync(hn, nrm, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
   std::vector<double> bn(hn, hn + nrhs);
@@ -1589,6 +1594,7 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_
     k_sub<<<nblk(tot), 256, 0, st>>>(Wr, Wb, Wax, tot);
     CU(cudaMemsetAsync(nrm, 0, 64 * sizeof(double), st));
     k_colnorm2<<<std::min<int64_t>(1024, nblk(tot)), 256, 0, st>>>(Wr, f->n, nrhs, nrm);
+    nl += 2;  // k_sub, k_colnorm2
     CU(cudaMemcpyAsync(hn, nrm, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     rel = 0.0;
@@ -1599,12 +1605,15 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_
     r = sweep_solve(f, L, Wr, nrhs, 0);
     if (r != RSRS_OK) return r;
     k_axpy<<<nblk(tot), 256, 0, st>>>(Wx, Wr, 1.0, tot);
+    ++nl;
   }
   k_rows_to_cm<<<nblk(tot), 256, 0, st>>>(Wx, f->perm_dev, f->n, nrhs, X, ld);
+  ++nl;
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(st));
   rr.iterations = it;
   rr.rel_residual = rel;
+  rr.kernel_launches = nl;
   if (rep) *rep = rr;
   if (rel > rtol) return fail(RSRS_E_NOT_CONVERGED, "refine: residual " + std::to_string(rel) + " > rtol");
   return RSRS_OK;
@@ -1704,11 +1713,13 @@ struct Gmres {
   int c;
   double *part, *h_dev;
   int nchunk;
+  int64_t* launches;  // kernels launched, for the report
   // h[0..kk)[col] = V_i^T w, copied to the host
   rsrs_status dots(const double* V, int kk, const double* w, double* h_host) {
     const int threads = (256 / c) * c;
     k_vdot_part<<<dim3((unsigned)nchunk, (unsigned)kk), threads, 0, st>>>(V, w, n, c, part);
     k_vdot_final<<<nblk((int64_t)kk * c), 256, 0, st>>>(part, nchunk, kk, c, h_dev);
+    *launches += 2;
     CU(cudaGetLastError());
     CU(cudaMemcpyAsync(h_host, h_dev, (size_t)kk * c * sizeof(double), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
@@ -1717,12 +1728,14 @@ struct Gmres {
   rsrs_status comb(double* w, const double* V, const double* h_host, int kk, double sign) {
     CU(cudaMemcpyAsync(h_dev, h_host, (size_t)kk * c * sizeof(double), cudaMemcpyHostToDevice, st));
     k_vcomb<<<nblk(n * c), 256, 0, st>>>(w, V, h_dev, kk, n, c, sign);
+    ++*launches;
     CU(cudaGetLastError());
     return RSRS_OK;
   }
   rsrs_status scale(const double* in, const double* s_host, double* out) {
     CU(cudaMemcpyAsync(h_dev, s_host, (size_t)c * sizeof(double), cudaMemcpyHostToDevice, st));
     k_colscale<<<nblk(n * c), 256, 0, st>>>(in, h_dev, n, c, out);
+    ++*launches;
     CU(cudaGetLastError());
     return RSRS_OK;
   }
@@ -1739,12 +1752,13 @@ rsrs_status rsrs_gmres(const rsrs_factor* f, const double* B, double* X, int64_t
   if (!X || nrhs > 64 || restart < 1 || restart > 64 || maxit < 1 || !(rtol >= 0.0))
     return fail(RSRS_E_INVAL, "gmres: bad arguments");
   cudaStream_t st = (cudaStream_t)stream;
-  Launch L{st, nullptr};
+  int64_t nl = 0;  // kernels launched, for the report
+  Launch L{st, &nl};
   DevPool pool;
   const int c = nrhs, m = restart;
   const int64_t n = f->n, tot = n * c;
   double *Wb, *Wx, *Ww, *V, *Z, *c1 = nullptr, *c2 = nullptr;
-  Gmres gm{st, n, c, nullptr, nullptr, (int)cdiv(n, kDotRows)};
+  Gmres gm{st, n, c, nullptr, nullptr, (int)cdiv(n, kDotRows), &nl};
   CU(pool.alloc(&Wb, tot));
   CU(pool.alloc(&Wx, tot));
   CU(pool.alloc(&Ww, tot));
@@ -1770,6 +1784,7 @@ rsrs_status rsrs_gmres(const rsrs_factor* f, const double* B, double* X, int64_t
     return op_apply(f, L, in, out, c, 0, 0, c1, c2);
   };
   k_cm_to_rows<<<nblk(tot), 256, 0, st>>>(B, ld, f->perm_dev, n, c, Wb);
+  ++nl;
   CU(cudaMemsetAsync(Wx, 0, tot * sizeof(double), st));
   std::vector<double> bn(c), beta(c), hcol((size_t)(m + 1) * c), h2((size_t)(m + 1) * c), sc(c);
   r = gm.dots(Wb, 1, Wb, bn.data());
@@ -1789,6 +1804,7 @@ rsrs_status rsrs_gmres(const rsrs_factor* f, const double* B, double* X, int64_t
       r = apply_A(Wx, Ww);
       if (r != RSRS_OK) return r;
       k_sub<<<nblk(tot), 256, 0, st>>>(Ww, Wb, Ww, tot);
+      ++nl;
       CU(cudaGetLastError());
     }
     first = false;
@@ -1878,10 +1894,12 @@ rsrs_status rsrs_gmres(const rsrs_factor* f, const double* B, double* X, int64_t
     }
   }
   k_rows_to_cm<<<nblk(tot), 256, 0, st>>>(Wx, f->perm_dev, n, c, X, ld);
+  ++nl;
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(st));
   rr.iterations = total;
   rr.rel_residual = rel;
+  rr.kernel_launches = nl;
   if (rep) *rep = rr;
   if (rel > rtol) return fail(RSRS_E_NOT_CONVERGED, "gmres: residual " + std::to_string(rel) + " > rtol");
   return RSRS_OK;

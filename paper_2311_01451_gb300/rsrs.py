@@ -91,7 +91,8 @@ class Stats(C.Structure):
 
 
 class RefineReport(C.Structure):
-    _fields_ = [("iterations", C.c_int), ("rel_residual", C.c_double), ("history", C.c_double * 64)]
+    _fields_ = [("iterations", C.c_int), ("rel_residual", C.c_double), ("history", C.c_double * 64),
+                ("kernel_launches", C.c_int64)]
 
 
 class BoxView(C.Structure):

@@ -143,3 +143,30 @@ def test_autotune_validates_before_device_work(R):
     assert e.value.name == "RSRS_E_INVAL"
     lib = R.lib()
     assert lib.rsrs_autotune(1, None, None, 32, s, None, 1, None, None, None, None) == 1
+
+
+STRUCTS = {"Operator": "rsrs_operator", "Tune": "rsrs_tune_t", "TuneReport": "rsrs_tune_report",
+           "Options": "rsrs_options", "TreeInfo": "rsrs_tree_info_t", "Stats": "rsrs_stats",
+           "RefineReport": "rsrs_refine_report", "BoxView": "rsrs_box_view"}
+
+
+def test_binding_struct_layouts_match_the_header(R, tmp_path):
+    """Every struct the binding passes through the C ABI has the header's size and field offsets
+    (a C program compiled against include/rsrs.h prints them; no device work)."""
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "rsrs.h"', "int main(void) {"]
+    want = []
+    for py, c in STRUCTS.items():
+        cls = getattr(R.rsrs, py)
+        lines.append(f'  printf("%zu\\n", sizeof({c}));')
+        want.append(C.sizeof(cls))
+        for name, *_ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({c}, {name}));')
+            want.append(getattr(cls, name).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == want
