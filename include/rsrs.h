@@ -307,9 +307,14 @@ rsrs_status rsrs_apply(const rsrs_factor* f, double* F_dev, int64_t ldf, int32_t
  * B or X).  Section 3.3's residual; nrhs <= 4096. */
 rsrs_status rsrs_residual(const rsrs_factor* f, const double* B_dev, const double* X_dev, double* R_dev,
                           int64_t ld, int32_t nrhs, void* stream);
-/* FP64 iterative refinement: X = A_approx^-1 B, then X += A_approx^-1 (B - A X)
- * with the FP64 residual of the operator the factor was built from, until
- * max_j ||B_j - A X_j|| / ||B_j|| <= rtol or maxit corrections. */
+/* Iterative refinement to FP64 accuracy (Sec. 3.3's residual, with the factor as the
+ * approximate inverse): X = A_approx^-1 B, then X += A_approx^-1 (B - A X) until
+ * max_j ||B_j - A X_j|| / ||B_j|| <= rtol or maxit corrections.  The residual is computed as
+ * rsrs_residual computes it (float-float for the built-in kernels unless opts->residual_fp64,
+ * FP64 through the callback otherwise).  B_dev, X_dev column-major N x nrhs with leading
+ * dimension ld, nrhs <= 64; X's input is ignored.  out (may be null): corrections, final
+ * relative residual, its history, kernels launched.  RSRS_E_NOT_CONVERGED (out still filled)
+ * when rtol is not reached; RSRS_E_NONFINITE for a non-finite residual. */
 rsrs_status rsrs_refine(const rsrs_factor* f, const double* B_dev, double* X_dev, int64_t ld,
                         int32_t nrhs, double rtol, int maxit, void* stream,
                         rsrs_refine_report* out);
