@@ -37,7 +37,7 @@ extern "C" {
 typedef enum {
   RSRS_OK = 0,
   RSRS_E_INVAL = 1,         /* bad argument (null pointer, size, layout)           */
-  RSRS_E_UNDERSAMPLED = 2,  /* s below the sample bound of Sec. 4.4 (see s_req)     */
+  RSRS_E_UNDERSAMPLED = 2,  /* s below the sample bound of Sec. 4.5 (see s_req)     */
   RSRS_E_SINGULAR = 3,      /* zero pivot in the LU of an X_RR block or the root    */
   RSRS_E_NONFINITE = 4,     /* NaN/Inf met in a sketch, a Gram or a pivot           */
   RSRS_E_NOMEM = 5,         /* device allocation failed                             */
@@ -193,7 +193,7 @@ typedef struct {
 rsrs_status rsrs_tree_build(const double* pts_host, int64_t n, int d, int leaf_cap,
                             rsrs_tree** out);
 /* Sizes of Algorithm 1 on this tree for rank k and oversampling p (p < 0: p = k),
- * including the sample bound of Sec. 4.4 (s_req). */
+ * including the sample bound of Sec. 4.5 (s_req). */
 rsrs_status rsrs_tree_info(const rsrs_tree* tree, int k, int p, rsrs_tree_info_t* out);
 /* perm_host[t] = original index of the point at tree position t (n entries). */
 rsrs_status rsrs_tree_perm(const rsrs_tree* tree, int64_t* perm_host);
@@ -304,10 +304,11 @@ rsrs_status rsrs_apply(const rsrs_factor* f, double* F_dev, int64_t ldf, int32_t
 /* R = B - A X for the operator the factor was built from, in the refinement's residual
  * arithmetic (float-float for the built-in kernels unless opts->residual_fp64, FP64 for a
  * callback); B_dev, X_dev, R_dev column-major N x nrhs with leading dimension ld (R may not alias
- * B or X).  Section 3.3's residual; nrhs <= 4096. */
+ * B or X).  The residual of iterative refinement, which the paper does not use (it pairs the
+ * factor with GMRES, Sec. 5); nrhs <= 4096. */
 rsrs_status rsrs_residual(const rsrs_factor* f, const double* B_dev, const double* X_dev, double* R_dev,
                           int64_t ld, int32_t nrhs, void* stream);
-/* Iterative refinement to FP64 accuracy (Sec. 3.3's residual, with the factor as the
+/* Iterative refinement to FP64 accuracy (an addition to the paper's method, with the factor as the
  * approximate inverse): X = A_approx^-1 B, then X += A_approx^-1 (B - A X) until
  * max_j ||B_j - A X_j|| / ||B_j|| <= rtol or maxit corrections.  The residual is computed as
  * rsrs_residual computes it (float-float for the built-in kernels unless opts->residual_fp64,
@@ -319,7 +320,7 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B_dev, double* X_dev
                         int32_t nrhs, double rtol, int maxit, void* stream,
                         rsrs_refine_report* out);
 /* Restarted GMRES(restart) (Saad and Schultz 1986) on A X = B with the factor as right
- * preconditioner, A (A_approx)^-1 Y = B, X = (A_approx)^-1 Y: the Krylov method Sec. 6 pairs
+ * preconditioner, A (A_approx)^-1 Y = B, X = (A_approx)^-1 Y: the Krylov method Sec. 5 pairs
  * with the factorization, against iterative refinement.  Every column is its own GMRES run (its
  * own Arnoldi basis, classical Gram-Schmidt applied twice, Givens rotations); the columns share
  * the launches.  Products with A in the refinement's residual arithmetic (float-float for the

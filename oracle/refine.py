@@ -10,7 +10,7 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
   seeded start block (30 iterations or 1e-3 relative change).
 * ``solve_error_bound``: the right side of eq. (err_solve_cond).
 * ``gmres``: restarted, right-preconditioned GMRES with the factor as preconditioner (the Krylov
-  method of the paper's experiments, Sec. 6), one right-hand side.
+  method of the paper's experiments, Sec. 5), one right-hand side.
 """
 from __future__ import annotations
 

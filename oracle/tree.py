@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
-Geometry of Sec. 3 (tree, adjacency, near/far field) and of Sec. 4.4 (active
-counts and the sample bound s_B), written plainly in Python with no shared code
+Geometry of Sec. 3 (tree, adjacency, near/far field), the active counts of
+Sec. 4.4 and the sample bound s_B of Sec. 4.5, written plainly in Python with no shared code
 with the CUDA library's own tree builder, so that the two can be compared.
 
 Readings where the paper is silent:

@@ -1,5 +1,5 @@
 // Adaptive 2^d-tree, 2:1 balance, neighbour lists and the processing schedule
-// of Algorithm 1 (Sec. 3, Sec. 4.4).
+// of Algorithm 1 (Sec. 3, Sec. 4.4) with the sample bound of Sec. 4.5.
 //
 // Rules (the paper leaves them open; the CPU oracle follows the same ones):
 //  * root cube [0,1]^d if all points lie in it, else the bounding cube anchored

@@ -1,4 +1,4 @@
-"""The matrix of the paper's Experiment 1 (Sec. 6.1): its diagonal, the cell integral of the log
+"""The matrix of the paper's Experiment 1 (Sec. 5.1): its diagonal, the cell integral of the log
 kernel, in closed form against 2D adaptive quadrature (the paper uses Quadpack for it), and the
 sample count the tree gives for it against the paper's n_samples."""
 import numpy as np

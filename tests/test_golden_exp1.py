@@ -1,10 +1,10 @@
-"""Pins from the numbers the paper prints for Experiment 1 (Sec. 6.1, summary table, sub-tables
+"""Pins from the numbers the paper prints for Experiment 1 (Sec. 5.1, summary table, sub-tables
 tab:laplace_grid_acc and tab:laplace_grid_niter), stored as typed in ``tests/golden/exp1_tables.txt``.
 
 The sample count is the one printed value our code must reproduce exactly: on the sqrt(N) x sqrt(N)
 grid with leaf m = 4k and p = k the paper uses n_samples = 37k + p at every N of its table (1520 at
 k = 40, 2280 at k = 60).  It follows from the tree, the neighbour lists and the active-set sizes at
-processing time (Sec. 4.4), so both the oracle's tree and the library's host tree are checked at all
+processing time (Sec. 4.4, 4.5), so both the oracle's tree and the library's host tree are checked at all
 five sizes.  The accuracy and GMRES columns come from other random test matrices on other hardware;
 the GPU test of Experiment 1 reads them as context, not as targets."""
 import math

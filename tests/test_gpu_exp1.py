@@ -1,4 +1,4 @@
-"""The paper's Experiment 1 at its smallest size (Sec. 6.1, Table tab:laplace_grid_acc): the
+"""The paper's Experiment 1 at its smallest size (Sec. 5.1, Table tab:laplace_grid_acc): the
 first-kind log-kernel matrix on the 284 x 284 grid (N = 80,656, cond(A) = 1.2e5), k = p = 40,
 n_samples = 1520, FP64 path.  relerr = ||A - A_approx|| / ||A|| and errsolve = ||I - A_approx^-1 A||
 (eq. error) by power iteration on the device (30 iterations or 1e-3 relative change, seeded start,

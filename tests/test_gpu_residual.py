@@ -1,4 +1,5 @@
-"""The refinement residual R = B - A X (Sec. 3.3) in float-float arithmetic against FP64.
+"""The refinement residual R = B - A X (iterative refinement, an addition to the paper) in float-float
+arithmetic against FP64.
 
 B is taken as A X plus a perturbation of 1e-10, so R is about 1e-10 of B: the regime of iterative
 refinement, where the residual is a small difference of large terms.  The float-float product

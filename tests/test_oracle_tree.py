@@ -1,4 +1,4 @@
-"""Pins for the oracle's tree, neighbour lists, colouring and sample bound (Sec. 3, Sec. 4.4)."""
+"""Pins for the oracle's tree, neighbour lists, colouring and sample bound (Sec. 3, Sec. 4.5)."""
 import numpy as np
 import pytest
 

@@ -113,7 +113,7 @@ def cell_log_mean(h: float) -> float:
 
 
 def exp1_problem(n_side: int = 284, k: int = 40, nrhs: int = 1) -> Problem:
-    """The matrix of the paper's Experiment 1 (Sec. 6.1, eq. Aentries_exp1): collocation points on
+    """The matrix of the paper's Experiment 1 (Sec. 5.1, eq. Aentries_exp1): collocation points on
     the uniform n_side x n_side grid of the unit square (cell centres), A_ij = log|x_i - x_j| / N for
     i != j and A_ii = the integral of log|x| over the point's cell (h^2 = 1/N times the cell mean),
     leaf m = 4k (c_cap = 4) and n_samples = s of the sample bound (1520 at N = 80,656, k = 40)."""
