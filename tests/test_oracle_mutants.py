@@ -50,7 +50,7 @@ TREE_PINS = [lambda: tt.test_tree_partition_and_balance(lambda: W.grid_points_2d
 GMRES_PINS = [lambda: tg.test_terminates_after_distinct_eigenvalue_count(3), tg.test_exact_preconditioner_one_iteration,
               tg.test_estimates_monotone_and_true_residual, tg.test_restarts_converge_to_dense_solution,
               tg.test_preconditioned_matches_refinement_fixed_point]
-REFINE_PINS = [tr.test_refinement_reaches_dense_solution] + GMRES_PINS
+REFINE_PINS = [tr.test_refinement_reaches_dense_solution, tr.test_refinement_stopping_rule_is_relative] + GMRES_PINS
 
 PINS = {"rsrs": RSRS_PINS, "linalg": LINALG_PINS, "operators": OPS_PINS, "tree": TREE_PINS,
         "refine": REFINE_PINS}
@@ -112,6 +112,8 @@ MUTANTS = [
     Mutant("balance_allows_two_levels", "tree", "deep = lvl >= a.level + 2", "deep = lvl >= a.level + 3"),
     # refinement and GMRES (oracle/refine.py)
     Mutant("refine_subtracts_correction", "refine", "x = x + rsrs.solve(fac, r)", "x = x - rsrs.solve(fac, r)"),
+    Mutant("refine_residual_with_the_factor", "refine", "r = b - op.matvec(x)", "r = b - rsrs.apply(fac, x)"),
+    Mutant("refine_stops_on_absolute_residual", "refine", "rel = np.linalg.norm(r) / bn", "rel = np.linalg.norm(r)"),
     Mutant("gmres_update_not_preconditioned", "refine", "x = x + precond(V[:, :k] @ y)", "x = x + V[:, :k] @ y"),
     Mutant("gmres_givens_sign", "refine", "g[k + 1], g[k] = -sn[k] * g[k], cs[k] * g[k]",
            "g[k + 1], g[k] = sn[k] * g[k], cs[k] * g[k]"),

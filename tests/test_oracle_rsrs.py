@@ -198,6 +198,22 @@ def test_refinement_reaches_dense_solution():
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-12
 
 
+def test_refinement_stopping_rule_is_relative():
+    """The refinement stops on the relative residual ||b - A x|| / ||b|| <= rtol: the method is
+    linear in b, so scaling b by 1e6 scales every iterate and leaves the history unchanged up to
+    rounding, and the run stops at the first step that reaches rtol."""
+    pr = W.small_problem(n_side=32, leaf=16, k=6)
+    tr, sc, fac, _ = rsrs.build(pr)
+    op = ops.make_operator(pr)
+    b = pr.rhs()
+    rtol = 1e-10
+    x1, h1 = refine.refine(fac, op, b, rtol=rtol)
+    x2, h2 = refine.refine(fac, op, 1e6 * b, rtol=rtol)
+    assert len(h1) == len(h2) and h1[-1] <= rtol and all(h > rtol for h in h1[:-1])
+    assert np.allclose(h1, h2, rtol=1e-6, atol=1e-15)
+    assert np.linalg.norm(x2 - 1e6 * x1) <= 1e-9 * np.linalg.norm(x2)
+
+
 def test_undersampled_is_refused():
     pr = W.small_problem(n_side=24, leaf=16, k=8)
     tr = Tree(pr.points, pr.leaf)
