@@ -71,6 +71,10 @@ MUTANTS = [
     Mutant("schur_sign", "rsrs", "Y[S] -= LcS @ YR", "Y[S] += LcS @ YR"),
     Mutant("schur_drops_neighbour_term", "rsrs", "Om[R] += UcS @ Om[S] + UcN @ Om[Nact]", "Om[R] += UcS @ Om[S]"),
     Mutant("e_update_missing_on_z", "rsrs", "            Z[R] -= T.T @ Z[S]\n", ""),
+    Mutant("e_update_missing_on_y", "rsrs", "            Y[R] -= T.T @ Y[S]\n", ""),
+    Mutant("schur_z_neighbour_sign", "rsrs", "Z[Nact] -= UcN.T @ ZR", "Z[Nact] += UcN.T @ ZR"),
+    Mutant("redundant_indices_stay_active", "rsrs", "act[box.id] = _tree_sorted(S, tree.pos)",
+           "act[box.id] = _tree_sorted(Bact, tree.pos)"),
     Mutant("f_update_wrong_sketch", "rsrs", "Ps[S] += T @ Ps[R]", "Ps[S] += T @ Om[R]"),
     Mutant("nullify_z_with_omega", "rsrs", "Zp = Z[Bact] @ la.null(Ps[BN])", "Zp = Z[Bact] @ la.null(Om[BN])"),
     Mutant("id_of_y_side_only", "rsrs", "la.cpqr_id(np.hstack([Yp, Zp])", "la.cpqr_id(np.hstack([Yp, Yp])"),
