@@ -100,6 +100,13 @@ MUTANTS = [
     Mutant("cpqr_t_columns_not_reordered", "linalg", "    t = t[:, order]\n", ""),
     Mutant("cpqr_floor_ignored", "linalg", "if best <= floor or", "if"),
     Mutant("householder_reflects_twice", "linalg", "a[j:, j:] -= 2.0 * np.outer", "a[j:, j:] -= 4.0 * np.outer"),
+    Mutant("cpqr_pivot_smallest_norm", "linalg", "best = norms.max()", "best = norms.min()"),
+    Mutant("cpqr_swap_forgets_perm", "linalg", "            perm[[j, p]] = perm[[p, j]]\n", ""),
+    Mutant("cpqr_t_from_lower_triangle", "linalg",
+           "t[:j0] = sla.solve_triangular(r11[:j0, :j0], r12[:j0], lower=False)",
+           "t[:j0] = sla.solve_triangular(r11[:j0, :j0].T, r12[:j0], lower=True)"),
+    Mutant("pinv_result_untransposed", "linalg", "return sla.solve_triangular(r, (y @ q).T, lower=False).T",
+           "return sla.solve_triangular(r, (y @ q).T, lower=False)"),
     # matrices (oracle/operators.py)
     Mutant("log_of_r_squared", "operators", "k = np.log(r)", "k = np.log(r * r)"),
     Mutant("invr_squared", "operators", "k = 1.0 / r\n", "k = 1.0 / (r * r)\n"),
