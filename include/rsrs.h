@@ -80,15 +80,19 @@ enum {
                         /* LU, the root, the solve and the refinement residual             */
 };
 
-/* Tile shapes of the tensor-core sampling product: column tile x pipeline stages (of 32 points
- * unless stated). */
+/* Tile shapes of the tensor-core sampling product: accumulators of 128 rows per CTA x column tile x
+ * pipeline stages (of 32 points unless stated).  Every CTA loads its own B tiles; two accumulators
+ * share each loaded B stage. */
 enum {
-  RSRS_SAMPLE_TILE_DEFAULT = 0,  /* the library's choice (256 x 4 of 16 points)                 */
-  RSRS_SAMPLE_TILE_256x2 = 1,    /* 256 columns per CTA, two stages                              */
-  RSRS_SAMPLE_TILE_128x3 = 2,    /* 128 columns, three stages                                    */
-  RSRS_SAMPLE_TILE_192x2 = 3,    /* 192 columns, two stages                                      */
-  RSRS_SAMPLE_TILE_256x4_K16 = 4, /* 256 columns, four stages of 16 points (64-byte swizzle)     */
-  RSRS_SAMPLE_TILE_192x5_K16 = 5  /* 192 columns, five stages of 16 points                       */
+  RSRS_SAMPLE_TILE_DEFAULT = 0,  /* the library's choice (2 x 256 x 3 of 16 points)             */
+  RSRS_SAMPLE_TILE_256x2 = 1,    /* one accumulator, 256 columns per CTA, two stages             */
+  RSRS_SAMPLE_TILE_128x3 = 2,    /* one accumulator, 128 columns, three stages                   */
+  RSRS_SAMPLE_TILE_192x2 = 3,    /* one accumulator, 192 columns, two stages                     */
+  RSRS_SAMPLE_TILE_256x4_K16 = 4, /* one accumulator, 256 columns, four stages of 16 points      */
+  RSRS_SAMPLE_TILE_192x5_K16 = 5, /* one accumulator, 192 columns, five stages of 16 points      */
+  RSRS_SAMPLE_TILE_2x256x3_K16 = 6, /* two accumulators (256 rows), 256 columns, three stages of  */
+                                    /* 16 points                                                  */
+  RSRS_SAMPLE_TILE_2x192x4_K16 = 7  /* two accumulators, 192 columns, four stages of 16 points    */
 };
 
 /* Launch shapes of the kernels whose best shape depends on the problem and the device; all zero

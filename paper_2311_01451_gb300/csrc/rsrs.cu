@@ -89,7 +89,7 @@ rsrs_status fail(rsrs_status st, const std::string& msg) {
 
 bool tune_valid(const rsrs_tune_t& t) {
   const int c = t.cpqr_cluster, th = t.cpqr_threads;
-  bool ok = t.sample_tile >= 0 && t.sample_tile <= RSRS_SAMPLE_TILE_192x5_K16;
+  bool ok = t.sample_tile >= 0 && t.sample_tile <= RSRS_SAMPLE_TILE_2x192x4_K16;
   ok = ok && (c == 0 || c == 2 || c == 4 || c == 8 || c == 16);
   ok = ok && (th == 0 || th == 256 || th == 512 || th == 1024);
   ok = ok && t.residual_split >= 0 && t.residual_split <= 16;
@@ -1299,10 +1299,11 @@ extern "C" rsrs_status rsrs_autotune(int nprob, const rsrs_tree* const* trees, c
   }
   if (tune_sample) {
     double bt = cur[RSRS_K_SAMPLE];
-    const int cand[] = {RSRS_SAMPLE_TILE_256x4_K16, RSRS_SAMPLE_TILE_256x2, RSRS_SAMPLE_TILE_128x3,
-                        RSRS_SAMPLE_TILE_192x2, RSRS_SAMPLE_TILE_192x5_K16};
+    const int cand[] = {RSRS_SAMPLE_TILE_2x256x3_K16, RSRS_SAMPLE_TILE_2x192x4_K16, RSRS_SAMPLE_TILE_256x4_K16,
+                        RSRS_SAMPLE_TILE_256x2, RSRS_SAMPLE_TILE_128x3, RSRS_SAMPLE_TILE_192x2,
+                        RSRS_SAMPLE_TILE_192x5_K16};
     for (int v : cand) {
-      if (v == best.sample_tile || (v == RSRS_SAMPLE_TILE_256x4_K16 && best.sample_tile == 0)) continue;
+      if (v == best.sample_tile || (v == RSRS_SAMPLE_TILE_2x256x3_K16 && best.sample_tile == 0)) continue;
       rsrs_tune_t t = best;
       t.sample_tile = v;
       st = time_build(t, cls);

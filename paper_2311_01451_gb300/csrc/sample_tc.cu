@@ -5,20 +5,22 @@
 // tensor memory.  The split follows Ootomo & Yokota (2022); products are then accurate to about
 // 2^-21 relative, the level of the FP32 arithmetic of the rest of the mixed path.
 //
-// Tile: D = 128 rows (TMEM lanes) x TN <= 256 columns (TMEM columns); KT points j per stage.
-//   A_hi, A_lo: K(x_i, x_j) for the 128 rows, generated by 16 producer warps (K-major rows of KT
+// Tile: RH accumulators of 128 rows (TMEM lanes) x TN <= 256 columns (TMEM columns) per CTA, i.e.
+// RH*128 rows that share every B stage; KT points j per stage.
+//   A_hi, A_lo: K(x_i, x_j) for the RH*128 rows, generated by 16 producer warps (K-major rows of KT
 //               TF32 values: 128-byte rows with the 128-byte swizzle for KT = 32, 64-byte rows
-//               with the 64-byte swizzle for KT = 16);
+//               with the 64-byte swizzle for KT = 16; the 128-row halves are consecutive atoms);
 //   B_hi, B_lo: in[j][c] for the tile's columns, from hi/lo planes split and transposed once
 //               before the product (FP64 -> FP32 conversion runs at FP64 rate on this part, so it
-//               must not sit in the inner loop), fetched by TMA straight into the same swizzled
-//               layout (the tensor map's swizzle is the canonical K-major one); the two CTAs of a
-//               cluster each load half of the columns and multicast it to both.
-// A seventeenth warp issues, from one thread, the TMA copies and the KT/8 K-steps x 3 products per
-// stage.  NST stages (default: TN = 256, KT = 16, four stages); per stage three mbarriers: A
-// written (512 arrivals), B landed (TMA transaction bytes) and stage free (tcgen05.commit of the
-// products of both CTAs that read it).  The copies of chunk c + NST - 1 are armed once the
-// products of chunk c - 1 are done, so the B tiles arrive NST - 1 products ahead.  Chunks that
+//               must not sit in the inner loop), fetched by one TMA copy per plane and stage
+//               straight into the same swizzled layout (the tensor map's swizzle is the canonical
+//               K-major one).  Each CTA loads its own B tile from this GPU's memory; with RH = 2
+//               one B tile feeds 256 rows, which halves the B traffic per product.
+// A seventeenth warp issues, from one thread, the TMA copies and the KT/8 K-steps x 3 x RH products
+// per stage.  NST stages (default: RH = 2, TN = 256, KT = 16, three stages); per stage three
+// mbarriers: A written (512 arrivals), B landed (TMA transaction bytes) and stage free
+// (tcgen05.commit of the products that read it).  The copies of chunk c + NST - 1 are armed once
+// the products of chunk c - 1 are done, so the B tiles arrive NST - 1 products ahead.  Chunks that
 // overlap the row tile (K_ii = 0) or hold the last points test indices; the others do not.  Every
 // wait is bounded: on expiry the kernel records kDevTimeout, waits (bounded) for its own copies
 // still in flight, frees its TMEM and returns.
@@ -59,17 +61,25 @@ struct Lay<16> {
     return (uint32_t)(row * 64 + (((k >> 2) ^ ((row >> 1) & 3)) << 4) + (k & 3) * 4);
   }
 };
-// One variant: column tile TN, points per stage KT and pipeline depth NST: stages of A_hi, A_lo
-// (128 x KT) and B_hi, B_lo (TN x KT); the TMEM accumulator takes the next power of two >= TN.
-template <int TN, int KT, int NST>
+// One variant: column tile TN, points per stage KT, pipeline depth NST and RH accumulators of 128
+// rows: stages of A_hi, A_lo (RH*128 x KT) and B_hi, B_lo (TN x KT); each accumulator takes the next
+// power of two >= TN TMEM columns.
+template <int TN, int KT, int NST, int RH>
 struct Tile {
-  static constexpr int A_BYTES = TM * KT * 4;
+  static constexpr int MR = RH * TM;  // rows per CTA
+  static constexpr int AH_BYTES = TM * KT * 4;  // one 128-row half of one A plane
+  static constexpr int A_BYTES = RH * AH_BYTES;
   static constexpr int B_BYTES = TN * KT * 4;
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
   static constexpr int SMEM_BYTES = NST * STAGE_BYTES + 1024;  // + alignment slack
-  static constexpr uint32_t TMEM_COLS = TN <= 32 ? 32 : TN <= 64 ? 64 : TN <= 128 ? 128 : 256;
-  static_assert(TN % 32 == 0 && TN >= 32 && TN <= 256, "MMA N and the multicast halves");
+  static constexpr uint32_t ACC_COLS = TN <= 32 ? 32 : TN <= 64 ? 64 : TN <= 128 ? 128 : 256;
+  static constexpr uint32_t TMEM_COLS = RH * ACC_COLS;
+  static constexpr int VPT = MR * KT / 512;  // kernel values per producer thread and stage
+  static_assert(TN % 32 == 0 && TN >= 32 && TN <= 256, "MMA N and the TMA box height");
   static_assert(KT == 16 || KT == 32, "K-slice of one stage");
+  static_assert(RH == 1 || RH == 2, "one or two 128-row accumulators");
+  static_assert(TMEM_COLS <= 512, "tensor memory columns");
+  static_assert(VPT % 4 == 0 && KT % VPT == 0, "producer values per thread");
   static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per CTA");
 };
 constexpr int NTHREADS = NPROD + 32;                      // + the TMA / MMA warp
@@ -108,15 +118,6 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
 }
-// The completion of this CTA's issued products arrives on the mbarrier at the same offset in every
-// CTA of the cluster pair (both read the stage's B tile halves that the pair loaded together).
-__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
-      "h"((uint16_t)3)
-      : "memory");
-}
-
 __device__ __forceinline__ void bar_init(uint32_t bar, int count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
@@ -142,22 +143,14 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
-// 2D tiled TMA load of box (TK points x half a column tile) at (x = first point, y = first column),
-// multicast to the same shared-memory offset (and mbarrier) in both CTAs of the cluster pair.
-__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+// 2D tiled TMA load of box (KT points x TN columns) at (x = first point, y = first column) into
+// this CTA's shared memory, completing on this CTA's mbarrier.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, "
-      "%3}], [%4], %5;" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"((uint16_t)3)
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
       : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
@@ -171,23 +164,25 @@ __device__ __forceinline__ float kvalf_tc(float r2) {
 // p32: the points in FP32, n rounded up to a multiple of TK and zero padded (so that every
 // producer load of a chunk stays in bounds).  Columns [0, ncols0) read in0 / write out0, columns
 // [ncols0, ncols) read in1 / write out1 (column c - ncols0); all four are row-major with ld.
-template <int KIND, int D, int TN, int KT, int NST>
+template <int KIND, int D, int TN, int KT, int NST, int RH>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_kmv_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
              const float* __restrict__ p32, int64_t n, double shift, double scale, const double* __restrict__ in0,
              const double* __restrict__ in1, double* __restrict__ out0, double* __restrict__ out1, int64_t ld,
              int64_t ncols0, int64_t ncols, int* err) {
-  using C = Tile<TN, KT, NST>;
-  constexpr int A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES, STAGE_BYTES = C::STAGE_BYTES;
-  constexpr int VPT = KT / 4;  // kernel values per producer thread and stage
-  constexpr uint32_t TMEM_COLS = C::TMEM_COLS;
+  using C = Tile<TN, KT, NST, RH>;
+  constexpr int MR = C::MR, AH_BYTES = C::AH_BYTES, A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES;
+  constexpr int STAGE_BYTES = C::STAGE_BYTES;
+  constexpr int VPT = C::VPT;       // kernel values per producer thread and stage
+  constexpr int TPR = KT / VPT;     // producer threads per row
+  constexpr uint32_t TMEM_COLS = C::TMEM_COLS, ACC_COLS = C::ACC_COLS;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_a[NST], full_b[NST], empty[NST];
   __shared__ uint32_t s_tmem;
   __shared__ int s_timeout;
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t i0 = (int64_t)blockIdx.x * TM, c0 = (int64_t)blockIdx.y * TN;
+  const int64_t i0 = (int64_t)blockIdx.x * MR, c0 = (int64_t)blockIdx.y * TN;
   const int ntile = (int)(ncols - c0 < TN ? ncols - c0 : TN);
   const int nmma = (ntile + 15) & ~15;  // MMA N: a multiple of 16 in [16, TN]
   const int64_t nchunk = (n + KT - 1) / KT;
@@ -197,7 +192,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int s = 0; s < NST; ++s) {
       bar_init(smem_u32(&full_a[s]), NPROD);
       bar_init(smem_u32(&full_b[s]), 1);
-      bar_init(smem_u32(&empty[s]), 2);  // the products of both CTAs of the pair
+      bar_init(smem_u32(&empty[s]), 1);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -211,14 +206,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
-  const uint32_t crank = cluster_rank();
-  // the partner must have initialised its barriers before any multicast reaches them
-  cluster_sync_all();
 
   if (warp < NPROD / 32) {
-    // ---- producers: kernel values of row arow, points akq..akq+7 of each chunk; the points of the
-    // next chunk are loaded while this chunk's values are computed ----
-    const int arow = tid >> 2, akq = (tid & 3) * VPT;
+    // ---- producers: kernel values of row arow, points akq..akq+VPT-1 of each chunk; the points of
+    // the next chunk are loaded while this chunk's values are computed ----
+    const int arow = tid / TPR, akq = (tid % TPR) * VPT;
     const int64_t gi = i0 + arow;
     const int gi32 = (int)gi;
     float pi[D];
@@ -250,7 +242,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // or hold the last points (block-uniform); rows beyond n are never stored, so their values
       // need no check
       const int64_t jc = ch * KT;
-      const bool check = (jc < i0 + TM && jc + KT > i0) || jc + KT > n;
+      const bool check = (jc < i0 + MR && jc + KT > i0) || jc + KT > n;
       auto gen = [&](auto check_tag) {
         constexpr bool CHECK = decltype(check_tag)::value;
 #pragma unroll
@@ -273,6 +265,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             hv[w] = tf32_hi(v);
             lv[w] = v - hv[w];
           }
+          // rows 128.. of a stage are the next 128-row atoms of the same swizzled layout
           const uint32_t off = Lay<KT>::off(arow, akq + q * 4);
           *reinterpret_cast<float4*>(Ahi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
           *reinterpret_cast<float4*>(Alo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
@@ -301,12 +294,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int st = (int)(ch % NST);
       unsigned char* Bhi = smem + st * STAGE_BYTES + 2 * A_BYTES;
       const uint32_t bar = smem_u32(&full_b[st]);
-      // this CTA loads half of the columns of the B tile for both CTAs of the pair; the stage's
-      // barrier counts the bytes of both halves of both planes
+      // the whole B tile of both planes, loaded by this CTA for its own products
       bar_expect_tx(bar, 2u * B_BYTES);
-      const uint32_t half = crank * (B_BYTES / 2);
-      tma_load_2d_pair(smem_u32(Bhi) + half, &tm_hi, (int)(ch * KT), (int)(c0 + crank * (TN / 2)), bar);
-      tma_load_2d_pair(smem_u32(Bhi + B_BYTES) + half, &tm_lo, (int)(ch * KT), (int)(c0 + crank * (TN / 2)), bar);
+      tma_load_2d(smem_u32(Bhi), &tm_hi, (int)(ch * KT), (int)c0, bar);
+      tma_load_2d(smem_u32(Bhi + B_BYTES), &tm_lo, (int)(ch * KT), (int)c0, bar);
       armed[st] = true;
       armed_par[st] = (uint32_t)((ch / NST) & 1);
     };
@@ -324,11 +315,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
       for (int kk = 0; kk < KT / 8; ++kk) {  // K = 8 TF32 values (32 bytes) per instruction
         const uint32_t ko = kk * 32;
-        mma_tf32(tmem, smem_desc<KT>(a_hi + ko), smem_desc<KT>(b_hi + ko), idesc, (ch > 0 || kk > 0) ? 1u : 0u);
-        mma_tf32(tmem, smem_desc<KT>(a_hi + ko), smem_desc<KT>(b_lo + ko), idesc, 1u);
-        mma_tf32(tmem, smem_desc<KT>(a_lo + ko), smem_desc<KT>(b_hi + ko), idesc, 1u);
+        const uint64_t bh = smem_desc<KT>(b_hi + ko), bl = smem_desc<KT>(b_lo + ko);
+#pragma unroll
+        for (int h = 0; h < RH; ++h) {  // both accumulators read the same B stage
+          const uint32_t td = tmem + (uint32_t)h * ACC_COLS, ho = (uint32_t)h * AH_BYTES + ko;
+          mma_tf32(td, smem_desc<KT>(a_hi + ho), bh, idesc, (ch > 0 || kk > 0) ? 1u : 0u);
+          mma_tf32(td, smem_desc<KT>(a_hi + ho), bl, idesc, 1u);
+          mma_tf32(td, smem_desc<KT>(a_lo + ho), bh, idesc, 1u);
+        }
       }
-      mma_commit_pair(smem_u32(&empty[st]));
+      mma_commit(smem_u32(&empty[st]));
       const int64_t nxt = ch + NST - 1;
       if (nxt < nchunk) {
         // chunk nxt reuses the stage of chunk ch - 1: free once that chunk's products are done
@@ -350,32 +346,37 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp < NPROD / 32 && nchunk > 0) {
-    // epilogue: warp w reads TMEM lanes 32*(w%4).. (its rows), columns (w/4)*64 .. +64
-    const int row = 32 * (warp & 3) + lane;
-    const int64_t gi = i0 + row;
+    // epilogue: warp w reads TMEM lanes 32*(w%4).. (its rows), columns (w/4)*64 .. +64 of each
+    // accumulator
     const int colbase = (warp >> 2) * 64;
-    for (int cc = 0; cc < 64; cc += 16) {
-      if (colbase + cc >= nmma) break;  // warp-uniform
-      uint32_t r[16];
-      const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(colbase + cc);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-          "%14, %15}, [%16];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(taddr)
-          : "memory");
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (gi < n) {
+#pragma unroll 1
+    for (int h = 0; h < RH; ++h) {
+      const int row = h * TM + 32 * (warp & 3) + lane;
+      const int64_t gi = i0 + row;
+      for (int cc = 0; cc < 64; cc += 16) {
+        if (colbase + cc >= nmma) break;  // warp-uniform
+        uint32_t r[16];
+        const uint32_t taddr =
+            tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)h * ACC_COLS + (uint32_t)(colbase + cc);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (gi < n) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int64_t gc = c0 + colbase + cc + q;
-          if (gc < ncols) {
-            const bool first = gc < ncols0;
-            const int64_t c = first ? gc : gc - ncols0;
-            const double* in = first ? in0 : in1;
-            double* out = first ? out0 : out1;
-            out[gi * ld + c] = shift * in[gi * ld + c] + scale * (double)__uint_as_float(r[q]);
+          for (int q = 0; q < 16; ++q) {
+            const int64_t gc = c0 + colbase + cc + q;
+            if (gc < ncols) {
+              const bool first = gc < ncols0;
+              const int64_t c = first ? gc : gc - ncols0;
+              const double* in = first ? in0 : in1;
+              double* out = first ? out0 : out1;
+              out[gi * ld + c] = shift * in[gi * ld + c] + scale * (double)__uint_as_float(r[q]);
+            }
           }
         }
       }
@@ -383,8 +384,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  // neither CTA leaves while its partner may still signal its barriers
-  cluster_sync_all();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   if (tid == 0 && s_timeout && err) atomicCAS(err, 0, kDevTimeout);
 }
@@ -415,22 +414,22 @@ EncodeTiled encode_fn() {
 }
 
 // Tensor map of one plane: ncols rows of n FP32 values, row pitch ldp values (ldp % 4 == 0 so that
-// the pitch is a multiple of 16 bytes); box = TK values x half a column tile (each CTA of a pair
-// loads one half), 128-byte swizzle, zero fill outside [0, n) x [0, ncols).
+// the pitch is a multiple of 16 bytes); box = KT values x a whole column tile, the swizzle of the
+// KT-point layout, zero fill outside [0, n) x [0, ncols).
 bool plane_map(CUtensorMap* m, const float* base, int64_t n, int64_t ncols, int64_t ldp, int tn, int kt,
                CUtensorMapSwizzle swz) {
   EncodeTiled enc = encode_fn();
   if (!enc || (ldp & 3) || ((uintptr_t)base & 15)) return false;
   cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)ncols};
   cuuint64_t strides[1] = {(cuuint64_t)ldp * sizeof(float)};
-  cuuint32_t box[2] = {(cuuint32_t)kt, (cuuint32_t)(tn / 2)};
+  cuuint32_t box[2] = {(cuuint32_t)kt, (cuuint32_t)tn};
   cuuint32_t estr[2] = {1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
              CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int TN, int KT, int NST>
+template <int TN, int KT, int NST, int RH>
 bool launch_variant(cudaStream_t st, int kind, const float* p32, int64_t n, double shift, double scale,
                     const double* in0, const double* in1, double* out0, double* out1, int64_t ld, int64_t ncols0,
                     int64_t ncols, const float* bhi, const float* blo, int64_t ldp, int* err) {
@@ -438,32 +437,22 @@ bool launch_variant(cudaStream_t st, int kind, const float* p32, int64_t n, doub
   if (!plane_map(&mh, bhi, n, ncols, ldp, TN, KT, Lay<KT>::TMA_SWIZZLE) ||
       !plane_map(&ml, blo, n, ncols, ldp, TN, KT, Lay<KT>::TMA_SWIZZLE))
     return false;
-  constexpr int SMEM = Tile<TN, KT, NST>::SMEM_BYTES;
+  using C = Tile<TN, KT, NST, RH>;
+  constexpr int SMEM = C::SMEM_BYTES;
   static std::once_flag attr;
   std::call_once(attr, [] {
-    cudaFuncSetAttribute(k_kmv_tc<RSRS_OP_LOG2D, 2, TN, KT, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-    cudaFuncSetAttribute(k_kmv_tc<RSRS_OP_INVR3D, 3, TN, KT, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    cudaFuncSetAttribute(k_kmv_tc<RSRS_OP_LOG2D, 2, TN, KT, NST, RH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         SMEM);
+    cudaFuncSetAttribute(k_kmv_tc<RSRS_OP_INVR3D, 3, TN, KT, NST, RH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         SMEM);
   });
-  // row tiles in pairs (one thread-block cluster each) that share the B tile of their column tile
-  const unsigned gx = (unsigned)(((n + TM - 1) / TM + 1) / 2 * 2);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(gx, (unsigned)((ncols + TN - 1) / TN));
-  cfg.blockDim = dim3(NTHREADS);
-  cfg.dynamicSmemBytes = SMEM;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 2;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
+  const dim3 grid((unsigned)((n + C::MR - 1) / C::MR), (unsigned)((ncols + TN - 1) / TN));
   if (kind == RSRS_OP_LOG2D)
-    cudaLaunchKernelEx(&cfg, k_kmv_tc<RSRS_OP_LOG2D, 2, TN, KT, NST>, mh, ml, p32, n, shift, scale, in0, in1, out0,
-                       out1, ld, ncols0, ncols, err);
+    k_kmv_tc<RSRS_OP_LOG2D, 2, TN, KT, NST, RH><<<grid, NTHREADS, SMEM, st>>>(mh, ml, p32, n, shift, scale, in0, in1,
+                                                                               out0, out1, ld, ncols0, ncols, err);
   else
-    cudaLaunchKernelEx(&cfg, k_kmv_tc<RSRS_OP_INVR3D, 3, TN, KT, NST>, mh, ml, p32, n, shift, scale, in0, in1, out0,
-                       out1, ld, ncols0, ncols, err);
+    k_kmv_tc<RSRS_OP_INVR3D, 3, TN, KT, NST, RH><<<grid, NTHREADS, SMEM, st>>>(mh, ml, p32, n, shift, scale, in0, in1,
+                                                                                out0, out1, ld, ncols0, ncols, err);
   return true;
 }
 
@@ -484,27 +473,20 @@ bool launch_kernel_matvec_tc(Launch L, int kind, const float* p32, int64_t n, do
                              int variant) {
   if (n <= 0 || ncols <= 0) return true;
   bool ok;
+#define RSRS_KMV_TC(TN, KT, NST, RH)                                                                              \
+  launch_variant<TN, KT, NST, RH>(L.st, kind, p32, n, shift, scale, in0, in1, out0, out1, ld, ncols0, ncols, bhi, \
+                                  blo, ldp, err)
   switch (variant) {
-    case RSRS_SAMPLE_TILE_128x3:
-      ok = launch_variant<128, 32, 3>(L.st, kind, p32, n, shift, scale, in0, in1, out0, out1, ld, ncols0, ncols, bhi,
-                                      blo, ldp, err);
-      break;
-    case RSRS_SAMPLE_TILE_192x2:
-      ok = launch_variant<192, 32, 2>(L.st, kind, p32, n, shift, scale, in0, in1, out0, out1, ld, ncols0, ncols, bhi,
-                                      blo, ldp, err);
-      break;
-    case RSRS_SAMPLE_TILE_256x2:
-      ok = launch_variant<256, 32, 2>(L.st, kind, p32, n, shift, scale, in0, in1, out0, out1, ld, ncols0, ncols, bhi,
-                                      blo, ldp, err);
-      break;
-    case RSRS_SAMPLE_TILE_192x5_K16:
-      ok = launch_variant<192, 16, 5>(L.st, kind, p32, n, shift, scale, in0, in1, out0, out1, ld, ncols0, ncols, bhi,
-                                      blo, ldp, err);
-      break;
-    default:  // RSRS_SAMPLE_TILE_256x4_K16: four stages keep the B-tile copies two products ahead
-      ok = launch_variant<256, 16, 4>(L.st, kind, p32, n, shift, scale, in0, in1, out0, out1, ld, ncols0, ncols, bhi,
-                                      blo, ldp, err);
+    case RSRS_SAMPLE_TILE_128x3: ok = RSRS_KMV_TC(128, 32, 3, 1); break;
+    case RSRS_SAMPLE_TILE_192x2: ok = RSRS_KMV_TC(192, 32, 2, 1); break;
+    case RSRS_SAMPLE_TILE_256x2: ok = RSRS_KMV_TC(256, 32, 2, 1); break;
+    case RSRS_SAMPLE_TILE_256x4_K16: ok = RSRS_KMV_TC(256, 16, 4, 1); break;
+    case RSRS_SAMPLE_TILE_192x5_K16: ok = RSRS_KMV_TC(192, 16, 5, 1); break;
+    case RSRS_SAMPLE_TILE_2x192x4_K16: ok = RSRS_KMV_TC(192, 16, 4, 2); break;
+    default:  // RSRS_SAMPLE_TILE_2x256x3_K16: two accumulators share each B stage
+      ok = RSRS_KMV_TC(256, 16, 3, 2);
   }
+#undef RSRS_KMV_TC
   if (ok && L.counter) ++*L.counter;
   return ok;
 }

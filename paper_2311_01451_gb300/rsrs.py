@@ -38,6 +38,7 @@ class Operator(C.Structure):
 
 RSRS_SAMPLE_TILE_DEFAULT, RSRS_SAMPLE_TILE_256x2, RSRS_SAMPLE_TILE_128x3, RSRS_SAMPLE_TILE_192x2 = 0, 1, 2, 3
 RSRS_SAMPLE_TILE_256x4_K16, RSRS_SAMPLE_TILE_192x5_K16 = 4, 5
+RSRS_SAMPLE_TILE_2x256x3_K16, RSRS_SAMPLE_TILE_2x192x4_K16 = 6, 7
 
 
 class Tune(C.Structure):

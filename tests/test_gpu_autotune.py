@@ -34,7 +34,7 @@ def _to_gpu(b):
 
 @pytest.mark.parametrize("d,kind,n,s", [(2, "log2d", 1000, 1100), (3, "invr3d", 777, 800), (2, "log2d", 21, 40),
                                         (2, "log2d", 200, 216)])
-@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7])
 def test_sample_tiles_match_default_and_fp64(R, d, kind, n, s, tile):
     pts = W.uniform_points(n, d, W.rng_for(98, n, 1))
     rng = np.random.default_rng(n + 1)
@@ -87,7 +87,7 @@ def test_autotune_cache_roundtrip(R, tmp_path):
     tune, rep = R.autotune(tree, R.RSRS_OP_LOG2D, pr.k, s, pr.diag_shift, pr.scale, reps=1, cache=cache)
     assert not rep["from_cache"] and rep["candidates"] >= 10
     assert 0 < rep["tuned_ms"] <= rep["default_ms"] * 1.05
-    assert tune["sample_tile"] in (0, 1, 2, 3, 4, 5) and tune["cpqr_cluster"] in (0, 2, 4, 8, 16)
+    assert tune["sample_tile"] in (0, 1, 2, 3, 4, 5, 6, 7) and tune["cpqr_cluster"] in (0, 2, 4, 8, 16)
     again, rep2 = R.autotune(tree, R.RSRS_OP_LOG2D, pr.k, s, pr.diag_shift, pr.scale, reps=1, cache=cache)
     assert rep2["from_cache"] and rep2["candidates"] == 0 and again == tune
     with open(cache) as fh:

@@ -107,7 +107,7 @@ def test_undersampled_rejected_before_device_work(R):
     assert e.value.name == "RSRS_E_INVAL"
 
 
-@pytest.mark.parametrize("tune", [{"sample_tile": 6}, {"cpqr_cluster": 3}, {"cpqr_threads": 100},
+@pytest.mark.parametrize("tune", [{"sample_tile": 8}, {"cpqr_cluster": 3}, {"cpqr_threads": 100},
                                   {"residual_split": 17}, {"sample_tile": -1}])
 def test_tune_values_validated_before_device_work(R, tune):
     t = R.Tree(W.grid_points_2d(64), 64)
