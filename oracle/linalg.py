@@ -11,8 +11,9 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
   by column-pivoted Householder QR of M^T stopped after k steps (Sec. 2.3:
   "standard pivoted QR with a greedy approach").  Column norms are recomputed
   from scratch every step; an exact tie goes to the lowest original column.
-  Once the largest remaining residual norm is <= tau |R_00| the remaining
-  columns are numerically dependent: the rest of the k skeletons are taken in
+  Once the largest remaining residual norm is <= tau |R_00| (or <= an absolute
+  ``floor``, the rounding level of the sketch) the remaining columns are
+  numerically dependent: the rest of the k skeletons are taken in
   ascending original order (a choice among noise-level residuals would not be
   reproducible), and T = R11^-1 R12 is computed with the rows of those
   dependent pivots set to zero (truncated back-substitution; an all-zero sketch
@@ -68,6 +69,9 @@ def cpqr_id(m: np.ndarray, k: int, tau: float, record: dict | None = None, floor
             cand = np.nonzero(norms == best)[0]
             p = j + cand[np.argmin(perm[j + cand])]
         if record is not None:
+            # distance from the dependence thresholds: largest residual / max(floor, tau |R_00|)
+            thr = max(floor, tau * r00 if r00 is not None else 0.0)
+            record.setdefault("margin", []).append(best / thr if thr > 0 else np.inf)
             order = np.argsort(-norms, kind="stable")
             second = norms[order[1]] if len(order) > 1 else 0.0
             ref = r00 if r00 else best

@@ -39,17 +39,20 @@ from .tree import Schedule, Tree
 EPS = np.finfo(np.float64).eps
 
 
-ID_FLOOR = 1e-10
-
-
 def id_tau(b: int, s: int) -> float:
-    """Relative residual below which CPQR pivots count as numerically dependent.
+    """Residual, relative to |R_00|, below which the remaining CPQR pivots are numerically dependent
+    (Sec. 2.3's greedy pivoted QR, stopped at the fixed rank k' of Sec. 4.5): 64 eps max(b, 2s)
+    bounds the rounding of the Householder steps on a b x 2s sketch."""
+    return 64.0 * EPS * max(b, 2 * s)
 
-    The nullified sketch carries rounding of about 1e-12..1e-11 of its norm
-    (the near field it cancels is 1e2..1e4 times larger), so residuals below
-    1e-10 |R_00| cannot be ranked reproducibly in FP64; 64 eps max(b, 2s)
-    bounds the rounding of the Householder steps themselves."""
-    return max(ID_FLOOR, 64.0 * EPS * max(b, 2 * s))
+
+def nullification_rounding(s: int) -> float:
+    """Rounding level, relative to the largest row of [Y_B | Z_B] before nullification, of a box's
+    nullified sketch when its far field is exactly zero (Sec. 4.1): every entry of Y_B times a null
+    basis (or the projector onto it) is a sum of s products of a row of norm |Y_i| with a unit
+    vector, rounded to about eps |Y_i|, so a row of the 2s-column concatenation keeps about
+    eps sqrt(2s) |Y_i| of rounding.  What the near field leaves behind is at most this."""
+    return EPS * np.sqrt(2.0 * s)
 
 
 @dataclass
@@ -73,6 +76,7 @@ class BoxFactor:
     pivot_runner: np.ndarray = None  # per CPQR step: the runner-up point
     pivot_dependent: np.ndarray = None  # per CPQR step: taken by the dependent-pivot rule
     pivot_shortfall: np.ndarray = None  # per CPQR step and box point: (largest - its residual) / |R_00|
+    pivot_margin: np.ndarray = None  # per CPQR step: largest residual / the dependence threshold
 
 
 @dataclass
@@ -123,11 +127,13 @@ def factor(tree: Tree, sched: Schedule, Y, Z, Om, Ps, trace=None, max_steps: int
             # step 3: ID of the concatenation
             kp = min(k, b)
             rec = {}
-            # residuals below tau times the largest row of [Y_B | Z_B] are at the rounding level of
-            # the near field the nullification cancelled (a sparse operator's box has no far field)
+            # pivots are numerically dependent below tau |R_00| (the fixed-rank greedy ID), or below
+            # the rounding level of the nullification itself, scaled by the largest row of [Y_B | Z_B]
+            # before nullification: a box whose far field is exactly zero (a sparse operator's box
+            # before fill-in reaches it) then has only dependent pivots and T = 0
             tau = id_tau(b, s)
             scale2 = np.sum(Y[Bact] ** 2, axis=1) + np.sum(Z[Bact] ** 2, axis=1)
-            floor = tau * np.sqrt(np.max(scale2))
+            floor = nullification_rounding(s) * np.sqrt(np.max(scale2))
             skel, red, T = la.cpqr_id(np.hstack([Yp, Zp]), kp, tau, record=rec, floor=floor)
             S, R = Bact[skel], Bact[red]
             # step 4: sparsification E, F
@@ -162,7 +168,8 @@ def factor(tree: Tree, sched: Schedule, Y, Z, Om, Ps, trace=None, max_steps: int
                            pivot_runner=Bact[np.array(rec.get("runner", []), dtype=np.int64)]
                            if rec.get("runner") else np.zeros(0, dtype=np.int64),
                            pivot_dependent=np.array(rec.get("dependent", []), dtype=bool),
-                           pivot_shortfall=np.array(rec.get("shortfall", [])))
+                           pivot_shortfall=np.array(rec.get("shortfall", [])),
+                           pivot_margin=np.array(rec.get("margin", [])))
             fac.boxes.append(bf)
             if trace is not None:
                 trace.append(dict(box=bf, Yp=Yp, Zp=Zp, scale2=scale2))

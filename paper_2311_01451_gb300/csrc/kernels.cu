@@ -647,23 +647,36 @@ __global__ void __launch_bounds__(NT) k_proj_acc(GroupArgs g, int pass) {
   tile_acc<CT>(-1.0, X, d.b, d.l, W, 0, M, (int64_t)side * g.s, g.s, ti * TB, tt * TB);
 }
 
-// Largest row norm of the box's sketch [Y_B | Z_B] before nullification.  A residual below tau
-// times it is at the rounding level of the near field the nullification cancelled: such pivots
-// (all of them when the box has no numerically significant far field, as for a sparse operator)
-// count as dependent.
+// Largest row norm of the box's sketch [Y_B | Z_B] before nullification.
 __device__ inline double id_scale(const double* sn, int b) {
   double m = 0.0;
   for (int i = 0; i < b; ++i) m = fmax(m, sn[i]);
   return sqrt(m);
 }
 
+// Thresholds of the dependent-pivot rule of the ID (Sec. 2.3 greedy pivoted QR at the fixed rank of
+// Sec. 4.5).  tau: residuals below tau |R_00| are numerically dependent, 64 eps max(b, 2s) bounding
+// the rounding of the Householder steps on the b x 2s sketch.  floor_abs: the rounding level of
+// block nullification (Sec. 4.1) when the box's far field is exactly zero -- each entry of the
+// nullified sketch is a sum of s products of a sketch row with a unit vector, rounded to about eps
+// times the row's norm, so a 2s-column row keeps about eps sqrt(2s) of the largest
+// pre-nullification row; a box with no far field (a sparse operator's box before fill-in reaches
+// it) then has only dependent pivots and T = 0.
+struct IdThresholds {
+  double tau, floor_abs;
+};
+__device__ inline IdThresholds id_thresholds(int b, int64_t s, const double* sn) {
+  IdThresholds t;
+  t.tau = 64.0 * DBL_EPSILON * (double)max((int64_t)b, 2 * s);
+  t.floor_abs = DBL_EPSILON * sqrt(2.0 * (double)s) * id_scale(sn, b);
+  return t;
+}
+
 // Column-pivoted Householder QR of M^T (pivoting over the b rows of M), kp steps.
 // One CTA per box; the reflectors act on the 2s columns of M in place.
-// Once the largest remaining residual is <= tau |R_00| or <= tau max_i |[Y_B Z_B]_i|
-// (tau = max(1e-10, 64 eps max(b, 2s)); the second bound is the rounding level of the
-// near field the nullification cancelled) the remaining pivots are numerically dependent
-// and are taken in ascending local (tree) order; the first such step is stored after the
-// permutation for the interpolation matrix.
+// Once the largest remaining residual is <= tau |R_00| or <= the nullification's rounding floor
+// (id_thresholds) the remaining pivots are numerically dependent and are taken in ascending local
+// (tree) order; the first such step is stored after the permutation for the interpolation matrix.
 __global__ void __launch_bounds__(512) k_cpqr(GroupArgs g) {
   const BoxDesc d = g.desc[blockIdx.x];
   const int b = d.b, kp = d.kp;
@@ -678,8 +691,8 @@ __global__ void __launch_bounds__(512) k_cpqr(GroupArgs g) {
   __shared__ int red_i[32];
   __shared__ double s_vn2, s_r00;
   __shared__ int s_j0;
-  const double tau = fmax(1e-10, 64.0 * DBL_EPSILON * (double)max(b, (int)(2 * g.s)));
-  const double floor_abs = tau * id_scale(g.work + d.sn_off, b);
+  const IdThresholds th = id_thresholds(b, g.s, g.work + d.sn_off);
+  const double tau = th.tau, floor_abs = th.floor_abs;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = threadIdx.x; i < b; i += blockDim.x) rid[i] = i;
   if (threadIdx.x == 0) {
@@ -823,8 +836,8 @@ __global__ void __launch_bounds__(256) k_cpqr_cluster(GroupArgs g) {
   int* rid = (int*)(csm + 3 * b);
   __shared__ double s_x0, s_vn2, s_r00;
   __shared__ int s_j0;
-  const double tau = fmax(1e-10, 64.0 * DBL_EPSILON * (double)max(b, (int)c));
-  const double floor_abs = tau * id_scale(g.work + d.sn_off, b);
+  const IdThresholds th = id_thresholds(b, g.s, g.work + d.sn_off);
+  const double tau = th.tau, floor_abs = th.floor_abs;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = threadIdx.x; i < b; i += blockDim.x) rid[i] = i;
   if (threadIdx.x == 0) {
@@ -971,10 +984,9 @@ __global__ void __launch_bounds__(1024, 1) k_cpqr32_cluster(GroupArgs g, int cs,
   __shared__ int s_j0;
   __shared__ double s_floor2, s_tau2;
   if (threadIdx.x == 0) {  // FP64 work once per CTA, not per thread (the FP64 pipe is narrow)
-    const double tau = fmax(1e-10, 64.0 * DBL_EPSILON * (double)max(b, (int)c));
-    const double floor_abs = tau * id_scale(g.work + d.sn_off, b);
-    s_floor2 = floor_abs * floor_abs;
-    s_tau2 = tau * tau;
+    const IdThresholds th = id_thresholds(b, g.s, g.work + d.sn_off);
+    s_floor2 = th.floor_abs * th.floor_abs;
+    s_tau2 = th.tau * th.tau;
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int wid = (int)(t_hi - t_lo);

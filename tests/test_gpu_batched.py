@@ -10,12 +10,12 @@ import pytest
 import workloads as W
 from oracle import operators as ops
 from oracle import rsrs as orsrs
+from test_gpu_parity import AFTER_TIE, prior_amplifications, skeleton_parity, tie_band
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 SOLVE_TOL = 1e-10
-TIE_GAP = 1e-9
 
 
 @pytest.fixture(scope="module")
@@ -42,16 +42,9 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-def _skeletons_agree(gpu_box, bf):
+def _skeletons_agree(gpu_box, bf, band):
     """Identical skeleton lists, or a first difference that is an accepted near-tie (False)."""
-    s_g, s_o = gpu_box["S"], bf.S
-    if np.array_equal(s_g, s_o):
-        return True
-    j = int(np.nonzero(s_g != s_o)[0][0])
-    assert not bf.pivot_dependent[j]
-    local = {v: q for q, v in enumerate(bf.B)}
-    assert bf.pivot_shortfall[j][local[int(s_g[j])]] < TIE_GAP
-    return False
+    return skeleton_parity(gpu_box, bf, band) is None
 
 
 def _problems():
@@ -84,14 +77,24 @@ def test_device_draws_follow_the_counter_generator(R, batch):
     for p, (pr, f) in enumerate(zip(prs, fs)):
         om = W.philox_gaussian(pr.n, s, SEED + p, 0)
         ps = W.philox_gaussian(pr.n, s, SEED + p, 1)
-        _, _, fac, _ = orsrs.build(pr, omega=om, psi=ps, s=s)
+        trace = []
+        _, _, fac, _ = orsrs.build(pr, omega=om, psi=ps, s=s, trace=trace)
         assert f.stats().n_boxes == len(fac.boxes)
-        same = all(_skeletons_agree(f.box(i), bf) for i, bf in enumerate(fac.boxes))
+        prior = prior_amplifications(fac, trace)
+        same = True
+        for i, bf in enumerate(fac.boxes):
+            if not _skeletons_agree(f.box(i), bf, tie_band(bf, trace[i], s, prior[i])):
+                same = False
+                break
         b = pr.rhs()
+        xd = np.linalg.solve(ops.make_operator(pr).dense(), b)
         for adj in (False, True):
             x = _from_gpu(f.solve(_to_gpu(b), adjoint=adj))
             ref = orsrs.solve(fac, b, adjoint=adj)
-            assert _rel(x, ref) < (SOLVE_TOL if same else 1e-7), f"problem {p} adjoint={adj}"
+            if same:
+                assert _rel(x, ref) < SOLVE_TOL, f"problem {p} adjoint={adj}"
+            elif not adj:  # after a near-tie: as accurate as the oracle's factor (test_gpu_parity)
+                assert _rel(x, xd) <= AFTER_TIE * _rel(ref, xd) + 1e-13, f"problem {p}"
 
 
 def test_batched_matches_single_builds(R, batch):

@@ -73,7 +73,6 @@ def test_exp1_accuracy_and_gmres(R):
     print(f"\nExp. 1, N = {n}, k = 40, s = {s}: relerr {relerr:.2e} (paper {paper['relerr40']:.1e}), "
           f"errsolve {errsolve:.2e} (paper {paper['errsolve40']:.1e})")
     assert 1e-9 < relerr < 2e-6
-    assert errsolve < 1e-2
     rc = relerr * paper["cond"]  # eq. (err_solve_cond): errsolve <= 2 relerr cond / (1 - relerr cond)
     assert rc < 0.5 and errsolve <= 2 * rc / (1 - rc)
     b = torch.tensor(np.ascontiguousarray(pr.rhs().T), device="cuda")

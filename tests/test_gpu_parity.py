@@ -1,19 +1,24 @@
 """GPU parity: the CUDA path through the C ABI against the CPU oracle on the same seeded inputs.
 
-Tolerances: the FP64 path follows a different but algebraically equivalent
-formulation (projector I - W^T (W W^T)^-1 W with two passes, least squares by
-Cholesky of the Gram; the oracle uses an explicit null basis and QR-based
-pseudoinverses), so results agree to rounding amplified by the conditioning
-of the near-field test rows, cond([Om_B; Om_N]) ~ (sqrt s + sqrt l)/(sqrt s -
-sqrt l) (about 10..100 here, squared by the normal equations), and by the
-conditioning of the ID, cond(R11) = |R_00|/|R_k'k'| (up to 1e10 with the 1e-10
-floor).  Hence: skeleton sets identical; the interpolation matrices compared
-through the well-conditioned reconstruction T^T M_S (1e-10 of ||M||); factor
-blocks and final sketches to 1e-7 relative, or to 1e-14 times the ID's
-amplification where that is larger (points on a line, whose far fields have
-rapidly decaying singular values: T = R11^-1 R12 itself is then determined only
-to about eps cond(R11), while T^T M_S and the solutions still agree);
-solutions to 1e-10.
+Tolerances (with the derivation for ill-conditioned IDs).  The FP64 path follows a
+different but algebraically equivalent formulation (projector I - W^T (W W^T)^-1 W with two passes,
+least squares by Cholesky of the Gram; the oracle uses an explicit null basis and QR-based
+pseudoinverses), so the two nullified sketches agree only to their rounding, about 1e-14 of the
+box's largest pre-nullification row (Sec. 4.1; the oracle's ``nullification_rounding`` level).
+The ID (Sec. 2.3) maps that difference into T = R11^-1 R12 amplified by the box's ID conditioning
+a_B = |[Y_B Z_B]|_rowmax / min |R_jj| over its accepted pivots, and every later block (E/F updates,
+extraction, LU, Schur updates, and the boxes processed after it, which read the updated sketches)
+inherits it.  Hence, per box i in processing order:
+
+    tol_i = max(P9's 1e-11, 1e-14 * max_{j <= i} a_j)
+
+for T, X_RR, Lc, Uc (each compared normwise against the largest entry of its block family in that
+box, so that tiny sub-blocks beside O(1) ones are not compared to their own scale), the final
+sketches and the root block use the case's largest tol_i.  T is also compared through its
+well-conditioned product T^T M_S (1e-10 of |M|), and skeleton sets must be identical except at an
+accepted tie (the two competing residuals within TIE_GAP |R_00| or the rounding floor, or a
+dependent-pivot decision taken at a residual within a factor 2 of its threshold).  Unrefined solutions, their
+adjoints and apply agree to 1e-10.  Every comparison records its worst ratio to its tolerance.
 """
 import numpy as np
 import pytest
@@ -26,48 +31,120 @@ from oracle import rsrs as orsrs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-BLOCK_TOL = 1e-7
+P9_BLOCK_TOL = 1e-11
+ROUNDING = 1e-14    # relative difference of the two implementations' nullified sketches (see above)
 RECON_TOL = 1e-10
 SOLVE_TOL = 1e-10
-TIE_GAP = 1e-9      # top-two residual norms within this fraction of |R_00|: either pivot is correct
-DIVERGED_TOL = 1e-7  # solutions of two valid factorizations that took different near-tie pivots
+TIE_GAP = 1e-10     # top-two residual norms within this fraction of |R_00|: either pivot is correct (P9)
+
+
+def box_amplification(bf, tr):
+    """a_B = |[Y_B Z_B]|_rowmax / (smallest accepted pivot residual) of one box, from the oracle's
+    trace: how much the ID (Sec. 2.3, T = R11^-1 R12) amplifies a perturbation of the nullified
+    sketch."""
+    nd = int(np.sum(~np.asarray(bf.pivot_dependent)))
+    if nd == 0:
+        return 1.0
+    m = np.hstack([tr["Yp"], tr["Zp"]])
+    r = np.linalg.qr(m[[list(bf.B).index(v) for v in bf.S[:nd]]].T, mode="r")
+    scale = np.sqrt(np.max(tr["scale2"]))
+    return max(1.0, scale / np.abs(np.diag(r)).min())
+
+
+def box_tols(fac, trace):
+    """Per-box tolerances tol_i = max(1e-11, 1e-14 max_{j<=i} a_j) (module docstring)."""
+    out, run = [], 1.0
+    for bf, tr in zip(fac.boxes, trace):
+        run = max(run, box_amplification(bf, tr))
+        out.append(max(P9_BLOCK_TOL, ROUNDING * run))
+    return out
 
 
 def id_amplification(fac, trace):
-    """max over boxes of |[Y_B Z_B]|_rowmax / (smallest accepted pivot residual), from the oracle's
-    trace: how much the ID of a box (Sec. 2.3, T = R11^-1 R12) amplifies the rounding of the
-    nullified sketch.  Two correct FP64 implementations agree on T, and on everything computed from
-    T alone, only to about 1e-14 times this factor."""
-    amp = 1.0
-    for bf, tr in zip(fac.boxes, trace):
-        nd = int(np.sum(~np.asarray(bf.pivot_dependent)))
-        if nd == 0:
-            continue
-        m = np.hstack([tr["Yp"], tr["Zp"]])
-        r = np.linalg.qr(m[[list(bf.B).index(v) for v in bf.S[:nd]]].T, mode="r")
-        scale = np.sqrt(np.max(tr["scale2"]))
-        amp = max(amp, scale / np.abs(np.diag(r)).min())
-    return amp
+    """Largest a_B over the case's boxes."""
+    return max([1.0] + [box_amplification(bf, tr) for bf, tr in zip(fac.boxes, trace)])
 
 
 def block_tol(fac, trace):
-    return max(BLOCK_TOL, 1e-14 * id_amplification(fac, trace))
+    return max(P9_BLOCK_TOL, ROUNDING * id_amplification(fac, trace))
 
 
-def skeleton_parity(gpu_box, bf):
-    """Compare skeleton lists.  Returns None when identical, or the step of an accepted near-tie:
-    the GPU took a point whose residual norm is within TIE_GAP |R_00| of the largest at that step of
-    the oracle's CPQR.  Any other difference fails."""
-    s_g, s_o = gpu_box["S"], bf.S
-    if np.array_equal(s_g, s_o):
+def prior_amplifications(fac, trace):
+    """Entry i: max_{j<i} a_j, the amplification that reaches box i's input sketches through the
+    boxes processed before it (1 for the first box)."""
+    out, run = [], 1.0
+    for bf, tr in zip(fac.boxes, trace):
+        out.append(run)
+        run = max(run, box_amplification(bf, tr))
+    return out
+
+
+def tie_band(bf, tr, s, prior_amp=1.0):
+    """Largest residual gap, relative to |R_00|, at which two correct implementations may order two
+    CPQR candidates differently: P9's 1e-10, or what the two implementations' sketches of this box
+    may differ by, where that is larger -- the nullification's rounding (the oracle's floor,
+    eps sqrt(2s) |[Y_B Z_B]|_rowmax) plus the earlier boxes' differences reaching this box's input
+    (ROUNDING x prior_amp of the same row scale).  Residuals closer than that cannot be ordered
+    reproducibly (boxes whose far field is weak, e.g. a sparse operator's boxes that see a little
+    fill, next to boxes whose IDs are ill-conditioned)."""
+    m = np.hstack([tr["Yp"], tr["Zp"]])
+    r00 = np.linalg.norm(m, axis=1).max()
+    pre = np.sqrt(np.max(tr["scale2"]))
+    spread = orsrs.nullification_rounding(s) * pre + ROUNDING * prior_amp * pre
+    return max(TIE_GAP, spread / r00) if r00 > 0 else np.inf
+
+
+THRESHOLD_BAND = 2.0  # a dependence decision within this factor of its threshold may go either way
+# After an accepted tie the two factorizations are different valid approximations of the same accuracy
+# class: the GPU's unrefined solution error against the dense solution must stay within this factor of
+# the oracle's (measured: 1.00 on the 64x64 grid, 2.2 on the 12^3 stencil at k = 8).
+AFTER_TIE = 4.0
+
+
+def _first_dependent(T):
+    """The first pivot from which every row of T is zero: where the dependent-pivot rule started
+    (None when T has no columns and tells nothing)."""
+    if T.shape[1] == 0:
         return None
-    j = int(np.nonzero(s_g != s_o)[0][0])
-    assert not bf.pivot_dependent[j], f"dependent pivots differ at step {j}"
+    nz = np.nonzero(np.any(T != 0, axis=1))[0]
+    return 0 if len(nz) == 0 else int(nz[-1]) + 1
+
+
+def skeleton_parity(gpu_box, bf, band=TIE_GAP):
+    """Compare one box's ID.  Returns None when the skeleton lists and the first dependent pivot
+    (read from the zero rows of T) agree, or the step of an accepted tie:
+
+    * a near-tie: the GPU took a point whose residual norm is within ``band`` |R_00| of the largest
+      at that step of the oracle's CPQR;
+    * a threshold tie: the two took different dependence decisions at a step whose largest residual
+      is within a factor THRESHOLD_BAND of the threshold (tau |R_00| or the rounding floor), where
+      either implementation's rounding can put it on either side.
+
+    Any other difference fails."""
+    s_g, s_o = gpu_box["S"], bf.S
+    kp = len(s_o)
+    js = int(np.nonzero(s_g != s_o)[0][0]) if not np.array_equal(s_g, s_o) else kp
+    dep = np.asarray(bf.pivot_dependent)
+    j0_o = int(np.argmax(dep)) if dep.any() else kp
+    j0_g = _first_dependent(gpu_box["T"])
+    jd = min(j0_g, j0_o) if j0_g is not None and j0_g != j0_o else kp
+    if js == kp and jd == kp:
+        return None
+    if jd <= js:
+        m = bf.pivot_margin[jd]
+        assert 1.0 / THRESHOLD_BAND <= m <= THRESHOLD_BAND, (
+            f"dependence decided differently at step {jd} (gpu from {j0_g}, oracle from {j0_o}); the "
+            f"largest residual is {m:.2e} times the threshold")
+        print(f"accepted threshold tie at step {jd}: residual {m:.2f} x threshold")
+        return jd
+    j = js
+    assert not dep[j], f"dependent pivots differ at step {j}"
     local = {v: q for q, v in enumerate(bf.B)}
     short = bf.pivot_shortfall[j][local[int(s_g[j])]]
-    assert short < TIE_GAP, (
+    assert short < band, (
         f"skeletons differ at step {j}: gpu {s_g[j]}, oracle {s_o[j]} (gpu's pick is {short:.2e} |R_00| "
-        f"below the largest residual)")
+        f"below the largest residual; tie band {band:.1e})")
+    print(f"accepted near-tie at step {j}: gap {short:.2e} |R_00| (band {band:.1e})")
     return j
 
 
@@ -128,36 +205,43 @@ def case(request, R):
 def test_skeletons_and_blocks_match_oracle(case):
     pr, fac, f, _, trace = case
     assert f.stats().n_boxes == len(fac.boxes)
-    if pr.name == "collinear":
-        # Measured on the GB300: boxes 0..232 agree within the tolerance below, but box 233's LcN
-        # (entries at most 1.4e-5, against O(1) entries elsewhere in the box) differs by 3e-4 of
-        # its own largest entry, 4e-9 in absolute terms: a block-by-block relative comparison is
-        # not meaningful for such tiny sub-blocks.  The final sketches, the solves and adjoint
-        # solves, refinement and the mixed path are compared for this case by the other tests.
-        pytest.skip("per-block relative comparison not meaningful for the collinear case's tiny LcN blocks")
-    tol = block_tol(fac, trace)
-    worst = 0.0
+    tols = box_tols(fac, trace)
+    prior = prior_amplifications(fac, trace)
+    worst = (0.0, 0.0, "")  # (error / tolerance, error, where)
     for i, bf in enumerate(fac.boxes):
         g = f.box(i)
-        if skeleton_parity(g, bf) is not None:
+        if skeleton_parity(g, bf, tie_band(bf, trace[i], fac.s, prior[i])) is not None:
+            print(f"{pr.name}: blocks compared up to box {i} (near-tie); worst {worst}")
             return  # an accepted near-tie: later boxes follow a different, equally valid path
         assert np.array_equal(g["R"], bf.R)
         assert np.array_equal(g["N"], bf.N)
-        # the ID through its well-conditioned product: T^T M_S with the oracle's nullified sketch
+        # the ID through its well-conditioned product: T^T M_S with the oracle's nullified sketch,
+        # to 1e-10 of |M| or the box's tolerance where the sketches it reads already differ more
         m = np.hstack([trace[i]["Yp"], trace[i]["Zp"]])
         pos = {v: q for q, v in enumerate(bf.B)}
         ms = m[[pos[v] for v in bf.S]]
         e = np.linalg.norm((g["T"] - bf.T).T @ ms) / np.linalg.norm(m)
-        assert e < RECON_TOL, f"box {i}: T^T M_S differs by {e:.2e}"
-        for nm, ref in (("XRR", bf.XRR), ("LcS", bf.LcS), ("LcN", bf.LcN), ("UcS", bf.UcS),
-                        ("UcN", bf.UcN)):
-            if ref.size:
-                e = np.abs(g[nm] - ref).max() / max(np.abs(ref).max(), 1e-300)
-                worst = max(worst, e)
-                assert e < tol, f"box {i} {nm}: {e:.2e}"
+        rtol = max(RECON_TOL, tols[i])
+        worst = max(worst, (e / rtol, e, f"box {i} T^T M_S"))
+        assert e < rtol, f"box {i}: T^T M_S differs by {e:.2e} (tolerance {rtol:.1e})"
+        for fam in (("T",), ("XRR",), ("LcS", "LcN"), ("UcS", "UcN")):
+            scale = max([np.abs(getattr(bf, nm)).max() for nm in fam if getattr(bf, nm).size] + [0.0])
+            if scale == 0.0:
+                continue
+            for nm in fam:
+                ref = getattr(bf, nm)
+                if ref.size:
+                    e = np.abs(g[nm] - ref).max() / scale
+                    worst = max(worst, (e / tols[i], e, f"box {i} {nm}"))
+                    assert e < tols[i], f"box {i} {nm}: {e:.2e} (tolerance {tols[i]:.1e})"
     idx, a = f.root()
     assert np.array_equal(idx, fac.root)
-    assert np.abs(a - fac.root_A).max() / np.abs(fac.root_A).max() < tol
+    tol = tols[-1] if tols else P9_BLOCK_TOL
+    e = np.abs(a - fac.root_A).max() / np.abs(fac.root_A).max()
+    worst = max(worst, (e / tol, e, "root"))
+    assert e < tol
+    print(f"{pr.name}: worst block error {worst[1]:.2e} at {worst[2]} ({worst[0]:.2e} of its tolerance; "
+          f"tolerances {min(tols, default=tol):.1e}..{tol:.1e})")
 
 
 def test_final_sketches_match_oracle(case):
@@ -165,18 +249,26 @@ def test_final_sketches_match_oracle(case):
     Y, Z, Om, Ps = f.sketches()
     fin = fac.final
     tol = block_tol(fac, trace)
+    worst = 0.0
     for a, b in ((Y, fin["Y"]), (Z, fin["Z"]), (Om, fin["Om"]), (Ps, fin["Ps"])):
-        assert np.abs(a - b).max() / np.abs(b).max() < tol
+        e = np.abs(a - b).max() / np.abs(b).max()
+        worst = max(worst, e)
+        assert e < tol
+    print(f"{pr.name}: final sketches agree to {worst:.2e} (tolerance {tol:.1e})")
 
 
 def test_solve_apply_match_oracle(case):
     pr, fac, f, _, _ = case
     b = pr.rhs()
+    worst = 0.0
     for adj in (False, True):
         x = _from_gpu(f.solve(_to_gpu(b), adjoint=adj))
-        assert _rel(x, orsrs.solve(fac, b, adjoint=adj)) < SOLVE_TOL
+        e1 = _rel(x, orsrs.solve(fac, b, adjoint=adj))
         y = _from_gpu(f.apply(_to_gpu(b), adjoint=adj))
-        assert _rel(y, orsrs.apply(fac, b, adjoint=adj)) < SOLVE_TOL
+        e2 = _rel(y, orsrs.apply(fac, b, adjoint=adj))
+        worst = max(worst, e1, e2)
+        assert e1 < SOLVE_TOL and e2 < SOLVE_TOL
+    print(f"{pr.name}: solve/apply (and adjoints) agree to {worst:.2e}")
     # exact inverse pair on the device
     z = f.apply(f.solve(_to_gpu(b)))
     assert _rel(_from_gpu(z), b) < 1e-12
@@ -227,10 +319,12 @@ def test_mixed_precision_refined_matches_fp64_oracle(R, case):
 
 def test_single_pass_projection_still_matches(R):
     pr = CASES["grid2d_1024"]()
-    tree, sched, fac, _ = orsrs.build(pr)
+    trace = []
+    tree, sched, fac, _ = orsrs.build(pr, trace=trace)
     f = _gpu_factor(R, pr, fac.s, passes=1)
+    prior = prior_amplifications(fac, trace)
     for i, bf in enumerate(fac.boxes):
-        if skeleton_parity(f.box(i), bf) is not None:
+        if skeleton_parity(f.box(i), bf, tie_band(bf, trace[i], fac.s, prior[i])) is not None:
             break
     b = pr.rhs()
     assert _rel(_from_gpu(f.solve(_to_gpu(b))), orsrs.solve(fac, b)) < 1e-8
@@ -249,16 +343,26 @@ def test_root_only_tree(R):
 def test_workload_grid_64x64(R):
     """The 64x64-grid workload (N=4096, leaf 64, k=32) at s = s_req, against the oracle."""
     pr = W.config(0)[0]
-    tree, sched, fac, _ = orsrs.build(pr)
+    trace = []
+    tree, sched, fac, _ = orsrs.build(pr, trace=trace)
     f = _gpu_factor(R, pr, fac.s)
     tie = None
+    prior = prior_amplifications(fac, trace)
     for i, bf in enumerate(fac.boxes):
-        tie = skeleton_parity(f.box(i), bf)
+        tie = skeleton_parity(f.box(i), bf, tie_band(bf, trace[i], fac.s, prior[i]))
         if tie is not None:
             break
     b = pr.rhs()
-    tol = SOLVE_TOL if tie is None else DIVERGED_TOL
-    assert _rel(_from_gpu(f.solve(_to_gpu(b))), orsrs.solve(fac, b)) < tol
+    x_gpu, x_or = _from_gpu(f.solve(_to_gpu(b))), orsrs.solve(fac, b)
+    if tie is None:
+        assert _rel(x_gpu, x_or) < SOLVE_TOL
+    else:
+        # after an accepted near-tie the two factorizations are different valid approximations:
+        # the GPU's must be as accurate as the oracle's against the dense solution
+        xd = np.linalg.solve(ops.make_operator(pr).dense(), b)
+        e_gpu, e_or = _rel(x_gpu, xd), _rel(x_or, xd)
+        print(f"grid 64x64 after a near-tie: unrefined errors gpu {e_gpu:.2e}, oracle {e_or:.2e}")
+        assert e_gpu <= AFTER_TIE * e_or + 1e-13
     # both factorizations reach the dense solution after refinement
     X = torch.zeros_like(_to_gpu(b))
     rep = f.refine(_to_gpu(b), X, rtol=1e-13, maxit=30)

@@ -13,13 +13,12 @@ import pytest
 import workloads as W
 from oracle import operators as ops
 from oracle import rsrs as orsrs
-from test_gpu_parity import id_amplification
+from test_gpu_parity import AFTER_TIE, id_amplification, prior_amplifications, skeleton_parity, tie_band
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 SOLVE_TOL = 1e-10
-TIE_GAP = 1e-9
 
 
 @pytest.fixture(scope="module")
@@ -64,6 +63,13 @@ def test_stencil_rejects_bad_coefficients(R):
 
 
 def test_stencil_fp64_matches_oracle(R):
+    """The 12^3 operator in FP64 against the oracle on the same test matrices.  Skeletons must agree
+    up to an accepted near-tie (tie_band: P9's 1e-10 of |R_00|, or the nullification's rounding
+    level for boxes whose far field is weak fill from eliminated neighbours).  Without a near-tie
+    the unrefined solutions agree to 1e-10 or to the ID's measured amplification of the rounding
+    (derived as in test_gpu_parity); after one, the two factorizations are different valid
+    approximations, and the GPU's unrefined solution must be as accurate as the oracle's against
+    the dense solution."""
     pr = _stencil_problem(12, 27, 8)
     trace = []
     tree_o, sched, fac, _ = orsrs.build(pr, trace=trace)
@@ -72,22 +78,28 @@ def test_stencil_fp64_matches_oracle(R):
     f = R.Factor(t, R.RSRS_OP_CALLBACK, pr.k, fac.s, shift=0.0, scale=1.0, omega=pr.omega(fac.s),
                  psi=pr.psi(fac.s), matvec=st)
     assert f.stats().n_boxes == len(fac.boxes)
-    same = True
+    tie = None
+    prior = prior_amplifications(fac, trace)
     for i, bf in enumerate(fac.boxes):
-        g = f.box(i)
-        if not np.array_equal(g["S"], bf.S):
-            j = int(np.nonzero(g["S"] != bf.S)[0][0])
-            local = {v: q for q, v in enumerate(bf.B)}
-            assert bf.pivot_shortfall[j][local[int(g["S"][j])]] < TIE_GAP
-            same = False
+        tie = skeleton_parity(f.box(i), bf, tie_band(bf, trace[i], fac.s, prior[i]))
+        if tie is not None:
+            print(f"stencil 12^3: tie at box {i} of {len(fac.boxes)} (amplification reaching it "
+                  f"{prior[i]:.1e})")
             break
     b = pr.rhs()
     x = _from_gpu(f.solve(_to_gpu(b)))
     ref = orsrs.solve(fac, b)
-    # some boxes see only a little fill from eliminated neighbours (far fields at 1e-10..1e-4 of
-    # the near field), whose IDs amplify the nullified sketch's rounding
-    tol = max(SOLVE_TOL, 1e-14 * id_amplification(fac, trace))
-    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) < (tol if same else 1e-3)
+    xd = np.linalg.solve(ops.make_operator(pr).dense(), b)
+    if tie is None:
+        tol = max(SOLVE_TOL, 1e-14 * id_amplification(fac, trace))
+        e = np.linalg.norm(x - ref) / np.linalg.norm(ref)
+        print(f"stencil 12^3: unrefined solutions agree to {e:.2e} (tolerance {tol:.1e})")
+        assert e < tol
+    else:
+        e_gpu = np.linalg.norm(x - xd) / np.linalg.norm(xd)
+        e_or = np.linalg.norm(ref - xd) / np.linalg.norm(xd)
+        print(f"stencil 12^3 after a near-tie: unrefined errors gpu {e_gpu:.2e}, oracle {e_or:.2e}")
+        assert e_gpu <= AFTER_TIE * e_or + 1e-13
     # the pair is an exact inverse on the device
     y = _from_gpu(f.apply(f.solve(_to_gpu(b))))
     assert np.linalg.norm(y - b) / np.linalg.norm(b) < 1e-12
@@ -95,7 +107,6 @@ def test_stencil_fp64_matches_oracle(R):
     X = torch.zeros_like(_to_gpu(b))
     rep = f.refine(_to_gpu(b), X, rtol=1e-13, maxit=40)
     assert rep.rel_residual <= 1e-13
-    xd = np.linalg.solve(ops.make_operator(pr).dense(), b)
     assert np.linalg.norm(_from_gpu(X) - xd) / np.linalg.norm(xd) < 1e-10
 
 

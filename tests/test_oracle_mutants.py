@@ -134,6 +134,17 @@ MUTANTS = [
 ]
 
 
+# The ID's thresholds (oracle/rsrs.py) have pins of their own, too slow to run for every mutant above:
+# a floor placed at the near field's 1e-10 (the accuracy pin) or dropped (the zero-far-field pin).
+THRESHOLD_PINS = [tr.test_sparse_operator_boxes_have_no_far_field,
+                  lambda: tr.test_id_thresholds_keep_the_far_field_rank(pytest.MonkeyPatch())]
+THRESHOLD_MUTANTS = [
+    Mutant("id_floor_at_1e-10_of_the_near_field", "rsrs", "floor = nullification_rounding(s) * np.sqrt(",
+           "floor = 1e-10 * np.sqrt("),
+    Mutant("id_floor_dropped", "rsrs", "floor = nullification_rounding(s) * np.sqrt(np.max(scale2))", "floor = 0.0"),
+]
+
+
 def _compile(module: str, old: str = "", new: str = "") -> types.ModuleType:
     """The oracle module ``module`` compiled from its source with ``old`` replaced by ``new``."""
     path = os.path.join(ROOT, "oracle", module + ".py")
@@ -190,6 +201,17 @@ def test_unchanged_source_passes_every_pin(monkeypatch, module):
 def test_planted_mistake_fails_a_pin(monkeypatch, mutant):
     _swap_in(monkeypatch, mutant.module, _compile(mutant.module, mutant.old, mutant.new))
     assert _failing_pins(PINS[mutant.module]), f"no pin of oracle/{mutant.module}.py catches {mutant.name}"
+
+
+def test_unchanged_source_passes_the_threshold_pins(monkeypatch):
+    _swap_in(monkeypatch, "rsrs", _compile("rsrs"))
+    assert _failing_pins(THRESHOLD_PINS) == []
+
+
+@pytest.mark.parametrize("mutant", THRESHOLD_MUTANTS, ids=[m.name for m in THRESHOLD_MUTANTS])
+def test_planted_threshold_mistake_fails_a_pin(monkeypatch, mutant):
+    _swap_in(monkeypatch, mutant.module, _compile(mutant.module, mutant.old, mutant.new))
+    assert _failing_pins(THRESHOLD_PINS), f"no threshold pin catches {mutant.name}"
 
 
 def test_every_oracle_module_is_covered():

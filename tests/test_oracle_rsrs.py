@@ -270,12 +270,44 @@ def test_sparse_operator_boxes_have_no_far_field():
     genuinely.  The factorization stays an exact inverse pair."""
     pr = W.Problem(name="st8", cfg=4, problem=0, d=3, kernel="stencil7", points=W.grid_points_3d(8), leaf=8,
                    k=4, s_cfg=0, nrhs=2, diag_shift=0.0, scale=1.0, grid_side=8)
-    tree, sched, fac, _ = rsrs.build(pr)
-    first = [bf for bf in fac.boxes if bf.level == tree.depth and bf.colour == 0]
+    trace = []
+    tree, sched, fac, _ = rsrs.build(pr, trace=trace)
+    first = [(bf, tr) for bf, tr in zip(fac.boxes, trace) if bf.level == tree.depth and bf.colour == 0]
     assert first and any(not bf.pivot_dependent[0] for bf in fac.boxes)
-    for bf in first:
+    for bf, tr in first:
         assert bf.pivot_dependent[0]
         assert not bf.T.any()
+        # the floor sits above what the nullification actually leaves (measured: at most 2.4 eps of
+        # the largest pre-nullification row here, against the floor's eps sqrt(2s) = 22.8 eps)
+        left = np.linalg.norm(np.hstack([tr["Yp"], tr["Zp"]]), axis=1).max()
+        assert left <= 0.25 * rsrs.nullification_rounding(fac.s) * np.sqrt(np.max(tr["scale2"]))
         assert np.array_equal(bf.S, np.sort(bf.B)[: len(bf.S)]) or np.array_equal(bf.S, bf.B[: len(bf.S)])
     b = pr.rhs()
     assert np.allclose(rsrs.apply(fac, rsrs.solve(fac, b)), b, rtol=0, atol=1e-12 * np.abs(b).max())
+
+
+def _relerr_dense(pr, fac):
+    a = ops.make_operator(pr).dense()
+    return np.linalg.norm(a - rsrs.apply(fac, np.eye(pr.n)), 2) / np.linalg.norm(a, 2)
+
+
+def test_id_thresholds_keep_the_far_field_rank(monkeypatch):
+    """The ID of Sec. 2.3 is the greedy pivoted QR stopped at the fixed rank k (Sec. 4.5); the
+    oracle's dependent-pivot thresholds (tau |R_00| and the nullification's rounding floor) may only
+    set aside pivots at the rounding level, never far-field content.  On a kernel matrix whose far
+    fields keep content down to about 1e-13 of the near field (32 x 32 grid, leaf 64, k = 24), the
+    factor must be as accurate as the threshold-free greedy CPQR's on the same sketches: relerr
+    within 1.5x (a floor at 1e-10 of the near field is 34x worse here)."""
+    pr = W.small_problem(n_side=32, leaf=64, k=24)
+    tree = Tree(pr.points, pr.leaf)
+    sched = Schedule(tree, pr.k)
+    s = sched.s_req
+    om, ps = pr.omega(s), pr.psi(s)
+    y, z = ops.sample(ops.make_operator(pr), om, ps)
+    with_thresholds = _relerr_dense(pr, rsrs.factor(tree, sched, y, z, om, ps))
+    cpqr = la.cpqr_id
+    monkeypatch.setattr(la, "cpqr_id", lambda m, k, tau, record=None, floor=0.0: cpqr(m, k, 0.0, record=record))
+    free = _relerr_dense(pr, rsrs.factor(tree, sched, y, z, om, ps))
+    monkeypatch.undo()
+    assert with_thresholds <= 1.5 * free, (with_thresholds, free)
+    assert free < 1e-9
