@@ -276,8 +276,8 @@ rsrs_status rsrs_refactor(rsrs_factor* f, uint64_t seed, void* stream);
 rsrs_status rsrs_solve(const rsrs_factor* f, double* F_dev, int64_t ldf, int32_t nrhs,
                        int adjoint, void* stream);
 /* rsrs_solve_noalloc: rsrs_solve for callers that must not allocate device memory.  The paper
- * has no counterpart: it is a deployment variant of rsrs_solve (the sweeps of eq. Ainvfact,
- * Sec. 3.2), computing the same result with the same kernels.
+ * has no counterpart: it is a deployment variant of rsrs_solve, computing the same result with the
+ * same kernels.
  *
  * Who needs it: rsrs_solve takes an N x nrhs staging block from cudaMalloc and returns it with
  * cudaFree on every call.  A caller whose device memory is all reserved by another allocator (a

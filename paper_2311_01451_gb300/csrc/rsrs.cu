@@ -118,6 +118,7 @@ struct DevPool {
     if (count <= 0) count = 1;
     cudaError_t e = cudaMalloc((void**)p, (size_t)count * sizeof(T));
     if (e == cudaSuccess) ptrs.push_back(*p);
+    else (void)cudaGetLastError();  // the status is returned; leave no stale error for later checks
     return e;
   }
 };

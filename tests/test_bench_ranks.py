@@ -81,3 +81,42 @@ def test_reference_arm_nonzero_rank_exits_without_work():
                         "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
     assert p.returncode == 0, p.stderr
     assert p.stdout.strip() == ""
+
+
+def _shard_main(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        allp = W.config(3)
+        mine = bench._shard(allp, world, rank)
+        shares = [None] * world
+        dist.all_gather_object(shares, [(p.problem, p.n) for p in mine])
+        # the job's work is every rank's right-hand sides: the whole batch's
+        _, units = bench._job_time(1.0, sum(p.nrhs for p in mine), "cpu")
+    finally:
+        dist.destroy_process_group()
+    with open(os.path.join(out_dir, f"shard{rank}.json"), "w") as f:
+        json.dump({"mine": [(p.problem, p.n) for p in mine], "shares": shares, "units": units,
+                   "all": [(p.problem, p.n) for p in allp]}, f)
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_batched_problems_are_sharded_across_ranks(tmp_path, world):
+    mp.start_processes(_shard_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    res = [json.load(open(tmp_path / f"shard{r}.json")) for r in range(world)]
+    allp = [tuple(x) for x in res[0]["all"]]
+    assert len(allp) == 64
+    seen = []
+    for r, x in enumerate(res):
+        mine = [tuple(v) for v in x["mine"]]
+        assert mine == allp[r::world]  # problem i on rank i mod world
+        assert [[tuple(v) for v in sh] for sh in x["shares"]] == [allp[q::world] for q in range(world)]
+        seen += mine
+        assert x["units"] == sum(1 for _ in allp)  # one RHS per problem, summed over the ranks
+    assert sorted(seen) == sorted(allp) and len(set(seen)) == len(allp)  # disjoint, and the union is the batch

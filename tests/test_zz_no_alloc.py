@@ -2,8 +2,9 @@
 
 The no-allocation solve stages the right-hand sides in the library's static device buffer instead
 of a per-call cudaMalloc; it runs the same kernels in the same order, so its results must equal
-rsrs_solve's bit for bit, also for two calls in a row that reuse the buffer.  This file is named to
-be collected last, so that it also runs after everything else has used the device.
+rsrs_solve's bit for bit, also for two calls in a row that reuse the buffer, and it must keep
+working when no device memory can be allocated at all.  This file is named to be collected last,
+so that it also runs after everything else has used the device.
 """
 import numpy as np
 import pytest
@@ -72,3 +73,39 @@ def test_noalloc_rejects_blocks_beyond_the_buffer(R, factor):
     assert e.value.name == "RSRS_E_INVAL" and "exceeds" in str(e.value)
     torch.cuda.synchronize()
     assert torch.equal(F, before)  # nothing was launched
+
+
+def test_noalloc_solves_with_device_memory_exhausted(R, factor):
+    """The reason the entry point exists: a caller whose device memory is all held by another
+    allocator.  Here PyTorch's allocator takes every block it can get; rsrs_solve then cannot obtain
+    its staging block and reports RSRS_E_NOMEM (a host-side error, nothing is launched), while
+    rsrs_solve_noalloc still solves, bit-identical to a solve made before the memory was taken."""
+    pr, f = factor
+    nrhs = 200  # 3000 x 200 doubles = 4.8 MB: within the static buffer, beyond what is left below
+    F = _block(pr.n, nrhs, 4)
+    ref = f.solve(F.clone())
+    warm = F.clone()
+    f.solve_noalloc(warm)  # the first call on the device resolves the buffer's address
+    G, H = F.clone(), F.clone()
+    torch.cuda.synchronize()
+    hold = []
+    try:
+        # PyTorch serves requests above 1 MiB from segments of at least 2 MiB (20 MiB between 1 and
+        # 10 MiB) and smaller ones from 2 MiB segments: the last, sub-MiB chunks leave < 2 MiB
+        for chunk in (1 << 30, 1 << 26, 1 << 24, 1 << 19):
+            while True:
+                try:
+                    hold.append(torch.empty(chunk, dtype=torch.uint8, device="cuda"))
+                except torch.cuda.OutOfMemoryError:
+                    break
+        free, _ = torch.cuda.mem_get_info()
+        assert free < F.numel() * 8, f"{free} bytes still free"
+        with pytest.raises(R.RSRSError) as e:
+            f.solve(H)
+        assert e.value.name == "RSRS_E_NOMEM"
+        f.solve_noalloc(G)
+        torch.cuda.synchronize()
+    finally:
+        del hold
+        torch.cuda.empty_cache()
+    assert torch.equal(G, ref)  # compared once the memory is back (the comparison allocates)
