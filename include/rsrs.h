@@ -138,9 +138,11 @@ typedef struct {
   int use_graph;          /* 1: capture the build's launch sequence as one CUDA graph    */
                           /* kept with the factors, so rsrs_refactor can replay it;    */
                           /* needs device-drawn test matrices; no per-class timings   */
-  int residual_fp64;      /* rsrs_refine with a built-in kernel: 0 default = residual in */
-                          /* float-float (48-bit) arithmetic on the FP32 pipe, about    */
-                          /* 1e-14 relative; 1 = residual in FP64 arithmetic            */
+  int residual_fp64;      /* residual arithmetic of rsrs_refine / rsrs_residual /        */
+                          /* rsrs_gmres with a built-in kernel, RSRS_RESIDUAL_*:       */
+                          /* 0 default (Ozaki scheme when its slice store fits in     */
+                          /* device memory, else float-float), 1 FP64, 2 float-float, */
+                          /* 3 Ozaki scheme only (RSRS_E_NOMEM when it does not fit)  */
   rsrs_tune_t tune;       /* launch shapes (zero: defaults); kept with the factor       */
 } rsrs_options;
 
@@ -183,12 +185,34 @@ typedef struct {
 /* Name of a kernel class ("gram", "schur", ...). */
 const char* rsrs_kernel_class_name(int cls);
 
+/* Arithmetic of the residual product B - A X of iterative refinement (an addition to the paper,
+ * which pairs the factor with GMRES, Sec. 5), for the built-in kernels:
+ *   FP64        the kernel evaluated and multiplied in FP64 arithmetic;
+ *   FLOAT_FLOAT the kernel and the products in float-float (48-bit) arithmetic on the FP32 pipe,
+ *               about 1e-14 of sum_j |K_ij x_j|;
+ *   OZAKI       the Ozaki scheme (Ozaki, Ogita, Oishi & Rump 2012) on the bf16 tensor cores: the
+ *               matrix's rows (float-float values) and the columns of X split into ten base-2^7
+ *               digits, every digit product exact, the sums exact in integers, about 2e-15 of
+ *               sum_j |K_ij x_j|.  The digits of the matrix are made at the factor's first
+ *               residual and kept with it (20 N^2 bytes of device memory; 86 GB at N = 65,536);
+ *               rsrs_refactor discards them (they are made again at the next residual).
+ * A callback operator's residual is the callback's (FP64). */
+enum {
+  RSRS_RESIDUAL_AUTO = 0,         /* OZAKI when its store fits next to 2 GiB + 5 % of the device's */
+                                  /* memory, else FLOAT_FLOAT                                      */
+  RSRS_RESIDUAL_FP64 = 1,
+  RSRS_RESIDUAL_FLOAT_FLOAT = 2,
+  RSRS_RESIDUAL_OZAKI = 3
+};
+
 typedef struct {
   int iterations;         /* corrections applied after the first solve                */
   double rel_residual;    /* final max over columns of ||b - A x|| / ||b||            */
   double history[64];     /* relative residual after each step                        */
   int64_t kernel_launches; /* kernels of this library the call launched (a matvec
                               callback's own launches are not counted)                */
+  int32_t residual_kind;  /* RSRS_RESIDUAL_FP64, _FLOAT_FLOAT or _OZAKI: the arithmetic the
+                             products with A used (FP64 for a callback)               */
 } rsrs_refine_report;
 
 /* ---- tree (Sec. 3: quad/octree, adjacency, 2:1 balance) --------------------
@@ -306,20 +330,20 @@ rsrs_status rsrs_solve_noalloc(const rsrs_factor* f, double* F, int64_t ldf, int
 rsrs_status rsrs_apply(const rsrs_factor* f, double* F_dev, int64_t ldf, int32_t nrhs,
                        int adjoint, void* stream);
 /* R = B - A X for the operator the factor was built from, in the refinement's residual
- * arithmetic (float-float for the built-in kernels unless opts->residual_fp64, FP64 for a
- * callback); B_dev, X_dev, R_dev column-major N x nrhs with leading dimension ld (R may not alias
- * B or X).  The residual of iterative refinement, which the paper does not use (it pairs the
- * factor with GMRES, Sec. 5); nrhs <= 4096. */
+ * arithmetic (RSRS_RESIDUAL_*, opts->residual_fp64; FP64 for a callback); B_dev, X_dev, R_dev
+ * column-major N x nrhs with leading dimension ld (R may not alias B or X).  The residual of
+ * iterative refinement, which the paper does not use (it pairs the factor with GMRES, Sec. 5);
+ * nrhs <= 4096.  RSRS_E_NONFINITE when two points coincide (the kernel is unbounded). */
 rsrs_status rsrs_residual(const rsrs_factor* f, const double* B_dev, const double* X_dev, double* R_dev,
                           int64_t ld, int32_t nrhs, void* stream);
 /* Iterative refinement to FP64 accuracy (an addition to the paper's method, with the factor as the
  * approximate inverse): X = A_approx^-1 B, then X += A_approx^-1 (B - A X) until
  * max_j ||B_j - A X_j|| / ||B_j|| <= rtol or maxit corrections.  The residual is computed as
- * rsrs_residual computes it (float-float for the built-in kernels unless opts->residual_fp64,
- * FP64 through the callback otherwise).  B_dev, X_dev column-major N x nrhs with leading
- * dimension ld, nrhs <= 64; X's input is ignored.  out (may be null): corrections, final
- * relative residual, its history, kernels launched.  RSRS_E_NOT_CONVERGED (out still filled)
- * when rtol is not reached; RSRS_E_NONFINITE for a non-finite residual. */
+ * rsrs_residual computes it (RSRS_RESIDUAL_*; FP64 through the callback for a callback operator).
+ * B_dev, X_dev column-major N x nrhs with leading dimension ld, nrhs <= 64; X's input is ignored.
+ * out (may be null): corrections, final relative residual, its history, kernels launched, the
+ * residual arithmetic used.  RSRS_E_NOT_CONVERGED (out still filled) when rtol is not reached;
+ * RSRS_E_NONFINITE for a non-finite residual. */
 rsrs_status rsrs_refine(const rsrs_factor* f, const double* B_dev, double* X_dev, int64_t ld,
                         int32_t nrhs, double rtol, int maxit, void* stream,
                         rsrs_refine_report* out);
@@ -327,8 +351,8 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B_dev, double* X_dev
  * preconditioner, A (A_approx)^-1 Y = B, X = (A_approx)^-1 Y: the Krylov method Sec. 5 pairs
  * with the factorization, against iterative refinement.  Every column is its own GMRES run (its
  * own Arnoldi basis, classical Gram-Schmidt applied twice, Givens rotations); the columns share
- * the launches.  Products with A in the refinement's residual arithmetic (float-float for the
- * built-in kernels unless opts->residual_fp64, the callback otherwise); X starts at 0 (its input
+ * the launches.  Products with A in the refinement's residual arithmetic (RSRS_RESIDUAL_*, the
+ * callback for a callback operator); X starts at 0 (its input
  * is ignored).  Stops when the true residual max_j ||B_j - A X_j|| / ||B_j|| <= rtol (checked
  * when the Arnoldi estimate reaches rtol, at each restart and at the end) or after maxit
  * iterations in total.  out: iterations = Krylov iterations (preconditioner solves),

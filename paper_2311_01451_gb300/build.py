@@ -13,7 +13,7 @@ LIB = os.path.join(OUT, "librsrs.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
-CU_SOURCES = ["kernels.cu", "sample.cu", "sample_tc.cu", "gemm_tc.cu", "residual_ff.cu", "root_lu.cu", "stencil7.cu", "rsrs.cu"]
+CU_SOURCES = ["kernels.cu", "sample.cu", "sample_tc.cu", "gemm_tc.cu", "residual_ff.cu", "residual_oz.cu", "root_lu.cu", "stencil7.cu", "rsrs.cu"]
 CXX_SOURCES = ["tree.cpp"]
 
 

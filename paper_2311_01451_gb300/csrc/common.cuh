@@ -105,6 +105,17 @@ void launch_kernel_matvec_ff(Launch L, int kind, const double* pts, int d, int64
                              const double* in, int64_t ld_in, double* out, int64_t ld_out, int64_t ncols,
                              float* scratch, int split);
 
+// The same product on the bf16 tensor cores by the Ozaki scheme (residual_oz.cu): a store of K's
+// slices made once (oz_store_bytes bytes, launch_oz_prepare; its status word records a coincident
+// point as kDevNonfinite and an expired wait as kDevTimeout), then any number of products, each with
+// oz_scratch_bytes(n) bytes of scratch per call.  Rows in tree order; ncols any.
+int64_t oz_store_bytes(int64_t n, int d);
+int* oz_status_word(void* store, int64_t n, int d);
+void launch_oz_prepare(Launch L, int kind, const double* pts, int d, int64_t n, void* store);
+int64_t oz_scratch_bytes(int64_t n);
+void launch_oz_matvec(Launch L, int64_t n, int d, const void* store, double shift, double scale, const double* in,
+                      int64_t ld_in, double* out, int64_t ld_out, int64_t ncols, void* scratch);
+
 int64_t tc_plane_ld(int64_t n);
 int64_t tc_points_len(int64_t n, int d);
 void launch_points_f32(Launch L, const double* pts, int64_t n, int d, float* out);

@@ -73,9 +73,16 @@ struct rsrs_factor {
   int max_r = 0;
   double *Y = nullptr, *Z = nullptr, *Om = nullptr, *Ps = nullptr;  // kept sketches (shared, rows from base)
   int sample_kernel = 0;  // mixed sampling: 1 FP32 SIMT, 2 tcgen05 3xTF32
-  int residual_fp64 = 0;  // refinement residual in FP64 instead of float-float
+  int residual_fp64 = 0;  // residual arithmetic, RSRS_RESIDUAL_*
   rsrs_tune_t tune{};     // launch shapes of the build and of the refinement residual
   rsrs_stats stats{};
+  // the Ozaki-scheme residual's store of K's digits, made at the first residual that uses it
+  // (oz_state 1), or found not to fit in device memory (-1); 0: not made yet
+  mutable void* oz_store = nullptr;
+  mutable int oz_state = 0;
+  ~rsrs_factor() {
+    if (oz_store) cudaFree(oz_store);
+  }
 };
 
 namespace {
@@ -418,7 +425,8 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
   if (o.mixed_cpqr < 0 || o.mixed_cpqr > 1) return fail(RSRS_E_INVAL, "build: unknown mixed_cpqr");
   if (o.mixed_gemm < 0 || o.mixed_gemm > 1) return fail(RSRS_E_INVAL, "build: unknown mixed_gemm");
   if (!tune_valid(o.tune)) return fail(RSRS_E_INVAL, "build: tune values out of range");
-  if (o.residual_fp64 < 0 || o.residual_fp64 > 1) return fail(RSRS_E_INVAL, "build: residual_fp64 is 0 or 1");
+  if (o.residual_fp64 < 0 || o.residual_fp64 > 3)
+    return fail(RSRS_E_INVAL, "build: residual_fp64 is one of RSRS_RESIDUAL_* (0..3)");
   if (nprob > 1 && (o.omega_host || o.psi_host || o.omega_dev || o.psi_dev))
     return fail(RSRS_E_INVAL, "build: caller test matrices are for single-problem builds");
   const bool graph = o.use_graph != 0;
@@ -503,7 +511,7 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
     f->ctx = ops[p].ctx;
     f->perm = T.perm;
     f->sample_kernel = o.sample_kernel == 0 ? 2 : o.sample_kernel;
-    f->residual_fp64 = o.residual_fp64 ? 1 : 0;
+    f->residual_fp64 = o.residual_fp64;
     f->tune = o.tune;
     F[p] = std::move(f);
   }
@@ -1148,6 +1156,89 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
   return RSRS_OK;
 }
 
+// ---- the refinement residual's product with A ---------------------------------------------------
+// Which arithmetic computes A x for a refinement, GMRES or rsrs_residual call, and its scratch.
+struct ResidualOp {
+  int kind = RSRS_RESIDUAL_FP64;  // RSRS_RESIDUAL_FP64 (op_apply), _FLOAT_FLOAT or _OZAKI
+  float* ffs = nullptr;
+  void* ozs = nullptr;
+};
+
+// The factor's store of K's digits for the Ozaki-scheme product, made on first use when it fits
+// next to a margin of 2 GiB + 5 % of the device's memory; RSRS_E_NOMEM when it does not.
+rsrs_status oz_ensure(const rsrs_factor* f, Launch L) {
+  if (f->oz_state == 1) return RSRS_OK;
+  if (f->oz_state < 0) return fail(RSRS_E_NOMEM, "Ozaki residual: the digit store does not fit");
+  const size_t bytes = (size_t)oz_store_bytes(f->n, f->d);
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    (void)cudaGetLastError();
+    fr = 0;
+  }
+  const size_t margin = ((size_t)2 << 30) + tot / 20;
+  if (fr < bytes + margin) {
+    f->oz_state = -1;
+    return fail(RSRS_E_NOMEM, "Ozaki residual: " + std::to_string(bytes >> 20) + " MiB of digits do not fit");
+  }
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    f->oz_state = -1;
+    return fail(RSRS_E_NOMEM, "Ozaki residual: allocation of the digit store failed");
+  }
+  f->oz_store = p;
+  launch_oz_prepare(L, f->kind, f->pts_dev, f->d, f->n, p);
+  CU(cudaGetLastError());
+  f->oz_state = 1;
+  return RSRS_OK;
+}
+
+rsrs_status residual_setup(const rsrs_factor* f, Launch L, DevPool& pool, int64_t ncols, ResidualOp& ro) {
+  ro = ResidualOp{};
+  if (f->kind == RSRS_OP_CALLBACK || f->residual_fp64 == RSRS_RESIDUAL_FP64) return RSRS_OK;
+  if (f->residual_fp64 != RSRS_RESIDUAL_FLOAT_FLOAT) {
+    rsrs_status r = oz_ensure(f, L);
+    if (r == RSRS_OK) {
+      uint8_t* scr = nullptr;
+      if (pool.alloc(&scr, oz_scratch_bytes(f->n)) == cudaSuccess) {
+        ro.kind = RSRS_RESIDUAL_OZAKI;
+        ro.ozs = scr;
+        return RSRS_OK;
+      }
+      r = fail(RSRS_E_NOMEM, "Ozaki residual: scratch allocation failed");
+    }
+    if (f->residual_fp64 == RSRS_RESIDUAL_OZAKI) return r;
+  }
+  ro.kind = RSRS_RESIDUAL_FLOAT_FLOAT;
+  CU(pool.alloc(&ro.ffs, ff_scratch_floats(f->n, f->d, (int)ncols, f->tune.residual_split)));
+  return RSRS_OK;
+}
+
+// out = A in (rows in tree order, ld = ncols) in the arithmetic of ro.
+rsrs_status residual_apply(const rsrs_factor* f, Launch L, const ResidualOp& ro, const double* in, double* out,
+                           int64_t ncols, double* c1, double* c2) {
+  if (ro.kind == RSRS_RESIDUAL_OZAKI) {
+    launch_oz_matvec(L, f->n, f->d, f->oz_store, f->shift, f->scale, in, ncols, out, ncols, ncols, ro.ozs);
+  } else if (ro.kind == RSRS_RESIDUAL_FLOAT_FLOAT) {
+    launch_kernel_matvec_ff(L, f->kind, f->pts_dev, f->d, f->n, f->shift, f->scale, in, ncols, out, ncols, ncols,
+                            ro.ffs, f->tune.residual_split);
+  } else {
+    return op_apply(f, L, in, out, ncols, 0, 0, c1, c2);
+  }
+  CU(cudaGetLastError());
+  return RSRS_OK;
+}
+
+// Device-detected conditions of the Ozaki product (read after the stream has synchronised).
+rsrs_status residual_check(const rsrs_factor* f, const ResidualOp& ro) {
+  if (ro.kind != RSRS_RESIDUAL_OZAKI) return RSRS_OK;
+  int h = 0;
+  CU(cudaMemcpy(&h, oz_status_word(f->oz_store, f->n, f->d), sizeof(int), cudaMemcpyDeviceToHost));
+  if (h == kDevNonfinite) return fail(RSRS_E_NONFINITE, "residual: two points coincide (the kernel is unbounded)");
+  if (h == kDevTimeout) return fail(RSRS_E_TIMEOUT, "residual: a bounded device wait expired");
+  return RSRS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1170,6 +1261,11 @@ rsrs_status rsrs_refactor(rsrs_factor* f, uint64_t seed, void* stream) {
   Shared* sh = f->sh.get();
   if (!sh || !sh->exec) return fail(RSRS_E_INVAL, "refactor: the factor was built without use_graph");
   cudaStream_t st = (cudaStream_t)stream;
+  if (f->oz_store) {  // made again at the next residual, so that a rebuild costs what a build does
+    cudaFree(f->oz_store);
+    f->oz_store = nullptr;
+  }
+  f->oz_state = 0;
   k_set_u64<<<1, 1, 0, st>>>(sh->seed_dev, seed);
   CU(cudaGetLastError());
   CU(cudaGraphLaunch(sh->exec, st));
@@ -1263,7 +1359,7 @@ extern "C" rsrs_status rsrs_autotune(int nprob, const rsrs_tree* const* trees, c
   for (int p = 0; p < nprob; ++p) builtin = builtin && ops[p].kind != RSRS_OP_CALLBACK;
   const bool tune_sample = mixed && builtin && (o.sample_kernel == 0 || o.sample_kernel == 2);
   const bool tune_cpqr = mixed && o.mixed_cpqr == 0;
-  const bool tune_resid = builtin && !o.residual_fp64;
+  const bool tune_resid = builtin && o.residual_fp64 == RSRS_RESIDUAL_FLOAT_FLOAT;
 
   // best-of-reps device time per kernel class of one build configuration
   auto time_build = [&](const rsrs_tune_t& t, double* cls) -> rsrs_status {
@@ -1567,10 +1663,9 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_
     CU(pool.alloc(&c1, tot));
     CU(pool.alloc(&c2, tot));
   }
-  // float-float residual scratch (built-in kernels)
-  const bool ff = f->kind != RSRS_OP_CALLBACK && !f->residual_fp64;
-  float* ffs = nullptr;
-  if (ff) CU(pool.alloc(&ffs, ff_scratch_floats(f->n, f->d, nrhs, f->tune.residual_split)));
+  ResidualOp ro;
+  r = residual_setup(f, L, pool, nrhs, ro);
+  if (r != RSRS_OK) return r;
   k_cm_to_rows<<<nblk(tot), 256, 0, st>>>(B, ld, f->perm_dev, f->n, nrhs, Wb);
   ++nl;
   CU(cudaMemcpyAsync(Wx, Wb, tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1587,11 +1682,7 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_
   double rel = 0.0;
   int it = 0;
   for (;; ++it) {
-    if (ff)
-      launch_kernel_matvec_ff(L, f->kind, f->pts_dev, f->d, f->n, f->shift, f->scale, Wx, nrhs, Wax, nrhs, nrhs, ffs,
-                              f->tune.residual_split);
-    else
-      r = op_apply(f, L, Wx, Wax, nrhs, 0, 0, c1, c2);
+    r = residual_apply(f, L, ro, Wx, Wax, nrhs, c1, c2);
     if (r != RSRS_OK) return r;
     k_sub<<<nblk(tot), 256, 0, st>>>(Wr, Wb, Wax, tot);
     CU(cudaMemsetAsync(nrm, 0, 64 * sizeof(double), st));
@@ -1599,6 +1690,10 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_
     nl += 2;  // k_sub, k_colnorm2
     CU(cudaMemcpyAsync(hn, nrm, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
+    if (it == 0) {
+      r = residual_check(f, ro);
+      if (r != RSRS_OK) return r;
+    }
     rel = 0.0;
     for (int j = 0; j < nrhs; ++j) rel = std::max(rel, std::sqrt(hn[j]) / std::max(std::sqrt(bn[j]), 1e-300));
     if (it < 64) rr.history[it] = rel;
@@ -1613,9 +1708,12 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_
   ++nl;
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(st));
+  r = residual_check(f, ro);
+  if (r != RSRS_OK) return r;
   rr.iterations = it;
   rr.rel_residual = rel;
   rr.kernel_launches = nl;
+  rr.residual_kind = ro.kind;
   if (rep) *rep = rr;
   if (rel > rtol) return fail(RSRS_E_NOT_CONVERGED, "refine: residual " + std::to_string(rel) + " > rtol");
   return RSRS_OK;
@@ -1634,26 +1732,22 @@ rsrs_status rsrs_residual(const rsrs_factor* f, const double* B, const double* X
   CU(pool.alloc(&Wb, tot));
   CU(pool.alloc(&Wx, tot));
   CU(pool.alloc(&Wax, tot));
-  const bool ff = f->kind != RSRS_OP_CALLBACK && !f->residual_fp64;
-  float* ffs = nullptr;
-  if (ff) CU(pool.alloc(&ffs, ff_scratch_floats(f->n, f->d, nrhs, f->tune.residual_split)));
+  ResidualOp ro;
+  r = residual_setup(f, L, pool, nrhs, ro);
+  if (r != RSRS_OK) return r;
   if (f->kind == RSRS_OP_CALLBACK) {
     CU(pool.alloc(&c1, tot));
     CU(pool.alloc(&c2, tot));
   }
   k_cm_to_rows<<<nblk(tot), 256, 0, st>>>(B, ld, f->perm_dev, f->n, nrhs, Wb);
   k_cm_to_rows<<<nblk(tot), 256, 0, st>>>(X, ld, f->perm_dev, f->n, nrhs, Wx);
-  if (ff)
-    launch_kernel_matvec_ff(L, f->kind, f->pts_dev, f->d, f->n, f->shift, f->scale, Wx, nrhs, Wax, nrhs, nrhs, ffs,
-                              f->tune.residual_split);
-  else
-    r = op_apply(f, L, Wx, Wax, nrhs, 0, 0, c1, c2);
+  r = residual_apply(f, L, ro, Wx, Wax, nrhs, c1, c2);
   if (r != RSRS_OK) return r;
   k_sub<<<nblk(tot), 256, 0, st>>>(Wx, Wb, Wax, tot);
   k_rows_to_cm<<<nblk(tot), 256, 0, st>>>(Wx, f->perm_dev, f->n, nrhs, Rout, ld);
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(st));
-  return RSRS_OK;
+  return residual_check(f, ro);
 }
 
 }  // extern "C"
@@ -1772,18 +1866,12 @@ rsrs_status rsrs_gmres(const rsrs_factor* f, const double* B, double* X, int64_t
     CU(pool.alloc(&c1, tot));
     CU(pool.alloc(&c2, tot));
   }
-  const bool ff = f->kind != RSRS_OP_CALLBACK && !f->residual_fp64;
-  float* ffs = nullptr;
-  if (ff) CU(pool.alloc(&ffs, ff_scratch_floats(n, f->d, c, f->tune.residual_split)));
+  ResidualOp ro;
+  r = residual_setup(f, L, pool, c, ro);
+  if (r != RSRS_OK) return r;
   // A y in the refinement's residual arithmetic
   auto apply_A = [&](const double* in, double* out) -> rsrs_status {
-    if (ff) {
-      launch_kernel_matvec_ff(L, f->kind, f->pts_dev, f->d, n, f->shift, f->scale, in, c, out, c, c, ffs,
-                              f->tune.residual_split);
-      CU(cudaGetLastError());
-      return RSRS_OK;
-    }
-    return op_apply(f, L, in, out, c, 0, 0, c1, c2);
+    return residual_apply(f, L, ro, in, out, c, c1, c2);
   };
   k_cm_to_rows<<<nblk(tot), 256, 0, st>>>(B, ld, f->perm_dev, n, c, Wb);
   ++nl;
@@ -1899,9 +1987,12 @@ rsrs_status rsrs_gmres(const rsrs_factor* f, const double* B, double* X, int64_t
   ++nl;
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(st));
+  r = residual_check(f, ro);
+  if (r != RSRS_OK) return r;
   rr.iterations = total;
   rr.rel_residual = rel;
   rr.kernel_launches = nl;
+  rr.residual_kind = ro.kind;
   if (rep) *rep = rr;
   if (rel > rtol) return fail(RSRS_E_NOT_CONVERGED, "gmres: residual " + std::to_string(rel) + " > rtol");
   return RSRS_OK;

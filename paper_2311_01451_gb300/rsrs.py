@@ -39,6 +39,7 @@ class Operator(C.Structure):
 RSRS_SAMPLE_TILE_DEFAULT, RSRS_SAMPLE_TILE_256x2, RSRS_SAMPLE_TILE_128x3, RSRS_SAMPLE_TILE_192x2 = 0, 1, 2, 3
 RSRS_SAMPLE_TILE_256x4_K16, RSRS_SAMPLE_TILE_192x5_K16 = 4, 5
 RSRS_SAMPLE_TILE_2x256x3_K16, RSRS_SAMPLE_TILE_2x192x4_K16 = 6, 7
+RSRS_RESIDUAL_AUTO, RSRS_RESIDUAL_FP64, RSRS_RESIDUAL_FLOAT_FLOAT, RSRS_RESIDUAL_OZAKI = 0, 1, 2, 3
 
 
 class Tune(C.Structure):
@@ -93,7 +94,7 @@ class Stats(C.Structure):
 
 class RefineReport(C.Structure):
     _fields_ = [("iterations", C.c_int), ("rel_residual", C.c_double), ("history", C.c_double * 64),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("residual_kind", C.c_int32)]
 
 
 class BoxView(C.Structure):
@@ -270,7 +271,7 @@ class Factor:
                  precision: int = RSRS_PREC_FP64, p: int = -1, omega: np.ndarray | None = None,
                  psi: np.ndarray | None = None, seed: int = 0, passes: int = 0, keep_sketches: bool = False,
                  matvec=None, stream=None, profile: bool = False,
-                 sample_kernel: int = 0, mixed_cpqr: int = 0, residual_fp64: bool = False,
+                 sample_kernel: int = 0, mixed_cpqr: int = 0, residual_fp64: bool = False, residual=None,
                  mixed_gemm: int = 0, use_graph: bool = False, tune=None):
         self.tree = tree
         self.n = tree.n
@@ -289,7 +290,8 @@ class Factor:
         opts = Options(precision=precision, p=p, proj_passes=passes, seed=seed,
                        keep_sketches=int(keep_sketches), profile=int(profile),
                        sample_kernel=sample_kernel,
-                       mixed_cpqr=mixed_cpqr, residual_fp64=int(residual_fp64), mixed_gemm=mixed_gemm,
+                       mixed_cpqr=mixed_cpqr,
+                       residual_fp64=int(residual_fp64) if residual is None else int(residual), mixed_gemm=mixed_gemm,
                        use_graph=int(use_graph), tune=_tune(tune))
         self._om = self._ps = None
         if omega is not None and hasattr(omega, "data_ptr"):  # device tensors (N, s), original order
@@ -411,7 +413,7 @@ class Factor:
 
 def build_batched(trees, kinds, k: int, s: int, shifts, scales, precision: int = RSRS_PREC_FP64, p: int = -1,
                   seed: int = 0, passes: int = 0, profile: bool = False, sample_kernel: int = 0,
-                  keep_sketches: bool = False, mixed_cpqr: int = 0, residual_fp64: bool = False,
+                  keep_sketches: bool = False, mixed_cpqr: int = 0, residual_fp64: bool = False, residual=None,
                   mixed_gemm: int = 0, use_graph: bool = False, tune=None,
                   stream=None) -> list:
     """rsrs_build_batched: factors of independent problems built in one set of launches."""
@@ -422,7 +424,8 @@ def build_batched(trees, kinds, k: int, s: int, shifts, scales, precision: int =
     opts = Options(precision=precision, p=p, proj_passes=passes, seed=seed, profile=int(profile),
                    sample_kernel=sample_kernel,
                    keep_sketches=int(keep_sketches), mixed_cpqr=mixed_cpqr,
-                   residual_fp64=int(residual_fp64), mixed_gemm=mixed_gemm, use_graph=int(use_graph),
+                   residual_fp64=int(residual_fp64) if residual is None else int(residual), mixed_gemm=mixed_gemm,
+                   use_graph=int(use_graph),
                    tune=_tune(tune))
     _check(lib().rsrs_build_batched(n, handles, ops, k, s, C.byref(opts), _stream_ptr(stream), outs))
     res = []

@@ -170,3 +170,11 @@ def test_binding_struct_layouts_match_the_header(R, tmp_path):
     subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     assert got == want
+
+
+@pytest.mark.parametrize("mode", [-1, 4])
+def test_residual_arithmetic_validated_before_device_work(R, mode):
+    t = R.Tree(W.grid_points_2d(64), 64)
+    with pytest.raises(R.RSRSError) as e:
+        R.Factor(t, R.RSRS_OP_LOG2D, 32, t.info(32).s_req, shift=1.0, scale=1 / 4096, residual=mode)
+    assert e.value.name == "RSRS_E_INVAL"
