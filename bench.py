@@ -336,6 +336,17 @@ def run_gpu(args):
 
     tune, tune_info = _autotune(args, R, tree, kind, pr.k, s, pr.diag_shift, pr.scale, prec)
 
+    if args.profile_step:  # ncu runs: W + K plain steps (build + refined solve) and nothing else
+        for i in range(args.warmup + args.steps):
+            f = R.Factor(tree, kind, pr.k, s, shift=pr.diag_shift, scale=pr.scale, precision=prec, seed=500 + i,
+                         sample_kernel=args.sample_kernel, tune=tune)
+            rep = f.refine(B, X, rtol=RTOL, maxit=30)
+            del f
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_step": True, "workload": pr.name, "refine_iterations": rep.iterations,
+                          "residual_kind": rep.residual_kind}), flush=True)
+        return
+
     def step(seed, profile=False):
         f = R.Factor(tree, kind, pr.k, s, shift=pr.diag_shift, scale=pr.scale, precision=prec, seed=seed,
                      profile=profile, sample_kernel=args.sample_kernel, tune=tune)
@@ -441,6 +452,28 @@ def run_gpu(args):
     t_sol = time.perf_counter() - a0
     line["solves_per_s_refined"] = pr.nrhs / t_ref
     line["solves_per_s_unrefined"] = pr.nrhs / t_sol
+    if rep.residual_kind == R.RSRS_RESIDUAL_OZAKI:
+        # the refinement's residual product (Ozaki scheme): per product it streams the factor's store of
+        # K's digits once, 20 bytes per matrix entry and group of 16 right-hand sides (HBM-bound);
+        # CUDA events on the launching stream around single rsrs_residual calls (store already made)
+        Rr = torch.empty_like(B)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        tms = []
+        for _ in range(3):
+            ev[0].record(stream)
+            f.residual(B, X, Rr)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            tms.append(ev[0].elapsed_time(ev[1]))
+        gb = 20.0 * pr.n * pr.n * ((pr.nrhs + 15) // 16) / 1e9
+        hbm = _peaks().get("hbm_gbs")
+        ach = gb / (min(tms) / 1e3)
+        line["kernel_classes"]["residual_ozaki"] = {
+            "ms": round(min(tms), 3), "gbytes": round(gb, 3), "launches": 4 * ((pr.nrhs + 15) // 16),
+            "bound": "hbm", "achieved_gbs": round(ach, 1), "peak_gbs": hbm,
+            "frac": round(ach / hbm, 4) if hbm else None, "traffic": _traffic("residual_ozaki", pr.name),
+            "note": "one rsrs_residual call (B - A X, 16 columns, including its host-side allocations), digits "
+                    "streamed once; of measured HBM copy peak"}
     # GMRES with the same factor as preconditioner (the paper's solver), to 1e-10 as in its tables
     Xg = torch.zeros_like(B)
     torch.cuda.synchronize()
@@ -616,6 +649,8 @@ def main():
     ap.add_argument("--tune", choices=["auto", "none"], default="auto",
                     help="launch shapes: the library's autotuner (cached) or the defaults")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--profile-step", action="store_true",
+                    help="profiling runs only: W + K plain build-and-refine steps, no timing or extra legs")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
