@@ -296,7 +296,10 @@ rsrs_status rsrs_autotune(int nprob, const rsrs_tree* const* trees, const rsrs_o
  * conditions as for rsrs_build. */
 rsrs_status rsrs_refactor(rsrs_factor* f, uint64_t seed, void* stream);
 
-/* F <- A_approx^-1 F (eq. Ainvfact), or its adjoint; F_dev column-major N x nrhs. */
+/* F <- A_approx^-1 F (eq. Ainvfact), or its adjoint; F_dev column-major N x nrhs.  A
+ * mixed-precision factor (RSRS_PREC_MIXED) sweeps in FP32 arithmetic on FP32 copies of its blocks
+ * (made at the end of its build): its solves serve as the approximate inverse of FP64 refinement
+ * and GMRES, whose FP64-accurate residuals set the final accuracy; an FP64 factor sweeps in FP64. */
 rsrs_status rsrs_solve(const rsrs_factor* f, double* F_dev, int64_t ldf, int32_t nrhs,
                        int adjoint, void* stream);
 /* rsrs_solve_noalloc: rsrs_solve for callers that must not allocate device memory.  The paper
@@ -308,18 +311,20 @@ rsrs_status rsrs_solve(const rsrs_factor* f, double* F_dev, int64_t ldf, int32_t
  * caching allocator such as PyTorch's holds freed blocks instead of returning them, so cudaMalloc
  * can fail while memory is nominally free) cannot make that call succeed, and a serving loop
  * cannot accept the implicit device-wide synchronisation of cudaFree while other streams run.
- * This entry point stages the block in one library-wide static device buffer instead and calls no
- * cudaMalloc, cudaFree or allocating library routine.
+ * This entry point stages the block in library-wide static device buffers instead (one of
+ * RSRS_NOALLOC_MAX_ELEMS doubles, and one of as many floats for a mixed-precision factor's FP32
+ * sweeps: 12 MiB held on every device that loads the library) and calls no cudaMalloc, cudaFree or
+ * allocating library routine.
  *
- * Limit: N * nrhs <= RSRS_NOALLOC_MAX_ELEMS (2^20 doubles = 8 MiB, e.g. N = 65,536 with 16
- * right-hand sides); larger blocks return RSRS_E_INVAL before any launch.  Nothing in the buffer
- * needs to start at zero: the first kernel writes every element the sweeps read.
+ * Limit: N * nrhs <= RSRS_NOALLOC_MAX_ELEMS (2^20, e.g. N = 65,536 with 16 right-hand sides);
+ * larger blocks return RSRS_E_INVAL before any launch.  Nothing in the buffers needs to start at
+ * zero: the first kernels write every element the sweeps read.
  *
- * The buffer is shared by all calls on a device: calls whose execution overlaps (on different
+ * The buffers are shared by all calls on a device: calls whose execution overlaps (on different
  * streams, or from host threads without ordering between them) race on it and give wrong
  * results; order them on one stream.  The call enqueues its kernels on `stream` and returns
  * without synchronising; F holds the solution once the stream has reached that point.  The first
- * call on each device resolves the buffer's address (cudaGetSymbolAddress with that device
+ * call on each device resolves the buffers' addresses (cudaGetSymbolAddress with that device
  * current); make that first call before any stream capture.  Arguments, layout and other errors
  * as rsrs_solve. */
 #define RSRS_NOALLOC_MAX_ELEMS (1 << 20)

@@ -221,6 +221,10 @@ struct SweepArgs {
   int nrhs;
   int adjoint;
   int64_t row_base;  // index lists hold rows of the build's shared index space: row - row_base in F
+  // FP32 sweeps (a mixed-precision factor's solve): FP32 copies of the blocks and of F; F32 set
+  // selects them
+  const float* fd32 = nullptr;
+  float* F32 = nullptr;
 };
 // C rows += alpha * op(A) * B rows; row sets 0 = R, 1 = S, 2 = SN; matrices 0 = T, 1 = LcT, 2 = Uc.
 void launch_sweep_op(Launch L, const SweepArgs& a, int cset, int mat, int trans, int bset, double alpha,
@@ -229,6 +233,9 @@ void launch_sweep_op(Launch L, const SweepArgs& a, int cset, int mat, int trans,
 void launch_sweep_diag(Launch L, const SweepArgs& a, int solve, int64_t items, int max_r);
 void launch_dense_apply(Launch L, const double* A, int64_t n, const int32_t* rows, int64_t row_base, double* F,
                         int nrhs, int adjoint);
+void launch_dense_apply(Launch L, const float* A, int64_t n, const int32_t* rows, int64_t row_base, float* F,
+                        int nrhs, int adjoint);
+void launch_to_f64(Launch L, const float* in, int64_t count, double* out);
 
 // Item counts (host planning) matching the device decoding of each kernel.
 int64_t items_gram(const std::vector<BoxDesc>& h);

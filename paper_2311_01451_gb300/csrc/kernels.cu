@@ -1595,6 +1595,22 @@ struct CntSweep {
     return cdv(m, 16);
   }
 };
+// The factor's blocks and the right-hand sides in the sweep's arithmetic: FP64, or the FP32 copies
+// a mixed-precision factor keeps for its solves.
+template <typename T>
+__device__ inline const T* sweep_fd(const SweepArgs& a);
+template <>
+__device__ inline const double* sweep_fd<double>(const SweepArgs& a) { return a.fd; }
+template <>
+__device__ inline const float* sweep_fd<float>(const SweepArgs& a) { return a.fd32; }
+template <typename T>
+__device__ inline T* sweep_F(const SweepArgs& a);
+template <>
+__device__ inline double* sweep_F<double>(const SweepArgs& a) { return a.F; }
+template <>
+__device__ inline float* sweep_F<float>(const SweepArgs& a) { return a.F32; }
+
+template <typename T>
 __global__ void __launch_bounds__(256) k_sweep(SweepArgs a, SweepOp op) {
   int64_t loc;
   int bi = find_item(a.desc, a.nbox, blockIdx.x, CntSweep{op.cset}, loc);
@@ -1604,35 +1620,37 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a, SweepOp op) {
   int64_t m, K;
   sweep_set(d, a.fi, op.cset, cidx, m);
   sweep_set(d, a.fi, op.bset, bidx, K);
-  const double* A;
+  const T* fd = sweep_fd<T>(a);
+  T* F = sweep_F<T>(a);
+  const T* A;
   int64_t lda;
-  if (op.mat == 0) { A = a.fd + fd_T(d); lda = d.r; }
-  else if (op.mat == 1) { A = a.fd + fd_LcT(d); lda = (int64_t)d.kp + d.n; }
-  else { A = a.fd + fd_Uc(d); lda = (int64_t)d.kp + d.n; }
+  if (op.mat == 0) { A = fd + fd_T(d); lda = d.r; }
+  else if (op.mat == 1) { A = fd + fd_LcT(d); lda = (int64_t)d.kp + d.n; }
+  else { A = fd + fd_Uc(d); lda = (int64_t)d.kp + d.n; }
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
   const int64_t i = loc * 16 + ty;
-  __shared__ double Bs[64][17];
+  __shared__ T Bs[64][17];
   for (int c0 = 0; c0 < a.nrhs; c0 += 16) {
     const int c = c0 + tx;
-    double acc = 0.0;
+    T acc = 0;
     for (int64_t q0 = 0; q0 < K; q0 += 64) {
       for (int e = threadIdx.x; e < 64 * 16; e += 256) {
         int qq = e >> 4, cc = e & 15;
         int64_t q = q0 + qq;
-        Bs[qq][cc] = (q < K && c0 + cc < a.nrhs) ? a.F[((int64_t)bidx[q] - a.row_base) * a.nrhs + c0 + cc] : 0.0;
+        Bs[qq][cc] = (q < K && c0 + cc < a.nrhs) ? F[((int64_t)bidx[q] - a.row_base) * a.nrhs + c0 + cc] : (T)0;
       }
       __syncthreads();
       if (i < m) {
         const int64_t qn = imin64(64, K - q0);
         for (int64_t qq = 0; qq < qn; ++qq) {
           int64_t q = q0 + qq;
-          double av = op.trans ? A[q * lda + i] : A[i * lda + q];
-          acc = fma(av, Bs[qq][tx], acc);
+          T av = op.trans ? A[q * lda + i] : A[i * lda + q];
+          acc = mad(av, Bs[qq][tx], acc);
         }
       }
       __syncthreads();
     }
-    if (i < m && c < a.nrhs) a.F[((int64_t)cidx[i] - a.row_base) * a.nrhs + c] += op.alpha * acc;
+    if (i < m && c < a.nrhs) F[((int64_t)cidx[i] - a.row_base) * a.nrhs + c] += (T)op.alpha * acc;
   }
 }
 // f_R <- M f_R with M = X_RR^-1 (solve) or X_RR (apply), or M^T for the adjoint; one CTA per
@@ -1642,6 +1660,7 @@ struct CntDiag {
   int nrhs;
   __host__ __device__ int64_t operator()(const BoxDesc& d) const { return cdv(nrhs, DC); }
 };
+template <typename T>
 __global__ void __launch_bounds__(256) k_sweep_diag(SweepArgs a, int solve) {
   int64_t loc;
   int bi = find_item(a.desc, a.nbox, blockIdx.x, CntDiag{a.nrhs}, loc);
@@ -1651,47 +1670,48 @@ __global__ void __launch_bounds__(256) k_sweep_diag(SweepArgs a, int solve) {
   const int nc = min(DC, a.nrhs - c0);
   const int64_t r = d.r;
   const int32_t* R = a.fi + fi_R(d);
-  const double* M = a.fd + (solve ? fd_Xinv(d) : fd_XRR(d));
-  extern __shared__ double dsm[];
-  double* in = dsm;  // r x DC
+  const T* M = sweep_fd<T>(a) + (solve ? fd_Xinv(d) : fd_XRR(d));
+  T* F = sweep_F<T>(a);
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  T* in = reinterpret_cast<T*>(dsm_raw);  // r x DC
   for (int64_t e = threadIdx.x; e < r * DC; e += blockDim.x) {
     int64_t i = e / DC;
     int c = (int)(e % DC);
-    in[e] = (c < nc) ? a.F[((int64_t)R[i] - a.row_base) * a.nrhs + c0 + c] : 0.0;
+    in[e] = (c < nc) ? F[((int64_t)R[i] - a.row_base) * a.nrhs + c0 + c] : (T)0;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double out[DC];
+  T out[DC];
   if (!a.adjoint) {  // warp per row, lanes along the row (coalesced)
     for (int64_t i = warp; i < r; i += nw) {
 #pragma unroll
-      for (int c = 0; c < DC; ++c) out[c] = 0.0;
+      for (int c = 0; c < DC; ++c) out[c] = 0;
       for (int64_t q = lane; q < r; q += 32) {
-        double m = M[i * r + q];
+        T m = M[i * r + q];
 #pragma unroll
-        for (int c = 0; c < DC; ++c) out[c] = fma(m, in[q * DC + c], out[c]);
+        for (int c = 0; c < DC; ++c) out[c] = mad(m, in[q * DC + c], out[c]);
       }
 #pragma unroll
       for (int c = 0; c < DC; ++c)
         for (int o = 16; o; o >>= 1) out[c] += __shfl_xor_sync(0xffffffffu, out[c], o);
       if (lane < nc) {
-        double v = out[0];
+        T v = out[0];
 #pragma unroll
         for (int c = 1; c < DC; ++c)
           if (lane == c) v = out[c];
-        a.F[((int64_t)R[i] - a.row_base) * a.nrhs + c0 + lane] = v;
+        F[((int64_t)R[i] - a.row_base) * a.nrhs + c0 + lane] = v;
       }
     }
   } else {  // thread per row, reading column i of M (coalesced across threads)
     for (int64_t i = threadIdx.x; i < r; i += blockDim.x) {
 #pragma unroll
-      for (int c = 0; c < DC; ++c) out[c] = 0.0;
+      for (int c = 0; c < DC; ++c) out[c] = 0;
       for (int64_t q = 0; q < r; ++q) {
-        double m = M[q * r + i];
+        T m = M[q * r + i];
 #pragma unroll
-        for (int c = 0; c < DC; ++c) out[c] = fma(m, in[q * DC + c], out[c]);
+        for (int c = 0; c < DC; ++c) out[c] = mad(m, in[q * DC + c], out[c]);
       }
-      for (int c = 0; c < nc; ++c) a.F[((int64_t)R[i] - a.row_base) * a.nrhs + c0 + c] = out[c];
+      for (int c = 0; c < nc; ++c) F[((int64_t)R[i] - a.row_base) * a.nrhs + c0 + c] = out[c];
     }
   }
 }
@@ -1728,30 +1748,38 @@ __global__ void __launch_bounds__(256) k_dense_inverse(const double* LU, const i
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) inv[i * n + col] = x[i];
 }
 // Dense root block times rows of F: F[rows] <- A F[rows] (or A^T), one CTA per column.
-__global__ void k_dense_apply(const double* A, int64_t n, const int32_t* rows, int64_t row_base, double* F, int nrhs,
+template <typename T>
+__global__ void k_dense_apply(const T* A, int64_t n, const int32_t* rows, int64_t row_base, T* F, int nrhs,
                               int adjoint) {
-  extern __shared__ double col[];
-  double* out = col + n;
+  extern __shared__ __align__(16) unsigned char col_raw[];
+  T* col = reinterpret_cast<T*>(col_raw);
+  T* out = col + n;
   const int c = blockIdx.x;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) col[i] = F[((int64_t)rows[i] - row_base) * nrhs + c];
   __syncthreads();
   if (adjoint) {
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-      double v = 0.0;
-      for (int64_t q = 0; q < n; ++q) v = fma(A[q * n + i], col[q], v);
+      T v = 0;
+      for (int64_t q = 0; q < n; ++q) v = mad(A[q * n + i], col[q], v);
       out[i] = v;
     }
   } else {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int64_t i = warp; i < n; i += nw) {
-      double v = 0.0;
-      for (int64_t q = lane; q < n; q += 32) v = fma(A[i * n + q], col[q], v);
+      T v = 0;
+      for (int64_t q = lane; q < n; q += 32) v = mad(A[i * n + q], col[q], v);
       for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       if (lane == 0) out[i] = v;
     }
   }
   __syncthreads();
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) F[((int64_t)rows[i] - row_base) * nrhs + c] = out[i];
+}
+
+// FP32 -> FP64, elementwise.
+__global__ void k_f32_to_f64(const float* __restrict__ in, int64_t count, double* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) out[e] = (double)in[e];
 }
 
 template <class K, class Cnt>
@@ -1961,12 +1989,19 @@ void launch_dense_lu_solve(Launch L, const double* LU, const int32_t* piv, int64
 void launch_sweep_op(Launch L, const SweepArgs& a, int cset, int mat, int trans, int bset, double alpha,
                      int64_t items) {
   if (items <= 0) return;
-  k_sweep<<<grid1(items), 256, 0, L.st>>>(a, SweepOp{cset, mat, trans, bset, alpha});
+  if (a.F32) k_sweep<float><<<grid1(items), 256, 0, L.st>>>(a, SweepOp{cset, mat, trans, bset, alpha});
+  else k_sweep<double><<<grid1(items), 256, 0, L.st>>>(a, SweepOp{cset, mat, trans, bset, alpha});
   count_launch(L);
 }
 void launch_sweep_diag(Launch L, const SweepArgs& a, int solve, int64_t items, int max_r) {
   if (items <= 0) return;
-  k_sweep_diag<<<grid1(items), 256, (size_t)max_r * DC * sizeof(double), L.st>>>(a, solve);
+  if (a.F32) k_sweep_diag<float><<<grid1(items), 256, (size_t)max_r * DC * sizeof(float), L.st>>>(a, solve);
+  else k_sweep_diag<double><<<grid1(items), 256, (size_t)max_r * DC * sizeof(double), L.st>>>(a, solve);
+  count_launch(L);
+}
+void launch_to_f64(Launch L, const float* in, int64_t count, double* out) {
+  if (count <= 0) return;
+  k_f32_to_f64<<<(unsigned)cdv(count, 256), 256, 0, L.st>>>(in, count, out);
   count_launch(L);
 }
 void launch_dense_inverse(Launch L, const double* LU, const int32_t* piv, int64_t n, double* inv) {
@@ -1977,12 +2012,22 @@ void launch_dense_inverse(Launch L, const double* LU, const int32_t* piv, int64_
   k_dense_inverse<<<(unsigned)n, 256, smem, L.st>>>(LU, piv, n, inv);
   count_launch(L);
 }
+template <typename T>
+void dense_apply_t(Launch L, const T* A, int64_t n, const int32_t* rows, int64_t row_base, T* F, int nrhs,
+                   int adjoint) {
+  const size_t smem = 2 * (size_t)n * sizeof(T);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_dense_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_dense_apply<T><<<nrhs, 256, smem, L.st>>>(A, n, rows, row_base, F, nrhs, adjoint);
+  count_launch(L);
+}
 void launch_dense_apply(Launch L, const double* A, int64_t n, const int32_t* rows, int64_t row_base, double* F,
                         int nrhs, int adjoint) {
-  const size_t smem = 2 * (size_t)n * sizeof(double);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_dense_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_dense_apply<<<nrhs, 256, smem, L.st>>>(A, n, rows, row_base, F, nrhs, adjoint);
-  count_launch(L);
+  dense_apply_t(L, A, n, rows, row_base, F, nrhs, adjoint);
+}
+void launch_dense_apply(Launch L, const float* A, int64_t n, const int32_t* rows, int64_t row_base, float* F,
+                        int nrhs, int adjoint) {
+  dense_apply_t(L, A, n, rows, row_base, F, nrhs, adjoint);
 }
 
 // Item counts for host planning (same functors as the device decoding).

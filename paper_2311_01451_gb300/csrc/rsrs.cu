@@ -69,6 +69,10 @@ struct rsrs_factor {
   double* root_A = nullptr;
   double* root_LU = nullptr;
   double* root_inv = nullptr;  // A~_BtBt^-1, for the block-diagonal solve
+  // mixed precision: FP32 copies of the blocks (same offsets as fd) and of the root inverse, for
+  // the solve sweeps in FP32 arithmetic
+  float* fd32 = nullptr;
+  float* root_inv32 = nullptr;
   int32_t* root_piv = nullptr;
   int max_r = 0;
   double *Y = nullptr, *Z = nullptr, *Om = nullptr, *Ps = nullptr;  // kept sketches (shared, rows from base)
@@ -728,6 +732,8 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
   int32_t* fi;
   CU(dalloc(&fd, fd_total));
   CU(dalloc(&fi, fi_total));
+  float* fd32 = nullptr;
+  if (o.precision == RSRS_PREC_MIXED) CU(dalloc(&fd32, fd_total));
   CU(dalloc(&perm_all, Ntot));
   double* pts_all;
   {
@@ -751,8 +757,10 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
       CU(dalloc(&F[p]->root_LU, nroot * nroot));
       CU(dalloc(&F[p]->root_piv, nroot));
       CU(dalloc(&F[p]->root_inv, nroot * nroot));
+      if (fd32) CU(dalloc(&F[p]->root_inv32, nroot * nroot));
       F[p]->desc_dev = desc_dev;
       F[p]->fd = fd;
+      F[p]->fd32 = fd32;
       F[p]->fi = fi;
       if (o.keep_sketches) {
         F[p]->Y = Y;
@@ -1071,6 +1079,13 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
       CU(cudaMemcpyAsync(F[p]->root_LU, F[p]->root_A, nroot * nroot * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
     if (rl_dev) timed(RSRS_K_ROOT, [&] { launch_root_lu_inverse(L, rl_dev, (int)rl.size(), max_root, err); });
+    if (fd32)  // FP32 copies for the mixed factor's solves
+      timed(RSRS_K_ROOT, [&] {
+        launch_to_f32(L, fd, fd_total, fd32);
+        for (int p = 0; p < nprob; ++p)
+          if (F[p]->root_size > 0)
+            launch_to_f32(L, F[p]->root_inv, F[p]->root_size * F[p]->root_size, F[p]->root_inv32);
+      });
     for (int p = 0; p < nprob; ++p) {
       const int64_t nroot = F[p]->root_size;
       if (nroot == 0) continue;
@@ -1151,6 +1166,7 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
       }
     f->stats.n_boxes = nb;
     f->stats.factor_bytes = fdb * 8 + fib * 4 + f->root_size * f->root_size * 24 + f->root_size * 8;
+    if (f->fd32) f->stats.factor_bytes += fdb * 4 + f->root_size * f->root_size * 4;
     out[p] = F[p].release();
   }
   return RSRS_OK;
@@ -1500,7 +1516,11 @@ extern "C" rsrs_status rsrs_autotune(int nprob, const rsrs_tree* const* trees, c
 // ---- sweeps on a tree-order row-major block ------------------------------------------
 namespace {
 
-rsrs_status sweep_solve(const rsrs_factor* f, Launch L, double* W, int nrhs, int adjoint) {
+// W <- A_approx^-1 W (eq. Ainvfact).  A mixed-precision factor solves in FP32 arithmetic when the
+// caller passes w32 (N x nrhs floats): W is converted once, swept with the FP32 copies of the
+// blocks, and converted back (its corrections feed FP64 refinement, whose residual sets the final
+// accuracy); an FP64 factor, or w32 null, sweeps in FP64.
+rsrs_status sweep_solve(const rsrs_factor* f, Launch L, double* W, int nrhs, int adjoint, float* w32 = nullptr) {
   SweepArgs a{};
   a.fd = f->fd;
   a.fi = f->fi;
@@ -1508,6 +1528,12 @@ rsrs_status sweep_solve(const rsrs_factor* f, Launch L, double* W, int nrhs, int
   a.nrhs = nrhs;
   a.adjoint = adjoint;
   a.row_base = f->base;
+  const bool fp32 = w32 && f->fd32;
+  if (fp32) {
+    a.fd32 = f->fd32;
+    a.F32 = w32;
+    launch_to_f32(L, W, f->n * nrhs, w32);
+  }
   // upward: V_1^-1 first (V^-1 = L E), or W^-* = U^* F^* for the adjoint
   for (const GroupView& g : f->groups) {
     a.desc = f->desc_dev + g.desc_off;
@@ -1523,7 +1549,10 @@ rsrs_status sweep_solve(const rsrs_factor* f, Launch L, double* W, int nrhs, int
     a.nbox = (int)g.h.size();
     launch_sweep_diag(L, a, 1, items_diag(g.h, nrhs), g.max_r);
   }
-  if (f->root_size > 0) launch_dense_apply(L, f->root_inv, f->root_size, f->root_idx, f->base, W, nrhs, adjoint);
+  if (f->root_size > 0) {
+    if (fp32) launch_dense_apply(L, f->root_inv32, f->root_size, f->root_idx, f->base, w32, nrhs, adjoint);
+    else launch_dense_apply(L, f->root_inv, f->root_size, f->root_idx, f->base, W, nrhs, adjoint);
+  }
   for (auto it = f->groups.rbegin(); it != f->groups.rend(); ++it) {
     const GroupView& g = *it;
     a.desc = f->desc_dev + g.desc_off;
@@ -1534,6 +1563,7 @@ rsrs_status sweep_solve(const rsrs_factor* f, Launch L, double* W, int nrhs, int
       launch_sweep_op(L, a, 0, /*LcT*/ 1, 0, 2, -1.0, items_sweep(g.h, 0));
     launch_sweep_op(L, a, /*C=S*/ 1, /*T*/ 0, 0, /*B=R*/ 0, -1.0, items_sweep(g.h, 1));
   }
+  if (fp32) launch_to_f64(L, w32, f->n * nrhs, W);
   CU(cudaGetLastError());
   return RSRS_OK;
 }
@@ -1592,9 +1622,11 @@ rsrs_status rsrs_solve(const rsrs_factor* f, double* F, int64_t ldf, int32_t nrh
   Launch L{st, nullptr};
   DevPool pool;
   double* W;
+  float* w32 = nullptr;
   CU(pool.alloc(&W, f->n * nrhs));
+  if (f->fd32) CU(pool.alloc(&w32, f->n * nrhs));
   k_cm_to_rows<<<nblk(f->n * nrhs), 256, 0, st>>>(F, ldf, f->perm_dev, f->n, nrhs, W);
-  r = sweep_solve(f, L, W, nrhs, adjoint);
+  r = sweep_solve(f, L, W, nrhs, adjoint, w32);
   if (r != RSRS_OK) return r;
   k_rows_to_cm<<<nblk(f->n * nrhs), 256, 0, st>>>(W, f->perm_dev, f->n, nrhs, F, ldf);
   CU(cudaGetLastError());
@@ -1659,6 +1691,8 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_
   CU(pool.alloc(&Wr, tot));
   CU(pool.alloc(&Wax, tot));
   CU(pool.alloc(&nrm, 2 * 64));
+  float* w32 = nullptr;
+  if (f->fd32) CU(pool.alloc(&w32, tot));
   if (f->kind == RSRS_OP_CALLBACK) {
     CU(pool.alloc(&c1, tot));
     CU(pool.alloc(&c2, tot));
@@ -1669,7 +1703,7 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_
   k_cm_to_rows<<<nblk(tot), 256, 0, st>>>(B, ld, f->perm_dev, f->n, nrhs, Wb);
   ++nl;
   CU(cudaMemcpyAsync(Wx, Wb, tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  r = sweep_solve(f, L, Wx, nrhs, 0);
+  r = sweep_solve(f, L, Wx, nrhs, 0, w32);
   if (r != RSRS_OK) return r;
   double hn[128];
   CU(cudaMemsetAsync(nrm, 0, 64 * sizeof(double), st));
@@ -1699,7 +1733,7 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_
     if (it < 64) rr.history[it] = rel;
     if (!std::isfinite(rel)) return fail(RSRS_E_NONFINITE, "refine: non-finite residual");
     if (rel <= rtol || it >= maxit) break;
-    r = sweep_solve(f, L, Wr, nrhs, 0);
+    r = sweep_solve(f, L, Wr, nrhs, 0, w32);
     if (r != RSRS_OK) return r;
     k_axpy<<<nblk(tot), 256, 0, st>>>(Wx, Wr, 1.0, tot);
     ++nl;
@@ -1860,6 +1894,8 @@ rsrs_status rsrs_gmres(const rsrs_factor* f, const double* B, double* X, int64_t
   CU(pool.alloc(&Ww, tot));
   CU(pool.alloc(&V, (int64_t)(m + 1) * tot));
   CU(pool.alloc(&Z, (int64_t)m * tot));
+  float* w32 = nullptr;  // the mixed factor's FP32 solve (the stored z_k keep GMRES exact in it)
+  if (f->fd32) CU(pool.alloc(&w32, tot));
   CU(pool.alloc(&gm.part, (int64_t)(m + 1) * gm.nchunk * c));
   CU(pool.alloc(&gm.h_dev, (int64_t)(m + 1) * c));
   if (f->kind == RSRS_OP_CALLBACK) {
@@ -1918,7 +1954,7 @@ rsrs_status rsrs_gmres(const rsrs_factor* f, const double* B, double* X, int64_t
       double* Vk = V + (int64_t)k * tot;
       double* Zk = Z + (int64_t)k * tot;
       CU(cudaMemcpyAsync(Zk, Vk, tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      r = sweep_solve(f, L, Zk, c, 0);  // z_k = M^-1 v_k
+      r = sweep_solve(f, L, Zk, c, 0, w32);  // z_k = M^-1 v_k
       if (r != RSRS_OK) return r;
       r = apply_A(Zk, Ww);              // w = A z_k
       if (r != RSRS_OK) return r;
@@ -2085,11 +2121,14 @@ rsrs_status rsrs_factor_sketches(const rsrs_factor* f, double* Yh, double* Zh, d
 // ---- solve without device allocation ---------------------------------------------------------
 // One static staging buffer per device (the module's copy of this array on that device).
 static __device__ __align__(256) double g_noalloc_stage[RSRS_NOALLOC_MAX_ELEMS];
+// ... and its FP32 copy, for a mixed-precision factor's FP32 solve
+static __device__ __align__(256) float g_noalloc_stage32[RSRS_NOALLOC_MAX_ELEMS];
 
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 double* g_noalloc_addr[kMaxDevices] = {};
+float* g_noalloc_addr32[kMaxDevices] = {};
 }  // namespace
 
 extern "C" rsrs_status rsrs_solve_noalloc(const rsrs_factor* f, double* F, int64_t ldf, int32_t nrhs, int adjoint,
@@ -2104,19 +2143,24 @@ extern "C" rsrs_status rsrs_solve_noalloc(const rsrs_factor* f, double* F, int64
   CU(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return fail(RSRS_E_INVAL, "solve_noalloc: device ordinal out of range");
   double* W = nullptr;
+  float* W32 = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_addr[dev]) {  // set-up, once per device, with that device current
       void* p = nullptr;
+      void* p32 = nullptr;
       CU(cudaGetSymbolAddress(&p, g_noalloc_stage));
+      CU(cudaGetSymbolAddress(&p32, g_noalloc_stage32));
       g_noalloc_addr[dev] = static_cast<double*>(p);
+      g_noalloc_addr32[dev] = static_cast<float*>(p32);
     }
     W = g_noalloc_addr[dev];
+    W32 = g_noalloc_addr32[dev];
   }
   cudaStream_t st = (cudaStream_t)stream;
   Launch L{st, nullptr};
   k_cm_to_rows<<<nblk(f->n * nrhs), 256, 0, st>>>(F, ldf, f->perm_dev, f->n, nrhs, W);
-  r = sweep_solve(f, L, W, nrhs, adjoint);
+  r = sweep_solve(f, L, W, nrhs, adjoint, f->fd32 ? W32 : nullptr);
   if (r != RSRS_OK) return r;
   k_rows_to_cm<<<nblk(f->n * nrhs), 256, 0, st>>>(W, f->perm_dev, f->n, nrhs, F, ldf);
   CU(cudaGetLastError());

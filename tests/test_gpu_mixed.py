@@ -90,9 +90,10 @@ def test_mixed_tensor_core_products(R, name):
 
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_mixed_solve_apply_inverse_pair(R, name):
-    """The mixed factor's sweeps run in float-float arithmetic on its FP64 blocks: its solve and apply
-    are exact inverses of each other to FP64-level rounding (adjoints too), and the solve agrees
-    with the FP64 refinement target to the factor's own accuracy."""
+    """The mixed factor's solve sweeps in FP32 arithmetic on FP32 copies of its blocks, its apply in
+    FP64: the two are inverses of each other to the FP32 solve's rounding (2^-24 times the sweeps'
+    growth; 2.4e-7..2.7e-7 measured, held to 32 x 2^-24 = 1.9e-6), adjoints too, and the solve
+    agrees with the FP64 refinement target to the factor's own accuracy."""
     pr = CASES[name]()
     tree = R.Tree(pr.points, pr.leaf)
     s = max(pr.s_cfg, tree.info(pr.k).s_req_mixed)
@@ -101,7 +102,7 @@ def test_mixed_solve_apply_inverse_pair(R, name):
     b = pr.rhs()
     for adj in (False, True):
         y = f.apply(f.solve(_to_gpu(b), adjoint=adj), adjoint=adj).cpu().numpy().T
-        assert np.linalg.norm(y - b) / np.linalg.norm(b) < 1e-12, adj
+        assert np.linalg.norm(y - b) / np.linalg.norm(b) < 32 * 2.0 ** -24, adj
     xd = np.linalg.solve(ops.make_operator(pr).dense(), b)
     x0 = f.solve(_to_gpu(b)).cpu().numpy().T
     assert np.linalg.norm(x0 - xd) / np.linalg.norm(xd) < 1e-2

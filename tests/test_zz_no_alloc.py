@@ -29,13 +29,16 @@ def R():
     return pkg
 
 
-@pytest.fixture(scope="module")
-def factor(R):
+@pytest.fixture(scope="module", params=["fp64", "mixed"])
+def factor(R, request):
+    """An FP64 factor (FP64 sweeps) and a mixed-precision one (FP32 sweeps through the second static
+    buffer)."""
     pr = W.small_problem(n=3000, d=2, leaf=24, k=10, nrhs=3, seed_problem=3)
     tree = R.Tree(pr.points, pr.leaf)
-    s = tree.info(pr.k).s_req
+    mixed = request.param == "mixed"
+    s = tree.info(pr.k).s_req_mixed if mixed else tree.info(pr.k).s_req
     f = R.Factor(tree, R.RSRS_OP_LOG2D, pr.k, s, shift=pr.diag_shift, scale=pr.scale,
-                 precision=R.RSRS_PREC_FP64, seed=5)
+                 precision=R.RSRS_PREC_MIXED if mixed else R.RSRS_PREC_FP64, seed=5)
     return pr, f
 
 
