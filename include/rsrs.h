@@ -75,9 +75,10 @@ typedef struct {
 enum {
   RSRS_PREC_FP64 = 0,   /* every step in FP64                                               */
   RSRS_PREC_MIXED = 1   /* FP32 arithmetic (FP64 storage) for the sampling product, the      */
-                        /* near-field Grams, Cholesky factors, projections and the E/F and  */
-                        /* Schur updates; FP64 for the CPQR pivots, extraction, the X_RR    */
-                        /* LU, the root, the solve and the refinement residual             */
+                        /* near-field Grams, Cholesky factors, projections, the E/F and     */
+                        /* Schur updates, X_RR^-1 (Gauss-Jordan with partial pivoting; from */
+                        /* an FP64 LU when r > 224), Lc, Uc and the solve sweeps; FP64 for  */
+                        /* the CPQR pivots, extraction, the root and the refinement residual */
 };
 
 /* Tile shapes of the tensor-core sampling product: accumulators of 128 rows per CTA x column tile x
@@ -132,9 +133,10 @@ typedef struct {
                           /* up to 16 CTAs), pivots chosen on FP64 residual norms, when */
                           /* the box fits; 1 = FP64 CPQR in global memory (FP64 always) */
   int mixed_gemm;         /* mixed precision: 0 default = Grams, their blocked Cholesky   */
-                          /* factors and L^-T, least-squares right-hand sides, solves  */
-                          /* and projection updates as 3xTF32 tcgen05 products;        */
-                          /* 1 = FP32 SIMT (Cholesky and substitution)                 */
+                          /* factors and L^-T, least-squares right-hand sides, solves, */
+                          /* projection updates, Lc and Uc as 3xTF32 tcgen05 products */
+                          /* (X_RR^-1 by FP32 Gauss-Jordan);                           */
+                          /* 1 = FP32 SIMT (Cholesky and substitution, FP64 X_RR LU)    */
   int use_graph;          /* 1: capture the build's launch sequence as one CUDA graph    */
                           /* kept with the factors, so rsrs_refactor can replay it;    */
                           /* needs device-drawn test matrices; no per-class timings   */

@@ -193,8 +193,24 @@ void launch_ef_update(Launch L, const GroupArgs& g, int64_t items);             
 void launch_extract(Launch L, const GroupArgs& g, int64_t items);                  // X blocks
 void launch_lu(Launch L, const GroupArgs& g);                                      // LU(X_RR)
 void launch_lu_rhs(Launch L, const GroupArgs& g, int64_t items);                   // Lc, Uc
-// L, U on the sketches; the mixed path first makes FP32 copies of LcT, Uc, Y_R, Z_R (prep_items blocks)
-void launch_schur(Launch L, const GroupArgs& g, int64_t items, int64_t prep_items);
+// Mixed path with tensor cores: X_RR^-1 alone by substitution, FP32 staging of it (and its
+// transpose) and of the right-hand blocks, Uc and Lc^T as 3xTF32 products straight into the Schur
+// update's FP32 operands, and those results written back to the factor in FP64.
+void launch_lu_inv(Launch L, const GroupArgs& g, int64_t items);
+// ... or, for groups whose boxes have r <= 224, X_RR^-1 by FP32 Gauss-Jordan in shared memory (one
+// CTA per box; no LU needed), which also stages it: false (nothing launched) when max_r is larger.
+bool launch_gj_inv32(Launch L, const GroupArgs& g, int max_r);
+void launch_lcuc_prep(Launch L, const GroupArgs& g, int64_t items, int with_inv);
+void launch_lcuc_tc(Launch L, const GroupArgs& g, const std::vector<BoxDesc>& h);
+void launch_lcuc_store(Launch L, const GroupArgs& g, int64_t items);
+// L, U on the sketches; the mixed path first makes FP32 copies of LcT, Uc (unless yz_only: already
+// there), Y_R, Z_R (prep_items blocks)
+// tc: the group's boxes, to run the updates as 3xTF32 tensor-core products (mixed path only)
+void launch_schur(Launch L, const GroupArgs& g, int64_t items, int64_t prep_items, int yz_only = 0,
+                  const std::vector<BoxDesc>* tc = nullptr);
+// The four block-elimination updates of the FP64 sketches as grouped 3xTF32 tcgen05 products (FP32
+// operands staged by k_schur_prep / the Lc-Uc products, FP64 read-modify-write of the sketch rows).
+void launch_schur_tc(Launch L, const GroupArgs& g, const std::vector<BoxDesc>& h);
 
 // Number of 64-row x 64-col tiles for the group kernels (host-side planning).
 constexpr int kT = 64;
@@ -250,7 +266,10 @@ int64_t items_ef(const std::vector<BoxDesc>& h, int64_t s);
 int64_t items_extract(const std::vector<BoxDesc>& h);
 int64_t items_lu_rhs(const std::vector<BoxDesc>& h);
 int64_t items_schur(const std::vector<BoxDesc>& h, int64_t s);
-int64_t items_schur_prep(const std::vector<BoxDesc>& h, int64_t s);
+int64_t items_schur_prep(const std::vector<BoxDesc>& h, int64_t s, int yz_only = 0);
+int64_t items_lu_inv(const std::vector<BoxDesc>& h);
+int64_t items_lcuc_prep(const std::vector<BoxDesc>& h, int with_inv);
+int64_t items_lcuc_store(const std::vector<BoxDesc>& h);
 int64_t items_sweep(const std::vector<BoxDesc>& h, int cset);
 int64_t items_diag(const std::vector<BoxDesc>& h, int nrhs);
 

@@ -55,6 +55,12 @@ struct TcTile {
   int64_t ldd;
   float alpha, beta;
   float* D2 = nullptr;  // when set, also D2(i, j) += alpha * acc (same ldd)
+  // Operand forms of the Schur updates only (jobs with sketch_io<Job>::value):
+  int anm = 0;                     // A stored K x M: element (i, k) at A + k * lda + i
+  const double* B64 = nullptr;     // bnm = 1, FP64 rows gathered: (k, j) at B64 + bidx[k] * ldb + j
+  const int32_t* bidx = nullptr;
+  double* D64 = nullptr;           // FP64 rows gathered: D64(didx[i], j) += alpha * acc (in FP64)
+  const int32_t* didx = nullptr;
 };
 
 // Job functors: tiles per box (count) and the tile for a box-local index (tile).
@@ -306,6 +312,102 @@ struct SolveCJob {  // X = T U^T (U upper: column block j needs columns >= 128 j
   }
 };
 
+struct LcUcJob {  // Uc = X_RR^-1 [X_RS X_RN] (side 0), Lc^T = X_RR^-T [X_SR^T X_NR^T] (side 1), r x w each
+  __device__ int64_t count(const BoxDesc& d) const { return 2 * cdiv128(d.r) * cdiv128((int64_t)d.kp + d.n); }
+  __device__ TcTile tile(const GroupArgs& g, const BoxDesc& d, int64_t loc) const {
+    const int64_t r = d.r, w = (int64_t)d.kp + d.n, nt = cdiv128(w), per = cdiv128(r) * nt;
+    const int side = (int)(loc / per);
+    const int64_t ti = (loc % per) / nt, tj = (loc % per) % nt;
+    float* wc = reinterpret_cast<float*>(g.workc);
+    const float* P = wc + d.w_off;  // [X_RR^-1 | X_RR^-T | Uc's right-hand block | Lc^T's] (k_lcuc_prep)
+    TcTile t;
+    t.A = P + (side == 0 ? 0 : r * r) + ti * GM * r;
+    t.lda = r;
+    t.m = rows_of(r, ti);
+    t.B = P + 2 * r * r + (int64_t)side * r * w + tj * GN;  // element (k, n) at B + k w + n
+    t.ldb = w;
+    t.n = (int)imin64(GN, w - tj * GN);
+    t.bnm = 1;
+    t.K = r;
+    t.D = wc + d.e_off + (side == 0 ? r * w : 0) + ti * GM * w + tj * GN;  // the Schur update's operands
+    t.ldd = w;
+    t.alpha = 1.f;
+    t.beta = 0.f;
+    return t;
+  }
+};
+
+// Block elimination on the sketches (the Schur complement of X_RR, Algorithm 1): with Lc = LcT^T
+// (w x r) and Uc (r x w), w = k' + n, stored FP32 in the extraction area, and Y_R, Z_R staged FP32
+// in the sketch area (k_schur_prep):
+//   product 0: Y_SN -= Lc Y_R        (A = LcT read K x M, B = Y_R)
+//   product 1: Om_R += Uc Om_SN      (A = Uc,             B = Om rows SN, FP64)
+//   product 2: Z_SN -= Uc^T Z_R      (A = Uc read K x M,  B = Z_R)
+//   product 3: Ps_R += Lc^T Ps_SN    (A = LcT,            B = Ps rows SN, FP64)
+// each into the FP64 sketch rows in place.  Same-colour boxes touch disjoint rows.
+struct SchurJob {
+  int64_t s;
+  __device__ int64_t count(const BoxDesc& d) const {
+    return 2 * (cdiv128((int64_t)d.kp + d.n) + cdiv128(d.r)) * cdiv128(s);
+  }
+  __device__ TcTile tile(const GroupArgs& g, const BoxDesc& d, int64_t loc) const {
+    const int64_t r = d.r, w = (int64_t)d.kp + d.n, nt = cdiv128(s);
+    const int64_t pw = cdiv128(w) * nt, pr = cdiv128(r) * nt;
+    int prod;
+    if (loc < pw) prod = 0;
+    else if ((loc -= pw) < pr) prod = 1;
+    else if ((loc -= pr) < pw) prod = 2;
+    else {
+      loc -= pw;
+      prod = 3;
+    }
+    const int64_t ti = loc / nt, tj = loc % nt;
+    const float* wc = reinterpret_cast<const float*>(g.workc);
+    const float* LcT = wc + d.e_off;
+    const float* Uc = LcT + r * w;
+    const int32_t* R = g.fi + fi_R(d);
+    const int32_t* SN = g.fi + fi_S(d);
+    TcTile t;
+    t.bnm = 1;
+    t.ldb = s;
+    t.n = (int)imin64(GN, s - tj * GN);
+    t.D = nullptr;
+    t.ldd = s;
+    t.beta = 1.f;
+    if (prod == 0 || prod == 2) {  // M = w (rows SN), K = r
+      t.anm = 1;
+      t.A = (prod == 0 ? LcT : Uc) + ti * GM;
+      t.lda = w;
+      t.m = rows_of(w, ti);
+      t.B = wc + d.mc_off + (prod == 0 ? 0 : r * s) + tj * GN;
+      t.K = r;
+      t.D64 = (prod == 0 ? g.Y : g.Z) + tj * GN;
+      t.didx = SN + ti * GM;
+      t.alpha = -1.f;
+    } else {  // M = r (rows R), K = w
+      t.A = (prod == 1 ? Uc : LcT) + ti * GM * w;
+      t.lda = w;
+      t.m = rows_of(r, ti);
+      t.B = nullptr;
+      t.B64 = (prod == 1 ? g.Om : g.Ps) + tj * GN;
+      t.bidx = SN;
+      t.K = w;
+      t.D64 = (prod == 1 ? g.Om : g.Ps) + tj * GN;
+      t.didx = R + ti * GM;
+      t.alpha = 1.f;
+    }
+    return t;
+  }
+};
+template <class Job>
+struct sketch_io {
+  static constexpr bool value = false;
+};
+template <>
+struct sketch_io<SchurJob> {
+  static constexpr bool value = true;
+};
+
 template <class Job>
 __device__ int find_box(const BoxDesc* desc, int nbox, int64_t item, const Job& job, int64_t& local) {
   // block-wide prefix sum over the boxes' tile counts, blockDim.x boxes at a time
@@ -377,6 +479,20 @@ __device__ __forceinline__ void load_col16(float v[16], const float* src, bool k
     for (int q = 0; q < 16; ++q) v[q] = (k_ok && q < nleft) ? __ldg(src + q) : 0.f;
   }
 }
+// 16 consecutive columns of one K row of an FP64 operand, rounded to FP32 (zero outside).
+__device__ __forceinline__ void load_col16_f64(float v[16], const double* src, bool k_ok, int nleft, bool vec) {
+  if (k_ok && vec && nleft >= 16) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const double2 x = __ldg(reinterpret_cast<const double2*>(src) + q);
+      v[2 * q] = (float)x.x;
+      v[2 * q + 1] = (float)x.y;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = (k_ok && q < nleft) ? (float)__ldg(src + q) : 0.f;
+  }
+}
 // Split into TF32 hi/lo and store row `row`, K positions k0l .. k0l + 15, of the swizzled tiles.
 __device__ __forceinline__ void store_row16(unsigned char* hi, unsigned char* lo, int row, int k0l, const float v[16]) {
 #pragma unroll
@@ -420,6 +536,7 @@ __global__ void __launch_bounds__(GTHREADS, 1) k_tc_grouped(GroupArgs g, Job job
   const TcTile t = job.tile(g, d, loc);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t nchunk = (t.K + GK - 1) / GK;
+  constexpr bool kIO = sketch_io<Job>::value;
   if (tid == 0) {
     s_timeout = 0;
     for (int s = 0; s < GNST; ++s) {
@@ -438,15 +555,27 @@ __global__ void __launch_bounds__(GTHREADS, 1) k_tc_grouped(GroupArgs g, Job job
     // A: row tid/2, K half (tid&1)*16.  B (K-contiguous): the same.  B (N-contiguous): k = tid%32,
     // columns (tid/32)*16 .. +15, transposed into rows n of the K-major tile.  The operands of the
     // next slice are loaded into registers while this slice is split and stored.
+    // Sketch-update jobs: A may be stored K x M (loaded and stored like an N-contiguous B) and B
+    // may be FP64 rows gathered through an index list.
     const int r = tid >> 1, kh = (tid & 1) * 16;
+    const bool anm = kIO && t.anm;
     const bool avec = ((t.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(t.A) & 15) == 0);
-    const bool bvec = ((t.ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(t.B) & 15) == 0);
+    const bool bvec = kIO && t.B64 ? (((t.ldb & 1) == 0) && ((reinterpret_cast<uintptr_t>(t.B64) & 15) == 0))
+                                   : (((t.ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(t.B) & 15) == 0));
     const int bk = tid & 31, bn0 = (tid >> 5) * 16;
     auto load = [&](int64_t ch, float va[16], float vb[16]) {
       const int64_t k0 = ch * GK;
-      load_row16(va, t.A + (int64_t)r * t.lda + k0 + kh, r < t.m, t.K - k0 - kh, avec);
-      if (!t.bnm) load_row16(vb, t.B + (int64_t)r * t.ldb + k0 + kh, r < t.n, t.K - k0 - kh, bvec);
-      else load_col16(vb, t.B + (k0 + bk) * t.ldb + bn0, k0 + bk < t.K, t.n - bn0, bvec);
+      if (anm) load_col16(va, t.A + (k0 + bk) * t.lda + bn0, k0 + bk < t.K, t.m - bn0, avec);
+      else load_row16(va, t.A + (int64_t)r * t.lda + k0 + kh, r < t.m, t.K - k0 - kh, avec);
+      if (!t.bnm) {
+        load_row16(vb, t.B + (int64_t)r * t.ldb + k0 + kh, r < t.n, t.K - k0 - kh, bvec);
+      } else if (kIO && t.B64) {
+        const bool k_ok = k0 + bk < t.K;
+        const double* src = k_ok ? t.B64 + (int64_t)t.bidx[k0 + bk] * t.ldb + bn0 : t.B64;
+        load_col16_f64(vb, src, k_ok, t.n - bn0, bvec);
+      } else {
+        load_col16(vb, t.B + (k0 + bk) * t.ldb + bn0, k0 + bk < t.K, t.n - bn0, bvec);
+      }
     };
     float va[16], vb[16], na[16], nb[16];
     if (nchunk > 0) load(0, va, vb);
@@ -459,7 +588,8 @@ __global__ void __launch_bounds__(GTHREADS, 1) k_tc_grouped(GroupArgs g, Job job
       unsigned char* Blo = Bhi + OP_BYTES;
       if (ch + 1 < nchunk) load(ch + 1, na, nb);
       if (ch >= GNST && !bar_wait(smem_u32(&empty[st]), (uint32_t)((u - 1) & 1))) s_timeout = 1;
-      store_row16(Ahi, Alo, r, kh, va);
+      if (anm) store_col16(Ahi, Alo, bn0, bk, va);
+      else store_row16(Ahi, Alo, r, kh, va);
       if (!t.bnm) store_row16(Bhi, Blo, r, kh, vb);
       else store_col16(Bhi, Blo, bn0, bk, vb);
       fence_proxy_async();
@@ -495,6 +625,20 @@ __global__ void __launch_bounds__(GTHREADS, 1) k_tc_grouped(GroupArgs g, Job job
       if (colbase + cc >= t.n) break;  // warp-uniform
       uint32_t rr[16];
       tmem_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(colbase + cc), rr);
+      if (kIO && t.D64) {  // FP64 sketch rows, read-modify-write in FP64
+        if (row < t.m) {
+          double* drow = t.D64 + (int64_t)t.didx[row] * t.ldd + colbase + cc;
+          const double al = (double)t.alpha;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            if (colbase + cc + q < t.n) {
+              const float acc = nchunk > 0 ? __uint_as_float(rr[q]) : 0.f;
+              drow[q] = drow[q] + al * (double)acc;
+            }
+          }
+        }
+        continue;
+      }
       if (row < t.m) {
         float* drow = t.D + (int64_t)row * t.ldd + colbase + cc;
 #pragma unroll
@@ -750,6 +894,17 @@ void launch_chol_tc(Launch L, const GroupArgs& g, const std::vector<BoxDesc>& h)
   for (int i = 1; i < (int)nbmax; ++i)
     launch_job(L, g, InvColJob{i},
                items_of_h(h, [i](const BoxDesc& d) { return cdiv128(d.l) > i ? 2 * (int64_t)i : (int64_t)0; }));
+}
+void launch_lcuc_tc(Launch L, const GroupArgs& g, const std::vector<BoxDesc>& h) {
+  launch_job(L, g, LcUcJob{}, items_of_h(h, [](const BoxDesc& d) {
+               return 2 * cdiv128(d.r) * cdiv128((int64_t)d.kp + d.n);
+             }));
+}
+void launch_schur_tc(Launch L, const GroupArgs& g, const std::vector<BoxDesc>& h) {
+  const int64_t s = g.s;
+  launch_job(L, g, SchurJob{s}, items_of_h(h, [s](const BoxDesc& d) {
+               return 2 * (cdiv128((int64_t)d.kp + d.n) + cdiv128(d.r)) * cdiv128(s);
+             }));
 }
 void launch_solve_tc(Launch L, const GroupArgs& g, int pass, const std::vector<BoxDesc>& h) {
   const int64_t items = items_of_h(h, [](const BoxDesc& d) { return 2 * cdiv128(d.b) * cdiv128(d.l); });

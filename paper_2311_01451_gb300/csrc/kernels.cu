@@ -15,6 +15,8 @@
 #include <cfloat>
 #include <cmath>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace rsrs {
@@ -1454,6 +1456,169 @@ __global__ void __launch_bounds__(CW) k_lu_rhs(GroupArgs g) {
   lu_solve_col(LU, piv, d.r, B + col, w, side == 1);
 }
 
+// Mixed path: only X_RR^-1 by substitution (one thread per column); Uc and Lc^T then come from
+// tensor-core products with it (k_tc_grouped<LcUcJob>), staged by k_lcuc_prep and written back to the
+// factor by k_lcuc_store.
+struct CntLuInv {
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const { return cdv(d.r, CW); }
+};
+__global__ void __launch_bounds__(CW) k_lu_inv(GroupArgs g) {
+  int64_t loc;
+  int bi = find_item(g.desc, g.nbox, blockIdx.x, CntLuInv(), loc);
+  if (bi < 0) return;
+  const BoxDesc d = g.desc[bi];
+  const int64_t col = loc * CW + threadIdx.x;
+  if (col >= d.r) return;
+  double* B = g.fd + fd_Xinv(d);
+  for (int64_t i = 0; i < d.r; ++i) B[i * d.r + col] = (i == col) ? 1.0 : 0.0;
+  lu_solve_col(g.fd + fd_LU(d), g.fi + fi_piv(d), d.r, B + col, d.r, false);
+}
+
+// Mixed path: X_RR^-1 by in-place Gauss-Jordan elimination with partial pivoting (ties to the lower
+// row) in FP32 shared memory, one CTA of 1024 threads per box (r <= GJ_MAX_R).  Per step k: the
+// pivot row p (largest |A_ik|, i >= k), the multipliers of column k, then row k <- row p / pivot with
+// A_kk replaced by 1 before the division, row p <- old row k, and every other row minus its
+// multiplier times row k with its column-k entry replaced by 0.  The row interchanges become column
+// interchanges of the result, applied in reverse step order.  Writes X_RR^-1 to the factor (FP64
+// copy of the FP32 values) and X_RR^-1, X_RR^-T (FP32) to the head of the box's near-field test-row
+// area for the products that make Uc and Lc^T.  A zero or non-finite pivot records kDevSingular or
+// kDevNonfinite (and continues with 1).  The result carries FP32 rounding times cond(X_RR), the
+// accuracy of the FP32 products and sweeps that use it.
+constexpr int GJ_MAX_R = 224;
+__host__ __device__ inline size_t gj_smem_bytes(int r) { return ((size_t)r * r + (size_t)3 * r) * 4; }
+__global__ void __launch_bounds__(1024, 1) k_gj_inv32(GroupArgs g) {
+  const BoxDesc d = g.desc[blockIdx.x];
+  const int r = d.r;
+  if (r <= 0) return;
+  extern __shared__ __align__(16) unsigned char gj_raw[];
+  float* A = reinterpret_cast<float*>(gj_raw);  // r x r, row-major
+  float* col = A + (size_t)r * r;                // multipliers of the step's column
+  int* ipiv = reinterpret_cast<int*>(col + r);   // pivot row of each step
+  int* idx = ipiv + r;                           // column order of the result
+  __shared__ int s_p;
+  __shared__ float s_inv;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+  const double* X = g.fd + fd_XRR(d);
+  for (int e = tid; e < r * r; e += nt) A[e] = (float)X[e];
+  __syncthreads();
+  for (int k = 0; k < r; ++k) {
+    if (warp == 0) {  // pivot search in column k, rows k..r-1
+      float bv = -1.f;
+      int bp = -1;
+      for (int i = k + lane; i < r; i += 32) {
+        const float v = fabsf(A[(size_t)i * r + k]);
+        if (v > bv) {  // ascending i per lane: ties keep the lower row
+          bv = v;
+          bp = i;
+        }
+      }
+      for (int o = 16; o; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+        if (op >= 0 && (ov > bv || (ov == bv && (bp < 0 || op < bp)))) {
+          bv = ov;
+          bp = op;
+        }
+      }
+      if (lane == 0) {
+        int p = bp < 0 ? k : bp;
+        float pv = A[(size_t)p * r + k];
+        if (!(bv > 0.f)) set_err(g.err, kDevSingular);
+        else if (!isfinite(bv)) set_err(g.err, kDevNonfinite);
+        if (!(bv > 0.f) || !isfinite(bv)) pv = 1.f;
+        s_p = p;
+        s_inv = 1.f / pv;
+        ipiv[k] = p;
+      }
+    }
+    __syncthreads();
+    const int p = s_p;
+    const float inv = s_inv;
+    // multipliers of column k after the interchange (old row k moves to p); none for row k
+    for (int i = tid; i < r; i += nt) col[i] = (i == k) ? 0.f : (i == p ? A[(size_t)k * r + k] : A[(size_t)i * r + k]);
+    __syncthreads();
+    for (int j = tid; j < r; j += nt) {
+      const float vk = A[(size_t)k * r + j], vp = A[(size_t)p * r + j];
+      A[(size_t)p * r + j] = vk;                     // (a no-op when p == k, overwritten just below)
+      A[(size_t)k * r + j] = (j == k ? 1.f : vp) * inv;
+    }
+    __syncthreads();
+    for (int i = warp; i < r; i += nt >> 5) {  // a warp per row, lanes along it
+      if (i == k) continue;
+      const float m = col[i];
+      float* Ai = A + (size_t)i * r;
+      for (int j = lane; j < r; j += 32) Ai[j] = fmaf(-m, A[(size_t)k * r + j], j == k ? 0.f : Ai[j]);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    for (int j = 0; j < r; ++j) idx[j] = j;
+    for (int k = r - 1; k >= 0; --k) {
+      const int q = ipiv[k];
+      const int t = idx[k];
+      idx[k] = idx[q];
+      idx[q] = t;
+    }
+  }
+  __syncthreads();
+  double* Xi = g.fd + fd_Xinv(d);
+  float* P = reinterpret_cast<float*>(g.workc) + d.w_off;
+  const size_t rr = (size_t)r * r;
+  for (int e = tid; e < r * r; e += nt) {
+    const int i = e / r, j = e - i * r;
+    const float v = A[(size_t)i * r + idx[j]];
+    Xi[e] = (double)v;
+    P[e] = v;
+    P[rr + (size_t)j * r + i] = v;
+  }
+}
+
+// FP32 operands of the products Uc = X_RR^-1 [X_RS X_RN] and Lc^T = X_RR^-T [X_SR^T X_NR^T], in the
+// box's near-field test-row area (free once the projections are done): [X_RR^-1 | X_RR^-T | the
+// right-hand blocks of Uc | of Lc^T], r x r, r x r, r x w, r x w (w = k' + n).
+struct CntLcUcPrep {
+  int with_inv;  // also stage X_RR^-1 (not when k_gj_inv32 has staged it)
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const {
+    const int64_t w = (int64_t)d.kp + d.n;
+    return cdv((with_inv ? (int64_t)d.r * d.r : 0) + 2 * (int64_t)d.r * w, 256);
+  }
+};
+__global__ void __launch_bounds__(256) k_lcuc_prep(GroupArgs g, int with_inv) {
+  int64_t loc;
+  int bi = find_item(g.desc, g.nbox, blockIdx.x, CntLcUcPrep{with_inv}, loc);
+  if (bi < 0) return;
+  const BoxDesc d = g.desc[bi];
+  const int64_t r = d.r, w = (int64_t)d.kp + d.n, rr = r * r, rw = r * w;
+  const int64_t e = loc * 256 + threadIdx.x + (with_inv ? 0 : rr);
+  float* P = reinterpret_cast<float*>(g.workc) + d.w_off;
+  if (e < rr) {
+    const float v = (float)g.fd[fd_Xinv(d) + e];
+    P[e] = v;
+    P[rr + (e % r) * r + e / r] = v;
+  } else if (e < rr + rw) {
+    P[2 * rr + (e - rr)] = (float)g.fd[fd_Uc(d) + (e - rr)];
+  } else if (e < rr + 2 * rw) {
+    P[2 * rr + rw + (e - rr - rw)] = (float)g.fd[fd_LcT(d) + (e - rr - rw)];
+  }
+}
+
+// The products' FP32 results (Lc^T then Uc in the extraction area, the Schur update's operands)
+// back into the factor in FP64.
+struct CntLcUcStore {
+  __host__ __device__ int64_t operator()(const BoxDesc& d) const {
+    return cdv(2 * (int64_t)d.r * ((int64_t)d.kp + d.n), 256);
+  }
+};
+__global__ void __launch_bounds__(256) k_lcuc_store(GroupArgs g) {
+  int64_t loc;
+  int bi = find_item(g.desc, g.nbox, blockIdx.x, CntLcUcStore(), loc);
+  if (bi < 0) return;
+  const BoxDesc d = g.desc[bi];
+  const int64_t e = loc * 256 + threadIdx.x;
+  if (e >= 2 * (int64_t)d.r * ((int64_t)d.kp + d.n)) return;
+  g.fd[fd_LcT(d) + e] = (double)reinterpret_cast<const float*>(g.workc)[d.e_off + e];
+}
+
 // Block elimination on the sketches: Y_SN -= Lc Y_R, Om_R += Uc Om_SN, Z_SN -= Uc^T Z_R,
 // Ps_R += Lc^T Ps_SN, with Lc = LcT^T stored r x (kp+n).
 struct CntSchur {
@@ -1501,24 +1666,27 @@ __global__ void __launch_bounds__(NT) k_schur(GroupArgs g) {
 // extraction and the CPQR).
 struct CntSchurPrep {
   int64_t s;
+  int yz_only;  // Lc^T and Uc are already in the workspace (made there by tensor-core products)
   __host__ __device__ int64_t operator()(const BoxDesc& d) const {
-    return cdv(2 * (int64_t)d.r * ((int64_t)d.kp + d.n) + 2 * (int64_t)d.r * s, 256);
+    return cdv((yz_only ? 0 : 2 * (int64_t)d.r * ((int64_t)d.kp + d.n)) + 2 * (int64_t)d.r * s, 256);
   }
 };
-__global__ void __launch_bounds__(256) k_schur_prep(GroupArgs g) {
+__global__ void __launch_bounds__(256) k_schur_prep(GroupArgs g, int yz_only) {
   int64_t loc;
-  int bi = find_item(g.desc, g.nbox, blockIdx.x, CntSchurPrep{g.s}, loc);
+  int bi = find_item(g.desc, g.nbox, blockIdx.x, CntSchurPrep{g.s, yz_only}, loc);
   if (bi < 0) return;
   const BoxDesc d = g.desc[bi];
   const int64_t w = (int64_t)d.kp + d.n, rw = (int64_t)d.r * w, rs = (int64_t)d.r * g.s;
   int64_t e = loc * 256 + threadIdx.x;
   float* wc = reinterpret_cast<float*>(g.workc);
-  if (e < 2 * rw) {
-    const double* src = g.fd + (e < rw ? fd_LcT(d) : fd_Uc(d));
-    wc[d.e_off + e] = (float)src[e < rw ? e : e - rw];
-    return;
+  if (!yz_only) {
+    if (e < 2 * rw) {
+      const double* src = g.fd + (e < rw ? fd_LcT(d) : fd_Uc(d));
+      wc[d.e_off + e] = (float)src[e < rw ? e : e - rw];
+      return;
+    }
+    e -= 2 * rw;
   }
-  e -= 2 * rw;
   if (e >= 2 * rs) return;
   const int side = (int)(e / rs);
   const int64_t i = (e % rs) / g.s, t = (e % rs) % g.s;
@@ -1963,12 +2131,44 @@ void launch_lu_rhs(Launch L, const GroupArgs& g, int64_t items) {
   k_lu_rhs<<<grid1(items), CW, 0, L.st>>>(g);
   count_launch(L);
 }
-void launch_schur(Launch L, const GroupArgs& g, int64_t items, int64_t prep_items) {
+void launch_lu_inv(Launch L, const GroupArgs& g, int64_t items) {
+  if (items <= 0) return;
+  k_lu_inv<<<grid1(items), CW, 0, L.st>>>(g);
+  count_launch(L);
+}
+void launch_lcuc_prep(Launch L, const GroupArgs& g, int64_t items, int with_inv) {
+  if (items <= 0) return;
+  k_lcuc_prep<<<grid1(items), 256, 0, L.st>>>(g, with_inv);
+  count_launch(L);
+}
+bool launch_gj_inv32(Launch L, const GroupArgs& g, int max_r) {
+  if (max_r > GJ_MAX_R) return false;
+  if (max_r <= 0 || g.nbox <= 0) return true;
+  const size_t smem = gj_smem_bytes(max_r);
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_gj_inv32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gj_smem_bytes(GJ_MAX_R));
+  });
+  k_gj_inv32<<<(unsigned)g.nbox, 1024, smem, L.st>>>(g);
+  count_launch(L);
+  return true;
+}
+void launch_lcuc_store(Launch L, const GroupArgs& g, int64_t items) {
+  if (items <= 0) return;
+  k_lcuc_store<<<grid1(items), 256, 0, L.st>>>(g);
+  count_launch(L);
+}
+void launch_schur(Launch L, const GroupArgs& g, int64_t items, int64_t prep_items, int yz_only,
+                  const std::vector<BoxDesc>* tc) {
   if (items <= 0) return;
   if (g.fp32) {
     if (prep_items > 0) {
-      k_schur_prep<<<grid1(prep_items), 256, 0, L.st>>>(g);
+      k_schur_prep<<<grid1(prep_items), 256, 0, L.st>>>(g, yz_only);
       count_launch(L);
+    }
+    if (tc) {
+      launch_schur_tc(L, g, *tc);
+      return;
     }
     k_schur32<<<grid1(items), NT, 0, L.st>>>(g);
   } else {
@@ -2033,6 +2233,11 @@ void launch_dense_apply(Launch L, const float* A, int64_t n, const int32_t* rows
 // Item counts for host planning (same functors as the device decoding).
 int64_t items_sweep(const std::vector<BoxDesc>& h, int cset) { return items_of<void>(h, CntSweep{cset}); }
 int64_t items_diag(const std::vector<BoxDesc>& h, int nrhs) { return items_of<void>(h, CntDiag{nrhs}); }
+int64_t items_lu_inv(const std::vector<BoxDesc>& h) { return items_of<void>(h, CntLuInv()); }
+int64_t items_lcuc_prep(const std::vector<BoxDesc>& h, int with_inv) {
+  return items_of<void>(h, CntLcUcPrep{with_inv});
+}
+int64_t items_lcuc_store(const std::vector<BoxDesc>& h) { return items_of<void>(h, CntLcUcStore()); }
 int64_t items_gram(const std::vector<BoxDesc>& h) { return items_of<void>(h, CntGram()); }
 int64_t items_chol_trsm(const std::vector<BoxDesc>& h, int p) { return items_of<void>(h, CntPanelRows{p}); }
 int64_t items_chol_update(const std::vector<BoxDesc>& h, int p) { return items_of<void>(h, CntUpdate{p}); }
@@ -2045,6 +2250,8 @@ int64_t items_ef(const std::vector<BoxDesc>& h, int64_t s) { return items_of<voi
 int64_t items_extract(const std::vector<BoxDesc>& h) { return items_of<void>(h, CntExtract()); }
 int64_t items_lu_rhs(const std::vector<BoxDesc>& h) { return items_of<void>(h, CntLuRhs()); }
 int64_t items_schur(const std::vector<BoxDesc>& h, int64_t s) { return items_of<void>(h, CntSchur{s}); }
-int64_t items_schur_prep(const std::vector<BoxDesc>& h, int64_t s) { return items_of<void>(h, CntSchurPrep{s}); }
+int64_t items_schur_prep(const std::vector<BoxDesc>& h, int64_t s, int yz_only) {
+  return items_of<void>(h, CntSchurPrep{s, yz_only});
+}
 
 }  // namespace rsrs

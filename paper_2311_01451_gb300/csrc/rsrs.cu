@@ -1012,9 +1012,27 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
       timed(RSRS_K_ID, [&] { launch_id_finish(L, ga, g.max_b); });
       timed(RSRS_K_EF, [&] { launch_ef_update(L, ga, items_ef(g.h, s)); });
       timed(RSRS_K_EXTRACT, [&] { launch_extract(L, ga, items_extract(g.h)); });
-      timed(RSRS_K_LU, [&] { launch_lu(L, ga); });
-      timed(RSRS_K_LU_RHS, [&] { launch_lu_rhs(L, ga, items_lu_rhs(g.h)); });
-      timed(RSRS_K_SCHUR, [&] { launch_schur(L, ga, items_schur(g.h, s), items_schur_prep(g.h, s)); });
+      int max_r = 0;
+      for (const BoxDesc& d : g.h) max_r = std::max(max_r, d.r);
+      // mixed path: X_RR^-1 by FP32 Gauss-Jordan where the boxes fit shared memory (no LU), else
+      // from the FP64 LU by substitution; Uc and Lc^T as tensor-core products with it
+      bool gj = false;
+      if (tcg) timed(RSRS_K_LU, [&] { gj = launch_gj_inv32(L, ga, max_r); });
+      if (!gj) timed(RSRS_K_LU, [&] { launch_lu(L, ga); });
+      if (tcg) {
+        timed(RSRS_K_LU_RHS, [&] {
+          if (!gj) launch_lu_inv(L, ga, items_lu_inv(g.h));
+          launch_lcuc_prep(L, ga, items_lcuc_prep(g.h, gj ? 0 : 1), gj ? 0 : 1);
+          launch_lcuc_tc(L, ga, g.h);
+          launch_lcuc_store(L, ga, items_lcuc_store(g.h));
+        });
+        timed(RSRS_K_SCHUR, [&] {
+          launch_schur(L, ga, items_schur(g.h, s), items_schur_prep(g.h, s, 1), 1);
+        });
+      } else {
+        timed(RSRS_K_LU_RHS, [&] { launch_lu_rhs(L, ga, items_lu_rhs(g.h)); });
+        timed(RSRS_K_SCHUR, [&] { launch_schur(L, ga, items_schur(g.h, s), items_schur_prep(g.h, s)); });
+      }
     }
     CU(cudaGetLastError());
   }

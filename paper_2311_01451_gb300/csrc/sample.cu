@@ -321,6 +321,7 @@ __global__ void k_split_t(const double* __restrict__ in, int64_t n, int64_t s, f
 }
 }  // namespace
 void launch_to_f32(Launch L, const double* in, int64_t count, float* out) {
+  if (count <= 0) return;
   k_to_f32<<<(unsigned)((count + 255) / 256), 256, 0, L.st>>>(in, count, out);
   if (L.counter) ++*L.counter;
 }

@@ -52,10 +52,11 @@ def test_fullsize_mixed_refined_solution(R, setup):
     r = b[idx] - _rows(pr, idx, x)
     # sampled residual rows, computed by the oracle, at the level of the device residual
     assert np.linalg.norm(r) / np.linalg.norm(b[idx]) < 1e-11
-    # apply(solve(b)) = b to rounding
+    # apply(solve(b)) = b to the rounding of the mixed factor's FP32 solve (2^-24 times the sweeps'
+    # growth; measured 3.7e-7)
     Fs = B.clone()
     f.apply(f.solve(Fs))
-    assert float(torch.linalg.norm(Fs - B) / torch.linalg.norm(B)) < 1e-12
+    assert float(torch.linalg.norm(Fs - B) / torch.linalg.norm(B)) < 32 * 2.0 ** -24
     # the unrefined mixed factor is a good preconditioner
     assert rep.history[0] < 1e-2
 

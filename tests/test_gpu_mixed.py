@@ -36,6 +36,9 @@ CASES = {
     "grid2d_4096": lambda: W.config(0)[0],
     "rand2d_3000": lambda: W.small_problem(n=3000, d=2, leaf=24, k=10, nrhs=2, seed_problem=3),
     "rand3d_1500": lambda: W.small_problem(n=1500, d=3, kernel="invr3d", leaf=20, k=8, nrhs=2, seed_problem=4),
+    # leaves of up to 340 points: colour groups whose X_RR blocks exceed 224 rows take the FP64 LU
+    # route to X_RR^-1, the others the FP32 Gauss-Jordan one, in the same factor
+    "rand2d_bigleaf_4000": lambda: W.small_problem(n=4000, d=2, leaf=340, k=10, nrhs=2, seed_problem=6),
 }
 
 
@@ -43,7 +46,7 @@ CASES = {
 def test_mixed_cpqr_variants(R, name):
     pr = CASES[name]()
     tree = R.Tree(pr.points, pr.leaf)
-    s = max(pr.s_cfg, tree.info(pr.k).s_req)
+    s = max(pr.s_cfg, tree.info(pr.k).s_req_mixed)
     b = pr.rhs()
     xd = np.linalg.solve(ops.make_operator(pr).dense(), b)
     fac, its = {}, {}
@@ -72,7 +75,7 @@ def test_mixed_tensor_core_products(R, name):
     dense solution."""
     pr = CASES[name]()
     tree = R.Tree(pr.points, pr.leaf)
-    s = max(pr.s_cfg, tree.info(pr.k).s_req)
+    s = max(pr.s_cfg, tree.info(pr.k).s_req_mixed)
     b = pr.rhs()
     xd = np.linalg.solve(ops.make_operator(pr).dense(), b)
     its = {}
