@@ -38,8 +38,8 @@ FP32_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.070e-3  # SMs x FP32 lanes x 2 x max SM 
 
 # Kernel classes of the mixed path: products on the tensor cores (3xTF32) and FP32 SIMT arithmetic;
 # the rest (LU, its solves, the root's LU and inverse) stay FP64.
-MIXED_TENSOR = {"sample", "gram", "chol", "proj_nt", "proj_solve", "proj_acc"}
-MIXED_FP32 = {"cpqr", "ef_update", "extract", "schur", "id_finish"}
+MIXED_TENSOR = {"sample", "gram", "chol", "proj_nt", "proj_solve", "proj_acc", "lu_rhs", "schur"}
+MIXED_FP32 = {"cpqr", "ef_update", "extract", "id_finish", "lu"}
 # Classes whose time is data movement (gathers, list copies): no FLOP roof.
 MOVE = {"lists", "gather"}
 

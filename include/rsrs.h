@@ -301,19 +301,23 @@ rsrs_status rsrs_refactor(rsrs_factor* f, uint64_t seed, void* stream);
 /* F <- A_approx^-1 F (eq. Ainvfact), or its adjoint; F_dev column-major N x nrhs.  A
  * mixed-precision factor (RSRS_PREC_MIXED) sweeps in FP32 arithmetic on FP32 copies of its blocks
  * (made at the end of its build): its solves serve as the approximate inverse of FP64 refinement
- * and GMRES, whose FP64-accurate residuals set the final accuracy; an FP64 factor sweeps in FP64. */
+ * and GMRES, whose FP64-accurate residuals set the final accuracy; an FP64 factor sweeps in FP64.
+ * Asynchronous on `stream` (like rsrs_apply): the call's scratch (N x nrhs doubles, and as many
+ * floats for a mixed factor) comes from CUDA's stream-ordered allocator and is released in stream
+ * order, so it neither synchronises the device nor waits for the stream; F_dev holds the result
+ * once the stream reaches it.  Concurrent calls on one factor are allowed (the factor is only
+ * read). */
 rsrs_status rsrs_solve(const rsrs_factor* f, double* F_dev, int64_t ldf, int32_t nrhs,
                        int adjoint, void* stream);
 /* rsrs_solve_noalloc: rsrs_solve for callers that must not allocate device memory.  The paper
  * has no counterpart: it is a deployment variant of rsrs_solve, computing the same result with the
  * same kernels.
  *
- * Who needs it: rsrs_solve takes an N x nrhs staging block from cudaMalloc and returns it with
- * cudaFree on every call.  A caller whose device memory is all reserved by another allocator (a
- * caching allocator such as PyTorch's holds freed blocks instead of returning them, so cudaMalloc
- * can fail while memory is nominally free) cannot make that call succeed, and a serving loop
- * cannot accept the implicit device-wide synchronisation of cudaFree while other streams run.
- * This entry point stages the block in library-wide static device buffers instead (one of
+ * Who needs it: rsrs_solve takes an N x nrhs staging block from CUDA's stream-ordered allocator
+ * on every call, whose pool grows from free device memory.  A caller whose device memory is all
+ * reserved by another allocator (a caching allocator such as PyTorch's holds freed blocks instead
+ * of returning them, so an allocation can fail while memory is nominally free) cannot make that
+ * call succeed.  This entry point stages the block in library-wide static device buffers instead (one of
  * RSRS_NOALLOC_MAX_ELEMS doubles, and one of as many floats for a mixed-precision factor's FP32
  * sweeps: 12 MiB held on every device that loads the library) and calls no cudaMalloc, cudaFree or
  * allocating library routine.
@@ -333,7 +337,7 @@ rsrs_status rsrs_solve(const rsrs_factor* f, double* F_dev, int64_t ldf, int32_t
 rsrs_status rsrs_solve_noalloc(const rsrs_factor* f, double* F, int64_t ldf, int32_t nrhs, int adjoint,
                                void* stream);
 
-/* F <- A_approx F (eq. Afact), or its adjoint. */
+/* F <- A_approx F (eq. Afact), or its adjoint; asynchronous on `stream`, scratch as for rsrs_solve. */
 rsrs_status rsrs_apply(const rsrs_factor* f, double* F_dev, int64_t ldf, int32_t nrhs,
                        int adjoint, void* stream);
 /* R = B - A X for the operator the factor was built from, in the refinement's residual
@@ -413,6 +417,13 @@ const char* rsrs_last_error(void);
  * when the wait expired (always, for arrive = 0), RSRS_OK when it completed, RSRS_E_INVAL for
  * arguments out of range.  Synchronises `stream`; allocates and frees one device int. */
 rsrs_status rsrs_wait_selftest(int64_t polls, int arrive, void* stream);
+
+/* Self-test of the FP64 <-> FP32 conversions the mixed path's sketch updates run on the integer
+ * pipes (no counterpart in the paper; IEEE 754 binary64/binary32 layouts).  For the n device
+ * doubles x: f[i] = x[i] rounded to binary32 (to nearest, ties to even), g[i] = f[i] widened to
+ * binary64; both device arrays of n.  They must equal the hardware conversions bit for bit
+ * (NaN payloads aside).  Asynchronous on `stream`; RSRS_E_INVAL for a null array with n > 0. */
+rsrs_status rsrs_convert_selftest(const double* x, int64_t n, float* f, double* g, void* stream);
 
 #ifdef __cplusplus
 }

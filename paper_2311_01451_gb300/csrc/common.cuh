@@ -172,6 +172,34 @@ void launch_solve_tc(Launch L, const GroupArgs& g, int pass, const std::vector<B
 // its arrival only when `arrive` is set; at most `polls` polls (clamped to 1..2^26).  An expired
 // wait records kDevTimeout in *err (device int) and the kernel returns.
 void launch_wait_selftest(Launch L, long long polls, int arrive, int* err);
+// f = f64_bits_to_f32(x), g = f32_to_f64_exact(f), elementwise (device arrays of n)
+void launch_convert_selftest(Launch L, const double* x, int64_t n, float* f, double* g);
+
+// FP64 <-> FP32 conversions on the integer pipes, from the IEEE 754 binary64 / binary32 layouts
+// (sign, biased exponent 11 / 8 bits, fraction 52 / 23 bits; biases 1023 / 127): this part's FP64
+// pipe, which the hardware conversions use, is the sketch updates' scarcest unit.  Values outside
+// the normal FP32 range (zero, subnormal, overflow, NaN) take the hardware conversion.
+// Round to nearest even of the binary64 value with high word hi and low word lo.
+__device__ inline float f64_bits_to_f32(uint32_t hi, uint32_t lo) {
+  const uint32_t e = (hi >> 20) & 0x7ffu;
+  if (e - 897u < 254u) {  // 897 <= e <= 1150: normal in binary32
+    uint32_t r = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const uint32_t rem = lo & 0x1fffffffu;
+    r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;  // a carry may reach the exponent
+    return __uint_as_float((hi & 0x80000000u) | r);
+  }
+  return (float)__hiloint2double((int)hi, (int)lo);
+}
+// The binary64 value of a binary32 (exact).
+__device__ inline double f32_to_f64_exact(float f) {
+  const uint32_t u = __float_as_uint(f), mag = u & 0x7fffffffu;
+  if (mag - 0x00800000u < 0x7f000000u)  // normal: widen the fraction, rebias the exponent by 896
+    return __hiloint2double((int)((u & 0x80000000u) | ((mag >> 3) + 0x38000000u)), (int)(mag << 29));
+  if (mag == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  return (double)f;
+}
+
+
 
 // Root blocks of a build: LU with partial pivoting in place in A (LAPACK interchange record in
 // piv) and the explicit inverse in inv, all problems at once, FP64.
@@ -200,6 +228,7 @@ void launch_lu_inv(Launch L, const GroupArgs& g, int64_t items);
 // ... or, for groups whose boxes have r <= 224, X_RR^-1 by FP32 Gauss-Jordan in shared memory (one
 // CTA per box; no LU needed), which also stages it: false (nothing launched) when max_r is larger.
 bool launch_gj_inv32(Launch L, const GroupArgs& g, int max_r);
+constexpr int kGaussJordanMaxR = 224;
 void launch_lcuc_prep(Launch L, const GroupArgs& g, int64_t items, int with_inv);
 void launch_lcuc_tc(Launch L, const GroupArgs& g, const std::vector<BoxDesc>& h);
 void launch_lcuc_store(Launch L, const GroupArgs& g, int64_t items);
@@ -244,7 +273,7 @@ struct SweepArgs {
 };
 // C rows += alpha * op(A) * B rows; row sets 0 = R, 1 = S, 2 = SN; matrices 0 = T, 1 = LcT, 2 = Uc.
 void launch_sweep_op(Launch L, const SweepArgs& a, int cset, int mat, int trans, int bset, double alpha,
-                     int64_t items);
+                     const std::vector<BoxDesc>& h);
 // f_R <- X_RR^-1 f_R (solve, from the stored inverse) or X_RR f_R (apply), adjoint as requested.
 void launch_sweep_diag(Launch L, const SweepArgs& a, int solve, int64_t items, int max_r);
 void launch_dense_apply(Launch L, const double* A, int64_t n, const int32_t* rows, int64_t row_base, double* F,
@@ -270,7 +299,6 @@ int64_t items_schur_prep(const std::vector<BoxDesc>& h, int64_t s, int yz_only =
 int64_t items_lu_inv(const std::vector<BoxDesc>& h);
 int64_t items_lcuc_prep(const std::vector<BoxDesc>& h, int with_inv);
 int64_t items_lcuc_store(const std::vector<BoxDesc>& h);
-int64_t items_sweep(const std::vector<BoxDesc>& h, int cset);
 int64_t items_diag(const std::vector<BoxDesc>& h, int nrhs);
 
 // Root block (dense): LU in place with partial pivoting, single CTA.

@@ -479,18 +479,24 @@ __device__ __forceinline__ void load_col16(float v[16], const float* src, bool k
     for (int q = 0; q < 16; ++q) v[q] = (k_ok && q < nleft) ? __ldg(src + q) : 0.f;
   }
 }
-// 16 consecutive columns of one K row of an FP64 operand, rounded to FP32 (zero outside).
-__device__ __forceinline__ void load_col16_f64(float v[16], const double* src, bool k_ok, int nleft, bool vec) {
+// 16 consecutive columns of one K row of an FP64 operand (zero outside), kept as the two 32-bit
+// halves of each value (v[2q] low, v[2q+1] high) so that the loads of the next slice stay in flight
+// until it is converted (a conversion here would wait for them).
+__device__ __forceinline__ void load_col16_f64(float v[32], const double* src, bool k_ok, int nleft, bool vec) {
+  auto put = [&](int q, double x) {
+    v[2 * q] = __int_as_float(__double2loint(x));
+    v[2 * q + 1] = __int_as_float(__double2hiint(x));
+  };
   if (k_ok && vec && nleft >= 16) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const double2 x = __ldg(reinterpret_cast<const double2*>(src) + q);
-      v[2 * q] = (float)x.x;
-      v[2 * q + 1] = (float)x.y;
+      put(2 * q, x.x);
+      put(2 * q + 1, x.y);
     }
   } else {
 #pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = (k_ok && q < nleft) ? (float)__ldg(src + q) : 0.f;
+    for (int q = 0; q < 16; ++q) put(q, (k_ok && q < nleft) ? __ldg(src + q) : 0.0);
   }
 }
 // Split into TF32 hi/lo and store row `row`, K positions k0l .. k0l + 15, of the swizzled tiles.
@@ -522,6 +528,17 @@ __device__ __forceinline__ void store_col16(unsigned char* hi, unsigned char* lo
   }
 }
 
+// 16-byte asynchronous copy global -> shared (both 16-byte aligned); the bytes beyond src_bytes
+// (0..16) are written as zeros and not read.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const float* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+// barrier of the eight producer warps only (the MMA warp does not take part)
+__device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(GPROD) : "memory"); }
+
 template <class Job>
 __global__ void __launch_bounds__(GTHREADS, 1) k_tc_grouped(GroupArgs g, Job job) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -551,7 +568,72 @@ __global__ void __launch_bounds__(GTHREADS, 1) k_tc_grouped(GroupArgs g, Job job
   fence_after();
   const uint32_t tmem = s_tmem;
 
-  if (warp < GPROD / 32) {
+  // Asynchronous producers, for tiles whose A and B are both K-contiguous with 16-byte aligned rows:
+  // slice ch's raw FP32 operands are copied in 16-byte pieces (eight lanes per 128-byte K row, four
+  // rows per warp instruction) into the hi tiles of stage ch % 3, two slices ahead of the split;
+  // once a slice has landed (cp.async.wait_group, then a barrier of the producer warps) each
+  // thread splits 16 values of A and of B in place: hi = v with the low 13 mantissa bits cleared,
+  // lo = v - hi.  Other tiles take the register path below.
+  const bool async16 = !kIO && !t.bnm && ((t.lda & 3) == 0) && ((t.ldb & 3) == 0) &&
+                       ((reinterpret_cast<uintptr_t>(t.A) & 15) == 0) && ((reinterpret_cast<uintptr_t>(t.B) & 15) == 0);
+  if (warp < GPROD / 32 && async16) {
+    auto issue = [&](int64_t ch) {
+      const int st = (int)(ch % GNST);
+      unsigned char* Ahi = smem + st * GSTAGE;
+      unsigned char* Bhi = Ahi + 2 * OP_BYTES;
+      const int64_t k0 = ch * GK;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = tid + GPROD * j, row = c >> 3, kc = (c & 7) * 4;
+        const int64_t kl = t.K - k0 - kc;  // valid K values from this piece on
+        const uint32_t kb = kl >= 4 ? 16u : (kl > 0 ? (uint32_t)kl * 4u : 0u);
+        const uint32_t ab = row < t.m ? kb : 0u, bb = row < t.n ? kb : 0u;
+        cp_async16(smem_u32(Ahi + sw128(row, kc)), ab ? t.A + (int64_t)row * t.lda + k0 + kc : t.A, ab);
+        cp_async16(smem_u32(Bhi + sw128(row, kc)), bb ? t.B + (int64_t)row * t.ldb + k0 + kc : t.B, bb);
+      }
+    };
+    const int srow = tid >> 1, skh = (tid & 1) * 16;
+    auto split = [&](unsigned char* hi, unsigned char* lo) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t off = sw128(srow, skh + 4 * q);
+        const float4 v = *reinterpret_cast<const float4*>(hi + off);
+        float4 h, l;
+        h.x = tf32_hi(v.x);
+        h.y = tf32_hi(v.y);
+        h.z = tf32_hi(v.z);
+        h.w = tf32_hi(v.w);
+        l.x = v.x - h.x;
+        l.y = v.y - h.y;
+        l.z = v.z - h.z;
+        l.w = v.w - h.w;
+        *reinterpret_cast<float4*>(hi + off) = h;
+        *reinterpret_cast<float4*>(lo + off) = l;
+      }
+    };
+    constexpr int64_t AHEAD = GNST - 1;
+    for (int64_t p = 0; p < AHEAD; ++p) {
+      if (p < nchunk) issue(p);
+      cp_async_commit();
+    }
+    for (int64_t ch = 0; ch < nchunk; ++ch) {
+      const int st = (int)(ch % GNST);
+      unsigned char* Ahi = smem + st * GSTAGE;
+      cp_async_wait<GNST - 2>();  // this thread's copies of slice ch are done
+      producer_sync();            // ... and every producer's
+      split(Ahi, Ahi + OP_BYTES);
+      split(Ahi + 2 * OP_BYTES, Ahi + 3 * OP_BYTES);
+      fence_proxy_async();
+      bar_arrive(smem_u32(&full[st]));
+      const int64_t nx = ch + AHEAD;  // into the stage the MMA of slice ch - 1 frees
+      if (nx < nchunk) {
+        if (nx >= GNST && !bar_wait(smem_u32(&empty[nx % GNST]), (uint32_t)(((nx / GNST) - 1) & 1))) s_timeout = 1;
+        issue(nx);
+      }
+      cp_async_commit();
+    }
+    cp_async_wait<0>();
+  } else if (warp < GPROD / 32) {
     // A: row tid/2, K half (tid&1)*16.  B (K-contiguous): the same.  B (N-contiguous): k = tid%32,
     // columns (tid/32)*16 .. +15, transposed into rows n of the K-major tile.  The operands of the
     // next slice are loaded into registers while this slice is split and stored.
@@ -563,22 +645,40 @@ __global__ void __launch_bounds__(GTHREADS, 1) k_tc_grouped(GroupArgs g, Job job
     const bool bvec = kIO && t.B64 ? (((t.ldb & 1) == 0) && ((reinterpret_cast<uintptr_t>(t.B64) & 15) == 0))
                                    : (((t.ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(t.B) & 15) == 0));
     const int bk = tid & 31, bn0 = (tid >> 5) * 16;
-    auto load = [&](int64_t ch, float va[16], float vb[16]) {
+    constexpr int NB = kIO ? 32 : 16;  // next-slice B registers (FP64 halves for the sketch updates)
+    auto load = [&](int64_t ch, float va[16], float vb[NB]) {
       const int64_t k0 = ch * GK;
       if (anm) load_col16(va, t.A + (k0 + bk) * t.lda + bn0, k0 + bk < t.K, t.m - bn0, avec);
       else load_row16(va, t.A + (int64_t)r * t.lda + k0 + kh, r < t.m, t.K - k0 - kh, avec);
       if (!t.bnm) {
         load_row16(vb, t.B + (int64_t)r * t.ldb + k0 + kh, r < t.n, t.K - k0 - kh, bvec);
       } else if (kIO && t.B64) {
-        const bool k_ok = k0 + bk < t.K;
-        const double* src = k_ok ? t.B64 + (int64_t)t.bidx[k0 + bk] * t.ldb + bn0 : t.B64;
-        load_col16_f64(vb, src, k_ok, t.n - bn0, bvec);
+        if constexpr (kIO) {
+          const bool k_ok = k0 + bk < t.K;
+          const double* src = k_ok ? t.B64 + (int64_t)t.bidx[k0 + bk] * t.ldb + bn0 : t.B64;
+          load_col16_f64(vb, src, k_ok, t.n - bn0, bvec);
+        }
       } else {
         load_col16(vb, t.B + (k0 + bk) * t.ldb + bn0, k0 + bk < t.K, t.n - bn0, bvec);
       }
     };
-    float va[16], vb[16], na[16], nb[16];
-    if (nchunk > 0) load(0, va, vb);
+    float va[16], vb[16], na[16], nb[NB];
+    // the current slice's B as FP32 from the raw registers
+    auto take_b = [&](const float raw[NB]) {
+      if constexpr (kIO) {
+        if (t.B64) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) vb[q] = f64_bits_to_f32(__float_as_uint(raw[2 * q + 1]), __float_as_uint(raw[2 * q]));
+          return;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) vb[q] = raw[q];
+    };
+    if (nchunk > 0) {
+      load(0, va, nb);
+      take_b(nb);
+    }
     for (int64_t ch = 0; ch < nchunk; ++ch) {
       const int st = (int)(ch % GNST);
       const int64_t u = ch / GNST;
@@ -595,10 +695,8 @@ __global__ void __launch_bounds__(GTHREADS, 1) k_tc_grouped(GroupArgs g, Job job
       fence_proxy_async();
       bar_arrive(smem_u32(&full[st]));
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        va[q] = na[q];
-        vb[q] = nb[q];
-      }
+      for (int q = 0; q < 16; ++q) va[q] = na[q];
+      take_b(nb);
     }
   } else if (lane == 0) {
     const uint32_t idesc = idesc_tf32(GM, GN);
@@ -621,24 +719,57 @@ __global__ void __launch_bounds__(GTHREADS, 1) k_tc_grouped(GroupArgs g, Job job
     // epilogue: warp w reads TMEM lanes 32*(w%4).. (its rows), columns (w/4)*64 .. +64
     const int row = 32 * (warp & 3) + lane;
     const int colbase = (warp >> 2) * 64;
+    if constexpr (kIO) {
+      if (t.D64) {  // FP64 sketch rows, read-modify-write in FP64; the next 16 values load meanwhile
+        const bool rok = row < t.m;
+        double* drow = rok ? t.D64 + (int64_t)t.didx[row] * t.ldd + colbase : t.D64;
+        const bool dvec = ((t.ldd & 1) == 0) && ((reinterpret_cast<uintptr_t>(t.D64) & 15) == 0);
+        const float al = t.alpha;  // +-1: the product's sign, exact in FP32
+        auto ld16 = [&](int cc, double v[16]) {
+          const int nleft = t.n - colbase - cc;
+          if (dvec && nleft >= 16) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const double2 x = reinterpret_cast<const double2*>(drow + cc)[q];
+              v[2 * q] = x.x;
+              v[2 * q + 1] = x.y;
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] = q < nleft ? drow[cc + q] : 0.0;
+          }
+        };
+        double cur[16], nxt[16];
+        if (rok && colbase < t.n) ld16(0, cur);
+        for (int cc = 0; cc < 64; cc += 16) {
+          if (colbase + cc >= t.n) break;  // warp-uniform
+          uint32_t rr[16];
+          tmem_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(colbase + cc), rr);
+          const bool more = cc + 16 < 64 && colbase + cc + 16 < t.n;
+          if (rok && more) ld16(cc + 16, nxt);
+          if (rok) {
+            const int nleft = t.n - colbase - cc;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) cur[q] += f32_to_f64_exact(nchunk > 0 ? al * __uint_as_float(rr[q]) : 0.f);
+            if (dvec && nleft >= 16) {
+#pragma unroll
+              for (int q = 0; q < 8; ++q) reinterpret_cast<double2*>(drow + cc)[q] = make_double2(cur[2 * q], cur[2 * q + 1]);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 16; ++q)
+                if (q < nleft) drow[cc + q] = cur[q];
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 16; ++q) cur[q] = nxt[q];
+        }
+      }
+    }
     for (int cc = 0; cc < 64; cc += 16) {
+      if (kIO && t.D64) break;
       if (colbase + cc >= t.n) break;  // warp-uniform
       uint32_t rr[16];
       tmem_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(colbase + cc), rr);
-      if (kIO && t.D64) {  // FP64 sketch rows, read-modify-write in FP64
-        if (row < t.m) {
-          double* drow = t.D64 + (int64_t)t.didx[row] * t.ldd + colbase + cc;
-          const double al = (double)t.alpha;
-#pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            if (colbase + cc + q < t.n) {
-              const float acc = nchunk > 0 ? __uint_as_float(rr[q]) : 0.f;
-              drow[q] = drow[q] + al * (double)acc;
-            }
-          }
-        }
-        continue;
-      }
       if (row < t.m) {
         float* drow = t.D + (int64_t)row * t.ldd + colbase + cc;
 #pragma unroll
@@ -842,6 +973,21 @@ __global__ void __launch_bounds__(32) k_wait_selftest(long long polls, int arriv
 
 }  // namespace
 
+namespace {
+__global__ void k_convert_selftest(const double* x, int64_t n, float* f, double* g) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  const float r = f64_bits_to_f32((uint32_t)__double2hiint(v), (uint32_t)__double2loint(v));
+  f[i] = r;
+  g[i] = f32_to_f64_exact(r);
+}
+}  // namespace
+void launch_convert_selftest(Launch L, const double* x, int64_t n, float* f, double* g) {
+  if (n <= 0) return;
+  k_convert_selftest<<<(unsigned)((n + 255) / 256), 256, 0, L.st>>>(x, n, f, g);
+  if (L.counter) ++*L.counter;
+}
 void launch_wait_selftest(Launch L, long long polls, int arrive, int* err) {
   polls = std::min(std::max(polls, 1ll), tc::kWaitLimit);
   k_wait_selftest<<<1, 32, 0, L.st>>>(polls, arrive, err);

@@ -1484,7 +1484,7 @@ __global__ void __launch_bounds__(CW) k_lu_inv(GroupArgs g) {
 // area for the products that make Uc and Lc^T.  A zero or non-finite pivot records kDevSingular or
 // kDevNonfinite (and continues with 1).  The result carries FP32 rounding times cond(X_RR), the
 // accuracy of the FP32 products and sweeps that use it.
-constexpr int GJ_MAX_R = 224;
+constexpr int GJ_MAX_R = kGaussJordanMaxR;
 __host__ __device__ inline size_t gj_smem_bytes(int r) { return ((size_t)r * r + (size_t)3 * r) * 4; }
 __global__ void __launch_bounds__(1024, 1) k_gj_inv32(GroupArgs g) {
   const BoxDesc d = g.desc[blockIdx.x];
@@ -1756,11 +1756,14 @@ __device__ inline void sweep_set(const BoxDesc& d, const int32_t* fi, int set, c
   else if (set == 1) { idx = fi + fi_S(d); m = d.kp; }
   else { idx = fi + fi_S(d); m = (int64_t)d.kp + d.n; }
 }
+// Output rows per CTA of the sweep products: op(A) = A^T (A stored K x m) takes a thread per
+// output row, op(A) = A (row-major m x K) a warp per two rows.
+constexpr int SW_T_ROWS = 128, SW_N_ROWS = 16;
 struct CntSweep {
-  int cset;
+  int cset, trans;
   __host__ __device__ int64_t operator()(const BoxDesc& d) const {
     int64_t m = cset == 0 ? d.r : (cset == 1 ? d.kp : (int64_t)d.kp + d.n);
-    return cdv(m, 16);
+    return cdv(m, trans ? SW_T_ROWS : SW_N_ROWS);
   }
 };
 // The factor's blocks and the right-hand sides in the sweep's arithmetic: FP64, or the FP32 copies
@@ -1778,47 +1781,121 @@ __device__ inline double* sweep_F<double>(const SweepArgs& a) { return a.F; }
 template <>
 __device__ inline float* sweep_F<float>(const SweepArgs& a) { return a.F32; }
 
+// C rows += alpha op(A) B rows for 16 right-hand sides at a time, B staged in shared memory in
+// chunks of K.  Transposed form (A stored K x m): thread i of the CTA owns output row i and its 16
+// sums; the threads read consecutive elements of each K row of A.
 template <typename T>
-__global__ void __launch_bounds__(256) k_sweep(SweepArgs a, SweepOp op) {
-  int64_t loc;
-  int bi = find_item(a.desc, a.nbox, blockIdx.x, CntSweep{op.cset}, loc);
-  if (bi < 0) return;
-  const BoxDesc d = a.desc[bi];
-  const int32_t *cidx, *bidx;
-  int64_t m, K;
+__device__ inline void sweep_operands(const SweepArgs& a, const SweepOp& op, const BoxDesc& d, const int32_t*& cidx,
+                                      int64_t& m, const int32_t*& bidx, int64_t& K, const T*& A, int64_t& lda) {
   sweep_set(d, a.fi, op.cset, cidx, m);
   sweep_set(d, a.fi, op.bset, bidx, K);
   const T* fd = sweep_fd<T>(a);
-  T* F = sweep_F<T>(a);
-  const T* A;
-  int64_t lda;
   if (op.mat == 0) { A = fd + fd_T(d); lda = d.r; }
   else if (op.mat == 1) { A = fd + fd_LcT(d); lda = (int64_t)d.kp + d.n; }
   else { A = fd + fd_Uc(d); lda = (int64_t)d.kp + d.n; }
-  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  const int64_t i = loc * 16 + ty;
-  __shared__ T Bs[64][17];
+}
+template <typename T>
+__global__ void __launch_bounds__(SW_T_ROWS) k_sweep_t(SweepArgs a, SweepOp op) {
+  int64_t loc;
+  int bi = find_item(a.desc, a.nbox, blockIdx.x, CntSweep{op.cset, 1}, loc);
+  if (bi < 0) return;
+  const BoxDesc d = a.desc[bi];
+  const int32_t *cidx, *bidx;
+  int64_t m, K, lda;
+  const T* A;
+  sweep_operands<T>(a, op, d, cidx, m, bidx, K, A, lda);
+  T* F = sweep_F<T>(a);
+  constexpr int QC = 64;
+  __shared__ __align__(16) T Bs[QC][16];
+  const int64_t i = loc * SW_T_ROWS + threadIdx.x;
   for (int c0 = 0; c0 < a.nrhs; c0 += 16) {
-    const int c = c0 + tx;
-    T acc = 0;
-    for (int64_t q0 = 0; q0 < K; q0 += 64) {
-      for (int e = threadIdx.x; e < 64 * 16; e += 256) {
-        int qq = e >> 4, cc = e & 15;
-        int64_t q = q0 + qq;
+    T acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = 0;
+    for (int64_t q0 = 0; q0 < K; q0 += QC) {
+      for (int e = threadIdx.x; e < QC * 16; e += SW_T_ROWS) {
+        const int qq = e >> 4, cc = e & 15;
+        const int64_t q = q0 + qq;
         Bs[qq][cc] = (q < K && c0 + cc < a.nrhs) ? F[((int64_t)bidx[q] - a.row_base) * a.nrhs + c0 + cc] : (T)0;
       }
       __syncthreads();
       if (i < m) {
-        const int64_t qn = imin64(64, K - q0);
-        for (int64_t qq = 0; qq < qn; ++qq) {
-          int64_t q = q0 + qq;
-          T av = op.trans ? A[q * lda + i] : A[i * lda + q];
-          acc = mad(av, Bs[qq][tx], acc);
+        const int qn = (int)imin64(QC, K - q0);
+        const T* Ai = A + q0 * lda + i;
+#pragma unroll 4
+        for (int qq = 0; qq < qn; ++qq) {
+          const T av = Ai[(int64_t)qq * lda];
+#pragma unroll
+          for (int c = 0; c < 16; ++c) acc[c] = mad(av, Bs[qq][c], acc[c]);
         }
       }
       __syncthreads();
     }
-    if (i < m && c < a.nrhs) F[((int64_t)cidx[i] - a.row_base) * a.nrhs + c] += (T)op.alpha * acc;
+    if (i < m) {
+      T* out = F + ((int64_t)cidx[i] - a.row_base) * a.nrhs + c0;
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        if (c0 + c < a.nrhs) out[c] += (T)op.alpha * acc[c];
+    }
+  }
+}
+// Row-major form (A m x K): warp w of the CTA owns output rows 2w and 2w + 1, its lanes stride
+// along K (consecutive elements of the A rows) with 16 partial sums per row, then reduce.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_n(SweepArgs a, SweepOp op) {
+  int64_t loc;
+  int bi = find_item(a.desc, a.nbox, blockIdx.x, CntSweep{op.cset, 0}, loc);
+  if (bi < 0) return;
+  const BoxDesc d = a.desc[bi];
+  const int32_t *cidx, *bidx;
+  int64_t m, K, lda;
+  const T* A;
+  sweep_operands<T>(a, op, d, cidx, m, bidx, K, A, lda);
+  T* F = sweep_F<T>(a);
+  constexpr int QC = 128;
+  __shared__ T Bs[QC][17];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t i0 = loc * SW_N_ROWS + 2 * warp;
+  for (int c0 = 0; c0 < a.nrhs; c0 += 16) {
+    T acc[2][16];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int c = 0; c < 16; ++c) acc[u][c] = 0;
+    for (int64_t q0 = 0; q0 < K; q0 += QC) {
+      for (int e = threadIdx.x; e < QC * 16; e += 256) {
+        const int qq = e >> 4, cc = e & 15;
+        const int64_t q = q0 + qq;
+        Bs[qq][cc] = (q < K && c0 + cc < a.nrhs) ? F[((int64_t)bidx[q] - a.row_base) * a.nrhs + c0 + cc] : (T)0;
+      }
+      __syncthreads();
+      const int qn = (int)imin64(QC, K - q0);
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (i0 + u < m) {
+          const T* Ai = A + (i0 + u) * lda + q0;
+          for (int qq = lane; qq < qn; qq += 32) {
+            const T av = Ai[qq];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[u][c] = mad(av, Bs[qq][c], acc[u][c]);
+          }
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc[u][c] += __shfl_xor_sync(0xffffffffu, acc[u][c], o);
+      T v = acc[u][0];
+#pragma unroll
+      for (int c = 1; c < 16; ++c)
+        if (lane == c) v = acc[u][c];
+      if (i0 + u < m && lane < 16 && c0 + lane < a.nrhs)
+        F[((int64_t)cidx[i0 + u] - a.row_base) * a.nrhs + c0 + lane] += (T)op.alpha * v;
+    }
   }
 }
 // f_R <- M f_R with M = X_RR^-1 (solve) or X_RR (apply), or M^T for the adjoint; one CTA per
@@ -2187,10 +2264,17 @@ void launch_dense_lu_solve(Launch L, const double* LU, const int32_t* piv, int64
 }
 
 void launch_sweep_op(Launch L, const SweepArgs& a, int cset, int mat, int trans, int bset, double alpha,
-                     int64_t items) {
+                     const std::vector<BoxDesc>& h) {
+  const int64_t items = items_of<void>(h, CntSweep{cset, trans});
   if (items <= 0) return;
-  if (a.F32) k_sweep<float><<<grid1(items), 256, 0, L.st>>>(a, SweepOp{cset, mat, trans, bset, alpha});
-  else k_sweep<double><<<grid1(items), 256, 0, L.st>>>(a, SweepOp{cset, mat, trans, bset, alpha});
+  const SweepOp op{cset, mat, trans, bset, alpha};
+  if (trans) {
+    if (a.F32) k_sweep_t<float><<<grid1(items), SW_T_ROWS, 0, L.st>>>(a, op);
+    else k_sweep_t<double><<<grid1(items), SW_T_ROWS, 0, L.st>>>(a, op);
+  } else {
+    if (a.F32) k_sweep_n<float><<<grid1(items), 256, 0, L.st>>>(a, op);
+    else k_sweep_n<double><<<grid1(items), 256, 0, L.st>>>(a, op);
+  }
   count_launch(L);
 }
 void launch_sweep_diag(Launch L, const SweepArgs& a, int solve, int64_t items, int max_r) {
@@ -2231,7 +2315,6 @@ void launch_dense_apply(Launch L, const float* A, int64_t n, const int32_t* rows
 }
 
 // Item counts for host planning (same functors as the device decoding).
-int64_t items_sweep(const std::vector<BoxDesc>& h, int cset) { return items_of<void>(h, CntSweep{cset}); }
 int64_t items_diag(const std::vector<BoxDesc>& h, int nrhs) { return items_of<void>(h, CntDiag{nrhs}); }
 int64_t items_lu_inv(const std::vector<BoxDesc>& h) { return items_of<void>(h, CntLuInv()); }
 int64_t items_lcuc_prep(const std::vector<BoxDesc>& h, int with_inv) {

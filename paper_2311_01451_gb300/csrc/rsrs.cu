@@ -134,6 +134,26 @@ struct DevPool {
   }
 };
 
+// Scratch of one call from the stream-ordered allocator: allocated and freed in the order of
+// `st`, so a call neither waits for the device nor serialises other streams.
+struct StreamPool {
+  cudaStream_t st;
+  std::vector<void*> ptrs;
+  explicit StreamPool(cudaStream_t s) : st(s) {}
+  ~StreamPool() {
+    for (void* p : ptrs) cudaFreeAsync(p, st);
+  }
+  template <class T>
+  cudaError_t alloc(T** p, int64_t count) {
+    *p = nullptr;
+    if (count <= 0) count = 1;
+    cudaError_t e = cudaMallocAsync((void**)p, (size_t)count * sizeof(T), st);
+    if (e == cudaSuccess) ptrs.push_back(*p);
+    else (void)cudaGetLastError();
+    return e;
+  }
+};
+
 // ---- layout conversions at the boundary ---------------------------------------
 // rows (tree order, row-major n x c) <-> column-major original order with ld.
 __global__ void k_cm_to_rows(const double* F, int64_t ld, const int32_t* perm, int64_t n, int c, double* W) {
@@ -248,7 +268,8 @@ const char* kClassNames[RSRS_NCLASS] = {"sample", "lists", "gram", "chol", "gath
                                         "schur", "root"};
 
 // Algorithmic FLOPs of one box per kernel class (what the step must compute, not padded tiles).
-void box_flops(const BoxDesc& d, int64_t s, int passes, double* fl) {
+// xinv: X_RR^-1 formed explicitly (Gauss-Jordan, r^3 multiply-adds) instead of an LU.
+void box_flops(const BoxDesc& d, int64_t s, int passes, double* fl, bool xinv) {
   const double b = d.b, l = d.l, kp = d.kp, r = d.r, w = d.kp + d.n, S = (double)s;
   fl[RSRS_K_GRAM] += 2.0 * l * (l + 1) * S;              // two SYRKs l x s
   fl[RSRS_K_CHOL] += 2.0 * l * l * l / 3.0;              // two Cholesky factorizations
@@ -259,7 +280,7 @@ void box_flops(const BoxDesc& d, int64_t s, int passes, double* fl) {
   fl[RSRS_K_ID] += r * kp * kp;
   fl[RSRS_K_EF] += 8.0 * r * kp * S;
   fl[RSRS_K_EXTRACT] += 4.0 * r * kp * (l + r);
-  fl[RSRS_K_LU] += 2.0 * r * r * r / 3.0;
+  fl[RSRS_K_LU] += xinv ? 2.0 * r * r * r : 2.0 * r * r * r / 3.0;
   fl[RSRS_K_LU_RHS] += 2.0 * 2.0 * r * r * w;
   fl[RSRS_K_SCHUR] += 8.0 * r * w * S;
 }
@@ -970,7 +991,10 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
       const LaunchGroup& g = groups[gi];
       ga.desc = desc_dev + g.desc_off;
       ga.nbox = (int)g.h.size();
-      for (const BoxDesc& d : g.h) box_flops(d, s, passes, fl);
+      int max_r = 0;
+      for (const BoxDesc& d : g.h) max_r = std::max(max_r, d.r);
+      const bool tcg_xinv = ga.fp32 && o.mixed_gemm == 0 && max_r <= kGaussJordanMaxR;
+      for (const BoxDesc& d : g.h) box_flops(d, s, passes, fl, tcg_xinv);
       timed(RSRS_K_LISTS, [&] { launch_copy_segments(L, segs_dev + g.seg_off, (int)g.nseg, act, iwork); });
       timed(RSRS_K_GATHER, [&] { launch_gather_box(L, ga, items_gather(g.h)); });
       const bool tcg = ga.fp32 && o.mixed_gemm == 0;
@@ -1012,8 +1036,6 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
       timed(RSRS_K_ID, [&] { launch_id_finish(L, ga, g.max_b); });
       timed(RSRS_K_EF, [&] { launch_ef_update(L, ga, items_ef(g.h, s)); });
       timed(RSRS_K_EXTRACT, [&] { launch_extract(L, ga, items_extract(g.h)); });
-      int max_r = 0;
-      for (const BoxDesc& d : g.h) max_r = std::max(max_r, d.r);
       // mixed path: X_RR^-1 by FP32 Gauss-Jordan where the boxes fit shared memory (no LU), else
       // from the FP64 LU by substitution; Uc and Lc^T as tensor-core products with it
       bool gj = false;
@@ -1027,7 +1049,7 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
           launch_lcuc_store(L, ga, items_lcuc_store(g.h));
         });
         timed(RSRS_K_SCHUR, [&] {
-          launch_schur(L, ga, items_schur(g.h, s), items_schur_prep(g.h, s, 1), 1);
+          launch_schur(L, ga, items_schur(g.h, s), items_schur_prep(g.h, s, 1), 1, &g.h);
         });
       } else {
         timed(RSRS_K_LU_RHS, [&] { launch_lu_rhs(L, ga, items_lu_rhs(g.h)); });
@@ -1538,6 +1560,31 @@ namespace {
 // caller passes w32 (N x nrhs floats): W is converted once, swept with the FP32 copies of the
 // blocks, and converted back (its corrections feed FP64 refinement, whose residual sets the final
 // accuracy); an FP64 factor, or w32 null, sweeps in FP64.
+// f_R <- X_RR^-1 f_R (solve) or X_RR f_R (apply) for every box: the boxes touch disjoint rows, so
+// one launch covers all levels when the factor's descriptors are contiguous (a single-problem
+// build), else one per group.
+void diag_sweep(const rsrs_factor* f, Launch L, SweepArgs a, int nrhs, int solve) {
+  bool contiguous = !f->groups.empty();
+  int64_t total = 0, items = 0;
+  for (size_t i = 0; i < f->groups.size(); ++i) {
+    const GroupView& g = f->groups[i];
+    if (g.desc_off != f->groups[0].desc_off + total) contiguous = false;
+    total += (int64_t)g.h.size();
+    items += items_diag(g.h, nrhs);
+  }
+  if (contiguous && total <= INT32_MAX) {
+    a.desc = f->desc_dev + f->groups[0].desc_off;
+    a.nbox = (int)total;
+    launch_sweep_diag(L, a, solve, items, f->max_r);
+    return;
+  }
+  for (const GroupView& g : f->groups) {
+    a.desc = f->desc_dev + g.desc_off;
+    a.nbox = (int)g.h.size();
+    launch_sweep_diag(L, a, solve, items_diag(g.h, nrhs), g.max_r);
+  }
+}
+
 rsrs_status sweep_solve(const rsrs_factor* f, Launch L, double* W, int nrhs, int adjoint, float* w32 = nullptr) {
   SweepArgs a{};
   a.fd = f->fd;
@@ -1556,17 +1603,13 @@ rsrs_status sweep_solve(const rsrs_factor* f, Launch L, double* W, int nrhs, int
   for (const GroupView& g : f->groups) {
     a.desc = f->desc_dev + g.desc_off;
     a.nbox = (int)g.h.size();
-    launch_sweep_op(L, a, /*C=R*/ 0, /*T*/ 0, /*trans*/ 1, /*B=S*/ 1, -1.0, items_sweep(g.h, 0));
+    launch_sweep_op(L, a, /*C=R*/ 0, /*T*/ 0, /*trans*/ 1, /*B=S*/ 1, -1.0, g.h);
     if (!adjoint)
-      launch_sweep_op(L, a, 2, /*LcT*/ 1, 1, 0, -1.0, items_sweep(g.h, 2));
+      launch_sweep_op(L, a, 2, /*LcT*/ 1, 1, 0, -1.0, g.h);
     else
-      launch_sweep_op(L, a, 2, /*Uc*/ 2, 1, 0, -1.0, items_sweep(g.h, 2));
+      launch_sweep_op(L, a, 2, /*Uc*/ 2, 1, 0, -1.0, g.h);
   }
-  for (const GroupView& g : f->groups) {
-    a.desc = f->desc_dev + g.desc_off;
-    a.nbox = (int)g.h.size();
-    launch_sweep_diag(L, a, 1, items_diag(g.h, nrhs), g.max_r);
-  }
+  diag_sweep(f, L, a, nrhs, 1);
   if (f->root_size > 0) {
     if (fp32) launch_dense_apply(L, f->root_inv32, f->root_size, f->root_idx, f->base, w32, nrhs, adjoint);
     else launch_dense_apply(L, f->root_inv, f->root_size, f->root_idx, f->base, W, nrhs, adjoint);
@@ -1576,10 +1619,10 @@ rsrs_status sweep_solve(const rsrs_factor* f, Launch L, double* W, int nrhs, int
     a.desc = f->desc_dev + g.desc_off;
     a.nbox = (int)g.h.size();
     if (!adjoint)
-      launch_sweep_op(L, a, 0, /*Uc*/ 2, 0, 2, -1.0, items_sweep(g.h, 0));
+      launch_sweep_op(L, a, 0, /*Uc*/ 2, 0, 2, -1.0, g.h);
     else
-      launch_sweep_op(L, a, 0, /*LcT*/ 1, 0, 2, -1.0, items_sweep(g.h, 0));
-    launch_sweep_op(L, a, /*C=S*/ 1, /*T*/ 0, 0, /*B=R*/ 0, -1.0, items_sweep(g.h, 1));
+      launch_sweep_op(L, a, 0, /*LcT*/ 1, 0, 2, -1.0, g.h);
+    launch_sweep_op(L, a, /*C=S*/ 1, /*T*/ 0, 0, /*B=R*/ 0, -1.0, g.h);
   }
   if (fp32) launch_to_f64(L, w32, f->n * nrhs, W);
   CU(cudaGetLastError());
@@ -1597,27 +1640,23 @@ rsrs_status sweep_apply(const rsrs_factor* f, Launch L, double* W, int nrhs, int
   for (const GroupView& g : f->groups) {  // W_1 first: F^-1 then U^-1 (or V^*: E^-* then L^-*)
     a.desc = f->desc_dev + g.desc_off;
     a.nbox = (int)g.h.size();
-    launch_sweep_op(L, a, 1, 0, 0, 0, 1.0, items_sweep(g.h, 1));
+    launch_sweep_op(L, a, 1, 0, 0, 0, 1.0, g.h);
     if (!adjoint)
-      launch_sweep_op(L, a, 0, 2, 0, 2, 1.0, items_sweep(g.h, 0));
+      launch_sweep_op(L, a, 0, 2, 0, 2, 1.0, g.h);
     else
-      launch_sweep_op(L, a, 0, 1, 0, 2, 1.0, items_sweep(g.h, 0));
+      launch_sweep_op(L, a, 0, 1, 0, 2, 1.0, g.h);
   }
-  for (const GroupView& g : f->groups) {
-    a.desc = f->desc_dev + g.desc_off;
-    a.nbox = (int)g.h.size();
-    launch_sweep_diag(L, a, 0, items_diag(g.h, nrhs), g.max_r);
-  }
+  diag_sweep(f, L, a, nrhs, 0);
   if (f->root_size > 0) launch_dense_apply(L, f->root_A, f->root_size, f->root_idx, f->base, W, nrhs, adjoint);
   for (auto it = f->groups.rbegin(); it != f->groups.rend(); ++it) {  // V_M first: L^-1 then E^-1
     const GroupView& g = *it;
     a.desc = f->desc_dev + g.desc_off;
     a.nbox = (int)g.h.size();
     if (!adjoint)
-      launch_sweep_op(L, a, 2, 1, 1, 0, 1.0, items_sweep(g.h, 2));
+      launch_sweep_op(L, a, 2, 1, 1, 0, 1.0, g.h);
     else
-      launch_sweep_op(L, a, 2, 2, 1, 0, 1.0, items_sweep(g.h, 2));
-    launch_sweep_op(L, a, 0, 0, 1, 1, 1.0, items_sweep(g.h, 0));
+      launch_sweep_op(L, a, 2, 2, 1, 0, 1.0, g.h);
+    launch_sweep_op(L, a, 0, 0, 1, 1, 1.0, g.h);
   }
   CU(cudaGetLastError());
   return RSRS_OK;
@@ -1638,7 +1677,7 @@ rsrs_status rsrs_solve(const rsrs_factor* f, double* F, int64_t ldf, int32_t nrh
   if (r != RSRS_OK) return r;
   cudaStream_t st = (cudaStream_t)stream;
   Launch L{st, nullptr};
-  DevPool pool;
+  StreamPool pool(st);
   double* W;
   float* w32 = nullptr;
   CU(pool.alloc(&W, f->n * nrhs));
@@ -1648,7 +1687,6 @@ rsrs_status rsrs_solve(const rsrs_factor* f, double* F, int64_t ldf, int32_t nrh
   if (r != RSRS_OK) return r;
   k_rows_to_cm<<<nblk(f->n * nrhs), 256, 0, st>>>(W, f->perm_dev, f->n, nrhs, F, ldf);
   CU(cudaGetLastError());
-  CU(cudaStreamSynchronize(st));
   return RSRS_OK;
 }
 
@@ -1657,7 +1695,7 @@ rsrs_status rsrs_apply(const rsrs_factor* f, double* F, int64_t ldf, int32_t nrh
   if (r != RSRS_OK) return r;
   cudaStream_t st = (cudaStream_t)stream;
   Launch L{st, nullptr};
-  DevPool pool;
+  StreamPool pool(st);
   double* W;
   CU(pool.alloc(&W, f->n * nrhs));
   k_cm_to_rows<<<nblk(f->n * nrhs), 256, 0, st>>>(F, ldf, f->perm_dev, f->n, nrhs, W);
@@ -1665,7 +1703,6 @@ rsrs_status rsrs_apply(const rsrs_factor* f, double* F, int64_t ldf, int32_t nrh
   if (r != RSRS_OK) return r;
   k_rows_to_cm<<<nblk(f->n * nrhs), 256, 0, st>>>(W, f->perm_dev, f->n, nrhs, F, ldf);
   CU(cudaGetLastError());
-  CU(cudaStreamSynchronize(st));
   return RSRS_OK;
 }
 
@@ -2181,6 +2218,13 @@ extern "C" rsrs_status rsrs_solve_noalloc(const rsrs_factor* f, double* F, int64
   r = sweep_solve(f, L, W, nrhs, adjoint, f->fd32 ? W32 : nullptr);
   if (r != RSRS_OK) return r;
   k_rows_to_cm<<<nblk(f->n * nrhs), 256, 0, st>>>(W, f->perm_dev, f->n, nrhs, F, ldf);
+  CU(cudaGetLastError());
+  return RSRS_OK;
+}
+
+extern "C" rsrs_status rsrs_convert_selftest(const double* x, int64_t n, float* f, double* g, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !f || !g))) return fail(RSRS_E_INVAL, "convert_selftest: bad arguments");
+  launch_convert_selftest(Launch{(cudaStream_t)stream, nullptr}, x, n, f, g);
   CU(cudaGetLastError());
   return RSRS_OK;
 }

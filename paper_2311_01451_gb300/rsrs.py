@@ -23,7 +23,7 @@ STATUS = {0: "RSRS_OK", 1: "RSRS_E_INVAL", 2: "RSRS_E_UNDERSAMPLED", 3: "RSRS_E_
           8: "RSRS_E_TIMEOUT", 9: "RSRS_E_NOT_CONVERGED"}
 
 EXPORTS = ["rsrs_tree_build", "rsrs_tree_info", "rsrs_tree_perm", "rsrs_tree_schedule", "rsrs_tree_free",
-           "rsrs_build", "rsrs_build_batched", "rsrs_refactor", "rsrs_solve", "rsrs_solve_noalloc", "rsrs_wait_selftest", "rsrs_apply", "rsrs_refine", "rsrs_residual", "rsrs_matvec", "rsrs_factor_stats",
+           "rsrs_build", "rsrs_build_batched", "rsrs_refactor", "rsrs_solve", "rsrs_solve_noalloc", "rsrs_wait_selftest", "rsrs_convert_selftest", "rsrs_apply", "rsrs_refine", "rsrs_residual", "rsrs_matvec", "rsrs_factor_stats",
            "rsrs_factor_box", "rsrs_factor_root", "rsrs_factor_sketches", "rsrs_factor_free",
            "rsrs_status_string", "rsrs_last_error", "rsrs_kernel_class_name", "rsrs_stencil7_create", "rsrs_stencil7_matvec", "rsrs_stencil7_free", "rsrs_autotune", "rsrs_gmres"]
 
@@ -139,6 +139,7 @@ def lib():
             "rsrs_autotune": [C.c_int, C.POINTER(vp), C.POINTER(Operator), C.c_int, C.c_int, C.POINTER(Options),
                               C.c_int, C.c_char_p, vp, C.POINTER(Tune), C.POINTER(TuneReport)],
             "rsrs_wait_selftest": [i64, C.c_int, vp],
+            "rsrs_convert_selftest": [vp, i64, vp, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -165,6 +166,20 @@ def wait_selftest(polls: int, arrive: bool, stream=None):
     ``polls`` polls), for an arrival made only when ``arrive`` is true.  Raises RSRSError
     (RSRS_E_TIMEOUT) when the wait expired; returns None when it completed."""
     _check(lib().rsrs_wait_selftest(int(polls), int(bool(arrive)), _stream_ptr(stream)))
+
+
+def convert_selftest(x, stream=None):
+    """rsrs_convert_selftest on a contiguous FP64 CUDA tensor: returns (f, g), the library's
+    integer-pipe rounding of x to FP32 and its exact widening back to FP64."""
+    import torch
+
+    if not (x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+        raise ValueError("x must be a contiguous float64 CUDA tensor")
+    f = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    g = torch.empty(x.shape, dtype=torch.float64, device=x.device)
+    _check(lib().rsrs_convert_selftest(C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(f.data_ptr()),
+                                       C.c_void_p(g.data_ptr()), _stream_ptr(stream)))
+    return f, g
 
 
 class RSRSError(RuntimeError):

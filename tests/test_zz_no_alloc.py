@@ -1,7 +1,7 @@
 """rsrs_solve_noalloc against rsrs_solve.
 
 The no-allocation solve stages the right-hand sides in the library's static device buffer instead
-of a per-call cudaMalloc; it runs the same kernels in the same order, so its results must equal
+of a per-call allocation (rsrs_solve's stream-ordered scratch); it runs the same kernels in the same order, so its results must equal
 rsrs_solve's bit for bit, also for two calls in a row that reuse the buffer, and it must keep
 working when no device memory can be allocated at all.  This file is named to be collected last,
 so that it also runs after everything else has used the device.
