@@ -182,6 +182,10 @@ typedef struct {
   double class_ms[RSRS_NCLASS];       /* CUDA-event time per class (opts.profile only)   */
   double class_gflop[RSRS_NCLASS];    /* algorithmic GFLOP per class (always filled)     */
   int64_t class_launches[RSRS_NCLASS];
+  int64_t solve_bytes;    /* algorithmic bytes one solve reads from the factor, in the  */
+                          /* solve's arithmetic (FP32 copies for a mixed factor): T    */
+                          /* twice (both sweeps), Lc and Uc once each, X_RR^-1 and the */
+                          /* root inverse once; right-hand-side traffic not counted    */
 } rsrs_stats;
 
 /* Name of a kernel class ("gram", "schur", ...). */

@@ -177,26 +177,52 @@ void launch_convert_selftest(Launch L, const double* x, int64_t n, float* f, dou
 
 // FP64 <-> FP32 conversions on the integer pipes, from the IEEE 754 binary64 / binary32 layouts
 // (sign, biased exponent 11 / 8 bits, fraction 52 / 23 bits; biases 1023 / 127): this part's FP64
-// pipe, which the hardware conversions use, is the sketch updates' scarcest unit.  Values outside
-// the normal FP32 range (zero, subnormal, overflow, NaN) take the hardware conversion.
+// pipe, which the hardware conversions use, is the mixed path's scarcest unit.  No FP64
+// instruction appears in either routine (a rarely taken hardware-conversion branch would still be
+// issued under predication).  They equal the hardware conversions bit for bit (NaN payloads aside).
 // Round to nearest even of the binary64 value with high word hi and low word lo.
 __device__ inline float f64_bits_to_f32(uint32_t hi, uint32_t lo) {
-  const uint32_t e = (hi >> 20) & 0x7ffu;
+  const uint32_t sign = hi & 0x80000000u, e = (hi >> 20) & 0x7ffu;
   if (e - 897u < 254u) {  // 897 <= e <= 1150: normal in binary32
     uint32_t r = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
     const uint32_t rem = lo & 0x1fffffffu;
     r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;  // a carry may reach the exponent
-    return __uint_as_float((hi & 0x80000000u) | r);
+    return __uint_as_float(sign | r);
   }
-  return (float)__hiloint2double((int)hi, (int)lo);
+  if (e >= 1151u) {  // beyond the binary32 range: infinity, or a quiet NaN
+    const bool nan = e == 0x7ffu && ((hi & 0xfffffu) | lo) != 0u;
+    return __uint_as_float(sign | (nan ? 0x7fc00000u : 0x7f800000u));
+  }
+  if (e < 873u) return __uint_as_float(sign);  // below 2^-150: rounds to zero
+  // 873 <= e <= 896: a binary32 subnormal (or the smallest normal after rounding), in units of
+  // 2^-149: the 53-bit significand shifted right by 926 - e (30..53), rounded to nearest even
+  const uint64_t m = ((uint64_t)((hi & 0xfffffu) | 0x100000u) << 32) | lo;
+  const uint32_t sh = 926u - e;
+  uint64_t q = m >> sh;
+  const uint64_t rem = m & ((1ull << sh) - 1ull), half = 1ull << (sh - 1u);
+  q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
+  return __uint_as_float(sign | (uint32_t)q);
 }
 // The binary64 value of a binary32 (exact).
 __device__ inline double f32_to_f64_exact(float f) {
-  const uint32_t u = __float_as_uint(f), mag = u & 0x7fffffffu;
-  if (mag - 0x00800000u < 0x7f000000u)  // normal: widen the fraction, rebias the exponent by 896
-    return __hiloint2double((int)((u & 0x80000000u) | ((mag >> 3) + 0x38000000u)), (int)(mag << 29));
-  if (mag == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
-  return (double)f;
+  const uint32_t u = __float_as_uint(f), sign = u & 0x80000000u, mag = u & 0x7fffffffu;
+  uint32_t hi, lo;
+  if (mag - 0x00800000u < 0x7f000000u) {  // normal: widen the fraction, rebias the exponent by 896
+    hi = sign | ((mag >> 3) + 0x38000000u);
+    lo = mag << 29;
+  } else if (mag >= 0x7f800000u) {  // infinity or NaN (payload kept)
+    hi = sign | 0x7ff00000u | ((mag & 0x7fffffu) >> 3);
+    lo = mag << 29;
+  } else if (mag == 0u) {
+    hi = sign;
+    lo = 0u;
+  } else {  // subnormal: normalise the leading one to bit 23, exponent 1 - sh in binary32 terms
+    const uint32_t sh = (uint32_t)__clz(mag) - 8u;
+    const uint32_t m = mag << sh;
+    hi = sign | ((897u - sh) << 20) | ((m & 0x7fffffu) >> 3);
+    lo = m << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
 }
 
 

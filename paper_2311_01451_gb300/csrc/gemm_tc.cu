@@ -869,25 +869,40 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_chol_diag_tc(GroupArgs g, int p
 #pragma unroll
         for (int cc = 0; cc < DW; ++cc) {
           const int r = c0 + lane + 32 * q;
-          if (r < DB) S[r * DLD + c0 + cc] = P[q][cc];
+          if (r < DB) {
+            S[r * DLD + c0 + cc] = P[q][cc];
+            Tb[cc * DB + r] = P[q][cc];  // the panel transposed, for the update below
+          }
         }
       if (lane == 0 && bad) s_bad = 1;
     }
     __syncthreads();
-    // rank-16 update of the trailing lower triangle
+    // rank-16 update of the trailing lower triangle, a 4 x 4 block (bi, bj <= bi) per thread
     const int c1 = c0 + DW;
     if (c1 < DB) {
-      const int ty = warp, tx = lane;
-      for (int i = c1 + ty; i < DB; i += DTHREADS / 32) {
-        float pi[DW];
+      const int nb4 = (DB - c1) / 4, nblk = nb4 * (nb4 + 1) / 2;  // at most 406 < DTHREADS
+      if (tid < nblk) {
+        int bi = (int)((sqrtf(8.f * (float)tid + 1.f) - 1.f) * 0.5f);
+        while (bi * (bi + 1) / 2 > tid) --bi;
+        while ((bi + 1) * (bi + 2) / 2 <= tid) ++bi;
+        const int bj = tid - bi * (bi + 1) / 2;
+        const int i0 = c1 + 4 * bi, j0 = c1 + 4 * bj;
+        float acc[4][4] = {};
 #pragma unroll
-        for (int k = 0; k < DW; ++k) pi[k] = S[i * DLD + c0 + k];
-        for (int j = c1 + tx; j <= i; j += 32) {
-          float acc = 0.f;
+        for (int k = 0; k < DW; ++k) {
+          const float4 a = *reinterpret_cast<const float4*>(Tb + k * DB + i0);
+          const float4 b = *reinterpret_cast<const float4*>(Tb + k * DB + j0);
+          const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-          for (int k = 0; k < DW; ++k) acc = fmaf(pi[k], S[j * DLD + c0 + k], acc);
-          S[i * DLD + j] -= acc;
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            if (j0 + v <= i0 + u) S[(i0 + u) * DLD + j0 + v] -= acc[u][v];
       }
     }
     __syncthreads();

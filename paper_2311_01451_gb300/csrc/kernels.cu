@@ -156,6 +156,18 @@ struct MatAT {
 };
 using MatA = MatAT<double>;
 
+// A value in the compute type; FP64 -> FP32 by the integer-pipe rounding (the FP64 pipe, which
+// the hardware conversion uses, is this part's scarcest unit).
+template <typename CT, typename S>
+__device__ inline CT to_ct(S v) {
+  if constexpr (sizeof(CT) == 4 && sizeof(S) == 8)
+    return f64_bits_to_f32((uint32_t)__double2hiint(v), (uint32_t)__double2loint(v));
+  else
+    return (CT)v;
+}
+template <typename CT>
+__device__ inline CT from_f64(double v) { return to_ct<CT>(v); }
+
 // C[crow(i)][coff + t] += alpha * sum_q A(i,q) B[brow(q)][t] for the 64 x 64 tile (i0, t0);
 // t ranges over ncols, q over K.
 template <typename CT, typename TA, typename TB, typename TC>
@@ -458,7 +470,7 @@ __global__ void k_gather_box(GroupArgs g) {
       CT* m = wc + d.mc_off + i * 2 * g.s;
       CT acc = 0;
       for (int64_t c = threadIdx.x; c < g.s; c += blockDim.x) {
-        const CT a = (CT)y[c], bz = (CT)z[c];
+        const CT a = from_f64<CT>(y[c]), bz = from_f64<CT>(z[c]);
         m[c] = a;
         m[g.s + c] = bz;
         acc = mad(a, a, mad(bz, bz, acc));
@@ -483,8 +495,8 @@ __global__ void k_gather_box(GroupArgs g) {
       CT* W = wc + d.w_off + i * g.s;
       CT* V = wc + d.w_off + ((int64_t)d.l + i) * g.s;
       for (int64_t c = threadIdx.x; c < g.s; c += blockDim.x) {
-        W[c] = (CT)w[c];
-        V[c] = (CT)v[c];
+        W[c] = from_f64<CT>(w[c]);
+        V[c] = from_f64<CT>(v[c]);
       }
     }
   }
@@ -1692,7 +1704,7 @@ __global__ void __launch_bounds__(256) k_schur_prep(GroupArgs g, int yz_only) {
   const int64_t i = (e % rs) / g.s, t = (e % rs) % g.s;
   const int32_t* Rl = g.fi + fi_R(d);
   const double* src = side == 0 ? g.Y : g.Z;
-  wc[d.mc_off + e] = (float)src[(int64_t)Rl[i] * g.s + t];
+  wc[d.mc_off + e] = from_f64<float>(src[(int64_t)Rl[i] * g.s + t]);
 }
 __global__ void __launch_bounds__(NT) k_schur32(GroupArgs g) {
   int64_t loc;

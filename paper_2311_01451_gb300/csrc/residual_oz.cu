@@ -127,6 +127,21 @@ __device__ __forceinline__ void digits(float v, float a[OZ_S]) {
   }
 }
 
+// Digits of the low part l of a normalised float-float value h + l (|l| <= 2^-24 |h|, |h| <= 1/2
+// after the row scale): |l| <= 2^-25, so 128^3 |l| <= 2^-4 and its first three digits are zero;
+// the remainder after them is 2^21 l exactly.
+__device__ __forceinline__ void digits_lo(float v, float a[OZ_S]) {
+  constexpr float kRound = 12582912.f;  // 1.5 * 2^23
+  a[0] = a[1] = a[2] = 0.f;
+  v *= 0x1p21f;
+#pragma unroll
+  for (int t = 3; t < OZ_S; ++t) {
+    const float y = v * 128.f;
+    a[t] = __fsub_rn(__fadd_rn(y, kRound), kRound);
+    v = y - a[t];
+  }
+}
+
 // Points as three floats each (exact), padded with zeros to npad points.
 __global__ void k_oz_f3(const double* __restrict__ pts, int64_t n, int d, int64_t npad, float3* __restrict__ out) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -261,9 +276,9 @@ __global__ void __launch_bounds__(SL_T) k_oz_slices(const float3* __restrict__ p
           if (gi >= n || gj >= n || gj == gi) kv = {0.f, 0.f};
           float dh[OZ_S], dl[OZ_S];
           digits(kv.h * inv, dh);
-          digits(kv.l * inv, dl);
+          digits_lo(kv.l * inv, dl);
 #pragma unroll
-          for (int t = 0; t < OZ_S; ++t) dg[q2][t] = dh[t] + dl[t];
+          for (int t = 0; t < OZ_S; ++t) dg[q2][t] = t < 3 ? dh[t] : dh[t] + dl[t];
         }
 #pragma unroll
         for (int t = 0; t < OZ_S; ++t) {

@@ -1197,16 +1197,19 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
     f->stats = bst;
     f->stats.n = f->n;
     f->stats.root_size = f->root_size;
-    int64_t nb = 0, fdb = 0, fib = 0;
+    int64_t nb = 0, fdb = 0, fib = 0, sweep = 0;
     for (const GroupView& v : f->groups)
       for (const BoxDesc& d : v.h) {
         ++nb;
         fdb += fd_size(d.kp, d.r, d.n);
         fib += fi_size(d.kp, d.r, d.n);
+        const int64_t r = d.r, w = (int64_t)d.kp + d.n;
+        sweep += 2 * (int64_t)d.kp * r + 2 * r * w + r * r;
       }
     f->stats.n_boxes = nb;
     f->stats.factor_bytes = fdb * 8 + fib * 4 + f->root_size * f->root_size * 24 + f->root_size * 8;
     if (f->fd32) f->stats.factor_bytes += fdb * 4 + f->root_size * f->root_size * 4;
+    f->stats.solve_bytes = (sweep + f->root_size * f->root_size) * (f->fd32 ? 4 : 8);
     out[p] = F[p].release();
   }
   return RSRS_OK;

@@ -89,7 +89,8 @@ class Stats(C.Structure):
                 ("root_size", C.c_int64), ("factor_bytes", C.c_int64), ("work_bytes", C.c_int64),
                 ("t_sample_ms", C.c_double), ("t_compress_ms", C.c_double), ("t_root_ms", C.c_double),
                 ("kernel_launches", C.c_int64), ("class_ms", C.c_double * NCLASS),
-                ("class_gflop", C.c_double * NCLASS), ("class_launches", C.c_int64 * NCLASS)]
+                ("class_gflop", C.c_double * NCLASS), ("class_launches", C.c_int64 * NCLASS),
+                ("solve_bytes", C.c_int64)]
 
 
 class RefineReport(C.Structure):

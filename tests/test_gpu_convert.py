@@ -48,6 +48,11 @@ def _inputs():
     # mantissa all ones below each power of two: rounding carries into the exponent
     e = rng.integers(-125, 127, size=5_000).astype(np.float64)
     cases.append(2.0**e * (2.0 - 2.0**-30))
+    # the binary32 subnormal range (results rounded to multiples of 2^-149, ties included)
+    sub = rng.random(20_000) * tiny * np.where(rng.random(20_000) < 0.5, -1.0, 1.0)
+    cases.append(sub)
+    cases.append(np.array([2.0**-150, 3 * 2.0**-151, 2.0**-149, 1.5 * 2.0**-149, 2.5 * 2.0**-149,
+                           tiny * (1 - 2.0**-25), tiny * (1 - 2.0**-24), tiny * (1 - 2.0**-23)]))
     return np.concatenate(cases)
 
 
