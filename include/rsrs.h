@@ -306,11 +306,14 @@ rsrs_status rsrs_refactor(rsrs_factor* f, uint64_t seed, void* stream);
  * mixed-precision factor (RSRS_PREC_MIXED) sweeps in FP32 arithmetic on FP32 copies of its blocks
  * (made at the end of its build): its solves serve as the approximate inverse of FP64 refinement
  * and GMRES, whose FP64-accurate residuals set the final accuracy; an FP64 factor sweeps in FP64.
- * Asynchronous on `stream` (like rsrs_apply): the call's scratch (N x nrhs doubles, and as many
- * floats for a mixed factor) comes from CUDA's stream-ordered allocator and is released in stream
- * order, so it neither synchronises the device nor waits for the stream; F_dev holds the result
- * once the stream reaches it.  Concurrent calls on one factor are allowed (the factor is only
- * read). */
+ * Each sweep direction runs as one cooperative launch of persistent CTAs over the factor's
+ * (level, colour) groups with a bounded grid-wide barrier between dependent steps (the root's
+ * dense step in between), or, where a cooperative launch is refused, as one launch per group and
+ * product; both compute the same values.  Asynchronous on `stream` (like rsrs_apply): the call's
+ * scratch (N x nrhs doubles, as many floats for a mixed factor, four barrier words) comes from
+ * CUDA's stream-ordered allocator and is released in stream order, so it neither synchronises the
+ * device nor waits for the stream; F_dev holds the result once the stream reaches it.  Concurrent
+ * calls on one factor are allowed (the factor is only read). */
 rsrs_status rsrs_solve(const rsrs_factor* f, double* F_dev, int64_t ldf, int32_t nrhs,
                        int adjoint, void* stream);
 /* rsrs_solve_noalloc: rsrs_solve for callers that must not allocate device memory.  The paper
@@ -321,10 +324,10 @@ rsrs_status rsrs_solve(const rsrs_factor* f, double* F_dev, int64_t ldf, int32_t
  * on every call, whose pool grows from free device memory.  A caller whose device memory is all
  * reserved by another allocator (a caching allocator such as PyTorch's holds freed blocks instead
  * of returning them, so an allocation can fail while memory is nominally free) cannot make that
- * call succeed.  This entry point stages the block in library-wide static device buffers instead (one of
- * RSRS_NOALLOC_MAX_ELEMS doubles, and one of as many floats for a mixed-precision factor's FP32
- * sweeps: 12 MiB held on every device that loads the library) and calls no cudaMalloc, cudaFree or
- * allocating library routine.
+ * call succeed.  This entry point stages the block in library-wide static device buffers instead
+ * (one of RSRS_NOALLOC_MAX_ELEMS doubles, one of as many floats for a mixed-precision factor's FP32
+ * sweeps, and four words for the fused sweeps' grid barrier: 12 MiB held on every device that
+ * loads the library) and calls no cudaMalloc, cudaFree or allocating library routine.
  *
  * Limit: N * nrhs <= RSRS_NOALLOC_MAX_ELEMS (2^20, e.g. N = 65,536 with 16 right-hand sides);
  * larger blocks return RSRS_E_INVAL before any launch.  Nothing in the buffers needs to start at
@@ -421,6 +424,13 @@ const char* rsrs_last_error(void);
  * when the wait expired (always, for arrive = 0), RSRS_OK when it completed, RSRS_E_INVAL for
  * arguments out of range.  Synchronises `stream`; allocates and frees one device int. */
 rsrs_status rsrs_wait_selftest(int64_t polls, int arrive, void* stream);
+
+/* The same for the grid-wide barrier of the fused solve sweeps (no counterpart in the paper): a
+ * cooperative launch of two CTAs meets at the barrier, CTA 1 only when arrive = 1; CTA 0 waits
+ * with at most `polls` polls (1..2^26).  RSRS_E_TIMEOUT when the wait expired (always, for
+ * arrive = 0), RSRS_OK when both arrived, RSRS_E_CUDA when the cooperative launch was refused,
+ * RSRS_E_INVAL for arguments out of range.  Synchronises `stream`; allocates four device words. */
+rsrs_status rsrs_grid_wait_selftest(int64_t polls, int arrive, void* stream);
 
 /* Self-test of the FP64 <-> FP32 conversions the mixed path's sketch updates run on the integer
  * pipes (no counterpart in the paper; IEEE 754 binary64/binary32 layouts).  For the n device

@@ -297,6 +297,29 @@ struct SweepArgs {
   const float* fd32 = nullptr;
   float* F32 = nullptr;
 };
+// One phase of the fused solve sweeps (k_sweep_fused): a group's sweep product or the diagonal
+// step over a range of boxes.  kind 0: C rows += alpha A^T B rows (A stored K x m, a thread per
+// output row, 256 rows per item); 1: C rows += alpha A B rows (A row-major, 16 rows per item);
+// 2: f_R <- X_RR^-1 f_R (solve = 1) or X_RR f_R, DC columns per item.  sync: a grid-wide barrier
+// follows the phase (the next phase reads rows this one writes).
+struct SweepPhase {
+  const BoxDesc* desc;
+  int nbox, kind, cset, mat, bset, solve, sync;
+  double alpha;
+  int64_t items;
+};
+constexpr int kSweepFusedThreads = 256, kSweepFusedRowsT = 256, kSweepFusedRowsN = 16;
+// Items of a sweep phase over boxes h (kind as above; nrhs for the diagonal step).
+int64_t sweep_phase_items(const std::vector<BoxDesc>& h, int kind, int cset, int nrhs);
+// The phases [ph, ph + nph) in one cooperative launch of persistent CTAs (all resident), with a
+// bounded grid-wide barrier after each phase marked sync: bar holds the barrier's arrival counter
+// and generation (zero on entry) and a status word (bar[2], kDevTimeout when a barrier wait gave
+// up).  Returns false, launching nothing, when a cooperative launch is not possible.
+bool launch_sweep_fused(Launch L, const SweepArgs& a, const SweepPhase* ph, int nph, int max_r, unsigned* bar);
+// Two CTAs meet at the fused sweeps' grid barrier (with at most `polls` polls per wait), CTA 1 only
+// when arrive is set; false when the cooperative launch is refused.
+bool launch_grid_wait_selftest(Launch L, unsigned* bar, long long polls, int arrive);
+
 // C rows += alpha * op(A) * B rows; row sets 0 = R, 1 = S, 2 = SN; matrices 0 = T, 1 = LcT, 2 = Uc.
 void launch_sweep_op(Launch L, const SweepArgs& a, int cset, int mat, int trans, int bset, double alpha,
                      const std::vector<BoxDesc>& h);

@@ -1772,10 +1772,10 @@ __device__ inline void sweep_set(const BoxDesc& d, const int32_t* fi, int set, c
 // output row, op(A) = A (row-major m x K) a warp per two rows.
 constexpr int SW_T_ROWS = 128, SW_N_ROWS = 16;
 struct CntSweep {
-  int cset, trans;
+  int cset, rows;  // output row set, output rows per item
   __host__ __device__ int64_t operator()(const BoxDesc& d) const {
     int64_t m = cset == 0 ? d.r : (cset == 1 ? d.kp : (int64_t)d.kp + d.n);
-    return cdv(m, trans ? SW_T_ROWS : SW_N_ROWS);
+    return cdv(m, rows);
   }
 };
 // The factor's blocks and the right-hand sides in the sweep's arithmetic: FP64, or the FP32 copies
@@ -1806,10 +1806,10 @@ __device__ inline void sweep_operands(const SweepArgs& a, const SweepOp& op, con
   else if (op.mat == 1) { A = fd + fd_LcT(d); lda = (int64_t)d.kp + d.n; }
   else { A = fd + fd_Uc(d); lda = (int64_t)d.kp + d.n; }
 }
-template <typename T>
-__global__ void __launch_bounds__(SW_T_ROWS) k_sweep_t(SweepArgs a, SweepOp op) {
+template <typename T, int ROWS>
+__device__ void sweep_t_item(const SweepArgs& a, const SweepOp& op, int64_t item) {
   int64_t loc;
-  int bi = find_item(a.desc, a.nbox, blockIdx.x, CntSweep{op.cset, 1}, loc);
+  int bi = find_item(a.desc, a.nbox, item, CntSweep{op.cset, ROWS}, loc);
   if (bi < 0) return;
   const BoxDesc d = a.desc[bi];
   const int32_t *cidx, *bidx;
@@ -1819,13 +1819,13 @@ __global__ void __launch_bounds__(SW_T_ROWS) k_sweep_t(SweepArgs a, SweepOp op) 
   T* F = sweep_F<T>(a);
   constexpr int QC = 64;
   __shared__ __align__(16) T Bs[QC][16];
-  const int64_t i = loc * SW_T_ROWS + threadIdx.x;
+  const int64_t i = loc * ROWS + threadIdx.x;
   for (int c0 = 0; c0 < a.nrhs; c0 += 16) {
     T acc[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) acc[c] = 0;
     for (int64_t q0 = 0; q0 < K; q0 += QC) {
-      for (int e = threadIdx.x; e < QC * 16; e += SW_T_ROWS) {
+      for (int e = threadIdx.x; e < QC * 16; e += ROWS) {
         const int qq = e >> 4, cc = e & 15;
         const int64_t q = q0 + qq;
         Bs[qq][cc] = (q < K && c0 + cc < a.nrhs) ? F[((int64_t)bidx[q] - a.row_base) * a.nrhs + c0 + cc] : (T)0;
@@ -1834,11 +1834,14 @@ __global__ void __launch_bounds__(SW_T_ROWS) k_sweep_t(SweepArgs a, SweepOp op) 
       if (i < m) {
         const int qn = (int)imin64(QC, K - q0);
         const T* Ai = A + q0 * lda + i;
-#pragma unroll 4
-        for (int qq = 0; qq < qn; ++qq) {
-          const T av = Ai[(int64_t)qq * lda];
+        for (int qq = 0; qq < qn; qq += 16) {  // 16 loads of A in flight, then their products
+          T av[16];
 #pragma unroll
-          for (int c = 0; c < 16; ++c) acc[c] = mad(av, Bs[qq][c], acc[c]);
+          for (int u = 0; u < 16; ++u) av[u] = qq + u < qn ? Ai[(int64_t)(qq + u) * lda] : (T)0;
+#pragma unroll
+          for (int u = 0; u < 16; ++u)
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[c] = mad(av[u], Bs[qq + u][c], acc[c]);
         }
       }
       __syncthreads();
@@ -1851,12 +1854,17 @@ __global__ void __launch_bounds__(SW_T_ROWS) k_sweep_t(SweepArgs a, SweepOp op) 
     }
   }
 }
+template <typename T>
+__global__ void __launch_bounds__(SW_T_ROWS) k_sweep_t(SweepArgs a, SweepOp op) {
+  sweep_t_item<T, SW_T_ROWS>(a, op, blockIdx.x);
+}
+
 // Row-major form (A m x K): warp w of the CTA owns output rows 2w and 2w + 1, its lanes stride
 // along K (consecutive elements of the A rows) with 16 partial sums per row, then reduce.
 template <typename T>
-__global__ void __launch_bounds__(256) k_sweep_n(SweepArgs a, SweepOp op) {
+__device__ void sweep_n_item(const SweepArgs& a, const SweepOp& op, int64_t item) {
   int64_t loc;
-  int bi = find_item(a.desc, a.nbox, blockIdx.x, CntSweep{op.cset, 0}, loc);
+  int bi = find_item(a.desc, a.nbox, item, CntSweep{op.cset, SW_N_ROWS}, loc);
   if (bi < 0) return;
   const BoxDesc d = a.desc[bi];
   const int32_t *cidx, *bidx;
@@ -1882,17 +1890,22 @@ __global__ void __launch_bounds__(256) k_sweep_n(SweepArgs a, SweepOp op) {
       }
       __syncthreads();
       const int qn = (int)imin64(QC, K - q0);
+      T av[2][QC / 32];  // the chunk's A values of both rows, all loads in flight together
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        if (i0 + u < m) {
-          const T* Ai = A + (i0 + u) * lda + q0;
-          for (int qq = lane; qq < qn; qq += 32) {
-            const T av = Ai[qq];
+      for (int u = 0; u < 2; ++u)
 #pragma unroll
-            for (int c = 0; c < 16; ++c) acc[u][c] = mad(av, Bs[qq][c], acc[u][c]);
-          }
+        for (int t = 0; t < QC / 32; ++t) {
+          const int qq = lane + 32 * t;
+          av[u][t] = (i0 + u < m && qq < qn) ? A[(i0 + u) * lda + q0 + qq] : (T)0;
         }
-      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int t = 0; t < QC / 32; ++t) {
+          const int qq = lane + 32 * t;
+#pragma unroll
+          for (int c = 0; c < 16; ++c) acc[u][c] = mad(av[u][t], Bs[qq][c], acc[u][c]);
+        }
       __syncthreads();
     }
 #pragma unroll
@@ -1910,6 +1923,11 @@ __global__ void __launch_bounds__(256) k_sweep_n(SweepArgs a, SweepOp op) {
     }
   }
 }
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_n(SweepArgs a, SweepOp op) {
+  sweep_n_item<T>(a, op, blockIdx.x);
+}
+
 // f_R <- M f_R with M = X_RR^-1 (solve) or X_RR (apply), or M^T for the adjoint; one CTA per
 // (box, group of DC columns): the rows R of F are staged in shared memory.
 constexpr int DC = 4;
@@ -1918,9 +1936,9 @@ struct CntDiag {
   __host__ __device__ int64_t operator()(const BoxDesc& d) const { return cdv(nrhs, DC); }
 };
 template <typename T>
-__global__ void __launch_bounds__(256) k_sweep_diag(SweepArgs a, int solve) {
+__device__ void sweep_diag_item(const SweepArgs& a, int solve, int64_t item, unsigned char* dsm_raw) {
   int64_t loc;
-  int bi = find_item(a.desc, a.nbox, blockIdx.x, CntDiag{a.nrhs}, loc);
+  int bi = find_item(a.desc, a.nbox, item, CntDiag{a.nrhs}, loc);
   if (bi < 0) return;
   const BoxDesc d = a.desc[bi];
   const int c0 = (int)loc * DC;
@@ -1929,7 +1947,6 @@ __global__ void __launch_bounds__(256) k_sweep_diag(SweepArgs a, int solve) {
   const int32_t* R = a.fi + fi_R(d);
   const T* M = sweep_fd<T>(a) + (solve ? fd_Xinv(d) : fd_XRR(d));
   T* F = sweep_F<T>(a);
-  extern __shared__ __align__(16) unsigned char dsm_raw[];
   T* in = reinterpret_cast<T*>(dsm_raw);  // r x DC
   for (int64_t e = threadIdx.x; e < r * DC; e += blockDim.x) {
     int64_t i = e / DC;
@@ -1972,6 +1989,81 @@ __global__ void __launch_bounds__(256) k_sweep_diag(SweepArgs a, int solve) {
     }
   }
 }
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_diag(SweepArgs a, int solve) {
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  sweep_diag_item<T>(a, solve, blockIdx.x, dsm_raw);
+}
+
+// ---- fused solve sweeps -----------------------------------------------------------------------
+// Barrier of all CTAs of a cooperative launch (all resident at once), in global memory: bar[0]
+// counts arrivals, bar[1] is the generation.  Thread 0 of each CTA makes its arrival without
+// waiting for the atomic's result; CTA 0 waits until every CTA has arrived, resets the count and
+// opens the next generation, which the other CTAs wait for.  Every wait gives up after max_polls
+// polls: it records kDevTimeout in bar[2] and returns false, and the CTA leaves the kernel (the
+// others then give up too).
+constexpr long long kGridPolls = 1ll << 25;
+__device__ bool grid_sync(unsigned* bar, long long max_polls = kGridPolls) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vcnt = bar;
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    atomicAdd(bar, 1u);  // result unused: a reduction, no round trip
+    int ok = 1;
+    long long polls = 0;
+    if (blockIdx.x == 0) {
+      while (*vcnt < gridDim.x) {
+        if (++polls > max_polls) {
+          ok = 0;
+          break;
+        }
+        if (polls > 256) __nanosleep(32);
+      }
+      if (ok) {
+        *vcnt = 0u;
+        __threadfence();
+        atomicAdd(bar + 1, 1u);
+      }
+    } else {
+      while (*vgen == gen) {
+        if (++polls > max_polls) {
+          ok = 0;
+          break;
+        }
+        if (polls > 256) __nanosleep(32);
+      }
+    }
+    if (!ok) atomicCAS(reinterpret_cast<int*>(bar + 2), 0, (int)kDevTimeout);
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+template <typename T>
+__global__ void __launch_bounds__(kSweepFusedThreads) k_sweep_fused(SweepArgs a, const SweepPhase* ph, int nph,
+                                                                   unsigned* bar) {
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  for (int p = 0; p < nph; ++p) {
+    const SweepPhase P = ph[p];
+    SweepArgs b = a;
+    b.desc = P.desc;
+    b.nbox = P.nbox;
+    const SweepOp op{P.cset, P.mat, P.kind == 0 ? 1 : 0, P.bset, P.alpha};
+    const int64_t items = P.kind == 2 ? (int64_t)P.nbox * ((a.nrhs + DC - 1) / DC) : P.items;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+      if (P.kind == 0) sweep_t_item<T, kSweepFusedRowsT>(b, op, it);
+      else if (P.kind == 1) sweep_n_item<T>(b, op, it);
+      else sweep_diag_item<T>(b, P.solve, it, dsm_raw);
+      __syncthreads();  // shared memory is reused by the next item
+    }
+    if (P.sync && p + 1 < nph && !grid_sync(bar)) return;
+  }
+}
+
 // Column of the inverse of an LU-factored matrix, staged in shared memory, solved cooperatively:
 // each substitution step updates the remaining entries in parallel.
 __global__ void __launch_bounds__(256) k_dense_inverse(const double* LU, const int32_t* piv, int64_t n,
@@ -2277,7 +2369,7 @@ void launch_dense_lu_solve(Launch L, const double* LU, const int32_t* piv, int64
 
 void launch_sweep_op(Launch L, const SweepArgs& a, int cset, int mat, int trans, int bset, double alpha,
                      const std::vector<BoxDesc>& h) {
-  const int64_t items = items_of<void>(h, CntSweep{cset, trans});
+  const int64_t items = items_of<void>(h, CntSweep{cset, trans ? SW_T_ROWS : SW_N_ROWS});
   if (items <= 0) return;
   const SweepOp op{cset, mat, trans, bset, alpha};
   if (trans) {
@@ -2288,6 +2380,60 @@ void launch_sweep_op(Launch L, const SweepArgs& a, int cset, int mat, int trans,
     else k_sweep_n<double><<<grid1(items), 256, 0, L.st>>>(a, op);
   }
   count_launch(L);
+}
+// Self-test of the grid barrier's bounded wait: two CTAs of a cooperative launch; CTA 1 takes part
+// only when `arrive` is set, so without it CTA 0's wait must expire after `polls` polls and record
+// kDevTimeout in bar[2].
+__global__ void k_grid_wait_selftest(unsigned* bar, long long polls, int arrive) {
+  if (blockIdx.x == 1 && !arrive) return;
+  (void)grid_sync(bar, polls);
+}
+bool launch_grid_wait_selftest(Launch L, unsigned* bar, long long polls, int arrive) {
+  void* kargs[] = {&bar, &polls, &arrive};
+  if (cudaLaunchCooperativeKernel((const void*)k_grid_wait_selftest, dim3(2), dim3(32), kargs, 0, L.st) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  count_launch(L);
+  return true;
+}
+int64_t sweep_phase_items(const std::vector<BoxDesc>& h, int kind, int cset, int nrhs) {
+  if (kind == 2) return items_of<void>(h, CntDiag{nrhs});
+  return items_of<void>(h, CntSweep{cset, kind == 0 ? kSweepFusedRowsT : kSweepFusedRowsN});
+}
+bool launch_sweep_fused(Launch L, const SweepArgs& a, const SweepPhase* ph, int nph, int max_r, unsigned* bar) {
+  if (nph <= 0) return true;
+  static_assert(kSweepFusedRowsN == SW_N_ROWS, "row-major items of the fused and the separate sweeps agree");
+  const size_t es = a.F32 ? sizeof(float) : sizeof(double);
+  const size_t smem = (size_t)std::max(max_r, 1) * DC * es;
+  int dev = 0, nsm = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  const void* fn = a.F32 ? (const void*)k_sweep_fused<float> : (const void*)k_sweep_fused<double>;
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return false;
+    }
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kSweepFusedThreads, smem) != cudaSuccess || per < 1) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  const unsigned grid = (unsigned)(std::min(per, 2) * nsm);  // fewer arrivals per barrier
+  SweepArgs args = a;
+  const SweepPhase* php = ph;
+  int n = nph;
+  unsigned* b = bar;
+  void* kargs[] = {&args, &php, &n, &b};
+  if (cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kSweepFusedThreads), kargs, smem, L.st) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  count_launch(L);
+  return true;
 }
 void launch_sweep_diag(Launch L, const SweepArgs& a, int solve, int64_t items, int max_r) {
   if (items <= 0) return;

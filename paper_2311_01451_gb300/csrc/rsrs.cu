@@ -84,8 +84,14 @@ struct rsrs_factor {
   // (oz_state 1), or found not to fit in device memory (-1); 0: not made yet
   mutable void* oz_store = nullptr;
   mutable int oz_state = 0;
+  // phase tables of the fused solve sweeps (device): for the solve (a = 0) and its adjoint (a = 1),
+  // the upward sweep followed by the diagonal step at ph_up[a], the downward sweep at ph_down[a]
+  SweepPhase* phases_dev = nullptr;
+  int64_t ph_up[2] = {0, 0}, ph_down[2] = {0, 0};
+  int nph_up[2] = {0, 0}, nph_down[2] = {0, 0};
   ~rsrs_factor() {
     if (oz_store) cudaFree(oz_store);
+    if (phases_dev) cudaFree(phases_dev);
   }
 };
 
@@ -133,6 +139,64 @@ struct DevPool {
     return e;
   }
 };
+
+// The fused solve's phase tables (see SweepPhase): per group of the factor, in the order of the
+// separate launches of sweep_solve, a barrier after every phase (each reads rows the previous one
+// writes); the diagonal step over all boxes closes the upward table (one phase when the factor's
+// descriptors are contiguous, else one per group without barriers between them).
+cudaError_t build_sweep_phases(rsrs_factor* f) {
+  std::vector<SweepPhase> all;
+  auto phase = [&](const GroupView& g, int kind, int cset, int mat, int bset, int sync) {
+    SweepPhase q{};
+    q.desc = f->desc_dev + g.desc_off;
+    q.nbox = (int)g.h.size();
+    q.kind = kind;
+    q.cset = cset;
+    q.mat = mat;
+    q.bset = bset;
+    q.solve = 1;
+    q.sync = sync;
+    q.alpha = -1.0;
+    q.items = kind == 2 ? 0 : sweep_phase_items(g.h, kind, cset, 0);
+    all.push_back(q);
+  };
+  bool contiguous = !f->groups.empty();
+  int64_t total = 0;
+  for (const GroupView& g : f->groups) {
+    if (g.desc_off != f->groups[0].desc_off + total) contiguous = false;
+    total += (int64_t)g.h.size();
+  }
+  for (int adj = 0; adj < 2; ++adj) {
+    f->ph_up[adj] = (int64_t)all.size();
+    for (const GroupView& g : f->groups) {
+      phase(g, 0, /*C=R*/ 0, /*T*/ 0, /*B=S*/ 1, 1);
+      phase(g, 0, /*C=SN*/ 2, adj ? /*Uc*/ 2 : /*LcT*/ 1, /*B=R*/ 0, 1);
+    }
+    if (contiguous && total <= INT32_MAX) {
+      GroupView all_boxes;
+      all_boxes.desc_off = f->groups[0].desc_off;
+      all_boxes.h.resize((size_t)total);
+      phase(all_boxes, 2, 0, 0, 0, 0);
+    } else {
+      for (const GroupView& g : f->groups) phase(g, 2, 0, 0, 0, 0);
+    }
+    f->nph_up[adj] = (int)((int64_t)all.size() - f->ph_up[adj]);
+    f->ph_down[adj] = (int64_t)all.size();
+    for (auto it = f->groups.rbegin(); it != f->groups.rend(); ++it) {
+      phase(*it, 1, /*C=R*/ 0, adj ? /*LcT*/ 1 : /*Uc*/ 2, /*B=SN*/ 2, 1);
+      phase(*it, 1, /*C=S*/ 1, /*T*/ 0, /*B=R*/ 0, 1);
+    }
+    f->nph_down[adj] = (int)((int64_t)all.size() - f->ph_down[adj]);
+  }
+  if (all.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void**)&f->phases_dev, all.size() * sizeof(SweepPhase));
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    f->phases_dev = nullptr;  // the solves then take the separate launches
+    return cudaSuccess;
+  }
+  return cudaMemcpy(f->phases_dev, all.data(), all.size() * sizeof(SweepPhase), cudaMemcpyHostToDevice);
+}
 
 // Scratch of one call from the stream-ordered allocator: allocated and freed in the order of
 // `st`, so a call neither waits for the device nor serialises other streams.
@@ -1210,6 +1274,7 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
     f->stats.factor_bytes = fdb * 8 + fib * 4 + f->root_size * f->root_size * 24 + f->root_size * 8;
     if (f->fd32) f->stats.factor_bytes += fdb * 4 + f->root_size * f->root_size * 4;
     f->stats.solve_bytes = (sweep + f->root_size * f->root_size) * (f->fd32 ? 4 : 8);
+    CU(build_sweep_phases(f));
     out[p] = F[p].release();
   }
   return RSRS_OK;
@@ -1588,7 +1653,11 @@ void diag_sweep(const rsrs_factor* f, Launch L, SweepArgs a, int nrhs, int solve
   }
 }
 
-rsrs_status sweep_solve(const rsrs_factor* f, Launch L, double* W, int nrhs, int adjoint, float* w32 = nullptr) {
+// bar (optional): three zeroed words of device scratch for the fused sweeps' grid barrier; with it
+// each sweep direction is one cooperative launch over the factor's phase table, else (or when the
+// cooperative launch is refused) one launch per group and product.
+rsrs_status sweep_solve(const rsrs_factor* f, Launch L, double* W, int nrhs, int adjoint, float* w32 = nullptr,
+                        unsigned* bar = nullptr) {
   SweepArgs a{};
   a.fd = f->fd;
   a.fi = f->fi;
@@ -1601,6 +1670,19 @@ rsrs_status sweep_solve(const rsrs_factor* f, Launch L, double* W, int nrhs, int
     a.fd32 = f->fd32;
     a.F32 = w32;
     launch_to_f32(L, W, f->n * nrhs, w32);
+  }
+  const int ad = adjoint ? 1 : 0;
+  if (bar && f->phases_dev &&
+      launch_sweep_fused(L, a, f->phases_dev + f->ph_up[ad], f->nph_up[ad], f->max_r, bar)) {
+    if (f->root_size > 0) {
+      if (fp32) launch_dense_apply(L, f->root_inv32, f->root_size, f->root_idx, f->base, w32, nrhs, adjoint);
+      else launch_dense_apply(L, f->root_inv, f->root_size, f->root_idx, f->base, W, nrhs, adjoint);
+    }
+    if (!launch_sweep_fused(L, a, f->phases_dev + f->ph_down[ad], f->nph_down[ad], f->max_r, bar))
+      return fail(RSRS_E_CUDA, "solve: the cooperative launch of the downward sweep failed");
+    if (fp32) launch_to_f64(L, w32, f->n * nrhs, W);
+    CU(cudaGetLastError());
+    return RSRS_OK;
   }
   // upward: V_1^-1 first (V^-1 = L E), or W^-* = U^* F^* for the adjoint
   for (const GroupView& g : f->groups) {
@@ -1629,6 +1711,14 @@ rsrs_status sweep_solve(const rsrs_factor* f, Launch L, double* W, int nrhs, int
   }
   if (fp32) launch_to_f64(L, w32, f->n * nrhs, W);
   CU(cudaGetLastError());
+  return RSRS_OK;
+}
+
+// Status of the fused sweeps run with barrier words bar (after the stream has reached them).
+rsrs_status sweep_status(const unsigned* bar) {
+  unsigned h[4] = {0, 0, 0, 0};
+  CU(cudaMemcpy(h, bar, sizeof(h), cudaMemcpyDeviceToHost));
+  if ((int)h[2] == kDevTimeout) return fail(RSRS_E_TIMEOUT, "solve: a grid barrier of the fused sweeps gave up");
   return RSRS_OK;
 }
 
@@ -1683,10 +1773,13 @@ rsrs_status rsrs_solve(const rsrs_factor* f, double* F, int64_t ldf, int32_t nrh
   StreamPool pool(st);
   double* W;
   float* w32 = nullptr;
+  unsigned* bar = nullptr;
   CU(pool.alloc(&W, f->n * nrhs));
   if (f->fd32) CU(pool.alloc(&w32, f->n * nrhs));
+  CU(pool.alloc(&bar, 4));
+  CU(cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), st));
   k_cm_to_rows<<<nblk(f->n * nrhs), 256, 0, st>>>(F, ldf, f->perm_dev, f->n, nrhs, W);
-  r = sweep_solve(f, L, W, nrhs, adjoint, w32);
+  r = sweep_solve(f, L, W, nrhs, adjoint, w32, bar);
   if (r != RSRS_OK) return r;
   k_rows_to_cm<<<nblk(f->n * nrhs), 256, 0, st>>>(W, f->perm_dev, f->n, nrhs, F, ldf);
   CU(cudaGetLastError());
@@ -1755,13 +1848,16 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_
     CU(pool.alloc(&c1, tot));
     CU(pool.alloc(&c2, tot));
   }
+  unsigned* bar = nullptr;  // the fused sweeps' barrier words, shared by this call's solves
+  CU(pool.alloc(&bar, 4));
+  CU(cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), st));
   ResidualOp ro;
   r = residual_setup(f, L, pool, nrhs, ro);
   if (r != RSRS_OK) return r;
   k_cm_to_rows<<<nblk(tot), 256, 0, st>>>(B, ld, f->perm_dev, f->n, nrhs, Wb);
   ++nl;
   CU(cudaMemcpyAsync(Wx, Wb, tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  r = sweep_solve(f, L, Wx, nrhs, 0, w32);
+  r = sweep_solve(f, L, Wx, nrhs, 0, w32, bar);
   if (r != RSRS_OK) return r;
   double hn[128];
   CU(cudaMemsetAsync(nrm, 0, 64 * sizeof(double), st));
@@ -1791,7 +1887,7 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_
     if (it < 64) rr.history[it] = rel;
     if (!std::isfinite(rel)) return fail(RSRS_E_NONFINITE, "refine: non-finite residual");
     if (rel <= rtol || it >= maxit) break;
-    r = sweep_solve(f, L, Wr, nrhs, 0, w32);
+    r = sweep_solve(f, L, Wr, nrhs, 0, w32, bar);
     if (r != RSRS_OK) return r;
     k_axpy<<<nblk(tot), 256, 0, st>>>(Wx, Wr, 1.0, tot);
     ++nl;
@@ -1801,6 +1897,8 @@ rsrs_status rsrs_refine(const rsrs_factor* f, const double* B, double* X, int64_
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(st));
   r = residual_check(f, ro);
+  if (r != RSRS_OK) return r;
+  r = sweep_status(bar);
   if (r != RSRS_OK) return r;
   rr.iterations = it;
   rr.rel_residual = rel;
@@ -1960,6 +2058,9 @@ rsrs_status rsrs_gmres(const rsrs_factor* f, const double* B, double* X, int64_t
     CU(pool.alloc(&c1, tot));
     CU(pool.alloc(&c2, tot));
   }
+  unsigned* bar = nullptr;  // the fused sweeps' barrier words, shared by this call's solves
+  CU(pool.alloc(&bar, 4));
+  CU(cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), st));
   ResidualOp ro;
   r = residual_setup(f, L, pool, c, ro);
   if (r != RSRS_OK) return r;
@@ -2012,7 +2113,7 @@ rsrs_status rsrs_gmres(const rsrs_factor* f, const double* B, double* X, int64_t
       double* Vk = V + (int64_t)k * tot;
       double* Zk = Z + (int64_t)k * tot;
       CU(cudaMemcpyAsync(Zk, Vk, tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      r = sweep_solve(f, L, Zk, c, 0, w32);  // z_k = M^-1 v_k
+      r = sweep_solve(f, L, Zk, c, 0, w32, bar);  // z_k = M^-1 v_k
       if (r != RSRS_OK) return r;
       r = apply_A(Zk, Ww);              // w = A z_k
       if (r != RSRS_OK) return r;
@@ -2082,6 +2183,8 @@ rsrs_status rsrs_gmres(const rsrs_factor* f, const double* B, double* X, int64_t
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(st));
   r = residual_check(f, ro);
+  if (r != RSRS_OK) return r;
+  r = sweep_status(bar);
   if (r != RSRS_OK) return r;
   rr.iterations = total;
   rr.rel_residual = rel;
@@ -2181,12 +2284,14 @@ rsrs_status rsrs_factor_sketches(const rsrs_factor* f, double* Yh, double* Zh, d
 static __device__ __align__(256) double g_noalloc_stage[RSRS_NOALLOC_MAX_ELEMS];
 // ... and its FP32 copy, for a mixed-precision factor's FP32 solve
 static __device__ __align__(256) float g_noalloc_stage32[RSRS_NOALLOC_MAX_ELEMS];
+static __device__ __align__(16) unsigned g_noalloc_bar[4];  // the fused sweeps' barrier words
 
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 double* g_noalloc_addr[kMaxDevices] = {};
 float* g_noalloc_addr32[kMaxDevices] = {};
+unsigned* g_noalloc_bar_addr[kMaxDevices] = {};
 }  // namespace
 
 extern "C" rsrs_status rsrs_solve_noalloc(const rsrs_factor* f, double* F, int64_t ldf, int32_t nrhs, int adjoint,
@@ -2202,6 +2307,7 @@ extern "C" rsrs_status rsrs_solve_noalloc(const rsrs_factor* f, double* F, int64
   if (dev < 0 || dev >= kMaxDevices) return fail(RSRS_E_INVAL, "solve_noalloc: device ordinal out of range");
   double* W = nullptr;
   float* W32 = nullptr;
+  unsigned* bar = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_addr[dev]) {  // set-up, once per device, with that device current
@@ -2209,16 +2315,21 @@ extern "C" rsrs_status rsrs_solve_noalloc(const rsrs_factor* f, double* F, int64
       void* p32 = nullptr;
       CU(cudaGetSymbolAddress(&p, g_noalloc_stage));
       CU(cudaGetSymbolAddress(&p32, g_noalloc_stage32));
+      void* pb = nullptr;
+      CU(cudaGetSymbolAddress(&pb, g_noalloc_bar));
       g_noalloc_addr[dev] = static_cast<double*>(p);
       g_noalloc_addr32[dev] = static_cast<float*>(p32);
+      g_noalloc_bar_addr[dev] = static_cast<unsigned*>(pb);
     }
     W = g_noalloc_addr[dev];
     W32 = g_noalloc_addr32[dev];
+    bar = g_noalloc_bar_addr[dev];
   }
   cudaStream_t st = (cudaStream_t)stream;
   Launch L{st, nullptr};
+  CU(cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), st));
   k_cm_to_rows<<<nblk(f->n * nrhs), 256, 0, st>>>(F, ldf, f->perm_dev, f->n, nrhs, W);
-  r = sweep_solve(f, L, W, nrhs, adjoint, f->fd32 ? W32 : nullptr);
+  r = sweep_solve(f, L, W, nrhs, adjoint, f->fd32 ? W32 : nullptr, bar);
   if (r != RSRS_OK) return r;
   k_rows_to_cm<<<nblk(f->n * nrhs), 256, 0, st>>>(W, f->perm_dev, f->n, nrhs, F, ldf);
   CU(cudaGetLastError());
@@ -2230,6 +2341,21 @@ extern "C" rsrs_status rsrs_convert_selftest(const double* x, int64_t n, float* 
   launch_convert_selftest(Launch{(cudaStream_t)stream, nullptr}, x, n, f, g);
   CU(cudaGetLastError());
   return RSRS_OK;
+}
+
+extern "C" rsrs_status rsrs_grid_wait_selftest(int64_t polls, int arrive, void* stream) {
+  if (polls <= 0 || polls > ((int64_t)1 << 26) || (arrive != 0 && arrive != 1))
+    return fail(RSRS_E_INVAL, "grid_wait_selftest: polls outside 1..2^26 or arrive not 0/1");
+  cudaStream_t st = (cudaStream_t)stream;
+  DevPool pool;
+  unsigned* bar = nullptr;
+  CU(pool.alloc(&bar, 4));
+  CU(cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), st));
+  if (!launch_grid_wait_selftest(Launch{st, nullptr}, bar, (long long)polls, arrive))
+    return fail(RSRS_E_CUDA, "grid_wait_selftest: the cooperative launch was refused");
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(st));
+  return sweep_status(bar) == RSRS_OK ? RSRS_OK : fail(RSRS_E_TIMEOUT, "grid_wait_selftest: the bounded wait expired");
 }
 
 extern "C" rsrs_status rsrs_wait_selftest(int64_t polls, int arrive, void* stream) {

@@ -23,7 +23,7 @@ STATUS = {0: "RSRS_OK", 1: "RSRS_E_INVAL", 2: "RSRS_E_UNDERSAMPLED", 3: "RSRS_E_
           8: "RSRS_E_TIMEOUT", 9: "RSRS_E_NOT_CONVERGED"}
 
 EXPORTS = ["rsrs_tree_build", "rsrs_tree_info", "rsrs_tree_perm", "rsrs_tree_schedule", "rsrs_tree_free",
-           "rsrs_build", "rsrs_build_batched", "rsrs_refactor", "rsrs_solve", "rsrs_solve_noalloc", "rsrs_wait_selftest", "rsrs_convert_selftest", "rsrs_apply", "rsrs_refine", "rsrs_residual", "rsrs_matvec", "rsrs_factor_stats",
+           "rsrs_build", "rsrs_build_batched", "rsrs_refactor", "rsrs_solve", "rsrs_solve_noalloc", "rsrs_wait_selftest", "rsrs_grid_wait_selftest", "rsrs_convert_selftest", "rsrs_apply", "rsrs_refine", "rsrs_residual", "rsrs_matvec", "rsrs_factor_stats",
            "rsrs_factor_box", "rsrs_factor_root", "rsrs_factor_sketches", "rsrs_factor_free",
            "rsrs_status_string", "rsrs_last_error", "rsrs_kernel_class_name", "rsrs_stencil7_create", "rsrs_stencil7_matvec", "rsrs_stencil7_free", "rsrs_autotune", "rsrs_gmres"]
 
@@ -140,6 +140,7 @@ def lib():
             "rsrs_autotune": [C.c_int, C.POINTER(vp), C.POINTER(Operator), C.c_int, C.c_int, C.POINTER(Options),
                               C.c_int, C.c_char_p, vp, C.POINTER(Tune), C.POINTER(TuneReport)],
             "rsrs_wait_selftest": [i64, C.c_int, vp],
+            "rsrs_grid_wait_selftest": [i64, C.c_int, vp],
             "rsrs_convert_selftest": [vp, i64, vp, vp, vp],
         }
         for name, args in sig.items():
@@ -167,6 +168,13 @@ def wait_selftest(polls: int, arrive: bool, stream=None):
     ``polls`` polls), for an arrival made only when ``arrive`` is true.  Raises RSRSError
     (RSRS_E_TIMEOUT) when the wait expired; returns None when it completed."""
     _check(lib().rsrs_wait_selftest(int(polls), int(bool(arrive)), _stream_ptr(stream)))
+
+
+def grid_wait_selftest(polls: int, arrive: bool, stream=None):
+    """rsrs_grid_wait_selftest: two CTAs meet at the fused sweeps' grid barrier (at most ``polls``
+    polls), the second only when ``arrive`` is true.  Raises RSRSError (RSRS_E_TIMEOUT) when the
+    wait expired; returns None when both arrived."""
+    _check(lib().rsrs_grid_wait_selftest(int(polls), int(bool(arrive)), _stream_ptr(stream)))
 
 
 def convert_selftest(x, stream=None):

@@ -2,7 +2,8 @@
 input or a wait that cannot complete, comes back as a status code, and leaves the context usable.
 
 * a bounded mbarrier wait that nothing completes (rsrs_wait_selftest with no arrival) expires and
-  reports RSRS_E_TIMEOUT; the same wait with its arrival completes;
+  reports RSRS_E_TIMEOUT; the same wait with its arrival completes; likewise the grid-wide
+  barrier of the fused solve sweeps with one of its two CTAs missing (rsrs_grid_wait_selftest);
 * a matvec callback that returns an error aborts the build with RSRS_E_CALLBACK;
 * a non-finite entry in the caller's test matrix reaches the pivot checks of the CPQR and LU
   kernels, which record it in the device status word (RSRS_E_NONFINITE or RSRS_E_SINGULAR); every
@@ -55,6 +56,18 @@ def test_bounded_wait_expires_with_status(R):
         R.wait_selftest(1 << 12, arrive=False)
     assert e.value.name == "RSRS_E_TIMEOUT"
     R.wait_selftest(1 << 12, arrive=True)  # the same wait, completed by its arrival
+    torch.cuda.synchronize()
+    _assert_context_usable(R)
+
+
+def test_grid_barrier_wait_expires_with_status(R):
+    """The fused solve sweeps' grid-wide barrier: with one CTA missing, the other's bounded wait
+    expires and reports RSRS_E_TIMEOUT; with both present it completes; the context stays usable
+    (a refined solve through the fused sweeps afterwards reaches the dense solution)."""
+    with pytest.raises(R.RSRSError) as e:
+        R.grid_wait_selftest(1 << 12, arrive=False)
+    assert e.value.name == "RSRS_E_TIMEOUT"
+    R.grid_wait_selftest(1 << 12, arrive=True)
     torch.cuda.synchronize()
     _assert_context_usable(R)
 
