@@ -307,10 +307,13 @@ struct SweepPhase {
   int nbox, kind, cset, mat, bset, solve, sync;
   double alpha;
   int64_t items;
+  const int2* map;  // kinds 0 and 1: item -> (box, tile of the box); kind 2 maps by division
 };
 constexpr int kSweepFusedThreads = 256, kSweepFusedRowsT = 256, kSweepFusedRowsN = 16;
 // Items of a sweep phase over boxes h (kind as above; nrhs for the diagonal step).
 int64_t sweep_phase_items(const std::vector<BoxDesc>& h, int kind, int cset, int nrhs);
+// Output-row tiles per box of a sweep product phase (kinds 0 and 1).
+int64_t sweep_phase_tiles(const BoxDesc& d, int kind, int cset);
 // The phases [ph, ph + nph) in one cooperative launch of persistent CTAs (all resident), with a
 // bounded grid-wide barrier after each phase marked sync: bar holds the barrier's arrival counter
 // and generation (zero on entry) and a status word (bar[2], kDevTimeout when a barrier wait gave

@@ -1807,9 +1807,16 @@ __device__ inline void sweep_operands(const SweepArgs& a, const SweepOp& op, con
   else { A = fd + fd_Uc(d); lda = (int64_t)d.kp + d.n; }
 }
 template <typename T, int ROWS>
-__device__ void sweep_t_item(const SweepArgs& a, const SweepOp& op, int64_t item) {
+__device__ void sweep_t_item(const SweepArgs& a, const SweepOp& op, int64_t item, const int2* map = nullptr) {
   int64_t loc;
-  int bi = find_item(a.desc, a.nbox, item, CntSweep{op.cset, ROWS}, loc);
+  int bi;
+  if (map) {
+    const int2 bl = map[item];
+    bi = bl.x;
+    loc = bl.y;
+  } else {
+    bi = find_item(a.desc, a.nbox, item, CntSweep{op.cset, ROWS}, loc);
+  }
   if (bi < 0) return;
   const BoxDesc d = a.desc[bi];
   const int32_t *cidx, *bidx;
@@ -1862,9 +1869,16 @@ __global__ void __launch_bounds__(SW_T_ROWS) k_sweep_t(SweepArgs a, SweepOp op) 
 // Row-major form (A m x K): warp w of the CTA owns output rows 2w and 2w + 1, its lanes stride
 // along K (consecutive elements of the A rows) with 16 partial sums per row, then reduce.
 template <typename T>
-__device__ void sweep_n_item(const SweepArgs& a, const SweepOp& op, int64_t item) {
+__device__ void sweep_n_item(const SweepArgs& a, const SweepOp& op, int64_t item, const int2* map = nullptr) {
   int64_t loc;
-  int bi = find_item(a.desc, a.nbox, item, CntSweep{op.cset, SW_N_ROWS}, loc);
+  int bi;
+  if (map) {
+    const int2 bl = map[item];
+    bi = bl.x;
+    loc = bl.y;
+  } else {
+    bi = find_item(a.desc, a.nbox, item, CntSweep{op.cset, SW_N_ROWS}, loc);
+  }
   if (bi < 0) return;
   const BoxDesc d = a.desc[bi];
   const int32_t *cidx, *bidx;
@@ -1936,9 +1950,17 @@ struct CntDiag {
   __host__ __device__ int64_t operator()(const BoxDesc& d) const { return cdv(nrhs, DC); }
 };
 template <typename T>
-__device__ void sweep_diag_item(const SweepArgs& a, int solve, int64_t item, unsigned char* dsm_raw) {
+__device__ void sweep_diag_item(const SweepArgs& a, int solve, int64_t item, unsigned char* dsm_raw,
+                                bool by_division = false) {
   int64_t loc;
-  int bi = find_item(a.desc, a.nbox, item, CntDiag{a.nrhs}, loc);
+  int bi;
+  if (by_division) {  // every box has cdv(nrhs, DC) items
+    const int64_t per = cdv(a.nrhs, DC);
+    bi = (int)(item / per);
+    loc = item % per;
+  } else {
+    bi = find_item(a.desc, a.nbox, item, CntDiag{a.nrhs}, loc);
+  }
   if (bi < 0) return;
   const BoxDesc d = a.desc[bi];
   const int c0 = (int)loc * DC;
@@ -2055,9 +2077,9 @@ __global__ void __launch_bounds__(kSweepFusedThreads) k_sweep_fused(SweepArgs a,
     const SweepOp op{P.cset, P.mat, P.kind == 0 ? 1 : 0, P.bset, P.alpha};
     const int64_t items = P.kind == 2 ? (int64_t)P.nbox * ((a.nrhs + DC - 1) / DC) : P.items;
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
-      if (P.kind == 0) sweep_t_item<T, kSweepFusedRowsT>(b, op, it);
-      else if (P.kind == 1) sweep_n_item<T>(b, op, it);
-      else sweep_diag_item<T>(b, P.solve, it, dsm_raw);
+      if (P.kind == 0) sweep_t_item<T, kSweepFusedRowsT>(b, op, it, P.map);
+      else if (P.kind == 1) sweep_n_item<T>(b, op, it, P.map);
+      else sweep_diag_item<T>(b, P.solve, it, dsm_raw, true);
       __syncthreads();  // shared memory is reused by the next item
     }
     if (P.sync && p + 1 < nph && !grid_sync(bar)) return;
@@ -2396,6 +2418,9 @@ bool launch_grid_wait_selftest(Launch L, unsigned* bar, long long polls, int arr
   }
   count_launch(L);
   return true;
+}
+int64_t sweep_phase_tiles(const BoxDesc& d, int kind, int cset) {
+  return CntSweep{cset, kind == 0 ? kSweepFusedRowsT : kSweepFusedRowsN}(d);
 }
 int64_t sweep_phase_items(const std::vector<BoxDesc>& h, int kind, int cset, int nrhs) {
   if (kind == 2) return items_of<void>(h, CntDiag{nrhs});

@@ -146,6 +146,8 @@ struct DevPool {
 // descriptors are contiguous, else one per group without barriers between them).
 cudaError_t build_sweep_phases(rsrs_factor* f) {
   std::vector<SweepPhase> all;
+  std::vector<int2> maps;             // item -> (box, tile) of every product phase, concatenated
+  std::vector<int64_t> map_off;       // per phase: its first map entry, or -1
   auto phase = [&](const GroupView& g, int kind, int cset, int mat, int bset, int sync) {
     SweepPhase q{};
     q.desc = f->desc_dev + g.desc_off;
@@ -158,6 +160,13 @@ cudaError_t build_sweep_phases(rsrs_factor* f) {
     q.sync = sync;
     q.alpha = -1.0;
     q.items = kind == 2 ? 0 : sweep_phase_items(g.h, kind, cset, 0);
+    q.map = nullptr;
+    map_off.push_back(kind == 2 ? -1 : (int64_t)maps.size());
+    if (kind != 2)
+      for (size_t b = 0; b < g.h.size(); ++b) {
+        const int64_t nt = sweep_phase_tiles(g.h[b], kind, cset);
+        for (int64_t t = 0; t < nt; ++t) maps.push_back(make_int2((int)b, (int)t));
+      }
     all.push_back(q);
   };
   bool contiguous = !f->groups.empty();
@@ -189,13 +198,21 @@ cudaError_t build_sweep_phases(rsrs_factor* f) {
     f->nph_down[adj] = (int)((int64_t)all.size() - f->ph_down[adj]);
   }
   if (all.empty()) return cudaSuccess;
-  cudaError_t e = cudaMalloc((void**)&f->phases_dev, all.size() * sizeof(SweepPhase));
+  // one allocation: the phase table, then the item maps (16-byte aligned)
+  const size_t tbytes = (all.size() * sizeof(SweepPhase) + 15) & ~(size_t)15;
+  const size_t bytes = tbytes + maps.size() * sizeof(int2);
+  cudaError_t e = cudaMalloc((void**)&f->phases_dev, bytes);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     f->phases_dev = nullptr;  // the solves then take the separate launches
     return cudaSuccess;
   }
-  return cudaMemcpy(f->phases_dev, all.data(), all.size() * sizeof(SweepPhase), cudaMemcpyHostToDevice);
+  const int2* map_dev = reinterpret_cast<const int2*>(reinterpret_cast<const char*>(f->phases_dev) + tbytes);
+  for (size_t i = 0; i < all.size(); ++i)
+    if (map_off[i] >= 0) all[i].map = map_dev + map_off[i];
+  e = cudaMemcpy(f->phases_dev, all.data(), all.size() * sizeof(SweepPhase), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess || maps.empty()) return e;
+  return cudaMemcpy(const_cast<int2*>(map_dev), maps.data(), maps.size() * sizeof(int2), cudaMemcpyHostToDevice);
 }
 
 // Scratch of one call from the stream-ordered allocator: allocated and freed in the order of

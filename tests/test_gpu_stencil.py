@@ -64,7 +64,7 @@ def test_stencil_rejects_bad_coefficients(R):
 
 def test_stencil_fp64_matches_oracle(R):
     """The 12^3 operator in FP64 against the oracle on the same test matrices.  Skeletons must agree
-    up to an accepted near-tie (tie_band: P9's 1e-10 of |R_00|, or the nullification's rounding
+    up to an accepted near-tie (tie_band: 1e-10 of |R_00|, or the nullification's rounding
     level for boxes whose far field is weak fill from eliminated neighbours).  Without a near-tie
     the unrefined solutions agree to 1e-10 or to the ID's measured amplification of the rounding
     (derived as in test_gpu_parity); after one, the two factorizations are different valid
