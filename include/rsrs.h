@@ -127,7 +127,12 @@ typedef struct {
   int keep_sketches;      /* keep the final Y, Z, Omega, Psi on the device (tests)     */
   int profile;            /* record CUDA-event time per kernel class into rsrs_stats    */
   int sample_kernel;      /* mixed precision, built-in kernels: 1 FP32 SIMT, 2 (and the  */
-                          /* default 0) 3xTF32 on the tensor cores (tcgen05, TMA)       */
+                          /* default 0) 3xTF32 on the tensor cores (tcgen05, TMA);      */
+                          /* FP64, one built-in-kernel problem: 3 = FP64-accurate       */
+                          /* products by the Ozaki scheme on the bf16 tensor cores (the */
+                          /* refinement residual's digit store, made by the build, 20 N^2 */
+                          /* bytes; the FP64 SIMT product when it does not fit), 0 =    */
+                          /* the FP64 SIMT product                                     */
   int mixed_cpqr;         /* mixed precision: 0 default = FP32 reflectors on the sketch  */
                           /* held in distributed shared memory (thread-block cluster of */
                           /* up to 16 CTAs), pivots chosen on FP64 residual norms, when */

@@ -84,6 +84,7 @@ struct rsrs_factor {
   // (oz_state 1), or found not to fit in device memory (-1); 0: not made yet
   mutable void* oz_store = nullptr;
   mutable int oz_state = 0;
+  bool oz_in_build = false;  // the store's digits are made by the build (and its graph) itself
   // phase tables of the fused solve sweeps (device): for the solve (a = 0) and its adjoint (a = 1),
   // the upward sweep followed by the diagonal step at ph_up[a], the downward sweep at ph_down[a]
   SweepPhase* phases_dev = nullptr;
@@ -139,6 +140,25 @@ struct DevPool {
     return e;
   }
 };
+
+// Device memory for the Ozaki residual's store of K's digits, when it fits with a margin (2 GiB +
+// 5 % of the device) for the rest of the work; the digits are made separately.
+bool oz_alloc_store(const rsrs_factor* f) {
+  const size_t bytes = (size_t)oz_store_bytes(f->n, f->d);
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  if (fr < bytes + ((size_t)2 << 30) + tot / 20) return false;
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  f->oz_store = p;
+  return true;
+}
 
 // The fused solve's phase tables (see SweepPhase): per group of the factor, in the order of the
 // separate launches of sweep_solve, a barrier after every phase (each reads rows the previous one
@@ -527,7 +547,9 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
   if (opts) o = *opts;
   if (o.precision != RSRS_PREC_FP64 && o.precision != RSRS_PREC_MIXED)
     return fail(RSRS_E_INVAL, "build: unknown precision");
-  if (o.sample_kernel < 0 || o.sample_kernel > 2) return fail(RSRS_E_INVAL, "build: unknown sample_kernel");
+  if (o.sample_kernel < 0 || o.sample_kernel > 3) return fail(RSRS_E_INVAL, "build: unknown sample_kernel");
+  if (o.sample_kernel == 3 && o.precision == RSRS_PREC_MIXED)
+    return fail(RSRS_E_INVAL, "build: sample_kernel 3 (Ozaki FP64 sampling) is for FP64 builds");
   if (o.mixed_cpqr < 0 || o.mixed_cpqr > 1) return fail(RSRS_E_INVAL, "build: unknown mixed_cpqr");
   if (o.mixed_gemm < 0 || o.mixed_gemm > 1) return fail(RSRS_E_INVAL, "build: unknown mixed_gemm");
   if (!tune_valid(o.tune)) return fail(RSRS_E_INVAL, "build: tune values out of range");
@@ -900,6 +922,14 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
   bool root32 = mixed && o.mixed_gemm == 0;
   for (int p = 0; p < nprob; ++p)
     if (F[p]->root_size > 0 && mixed_sample_bound(0, F[p]->root_size) > s) root32 = false;
+  // FP64 sampling through the Ozaki product (sample_kernel 3, one built-in-kernel problem): the
+  // digit store (which the refinement residuals then reuse) and the product's scratch, before
+  // any capture; without room for the store the FP64 SIMT product runs instead
+  uint8_t* oz_scr = nullptr;
+  const bool oz_sample = !mixed && o.sample_kernel == 3 && nprob == 1 && F[0]->kind != RSRS_OP_CALLBACK &&
+                         (F[0]->oz_store || oz_alloc_store(F[0].get())) &&
+                         pool.alloc(&oz_scr, oz_scratch_bytes(F[0]->n)) == cudaSuccess;
+  if (oz_sample) F[0]->oz_in_build = true;
   // tensor-core path: hi/lo planes of [Omega Psi] (2s x N each) and the FP32 points; SIMT path:
   // an FP32 copy of one side
   if (mixed && any_builtin)
@@ -1035,6 +1065,15 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
           if (!launch_kernel_matvec_tc(L, fp->kind, p32, fp->n, fp->shift, fp->scale, Om + off, Ps + off, Y + off,
                                        Z + off, s, s, 2 * s, hi, lo, ldp, err, o.tune.sample_tile))
             r1 = fail(RSRS_E_CUDA, "could not encode the TMA tensor maps of the sampling product");
+          continue;
+        }
+        if (oz_sample) {
+          // FP64-accurate Y = A Omega and Z = A Psi (the built-in kernels are symmetric) from exact
+          // bf16 digit products, 16 columns per pass over the store
+          launch_oz_prepare(L, fp->kind, fp->pts_dev, fp->d, fp->n, fp->oz_store);
+          launch_oz_matvec(L, fp->n, fp->d, fp->oz_store, fp->shift, fp->scale, Om + off, s, Y + off, s, s, oz_scr);
+          launch_oz_matvec(L, fp->n, fp->d, fp->oz_store, fp->shift, fp->scale, Ps + off, s, Z + off, s, s, oz_scr);
+          fp->oz_state = 1;
           continue;
         }
         r1 = op_apply(fp, L, Om + off, Y + off, s, 0, fp32, cm_in, cm_out, err, conv);
@@ -1239,6 +1278,12 @@ rsrs_status build_impl(int nprob, const rsrs_tree* const* trees, const rsrs_oper
   if (herr == kDevSingular) return fail(RSRS_E_SINGULAR, "zero pivot in an LU factorization");
   if (herr == kDevNonfinite) return fail(RSRS_E_NONFINITE, "non-finite or non-positive pivot");
   if (herr == kDevTimeout) return fail(RSRS_E_TIMEOUT, "a bounded device wait expired");
+  if (oz_sample) {
+    int hoz = 0;
+    CU(cudaMemcpy(&hoz, oz_status_word(F[0]->oz_store, F[0]->n, F[0]->d), sizeof(int), cudaMemcpyDeviceToHost));
+    if (hoz == kDevNonfinite) return fail(RSRS_E_NONFINITE, "sampling: two points coincide (the kernel is unbounded)");
+    if (hoz == kDevTimeout) return fail(RSRS_E_TIMEOUT, "sampling: a bounded device wait expired");
+  }
   float t01 = 0.f, t12 = 0.f, t23 = 0.f;
   if (!graph) {
     CU(cudaEventElapsedTime(&t01, ev[0], ev[1]));
@@ -1402,11 +1447,15 @@ rsrs_status rsrs_refactor(rsrs_factor* f, uint64_t seed, void* stream) {
   Shared* sh = f->sh.get();
   if (!sh || !sh->exec) return fail(RSRS_E_INVAL, "refactor: the factor was built without use_graph");
   cudaStream_t st = (cudaStream_t)stream;
-  if (f->oz_store) {  // made again at the next residual, so that a rebuild costs what a build does
-    cudaFree(f->oz_store);
-    f->oz_store = nullptr;
+  if (f->oz_in_build) {
+    // the build's own sampling makes the digits: the replay below makes them again
+  } else {
+    if (f->oz_store) {  // made again at the next residual, so that a rebuild costs what a build does
+      cudaFree(f->oz_store);
+      f->oz_store = nullptr;
+    }
+    f->oz_state = 0;
   }
-  f->oz_state = 0;
   k_set_u64<<<1, 1, 0, st>>>(sh->seed_dev, seed);
   CU(cudaGetLastError());
   CU(cudaGraphLaunch(sh->exec, st));

@@ -204,6 +204,10 @@ def case(request, R):
 
 def test_skeletons_and_blocks_match_oracle(case):
     pr, fac, f, _, trace = case
+    _check_blocks(pr, fac, f, trace)
+
+
+def _check_blocks(pr, fac, f, trace):
     assert f.stats().n_boxes == len(fac.boxes)
     tols = box_tols(fac, trace)
     prior = prior_amplifications(fac, trace)
@@ -246,6 +250,10 @@ def test_skeletons_and_blocks_match_oracle(case):
 
 def test_final_sketches_match_oracle(case):
     pr, fac, f, _, trace = case
+    _check_sketches(pr, fac, f, trace)
+
+
+def _check_sketches(pr, fac, f, trace):
     Y, Z, Om, Ps = f.sketches()
     fin = fac.final
     tol = block_tol(fac, trace)
@@ -255,6 +263,30 @@ def test_final_sketches_match_oracle(case):
         worst = max(worst, e)
         assert e < tol
     print(f"{pr.name}: final sketches agree to {worst:.2e} (tolerance {tol:.1e})")
+
+
+@pytest.mark.parametrize("name", ["rand2d_3000", "rand3d_1500", "collinear2d"])
+def test_ozaki_fp64_sampling_matches_oracle(R, name):
+    """FP64 builds whose sampling product runs by the Ozaki scheme (sample_kernel 3: exact bf16
+    digit products, FP64-accurate) against the oracle, under the same checks as the FP64 SIMT
+    product: skeletons and blocks within the case's derived tolerances, the final sketches, solves
+    to 1e-10; a refinement then reaches the dense solution with the build's own digit store."""
+    pr = CASES[name]()
+    trace = []
+    _, _, fac, _ = orsrs.build(pr, trace=trace)
+    t = R.Tree(pr.points, pr.leaf)
+    f = R.Factor(t, R.kind_of(pr.kernel), pr.k, fac.s, shift=pr.diag_shift, scale=pr.scale, precision=0,
+                 omega=pr.omega(fac.s), psi=pr.psi(fac.s), keep_sketches=True, sample_kernel=3)
+    _check_blocks(pr, fac, f, trace)
+    _check_sketches(pr, fac, f, trace)
+    b = pr.rhs()
+    x = _from_gpu(f.solve(_to_gpu(b)))
+    assert _rel(x, orsrs.solve(fac, b)) < 1e-10
+    X = torch.zeros_like(_to_gpu(b))
+    rep = f.refine(_to_gpu(b), X, rtol=1e-13, maxit=30)
+    assert rep.rel_residual <= 1e-13 and rep.residual_kind == R.RSRS_RESIDUAL_OZAKI
+    xd = np.linalg.solve(ops.make_operator(pr).dense(), b)
+    assert _rel(_from_gpu(X), xd) < 1e-11
 
 
 def test_solve_apply_match_oracle(case):
