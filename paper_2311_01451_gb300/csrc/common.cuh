@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "../../include/rsrs.h"
@@ -65,6 +66,23 @@ struct Seg {
 };
 
 // ---- launch wrappers (defined in kernels.cu) --------------------------------
+// Runs f once per device: kernel attributes (dynamic shared memory, cluster sizes) belong to a
+// device's context, so a process that launches on several devices sets them on each.
+struct PerDeviceOnce {
+  static constexpr int kDevices = 64;
+  std::once_flag flags[kDevices];
+  template <class F>
+  void operator()(F&& f) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevices) {
+      (void)cudaGetLastError();
+      f();
+      return;
+    }
+    std::call_once(flags[dev], f);
+  }
+};
+
 struct Launch {
   cudaStream_t st;
   int64_t* counter;  // kernels launched (for stats), may be null

@@ -956,11 +956,8 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_chol_diag_tc(GroupArgs g, int p
 template <class Job>
 void launch_job(Launch L, const GroupArgs& g, const Job& job, int64_t items) {
   if (items <= 0) return;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_tc_grouped<Job>, cudaFuncAttributeMaxDynamicSharedMemorySize, GSMEM);
-    attr = true;
-  }
+  static PerDeviceOnce attr;
+  attr([] { cudaFuncSetAttribute(k_tc_grouped<Job>, cudaFuncAttributeMaxDynamicSharedMemorySize, GSMEM); });
   k_tc_grouped<Job><<<(unsigned)items, GTHREADS, GSMEM, L.st>>>(g, job);
   if (L.counter) ++*L.counter;
 }
@@ -1025,11 +1022,8 @@ void launch_proj_acc_tc(Launch L, const GroupArgs& g, int pass, const std::vecto
 void launch_chol_tc(Launch L, const GroupArgs& g, const std::vector<BoxDesc>& h) {
   int64_t nbmax = 0;
   for (const BoxDesc& d : h) nbmax = std::max<int64_t>(nbmax, cdiv128(d.l));
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_chol_diag_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, DSMEM);
-    attr = true;
-  }
+  static PerDeviceOnce attr;
+  attr([] { cudaFuncSetAttribute(k_chol_diag_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, DSMEM); });
   // left-looking: column block p takes all earlier panels in one product (K = 128 p), then its
   // diagonal block is factored and inverted and the blocks below it are scaled
   for (int p = 0; p < (int)nbmax; ++p) {

@@ -2193,14 +2193,13 @@ void launch_chol_panel(Launch L, const GroupArgs& g, int panel) {
 }
 void launch_chol_trsm(Launch L, const GroupArgs& g, int panel, int64_t items) {
   if (items <= 0) return;
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  attr([] {
     cudaFuncSetAttribute(k_chol_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(2 * TB * (TB + 1) * sizeof(double)));
     cudaFuncSetAttribute(k_chol_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(2 * TB * (TB + 1) * sizeof(float)));
-    attr = true;
-  }
+  });
   if (g.fp32) k_chol_trsm<float><<<grid1(items), NT, 2 * TB * (TB + 1) * sizeof(float), L.st>>>(g, panel);
   else k_chol_trsm<double><<<grid1(items), NT, 2 * TB * (TB + 1) * sizeof(double), L.st>>>(g, panel);
   count_launch(L);
@@ -2260,12 +2259,11 @@ static size_t cpqr32_smem(int max_b, int cs, int C) {
 constexpr size_t kCpqr32MaxSmem = 220 * 1024;
 bool launch_cpqr32(Launch L, const GroupArgs& g, int max_b, int cluster, int threads) {
   const int64_t c = 2 * g.s;
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  attr([] {
     cudaFuncSetAttribute(k_cpqr32_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaFuncSetAttribute(k_cpqr32_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCpqr32MaxSmem);
-    attr = true;
-  }
+  });
   auto slice = [c](int q) { return (int)((cdiv(c, q) + 3) / 4 * 4); };
   // smallest cluster whose shared memory holds the slices; otherwise 16 CTAs on slices in place
   int C = 16, in_global = 1;
@@ -2348,8 +2346,8 @@ bool launch_gj_inv32(Launch L, const GroupArgs& g, int max_r) {
   if (max_r > GJ_MAX_R) return false;
   if (max_r <= 0 || g.nbox <= 0) return true;
   const size_t smem = gj_smem_bytes(max_r);
-  static std::once_flag attr;
-  std::call_once(attr, [] {
+  static PerDeviceOnce attr;
+  attr([] {
     cudaFuncSetAttribute(k_gj_inv32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gj_smem_bytes(GJ_MAX_R));
   });
   k_gj_inv32<<<(unsigned)g.nbox, 1024, smem, L.st>>>(g);

@@ -581,8 +581,8 @@ int64_t oz_scratch_bytes(int64_t n) {
 void launch_oz_matvec(Launch L, int64_t n, int d, const void* store, double shift, double scale, const double* in,
                       int64_t ld_in, double* out, int64_t ld_out, int64_t ncols, void* scratch) {
   if (n <= 0 || ncols <= 0) return;
-  static std::once_flag attr;
-  std::call_once(attr, [] { cudaFuncSetAttribute(k_oz_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM); });
+  static PerDeviceOnce attr;
+  attr([] { cudaFuncSetAttribute(k_oz_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM); });
   const uint8_t* base = static_cast<const uint8_t*>(store);
   const int* row_exp = reinterpret_cast<const int*>(base + oz_rowexp_off(n));
   int* err = oz_status_word(const_cast<void*>(store), n, d);

@@ -439,8 +439,8 @@ bool launch_variant(cudaStream_t st, int kind, const float* p32, int64_t n, doub
     return false;
   using C = Tile<TN, KT, NST, RH>;
   constexpr int SMEM = C::SMEM_BYTES;
-  static std::once_flag attr;
-  std::call_once(attr, [] {
+  static PerDeviceOnce attr;
+  attr([] {
     cudaFuncSetAttribute(k_kmv_tc<RSRS_OP_LOG2D, 2, TN, KT, NST, RH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          SMEM);
     cudaFuncSetAttribute(k_kmv_tc<RSRS_OP_INVR3D, 3, TN, KT, NST, RH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
