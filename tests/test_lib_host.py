@@ -178,3 +178,14 @@ def test_residual_arithmetic_validated_before_device_work(R, mode):
     with pytest.raises(R.RSRSError) as e:
         R.Factor(t, R.RSRS_OP_LOG2D, 32, t.info(32).s_req, shift=1.0, scale=1 / 4096, residual=mode)
     assert e.value.name == "RSRS_E_INVAL"
+
+
+@pytest.mark.parametrize("kernel,precision", [(4, 0), (-1, 0), (3, 1)])
+def test_sample_kernel_validated_before_device_work(R, kernel, precision):
+    """sample_kernel out of range, and the Ozaki FP64 sampling (3) asked of a mixed build, are
+    refused with RSRS_E_INVAL before any device work."""
+    t = R.Tree(W.grid_points_2d(64), 64)
+    with pytest.raises(R.RSRSError) as e:
+        R.Factor(t, R.RSRS_OP_LOG2D, 32, t.info(32).s_req_mixed, shift=1.0, scale=1 / 4096, precision=precision,
+                 sample_kernel=kernel)
+    assert e.value.name == "RSRS_E_INVAL"
